@@ -1,0 +1,814 @@
+/*
+ * mra_oracle.c -- TEST INFRASTRUCTURE, NOT PART OF THE LIBRARY.
+ *
+ * A plain, slow, FP64 CPU restatement of what the GPU library computes:
+ * projection of a Gaussian sum onto the Legendre scaling-function basis,
+ * the trapezoid Gaussian fit of 1/r and exp(-mu r)/r, the 1-D operator
+ * blocks, the norm screen and the separated operator apply by direct
+ * summation.  Every routine follows the paper (Harrison et al., "MADNESS: A
+ * Multiresolution, Adaptive Numerical Environment for Scientific Simulation",
+ * arXiv 1507.01888) section or equation it cites.  It shares no code, header,
+ * table or constant with the CUDA library; only the tests, the smoke check and
+ * the benchmark's CPU-baseline leg load it.
+ *
+ * Conventions (the same readings the library documents):
+ *   cell [-L, L]^3, level n has 2^n boxes per dimension of width h_n = 2L/2^n;
+ *   box key = level<<57 | x<<38 | y<<19 | z  (19 bits per translation);
+ *   coefficient tensor s[ix][iy][iz], ix slowest, k^3 doubles per box;
+ *   phi_i(x) = sqrt(2i+1) P_i(2x-1) on (0,1)                (Sec. 2.1, eq. scalingfunc)
+ *   phi^n_{b,i}(x) = h_n^{-1/2} phi_i((x+L)/h_n - b)         (Sec. 2.1, scaled to the cell)
+ *
+ * Compiled with -ffp-contract=off so that no FMA contraction happens here.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846264338327950288
+#define ORC_MAXK 32
+#define GLQ 20 /* points per panel in the composite Gauss-Legendre rules */
+
+/* ------------------------------------------------------------------------ */
+/* Legendre polynomials and Gauss-Legendre nodes                             */
+/* ------------------------------------------------------------------------ */
+
+/* P_0..P_{n-1}(x) by the three-term recurrence (n+1)P_{n+1} = (2n+1)xP_n - nP_{n-1}. */
+static void legendre_upto(int n, double x, double *p) {
+  if (n <= 0) return;
+  p[0] = 1.0;
+  if (n == 1) return;
+  p[1] = x;
+  for (int m = 1; m + 1 < n; ++m)
+    p[m + 1] = ((2.0 * m + 1.0) * x * p[m] - (double)m * p[m - 1]) / (m + 1.0);
+}
+
+/* Scaling functions phi_i(x) = sqrt(2i+1) P_i(2x-1), i < k, for x in [0,1]
+ * (Sec. 2.1, eq. scalingfunc).  Outside [0,1] they are zero. */
+void orc_phi_all(int k, double x, double *out) {
+  if (x < 0.0 || x > 1.0) {
+    for (int i = 0; i < k; ++i) out[i] = 0.0;
+    return;
+  }
+  double p[ORC_MAXK];
+  legendre_upto(k, 2.0 * x - 1.0, p);
+  for (int i = 0; i < k; ++i) out[i] = sqrt(2.0 * i + 1.0) * p[i];
+}
+
+/* n-point Gauss-Legendre rule on [-1,1]: Newton iteration on P_n from the
+ * usual cosine starting guesses; weights 2/((1-x^2) P_n'(x)^2). */
+void orc_gauss_legendre(int n, double *x, double *w) {
+  for (int i = 0; i < n; ++i) {
+    double z = cos(ORC_PI * (i + 0.75) / (n + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int m = 1; m < n; ++m) {
+        double p2 = ((2.0 * m + 1.0) * z * p1 - (double)m * p0) / (m + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) { p1 = z; p0 = 1.0; }
+      /* p1 = P_n(z), p0 = P_{n-1}(z) */
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-17) break;
+    }
+    {
+      double p0 = 1.0, p1 = z;
+      for (int m = 1; m < n; ++m) {
+        double p2 = ((2.0 * m + 1.0) * z * p1 - (double)m * p0) / (m + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) { p1 = z; p0 = 1.0; }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+    }
+    x[n - 1 - i] = z;
+    w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+static double GLX[GLQ], GLW[GLQ];
+static int gl_ready = 0;
+static void gl_init(void) {
+  if (!gl_ready) {
+    orc_gauss_legendre(GLQ, GLX, GLW);
+    gl_ready = 1;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Graded composite quadrature of a Gaussian against the scaling functions   */
+/* ------------------------------------------------------------------------ */
+
+static int cmp_double(const void *a, const void *b) {
+  double x = *(const double *)a, y = *(const double *)b;
+  return (x > y) - (x < y);
+}
+
+/* Break points on [a,b] graded geometrically away from the peak p (in [a,b])
+ * with first width delta, and no panel wider than 1/8.  Returns count. */
+static int graded_breaks(double a, double b, double p, double delta, double *bp, int cap) {
+  int n = 0;
+  bp[n++] = a;
+  bp[n++] = b;
+  if (p > a && p < b && n < cap) bp[n++] = p;
+  for (double d = delta; n + 2 < cap; d *= 2.0) {
+    int added = 0;
+    if (p + d < b) { bp[n++] = p + d; added = 1; }
+    if (p - d > a) { bp[n++] = p - d; added = 1; }
+    if (!added) break;
+  }
+  qsort(bp, n, sizeof(double), cmp_double);
+  /* subdivide wide gaps uniformly */
+  int m = n;
+  for (int i = 0; i + 1 < n; ++i) {
+    double gap = bp[i + 1] - bp[i];
+    int pieces = (int)ceil(gap / 0.125);
+    for (int q = 1; q < pieces && m < cap; ++q) bp[m++] = bp[i] + gap * q / pieces;
+  }
+  qsort(bp, m, sizeof(double), cmp_double);
+  int u = 0;
+  for (int i = 0; i < m; ++i)
+    if (u == 0 || bp[i] > bp[u - 1]) bp[u++] = bp[i];
+  return u;
+}
+
+/* out[j] = int_0^1 exp(-T (u-uc)^2) phi_j(u) du, j < k, with uc = base + x
+ * (base an integer, so that the distance from uc to the nearer end of [0,1]
+ * is formed without cancellation).
+ * The integrand is negligible (below e^-46 of its maximum on [0,1]) outside
+ * |u-uc| <= sqrt(dmin^2 + 46/T), dmin = dist(uc,[0,1]); inside, composite
+ * 20-point Gauss-Legendre panels graded from the point p of [0,1] closest to
+ * uc.  Nodes are placed by their offset from p, and u - uc = off + (p - uc). */
+static void gauss_phi_integral(int k, double T, double base, double x, double *out) {
+  gl_init();
+  for (int j = 0; j < k; ++j) out[j] = 0.0;
+  double uc = base + x;
+  double p, e; /* peak point in [0,1] and e = p - uc */
+  if (uc <= 0.0) { p = 0.0; e = (0.0 - base) - x; }
+  else if (uc >= 1.0) { p = 1.0; e = (1.0 - base) - x; }
+  else { p = uc; e = 0.0; }
+  double dmin = fabs(e);
+  double a = 0.0, b = 1.0, delta;
+  if (T > 0.0) {
+    double W = sqrt(dmin * dmin + 46.0 / T);
+    /* the relevant interval around uc, intersected with [0,1] */
+    if (p - e - W > a) a = p - e - W;
+    if (p - e + W < b) b = p - e + W;
+    if (a >= b) return;
+    double s1 = 1.0 / sqrt(T);
+    double s2 = dmin > 0.0 ? 1.0 / (2.0 * T * dmin) : s1;
+    delta = (s1 < s2 ? s1 : s2) / 16.0;
+  } else {
+    delta = 0.125;
+  }
+  if (p < a) p = a;
+  if (p > b) p = b;
+  double bp[512];
+  /* break points as offsets from p */
+  int nb = graded_breaks(a - p, b - p, 0.0, delta, bp, 512);
+  double ph[ORC_MAXK];
+  double epk = (p - uc); /* equals e unless p was moved onto the relevant interval */
+  if (p == 0.0 || p == 1.0) epk = e;
+  for (int q = 0; q + 1 < nb; ++q) {
+    double lo = bp[q], hi = bp[q + 1], half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
+    for (int g = 0; g < GLQ; ++g) {
+      double off = mid + half * GLX[g];
+      double w = off + epk;
+      double ex = exp(-T * w * w) * half * GLW[g];
+      orc_phi_all(k, p + off, ph);
+      for (int j = 0; j < k; ++j) out[j] += ex * ph[j];
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Two-scale matrices (Sec. 2.2: P^{n+1} = P^n + Q^n)                        */
+/* ------------------------------------------------------------------------ */
+
+/* U^{(c)}[i][j] = 2^{-1/2} int_0^1 phi_i(y) phi_j((y+c)/2) dy: the level-(n+1)
+ * coefficient i, in child c, of the level-n scaling function j. */
+void orc_two_scale(int k, double *U0, double *U1) {
+  int nq = k + 2;
+  double x[64], w[64], pi_[ORC_MAXK], pj[ORC_MAXK];
+  orc_gauss_legendre(nq, x, w);
+  for (int c = 0; c < 2; ++c) {
+    double *U = c == 0 ? U0 : U1;
+    for (int i = 0; i < k * k; ++i) U[i] = 0.0;
+    for (int q = 0; q < nq; ++q) {
+      double y = 0.5 * (x[q] + 1.0), wy = 0.5 * w[q];
+      orc_phi_all(k, y, pi_);
+      orc_phi_all(k, 0.5 * (y + c), pj);
+      for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) U[i * k + j] += wy * pi_[i] * pj[j] / sqrt(2.0);
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gaussian fit of the kernel (Sec. 2.3)                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Trapezoid rule with step h from s_lo on
+ *   exp(-mu r)/r = (2/sqrt(pi)) int exp(-r^2 e^{2s} - mu^2 e^{-2s}/4 + s) ds
+ * (mu = 0 is the 1/r identity printed in Sec. 2.3):
+ *   c_m = (2/sqrt(pi)) h exp(s_m - mu^2 e^{-2 s_m}/4),  t_m = e^{2 s_m}. */
+void orc_fit_coeffs(double mu, int M, double h, double s_lo, double *c, double *t) {
+  for (int m = 0; m < M; ++m) {
+    double s = s_lo + m * h;
+    c[m] = 2.0 / sqrt(ORC_PI) * h * exp(s - mu * mu * exp(-2.0 * s) / 4.0);
+    t[m] = exp(2.0 * s);
+  }
+}
+
+static double fit_r_point(double r_lo, double r_hi, int p, int npts) {
+  return r_lo * pow(r_hi / r_lo, (double)p / (double)(npts - 1));
+}
+
+/* max over npts log-spaced r in [r_lo, r_hi] of |sum c e^{-t r^2} - K(r)| / K(r). */
+double orc_fit_maxerr(double mu, int M, const double *c, const double *t, double r_lo, double r_hi,
+                      int npts) {
+  double worst = 0.0;
+  for (int p = 0; p < npts; ++p) {
+    double r = fit_r_point(r_lo, r_hi, p, npts);
+    double K = exp(-mu * r) / r, sum = 0.0;
+    for (int m = 0; m < M; ++m) sum += c[m] * exp(-t[m] * r * r);
+    double e = fabs(sum - K) / K;
+    if (e > worst) worst = e;
+  }
+  return worst;
+}
+
+/* Grid search: h = (5+i)/100, i = 0..115 (0.05..1.20); s_lo = (j-100)/4,
+ * j = 0..112 (-25..3).  Minimise the max relative error on 3000 log-spaced
+ * points; the first strict minimum in (i, j) order wins, so ties go to the
+ * smaller h. */
+int orc_fit_search(double mu, int M, double r_lo, double r_hi, double *h_out, double *slo_out,
+                   double *err_out, int nthreads) {
+  const int NH = 116, NS = 113, NP = 3000;
+  double *errs = (double *)malloc(sizeof(double) * NH * NS);
+  if (!errs) return -1;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic)
+#endif
+  for (int cand = 0; cand < NH * NS; ++cand) {
+    int i = cand / NS, j = cand % NS;
+    double h = (5.0 + i) / 100.0, s_lo = (j - 100.0) / 4.0;
+    double c[512], t[512];
+    orc_fit_coeffs(mu, M, h, s_lo, c, t);
+    errs[cand] = orc_fit_maxerr(mu, M, c, t, r_lo, r_hi, NP);
+  }
+  int best = 0;
+  for (int cand = 1; cand < NH * NS; ++cand)
+    if (errs[cand] < errs[best]) best = cand;
+  *h_out = (5.0 + best / NS) / 100.0;
+  *slo_out = (best % NS - 100.0) / 4.0;
+  *err_out = errs[best];
+  free(errs);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Operator blocks (Sec. 2.2 Toeplitz property, Sec. 2.3 separated form)     */
+/* ------------------------------------------------------------------------ */
+
+/* R[i][j] = h int_0^1 du phi_i(u) int_0^1 dv phi_j(v) exp(-T (u - v + l)^2),
+ * the 1-D block connecting source box b to target box b+l at a level of
+ * width h for one Gaussian exp(-t x^2), T = t h^2.  Iterated (u outer,
+ * v inner) composite Gauss-Legendre; the outer panels are graded around the
+ * points where the Gaussian ridge u - v + l = 0 enters or leaves the square. */
+void orc_block(int k, double h, double T, long l, double *R) {
+  gl_init();
+  for (int i = 0; i < k * k; ++i) R[i] = 0.0;
+  /* The ridge v = u + l meets v=0 at u=-l and v=1 at u=1-l.  Each of the two
+   * points, clamped to [0,1], anchors graded outer panels whose nodes are
+   * placed by their offset from the anchor (u = anchor + off, and the inner
+   * integral receives u + l = (anchor + l) + off with anchor + l an integer). */
+  double pts[2] = {(double)-l, 1.0 - (double)l};
+  double anc[2], dl[2];
+  for (int q = 0; q < 2; ++q) {
+    double p = pts[q];
+    dl[q] = p < 0.0 ? -p : (p > 1.0 ? p - 1.0 : 0.0);
+    anc[q] = p < 0.0 ? 0.0 : (p > 1.0 ? 1.0 : p);
+  }
+  int nseg = (anc[0] == anc[1]) ? 1 : 2;
+  double G[ORC_MAXK], ph[ORC_MAXK];
+  for (int sg = 0; sg < nseg; ++sg) {
+    double A = anc[sg], d = dl[sg];
+    if (nseg == 1 && dl[1] < d) d = dl[1];
+    /* segment of [0,1] served by this anchor */
+    double lo_u = 0.0, hi_u = 1.0;
+    if (nseg == 2) {
+      double m = 0.5 * (anc[0] + anc[1]);
+      if (A <= m) hi_u = m; else lo_u = m;
+    }
+    double delta;
+    if (T > 0.0) {
+      double s1 = 1.0 / sqrt(T);
+      double s2 = d > 0.0 ? 1.0 / (2.0 * T * d) : s1;
+      delta = (s1 < s2 ? s1 : s2) / 16.0;
+    } else {
+      delta = 0.125;
+    }
+    double bp[512];
+    int nb = graded_breaks(lo_u - A, hi_u - A, 0.0, delta, bp, 512);
+    double base = A + (double)l;
+    for (int q = 0; q + 1 < nb; ++q) {
+      double lo = bp[q], hi = bp[q + 1], half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
+      for (int g = 0; g < GLQ; ++g) {
+        double off = mid + half * GLX[g];
+        gauss_phi_integral(k, T, base, off, G);
+        orc_phi_all(k, A + off, ph);
+        double wq = h * half * GLW[g];
+        for (int i = 0; i < k; ++i)
+          for (int j = 0; j < k; ++j) R[i * k + j] += wq * ph[i] * G[j];
+      }
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Keys                                                                      */
+/* ------------------------------------------------------------------------ */
+
+static uint64_t make_key(int n, long x, long y, long z) {
+  return ((uint64_t)n << 57) | ((uint64_t)x << 38) | ((uint64_t)y << 19) | (uint64_t)z;
+}
+static void split_key(uint64_t key, int *n, long *x, long *y, long *z) {
+  *n = (int)(key >> 57);
+  *x = (long)((key >> 38) & 0x7FFFF);
+  *y = (long)((key >> 19) & 0x7FFFF);
+  *z = (long)(key & 0x7FFFF);
+}
+static int cmp_u64(const void *a, const void *b) {
+  uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+  return (x > y) - (x < y);
+}
+static long find_key(const uint64_t *keys, long n, uint64_t key) {
+  long lo = 0, hi = n - 1;
+  while (lo <= hi) {
+    long mid = (lo + hi) / 2;
+    if (keys[mid] == key) return mid;
+    if (keys[mid] < key) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return -1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Projection (Sec. 2.1, eq. projection, and the adaptive refinement text)   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int ng;
+  const double *coef, *expnt, *cx, *cy, *cz;
+} orc_gsum;
+
+/* s^n_b = int f phi^n_b, exactly (to quadrature rounding), for the Gaussian
+ * sum f = sum_g coef_g exp(-a_g |x - c_g|^2); separable per Gaussian:
+ * s[ix][iy][iz] = sum_g coef_g X_g[ix] Y_g[iy] Z_g[iz] with
+ * X_g[i] = h^{1/2} int_0^1 exp(-a_g h^2 (u - uc)^2) phi_i(u) du. */
+static void project_box(const orc_gsum *f, int k, double L, int n, long bx, long by, long bz,
+                        double *s) {
+  double h = 2.0 * L / (double)(1L << n);
+  double sh = sqrt(h);
+  double X[ORC_MAXK], Y[ORC_MAXK], Z[ORC_MAXK];
+  int k3 = k * k * k;
+  for (int i = 0; i < k3; ++i) s[i] = 0.0;
+  for (int g = 0; g < f->ng; ++g) {
+    double a = f->expnt[g], T = a * h * h;
+    gauss_phi_integral(k, T, (double)-bx, (f->cx[g] + L) / h, X);
+    gauss_phi_integral(k, T, (double)-by, (f->cy[g] + L) / h, Y);
+    gauss_phi_integral(k, T, (double)-bz, (f->cz[g] + L) / h, Z);
+    double cf = f->coef[g] * sh * sh * sh;
+    for (int ix = 0; ix < k; ++ix)
+      for (int iy = 0; iy < k; ++iy)
+        for (int iz = 0; iz < k; ++iz) s[(ix * k + iy) * k + iz] += cf * X[ix] * Y[iy] * Z[iz];
+  }
+}
+
+typedef struct {
+  uint64_t key;
+  long idx;
+} keyidx;
+static int cmp_keyidx(const void *a, const void *b) {
+  uint64_t x = ((const keyidx *)a)->key, y = ((const keyidx *)b)->key;
+  return (x > y) - (x < y);
+}
+
+/* Projection onto a uniform level (uniform_level >= 0) or adaptive refinement:
+ * start from every box at level init_level-1 as a parent; project the parent
+ * and its 8 children exactly; d = s_children - U s_parent (two-scale, tensor
+ * product); if ||d||_F <= thresh, or the children are at max_level, the
+ * children become leaves, else every child becomes a parent.  Output keys are
+ * sorted ascending.  min_margin = min |(||d|| - thresh)/thresh| over the
+ * refinement decisions that were not forced by max_level. */
+int orc_project(int ng, const double *coef, const double *expnt, const double *cx,
+                const double *cy, const double *cz, int k, double L, double thresh, int init_level,
+                int max_level, int uniform_level, long cap, uint64_t *keys, double *coeffs,
+                long *n_out, double *min_margin, int nthreads) {
+  orc_gsum f = {ng, coef, expnt, cx, cy, cz};
+  int k3 = k * k * k;
+  if (k < 1 || k > ORC_MAXK) return -1;
+  gl_init(); /* before any parallel region */
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+  *min_margin = INFINITY;
+  if (uniform_level >= 0) {
+    long nb = 1L << uniform_level, total = nb * nb * nb;
+    if (total > cap) return -2;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic)
+#endif
+    for (long b = 0; b < total; ++b) {
+      long bx = b / (nb * nb), by = (b / nb) % nb, bz = b % nb;
+      keys[b] = make_key(uniform_level, bx, by, bz);
+      project_box(&f, k, L, uniform_level, bx, by, bz, coeffs + b * k3);
+    }
+    *n_out = total;
+    return 0;
+  }
+  if (init_level < 1 || max_level < init_level || max_level > 19) return -1;
+  double U[2][ORC_MAXK * ORC_MAXK];
+  orc_two_scale(k, U[0], U[1]);
+  /* parent list at level init_level-1 */
+  int pl = init_level - 1;
+  long np = 1L << (3 * pl);
+  uint64_t *par = (uint64_t *)malloc(sizeof(uint64_t) * (np > 0 ? np : 1));
+  for (long b = 0; b < np; ++b) {
+    long nb = 1L << pl;
+    par[b] = make_key(pl, b / (nb * nb), (b / nb) % nb, b % nb);
+  }
+  long nleaf = 0;
+  int err = 0;
+  double margin = INFINITY;
+  while (np > 0 && !err) {
+    uint64_t *next = (uint64_t *)malloc(sizeof(uint64_t) * 8 * np);
+    char *refine = (char *)malloc(np);
+    double *child = (double *)malloc(sizeof(double) * 8 * k3 * np);
+    double *pmarg = (double *)malloc(sizeof(double) * np);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic)
+#endif
+    for (long p = 0; p < np; ++p) {
+      int n;
+      long x, y, z;
+      split_key(par[p], &n, &x, &y, &z);
+      double *sp = (double *)malloc(sizeof(double) * k3);
+      double *t1 = (double *)malloc(sizeof(double) * k3);
+      double *t2 = (double *)malloc(sizeof(double) * k3);
+      project_box(&f, k, L, n, x, y, z, sp);
+      double dn2 = 0.0;
+      for (int c = 0; c < 8; ++c) {
+        int cxb = (c >> 2) & 1, cyb = (c >> 1) & 1, czb = c & 1;
+        double *sc = child + ((long)p * 8 + c) * k3;
+        project_box(&f, k, L, n + 1, 2 * x + cxb, 2 * y + cyb, 2 * z + czb, sc);
+        /* (U^{cx} x U^{cy} x U^{cz}) s_parent, one mode at a time */
+        for (int ix = 0; ix < k; ++ix)
+          for (int jy = 0; jy < k; ++jy)
+            for (int jz = 0; jz < k; ++jz) {
+              double acc = 0.0;
+              for (int jx = 0; jx < k; ++jx)
+                acc += U[cxb][ix * k + jx] * sp[(jx * k + jy) * k + jz];
+              t1[(ix * k + jy) * k + jz] = acc;
+            }
+        for (int ix = 0; ix < k; ++ix)
+          for (int iy = 0; iy < k; ++iy)
+            for (int jz = 0; jz < k; ++jz) {
+              double acc = 0.0;
+              for (int jy = 0; jy < k; ++jy)
+                acc += U[cyb][iy * k + jy] * t1[(ix * k + jy) * k + jz];
+              t2[(ix * k + iy) * k + jz] = acc;
+            }
+        for (int ix = 0; ix < k; ++ix)
+          for (int iy = 0; iy < k; ++iy)
+            for (int iz = 0; iz < k; ++iz) {
+              double acc = 0.0;
+              for (int jz = 0; jz < k; ++jz)
+                acc += U[czb][iz * k + jz] * t2[(ix * k + iy) * k + jz];
+              double d = sc[(ix * k + iy) * k + iz] - acc;
+              dn2 += d * d;
+            }
+      }
+      double dn = sqrt(dn2);
+      int forced = (n + 1 >= max_level);
+      refine[p] = (!forced && dn > thresh) ? 1 : 0;
+      pmarg[p] = forced ? INFINITY : fabs(dn - thresh) / thresh;
+      free(sp);
+      free(t1);
+      free(t2);
+    }
+    long nn = 0;
+    for (long p = 0; p < np; ++p) {
+      if (pmarg[p] < margin) margin = pmarg[p];
+      int n;
+      long x, y, z;
+      split_key(par[p], &n, &x, &y, &z);
+      for (int c = 0; c < 8; ++c) {
+        int cxb = (c >> 2) & 1, cyb = (c >> 1) & 1, czb = c & 1;
+        uint64_t ck = make_key(n + 1, 2 * x + cxb, 2 * y + cyb, 2 * z + czb);
+        if (refine[p]) {
+          next[nn++] = ck;
+        } else {
+          if (nleaf >= cap) { err = -2; break; }
+          keys[nleaf] = ck;
+          memcpy(coeffs + nleaf * k3, child + ((long)p * 8 + c) * k3, sizeof(double) * k3);
+          ++nleaf;
+        }
+      }
+      if (err) break;
+    }
+    free(refine);
+    free(child);
+    free(pmarg);
+    free(par);
+    par = next;
+    np = nn;
+  }
+  free(par);
+  if (err) return err;
+  /* sort leaves by key */
+  keyidx *ki = (keyidx *)malloc(sizeof(keyidx) * (nleaf > 0 ? nleaf : 1));
+  for (long i = 0; i < nleaf; ++i) { ki[i].key = keys[i]; ki[i].idx = i; }
+  qsort(ki, nleaf, sizeof(keyidx), cmp_keyidx);
+  double *tmp = (double *)malloc(sizeof(double) * k3 * (nleaf > 0 ? nleaf : 1));
+  for (long i = 0; i < nleaf; ++i) {
+    keys[i] = ki[i].key;
+    memcpy(tmp + i * k3, coeffs + ki[i].idx * k3, sizeof(double) * k3);
+  }
+  memcpy(coeffs, tmp, sizeof(double) * k3 * nleaf);
+  free(tmp);
+  free(ki);
+  *n_out = nleaf;
+  *min_margin = margin;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Separated operator apply by direct summation (Sec. 2.3)                   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int n, D;        /* level, max |l_d| */
+  double h;
+  double *R;       /* [M][2D+1][k*k] */
+  double *N;       /* [M][2D+1] Frobenius norms */
+} level_blocks;
+
+/* Result: for every source box b (level n), every displacement l in D(b) with
+ * b+l inside the cell, and every Gaussian term mu that passes the screen
+ *   B = |c_mu| * ||R^n_{mu,lx}||_F ||R^n_{mu,ly}||_F ||R^n_{mu,lz}||_F * ||s_b||_F >= tau,
+ *   r_{n,b+l}[ix iy iz] += c_mu sum_j Rx[ix][jx] Ry[iy][jy] Rz[iz][jz] s_b[jx jy jz]
+ * with the three mode products done one after another (Sec. 2.3).
+ * D(b): stencil=1 -> all |l|_inf <= min(1, 2^n-1); stencil=0 -> shells
+ * d = 0,1,2,... of |l|_inf up to min(max_disp, 2^n-1), stopping after the
+ * first shell in which no term is kept.
+ * If n_sample > 0 only the destination keys listed in sample_keys that are in
+ * the destination set are computed (in that order, skipping the others).
+ * Per destination: out_bound = sum of B over kept terms, out_marginal = sum of
+ * B over terms whose B is within 1e-9 relative of tau (decisions that rounding
+ * could flip).  stats: [0] (source,l) pairs with a kept term, [1] kept terms,
+ * [2] screened terms (within D(b)), [3] sources whose last allowed shell still
+ * kept terms (truncated by max_disp). */
+int orc_apply(int k, double L, long n_in, const uint64_t *keys, const double *coeffs, int M,
+              const double *c, const double *t, int stencil, int max_disp, double tau,
+              long n_sample, const uint64_t *sample_keys, long cap, uint64_t *out_keys,
+              double *out_coeffs, double *out_bound, double *out_marginal, long *n_out,
+              long *stats, int nthreads) {
+  int k2 = k * k, k3 = k * k * k;
+  if (k < 1 || k > ORC_MAXK || M < 1) return -1;
+  gl_init(); /* before any parallel region */
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+  for (long i = 1; i < n_in; ++i)
+    if (keys[i] <= keys[i - 1]) return -1; /* input keys must be sorted and unique */
+  /* levels present */
+  int present[20] = {0};
+  for (long i = 0; i < n_in; ++i) {
+    int n = (int)(keys[i] >> 57);
+    if (n > 19) return -1;
+    present[n] = 1;
+  }
+  level_blocks lb[20];
+  memset(lb, 0, sizeof(lb));
+  for (int n = 0; n < 20; ++n) {
+    if (!present[n]) continue;
+    long nb = 1L << n;
+    int D = stencil == 1 ? 1 : max_disp;
+    if (D > nb - 1) D = (int)(nb - 1);
+    if (D < 0) D = 0;
+    lb[n].n = n;
+    lb[n].D = D;
+    lb[n].h = 2.0 * L / (double)nb;
+    int nl = 2 * D + 1;
+    lb[n].R = (double *)malloc(sizeof(double) * (size_t)M * nl * k2);
+    lb[n].N = (double *)malloc(sizeof(double) * (size_t)M * nl);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic)
+#endif
+    for (int q = 0; q < M * nl; ++q) {
+      int mu = q / nl, li = q % nl;
+      double *R = lb[n].R + (size_t)q * k2;
+      double h = lb[n].h;
+      orc_block(k, h, t[mu] * h * h, (long)(li - D), R);
+      double s = 0.0;
+      for (int i = 0; i < k2; ++i) s += R[i] * R[i];
+      lb[n].N[q] = sqrt(s);
+    }
+  }
+  /* source norms and shell radii */
+  double *snorm = (double *)malloc(sizeof(double) * (n_in > 0 ? n_in : 1));
+  int *dstop = (int *)malloc(sizeof(int) * (n_in > 0 ? n_in : 1));
+  long truncated = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic) reduction(+ : truncated)
+#endif
+  for (long b = 0; b < n_in; ++b) {
+    const double *s = coeffs + b * k3;
+    double a = 0.0;
+    for (int i = 0; i < k3; ++i) a += s[i] * s[i];
+    snorm[b] = sqrt(a);
+    int n;
+    long x, y, z;
+    split_key(keys[b], &n, &x, &y, &z);
+    long nb = 1L << n;
+    int D = lb[n].D, nl = 2 * D + 1;
+    if (stencil == 1) {
+      dstop[b] = D + 1;
+      continue;
+    }
+    int d;
+    for (d = 0; d <= D; ++d) {
+      int kept = 0;
+      for (int lx = -d; lx <= d && !kept; ++lx)
+        for (int ly = -d; ly <= d && !kept; ++ly)
+          for (int lz = -d; lz <= d && !kept; ++lz) {
+            int m = abs(lx) > abs(ly) ? abs(lx) : abs(ly);
+            if (abs(lz) > m) m = abs(lz);
+            if (m != d) continue;
+            if (x + lx < 0 || x + lx >= nb || y + ly < 0 || y + ly >= nb || z + lz < 0 ||
+                z + lz >= nb)
+              continue;
+            for (int mu = 0; mu < M && !kept; ++mu) {
+              double B = fabs(c[mu]) * lb[n].N[mu * nl + lx + D] * lb[n].N[mu * nl + ly + D] *
+                         lb[n].N[mu * nl + lz + D] * snorm[b];
+              if (B >= tau) kept = 1;
+            }
+          }
+      if (!kept) break;
+    }
+    dstop[b] = d; /* shells 0..d-1 are in D(b) */
+    if (d == D + 1) truncated += 1;
+  }
+  /* destination set */
+  long maxd = 0;
+  for (long b = 0; b < n_in; ++b) {
+    long w = 2L * dstop[b] - 1;
+    if (w > 0) maxd += w * w * w;
+  }
+  uint64_t *dest = (uint64_t *)malloc(sizeof(uint64_t) * (maxd > 0 ? maxd : 1));
+  long nd = 0;
+  for (long b = 0; b < n_in; ++b) {
+    int n;
+    long x, y, z;
+    split_key(keys[b], &n, &x, &y, &z);
+    long nb = 1L << n;
+    int D = lb[n].D, nl = 2 * D + 1, r = dstop[b] - 1;
+    for (int lx = -r; lx <= r; ++lx)
+      for (int ly = -r; ly <= r; ++ly)
+        for (int lz = -r; lz <= r; ++lz) {
+          if (x + lx < 0 || x + lx >= nb || y + ly < 0 || y + ly >= nb || z + lz < 0 ||
+              z + lz >= nb)
+            continue;
+          int any = 0;
+          for (int mu = 0; mu < M && !any; ++mu) {
+            double B = fabs(c[mu]) * lb[n].N[mu * nl + lx + D] * lb[n].N[mu * nl + ly + D] *
+                       lb[n].N[mu * nl + lz + D] * snorm[b];
+            if (B >= tau) any = 1;
+          }
+          if (any) dest[nd++] = make_key(n, x + lx, y + ly, z + lz);
+        }
+  }
+  qsort(dest, nd, sizeof(uint64_t), cmp_u64);
+  long nu = 0;
+  for (long i = 0; i < nd; ++i)
+    if (nu == 0 || dest[i] != dest[nu - 1]) dest[nu++] = dest[i];
+  /* which destinations to compute */
+  uint64_t *todo = dest;
+  long ntodo = nu;
+  uint64_t *sel = NULL;
+  if (n_sample > 0) {
+    sel = (uint64_t *)malloc(sizeof(uint64_t) * n_sample);
+    ntodo = 0;
+    for (long i = 0; i < n_sample; ++i)
+      if (find_key(dest, nu, sample_keys[i]) >= 0) sel[ntodo++] = sample_keys[i];
+    todo = sel;
+  }
+  if (ntodo > cap) {
+    *n_out = ntodo; /* tell the caller how much room is needed */
+    free(dest); free(sel); free(snorm); free(dstop);
+    for (int n = 0; n < 20; ++n) { free(lb[n].R); free(lb[n].N); }
+    return -2;
+  }
+  long pairs = 0, kept_terms = 0, screened = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic) reduction(+ : pairs, kept_terms, screened)
+#endif
+  for (long di = 0; di < ntodo; ++di) {
+    int n;
+    long x, y, z;
+    split_key(todo[di], &n, &x, &y, &z);
+    long nb = 1L << n;
+    int D = lb[n].D, nl = 2 * D + 1;
+    double *r = out_coeffs + di * k3;
+    double *t1 = (double *)malloc(sizeof(double) * k3);
+    double *t2 = (double *)malloc(sizeof(double) * k3);
+    for (int i = 0; i < k3; ++i) r[i] = 0.0;
+    double bsum = 0.0, msum = 0.0;
+    for (int lx = -D; lx <= D; ++lx)
+      for (int ly = -D; ly <= D; ++ly)
+        for (int lz = -D; lz <= D; ++lz) {
+          long sx = x - lx, sy = y - ly, sz = z - lz;
+          if (sx < 0 || sx >= nb || sy < 0 || sy >= nb || sz < 0 || sz >= nb) continue;
+          long b = find_key(keys, n_in, make_key(n, sx, sy, sz));
+          if (b < 0) continue;
+          int m = abs(lx) > abs(ly) ? abs(lx) : abs(ly);
+          if (abs(lz) > m) m = abs(lz);
+          if (m >= dstop[b]) continue;
+          const double *s = coeffs + b * k3;
+          int any = 0;
+          for (int mu = 0; mu < M; ++mu) {
+            const double *Rx = lb[n].R + ((size_t)mu * nl + lx + D) * k2;
+            const double *Ry = lb[n].R + ((size_t)mu * nl + ly + D) * k2;
+            const double *Rz = lb[n].R + ((size_t)mu * nl + lz + D) * k2;
+            double B = fabs(c[mu]) * lb[n].N[mu * nl + lx + D] * lb[n].N[mu * nl + ly + D] *
+                       lb[n].N[mu * nl + lz + D] * snorm[b];
+            if (!(B >= tau)) {
+              screened += 1;
+              continue;
+            }
+            any = 1;
+            kept_terms += 1;
+            bsum += B;
+            if (tau > 0.0 && fabs(B - tau) <= 1e-9 * tau) msum += B;
+            /* t1 = s x_1 Rx */
+            for (int ix = 0; ix < k; ++ix)
+              for (int jy = 0; jy < k; ++jy)
+                for (int jz = 0; jz < k; ++jz) {
+                  double acc = 0.0;
+                  for (int jx = 0; jx < k; ++jx) acc += Rx[ix * k + jx] * s[(jx * k + jy) * k + jz];
+                  t1[(ix * k + jy) * k + jz] = acc;
+                }
+            /* t2 = t1 x_2 Ry */
+            for (int ix = 0; ix < k; ++ix)
+              for (int iy = 0; iy < k; ++iy)
+                for (int jz = 0; jz < k; ++jz) {
+                  double acc = 0.0;
+                  for (int jy = 0; jy < k; ++jy)
+                    acc += Ry[iy * k + jy] * t1[(ix * k + jy) * k + jz];
+                  t2[(ix * k + iy) * k + jz] = acc;
+                }
+            /* r += c_mu (t2 x_3 Rz) */
+            for (int ix = 0; ix < k; ++ix)
+              for (int iy = 0; iy < k; ++iy)
+                for (int iz = 0; iz < k; ++iz) {
+                  double acc = 0.0;
+                  for (int jz = 0; jz < k; ++jz)
+                    acc += Rz[iz * k + jz] * t2[(ix * k + iy) * k + jz];
+                  r[(ix * k + iy) * k + iz] += c[mu] * acc;
+                }
+          }
+          if (any) pairs += 1;
+        }
+    out_keys[di] = todo[di];
+    if (out_bound) out_bound[di] = bsum;
+    if (out_marginal) out_marginal[di] = msum;
+    free(t1);
+    free(t2);
+  }
+  *n_out = ntodo;
+  if (stats) {
+    stats[0] = pairs;
+    stats[1] = kept_terms;
+    stats[2] = screened;
+    stats[3] = truncated;
+  }
+  free(dest);
+  free(sel);
+  free(snorm);
+  free(dstop);
+  for (int n = 0; n < 20; ++n) {
+    free(lb[n].R);
+    free(lb[n].N);
+  }
+  return 0;
+}

@@ -1,0 +1,354 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with itself: each check is a library routine
+(numpy / scipy / mpmath), a closed form, an invariant, the paper's printed
+worked-example values (Sec. 3.1), or a brute-force integral on a tiny case.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+mpmath = pytest.importorskip("mpmath")
+
+
+# ----------------------------------------------------------------- basis (Sec. 2.1)
+
+@pytest.mark.parametrize("n", [1, 2, 3, 6, 10, 14, 20, 30])
+def test_gauss_legendre_matches_numpy(n):
+    x, w = O.gauss_legendre(n)
+    xn, wn = np.polynomial.legendre.leggauss(n)
+    assert np.abs(x - xn).max() < 1e-14
+    assert np.abs(w - wn).max() < 1e-14
+
+
+@pytest.mark.parametrize("k", [1, 4, 10, 14])
+def test_phi_is_scaled_legendre_and_orthonormal(k):
+    xg, wg = np.polynomial.legendre.leggauss(k + 3)
+    u = 0.5 * (xg + 1.0)
+    P = np.stack([O.phi(k, ui) for ui in u])           # [q, i]
+    for i in range(k):
+        e = np.zeros(i + 1); e[i] = 1.0
+        ref = math.sqrt(2 * i + 1) * np.polynomial.legendre.legval(2 * u - 1, e)
+        assert np.abs(P[:, i] - ref).max() < 1e-12 * max(1.0, np.abs(ref).max())
+    G = (P * (0.5 * wg)[:, None]).T @ P
+    assert np.abs(G - np.eye(k)).max() < 1e-13
+    assert np.all(O.phi(k, -0.1) == 0) and np.all(O.phi(k, 1.1) == 0)
+
+
+@pytest.mark.parametrize("k", [2, 6, 10])
+def test_two_scale_orthogonality_and_reproduction(k):
+    U0, U1 = O.two_scale(k)
+    assert np.abs(U0.T @ U0 + U1.T @ U1 - np.eye(k)).max() < 1e-13
+    # a parent polynomial (degree < k) projected directly onto each child
+    rng = np.random.default_rng(k)
+    sp = rng.standard_normal(k)
+    xg, wg = np.polynomial.legendre.leggauss(2 * k)
+    for c, U in enumerate((U0, U1)):
+        y = 0.5 * (xg + 1)
+        direct = np.zeros(k)
+        for q in range(len(y)):
+            parent_val = O.phi(k, 0.5 * (y[q] + c)) @ sp          # unnormalised parent-local value
+            direct += 0.5 * wg[q] * parent_val * O.phi(k, y[q]) / math.sqrt(2.0)
+        assert np.abs(U @ sp - direct).max() < 1e-13
+
+
+# ----------------------------------------------------------------- fit (Sec. 2.3)
+
+def _mp_maxerr(mu, c, t, r_lo, r_hi, npts=10000):
+    mpmath.mp.dps = 30
+    worst = mpmath.mpf(0)
+    rs = np.exp(np.linspace(math.log(r_lo), math.log(r_hi), npts))
+    cs = [mpmath.mpf(float(x)) for x in c]
+    ts = [mpmath.mpf(float(x)) for x in t]
+    for r in rs[::7]:
+        r = mpmath.mpf(float(r))
+        K = mpmath.exp(-mu * r) / r
+        s = mpmath.fsum(ci * mpmath.exp(-ti * r * r) for ci, ti in zip(cs, ts))
+        worst = max(worst, abs(s - K) / K)
+    return float(worst)
+
+
+def test_integral_identities_sec23():
+    """r^{-1} = 2/sqrt(pi) int exp(-r^2 e^{2s} + s) ds (Sec. 2.3), and its BSH generalisation
+    exp(-mu r)/r = 2/sqrt(pi) int exp(-r^2 e^{2s} - mu^2 e^{-2s}/4 + s) ds."""
+    mpmath.mp.dps = 20
+    for r in (1e-3, 0.5, 3.0):
+        for mu in (0.0, 0.5, 1.0):
+            f = lambda s: mpmath.exp(-r * r * mpmath.exp(2 * s) - mu * mu * mpmath.exp(-2 * s) / 4 + s)
+            # the integrand is below e^-50 of its peak outside [-60, 14] for these r
+            val = 2 / mpmath.sqrt(mpmath.pi) * mpmath.quad(f, mpmath.linspace(-60, 14, 38))
+            assert abs(val - mpmath.exp(-mu * r) / r) < 1e-15 * mpmath.exp(-mu * r) / r
+
+
+def test_fit_coefficients_are_the_trapezoid_rule():
+    c, t = O.fit_coeffs(0.7, 5, 0.3, -2.0)
+    for m in range(5):
+        s = -2.0 + 0.3 * m
+        assert t[m] == pytest.approx(math.exp(2 * s), rel=1e-15)
+        assert c[m] == pytest.approx(2 / math.sqrt(math.pi) * 0.3 * math.exp(s - 0.49 * math.exp(-2 * s) / 4),
+                                     rel=1e-14)
+
+
+@pytest.mark.parametrize("mu,M,r_hi", [(0.0, 20, 64.0), (1.0, 60, math.log(1e6)), (0.0, 60, 12.0)])
+def test_fit_error_matches_extended_precision(mu, M, r_hi):
+    h, s_lo, err, c, t = O.fit_search(mu, M, 1e-4, r_hi)
+    ref = _mp_maxerr(mu, c, t, 1e-4, r_hi)
+    # 3000-point FP64 estimate and a 1430-point extended-precision estimate agree
+    assert 0.8 * err <= ref <= 1.05 * err
+    # the surveyed error level at the literal term counts
+    assert err < {20: 2.5e-2, 60: 1e-4}[M] if M in (20, 60) and mu in (0.0, 1.0) and r_hi > 12 else True
+
+
+def test_fit_error_decreases_and_reaches_eps():
+    """M = O(log R log 1/eps) (Sec. 2.3): more terms -> smaller error; 100 terms reach 1e-6 on [1e-4, 12]."""
+    errs = [O.fit_search(0.0, M, 1e-4, 12.0)[2] for M in (40, 60, 80, 100)]
+    assert all(a > b for a, b in zip(errs, errs[1:]))
+    assert errs[-1] < 1e-6
+
+
+# ----------------------------------------------------------------- blocks (Sec. 2.2 / 2.3)
+
+def _mp_R00(h, T, l):
+    """h int_{-1}^{1} (1-|z|) exp(-T (z+l)^2) dz in erf/exp form (enough digits for the
+    cancellation between erf values near 1 at far displacements)."""
+    mpmath.mp.dps = 160
+    T = mpmath.mpf(T); l = mpmath.mpf(l)
+    st = mpmath.sqrt(T)
+    I = lambda a, b: mpmath.sqrt(mpmath.pi) / (2 * st) * (mpmath.erf(st * (b + l)) - mpmath.erf(st * (a + l)))
+    J = lambda a, b: (mpmath.exp(-T * (a + l) ** 2) - mpmath.exp(-T * (b + l) ** 2)) / (2 * T) - l * I(a, b)
+    return float(h * (I(-1, 0) + J(-1, 0) + I(0, 1) - J(0, 1)))
+
+
+@pytest.mark.parametrize("T", [1e-3, 0.1, 1.0, 7.0, 50.0, 1e3, 1e6, 1e10])
+@pytest.mark.parametrize("l", [0, 1, -1, 2, 5])
+def test_block_R00_closed_form(T, l):
+    h = 1.7
+    R = O.block(4, h, T, l)
+    ref = _mp_R00(h, T, l)
+    if ref < 1e-290:
+        assert abs(R[0, 0]) < 1e-280
+    else:
+        assert abs(R[0, 0] - ref) <= 1e-13 * abs(ref)
+
+
+def test_block_R00_at_zero_closed_form():
+    """R_00(0) = h[sqrt(pi/T) erf(sqrt T) - (1-e^{-T})/T]."""
+    mpmath.mp.dps = 40
+    for T in (0.3, 2.0, 40.0):
+        ref = 2.0 * (mpmath.sqrt(mpmath.pi / T) * mpmath.erf(mpmath.sqrt(T)) - (1 - mpmath.exp(-T)) / T)
+        assert O.block(3, 2.0, T, 0)[0, 0] == pytest.approx(float(ref), rel=1e-14)
+
+
+@pytest.mark.parametrize("T,l", [(0.5, 0), (3.0, 1), (3.0, -2), (200.0, 1), (2e3, 0)])
+def test_block_general_entries_vs_mpmath(T, l):
+    k, h = 3, 0.8
+    mpmath.mp.dps = 25
+    R = O.block(k, h, T, l)
+    leg = [lambda x: 1, lambda x: math.sqrt(3) * (2 * x - 1), lambda x: math.sqrt(5) * (6 * x * x - 6 * x + 1)]
+    for i in range(k):
+        for j in range(k):
+            # split the outer integral where the ridge u-v+l=0 meets the square's edges
+            pts = sorted(set([0, 1] + [p for p in (-l, 1 - l) if 0 < p < 1]))
+            def inner(u):
+                vc = u + l
+                vpts = sorted(set([0, 1] + ([vc] if 0 < vc < 1 else [])))
+                return mpmath.quad(lambda v: leg[j](v) * mpmath.exp(-T * (u - v + l) ** 2), vpts)
+            val = h * mpmath.quad(lambda u: leg[i](u) * inner(u), pts)
+            scale = max(abs(R).max(), 1e-300)
+            assert abs(R[i, j] - float(val)) <= 1e-12 * scale
+
+
+def test_block_symmetries_and_sum_rule():
+    k, h, T = 6, 1.3, 2.5
+    S = np.array([[(-1) ** (i + j) for j in range(k)] for i in range(k)])
+    tot = 0.0
+    for l in range(-12, 13):
+        Rl, Rm = O.block(k, h, T, l), O.block(k, h, T, -l)
+        assert np.abs(Rl - S * Rm).max() <= 1e-14 * max(np.abs(Rl).max(), 1e-300)
+        assert np.abs(Rl - Rm.T).max() <= 1e-14 * max(np.abs(Rl).max(), 1e-300)
+        tot += Rl[0, 0]
+    assert tot == pytest.approx(h * math.sqrt(math.pi / T), rel=1e-13)
+
+
+def test_block_limits():
+    k, h = 5, 2.0
+    R = O.block(k, h, 1e-9, 0)
+    E = np.zeros((k, k)); E[0, 0] = 1.0
+    assert np.abs(R - h * E).max() < 1e-8
+    T = 1e9
+    R = O.block(k, h, T, 0)
+    assert np.abs(math.sqrt(T / math.pi) * R / h - np.eye(k)).max() < 1e-3
+
+
+# ----------------------------------------------------------------- projection (eq. projection)
+
+def test_projection_1d_factor_vs_mpmath():
+    """Single box, single Gaussian: s[i,j,k] = coef X_i Y_j Z_k with X_i = int_box e^{-a(x-c)^2} phi_i dx."""
+    k, L, lev = 4, 4.0, 2
+    g = {"coef": np.array([1.3]), "expnt": np.array([3.0]), "cx": np.array([0.4]), "cy": np.array([-1.1]),
+         "cz": np.array([2.2])}
+    keys, s, _ = O.project(g, k, L, uniform_level=lev)
+    n, x, y, z = O.split_keys(keys)
+    h = 2 * L / 2 ** lev
+    mpmath.mp.dps = 30
+    b = int(np.where((x == 2) & (y == 1) & (z == 3))[0][0])
+    def fac(cc, bb):
+        return [float(mpmath.sqrt(h) * mpmath.quad(
+            lambda u: mpmath.exp(-3.0 * (h * (u + bb) - L - cc) ** 2) *
+            math.sqrt(2 * i + 1) * mpmath.legendre(i, 2 * u - 1), [0, 1])) for i in range(k)]
+    X, Y, Z = fac(0.4, 2), fac(-1.1, 1), fac(2.2, 3)
+    ref = 1.3 * np.einsum("i,j,k->ijk", X, Y, Z)
+    assert np.abs(s[b] - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_projection_trace_and_norm_closed_forms():
+    """Unit-charge Gaussians well inside the cell: sum_b s_b[000] h^{3/2} = 1 per Gaussian; on a
+    resolved adaptive tree sum ||s_b||^2 -> ||f||^2 = sum_gg' cc' (pi/(a+a'))^{3/2} e^{-aa'/(a+a')|c-c'|^2}."""
+    f = W.gaussian_sum(3, 0.5, 5.0, seed=11, centre_box=10.0)
+    keys, s, marg = O.project(f, 8, 32.0, thresh=1e-9, init_level=2, max_level=12)
+    n, *_ = O.split_keys(keys)
+    h = 64.0 / 2.0 ** n
+    assert (s[:, 0, 0, 0] * h ** 1.5).sum() == pytest.approx(3.0, rel=1e-13)
+    a, c = f["expnt"], np.stack([f["cx"], f["cy"], f["cz"]], 1)
+    co = f["coef"]
+    ref = 0.0
+    for i in range(3):
+        for j in range(3):
+            p = a[i] + a[j]
+            ref += co[i] * co[j] * (math.pi / p) ** 1.5 * math.exp(-a[i] * a[j] / p * ((c[i] - c[j]) ** 2).sum())
+    assert (s ** 2).sum() == pytest.approx(ref, rel=1e-9)
+
+
+def test_paper_worked_example_trace_norm():
+    """Sec. 3.1: g = exp(-|x|^2) on [-6,6]^3; trace 5.5683279, norm 1.403104 (printed values)."""
+    keys, s, _ = O.project(W.paper_gaussian(), 10, 6.0, uniform_level=2)
+    h = 12.0 / 4
+    assert abs((s[:, 0, 0, 0] * h ** 1.5).sum() - 5.5683279) < 1e-7
+    assert abs(math.sqrt((s ** 2).sum()) - 1.403104) < 1e-6
+
+
+# ----------------------------------------------------------------- apply (Sec. 2.3, Sec. 3.1)
+
+def test_paper_worked_example_self_energy():
+    """Sec. 3.1, eq. gaussian-interaction: <g, |x-y|^{-1} * g> = pi^{5/2} sqrt(2) = 24.739429."""
+    L = 6.0
+    keys, s, _ = O.project(W.paper_gaussian(), 10, L, uniform_level=2)
+    _, _, err, c, t = O.fit_search(0.0, 100, 1e-4, 2 * L)
+    assert err < 1e-6
+    r = O.apply(keys, s, c, t, L, stencil=0, max_disp=3, tau=0.0)
+    assert (r.keys == keys).all()
+    E = float((r.coeffs * s).sum())
+    assert abs(E - 24.739429) < 1e-6 * 24.739429
+    assert E == pytest.approx(math.pi ** 2.5 * math.sqrt(2.0), rel=1e-6)
+
+
+def test_single_gaussian_term_closed_form():
+    """int e^{-t|x-y|^2} e^{-a|y-c|^2} dy = (pi/(t+a))^{3/2} e^{-(ta/(t+a))|x-c|^2} (Gaussian * Gaussian)."""
+    L, k, lev = 4.0, 10, 2
+    a, tt = 1.5, 0.8
+    cc = np.array([0.3, -0.2, 0.5])
+    f = {"coef": np.array([1.0]), "expnt": np.array([a]), "cx": cc[:1], "cy": cc[1:2], "cz": cc[2:]}
+    keys, s, _ = O.project(f, k, L, uniform_level=lev)
+    r = O.apply(keys, s, np.array([1.0]), np.array([tt]), L, stencil=0, max_disp=3, tau=0.0)
+    g = {"coef": np.array([(math.pi / (tt + a)) ** 1.5]), "expnt": np.array([tt * a / (tt + a)]),
+         "cx": cc[:1], "cy": cc[1:2], "cz": cc[2:]}
+    k2, s2, _ = O.project(g, k, L, uniform_level=lev)
+    assert (k2 == r.keys).all()
+    err = np.sqrt(((r.coeffs - s2) ** 2).sum() / (s2 ** 2).sum())
+    assert err < 1e-7
+
+
+def test_apply_adjoint_and_linear():
+    L, k, lev = 8.0, 5, 2
+    f = W.gaussian_sum(2, 0.3, 3.0, seed=5, centre_box=4.0)
+    g = W.gaussian_sum(2, 0.3, 3.0, seed=6, centre_box=4.0)
+    kf, sf, _ = O.project(f, k, L, uniform_level=lev)
+    kg, sg, _ = O.project(g, k, L, uniform_level=lev)
+    c, t = O.fit_coeffs(0.0, 12, 0.6, -3.0)
+    Tf = O.apply(kf, sf, c, t, L, stencil=0, max_disp=3, tau=0.0)
+    Tg = O.apply(kg, sg, c, t, L, stencil=0, max_disp=3, tau=0.0)
+    lhs, rhs = (sg * Tf.coeffs).sum(), (Tg.coeffs * sf).sum()
+    assert lhs == pytest.approx(rhs, rel=1e-13)
+    Tfg = O.apply(kf, 2.5 * sf + sg, c, t, L, stencil=0, max_disp=3, tau=0.0)
+    assert np.abs(Tfg.coeffs - (2.5 * Tf.coeffs + Tg.coeffs)).max() < 1e-12 * np.abs(Tfg.coeffs).max()
+
+
+def test_apply_translation_by_whole_boxes():
+    """Toeplitz (Sec. 2.2): moving the input by one box moves the output by one box."""
+    k, L, lev = 4, 8.0, 3
+    keys, s = W.random_tree_coeffs(6, k, lev, seed=3)
+    n, x, y, z = O.split_keys(keys)
+    keep = (x >= 1) & (x <= 5) & (y >= 1) & (y <= 5) & (z >= 1) & (z <= 5)
+    keys, s, x, y, z = keys[keep], s[keep], x[keep], y[keep], z[keep]
+    shifted = O.make_key(lev, 0, 0, 0) | ((x + 1).astype(np.uint64) << np.uint64(38)) | \
+        (y.astype(np.uint64) << np.uint64(19)) | z.astype(np.uint64)
+    order = np.argsort(shifted)
+    c, t = O.fit_coeffs(0.0, 6, 0.8, -2.0)
+    r0 = O.apply(keys, s, c, t, L, stencil=1, tau=0.0)
+    r1 = O.apply(shifted[order], s[order], c, t, L, stencil=1, tau=0.0)
+    n0, x0, y0, z0 = O.split_keys(r0.keys)
+    inner = (x0 + 1 <= 7)
+    want = O.make_key(lev, 0, 0, 0) | ((x0[inner] + 1).astype(np.uint64) << np.uint64(38)) | \
+        (y0[inner].astype(np.uint64) << np.uint64(19)) | z0[inner].astype(np.uint64)
+    pos = np.searchsorted(r1.keys, want)
+    assert (r1.keys[pos] == want).all()
+    assert np.abs(r1.coeffs[pos] - r0.coeffs[inner]).max() < 1e-14 * np.abs(r0.coeffs).max()
+
+
+def test_apply_brute_force_6d():
+    """Tiny tree (level 1, k=2, one Gaussian term): r_{b'}[i] = int_{b'} phi_i(x) int e^{-t|x-y|^2} f(y) dy dx,
+    evaluated as a plain 6-D tensor Gauss-Legendre sum over box pairs (no separation)."""
+    k, L, lev, tt = 2, 1.0, 1, 0.7
+    keys, s = W.random_tree_coeffs(8, k, lev, seed=9)
+    r = O.apply(keys, s, np.array([1.0]), np.array([tt]), L, stencil=1, tau=0.0)
+    h = 2 * L / 2 ** lev
+    xg, wg = np.polynomial.legendre.leggauss(14)
+    u, wu = 0.5 * (xg + 1), 0.5 * wg
+    ph = np.stack([np.ones_like(u), math.sqrt(3) * (2 * u - 1)], 1) / math.sqrt(h)  # [q, i] scaled
+    _, bx, by, bz = O.split_keys(keys)
+    pos = lambda b: -L + h * (b + u)                                             # [q]
+    for d, dk in enumerate(r.keys):
+        _, dx, dy, dz = O.split_keys(np.array([dk]))
+        X = [pos(dx[0]), pos(dy[0]), pos(dz[0])]
+        acc = np.zeros((k, k, k))
+        for b in range(len(keys)):
+            Y = [pos(bx[b]), pos(by[b]), pos(bz[b])]
+            # f on source quadrature grid: f(y) = sum_j s_b[j] phi_j(y)
+            fy = np.einsum("abc,pa,qb,rc->pqr", s[b], ph, ph, ph)
+            K = [np.exp(-tt * (X[e][:, None] - Y[e][None, :]) ** 2) for e in range(3)]  # [p_x, q_y]
+            # brute 6-D sum: sum_{x,y} w_x w_y phi_i(x) K(x-y) f(y) (h^3 Jacobians for both boxes)
+            wK = [K[e] * (wu[:, None] * wu[None, :]) * h * h for e in range(3)]
+            full = np.einsum("ap,bq,cr,pqr->abc", wK[0], wK[1], wK[2], fy)               # [x grid]
+            acc += np.einsum("abc,ai,bj,ck->ijk", full, ph, ph, ph)
+        assert np.abs(r.coeffs[d] - acc).max() < 1e-12 * max(np.abs(acc).max(), 1e-300)
+
+
+def test_screen_bound_dominates_true_term_norm():
+    """Every kept term's norm is below its bound B = |c| prod ||R_d||_F ||s||_F."""
+    k, L, lev = 5, 16.0, 3
+    keys, s = W.random_tree_coeffs(20, k, lev, seed=4)
+    c, t = O.fit_coeffs(0.0, 10, 0.7, -3.0)
+    h = 2 * L / 2 ** lev
+    rng = np.random.default_rng(0)
+    for _ in range(30):
+        b = rng.integers(len(keys)); mu = rng.integers(len(c)); l = rng.integers(-1, 2, size=3)
+        R = [O.block(k, h, t[mu] * h * h, int(li)) for li in l]
+        term = c[mu] * np.einsum("ai,bj,ck,ijk->abc", R[0], R[1], R[2], s[b])
+        B = abs(c[mu]) * np.prod([np.linalg.norm(Ri) for Ri in R]) * np.linalg.norm(s[b])
+        assert np.linalg.norm(term) <= B * (1 + 1e-14)
+
+
+def test_screen_and_shells_on_adaptive_tree():
+    """Shell enumeration with the norm screen: every kept term has B >= tau; raising tau keeps fewer."""
+    f = W.gaussian_sum(2, 1.0, 100.0, seed=21, centre_box=10.0)
+    keys, s, _ = O.project(f, 6, 32.0, thresh=1e-4, init_level=2, max_level=8)
+    c, t = O.fit_coeffs(0.0, 20, 0.9, -8.0)
+    r1 = O.apply(keys, s, c, t, 32.0, stencil=0, max_disp=2, tau=1e-6)
+    r2 = O.apply(keys, s, c, t, 32.0, stencil=0, max_disp=2, tau=1e-4)
+    assert r2.terms < r1.terms
+    assert r1.terms > 0 and r1.screened > 0
+    assert np.all(r1.bound > 0)

@@ -1,0 +1,127 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle checks.
+
+This module only draws random numbers and names workload shapes.  It holds
+none of the method's arithmetic (no projection, fit, block or apply code), so
+the CUDA library and the CPU oracle can both be fed from it without sharing
+any computation.
+
+Every function is a sum of normalised (unit-charge) Gaussians
+    f(x) = sum_g (a_g/pi)^{3/2} exp(-a_g |x - c_g|^2)
+in the cell [-L, L]^3 with L = 32, exponents log-uniform in a stated range and
+centres uniform in [-20, 20]^3.  They stand in for the molecular densities and
+orbitals the paper applies its operators to (Sec. 3.2-3.4); the paper measures
+on no public data set.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+L_CELL = 32.0
+POISSON = 0
+BSH = 1
+
+
+def gaussian_sum(n: int, a_lo: float, a_hi: float, seed: int, centre_box: float = 20.0) -> dict:
+    """n unit-charge Gaussians, a ~ log-uniform[a_lo, a_hi], centres ~ U[-centre_box, centre_box]^3."""
+    rng = np.random.default_rng(seed)
+    a = np.exp(rng.uniform(np.log(a_lo), np.log(a_hi), size=n))
+    c = rng.uniform(-centre_box, centre_box, size=(n, 3))
+    return {
+        "coef": (a / np.pi) ** 1.5,
+        "expnt": a,
+        "cx": c[:, 0].copy(),
+        "cy": c[:, 1].copy(),
+        "cz": c[:, 2].copy(),
+    }
+
+
+def paper_gaussian() -> dict:
+    """g(x) = exp(-|x|^2), the worked example of Sec. 3.1 (cell [-6, 6]^3)."""
+    return {"coef": np.array([1.0]), "expnt": np.array([1.0]), "cx": np.zeros(1), "cy": np.zeros(1),
+            "cz": np.zeros(1)}
+
+
+@dataclass
+class Workload:
+    name: str
+    funcs: list            # list of gaussian-sum dicts
+    k: int
+    L: float
+    thresh: float           # projection threshold (adaptive) or 0
+    uniform_level: int      # -1 = adaptive
+    kernel: int             # POISSON / BSH
+    mu: float
+    M: int                  # Gaussian terms
+    fit_eps: float          # requested fit accuracy (sets the BSH range)
+    stencil: int            # 1 = 27 nearest, 0 = shells
+    max_disp: int
+    tau: float              # screen threshold (0 = no screen)
+    init_level: int = 2
+    max_level: int = 19
+    extra: dict = field(default_factory=dict)
+
+
+def poisson_m20_uniform_k6() -> Workload:
+    """Plain FP64 Poisson apply: 3 Gaussians a~logU[10,1e3], uniform level 3 (512 boxes), k=6,
+    1/r as 20 Gaussians on [1e-4, 2L], 27 nearest displacements, no screen."""
+    return Workload("poisson_m20_uniform_l3_k6", [gaussian_sum(3, 10.0, 1e3, seed=1)], k=6, L=L_CELL,
+                    thresh=0.0, uniform_level=3, kernel=POISSON, mu=0.0, M=20, fit_eps=1e-4, stencil=1,
+                    max_disp=1, tau=0.0)
+
+
+def bsh_m60_adaptive_k10() -> Workload:
+    """Mixed-precision BSH apply: 8 Gaussians a~logU[1,1e4], adaptive k=10, thresh 1e-6,
+    exp(-r)/r as 60 Gaussians, screen tau = 0.01*thresh within |l|_inf <= 1."""
+    return Workload("bsh_m60_adaptive_k10", [gaussian_sum(8, 1.0, 1e4, seed=2)], k=10, L=L_CELL,
+                    thresh=1e-6, uniform_level=-1, kernel=BSH, mu=1.0, M=60, fit_eps=1e-6, stencil=0,
+                    max_disp=1, tau=1e-8)
+
+
+def poisson_batched_64() -> Workload:
+    """Batched Poisson apply: 64 functions (seeds 3000..3063) of 1-16 Gaussians a~logU[1,1e3],
+    k=8, thresh 1e-5, 1/r as 40 Gaussians."""
+    rng = np.random.default_rng(3)
+    counts = rng.integers(1, 17, size=64)
+    funcs = [gaussian_sum(int(counts[i]), 1.0, 1e3, seed=3000 + i) for i in range(64)]
+    return Workload("poisson_batched64_k8", funcs, k=8, L=L_CELL, thresh=1e-5, uniform_level=-1,
+                    kernel=POISSON, mu=0.0, M=40, fit_eps=1e-5, stencil=0, max_disp=1, tau=1e-7)
+
+
+def bsh_learned_k10() -> Workload:
+    """Learned-screen BSH apply: 32 Gaussians a~logU[1,1e4], k=10, thresh 1e-7, mu=0.5, M=80."""
+    return Workload("bsh_m80_adaptive_k10_learned", [gaussian_sum(32, 1.0, 1e4, seed=4)], k=10, L=L_CELL,
+                    thresh=1e-7, uniform_level=-1, kernel=BSH, mu=0.5, M=80, fit_eps=1e-7, stencil=0,
+                    max_disp=1, tau=1e-9)
+
+
+def poisson_k14_large() -> Workload:
+    """Full-size Poisson apply: 64 Gaussians a~logU[1,1e6], k=14, thresh 1e-8, M=100."""
+    return Workload("poisson_m100_adaptive_k14", [gaussian_sum(64, 1.0, 1e6, seed=5)], k=14, L=L_CELL,
+                    thresh=1e-8, uniform_level=-1, kernel=POISSON, mu=0.0, M=100, fit_eps=1e-8, stencil=0,
+                    max_disp=1, tau=1e-10)
+
+
+WORKLOADS = {
+    "poisson_m20_uniform_l3_k6": poisson_m20_uniform_k6,
+    "bsh_m60_adaptive_k10": bsh_m60_adaptive_k10,
+    "poisson_batched64_k8": poisson_batched_64,
+    "bsh_m80_adaptive_k10_learned": bsh_learned_k10,
+    "poisson_m100_adaptive_k14": poisson_k14_large,
+}
+
+
+def random_tree_coeffs(n_boxes: int, k: int, level: int, seed: int, fill: float = 1.0):
+    """Random sorted box keys at one level and N(0,1) coefficients, for parity tests.
+    fill in (0,1]: fraction of the 8^level boxes present (drawn without replacement)."""
+    rng = np.random.default_rng(seed)
+    nb = 1 << level
+    total = nb ** 3
+    m = min(n_boxes, total)
+    idx = np.sort(rng.choice(total, size=m, replace=False)) if m < total else np.arange(total)
+    x, y, z = idx // (nb * nb), (idx // nb) % nb, idx % nb
+    keys = (np.uint64(level) << np.uint64(57)) | (x.astype(np.uint64) << np.uint64(38)) | \
+        (y.astype(np.uint64) << np.uint64(19)) | z.astype(np.uint64)
+    coeffs = rng.standard_normal((m, k, k, k))
+    return keys.astype(np.uint64), coeffs
