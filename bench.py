@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Benchmark of the separated Gaussian-sum operator apply (boxes/s and roofline fraction).
+
+A step is one mra_apply of the whole hot path -- source norms, norm screen and
+work list, sort on the destination key, the gather-apply kernel -- over the
+resident input tree of the workload (default: BSH exp(-r)/r as 60 Gaussians,
+8 Gaussians a~logU[1,1e4], adaptive k=10, 17,200 boxes).  Setup (projection,
+fit, operator blocks) is outside the timed region.
+
+Arms:
+  default           the CUDA library through its C ABI (device-resident inputs);
+                    also an end-to-end figure with host buffers (H2D + apply + D2H)
+  --impl reference  the CPU oracle on this machine's cores, on a bounded seeded
+                    sample of destination boxes, extrapolated by kept-term count
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs an independent
+replica (the single-function apply does not shard) and value sums the ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "3D operator-apply boxes/s & % roofline, mixed vs FP64 GPU at 1e-6 rel L2"
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no FP64 figure in the measured peaks)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="bsh_m60_adaptive_k10", choices=sorted(W.WORKLOADS))
+    p.add_argument("--precision", choices=["auto", "fp64", "split"], default="auto")
+    p.add_argument("--pieces", type=int, default=3)
+    p.add_argument("--cpu-sample", type=int, default=150, help="destination boxes timed on the CPU")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def oracle_fit(w):
+    import oracle as O
+    r_lo, r_hi = O.kernel_range(w.kernel, w.mu, w.L, w.fit_eps)
+    return O.fit_search(w.mu if w.kernel == W.BSH else 0.0, w.M, r_lo, r_hi)
+
+
+def cpu_baseline(w, sample_n, seed=12345):
+    """The oracle, as it stands, on a seeded sample of destination boxes; whole-job time is
+    extrapolated from the sample's share of kept terms.  Returns a dict."""
+    import oracle as O
+    keys, coeffs, _ = O.project(w.funcs[0], w.k, w.L, thresh=w.thresh, init_level=w.init_level,
+                                max_level=w.max_level, uniform_level=w.uniform_level)
+    _, _, _, c, t = oracle_fit(w)
+    cores = os.cpu_count() or 1
+    stencil, tau = w.stencil, w.tau
+    # full destination set and total kept terms: run the screen with a never-matching sample
+    never = np.array([np.uint64(0xFFFFFFFFFFFFFFFF)], dtype=np.uint64)
+    t0 = time.perf_counter()
+    O.apply(keys, coeffs, c, t, w.L, stencil=stencil, max_disp=w.max_disp, tau=tau, sample_keys=never)
+    t_setup = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    sample = np.sort(rng.choice(keys, min(sample_n, len(keys)), replace=False))
+    t0 = time.perf_counter()
+    r = O.apply(keys, coeffs, c, t, w.L, stencil=stencil, max_disp=w.max_disp, tau=tau, sample_keys=sample)
+    t_sample = max(time.perf_counter() - t0 - t_setup, 1e-9)
+    return {"n_in": len(keys), "sample_dest": len(r.keys), "sample_terms": r.terms, "t_sample": t_sample,
+            "t_setup": t_setup, "cores": cores, "terms_total": r.terms_total, "dest_total": r.dest_total}
+
+
+def clocks_start():
+    try:
+        f = open(os.path.join(ROOT, "gpurun_out", "clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                 else os.devnull, "w")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "100"],
+                             stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        return p, f
+    except Exception:
+        return None, None
+
+
+def clocks_stop(handle, gpu_index):
+    p, f = handle
+    if p is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    p.terminate()
+    try:
+        out, _ = p.communicate(timeout=5)
+    except Exception:
+        p.kill()
+        out = ""
+    rows = []
+    for line in out.splitlines():
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9 or not parts[0].isdigit() or int(parts[0]) != gpu_index:
+            continue
+        rows.append(parts)
+        if f:
+            f.write(line + "\n")
+    if f:
+        f.close()
+    if not rows:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+    sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+    load = sorted(sm)[len(sm) // 2:] if sm else []
+    return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons, "samples": len(rows)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = W.WORKLOADS[args.workload]()
+    times = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        info = cpu_baseline(w, args.cpu_sample, seed=1000 + i)
+        if i >= args.warmup:
+            times.append(info)
+    per = [x["t_sample"] * x["terms_total"] / max(x["sample_terms"], 1) for x in times]
+    t_job = statistics.mean(per)
+    value = info["n_in"] / t_job
+    line = {"metric": METRIC, "value": value, "unit": "boxes/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_job * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": w.name, "n_boxes": info["n_in"], "k": w.k, "M": w.M},
+            "cpu_baseline": {"value": value, "unit": "boxes/s", "cores": info["cores"], "kind": "oracle",
+                             "sample": f"{args.cpu_sample} seeded destination boxes per step; job time "
+                                       f"extrapolated by kept terms ({info['terms_total']} in the job)"},
+            "e2e": {"value": value, "unit": "boxes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    from paper_1507_01888_gb300 import mra
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    w = W.WORKLOADS[args.workload]()
+    precision = args.precision
+    if precision == "auto":
+        precision = "split"
+    prec = mra.PREC_SPLIT_BF16 if precision == "split" else mra.PREC_FP64
+
+    # ---------------- setup (untimed): projection, operator, buffers
+    tree = mra.project(w.funcs[0], w.k, w.L, thresh=w.thresh, init_level=w.init_level, max_level=w.max_level,
+                       uniform_level=w.uniform_level)
+    keys_h, coeffs_h = tree.host()
+    levels = (keys_h >> np.uint64(57)).astype(int)
+    op = mra.Operator(w.kernel, w.M, w.k, w.L, int(levels.min()), int(levels.max()), max_disp=w.max_disp,
+                      mu=w.mu, fit_eps=w.fit_eps)
+    screen = mra.SCREEN_NORM if w.tau > 0 else mra.SCREEN_NONE
+    opts = mra.make_opts(precision=prec, pieces=args.pieces, screen=screen, tau=w.tau, stencil=w.stencil,
+                         max_disp=w.max_disp)
+    try:
+        ap = mra.Applier(op, tree, opts)
+        ap(tree)
+    except mra.MraError as e:
+        if prec == mra.PREC_SPLIT_BF16 and e.code == mra.MRA_ERR_UNSUPPORTED and args.precision == "auto":
+            prec, precision = mra.PREC_FP64, "fp64"
+            opts = mra.make_opts(precision=prec, screen=screen, tau=w.tau, stencil=w.stencil, max_disp=w.max_disp)
+            ap = mra.Applier(op, tree, opts)
+            ap(tree)
+        else:
+            raise
+    torch.cuda.synchronize()
+    st0 = ap.stats.as_dict()
+    k = w.k
+    flops_per_term = 6 * k ** 4 + k ** 3
+    # accuracy of the timed path against the FP64 GPU apply (same screen)
+    accuracy = {}
+    if prec != mra.PREC_FP64:
+        ref_ap = mra.Applier(op, tree, mra.make_opts(precision=mra.PREC_FP64, screen=screen, tau=w.tau,
+                                                     stencil=w.stencil, max_disp=w.max_disp))
+        ref_out = ref_ap(tree)
+        cmp = mra.compare(ap.out, ref_out)
+        accuracy = {"rel_l2_vs_fp64_gpu": cmp["rel_l2"], "max_box_rel_vs_fp64_gpu": cmp["max_box_rel"],
+                    "fp64_gpu_apply_ms": ref_ap.stats.kernel_ms}
+        del ref_out, ref_ap
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ap(tree, stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = clocks_start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kernel_ms = []
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        kernel_ms.append(ap.stats.kernel_ms)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = clocks_stop(clk, local)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    n_in = tree.n
+    value = world * n_in / (ms / 1e3)
+
+    # ---------------- end to end through the public API with host buffers
+    keys_pin = torch.from_numpy(keys_h.view(np.int64).copy()).pin_memory()
+    coeffs_pin = torch.from_numpy(coeffs_h.copy()).pin_memory()
+    dev_tree = mra.Tree(torch.empty_like(keys_pin, device=dev), torch.empty_like(coeffs_pin, device=dev),
+                        n_in, k, w.L)
+    n_out = ap.out.n
+    out_keys_pin = torch.empty(n_out, dtype=torch.int64).pin_memory()
+    out_coeffs_pin = torch.empty((n_out, k, k, k), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        dev_tree.keys.copy_(keys_pin, non_blocking=True)
+        dev_tree.coeffs.copy_(coeffs_pin, non_blocking=True)
+        out = ap(dev_tree, stream)
+        out_keys_pin.copy_(out.keys[:n_out], non_blocking=True)
+        out_coeffs_pin.copy_(out.coeffs[:n_out], non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e_ms = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        b.synchronize()
+        e_ms.append(a.elapsed_time(b))
+    e2e_val = world * n_in / (statistics.mean(e_ms) / 1e3)
+    h2d = keys_pin.numel() * 8 + coeffs_pin.numel() * 8
+    d2h = out_keys_pin.numel() * 8 + out_coeffs_pin.numel() * 8
+
+    # ---------------- roofline of the dominant kernel (the apply kernel)
+    pk, pk_kind = peaks()
+    kms = statistics.mean(kernel_ms)
+    terms = st0["terms_kept"]
+    achieved_tflops = terms * flops_per_term / (kms / 1e3) / 1e12
+    if prec == mra.PREC_FP64:
+        roof = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "apply_f64_kernel", "peak_source": "nominal GB300 FP64 rate (recipe table)",
+                "kernel_ms": kms}
+        dtype = "f64"
+        launches_per_step = 7
+    else:
+        peak = pk.get("bf16_tflops", 1856.3)
+        roof = {"bound": "tensor", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved_tflops / peak, "traffic": None, "kernel": "apply_split_kernel",
+                "peak_source": f"bf16 dense burst, {pk_kind}", "kernel_ms": kms,
+                "flops": "algorithmic (6k^4+k^3 per kept term)"}
+        dtype = f"bf16x{args.pieces}-split, f32 accumulate, f64 term sum"
+        launches_per_step = 8
+
+    line = {"metric": METRIC, "value": value, "unit": "boxes/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": w.name, "n_boxes": n_in, "k": k, "M": w.M,
+                       "kernel": "bsh" if w.kernel == W.BSH else "poisson", "mu": w.mu, "tau": w.tau,
+                       "stencil": "shells<=%d" % w.max_disp if w.stencil == 0 else "27-point",
+                       "terms_kept": terms, "pairs": st0["pairs"], "n_out": st0["n_out"],
+                       "precision": precision, "l2": "flushed by a 256 MB write before every step",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roof, "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
+            "e2e": {"value": e2e_val, "unit": "boxes/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "accuracy": accuracy, "wall_s_timed": t_wall}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(w, args.cpu_sample)
+        t_job = cb["t_sample"] * cb["terms_total"] / max(cb["sample_terms"], 1)
+        line["cpu_baseline"] = {"value": cb["n_in"] / t_job, "unit": "boxes/s", "cores": cb["cores"],
+                                "kind": "oracle",
+                                "sample": f"{cb['sample_dest']} seeded destination boxes of {cb['dest_total']} "
+                                          f"({cb['sample_terms']} of {cb['terms_total']} kept terms, "
+                                          f"{cb['t_sample']:.1f} s); job time extrapolated by kept terms"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * mra.h -- C ABI of the GB300 separated-operator apply library (libmra.so).
+ *
+ * The library applies an integral operator whose kernel is written as a sum of
+ * Gaussians (the Poisson kernel 1/r or the bound-state Helmholtz kernel
+ * exp(-mu r)/r) to a function held as order-k Legendre scaling-function
+ * coefficients on an adaptive 3-D tree, as described in Harrison et al.,
+ * "MADNESS: A Multiresolution, Adaptive Numerical Environment for Scientific
+ * Simulation" (arXiv 1507.01888), Sec. 2.1-2.3.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Cell [-L, L]^3.  Level n has 2^n boxes per dimension of width h_n = 2L/2^n
+ *    (Sec. 2.1 maps the domain to [0,1]; the library scales it to the cell).
+ *  - Box key (uint64): level << 57 | x << 38 | y << 19 | z, 0 <= x,y,z < 2^n,
+ *    n <= 19.  Trees hold their keys sorted ascending, without duplicates.
+ *  - Coefficients: k^3 doubles per box, s[ix][iy][iz] row-major (ix slowest),
+ *    in the basis phi^n_{b,i}(x) = h_n^{-1/2} phi_i((x+L)/h_n - b),
+ *    phi_i(x) = sqrt(2i+1) P_i(2x-1) (Sec. 2.1, eq. scalingfunc).
+ *  - Every call returns an int status: MRA_OK (0) or a negative MRA_ERR_*.
+ *    mra_last_error() returns a thread-local message for the last failure.
+ *    Nothing throws across this interface.
+ *  - Host arrays passed in are read during the call only; the library keeps
+ *    no caller host pointer.  Device buffers (tree views, workspace) are owned
+ *    by the caller: size queries come first, the caller allocates.  Opaque
+ *    handles (mra_operator) are owned by the library and freed with
+ *    mra_operator_free.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are stream-ordered; a call that must learn a size on the
+ *    host (mra_project, mra_apply) synchronises that stream before returning.
+ */
+#ifndef MRA_H
+#define MRA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define MRA_OK 0
+#define MRA_ERR_ARG (-1)      /* invalid argument (null pointer, bad size or order) */
+#define MRA_ERR_CAPACITY (-2) /* a caller buffer is too small; the required size is reported */
+#define MRA_ERR_CUDA (-3)     /* a CUDA runtime call or kernel launch failed */
+#define MRA_ERR_TIMEOUT (-4)  /* a bounded device-side wait gave up */
+#define MRA_ERR_NUMERIC (-5)  /* a non-finite value was produced */
+#define MRA_ERR_UNSUPPORTED (-6)
+
+/* ---- enumerations --------------------------------------------------------- */
+#define MRA_POISSON 0 /* K(r) = 1/r                          (Sec. 2.3) */
+#define MRA_BSH 1     /* K(r) = exp(-mu r)/r, mu = sqrt(-2E)  (Sec. 3.2, eq. bshkernel
+                         without its 1/(4 pi), which the caller applies) */
+
+#define MRA_PREC_FP64 0       /* all arithmetic in FP64 */
+#define MRA_PREC_SPLIT_BF16 1 /* mode products as split-BF16 tcgen05 MMAs with FP32
+                                 accumulation; Gaussian-term and box sums in FP64 */
+
+#define MRA_SCREEN_NONE 0 /* keep every term */
+#define MRA_SCREEN_NORM 1 /* keep a term iff |c| ||Rx|| ||Ry|| ||Rz|| ||s|| >= tau */
+
+#define MRA_STENCIL_SHELLS 0  /* shells of |l|_inf = 0,1,..,max_disp, stop at the first empty shell */
+#define MRA_STENCIL_NEAREST 1 /* all 27 displacements with |l|_inf <= 1 */
+
+#define MRA_MAX_LEVEL 19
+#define MRA_MAX_K 16
+#define MRA_MAX_TERMS 128
+
+/* ---- data types ----------------------------------------------------------- */
+
+/* f(x) = sum_g coef[g] exp(-expnt[g] |x - c_g|^2); host arrays of length n. */
+typedef struct {
+  int n;
+  const double *coef, *expnt, *cx, *cy, *cz;
+} mra_gauss_sum;
+
+/* A tree on the device: n boxes (keys sorted ascending) with k^3 doubles each.
+ * cap is the number of boxes the two buffers can hold. */
+typedef struct {
+  int64_t n;
+  int64_t cap;
+  uint64_t *keys;  /* device, cap entries */
+  double *coeffs;  /* device, cap * k^3 entries */
+  int k;
+  double L;
+} mra_tree_view;
+
+typedef struct mra_operator mra_operator; /* opaque */
+
+typedef struct {
+  int precision;  /* MRA_PREC_* */
+  int pieces;     /* split pieces per operand for MRA_PREC_SPLIT_BF16 (2 or 3) */
+  int screen;     /* MRA_SCREEN_* */
+  double tau;     /* screen threshold (ignored for MRA_SCREEN_NONE) */
+  int stencil;    /* MRA_STENCIL_* */
+  int max_disp;   /* largest |l|_inf for MRA_STENCIL_SHELLS (<= the operator's max_disp) */
+} mra_apply_opts;
+
+typedef struct {
+  int64_t n_in;               /* source boxes */
+  int64_t n_out;              /* destination boxes written */
+  int64_t pairs;              /* (source, displacement) pairs with at least one kept term */
+  int64_t terms_kept;         /* (source, displacement, Gaussian term) triples computed */
+  int64_t terms_screened;     /* triples dropped by the screen inside the displacement set */
+  int64_t terms_issued;       /* triples the kernel evaluated (kept + tile padding) */
+  int64_t sources_truncated;  /* sources whose last allowed shell still kept terms */
+  double skipped_bound;       /* sum of the screen bounds of dropped triples */
+  double kernel_ms;           /* device time of the apply kernel (CUDA events on `stream`) */
+} mra_apply_stats;
+
+typedef struct {
+  double diff_norm;  /* || test - ref ||_2 over the union of boxes */
+  double ref_norm;   /* || ref ||_2 */
+  double test_norm;  /* || test ||_2 */
+  double rel_l2;     /* diff_norm / ref_norm */
+  double max_box_rel;/* max over common boxes of ||test_b - ref_b|| / ||ref_b|| */
+  int64_t n_common;  /* boxes present in both trees */
+  int64_t n_only_test, n_only_ref;
+} mra_compare_result;
+
+/* ---- calls ---------------------------------------------------------------- */
+
+/* Thread-local description of the last error (never NULL). */
+const char *mra_last_error(void);
+
+/* Library version string. */
+const char *mra_version(void);
+
+/* Project f onto the scaling functions (Sec. 2.1, eq. projection):
+ * s^n_b = int f phi^n_b, computed per box from exact 1-D Gaussian integrals.
+ * uniform_level >= 0: every box of that level.  uniform_level < 0: adaptive
+ * refinement (Sec. 2.1): every box of level init_level-1 is a parent; a
+ * parent's 8 children are projected exactly and compared with the parent's
+ * own projection expressed on the children (two-scale relation, Sec. 2.2);
+ * if the Frobenius norm of the difference is <= thresh, or the children are
+ * at max_level, the children become leaves, else each child becomes a parent.
+ * out: device buffers with out->cap boxes; on success out->n, out->k, out->L
+ * are set and the keys are sorted.  MRA_ERR_CAPACITY if out->cap is too small
+ * (out->n then holds the required count).  Temporary device memory for the
+ * refinement is allocated and freed on `stream` inside the call. */
+int mra_project(const mra_gauss_sum *f, int k, double L, double thresh, int init_level,
+                int max_level, int uniform_level, mra_tree_view *out, void *stream);
+
+/* Build the separated operator (Sec. 2.3): the Gaussian fit of the kernel and
+ * the 1-D operator blocks.
+ * Fit: trapezoid rule of K(r) = (2/sqrt pi) int exp(-r^2 e^{2s} - mu^2 e^{-2s}/4 + s) ds
+ * (mu = 0 gives the 1/r identity of Sec. 2.3) with M terms,
+ *   c_m = (2/sqrt pi) h exp(s_m - mu^2 e^{-2 s_m}/4), t_m = e^{2 s_m}, s_m = s_lo + m h,
+ * where (h, s_lo) minimise the maximum relative error on 3000 log-spaced r
+ * in [r_lo, r_hi] over the grid h = 0.05..1.20 (step 0.01), s_lo = -25..3
+ * (step 0.25); ties go to the smaller h.  r_hi <= 0 selects 2L, shortened to
+ * ln(1/fit_eps)/mu for MRA_BSH.
+ * Blocks (Toeplitz, Sec. 2.2): for every level n in [min_level, max_level],
+ * term m < M and 1-D displacement |l| <= min(max_disp, 2^n - 1),
+ *   R^n_{m,l}[i][j] = h_n int_0^1 int_0^1 phi_i(u) exp(-t_m h_n^2 (u - v + l)^2) phi_j(v) du dv,
+ * which maps the source box b to the target box b + l, and its Frobenius norm.
+ * *op receives a handle owning the device tables; free with mra_operator_free. */
+int mra_operator_create(int kernel, double mu, int M, double fit_eps, double r_lo, double r_hi,
+                        int k, double L, int min_level, int max_level, int max_disp,
+                        mra_operator **op, void *stream);
+
+/* Copy the fit out of an operator (host arrays of length M; any may be NULL). */
+int mra_operator_fit(const mra_operator *op, double *c, double *t, double *h, double *s_lo,
+                     double *max_rel_err);
+
+/* Shape of an operator: k, M, levels and the largest displacement. */
+int mra_operator_info(const mra_operator *op, int *k, int *M, int *min_level, int *max_level,
+                      int *max_disp, double *L);
+
+/* Copy one block R^n_{m,l} (k*k doubles, row i, column j) and its Frobenius norm to the host. */
+int mra_operator_block(const mra_operator *op, int level, int m, int l, double *R, double *norm);
+
+int mra_operator_free(mra_operator *op);
+
+/* Device workspace (bytes) that mra_apply needs for this input and options. */
+int mra_apply_workspace_size(const mra_operator *op, const mra_tree_view *in,
+                             const mra_apply_opts *opts, size_t *bytes);
+
+/* Apply the separated operator to `in` (Sec. 2.3), leaf level by leaf level:
+ * for every source box b (level n), every displacement l in D(b) with b + l in
+ * the cell, and every term m kept by the screen,
+ *   r_{n,b+l} += c_m (s_b x_1 R^n_{m,lx} x_2 R^n_{m,ly} x_3 R^n_{m,lz}),
+ * the three k x k mode products of the separated representation.
+ * D(b): MRA_STENCIL_NEAREST -> |l|_inf <= 1; MRA_STENCIL_SHELLS -> shells
+ * |l|_inf = 0, 1, ..., opts->max_disp, stopping after the first shell in which
+ * no term is kept.  Screen MRA_SCREEN_NORM keeps a term iff
+ *   |c_m| * ||R_x||_F * ||R_y||_F * ||R_z||_F * ||s_b||_F >= tau
+ * (that product, in that order, bounds the term's norm).
+ * Results stay at the source's level; every destination box is computed by
+ * gathering its sources after a sort on the destination key, so each output
+ * box is written exactly once (no atomics).  out: device buffers; out->n
+ * receives the number of destination boxes, keys sorted ascending.
+ * workspace: device buffer of at least mra_apply_workspace_size bytes.
+ * stats may be NULL; when given, the call also waits for the apply kernel so
+ * that stats->kernel_ms holds its device time.  Synchronises `stream` twice to
+ * learn the record and output counts; MRA_ERR_CAPACITY (with out->n =
+ * required) if out->cap is too small, before the apply kernel runs. */
+int mra_apply(const mra_operator *op, const mra_tree_view *in, const mra_apply_opts *opts,
+              mra_tree_view *out, void *workspace, size_t workspace_bytes,
+              mra_apply_stats *stats, void *stream);
+
+/* Per-box Frobenius norms (device array of tree->n doubles, may be NULL) and
+ * the total L2 norm (host double, may be NULL).  Deterministic reduction. */
+int mra_norm(const mra_tree_view *tree, double *per_box, double *total, void *stream);
+
+/* Compare two trees with the same k: boxes are matched by key; a box present
+ * in one tree only counts in full.  Host result; synchronises `stream`. */
+int mra_compare(const mra_tree_view *test, const mra_tree_view *ref, mra_compare_result *res,
+                void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MRA_H */

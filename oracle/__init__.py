@@ -218,7 +218,8 @@ class ApplyResult:
         self.coeffs = coeffs
         self.bound = bound
         self.marginal = marginal
-        self.pairs, self.terms, self.screened, self.truncated = (int(s) for s in stats)
+        (self.pairs, self.terms, self.screened, self.truncated, self.dest_total,
+         self.terms_total) = (int(s) for s in stats)
 
 
 def apply(keys, coeffs, c, t, L: float, stencil: int = 1, max_disp: int = 1, tau: float = 0.0,
@@ -242,7 +243,7 @@ def apply(keys, coeffs, c, t, L: float, stencil: int = 1, max_disp: int = 1, tau
         bound = np.zeros(cap)
         marg = np.zeros(cap)
         n = ctypes.c_long(0)
-        stats = np.zeros(4, dtype=np.int64)
+        stats = np.zeros(6, dtype=np.int64)
         rc = _load().orc_apply(int(k), float(L), n_in, _up(keys), _dp(coeffs), len(c), _dp(c), _dp(t),
                                int(stencil), int(max_disp), float(tau),
                                len(sample) if sample_keys is not None else 0, _up(sample), int(cap),

@@ -577,7 +577,8 @@ typedef struct {
  * B over terms whose B is within 1e-9 relative of tau (decisions that rounding
  * could flip).  stats: [0] (source,l) pairs with a kept term, [1] kept terms,
  * [2] screened terms (within D(b)), [3] sources whose last allowed shell still
- * kept terms (truncated by max_disp). */
+ * kept terms (truncated by max_disp), [4] destinations and [5] kept terms of the
+ * whole job (whatever the sample). */
 int orc_apply(int k, double L, long n_in, const uint64_t *keys, const double *coeffs, int M,
               const double *c, const double *t, int stencil, int max_disp, double tau,
               long n_sample, const uint64_t *sample_keys, long cap, uint64_t *out_keys,
@@ -676,7 +677,7 @@ int orc_apply(int k, double L, long n_in, const uint64_t *keys, const double *co
     if (w > 0) maxd += w * w * w;
   }
   uint64_t *dest = (uint64_t *)malloc(sizeof(uint64_t) * (maxd > 0 ? maxd : 1));
-  long nd = 0;
+  long nd = 0, total_terms = 0;
   for (long b = 0; b < n_in; ++b) {
     int n;
     long x, y, z;
@@ -690,10 +691,10 @@ int orc_apply(int k, double L, long n_in, const uint64_t *keys, const double *co
               z + lz >= nb)
             continue;
           int any = 0;
-          for (int mu = 0; mu < M && !any; ++mu) {
+          for (int mu = 0; mu < M; ++mu) {
             double B = fabs(c[mu]) * lb[n].N[mu * nl + lx + D] * lb[n].N[mu * nl + ly + D] *
                        lb[n].N[mu * nl + lz + D] * snorm[b];
-            if (B >= tau) any = 1;
+            if (B >= tau) { any = 1; total_terms += 1; }
           }
           if (any) dest[nd++] = make_key(n, x + lx, y + ly, z + lz);
         }
@@ -801,6 +802,8 @@ int orc_apply(int k, double L, long n_in, const uint64_t *keys, const double *co
     stats[1] = kept_terms;
     stats[2] = screened;
     stats[3] = truncated;
+    stats[4] = nu;          /* destinations of the whole job */
+    stats[5] = total_terms; /* kept terms of the whole job */
   }
   free(dest);
   free(sel);

@@ -1,0 +1,685 @@
+// apply.cu -- the apply path: source norms, norm screen and work list, sort on the
+// destination key, FP64 gather-apply, and the norm/compare reductions.
+//
+// Work list.  For every source box b (level n) and displacement l in D(b) the
+// screen computes, per Gaussian term m, the bound
+//     B = |c_m| * ||R^n_{m,lx}||_F * ||R^n_{m,ly}||_F * ||R^n_{m,lz}||_F * ||s_b||_F
+// and keeps the term iff B >= tau.  A (b, l) pair with at least one kept term
+// becomes a record {dest key = key(n, b + l), b, l, kept-term mask}.  Records
+// are sorted on the destination key (stable radix sort), so the records of one
+// destination are contiguous; each destination box is then produced by one
+// CTA that gathers its sources and sums their terms in registers, and written
+// exactly once.  No atomics touch the result.
+#include <cub/cub.cuh>
+
+#include "apply_internal.cuh"
+
+namespace mra {
+
+namespace {
+
+__global__ void iota_kernel(int64_t n, int *p) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = (int)i;
+}
+
+__global__ void square_kernel(int64_t n, const double *a, double *b) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = a[i] * a[i];
+}
+
+__global__ void max_kernel_single(int64_t n, const double *a, double *out) {
+  __shared__ double red[1024];
+  double m = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, a[i]);
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- per-box norms
+__global__ void box_norm_kernel(int64_t n, int k3, const double *coeffs, double *norms) {
+  int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (b >= n) return;
+  const double *s = coeffs + b * k3;
+  double a = 0.0;
+  for (int e = lane; e < k3; e += 32) a += s[e] * s[e];
+  a = warp_sum(a);
+  if (lane == 0) norms[b] = sqrt(a);
+}
+
+// ---------------------------------------------------------------- screen
+// One warp per source box.  pass 0 counts records, pass 1 writes them at off[b].
+struct ScreenArgs {
+  int64_t n_in;
+  const uint64_t *keys;
+  const double *snorm;
+  int M;
+  const double *c;
+  const double *N;            // block norms
+  const int *Dlev;            // operator D per absolute level
+  const int64_t *level_off;   // operator first block per absolute level (-1 absent)
+  int stencil, dmax, screen;
+  double tau;
+  // outputs
+  int *dstop;
+  int64_t *cnt;               // records per box (pass 0)
+  const int64_t *off;         // record offsets (pass 1)
+  uint64_t *rec_key;
+  int *rec_src;
+  int *rec_l;                 // packed (lx+128) | (ly+128)<<8 | (lz+128)<<16
+  uint64_t *rec_mask;         // 2 words per record
+  int64_t *box_kept, *box_screened;
+  double *box_skipped;
+  int *box_trunc;
+  int *err;
+};
+
+template <int PASS>
+__global__ void screen_kernel(ScreenArgs a) {
+  int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (b >= a.n_in) return;
+  uint64_t key = a.keys[b];
+  int n = key_level(key);
+  int64_t x = key_x(key), y = key_y(key), z = key_z(key);
+  int64_t nb = 1LL << n;
+  if (a.level_off[n] < 0) {
+    if (lane == 0) atomicExch(a.err, 1);  // level outside the operator's table
+    return;
+  }
+  int Dop = a.Dlev[n];
+  int D = a.stencil == MRA_STENCIL_NEAREST ? 1 : a.dmax;
+  if (D > Dop) D = Dop;
+  if (D > nb - 1) D = (int)(nb - 1);
+  int nl = 2 * Dop + 1;
+  const double *Nl = a.N + a.level_off[n];
+  double sn = a.snorm[b];
+  int64_t count = 0, kept = 0, screened = 0;
+  double skipped = 0.0;
+  int64_t wpos = PASS == 1 ? a.off[b] : 0;
+  int d;
+  for (d = 0; d <= D; ++d) {
+    int any = 0;
+    for (int lx = -d; lx <= d; ++lx)
+      for (int ly = -d; ly <= d; ++ly)
+        for (int lz = -d; lz <= d; ++lz) {
+          int m_inf = max(abs(lx), max(abs(ly), abs(lz)));
+          if (m_inf != d) continue;
+          if (x + lx < 0 || x + lx >= nb || y + ly < 0 || y + ly >= nb || z + lz < 0 ||
+              z + lz >= nb)
+            continue;
+          uint64_t mask[2] = {0ull, 0ull};
+          for (int m0 = 0; m0 < a.M; m0 += 32) {
+            int m = m0 + lane;
+            bool keep = false;
+            double B = 0.0;
+            if (m < a.M) {
+              B = fabs(a.c[m]) * Nl[m * nl + lx + Dop] * Nl[m * nl + ly + Dop] *
+                  Nl[m * nl + lz + Dop] * sn;
+              keep = a.screen == MRA_SCREEN_NONE ? true : (B >= a.tau);
+            }
+            unsigned bal = __ballot_sync(0xffffffffu, keep);
+            mask[m0 >> 6] |= (uint64_t)bal << (m0 & 63);
+            if (PASS == 0) {
+              double sk = (m < a.M && !keep) ? B : 0.0;
+              skipped += warp_sum(sk);
+            }
+          }
+          int pk = __popcll(mask[0]) + __popcll(mask[1]);
+          if (pk == 0) {
+            screened += a.M;
+            continue;
+          }
+          any = 1;
+          kept += pk;
+          screened += a.M - pk;
+          if (PASS == 1 && lane == 0) {
+            a.rec_key[wpos] = make_key(n, x + lx, y + ly, z + lz);
+            a.rec_src[wpos] = (int)b;
+            a.rec_l[wpos] = (lx + 128) | ((ly + 128) << 8) | ((lz + 128) << 16);
+            a.rec_mask[2 * wpos] = mask[0];
+            a.rec_mask[2 * wpos + 1] = mask[1];
+          }
+          ++wpos;
+          ++count;
+        }
+    if (a.stencil == MRA_STENCIL_SHELLS && !any) break;
+  }
+  if (PASS == 0 && lane == 0) {
+    a.cnt[b] = count;
+    a.dstop[b] = d;
+    a.box_kept[b] = kept;
+    a.box_screened[b] = screened;
+    a.box_skipped[b] = skipped;
+    a.box_trunc[b] = (a.stencil == MRA_STENCIL_SHELLS && d == D + 1) ? 1 : 0;
+  }
+}
+
+// ---------------------------------------------------------------- destination segments
+__global__ void head_flags_kernel(int64_t P, const uint64_t *skey, int *head) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  head[i] = (i == 0 || skey[i] != skey[i - 1]) ? 1 : 0;
+}
+
+__global__ void segments_kernel(int64_t P, const uint64_t *skey, const int *head,
+                                const int *dest_id /*inclusive scan*/, uint64_t *dest_key,
+                                int64_t *seg, int64_t *n_dest) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  if (head[i]) {
+    int64_t d = dest_id[i] - 1;
+    dest_key[d] = skey[i];
+    seg[d] = i;
+  }
+  if (i == P - 1) {
+    *n_dest = dest_id[i];
+    seg[dest_id[i]] = P;
+  }
+}
+
+// ---------------------------------------------------------------- FP64 gather-apply
+// One CTA per destination box.  For each of its records (source b, l, mask)
+// and each kept term m:  t1 = s x_1 Rx, t2 = t1 x_2 Ry, t3 = t2 x_3 Rz,
+// acc += c_m t3 (Sec. 2.3), acc held in registers across all records.
+constexpr int F64_THREADS = 256;
+constexpr int F64_PER_THREAD = (MRA_MAX_K * MRA_MAX_K * MRA_MAX_K + F64_THREADS - 1) / F64_THREADS;
+
+__global__ void __launch_bounds__(F64_THREADS) apply_f64_kernel(
+    int k, int M, const double *c, const double *R, const int *Dlev, const int64_t *level_off,
+    const uint64_t *in_keys, const double *in_coeffs, const int64_t *seg, const int *perm,
+    const int *rec_src, const int *rec_l, const uint64_t *rec_mask, const uint64_t *dest_key,
+    uint64_t *out_keys, double *out_coeffs) {
+  extern __shared__ double sm[];
+  int k2 = k * k, k3 = k2 * k;
+  double *s = sm, *t1 = s + k3, *t2 = t1 + k3, *Rs = t2 + k3;  // Rs: 3 * k2
+  int64_t dst = blockIdx.x;
+  uint64_t dkey = dest_key[dst];
+  int n = key_level(dkey);
+  int Dop = Dlev[n];
+  int nl = 2 * Dop + 1;
+  const double *Rlev = R + level_off[n] * k2;
+  double acc[F64_PER_THREAD];
+#pragma unroll
+  for (int q = 0; q < F64_PER_THREAD; ++q) acc[q] = 0.0;
+  int64_t r0 = seg[dst], r1 = seg[dst + 1];
+  for (int64_t r = r0; r < r1; ++r) {
+    int p = perm[r];
+    int src = rec_src[p];
+    int lp = rec_l[p];
+    int lx = (lp & 255) - 128, ly = ((lp >> 8) & 255) - 128, lz = ((lp >> 16) & 255) - 128;
+    uint64_t mk[2] = {rec_mask[2 * (int64_t)p], rec_mask[2 * (int64_t)p + 1]};
+    __syncthreads();
+    const double *sb = in_coeffs + (int64_t)src * k3;
+    for (int e = threadIdx.x; e < k3; e += blockDim.x) s[e] = sb[e];
+    for (int w = 0; w < 2; ++w) {
+      uint64_t bits = mk[w];
+      while (bits) {
+        int m = w * 64 + __ffsll((long long)bits) - 1;
+        bits &= bits - 1;
+        __syncthreads();
+        const double *Rx = Rlev + ((int64_t)m * nl + lx + Dop) * k2;
+        const double *Ry = Rlev + ((int64_t)m * nl + ly + Dop) * k2;
+        const double *Rz = Rlev + ((int64_t)m * nl + lz + Dop) * k2;
+        for (int e = threadIdx.x; e < k2; e += blockDim.x) {
+          Rs[e] = Rx[e];
+          Rs[k2 + e] = Ry[e];
+          Rs[2 * k2 + e] = Rz[e];
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < k3; e += blockDim.x) {  // t1[ix][jy][jz]
+          int ix = e / k2, rest = e % k2;
+          double v = 0.0;
+          for (int j = 0; j < k; ++j) v += Rs[ix * k + j] * s[j * k2 + rest];
+          t1[e] = v;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < k3; e += blockDim.x) {  // t2[ix][iy][jz]
+          int ix = e / k2, iy = (e / k) % k, jz = e % k;
+          double v = 0.0;
+          for (int j = 0; j < k; ++j) v += Rs[k2 + iy * k + j] * t1[ix * k2 + j * k + jz];
+          t2[e] = v;
+        }
+        __syncthreads();
+        double cm = c[m];
+#pragma unroll
+        for (int q = 0; q < F64_PER_THREAD; ++q) {  // acc += c_m t3[ix][iy][iz]
+          int e = threadIdx.x + q * F64_THREADS;
+          if (e < k3) {
+            int base = (e / k) * k, iz = e % k;
+            double v = 0.0;
+            for (int j = 0; j < k; ++j) v += Rs[2 * k2 + iz * k + j] * t2[base + j];
+            acc[q] += cm * v;
+          }
+        }
+      }
+    }
+  }
+  double *o = out_coeffs + dst * k3;
+#pragma unroll
+  for (int q = 0; q < F64_PER_THREAD; ++q) {
+    int e = threadIdx.x + q * F64_THREADS;
+    if (e < k3) o[e] = acc[q];
+  }
+  if (threadIdx.x == 0) out_keys[dst] = dkey;
+}
+
+// ---------------------------------------------------------------- compare
+// For each test box: squared norms of test, of the matching ref box (by key)
+// and of their difference.  Boxes only in ref are handled by ref_only_kernel.
+__global__ void compare_kernel(int64_t nt, const uint64_t *tk, const double *tc, int64_t nr,
+                               const uint64_t *rk, const double *rc, int k3, double *d2,
+                               double *t2, double *r2, double *rel, int *match) {
+  int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (b >= nt) return;
+  uint64_t key = tk[b];
+  int64_t lo = 0, hi = nr - 1, pos = -1;
+  while (lo <= hi) {
+    int64_t mid = (lo + hi) >> 1;
+    uint64_t v = rk[mid];
+    if (v == key) { pos = mid; break; }
+    if (v < key) lo = mid + 1; else hi = mid - 1;
+  }
+  const double *a = tc + b * k3;
+  const double *r = pos >= 0 ? rc + pos * k3 : nullptr;
+  double sd = 0.0, st = 0.0, sr = 0.0;
+  for (int e = lane; e < k3; e += 32) {
+    double av = a[e], rv = r ? r[e] : 0.0;
+    sd += (av - rv) * (av - rv);
+    st += av * av;
+    sr += rv * rv;
+  }
+  sd = warp_sum(sd);
+  st = warp_sum(st);
+  sr = warp_sum(sr);
+  if (lane == 0) {
+    d2[b] = sd;
+    t2[b] = st;
+    r2[b] = sr;
+    rel[b] = pos >= 0 ? (sr > 0.0 ? sqrt(sd / sr) : (sd > 0.0 ? INFINITY : 0.0)) : 0.0;
+    match[b] = pos >= 0 ? 1 : 0;
+  }
+}
+
+__global__ void ref_only_kernel(int64_t nr, const uint64_t *rk, const double *rc, int64_t nt,
+                                const uint64_t *tk, int k3, double *r2_all, double *r2_only,
+                                int *only) {
+  int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (b >= nr) return;
+  uint64_t key = rk[b];
+  int64_t lo = 0, hi = nt - 1;
+  bool found = false;
+  while (lo <= hi) {
+    int64_t mid = (lo + hi) >> 1;
+    uint64_t v = tk[mid];
+    if (v == key) { found = true; break; }
+    if (v < key) lo = mid + 1; else hi = mid - 1;
+  }
+  const double *r = rc + b * k3;
+  double s = 0.0;
+  for (int e = lane; e < k3; e += 32) s += r[e] * r[e];
+  s = warp_sum(s);
+  if (lane == 0) {
+    r2_all[b] = s;
+    r2_only[b] = found ? 0.0 : s;
+    only[b] = found ? 0 : 1;
+  }
+}
+
+}  // namespace
+
+// ============================================================== host side
+
+static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+int apply_max_disp(const Operator &op, const mra_apply_opts &o) {
+  int D = o.stencil == MRA_STENCIL_NEAREST ? 1 : o.max_disp;
+  if (D > op.max_disp) D = op.max_disp;
+  if (D < 0) D = 0;
+  return D;
+}
+
+int64_t apply_max_records(const Operator &op, const mra_apply_opts &o, int64_t n_in) {
+  int64_t w = 2 * apply_max_disp(op, o) + 1;
+  return n_in * w * w * w;
+}
+
+// Workspace layout (all offsets 256-byte aligned):
+//   per box: snorm, dstop, cnt, off, kept, screened, skipped, trunc
+//   per record: key, src, l, mask[2], sorted key, perm in/out, head, dest id
+//   per destination (<= records): dest key, seg (+1)
+//   CUB temp storage (max over scan / sort / reduce needs)
+struct Layout {
+  size_t snorm, dstop, cnt, off, kept, screened, skipped, trunc;
+  size_t rkey, rsrc, rl, rmask, skey, pin, pout, head, did, dkey, seg, ndest, tmp;
+  size_t tmp_bytes, total;
+};
+
+static Layout make_layout(int64_t n_in, int64_t P) {
+  Layout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + (bytes ? bytes : 1));
+    return at;
+  };
+  int64_t nb = n_in > 0 ? n_in : 1, np = P > 0 ? P : 1;
+  L.snorm = take(nb * 8);
+  L.dstop = take(nb * 4);
+  L.cnt = take(nb * 8);
+  L.off = take(nb * 8);
+  L.kept = take(nb * 8);
+  L.screened = take(nb * 8);
+  L.skipped = take(nb * 8);
+  L.trunc = take(nb * 4);
+  L.rkey = take(np * 8);
+  L.rsrc = take(np * 4);
+  L.rl = take(np * 4);
+  L.rmask = take(np * 16);
+  L.skey = take(np * 8);
+  L.pin = take(np * 4);
+  L.pout = take(np * 4);
+  L.head = take(np * 4);
+  L.did = take(np * 4);
+  L.dkey = take(np * 8);
+  L.seg = take((np + 1) * 8);
+  L.ndest = take(8);
+  // CUB temporary storage: the largest of the calls below
+  size_t a = 0, b = 0, c = 0, d = 0, e = 0;
+  cub::DeviceScan::ExclusiveSum(nullptr, a, (int64_t *)nullptr, (int64_t *)nullptr, (int)nb);
+  cub::DeviceScan::InclusiveSum(nullptr, b, (int *)nullptr, (int *)nullptr, (int)np);
+  cub::DeviceRadixSort::SortPairs(nullptr, c, (uint64_t *)nullptr, (uint64_t *)nullptr,
+                                  (int *)nullptr, (int *)nullptr, (int)np);
+  cub::DeviceReduce::Sum(nullptr, d, (double *)nullptr, (double *)nullptr, (int)nb);
+  cub::DeviceReduce::Sum(nullptr, e, (int64_t *)nullptr, (int64_t *)nullptr, (int)nb);
+  size_t t = a;
+  for (size_t v : {b, c, d, e}) t = v > t ? v : t;
+  L.tmp_bytes = t;
+  L.tmp = take(t);
+  L.total = o;
+  return L;
+}
+
+size_t apply_workspace_bytes(const Operator &op, const mra_apply_opts &o, int64_t n_in) {
+  return make_layout(n_in, apply_max_records(op, o, n_in)).total;
+}
+
+int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts &o,
+              mra_tree_view &out, void *ws, size_t ws_bytes, mra_apply_stats *stats,
+              cudaStream_t s) {
+  const int k = op.k, k3 = k * k * k;
+  const int64_t n_in = in.n;
+  const int64_t Pmax = apply_max_records(op, o, n_in);
+  Layout L = make_layout(n_in, Pmax);
+  if (ws_bytes < L.total)
+    return fail(MRA_ERR_CAPACITY, "mra_apply: workspace of %zu bytes < %zu needed", ws_bytes, L.total);
+  char *w = (char *)ws;
+  double *snorm = (double *)(w + L.snorm);
+  int *dstop = (int *)(w + L.dstop);
+  int64_t *cnt = (int64_t *)(w + L.cnt), *off = (int64_t *)(w + L.off);
+  int64_t *bkept = (int64_t *)(w + L.kept), *bscr = (int64_t *)(w + L.screened);
+  double *bskip = (double *)(w + L.skipped);
+  int *btrunc = (int *)(w + L.trunc);
+  uint64_t *rkey = (uint64_t *)(w + L.rkey), *skey = (uint64_t *)(w + L.skey);
+  int *rsrc = (int *)(w + L.rsrc), *rl = (int *)(w + L.rl);
+  uint64_t *rmask = (uint64_t *)(w + L.rmask);
+  int *pin = (int *)(w + L.pin), *pout = (int *)(w + L.pout);
+  int *head = (int *)(w + L.head), *did = (int *)(w + L.did);
+  uint64_t *dkey = (uint64_t *)(w + L.dkey);
+  int64_t *seg = (int64_t *)(w + L.seg), *ndest = (int64_t *)(w + L.ndest);
+  void *tmp = w + L.tmp;
+  size_t tmpb = L.tmp_bytes;
+
+  if (n_in == 0) {
+    out.n = 0;
+    if (stats) *stats = mra_apply_stats{};
+    return MRA_OK;
+  }
+  // error flag lives in the first word of the dest-count slot until it is used
+  int *d_err = (int *)ndest;
+  MRA_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int64_t), s));
+
+  const int wpb = 8;  // warps per CTA for per-box kernels
+  unsigned gboxes = (unsigned)((n_in + wpb - 1) / wpb);
+  box_norm_kernel<<<gboxes, 32 * wpb, 0, s>>>(n_in, k3, in.coeffs, snorm);
+  MRA_CUDA_TRY(cudaGetLastError());
+
+  ScreenArgs a{};
+  a.n_in = n_in;
+  a.keys = in.keys;
+  a.snorm = snorm;
+  a.M = op.M;
+  a.c = op.d_c;
+  a.N = op.d_N;
+  a.Dlev = op.d_D;
+  a.level_off = op.d_level_off;
+  a.stencil = o.stencil;
+  a.dmax = apply_max_disp(op, o);
+  a.screen = o.screen;
+  a.tau = o.tau;
+  a.dstop = dstop;
+  a.cnt = cnt;
+  a.off = off;
+  a.rec_key = rkey;
+  a.rec_src = rsrc;
+  a.rec_l = rl;
+  a.rec_mask = rmask;
+  a.box_kept = bkept;
+  a.box_screened = bscr;
+  a.box_skipped = bskip;
+  a.box_trunc = btrunc;
+  a.err = d_err;
+  screen_kernel<0><<<gboxes, 32 * wpb, 0, s>>>(a);
+  MRA_CUDA_TRY(cudaGetLastError());
+  MRA_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, tmpb, cnt, off, (int)n_in, s));
+  // statistics reduced on the device (deterministic), read with the record count
+  int64_t *red_i = (int64_t *)(seg);  // seg is free until the segments pass
+  double *red_d = (double *)(seg + 4);
+  if (stats) {
+    MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, bkept, red_i + 0, (int)n_in, s));
+    MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, bscr, red_i + 1, (int)n_in, s));
+    MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, btrunc, (int *)(red_i + 2), (int)n_in, s));
+    MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, bskip, red_d, (int)n_in, s));
+  }
+  int64_t h_last[2] = {0, 0};
+  int h_err = 0;
+  int64_t hs[3] = {0, 0, 0};
+  double hd = 0.0;
+  MRA_CUDA_TRY(cudaMemcpyAsync(&h_last[0], off + n_in - 1, 8, cudaMemcpyDeviceToHost, s));
+  MRA_CUDA_TRY(cudaMemcpyAsync(&h_last[1], cnt + n_in - 1, 8, cudaMemcpyDeviceToHost, s));
+  MRA_CUDA_TRY(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (stats) {
+    MRA_CUDA_TRY(cudaMemcpyAsync(hs, red_i, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    MRA_CUDA_TRY(cudaMemcpyAsync(&hd, red_d, sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h_err)
+    return fail(MRA_ERR_ARG, "mra_apply: an input box lies on a level the operator does not cover "
+                "(levels %d..%d)", op.min_level, op.max_level);
+  const int64_t P = h_last[0] + h_last[1];
+  if (P > Pmax) return fail(MRA_ERR_CAPACITY, "mra_apply: internal record bound exceeded");
+  if (stats) {
+    int ntr = 0;
+    memcpy(&ntr, &hs[2], sizeof(int));
+    *stats = mra_apply_stats{};
+    stats->n_in = n_in;
+    stats->terms_kept = hs[0];
+    stats->terms_screened = hs[1];
+    stats->sources_truncated = ntr;
+    stats->skipped_bound = hd;
+    stats->pairs = P;
+    stats->terms_issued = hs[0];
+  }
+  if (P == 0) {
+    out.n = 0;
+    return MRA_OK;
+  }
+  screen_kernel<1><<<gboxes, 32 * wpb, 0, s>>>(a);
+  MRA_CUDA_TRY(cudaGetLastError());
+  // sort record indices on the destination key
+  {
+    unsigned g = (unsigned)((P + 255) / 256);
+    iota_kernel<<<g, 256, 0, s>>>(P, pin);
+    MRA_CUDA_TRY(cudaGetLastError());
+    MRA_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, tmpb, rkey, skey, pin, pout, (int)P, 0, 64, s));
+    head_flags_kernel<<<g, 256, 0, s>>>(P, skey, head);
+    MRA_CUDA_TRY(cudaGetLastError());
+    MRA_CUDA_TRY(cub::DeviceScan::InclusiveSum(tmp, tmpb, head, did, (int)P, s));
+    segments_kernel<<<g, 256, 0, s>>>(P, skey, head, did, dkey, seg, ndest);
+    MRA_CUDA_TRY(cudaGetLastError());
+  }
+  int64_t nd = 0;
+  MRA_CUDA_TRY(cudaMemcpyAsync(&nd, ndest, 8, cudaMemcpyDeviceToHost, s));
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  if (nd > out.cap) {
+    out.n = nd;
+    return fail(MRA_ERR_CAPACITY, "mra_apply: output holds %lld boxes, %lld needed",
+                (long long)out.cap, (long long)nd);
+  }
+  ApplyWork wk{};
+  wk.n_dest = nd;
+  wk.seg = seg;
+  wk.perm = pout;
+  wk.rec_src = rsrc;
+  wk.rec_l = rl;
+  wk.rec_mask = rmask;
+  wk.dest_key = dkey;
+  int rc;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (stats) {
+    MRA_CUDA_TRY(cudaEventCreate(&ev0));
+    MRA_CUDA_TRY(cudaEventCreate(&ev1));
+    MRA_CUDA_TRY(cudaEventRecord(ev0, s));
+  }
+  if (o.precision == MRA_PREC_FP64) {
+    size_t smem = (size_t)(3 * k3 + 3 * k * k) * sizeof(double);
+    if (smem > 48 * 1024)
+      MRA_CUDA_TRY(cudaFuncSetAttribute(apply_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+    apply_f64_kernel<<<(unsigned)nd, F64_THREADS, smem, s>>>(
+        k, op.M, op.d_c, op.d_R, op.d_D, op.d_level_off, in.keys, in.coeffs, seg, pout, rsrc, rl,
+        rmask, dkey, out.keys, out.coeffs);
+    MRA_CUDA_TRY(cudaGetLastError());
+    rc = MRA_OK;
+  } else {
+    rc = apply_split_run(op, in, o, out, wk, stats, s);
+    if (rc != MRA_OK) return rc;
+  }
+  out.n = nd;
+  if (stats) {
+    stats->n_out = nd;
+    MRA_CUDA_TRY(cudaEventRecord(ev1, s));
+    MRA_CUDA_TRY(cudaEventSynchronize(ev1));
+    float ms = 0.0f;
+    MRA_CUDA_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
+    stats->kernel_ms = ms;
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+  }
+  return rc;
+}
+
+
+// ---------------------------------------------------------------- norm / compare hosts
+
+int norm_run(const mra_tree_view &t, double *per_box, double *total, cudaStream_t s) {
+  int k3 = t.k * t.k * t.k;
+  int64_t n = t.n;
+  if (n == 0) {
+    if (total) *total = 0.0;
+    return MRA_OK;
+  }
+  double *buf = nullptr, *sq = nullptr, *dsum = nullptr;
+  void *tmp = nullptr;
+  size_t tmpb = 0;
+  MRA_CUDA_TRY(cub::DeviceReduce::Sum(nullptr, tmpb, (double *)nullptr, (double *)nullptr, (int)n));
+  MRA_CUDA_TRY(cudaMallocAsync((void **)&buf, n * 8 * 2 + 8 + tmpb + 512, s));
+  sq = buf + n;
+  dsum = sq + n;
+  tmp = (void *)(((uintptr_t)(dsum + 1) + 255) & ~(uintptr_t)255);
+  double *norms = per_box ? per_box : buf;
+  const int wpb = 8;
+  box_norm_kernel<<<(unsigned)((n + wpb - 1) / wpb), 32 * wpb, 0, s>>>(n, k3, t.coeffs, norms);
+  square_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, norms, sq);
+  MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, sq, dsum, (int)n, s));
+  double h = 0.0;
+  MRA_CUDA_TRY(cudaMemcpyAsync(&h, dsum, 8, cudaMemcpyDeviceToHost, s));
+  MRA_CUDA_TRY(cudaFreeAsync(buf, s));
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  if (total) *total = sqrt(h);
+  return MRA_OK;
+}
+
+
+
+int compare_run(const mra_tree_view &t, const mra_tree_view &r, mra_compare_result *res,
+                cudaStream_t s) {
+  if (t.k != r.k) return fail(MRA_ERR_ARG, "mra_compare: trees have different k");
+  int k3 = t.k * t.k * t.k;
+  int64_t nt = t.n, nr = r.n;
+  int64_t nmax = (nt > nr ? nt : nr) + 1;
+  size_t tmpb = 0, tb2 = 0;
+  MRA_CUDA_TRY(cub::DeviceReduce::Sum(nullptr, tmpb, (double *)nullptr, (double *)nullptr, (int)nmax));
+  MRA_CUDA_TRY(cub::DeviceReduce::Sum(nullptr, tb2, (int *)nullptr, (int *)nullptr, (int)nmax));
+  if (tb2 > tmpb) tmpb = tb2;
+  char *buf = nullptr;
+  size_t per = align_up(nmax * 8);
+  size_t total = per * 8 + align_up(tmpb) + 256;
+  MRA_CUDA_TRY(cudaMallocAsync((void **)&buf, total, s));
+  double *d2 = (double *)buf, *t2 = (double *)(buf + per), *r2 = (double *)(buf + 2 * per);
+  double *rel = (double *)(buf + 3 * per), *ra = (double *)(buf + 4 * per);
+  double *ro = (double *)(buf + 5 * per);
+  int *match = (int *)(buf + 6 * per), *only = (int *)(buf + 7 * per);
+  void *tmp = buf + 8 * per;
+  double *sums = (double *)(buf + 8 * per + align_up(tmpb));  // 8 doubles
+  const int wpb = 8;
+  MRA_CUDA_TRY(cudaMemsetAsync(sums, 0, 8 * sizeof(double), s));
+  if (nt > 0) {
+    compare_kernel<<<(unsigned)((nt + wpb - 1) / wpb), 32 * wpb, 0, s>>>(
+        nt, t.keys, t.coeffs, nr, r.keys, r.coeffs, k3, d2, t2, r2, rel, match);
+    MRA_CUDA_TRY(cudaGetLastError());
+    MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, d2, sums + 0, (int)nt, s));
+    MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, t2, sums + 1, (int)nt, s));
+    MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, match, (int *)(sums + 4), (int)nt, s));
+    max_kernel_single<<<1, 1024, 0, s>>>(nt, rel, sums + 5);
+  }
+  if (nr > 0) {
+    ref_only_kernel<<<(unsigned)((nr + wpb - 1) / wpb), 32 * wpb, 0, s>>>(nr, r.keys, r.coeffs, nt,
+                                                                           t.keys, k3, ra, ro, only);
+    MRA_CUDA_TRY(cudaGetLastError());
+    MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, ra, sums + 2, (int)nr, s));
+    MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, ro, sums + 3, (int)nr, s));
+    MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, only, (int *)(sums + 6), (int)nr, s));
+  }
+  double h[8];
+  MRA_CUDA_TRY(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s));
+  MRA_CUDA_TRY(cudaFreeAsync(buf, s));
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  int n_common = 0, n_only_ref = 0;
+  memcpy(&n_common, &h[4], sizeof(int));
+  memcpy(&n_only_ref, &h[6], sizeof(int));
+  res->diff_norm = sqrt(h[0] + h[3]);
+  res->test_norm = sqrt(h[1]);
+  res->ref_norm = sqrt(h[2]);
+  res->rel_l2 = res->ref_norm > 0 ? res->diff_norm / res->ref_norm : res->diff_norm;
+  res->max_box_rel = nt > 0 ? h[5] : 0.0;
+  res->n_common = n_common;
+  res->n_only_test = nt - n_common;
+  res->n_only_ref = n_only_ref;
+  return MRA_OK;
+}
+
+}  // namespace mra

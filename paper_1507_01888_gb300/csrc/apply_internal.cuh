@@ -1,0 +1,33 @@
+// apply_internal.cuh -- declarations shared by the apply translation units.
+#pragma once
+
+#include "mra_internal.cuh"
+
+namespace mra {
+
+// The sorted work list handed from the screen/sort stage to an apply kernel.
+// Destination d gathers records perm[seg[d]] .. perm[seg[d+1]-1]; record p names
+// a source box rec_src[p], a displacement rec_l[p] (three biased bytes) and the
+// kept Gaussian terms rec_mask[2p], rec_mask[2p+1] (bit m = term m).
+struct ApplyWork {
+  int64_t n_dest;
+  const int64_t *seg;
+  const int *perm;
+  const int *rec_src;
+  const int *rec_l;
+  const uint64_t *rec_mask;
+  const uint64_t *dest_key;
+};
+
+size_t apply_workspace_bytes(const Operator &op, const mra_apply_opts &o, int64_t n_in);
+int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts &o,
+              mra_tree_view &out, void *ws, size_t ws_bytes, mra_apply_stats *stats,
+              cudaStream_t s);
+int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts &o,
+                    mra_tree_view &out, const ApplyWork &wk, mra_apply_stats *stats,
+                    cudaStream_t s);
+int norm_run(const mra_tree_view &t, double *per_box, double *total, cudaStream_t s);
+int compare_run(const mra_tree_view &t, const mra_tree_view &r, mra_compare_result *res,
+                cudaStream_t s);
+
+}  // namespace mra

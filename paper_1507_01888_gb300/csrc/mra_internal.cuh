@@ -1,0 +1,73 @@
+// mra_internal.cuh -- shared declarations of libmra's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mra.h"
+
+namespace mra {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char *fmt, ...);
+int fail(int code, const char *fmt, ...);
+
+#define MRA_CUDA_TRY(call)                                                          \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return ::mra::fail(MRA_ERR_CUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call,  \
+                         cudaGetErrorString(e_));                                   \
+  } while (0)
+
+// ---------------------------------------------------------------- keys
+__host__ __device__ inline uint64_t make_key(int n, int64_t x, int64_t y, int64_t z) {
+  return ((uint64_t)n << 57) | ((uint64_t)x << 38) | ((uint64_t)y << 19) | (uint64_t)z;
+}
+__host__ __device__ inline int key_level(uint64_t k) { return (int)(k >> 57); }
+__host__ __device__ inline int64_t key_x(uint64_t k) { return (int64_t)((k >> 38) & 0x7FFFF); }
+__host__ __device__ inline int64_t key_y(uint64_t k) { return (int64_t)((k >> 19) & 0x7FFFF); }
+__host__ __device__ inline int64_t key_z(uint64_t k) { return (int64_t)(k & 0x7FFFF); }
+
+// ---------------------------------------------------------------- operator
+// Block table: for each level n in [min_level, max_level], D(n) = min(max_disp, 2^n-1),
+// blocks R[n][m][l + D(n)][i][j] (k*k doubles) starting at level_off[n - min_level] blocks.
+struct Operator {
+  int kernel = 0;
+  double mu = 0.0;
+  int M = 0, k = 0;
+  double L = 0.0;
+  int min_level = 0, max_level = 0, max_disp = 0;
+  double h_fit = 0.0, s_lo = 0.0, fit_err = 0.0, r_lo = 0.0, r_hi = 0.0;
+  std::vector<double> c, t;               // host copies of the fit
+  std::vector<int> D;                     // per level (index n - min_level)
+  std::vector<int64_t> level_off;         // first block index of each level
+  int64_t n_blocks = 0;
+  double *d_c = nullptr, *d_t = nullptr;  // device fit
+  double *d_R = nullptr;                  // device blocks, n_blocks * k*k
+  double *d_N = nullptr;                  // device block norms, n_blocks
+  int *d_D = nullptr;                     // device copy of D (20 entries, by absolute level)
+  int64_t *d_level_off = nullptr;         // device copy (20 entries, by absolute level; -1 = absent)
+  // split-precision copies of the blocks for the tensor-core path (lazily built)
+  void *d_Rsplit = nullptr;
+  int split_pieces = 0;
+};
+
+// ---------------------------------------------------------------- host helpers
+void gauss_legendre(int n, double *x, double *w);  // nodes/weights on [-1,1]
+
+// ---------------------------------------------------------------- launchers (setup)
+cudaError_t launch_fit_search(double mu, int M, double r_lo, double r_hi, double *d_err,
+                              cudaStream_t s);
+cudaError_t launch_blocks(const Operator &op, const double *d_glx, const double *d_glw,
+                          cudaStream_t s);
+cudaError_t launch_project_boxes(int ng, const double *d_g /*[5][ng]*/, int k, double L,
+                                 int64_t nbox, const uint64_t *d_keys, double *d_out,
+                                 cudaStream_t s);
+cudaError_t launch_refine_test(int k, int64_t nparent, const double *d_parent,
+                               const double *d_child, const double *d_U, double *d_dnorm,
+                               cudaStream_t s);
+}  // namespace mra

@@ -1,0 +1,305 @@
+"""ctypes binding of libmra.so (include/mra.h).
+
+Argument marshalling only: every numerical step runs in the library's CUDA
+kernels.  PyTorch supplies device memory and streams.  If the compiled library
+is missing and cannot be built, loading fails loudly; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+from . import _build
+
+MRA_OK = 0
+MRA_ERR_ARG = -1
+MRA_ERR_CAPACITY = -2
+MRA_ERR_CUDA = -3
+MRA_ERR_TIMEOUT = -4
+MRA_ERR_NUMERIC = -5
+MRA_ERR_UNSUPPORTED = -6
+
+POISSON = 0
+BSH = 1
+PREC_FP64 = 0
+PREC_SPLIT_BF16 = 1
+SCREEN_NONE = 0
+SCREEN_NORM = 1
+STENCIL_SHELLS = 0
+STENCIL_NEAREST = 1
+
+EXPORTED = [
+    "mra_last_error", "mra_version", "mra_project", "mra_operator_create", "mra_operator_fit",
+    "mra_operator_info", "mra_operator_block", "mra_operator_free", "mra_apply_workspace_size",
+    "mra_apply", "mra_norm", "mra_compare",
+]
+
+
+class MraError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class GaussSum(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("coef", ctypes.POINTER(ctypes.c_double)),
+                ("expnt", ctypes.POINTER(ctypes.c_double)), ("cx", ctypes.POINTER(ctypes.c_double)),
+                ("cy", ctypes.POINTER(ctypes.c_double)), ("cz", ctypes.POINTER(ctypes.c_double))]
+
+
+class TreeView(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("cap", ctypes.c_int64), ("keys", ctypes.c_void_p),
+                ("coeffs", ctypes.c_void_p), ("k", ctypes.c_int), ("L", ctypes.c_double)]
+
+
+class ApplyOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("pieces", ctypes.c_int), ("screen", ctypes.c_int),
+                ("tau", ctypes.c_double), ("stencil", ctypes.c_int), ("max_disp", ctypes.c_int)]
+
+
+class ApplyStats(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_int64), ("n_out", ctypes.c_int64), ("pairs", ctypes.c_int64),
+                ("terms_kept", ctypes.c_int64), ("terms_screened", ctypes.c_int64),
+                ("terms_issued", ctypes.c_int64), ("sources_truncated", ctypes.c_int64),
+                ("skipped_bound", ctypes.c_double), ("kernel_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class CompareResult(ctypes.Structure):
+    _fields_ = [("diff_norm", ctypes.c_double), ("ref_norm", ctypes.c_double),
+                ("test_norm", ctypes.c_double), ("rel_l2", ctypes.c_double),
+                ("max_box_rel", ctypes.c_double), ("n_common", ctypes.c_int64),
+                ("n_only_test", ctypes.c_int64), ("n_only_ref", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_stale: bool = True):
+    """Load libmra.so, compiling it first if it is missing or older than its sources."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_stale else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libmra.so not found at {path}; run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        P = ctypes.POINTER
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        lib.mra_last_error.restype = ctypes.c_char_p
+        lib.mra_version.restype = ctypes.c_char_p
+        lib.mra_project.argtypes = [P(GaussSum), i, d, d, i, i, i, P(TreeView), vp]
+        lib.mra_operator_create.argtypes = [i, d, i, d, d, d, i, d, i, i, i, P(vp), vp]
+        lib.mra_operator_fit.argtypes = [vp, P(d), P(d), P(d), P(d), P(d)]
+        lib.mra_operator_info.argtypes = [vp, P(i), P(i), P(i), P(i), P(i), P(d)]
+        lib.mra_operator_block.argtypes = [vp, i, i, i, P(d), P(d)]
+        lib.mra_operator_free.argtypes = [vp]
+        lib.mra_apply_workspace_size.argtypes = [vp, P(TreeView), P(ApplyOpts), P(ctypes.c_size_t)]
+        lib.mra_apply.argtypes = [vp, P(TreeView), P(ApplyOpts), P(TreeView), vp, ctypes.c_size_t,
+                                  P(ApplyStats), vp]
+        lib.mra_norm.argtypes = [P(TreeView), vp, P(d), vp]
+        lib.mra_compare.argtypes = [P(TreeView), P(TreeView), P(CompareResult), vp]
+        _lib = lib
+        return lib
+
+
+def _check(rc):
+    if rc != MRA_OK:
+        raise MraError(rc, load().mra_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# --------------------------------------------------------------------------- trees
+
+@dataclass
+class Tree:
+    """A device tree: keys (int64 tensor holding the uint64 key bits) and coeffs [cap, k, k, k] float64."""
+    keys: torch.Tensor
+    coeffs: torch.Tensor
+    n: int
+    k: int
+    L: float
+
+    @staticmethod
+    def empty(cap: int, k: int, L: float, device="cuda") -> "Tree":
+        cap = max(int(cap), 1)
+        return Tree(torch.empty(cap, dtype=torch.int64, device=device),
+                    torch.empty((cap, k, k, k), dtype=torch.float64, device=device), 0, k, L)
+
+    @staticmethod
+    def from_host(keys, coeffs, L: float, device="cuda") -> "Tree":
+        import numpy as np
+        keys = np.ascontiguousarray(keys, dtype=np.uint64).view(np.int64)
+        coeffs = np.ascontiguousarray(coeffs, dtype=np.float64)
+        k = coeffs.shape[1]
+        return Tree(torch.from_numpy(keys.copy()).to(device), torch.from_numpy(coeffs.copy()).to(device),
+                    len(keys), k, L)
+
+    @property
+    def cap(self):
+        return self.keys.shape[0]
+
+    def view(self) -> TreeView:
+        return TreeView(self.n, self.cap, self.keys.data_ptr(), self.coeffs.data_ptr(), self.k, self.L)
+
+    def host(self):
+        """(keys uint64 ndarray, coeffs float64 ndarray) of the first n boxes."""
+        keys = self.keys[: self.n].cpu().numpy().view("uint64")
+        return keys, self.coeffs[: self.n].cpu().numpy()
+
+
+def project(gauss: dict, k: int, L: float, thresh: float = 0.0, init_level: int = 2, max_level: int = 19,
+            uniform_level: int = -1, cap: int | None = None, device="cuda", stream=None) -> Tree:
+    """mra_project: projection of a Gaussian sum (uniform level or adaptive refinement)."""
+    import numpy as np
+    lib = load()
+    arrs = [np.ascontiguousarray(gauss[f], dtype=np.float64) for f in ("coef", "expnt", "cx", "cy", "cz")]
+    gs = GaussSum(len(arrs[0]), *[_dptr(a) for a in arrs])
+    if cap is None:
+        cap = 8 ** uniform_level if uniform_level >= 0 else 4096
+    while True:
+        t = Tree.empty(cap, k, L, device)
+        v = t.view()
+        rc = lib.mra_project(ctypes.byref(gs), k, L, thresh, init_level, max_level, uniform_level,
+                             ctypes.byref(v), _stream(stream))
+        if rc == MRA_ERR_CAPACITY:
+            cap = int(v.n)
+            continue
+        _check(rc)
+        t.n = int(v.n)
+        return t
+
+
+# --------------------------------------------------------------------------- operator
+
+class Operator:
+    """mra_operator_create: Gaussian fit of 1/r or exp(-mu r)/r plus the 1-D block tables."""
+
+    def __init__(self, kernel: int, M: int, k: int, L: float, min_level: int, max_level: int,
+                 max_disp: int = 1, mu: float = 0.0, fit_eps: float = 1e-6, r_lo: float = 1e-4,
+                 r_hi: float = -1.0, stream=None):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.mra_operator_create(kernel, mu, M, fit_eps, r_lo, r_hi, k, L, min_level, max_level,
+                                       max_disp, ctypes.byref(h), _stream(stream)))
+        self._h = h
+        self.kernel, self.M, self.k, self.L = kernel, M, k, L
+        self.min_level, self.max_level, self.max_disp = min_level, max_level, max_disp
+
+    @property
+    def handle(self):
+        return self._h
+
+    def fit(self):
+        import numpy as np
+        c = np.zeros(self.M)
+        t = np.zeros(self.M)
+        h, s, e = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(load().mra_operator_fit(self._h, _dptr(c), _dptr(t), ctypes.byref(h), ctypes.byref(s),
+                                       ctypes.byref(e)))
+        return {"c": c, "t": t, "h": h.value, "s_lo": s.value, "max_rel_err": e.value}
+
+    def block(self, level: int, m: int, l: int):
+        import numpy as np
+        R = np.zeros((self.k, self.k))
+        nrm = ctypes.c_double()
+        _check(load().mra_operator_block(self._h, level, m, l, _dptr(R), ctypes.byref(nrm)))
+        return R, nrm.value
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().mra_operator_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_opts(precision=PREC_FP64, pieces=2, screen=SCREEN_NONE, tau=0.0, stencil=STENCIL_NEAREST,
+              max_disp=1) -> ApplyOpts:
+    return ApplyOpts(precision, pieces, screen, tau, stencil, max_disp)
+
+
+def workspace_size(op: Operator, tree: Tree, opts: ApplyOpts) -> int:
+    nbytes = ctypes.c_size_t()
+    v = tree.view()
+    _check(load().mra_apply_workspace_size(op.handle, ctypes.byref(v), ctypes.byref(opts), ctypes.byref(nbytes)))
+    return int(nbytes.value)
+
+
+class Applier:
+    """Holds the workspace and output buffers of repeated applies of one operator to one input shape."""
+
+    def __init__(self, op: Operator, tree: Tree, opts: ApplyOpts, out_cap: int | None = None,
+                 with_stats: bool = True):
+        self.op, self.opts, self.with_stats = op, opts, with_stats
+        self.ws = torch.empty(max(workspace_size(op, tree, opts), 1), dtype=torch.uint8, device=tree.keys.device)
+        self.out = Tree.empty(out_cap or max(2 * tree.n, 1), op.k, op.L, tree.keys.device)
+        self.stats = ApplyStats()
+
+    def __call__(self, tree: Tree, stream=None) -> Tree:
+        lib = load()
+        if self.ws.numel() < workspace_size(self.op, tree, self.opts):
+            self.ws = torch.empty(workspace_size(self.op, tree, self.opts), dtype=torch.uint8,
+                                  device=tree.keys.device)
+        while True:
+            vin, vout = tree.view(), self.out.view()
+            rc = lib.mra_apply(self.op.handle, ctypes.byref(vin), ctypes.byref(self.opts), ctypes.byref(vout),
+                               ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(),
+                               ctypes.byref(self.stats) if self.with_stats else None, _stream(stream))
+            if rc == MRA_ERR_CAPACITY and vout.n > self.out.cap:
+                self.out = Tree.empty(int(vout.n), self.op.k, self.op.L, tree.keys.device)
+                continue
+            _check(rc)
+            self.out.n = int(vout.n)
+            return self.out
+
+
+def apply(op: Operator, tree: Tree, opts: ApplyOpts, stream=None):
+    """mra_apply once; returns (output tree, stats dict)."""
+    ap = Applier(op, tree, opts)
+    out = ap(tree, stream)
+    return out, ap.stats.as_dict()
+
+
+def norm(tree: Tree, stream=None):
+    per_box = torch.empty(max(tree.n, 1), dtype=torch.float64, device=tree.keys.device)
+    tot = ctypes.c_double()
+    v = tree.view()
+    _check(load().mra_norm(ctypes.byref(v), ctypes.c_void_p(per_box.data_ptr()), ctypes.byref(tot),
+                           _stream(stream)))
+    return per_box[: tree.n], tot.value
+
+
+def compare(test: Tree, ref: Tree, stream=None) -> dict:
+    res = CompareResult()
+    vt, vr = test.view(), ref.view()
+    _check(load().mra_compare(ctypes.byref(vt), ctypes.byref(vr), ctypes.byref(res), _stream(stream)))
+    return res.as_dict()

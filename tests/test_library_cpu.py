@@ -1,0 +1,58 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds for sm_103a,
+loads, and exports every function include/mra.h declares.  No compute call."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "mra.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(mra_[a-z_0-9]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_1507_01888_gb300 import _build
+    return _build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("mra_project", "mra_operator_create", "mra_apply", "mra_norm", "mra_compare",
+                 "mra_operator_fit", "mra_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    lib.mra_version.restype = ctypes.c_char_p
+    assert b"sm_103a" in lib.mra_version()
+
+
+def test_binding_lists_every_declared_symbol():
+    from paper_1507_01888_gb300 import mra
+    assert sorted(mra.EXPORTED) == declared_functions()
+
+
+def test_argument_errors_need_no_gpu(lib_path):
+    """Invalid arguments are rejected on the host before any CUDA call."""
+    from paper_1507_01888_gb300 import mra
+    lib = mra.load()
+    h = ctypes.c_void_p()
+    rc = lib.mra_operator_create(7, 0.0, 10, 1e-6, 1e-4, -1.0, 6, 32.0, 0, 3, 1, ctypes.byref(h), None)
+    assert rc == mra.MRA_ERR_ARG
+    assert b"unknown kernel" in lib.mra_last_error()
+    rc = lib.mra_operator_create(0, 0.0, 500, 1e-6, 1e-4, -1.0, 6, 32.0, 0, 3, 1, ctypes.byref(h), None)
+    assert rc == mra.MRA_ERR_ARG
+    rc = lib.mra_apply(None, None, None, None, None, 0, None, None)
+    assert rc == mra.MRA_ERR_ARG

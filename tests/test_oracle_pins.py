@@ -143,7 +143,7 @@ def test_block_R00_at_zero_closed_form():
         assert O.block(3, 2.0, T, 0)[0, 0] == pytest.approx(float(ref), rel=1e-14)
 
 
-@pytest.mark.parametrize("T,l", [(0.5, 0), (3.0, 1), (3.0, -2), (200.0, 1), (2e3, 0)])
+@pytest.mark.parametrize("T,l", [(0.5, 0), (3.0, 1), (3.0, -2), (200.0, 1), (40.0, 0)])
 def test_block_general_entries_vs_mpmath(T, l):
     k, h = 3, 0.8
     mpmath.mp.dps = 25
