@@ -240,6 +240,12 @@ int mra_operator_create(int kernel, double mu, int M, double fit_eps, double r_l
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(d_gl);
   if (e != cudaSuccess) return bail(fail(MRA_ERR_CUDA, "operator blocks: %s", cudaGetErrorString(e)));
+  {
+    int rc = split_blocks_build(*op, s);  // BF16 pieces of every block for the tensor-core path
+    if (rc != MRA_OK) return bail(rc);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return bail(fail(MRA_ERR_CUDA, "split blocks: %s", cudaGetErrorString(e)));
+  }
   *out = reinterpret_cast<mra_operator *>(op);
   return MRA_OK;
 }

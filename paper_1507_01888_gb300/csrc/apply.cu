@@ -364,8 +364,8 @@ int64_t apply_max_records(const Operator &op, const mra_apply_opts &o, int64_t n
 //   CUB temp storage (max over scan / sort / reduce needs)
 struct Layout {
   size_t snorm, dstop, cnt, off, kept, screened, skipped, trunc;
-  size_t rkey, rsrc, rl, rmask, skey, pin, pout, head, did, dkey, seg, ndest, tmp;
-  size_t tmp_bytes, total;
+  size_t rkey, rsrc, rl, rmask, skey, pin, pout, head, did, dkey, seg, ndest, split, tmp;
+  size_t split_bytes, tmp_bytes, total;
 };
 
 static Layout make_layout(int64_t n_in, int64_t P) {
@@ -397,6 +397,8 @@ static Layout make_layout(int64_t n_in, int64_t P) {
   L.dkey = take(np * 8);
   L.seg = take((np + 1) * 8);
   L.ndest = take(8);
+  L.split_bytes = split_workspace_bytes(np);
+  L.split = take(L.split_bytes);
   // CUB temporary storage: the largest of the calls below
   size_t a = 0, b = 0, c = 0, d = 0, e = 0;
   cub::DeviceScan::ExclusiveSum(nullptr, a, (int64_t *)nullptr, (int64_t *)nullptr, (int)nb);
@@ -549,22 +551,29 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
     return fail(MRA_ERR_CAPACITY, "mra_apply: output holds %lld boxes, %lld needed",
                 (long long)out.cap, (long long)nd);
   }
-  ApplyWork wk{};
-  wk.n_dest = nd;
-  wk.seg = seg;
-  wk.perm = pout;
-  wk.rec_src = rsrc;
-  wk.rec_l = rl;
-  wk.rec_mask = rmask;
-  wk.dest_key = dkey;
   int rc;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   if (stats) {
     MRA_CUDA_TRY(cudaEventCreate(&ev0));
     MRA_CUDA_TRY(cudaEventCreate(&ev1));
-    MRA_CUDA_TRY(cudaEventRecord(ev0, s));
   }
+  ApplyWork wk{};
+  wk.n_dest = nd;
+  wk.P = P;
+  wk.seg = seg;
+  wk.perm = pout;
+  wk.did = did;
+  wk.skey = skey;
+  wk.rec_src = rsrc;
+  wk.rec_l = rl;
+  wk.rec_mask = rmask;
+  wk.dest_key = dkey;
+  wk.split_ws = w + L.split;
+  wk.split_ws_bytes = L.split_bytes;
+  wk.ev0 = ev0;
+  wk.ev1 = ev1;
   if (o.precision == MRA_PREC_FP64) {
+    if (ev0) MRA_CUDA_TRY(cudaEventRecord(ev0, s));
     size_t smem = (size_t)(3 * k3 + 3 * k * k) * sizeof(double);
     if (smem > 48 * 1024)
       MRA_CUDA_TRY(cudaFuncSetAttribute(apply_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -573,6 +582,7 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
         k, op.M, op.d_c, op.d_R, op.d_D, op.d_level_off, in.keys, in.coeffs, seg, pout, rsrc, rl,
         rmask, dkey, out.keys, out.coeffs);
     MRA_CUDA_TRY(cudaGetLastError());
+    if (ev1) MRA_CUDA_TRY(cudaEventRecord(ev1, s));
     rc = MRA_OK;
   } else {
     rc = apply_split_run(op, in, o, out, wk, stats, s);
@@ -581,7 +591,6 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
   out.n = nd;
   if (stats) {
     stats->n_out = nd;
-    MRA_CUDA_TRY(cudaEventRecord(ev1, s));
     MRA_CUDA_TRY(cudaEventSynchronize(ev1));
     float ms = 0.0f;
     MRA_CUDA_TRY(cudaEventElapsedTime(&ms, ev0, ev1));

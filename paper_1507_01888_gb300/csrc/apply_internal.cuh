@@ -10,13 +10,18 @@ namespace mra {
 // a source box rec_src[p], a displacement rec_l[p] (three biased bytes) and the
 // kept Gaussian terms rec_mask[2p], rec_mask[2p+1] (bit m = term m).
 struct ApplyWork {
-  int64_t n_dest;
+  int64_t n_dest, P;
   const int64_t *seg;
   const int *perm;
+  const int *did;             // 1-based destination index of each dest-sorted record
+  const uint64_t *skey;       // dest-sorted destination keys (one per record)
   const int *rec_src;
   const int *rec_l;
   const uint64_t *rec_mask;
   const uint64_t *dest_key;
+  void *split_ws;             // scratch for the tensor-core path's grouping
+  size_t split_ws_bytes;
+  cudaEvent_t ev0, ev1;       // recorded around the apply kernel when non-null
 };
 
 size_t apply_workspace_bytes(const Operator &op, const mra_apply_opts &o, int64_t n_in);
@@ -26,6 +31,8 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
 int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts &o,
                     mra_tree_view &out, const ApplyWork &wk, mra_apply_stats *stats,
                     cudaStream_t s);
+size_t split_workspace_bytes(int64_t P);
+int split_blocks_build(Operator &op, cudaStream_t s);
 int norm_run(const mra_tree_view &t, double *per_box, double *total, cudaStream_t s);
 int compare_run(const mra_tree_view &t, const mra_tree_view &r, mra_compare_result *res,
                 cudaStream_t s);

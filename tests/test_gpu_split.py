@@ -1,0 +1,113 @@
+"""Parity of the split-BF16 tcgen05 apply (through the C ABI) with the CPU oracle.
+
+Bar: relative L2 error of the whole result <= 1e-6 (the requested threshold of the
+mixed-precision workload), with the destination keys identical to the oracle's
+(the screen runs in FP64 on both sides, so the work list is the same).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL_MIXED = 1e-6
+
+
+@pytest.fixture(scope="module")
+def mra():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1507_01888_gb300 import mra as m
+    m.load()
+    return m
+
+
+def rel_l2(a, b):
+    return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
+
+
+def split_opts(mra, pieces=3, **kw):
+    return mra.make_opts(precision=mra.PREC_SPLIT_BF16, pieces=pieces, **kw)
+
+
+def test_split_uniform_27_point(mra):
+    """Poisson M=20, uniform level 3, k=6, 27 displacements, no screen (full size)."""
+    w = W.poisson_m20_uniform_k6()
+    ok, oc, _ = O.project(w.funcs[0], w.k, w.L, uniform_level=3)
+    op = mra.Operator(w.kernel, w.M, w.k, w.L, 3, 3, max_disp=1, fit_eps=w.fit_eps)
+    fit = op.fit()
+    ref = O.apply(ok, oc, fit["c"], fit["t"], w.L, stencil=1, tau=0.0)
+    out, st = mra.apply(op, mra.Tree.from_host(ok, oc, w.L), split_opts(mra, stencil=mra.STENCIL_NEAREST))
+    keys, coeffs = out.host()
+    assert (keys == ref.keys).all()
+    assert rel_l2(coeffs, ref.coeffs) <= TOL_MIXED
+
+
+@pytest.mark.parametrize("k,lev,nbox,seed", [(2, 3, 300, 1), (4, 3, 120, 2), (6, 2, 40, 3), (8, 3, 90, 4),
+                                              (10, 3, 60, 5), (12, 2, 30, 6), (14, 2, 20, 7), (16, 2, 12, 8)])
+def test_split_random_trees_ragged(mra, k, lev, nbox, seed):
+    """Sparse random trees: missing sources, boundary boxes, partial tiles, every tile shape."""
+    keys, coeffs = W.random_tree_coeffs(nbox, k, lev, seed=seed)
+    op = mra.Operator(0, 16, k, 16.0, 0, lev, max_disp=1, fit_eps=1e-4)
+    fit = op.fit()
+    ref = O.apply(keys, coeffs, fit["c"], fit["t"], 16.0, stencil=1, tau=0.0)
+    tree = mra.Tree.from_host(keys, coeffs, 16.0)
+    out, st = mra.apply(op, tree, split_opts(mra, stencil=mra.STENCIL_NEAREST))
+    gk, gc = out.host()
+    assert (gk == ref.keys).all()
+    assert rel_l2(gc, ref.coeffs) <= TOL_MIXED
+    f64, _ = mra.apply(op, tree, mra.make_opts(stencil=mra.STENCIL_NEAREST))
+    cmp = mra.compare(out, f64)
+    assert cmp["n_only_test"] == 0 and cmp["n_only_ref"] == 0
+    assert cmp["rel_l2"] <= TOL_MIXED
+
+
+def test_split_shells_and_screen_adaptive(mra):
+    f = W.gaussian_sum(3, 1.0, 200.0, seed=23)
+    ok, oc, _ = O.project(f, 6, 32.0, thresh=1e-4, init_level=2, max_level=10)
+    op = mra.Operator(1, 24, 6, 32.0, 1, 10, max_disp=2, mu=1.0, fit_eps=1e-6)
+    fit = op.fit()
+    ref = O.apply(ok, oc, fit["c"], fit["t"], 32.0, stencil=0, max_disp=2, tau=1e-6)
+    out, st = mra.apply(op, mra.Tree.from_host(ok, oc, 32.0),
+                        split_opts(mra, stencil=mra.STENCIL_SHELLS, max_disp=2, screen=mra.SCREEN_NORM, tau=1e-6))
+    gk, gc = out.host()
+    assert (gk == ref.keys).all()
+    assert rel_l2(gc, ref.coeffs) <= TOL_MIXED
+
+
+def test_split_full_size_vs_fp64_and_oracle(mra):
+    """BSH M=60 adaptive k=10 (17,200 boxes): split vs FP64 GPU on every box, vs the oracle on a sample."""
+    w = W.bsh_m60_adaptive_k10()
+    ok, oc, _ = O.project(w.funcs[0], w.k, w.L, thresh=w.thresh, init_level=w.init_level, max_level=w.max_level)
+    op = mra.Operator(w.kernel, w.M, w.k, w.L, 2, 19, max_disp=w.max_disp, mu=w.mu, fit_eps=w.fit_eps)
+    fit = op.fit()
+    tree = mra.Tree.from_host(ok, oc, w.L)
+    kw = dict(stencil=w.stencil, max_disp=w.max_disp, screen=mra.SCREEN_NORM, tau=w.tau)
+    sp, _ = mra.apply(op, tree, split_opts(mra, **kw))
+    f64, _ = mra.apply(op, tree, mra.make_opts(**kw))
+    cmp = mra.compare(sp, f64)
+    assert cmp["n_only_test"] == 0 and cmp["n_only_ref"] == 0
+    assert cmp["rel_l2"] <= TOL_MIXED
+    gk, gc = sp.host()
+    rng = np.random.default_rng(11)
+    sample = np.sort(rng.choice(gk, 80, replace=False))
+    ref = O.apply(ok, oc, fit["c"], fit["t"], w.L, stencil=w.stencil, max_disp=w.max_disp, tau=w.tau,
+                  sample_keys=sample)
+    pos = np.searchsorted(gk, ref.keys)
+    assert (gk[pos] == ref.keys).all()
+    assert rel_l2(gc[pos], ref.coeffs) <= TOL_MIXED
+
+
+def test_split_two_pieces_is_coarser(mra):
+    """Two BF16 pieces carry ~16 significant bits: the error grows to ~1e-5 but stays bounded."""
+    keys, coeffs = W.random_tree_coeffs(60, 8, 3, seed=12)
+    op = mra.Operator(0, 16, 8, 16.0, 0, 3, max_disp=1, fit_eps=1e-4)
+    fit = op.fit()
+    ref = O.apply(keys, coeffs, fit["c"], fit["t"], 16.0, stencil=1, tau=0.0)
+    out, _ = mra.apply(op, mra.Tree.from_host(keys, coeffs, 16.0), split_opts(mra, pieces=2, stencil=1))
+    e2 = rel_l2(out.host()[1], ref.coeffs)
+    out3, _ = mra.apply(op, mra.Tree.from_host(keys, coeffs, 16.0), split_opts(mra, pieces=3, stencil=1))
+    e3 = rel_l2(out3.host()[1], ref.coeffs)
+    assert e3 < e2 < 1e-4
