@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) apply_split_kernel(SplitArgs
   __shared__ int slot_src[MAX_G];
   __shared__ uint64_t slot_mask[MAX_G][2];
   __shared__ uint64_t uni[2];
-  __shared__ int g_level, g_l, s_abort;
+  __shared__ int g_level, g_l;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tile = blockIdx.x;
@@ -119,10 +119,8 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) apply_split_kernel(SplitArgs
     for (int i = tid; i < n16; i += SPLIT_THREADS) z[i] = make_int4(0, 0, 0, 0);
   }
   const uint32_t bar_a = tc::smem_u32(&bar);
-  if (tid == 0) {
-    tc::mbar_init(bar_a, 1);
-    s_abort = 0;
-  }
+  if (tid == 0) tc::mbar_init(bar_a, 1);
+  bool aborted = false;  // identical in every thread: set only from a CTA-wide vote
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(&tmem_holder), TMEM_COLS);
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   tc::fence_proxy_async_smem();
@@ -163,10 +161,8 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) apply_split_kernel(SplitArgs
     phase ^= 1u;
     int bad = __syncthreads_or(!ok);
     if (bad) {
-      if (tid == 0) {
-        atomicExch(a.err, 1);
-        s_abort = 1;
-      }
+      aborted = true;
+      if (tid == 0) atomicExch(a.err, 1);
     }
     tc::fence_after_sync();
     return !bad;
@@ -204,7 +200,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) apply_split_kernel(SplitArgs
   };
 
   const int g0 = a.tile_gstart[tile], g1 = a.tile_gstart[tile + 1];
-  for (int g = g0; g < g1 && !s_abort; ++g) {
+  for (int g = g0; g < g1 && !aborted; ++g) {
     const int r0 = a.grp_start[g], r1 = a.grp_start[g + 1];
     if (tid < MAX_G) {
       slot_src[tid] = -1;
@@ -248,9 +244,9 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) apply_split_kernel(SplitArgs
     const int Dop = a.Dlev[lev], nl = 2 * Dop + 1;
     const int ld[3] = {(lp & 255) - 128, ((lp >> 8) & 255) - 128, ((lp >> 16) & 255) - 128};
     const int64_t lbase = a.level_off[lev];
-    for (int w = 0; w < 2 && !s_abort; ++w) {
+    for (int w = 0; w < 2 && !aborted; ++w) {
       uint64_t bits = uni[w];
-      while (bits && !s_abort) {
+      while (bits && !aborted) {
         const int m = w * 64 + __ffsll((long long)bits) - 1;
         bits &= bits - 1;
         // B operands of the three stages: blocks (m, lx), (m, ly), (m, lz)
@@ -319,7 +315,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) apply_split_kernel(SplitArgs
     __syncthreads();
   }
   // write the destinations: row (i, ix, iy), columns iz
-  if (!s_abort) {
+  if (!aborted) {
 #pragma unroll
     for (int q = 0; q < MAX_TILES / 2 + 1; ++q) {
       int t = half + 2 * q;
@@ -340,7 +336,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) apply_split_kernel(SplitArgs
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (s_abort && tid == 0) tc::mbar_wait(bar_a, phase ^ 1u, WAIT_CYCLES);  // let in-flight MMAs finish
+  if (aborted && tid == 0) tc::mbar_wait(bar_a, phase ^ 1u, WAIT_CYCLES);  // let in-flight MMAs finish
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, TMEM_COLS);
 }
