@@ -34,7 +34,9 @@ namespace {
 
 constexpr int SPLIT_THREADS = 256;      // 8 warps: two warps per tensor-memory lane quarter
 constexpr int MAX_TILES = 7;            // 128-row MMA tiles per stage (G k^2 <= 896)
-constexpr int TILE_BYTES = 4096;        // one 128 x 16 BF16 operand tile
+constexpr int MG_BYTES = 272;           // stride of the 8-row groups: 256 B of core matrices + 16 B
+                                        // so that consecutive groups start 4 banks apart
+constexpr int TILE_BYTES = 16 * MG_BYTES;  // one 128 x 16 BF16 operand tile
 constexpr int BPIECE_BYTES = 512;       // one 16 x 16 BF16 block piece
 constexpr int BSTAGE_BYTES = 3 * BPIECE_BYTES;
 constexpr int MAX_G = 32;
@@ -46,12 +48,13 @@ __host__ __device__ inline int tile_boxes(int k) {
   return g > MAX_G ? MAX_G : (g < 1 ? 1 : g);
 }
 
-// byte offset of element (row m, contraction kk) in an MN-major operand
-// (core matrices of 8 contraction rows x 8 consecutive rows; 16 row-groups of a
-// 128-row tile at 256 B, the two contraction groups at 128 B)
+// byte offset of element (row m, contraction kk) in an MN-major operand: core
+// matrices of 8 contraction rows x 8 consecutive rows (128 B); the two
+// contraction groups of a row group 128 B apart (descriptor LBO), the 16 row
+// groups of a 128-row tile MG_BYTES apart (descriptor SBO)
 __device__ __forceinline__ uint32_t a_off(int m, int kk) {
-  return (uint32_t)((m >> 7) * TILE_BYTES + ((m & 127) >> 3) * 256 + (kk >> 3) * 128 + (kk & 7) * 16 +
-                    (m & 7) * 2);
+  return (uint32_t)((m >> 7) * TILE_BYTES + ((m & 127) >> 3) * MG_BYTES + (kk >> 3) * 128 +
+                    (kk & 7) * 16 + (m & 7) * 2);
 }
 
 __device__ __forceinline__ void split3(double x, __nv_bfloat16 &p0, __nv_bfloat16 &p1,
@@ -146,7 +149,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) apply_split_kernel(SplitArgs
     for (int t = 0; t < T; ++t) {
       uint32_t d = tmem + (uint32_t)(t * 48);
       for (int p = 0; p < P; ++p) {
-        uint64_t ad = tc::smem_desc(tc::smem_u32(A + (p * T + t) * TILE_BYTES), 128, 256);
+        uint64_t ad = tc::smem_desc(tc::smem_u32(A + (p * T + t) * TILE_BYTES), 128, MG_BYTES);
         uint64_t bd = tc::smem_desc(bdesc_addr, 128, 256);
         // A piece p times B pieces 0..P-1-p (stacked along N) into column groups p..P-1
         tc::mma_bf16(d + 16 * p, ad, bd, idesc_n[P - 1 - p], p > 0 ? 1u : 0u);
@@ -186,16 +189,33 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) apply_split_kernel(SplitArgs
   };
 
   // write the k values of output row (b, c) with new index d into the next operand:
-  // element [contraction a][row (i, b, c, d)] for d = 0..k-1
+  // element [contraction a][row (i, b, c, d)] for d = 0..k-1.  For even k the run
+  // starts on an even row, so pairs of rows share one 32-bit word.
   auto store_run = [&](unsigned char *A, int i, int a_idx, int b_idx, const float *v) {
     int mrow = i * k2 + b_idx * k;  // rows (i, b, d) for d = 0..k-1
-    for (int d = 0; d < k; ++d) {
-      __nv_bfloat16 p0, p1, p2;
-      split3f(v[d], p0, p1, p2);
-      uint32_t off = a_off(mrow + d, a_idx);
-      *(__nv_bfloat16 *)(A + off) = p0;
-      *(__nv_bfloat16 *)(A + T * TILE_BYTES + off) = p1;
-      if (P > 2) *(__nv_bfloat16 *)(A + 2 * T * TILE_BYTES + off) = p2;
+    const int stride = T * TILE_BYTES;
+    if ((k & 1) == 0) {
+#pragma unroll
+      for (int d = 0; d < 16; d += 2) {
+        if (d < k) {
+          __nv_bfloat16 a0, a1, a2, b0, b1, b2;
+          split3f(v[d], a0, a1, a2);
+          split3f(v[d + 1], b0, b1, b2);
+          uint32_t off = a_off(mrow + d, a_idx);
+          *(__nv_bfloat162 *)(A + off) = __halves2bfloat162(a0, b0);
+          *(__nv_bfloat162 *)(A + stride + off) = __halves2bfloat162(a1, b1);
+          if (P > 2) *(__nv_bfloat162 *)(A + 2 * stride + off) = __halves2bfloat162(a2, b2);
+        }
+      }
+    } else {
+      for (int d = 0; d < k; ++d) {
+        __nv_bfloat16 p0, p1, p2;
+        split3f(v[d], p0, p1, p2);
+        uint32_t off = a_off(mrow + d, a_idx);
+        *(__nv_bfloat16 *)(A + off) = p0;
+        *(__nv_bfloat16 *)(A + stride + off) = p1;
+        if (P > 2) *(__nv_bfloat16 *)(A + 2 * stride + off) = p2;
+      }
     }
   };
 
@@ -227,18 +247,40 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) apply_split_kernel(SplitArgs
       }
     }
     __syncthreads();
-    // stage-1 operand: sources, rows (i, jy, jz), contraction jx
-    for (int e = tid; e < G * k3; e += SPLIT_THREADS) {
-      int i = e / k3, rest = e - i * k3;
-      int jx = rest / k2, q = rest - jx * k2;
-      int src = slot_src[i];
-      double x = src >= 0 ? a.in_coeffs[(int64_t)src * k3 + rest] : 0.0;
-      __nv_bfloat16 p0, p1, p2;
-      split3(x, p0, p1, p2);
-      uint32_t off = a_off(i * k2 + q, jx);
-      *(__nv_bfloat16 *)(A1 + off) = p0;
-      *(__nv_bfloat16 *)(A1 + T * TILE_BYTES + off) = p1;
-      if (P > 2) *(__nv_bfloat16 *)(A1 + 2 * T * TILE_BYTES + off) = p2;
+    // stage-1 operand: sources, rows (i, jy, jz), contraction jx (pairs of rows when k is even)
+    if ((k & 1) == 0) {
+      for (int e = tid; e < G * k3 / 2; e += SPLIT_THREADS) {
+        int e2 = 2 * e;
+        int i = e2 / k3, rest = e2 - i * k3;
+        int jx = rest / k2, q = rest - jx * k2;
+        int src = slot_src[i];
+        double x0 = 0.0, x1 = 0.0;
+        if (src >= 0) {
+          double2 xx = *(const double2 *)(a.in_coeffs + (int64_t)src * k3 + rest);
+          x0 = xx.x;
+          x1 = xx.y;
+        }
+        __nv_bfloat16 a0, a1, a2, b0, b1, b2;
+        split3(x0, a0, a1, a2);
+        split3(x1, b0, b1, b2);
+        uint32_t off = a_off(i * k2 + q, jx);
+        *(__nv_bfloat162 *)(A1 + off) = __halves2bfloat162(a0, b0);
+        *(__nv_bfloat162 *)(A1 + T * TILE_BYTES + off) = __halves2bfloat162(a1, b1);
+        if (P > 2) *(__nv_bfloat162 *)(A1 + 2 * T * TILE_BYTES + off) = __halves2bfloat162(a2, b2);
+      }
+    } else {
+      for (int e = tid; e < G * k3; e += SPLIT_THREADS) {
+        int i = e / k3, rest = e - i * k3;
+        int jx = rest / k2, q = rest - jx * k2;
+        int src = slot_src[i];
+        double x = src >= 0 ? a.in_coeffs[(int64_t)src * k3 + rest] : 0.0;
+        __nv_bfloat16 p0, p1, p2;
+        split3(x, p0, p1, p2);
+        uint32_t off = a_off(i * k2 + q, jx);
+        *(__nv_bfloat16 *)(A1 + off) = p0;
+        *(__nv_bfloat16 *)(A1 + T * TILE_BYTES + off) = p1;
+        if (P > 2) *(__nv_bfloat16 *)(A1 + 2 * T * TILE_BYTES + off) = p2;
+      }
     }
     const int lev = g_level, lp = g_l;
     const int Dop = a.Dlev[lev], nl = 2 * Dop + 1;
