@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--pieces", type=int, default=3)
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU seconds of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--clocks-csv", default=None, help="also write the nvidia-smi samples here")
     return p.parse_args()
 
 
@@ -120,10 +121,9 @@ def cpu_baseline(w, target_s=12.0, seed=12345):
             "t_setup": t_setup, "cores": cores, "terms_total": r.terms_total, "dest_total": r.dest_total}
 
 
-def clocks_start():
+def clocks_start(path=None):
     try:
-        f = open(os.path.join(ROOT, "gpurun_out", "clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                 else os.devnull, "w")
+        f = open(path, "w") if path else None
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -259,7 +259,7 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clk = clocks_start()
+    clk = clocks_start(args.clocks_csv)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     kernel_ms = []
     t_wall = time.perf_counter()
