@@ -66,6 +66,7 @@ extern "C" {
 #define MRA_MAX_LEVEL 19
 #define MRA_MAX_K 16
 #define MRA_MAX_TERMS 128
+#define MRA_NOALLOC_MAX_BOXES (1 << 20) /* largest tree mra_norm_noalloc accepts */
 
 /* ---- data types ----------------------------------------------------------- */
 
@@ -203,6 +204,26 @@ int mra_apply(const mra_operator *op, const mra_tree_view *in, const mra_apply_o
 /* Per-box Frobenius norms (device array of tree->n doubles, may be NULL) and
  * the total L2 norm (host double, may be NULL).  Deterministic reduction. */
 int mra_norm(const mra_tree_view *tree, double *per_box, double *total, void *stream);
+
+/* mra_norm without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory -- code
+ * whose device memory is owned entirely by another allocator (a framework's
+ * caching allocator, or an application with a fixed memory budget), where a
+ * cudaMalloc would fail or fragment that pool, and latency-critical loops that
+ * cannot afford the device-wide synchronisation cudaMalloc/cudaFree may cause.
+ * Same results as mra_norm (per-box norms into the caller's device array
+ * per_box, may be NULL; total into the host double, may be NULL).
+ * Scratch is one fixed array of MRA_NOALLOC_MAX_BOXES + 32 doubles (8 MiB) in
+ * the library's device memory, present on every GPU that loads the library
+ * until the process exits; trees with more boxes are rejected with
+ * MRA_ERR_CAPACITY before any GPU work.  The first call on each device looks up
+ * the array's device address (with that device current); make that first call
+ * before any stream capture.  All calls share the array and nothing carries
+ * over between calls (every slot read is written earlier in the same call), but
+ * calls that overlap on the GPU (e.g. on two streams) race on it.  The call
+ * allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ * Synchronises `stream`. */
+int mra_norm_noalloc(const mra_tree_view *tree, double *per_box, double *total, void *stream);
 
 /* Compare two trees with the same k: boxes are matched by key; a box present
  * in one tree only counts in full.  Host result; synchronises `stream`. */

@@ -35,8 +35,9 @@ STENCIL_NEAREST = 1
 EXPORTED = [
     "mra_last_error", "mra_version", "mra_project", "mra_operator_create", "mra_operator_fit",
     "mra_operator_info", "mra_operator_block", "mra_operator_free", "mra_apply_workspace_size",
-    "mra_apply", "mra_norm", "mra_compare",
+    "mra_apply", "mra_norm", "mra_norm_noalloc", "mra_compare",
 ]
+NOALLOC_MAX_BOXES = 1 << 20
 
 
 class MraError(RuntimeError):
@@ -113,6 +114,7 @@ def load(build_if_stale: bool = True):
         lib.mra_apply.argtypes = [vp, P(TreeView), P(ApplyOpts), P(TreeView), vp, ctypes.c_size_t,
                                   P(ApplyStats), vp]
         lib.mra_norm.argtypes = [P(TreeView), vp, P(d), vp]
+        lib.mra_norm_noalloc.argtypes = [P(TreeView), vp, P(d), vp]
         lib.mra_compare.argtypes = [P(TreeView), P(TreeView), P(CompareResult), vp]
         _lib = lib
         return lib
@@ -296,6 +298,18 @@ def norm(tree: Tree, stream=None):
     _check(load().mra_norm(ctypes.byref(v), ctypes.c_void_p(per_box.data_ptr()), ctypes.byref(tot),
                            _stream(stream)))
     return per_box[: tree.n], tot.value
+
+
+def norm_noalloc(tree: Tree, per_box: torch.Tensor | None = None, stream=None):
+    """mra_norm_noalloc: the same norms, computed in the library's fixed device scratch.
+
+    For callers that cannot allocate device memory; per_box (float64, >= tree.n
+    entries on the tree's device) is the caller's, or None."""
+    tot = ctypes.c_double()
+    v = tree.view()
+    ptr = ctypes.c_void_p(per_box.data_ptr()) if per_box is not None else None
+    _check(load().mra_norm_noalloc(ctypes.byref(v), ptr, ctypes.byref(tot), _stream(stream)))
+    return tot.value
 
 
 def compare(test: Tree, ref: Tree, stream=None) -> dict:
