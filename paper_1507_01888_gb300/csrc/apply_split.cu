@@ -43,10 +43,6 @@ constexpr int MAX_G = 32;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr long long WAIT_CYCLES = 4000000000LL;  // bounded mbarrier wait (~2 s)
 
-__host__ __device__ inline int tile_boxes(int k) {
-  int g = 896 / (k * k);
-  return g > MAX_G ? MAX_G : (g < 1 ? 1 : g);
-}
 
 // byte offset of element (row m, contraction kk) in an MN-major operand: core
 // matrices of 8 contraction rows x 8 consecutive rows (128 B); the two
@@ -95,282 +91,358 @@ struct SplitArgs {
   int *err;
 };
 
-// KC >= k: compile-time column count of the FP64 accumulators (8, 12 or 16).
-template <int KC>
+// Exact widening of an FP32 value to FP64 with integer operations (IEEE layouts:
+// 8-bit exponent bias 127 -> 11-bit bias 1023, 23-bit -> 52-bit fraction), so that
+// only the multiply-add of the term sum uses the FP64 pipe.  FP32 subnormals
+// (|x| < 1.2e-38) become zero.
+__device__ __forceinline__ double widen(float f) {
+  uint32_t u = __float_as_uint(f);
+  uint32_t e = (u >> 23) & 0xFFu;
+  uint64_t sign = (uint64_t)(u >> 31) << 63;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  uint64_t ee = (e == 0xFFu) ? 2047u : (uint64_t)(e + 896u);
+  return __longlong_as_double((long long)(sign | (ee << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29)));
+}
+
+// Named barrier over one warpgroup (128 threads) with an OR vote.
+__device__ __forceinline__ bool wg_vote_or(int barrier_id, bool flag) {
+  uint32_t out;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, 128, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(out)
+      : "r"((uint32_t)flag), "r"(barrier_id)
+      : "memory");
+  return out != 0;
+}
+__device__ __forceinline__ void wg_sync(int barrier_id) {
+  asm volatile("bar.sync %0, 128;" ::"r"(barrier_id) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Compile-time shape for an even k: KC = k, TMAX tiles of 128 rows per stage.
+__host__ __device__ constexpr int tmax_for(int k) { return k <= 10 ? 7 : (k <= 12 ? 6 : (k <= 14 ? 5 : 4)); }
+__host__ __device__ constexpr int g_for(int k) {
+  return (128 * tmax_for(k)) / (k * k) > MAX_G ? MAX_G : (128 * tmax_for(k)) / (k * k);
+}
+
+// Warp roles: warpgroup 0 (warps 0-3) loads each group's sources and each term's
+// blocks, turns stage-1/2 outputs into the next stage's operands, and its thread 0
+// issues every MMA; warpgroup 1 (warps 4-7) adds each term's stage-3 output into
+// the FP64 accumulators.  Stage 3 of term q runs while warpgroup 0 already
+// works on term q+1; tensor memory holds D12 (stages 1 and 2, P column groups of 16
+// per tile) and, separately, D3 (stage 3, one column group per tile).
+template <int K>
 __global__ void __launch_bounds__(SPLIT_THREADS, 1) apply_split_kernel(SplitArgs a) {
+  constexpr int TM = tmax_for(K);
   extern __shared__ __align__(1024) unsigned char smem[];
   const int k = a.k, k2 = k * k, k3 = k2 * k, P = a.P, G = a.G, T = a.T;
   const int rows = G * k2;
-  unsigned char *A1 = smem;                               // [P][T][4096]
-  unsigned char *A23 = A1 + P * T * TILE_BYTES;           // [P][T][4096]
-  unsigned char *Bt = A23 + P * T * TILE_BYTES;           // [3 stages][1536]
-  __shared__ __align__(8) uint64_t bar;
+  unsigned char *A1 = smem;                          // [P][T][TILE_BYTES] stage-1 operand (sources)
+  unsigned char *A23 = A1 + P * T * TILE_BYTES;      // [P][T][TILE_BYTES] stage-2/3 operand
+  unsigned char *Bt = A23 + P * T * TILE_BYTES;      // [2 buffers][3 stages][1536]
+  __shared__ __align__(8) uint64_t bar12, bar3, bar_free, bar_drain;
   __shared__ uint32_t tmem_holder;
   __shared__ int slot_src[MAX_G];
   __shared__ uint64_t slot_mask[MAX_G][2];
   __shared__ uint64_t uni[2];
-  __shared__ int g_level, g_l;
+  __shared__ int g_level, g_l, total_it;
+  __shared__ double ring_c[2];
+  __shared__ uint32_t ring_keep[2];
+  __shared__ volatile int abort_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wg = warp >> 2, quarter = warp & 3;
   const int tile = blockIdx.x;
-  const int quarter = warp & 3, half = warp >> 2;
+  const int g0 = a.tile_gstart[tile], g1 = a.tile_gstart[tile + 1];
 
-  // zero all operand buffers once: the contraction padding (16 - k) and row padding stay zero
-  {
+  {  // zero all operand buffers once: contraction and row padding stay zero
     int4 *z = (int4 *)smem;
-    int n16 = (2 * P * T * TILE_BYTES + 3 * BSTAGE_BYTES) / 16;
+    int n16 = (2 * P * T * TILE_BYTES + 6 * BSTAGE_BYTES) / 16;
     for (int i = tid; i < n16; i += SPLIT_THREADS) z[i] = make_int4(0, 0, 0, 0);
   }
-  const uint32_t bar_a = tc::smem_u32(&bar);
-  if (tid == 0) tc::mbar_init(bar_a, 1);
-  bool aborted = false;  // identical in every thread: set only from a CTA-wide vote
+  if (tid == 0) {
+    tc::mbar_init(tc::smem_u32(&bar12), 1);
+    tc::mbar_init(tc::smem_u32(&bar3), 1);
+    tc::mbar_init(tc::smem_u32(&bar_free), 1);
+    tc::mbar_init(tc::smem_u32(&bar_drain), 1);
+    abort_flag = 0;
+    total_it = 0;
+  }
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(&tmem_holder), TMEM_COLS);
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   tc::fence_proxy_async_smem();
+  __syncthreads();
+  // total number of (group, term) iterations of this tile, for warpgroup 1's loop
+  if (warp == 0) {
+    int cnt = 0;
+    for (int g = g0; g < g1; ++g) {
+      uint64_t u0 = 0, u1 = 0;
+      for (int r = a.grp_start[g] + lane; r < a.grp_start[g + 1]; r += 32) {
+        int p = a.perm[a.val2[r]];
+        u0 |= a.rec_mask[2 * (int64_t)p];
+        u1 |= a.rec_mask[2 * (int64_t)p + 1];
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        u0 |= __shfl_xor_sync(0xffffffffu, u0, o);
+        u1 |= __shfl_xor_sync(0xffffffffu, u1, o);
+      }
+      cnt += __popcll(u0) + __popcll(u1);
+    }
+    if (lane == 0) total_it = cnt;
+  }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_holder;
-  uint32_t phase = 0;
+  const uint32_t d3col = (uint32_t)(T * 48);
+  const uint32_t b12 = tc::smem_u32(&bar12), b3 = tc::smem_u32(&bar3), bfree = tc::smem_u32(&bar_free);
+  const int nit = total_it;
 
-  double acc[4][KC];
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int j = 0; j < KC; ++j) acc[q][j] = 0.0;
-
-  const uint32_t idesc_n[3] = {tc::idesc_bf16(128, 16, 1, 0), tc::idesc_bf16(128, 32, 1, 0),
-                               tc::idesc_bf16(128, 48, 1, 0)};
-
-  // Issue one stage: for every 128-row tile, the P MMAs over the A pieces.
-  auto issue_stage = [&](const unsigned char *A, const unsigned char *B) {
-    tc::fence_after_sync();
-    const uint32_t bdesc_addr = tc::smem_u32(B);
-    for (int t = 0; t < T; ++t) {
-      uint32_t d = tmem + (uint32_t)(t * 48);
-      for (int p = 0; p < P; ++p) {
-        uint64_t ad = tc::smem_desc(tc::smem_u32(A + (p * T + t) * TILE_BYTES), 128, MG_BYTES);
-        uint64_t bd = tc::smem_desc(bdesc_addr, 128, 256);
-        // A piece p times B pieces 0..P-1-p (stacked along N) into column groups p..P-1
-        tc::mma_bf16(d + 16 * p, ad, bd, idesc_n[P - 1 - p], p > 0 ? 1u : 0u);
-      }
-    }
-    tc::mma_commit(bar_a);
-  };
-
-  // Every thread waits for the stage's MMAs; the CTA then agrees on the outcome.
-  auto wait_mma = [&]() -> bool {
-    bool ok = tc::mbar_wait(bar_a, phase, WAIT_CYCLES);
-    phase ^= 1u;
-    int bad = __syncthreads_or(!ok);
-    if (bad) {
-      aborted = true;
-      if (tid == 0) atomicExch(a.err, 1);
-    }
-    tc::fence_after_sync();
-    return !bad;
-  };
-
-  // Sum of this thread's P column groups of tile t (k values).
-  auto load_tile = [&](int t, float *v) {
-    uint32_t base = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(t * 48);
-    float c0[16], c1[16], c2[16];
-    tc::tmem_ld16(base, c0);
-    if (P > 1) tc::tmem_ld16(base + 16, c1);
-    if (P > 2) tc::tmem_ld16(base + 32, c2);
-    tc::tmem_ld_wait();
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      float s = c0[j];
-      if (P == 2) s = c1[j] + c0[j];
-      if (P == 3) s = (c2[j] + c1[j]) + c0[j];
-      v[j] = s;
-    }
-  };
-
-  // write the k values of output row (b, c) with new index d into the next operand:
-  // element [contraction a][row (i, b, c, d)] for d = 0..k-1.  For even k the run
-  // starts on an even row, so pairs of rows share one 32-bit word.
-  auto store_run = [&](unsigned char *A, int i, int a_idx, int b_idx, const float *v) {
-    int mrow = i * k2 + b_idx * k;  // rows (i, b, d) for d = 0..k-1
-    const int stride = T * TILE_BYTES;
-    if ((k & 1) == 0) {
-#pragma unroll
-      for (int d = 0; d < 16; d += 2) {
-        if (d < k) {
-          __nv_bfloat16 a0, a1, a2, b0, b1, b2;
-          split3f(v[d], a0, a1, a2);
-          split3f(v[d + 1], b0, b1, b2);
-          uint32_t off = a_off(mrow + d, a_idx);
-          *(__nv_bfloat162 *)(A + off) = __halves2bfloat162(a0, b0);
-          *(__nv_bfloat162 *)(A + stride + off) = __halves2bfloat162(a1, b1);
-          if (P > 2) *(__nv_bfloat162 *)(A + 2 * stride + off) = __halves2bfloat162(a2, b2);
+  if (wg == 0) {
+    // ======================================================= warpgroup 0 + MMA issue
+    const uint32_t idesc_n[3] = {tc::idesc_bf16(128, 16, 1, 0), tc::idesc_bf16(128, 32, 1, 0),
+                                 tc::idesc_bf16(128, 48, 1, 0)};
+    uint32_t p12 = 0, pfree = 0;
+    int it = 0;
+    bool bad = false;
+    auto issue_stacked = [&](const unsigned char *A, const unsigned char *B) {
+      tc::fence_after_sync();
+      for (int t = 0; t < T; ++t) {
+        uint32_t d = tmem + (uint32_t)(t * 48);
+        for (int p = 0; p < P; ++p) {
+          uint64_t ad = tc::smem_desc(tc::smem_u32(A + (p * T + t) * TILE_BYTES), 128, MG_BYTES);
+          uint64_t bd = tc::smem_desc(tc::smem_u32(B), 128, 256);
+          // A piece p times B pieces 0..P-1-p (stacked along N) into column groups p..P-1
+          tc::mma_bf16(d + 16 * p, ad, bd, idesc_n[P - 1 - p], p > 0 ? 1u : 0u);
         }
       }
-    } else {
-      for (int d = 0; d < k; ++d) {
-        __nv_bfloat16 p0, p1, p2;
-        split3f(v[d], p0, p1, p2);
+      tc::mma_commit(b12);
+    };
+    auto wait12 = [&]() -> bool {
+      bool ok = tc::mbar_wait(b12, p12, WAIT_CYCLES);
+      p12 ^= 1u;
+      bool any_bad = wg_vote_or(1, !ok || abort_flag);
+      tc::fence_after_sync();
+      return !any_bad;
+    };
+    // this thread's row of tile t: sum of the P column groups
+    auto load_tile = [&](int t, float *v) {
+      uint32_t base = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(t * 48);
+      float c0[16], c1[16], c2[16];
+      tc::tmem_ld16(base, c0);
+      if (P > 1) tc::tmem_ld16(base + 16, c1);
+      if (P > 2) tc::tmem_ld16(base + 32, c2);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = P == 3 ? (c2[j] + c1[j]) + c0[j] : (P == 2 ? c1[j] + c0[j] : c0[j]);
+    };
+    // element [contraction a][row (i, b, d)] for d = 0..k-1, pairs of rows per 32-bit store
+    auto store_run = [&](int i, int a_idx, int b_idx, const float *v) {
+      int mrow = i * k2 + b_idx * k;
+      const int stride = T * TILE_BYTES;
+#pragma unroll
+      for (int d = 0; d < K; d += 2) {
+        __nv_bfloat16 x0, x1, x2, y0, y1, y2;
+        split3f(v[d], x0, x1, x2);
+        split3f(v[d + 1], y0, y1, y2);
         uint32_t off = a_off(mrow + d, a_idx);
-        *(__nv_bfloat16 *)(A + off) = p0;
-        *(__nv_bfloat16 *)(A + stride + off) = p1;
-        if (P > 2) *(__nv_bfloat16 *)(A + 2 * stride + off) = p2;
+        *(__nv_bfloat162 *)(A23 + off) = __halves2bfloat162(x0, y0);
+        *(__nv_bfloat162 *)(A23 + stride + off) = __halves2bfloat162(x1, y1);
+        if (P > 2) *(__nv_bfloat162 *)(A23 + 2 * stride + off) = __halves2bfloat162(x2, y2);
       }
-    }
-  };
-
-  const int g0 = a.tile_gstart[tile], g1 = a.tile_gstart[tile + 1];
-  for (int g = g0; g < g1 && !aborted; ++g) {
-    const int r0 = a.grp_start[g], r1 = a.grp_start[g + 1];
-    if (tid < MAX_G) {
-      slot_src[tid] = -1;
-      slot_mask[tid][0] = slot_mask[tid][1] = 0ull;
-    }
-    if (tid == 0) uni[0] = uni[1] = 0ull;
-    __syncthreads();
-    for (int r = r0 + tid; r < r1; r += SPLIT_THREADS) {
-      int i = a.val2[r];
-      int p = a.perm[i];
-      int slot = (a.did[i] - 1) - tile * G;
-      if (slot < 0 || slot >= G) {
-        atomicExch(a.err, 2);
-        continue;
+    };
+    for (int g = g0; g < g1 && !bad; ++g) {
+      const int r0 = a.grp_start[g], r1 = a.grp_start[g + 1];
+      if (tid < MAX_G) {
+        slot_src[tid] = -1;
+        slot_mask[tid][0] = slot_mask[tid][1] = 0ull;
       }
-      slot_src[slot] = a.rec_src[p];
-      slot_mask[slot][0] = a.rec_mask[2 * (int64_t)p];
-      slot_mask[slot][1] = a.rec_mask[2 * (int64_t)p + 1];
-      atomicOr((unsigned long long *)&uni[0], (unsigned long long)a.rec_mask[2 * (int64_t)p]);
-      atomicOr((unsigned long long *)&uni[1], (unsigned long long)a.rec_mask[2 * (int64_t)p + 1]);
-      if (r == r0) {
-        g_l = a.rec_l[p];
-        g_level = key_level(a.dest_key[a.did[i] - 1]);
+      if (tid == 0) uni[0] = uni[1] = 0ull;
+      wg_sync(1);
+      for (int r = r0 + tid; r < r1; r += 128) {
+        int i = a.val2[r];
+        int p = a.perm[i];
+        int slot = (a.did[i] - 1) - tile * G;
+        if (slot < 0 || slot >= G) {
+          atomicExch(a.err, 2);
+          continue;
+        }
+        slot_src[slot] = a.rec_src[p];
+        slot_mask[slot][0] = a.rec_mask[2 * (int64_t)p];
+        slot_mask[slot][1] = a.rec_mask[2 * (int64_t)p + 1];
+        atomicOr((unsigned long long *)&uni[0], (unsigned long long)a.rec_mask[2 * (int64_t)p]);
+        atomicOr((unsigned long long *)&uni[1], (unsigned long long)a.rec_mask[2 * (int64_t)p + 1]);
+        if (r == r0) {
+          g_l = a.rec_l[p];
+          g_level = key_level(a.dest_key[a.did[i] - 1]);
+        }
       }
-    }
-    __syncthreads();
-    // stage-1 operand: sources, rows (i, jy, jz), contraction jx (pairs of rows when k is even)
-    if ((k & 1) == 0) {
-      for (int e = tid; e < G * k3 / 2; e += SPLIT_THREADS) {
+      wg_sync(1);
+      // stage-1 operand: sources, rows (i, jy, jz), contraction jx; pairs of rows per store.
+      // The previous group's stage-1 MMAs are complete (their stage 2 was waited for).
+      for (int e = tid; e < G * k3 / 2; e += 128) {
         int e2 = 2 * e;
         int i = e2 / k3, rest = e2 - i * k3;
         int jx = rest / k2, q = rest - jx * k2;
         int src = slot_src[i];
-        double x0 = 0.0, x1 = 0.0;
-        if (src >= 0) {
-          double2 xx = *(const double2 *)(a.in_coeffs + (int64_t)src * k3 + rest);
-          x0 = xx.x;
-          x1 = xx.y;
-        }
-        __nv_bfloat16 a0, a1, a2, b0, b1, b2;
-        split3(x0, a0, a1, a2);
-        split3(x1, b0, b1, b2);
+        double2 xx = make_double2(0.0, 0.0);
+        if (src >= 0) xx = *(const double2 *)(a.in_coeffs + (int64_t)src * k3 + rest);
+        __nv_bfloat16 x0, x1, x2, y0, y1, y2;
+        split3(xx.x, x0, x1, x2);
+        split3(xx.y, y0, y1, y2);
         uint32_t off = a_off(i * k2 + q, jx);
-        *(__nv_bfloat162 *)(A1 + off) = __halves2bfloat162(a0, b0);
-        *(__nv_bfloat162 *)(A1 + T * TILE_BYTES + off) = __halves2bfloat162(a1, b1);
-        if (P > 2) *(__nv_bfloat162 *)(A1 + 2 * T * TILE_BYTES + off) = __halves2bfloat162(a2, b2);
+        *(__nv_bfloat162 *)(A1 + off) = __halves2bfloat162(x0, y0);
+        *(__nv_bfloat162 *)(A1 + T * TILE_BYTES + off) = __halves2bfloat162(x1, y1);
+        if (P > 2) *(__nv_bfloat162 *)(A1 + 2 * T * TILE_BYTES + off) = __halves2bfloat162(x2, y2);
       }
-    } else {
-      for (int e = tid; e < G * k3; e += SPLIT_THREADS) {
-        int i = e / k3, rest = e - i * k3;
-        int jx = rest / k2, q = rest - jx * k2;
-        int src = slot_src[i];
-        double x = src >= 0 ? a.in_coeffs[(int64_t)src * k3 + rest] : 0.0;
-        __nv_bfloat16 p0, p1, p2;
-        split3(x, p0, p1, p2);
-        uint32_t off = a_off(i * k2 + q, jx);
-        *(__nv_bfloat16 *)(A1 + off) = p0;
-        *(__nv_bfloat16 *)(A1 + T * TILE_BYTES + off) = p1;
-        if (P > 2) *(__nv_bfloat16 *)(A1 + 2 * T * TILE_BYTES + off) = p2;
-      }
-    }
-    const int lev = g_level, lp = g_l;
-    const int Dop = a.Dlev[lev], nl = 2 * Dop + 1;
-    const int ld[3] = {(lp & 255) - 128, ((lp >> 8) & 255) - 128, ((lp >> 16) & 255) - 128};
-    const int64_t lbase = a.level_off[lev];
-    for (int w = 0; w < 2 && !aborted; ++w) {
-      uint64_t bits = uni[w];
-      while (bits && !aborted) {
-        const int m = w * 64 + __ffsll((long long)bits) - 1;
-        bits &= bits - 1;
-        // B operands of the three stages: blocks (m, lx), (m, ly), (m, lz)
-        for (int e = tid; e < 3 * (BSTAGE_BYTES / 16); e += SPLIT_THREADS) {
-          int st = e / (BSTAGE_BYTES / 16), q = e - st * (BSTAGE_BYTES / 16);
-          int64_t blk = lbase + (int64_t)m * nl + ld[st] + Dop;
-          ((int4 *)(Bt + st * BSTAGE_BYTES))[q] = ((const int4 *)(a.Bsplit + blk * BSTAGE_BYTES))[q];
-        }
-        tc::fence_proxy_async_smem();
-        tc::fence_before_sync();
-        __syncthreads();
-        // ---- stage 1
-        if (tid == 0) issue_stage(A1, Bt);
-        if (!wait_mma()) break;
-        for (int t = half; t < T; t += 2) {
-          float v[16];
-          load_tile(t, v);
-          int m1 = t * 128 + quarter * 32 + lane;
-          if (m1 < rows) {
-            int i = m1 / k2, rem = m1 - i * k2, jy = rem / k, jz = rem - jy * k;
-            store_run(A23, i, jy, jz, v);  // element [jy][(i, jz, ix)]
+      const int lev = g_level, lp = g_l;
+      const int Dop = a.Dlev[lev], nl = 2 * Dop + 1;
+      const int ldx = (lp & 255) - 128, ldy = ((lp >> 8) & 255) - 128, ldz = ((lp >> 16) & 255) - 128;
+      const int64_t lbase = a.level_off[lev];
+      for (int w = 0; w < 2 && !bad; ++w) {
+        uint64_t bits = uni[w];
+        while (bits && !bad) {
+          const int m = w * 64 + __ffsll((long long)bits) - 1;
+          bits &= bits - 1;
+          const int buf = it & 1;
+          unsigned char *Bb = Bt + buf * 3 * BSTAGE_BYTES;
+          // blocks of this term (buffer `buf` was last read by stage 3 of term it-2, which
+          // completed before stage 2 of term it-1)
+          for (int e = tid; e < 3 * (BSTAGE_BYTES / 16); e += 128) {
+            int st = e / (BSTAGE_BYTES / 16), q = e - st * (BSTAGE_BYTES / 16);
+            int ld = st == 0 ? ldx : (st == 1 ? ldy : ldz);
+            int64_t blk = lbase + (int64_t)m * nl + ld + Dop;
+            ((int4 *)(Bb + st * BSTAGE_BYTES))[q] = ((const int4 *)(a.Bsplit + blk * BSTAGE_BYTES))[q];
           }
-        }
-        tc::fence_proxy_async_smem();
-        tc::fence_before_sync();
-        __syncthreads();
-        // ---- stage 2
-        if (tid == 0) issue_stage(A23, Bt + BSTAGE_BYTES);
-        if (!wait_mma()) break;
-        for (int t = half; t < T; t += 2) {  // stage-2 reads of A23 are complete: rewrite it
-          float v[16];
-          load_tile(t, v);
-          int m2 = t * 128 + quarter * 32 + lane;
-          if (m2 < rows) {
-            int i = m2 / k2, rem = m2 - i * k2, jz = rem / k, ix = rem - jz * k;
-            store_run(A23, i, jz, ix, v);  // element [jz][(i, ix, iy)]
+          if (tid == 0) {  // term info for warpgroup 1 (slot `buf` was consumed by term it-2)
+            uint32_t keep = 0;
+            for (int i = 0; i < G; ++i) keep |= (uint32_t)((slot_mask[i][w] >> (m & 63)) & 1ull) << i;
+            ring_keep[buf] = keep;
+            ring_c[buf] = a.c[m];
           }
-        }
-        tc::fence_proxy_async_smem();
-        tc::fence_before_sync();
-        __syncthreads();
-        // ---- stage 3
-        if (tid == 0) issue_stage(A23, Bt + 2 * BSTAGE_BYTES);
-        if (!wait_mma()) break;
-        const double cm = a.c[m];
-#pragma unroll
-        for (int q = 0; q < MAX_TILES / 2 + 1; ++q) {
-          int t = half + 2 * q;
-          if (t < T) {
+          tc::fence_proxy_async_smem();
+          tc::fence_before_sync();
+          wg_sync(1);
+          // ---- stage 1: rows (i, jy, jz), contraction jx
+          if (tid == 0) issue_stacked(A1, Bb);
+          if (!wait12()) { bad = true; break; }
+          for (int t = 0; t < T; ++t) {
             float v[16];
             load_tile(t, v);
-            int m3 = t * 128 + quarter * 32 + lane;
-            if (m3 < rows) {
-              int i = m3 / k2;
-              bool kept = (slot_mask[i][w] >> (m & 63)) & 1ull;
-              double wgt = kept ? cm : 0.0;
-#pragma unroll
-              for (int j = 0; j < KC; ++j) acc[q][j] += wgt * (double)v[j];
+            int m1 = t * 128 + quarter * 32 + lane;
+            if (m1 < rows) {
+              int i = m1 / k2, rem = m1 - i * k2, jy = rem / k, jz = rem - jy * k;
+              store_run(i, jy, jz, v);  // element [jy][(i, jz, ix)]
             }
           }
+          tc::fence_proxy_async_smem();
+          tc::fence_before_sync();
+          wg_sync(1);
+          // ---- stage 2: rows (i, jz, ix), contraction jy
+          if (tid == 0) issue_stacked(A23, Bb + BSTAGE_BYTES);
+          if (!wait12()) { bad = true; break; }
+          for (int t = 0; t < T; ++t) {
+            float v[16];
+            load_tile(t, v);
+            int m2 = t * 128 + quarter * 32 + lane;
+            if (m2 < rows) {
+              int i = m2 / k2, rem = m2 - i * k2, jz = rem / k, ix = rem - jz * k;
+              store_run(i, jz, ix, v);  // element [jz][(i, ix, iy)]
+            }
+          }
+          tc::fence_proxy_async_smem();
+          tc::fence_before_sync();
+          wg_sync(1);
+          // ---- stage 3: rows (i, ix, iy), contraction jz, into D3 once warpgroup 1 is done with it
+          if (tid == 0) {
+            bool ok = true;
+            if (it > 0) {
+              ok = tc::mbar_wait(bfree, pfree, WAIT_CYCLES);
+              pfree ^= 1u;
+            }
+            if (!ok) {
+              abort_flag = 1;
+              atomicExch(a.err, 1);
+            } else {
+              tc::fence_after_sync();
+              const unsigned char *B = Bb + 2 * BSTAGE_BYTES;
+              for (int t = 0; t < T; ++t) {
+                uint32_t d = tmem + d3col + (uint32_t)(t * 16);
+                bool first = true;
+                for (int s2 = P - 1; s2 >= 0; --s2)  // smaller products first
+                  for (int p = 0; p <= s2; ++p) {
+                    int q = s2 - p;
+                    uint64_t ad = tc::smem_desc(tc::smem_u32(A23 + (p * T + t) * TILE_BYTES), 128, MG_BYTES);
+                    uint64_t bd = tc::smem_desc(tc::smem_u32(B + q * BPIECE_BYTES), 128, 256);
+                    tc::mma_bf16(d, ad, bd, idesc_n[0], first ? 0u : 1u);
+                    first = false;
+                  }
+              }
+              tc::mma_commit(b3);
+            }
+          }
+          ++it;
+          if (wg_vote_or(1, abort_flag)) { bad = true; break; }
         }
-        tc::fence_before_sync();
-        __syncthreads();
       }
+      wg_sync(1);
     }
-    __syncthreads();
-  }
-  // write the destinations: row (i, ix, iy), columns iz
-  if (!aborted) {
+    if (bad) abort_flag = 1;
+  } else {
+    // ======================================================= warpgroup 1: FP64 term sums
+    double acc[TM][K];
 #pragma unroll
-    for (int q = 0; q < MAX_TILES / 2 + 1; ++q) {
-      int t = half + 2 * q;
-      int m3 = t * 128 + quarter * 32 + lane;
-      if (t < T && m3 < rows) {
-        int i = m3 / k2, rem = m3 - i * k2;
-        int64_t dst = (int64_t)tile * G + i;
-        if (dst < a.n_dest) {
-          double *o = a.out_coeffs + dst * k3 + (int64_t)rem * k;
+    for (int t = 0; t < TM; ++t)
 #pragma unroll
-          for (int j = 0; j < KC; ++j)
-            if (j < k) o[j] = acc[q][j];
-          if (rem == 0) a.out_keys[dst] = a.dest_key[dst];
+      for (int j = 0; j < K; ++j) acc[t][j] = 0.0;
+    uint32_t p3 = 0;
+    bool bad = false;
+    for (int it = 0; it < nit; ++it) {
+      bool ok = tc::mbar_wait(b3, p3, WAIT_CYCLES);
+      p3 ^= 1u;
+      if (wg_vote_or(2, !ok || abort_flag)) {
+        bad = true;
+        break;
+      }
+      tc::fence_after_sync();
+      const double cm = ring_c[it & 1];
+      const uint32_t keep = ring_keep[it & 1];
+#pragma unroll
+      for (int t = 0; t < TM; ++t) {
+        if (t < T) {
+          float v[16];
+          tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + d3col + (uint32_t)(t * 16), v);
+          tc::tmem_ld_wait();
+          int m3 = t * 128 + quarter * 32 + lane;
+          if (m3 < rows && ((keep >> (m3 / k2)) & 1u)) {
+#pragma unroll
+            for (int j = 0; j < K; ++j) acc[t][j] = fma(cm, widen(v[j]), acc[t][j]);
+          }
+        }
+      }
+      tc::fence_before_sync();
+      wg_sync(2);
+      if (tid == 128) mbar_arrive(bfree);
+    }
+    if (bad) abort_flag = 1;
+    // write the destinations: row (i, ix, iy), columns iz
+    if (!bad) {
+#pragma unroll
+      for (int t = 0; t < TM; ++t) {
+        int m3 = t * 128 + quarter * 32 + lane;
+        if (t < T && m3 < rows) {
+          int i = m3 / k2, rem = m3 - i * k2;
+          int64_t dst = (int64_t)tile * G + i;
+          if (dst < a.n_dest) {
+            double *o = a.out_coeffs + dst * k3 + (int64_t)rem * k;
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+              if (j < k) o[j] = acc[t][j];
+            if (rem == 0) a.out_keys[dst] = a.dest_key[dst];
+          }
         }
       }
     }
@@ -378,8 +450,16 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) apply_split_kernel(SplitArgs
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (aborted && tid == 0) tc::mbar_wait(bar_a, phase ^ 1u, WAIT_CYCLES);  // let in-flight MMAs finish
-  __syncthreads();
+  if (abort_flag) {
+    if (tid == 0) atomicExch(a.err, 1);
+    // let any MMA still in flight finish before the tensor memory is released: a
+    // commit tracks every tcgen05 operation this thread issued before it
+    if (tid == 0) {
+      tc::mma_commit(tc::smem_u32(&bar_drain));
+      tc::mbar_wait(tc::smem_u32(&bar_drain), 0, WAIT_CYCLES);
+    }
+    __syncthreads();
+  }
   if (warp == 0) tc::tmem_dealloc(tmem, TMEM_COLS);
 }
 
@@ -463,9 +543,10 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
                     mra_tree_view &out, const ApplyWork &wk, mra_apply_stats *stats,
                     cudaStream_t s) {
   if (!op.d_Rsplit) return fail(MRA_ERR_ARG, "mra_apply: operator has no split blocks");
-  const int k = op.k, G = tile_boxes(k);
+  const int k = op.k;
+  if (k & 1) return fail(MRA_ERR_UNSUPPORTED, "split apply: odd k=%d not supported (use MRA_PREC_FP64)", k);
+  const int G = g_for(k);
   const int T = (G * k * k + 127) / 128;
-  if (T > MAX_TILES) return fail(MRA_ERR_UNSUPPORTED, "split apply: tile too large for k=%d", k);
   const int64_t P = wk.P, nd = wk.n_dest;
   const int n_tiles = (int)((nd + G - 1) / G);
   // carve the split-path workspace
@@ -519,8 +600,18 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
   a.out_keys = out.keys;
   a.out_coeffs = out.coeffs;
   a.err = err;
-  size_t smem = (size_t)2 * a.P * T * TILE_BYTES + 3 * BSTAGE_BYTES + 1024;
-  void (*kern)(SplitArgs) = k <= 8 ? apply_split_kernel<8> : (k <= 12 ? apply_split_kernel<12> : apply_split_kernel<16>);
+  size_t smem = (size_t)2 * a.P * T * TILE_BYTES + 6 * BSTAGE_BYTES + 1024;
+  void (*kern)(SplitArgs) = nullptr;
+  switch (k) {
+    case 2: kern = apply_split_kernel<2>; break;
+    case 4: kern = apply_split_kernel<4>; break;
+    case 6: kern = apply_split_kernel<6>; break;
+    case 8: kern = apply_split_kernel<8>; break;
+    case 10: kern = apply_split_kernel<10>; break;
+    case 12: kern = apply_split_kernel<12>; break;
+    case 14: kern = apply_split_kernel<14>; break;
+    default: kern = apply_split_kernel<16>; break;
+  }
   MRA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (wk.ev0) MRA_CUDA_TRY(cudaEventRecord(wk.ev0, s));
   kern<<<(unsigned)n_tiles, SPLIT_THREADS, smem, s>>>(a);
