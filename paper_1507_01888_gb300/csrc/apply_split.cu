@@ -33,14 +33,12 @@ namespace mra {
 namespace {
 
 constexpr int SPLIT_THREADS = 256;      // 8 warps: two warps per tensor-memory lane quarter
-constexpr int MAX_TILES = 7;            // 128-row MMA tiles per stage (G k^2 <= 896)
 constexpr int MG_BYTES = 272;           // stride of the 8-row groups: 256 B of core matrices + 16 B
                                         // so that consecutive groups start 4 banks apart
 constexpr int TILE_BYTES = 16 * MG_BYTES;  // one 128 x 16 BF16 operand tile
 constexpr int BPIECE_BYTES = 512;       // one 16 x 16 BF16 block piece
 constexpr int BSTAGE_BYTES = 3 * BPIECE_BYTES;
 constexpr int MAX_G = 32;
-constexpr uint32_t TMEM_COLS = 512;
 constexpr long long WAIT_CYCLES = 4000000000LL;  // bounded mbarrier wait (~2 s)
 
 
@@ -62,14 +60,6 @@ __device__ __forceinline__ void split3(double x, __nv_bfloat16 &p0, __nv_bfloat1
   p2 = __double2bfloat16(r);
 }
 
-__device__ __forceinline__ void split3f(float x, __nv_bfloat16 &p0, __nv_bfloat16 &p1,
-                                        __nv_bfloat16 &p2) {
-  p0 = __float2bfloat16_rn(x);
-  float r = x - __bfloat162float(p0);
-  p1 = __float2bfloat16_rn(r);
-  r -= __bfloat162float(p1);
-  p2 = __float2bfloat16_rn(r);
-}
 
 struct SplitArgs {
   int k, M, P, G, T;
@@ -122,35 +112,56 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// Compile-time shape for an even k: KC = k, TMAX tiles of 128 rows per stage.
-__host__ __device__ constexpr int tmax_for(int k) { return k <= 10 ? 7 : (k <= 12 ? 6 : (k <= 14 ? 5 : 4)); }
+// Compile-time shape for an even k: TM tiles of 128 rows per stage and MINB CTAs per SM.
+// k <= 10: four tiles and two CTAs per SM (each CTA's serial chain of MMA waits and
+// tensor-memory loads hides behind the other's); k >= 12: one CTA with more tiles.
+__host__ __device__ constexpr int tm_for(int k) { return k <= 2 ? 1 : (k <= 10 ? 4 : (k <= 12 ? 6 : (k <= 14 ? 5 : 4))); }
+__host__ __device__ constexpr int minb_for(int k) { return k <= 10 ? 2 : 1; }
 __host__ __device__ constexpr int g_for(int k) {
-  return (128 * tmax_for(k)) / (k * k) > MAX_G ? MAX_G : (128 * tmax_for(k)) / (k * k);
+  return (128 * tm_for(k)) / (k * k) > MAX_G ? MAX_G : (128 * tm_for(k)) / (k * k);
+}
+// tensor-memory columns: D12 (16 T) and two D3 buffers (2 x 16 T), rounded to a power of two
+__host__ __device__ constexpr uint32_t tmem_cols_for(int k) {
+  return 48 * tm_for(k) <= 64 ? 64u : (48 * tm_for(k) <= 128 ? 128u : (48 * tm_for(k) <= 256 ? 256u : 512u));
 }
 
-// Warp roles: warpgroup 0 (warps 0-3) loads each group's sources and each term's
-// blocks, turns stage-1/2 outputs into the next stage's operands, and its thread 0
-// issues every MMA; warpgroup 1 (warps 4-7) adds each term's stage-3 output into
-// the FP64 accumulators.  Stage 3 of term q runs while warpgroup 0 already
-// works on term q+1; tensor memory holds D12 (stages 1 and 2, P column groups of 16
-// per tile) and, separately, D3 (stage 3, one column group per tile).
+// Split x and y into three BF16 pieces each (x = x0 + x1 + x2 to 24 bits), packed in pairs.
+__device__ __forceinline__ void split_pair(float x, float y, __nv_bfloat162 &h0, __nv_bfloat162 &h1,
+                                           __nv_bfloat162 &h2) {
+  h0 = __floats2bfloat162_rn(x, y);
+  float2 f0 = __bfloat1622float2(h0);
+  float rx = x - f0.x, ry = y - f0.y;
+  h1 = __floats2bfloat162_rn(rx, ry);
+  float2 f1 = __bfloat1622float2(h1);
+  h2 = __floats2bfloat162_rn(rx - f1.x, ry - f1.y);
+}
+
+// Warp roles: warpgroup 0 (warps 0-3) stages each group's sources, turns stage-1/2
+// outputs into the next stage's operands, and its thread 0 issues every MMA and every
+// block-tile copy (one term ahead); warpgroup 1 (warps 4-7) adds each term's stage-3
+// output into the FP64 accumulators while warpgroup 0 works on the next terms.  Every
+// stage accumulates all kept piece products in one 16-column FP32 group per tile:
+// D12 (stages 1 and 2) at columns [0, 16T), D3 (stage 3) double-buffered at
+// [16T, 32T) and [32T, 48T).  Each D3 buffer b has its own "done" (MMA commit) and
+// "free" (warpgroup 1 finished reading) barrier, so no barrier runs more than one
+// phase ahead of its waiter; term info goes through a 4-deep ring.
 template <int K>
-__global__ void __launch_bounds__(SPLIT_THREADS, 1) apply_split_kernel(SplitArgs a) {
-  constexpr int TM = tmax_for(K);
+__global__ void __launch_bounds__(SPLIT_THREADS, minb_for(K)) apply_split_kernel(SplitArgs a) {
+  constexpr int TM = tm_for(K);
   extern __shared__ __align__(1024) unsigned char smem[];
   const int k = a.k, k2 = k * k, k3 = k2 * k, P = a.P, G = a.G, T = a.T;
   const int rows = G * k2;
   unsigned char *A1 = smem;                          // [P][T][TILE_BYTES] stage-1 operand (sources)
   unsigned char *A23 = A1 + P * T * TILE_BYTES;      // [P][T][TILE_BYTES] stage-2/3 operand
   unsigned char *Bt = A23 + P * T * TILE_BYTES;      // [2 buffers][3 stages][1536]
-  __shared__ __align__(8) uint64_t bar12, bar3, bar_free, bar_drain;
+  __shared__ __align__(8) uint64_t bar12, bar3[2], bar_free[2], bar_drain, bar_b[2];
   __shared__ uint32_t tmem_holder;
   __shared__ int slot_src[MAX_G];
   __shared__ uint64_t slot_mask[MAX_G][2];
   __shared__ uint64_t uni[2];
   __shared__ int g_level, g_l, total_it;
-  __shared__ double ring_c[2];
-  __shared__ uint32_t ring_keep[2];
+  __shared__ double ring_c[4];
+  __shared__ uint32_t ring_keep[4];
   __shared__ volatile int abort_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -158,25 +169,28 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) apply_split_kernel(SplitArgs
   const int tile = blockIdx.x;
   const int g0 = a.tile_gstart[tile], g1 = a.tile_gstart[tile + 1];
 
-  {  // zero all operand buffers once: contraction and row padding stay zero
+  {  // zero the operand buffers once: contraction and row padding stay zero
     int4 *z = (int4 *)smem;
-    int n16 = (2 * P * T * TILE_BYTES + 6 * BSTAGE_BYTES) / 16;
+    int n16 = (2 * P * T * TILE_BYTES) / 16;
     for (int i = tid; i < n16; i += SPLIT_THREADS) z[i] = make_int4(0, 0, 0, 0);
   }
   if (tid == 0) {
     tc::mbar_init(tc::smem_u32(&bar12), 1);
-    tc::mbar_init(tc::smem_u32(&bar3), 1);
-    tc::mbar_init(tc::smem_u32(&bar_free), 1);
+    tc::mbar_init(tc::smem_u32(&bar3[0]), 1);
+    tc::mbar_init(tc::smem_u32(&bar3[1]), 1);
+    tc::mbar_init(tc::smem_u32(&bar_free[0]), 1);
+    tc::mbar_init(tc::smem_u32(&bar_free[1]), 1);
     tc::mbar_init(tc::smem_u32(&bar_drain), 1);
+    tc::mbar_init(tc::smem_u32(&bar_b[0]), 1);
+    tc::mbar_init(tc::smem_u32(&bar_b[1]), 1);
     abort_flag = 0;
     total_it = 0;
   }
-  if (warp == 0) tc::tmem_alloc(tc::smem_u32(&tmem_holder), TMEM_COLS);
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(&tmem_holder), tmem_cols_for(K));
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   tc::fence_proxy_async_smem();
   __syncthreads();
-  // total number of (group, term) iterations of this tile, for warpgroup 1's loop
-  if (warp == 0) {
+  if (warp == 0) {  // number of (group, term) iterations of this tile, for warpgroup 1
     int cnt = 0;
     for (int g = g0; g < g1; ++g) {
       uint64_t u0 = 0, u1 = 0;
@@ -197,30 +211,36 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) apply_split_kernel(SplitArgs
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_holder;
-  const uint32_t d3col = (uint32_t)(T * 48);
-  const uint32_t b12 = tc::smem_u32(&bar12), b3 = tc::smem_u32(&bar3), bfree = tc::smem_u32(&bar_free);
+  const uint32_t d3col = (uint32_t)(T * 16);
+  const uint32_t b12 = tc::smem_u32(&bar12);
+  const uint32_t b3[2] = {tc::smem_u32(&bar3[0]), tc::smem_u32(&bar3[1])};
+  const uint32_t bfree[2] = {tc::smem_u32(&bar_free[0]), tc::smem_u32(&bar_free[1])};
+  const uint32_t bb[2] = {tc::smem_u32(&bar_b[0]), tc::smem_u32(&bar_b[1])};
   const int nit = total_it;
+  const uint32_t idesc16 = tc::idesc_bf16(128, 16, 1, 0);
+
+  // one stage: for every tile, the products A_p B_q with p + q < P (smallest first) into
+  // the tile's 16 columns at `dcol`
+  auto issue_stage = [&](const unsigned char *A, const unsigned char *B, uint32_t dcol) {
+    for (int t = 0; t < T; ++t) {
+      uint32_t d = tmem + dcol + (uint32_t)(t * 16);
+      bool first = true;
+      for (int s2 = P - 1; s2 >= 0; --s2)
+        for (int p = 0; p <= s2; ++p) {
+          int q = s2 - p;
+          uint64_t ad = tc::smem_desc(tc::smem_u32(A + (p * T + t) * TILE_BYTES), 128, MG_BYTES);
+          uint64_t bd = tc::smem_desc(tc::smem_u32(B + q * BPIECE_BYTES), 128, 256);
+          tc::mma_bf16(d, ad, bd, idesc16, first ? 0u : 1u);
+          first = false;
+        }
+    }
+  };
 
   if (wg == 0) {
-    // ======================================================= warpgroup 0 + MMA issue
-    const uint32_t idesc_n[3] = {tc::idesc_bf16(128, 16, 1, 0), tc::idesc_bf16(128, 32, 1, 0),
-                                 tc::idesc_bf16(128, 48, 1, 0)};
-    uint32_t p12 = 0, pfree = 0;
+    // ======================================================= warpgroup 0 + MMA / copy issue
+    uint32_t p12 = 0;
     int it = 0;
     bool bad = false;
-    auto issue_stacked = [&](const unsigned char *A, const unsigned char *B) {
-      tc::fence_after_sync();
-      for (int t = 0; t < T; ++t) {
-        uint32_t d = tmem + (uint32_t)(t * 48);
-        for (int p = 0; p < P; ++p) {
-          uint64_t ad = tc::smem_desc(tc::smem_u32(A + (p * T + t) * TILE_BYTES), 128, MG_BYTES);
-          uint64_t bd = tc::smem_desc(tc::smem_u32(B), 128, 256);
-          // A piece p times B pieces 0..P-1-p (stacked along N) into column groups p..P-1
-          tc::mma_bf16(d + 16 * p, ad, bd, idesc_n[P - 1 - p], p > 0 ? 1u : 0u);
-        }
-      }
-      tc::mma_commit(b12);
-    };
     auto wait12 = [&]() -> bool {
       bool ok = tc::mbar_wait(b12, p12, WAIT_CYCLES);
       p12 ^= 1u;
@@ -228,31 +248,37 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) apply_split_kernel(SplitArgs
       tc::fence_after_sync();
       return !any_bad;
     };
-    // this thread's row of tile t: sum of the P column groups
-    auto load_tile = [&](int t, float *v) {
-      uint32_t base = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(t * 48);
-      float c0[16], c1[16], c2[16];
-      tc::tmem_ld16(base, c0);
-      if (P > 1) tc::tmem_ld16(base + 16, c1);
-      if (P > 2) tc::tmem_ld16(base + 32, c2);
-      tc::tmem_ld_wait();
+    // copies of the three blocks (m; lx, ly, lz) into buffer `buf`
+    auto fetch_blocks = [&](int buf, int m, int64_t lbase, int nl, int Dop, int lx, int ly, int lz) {
+      unsigned char *Bb = Bt + buf * 3 * BSTAGE_BYTES;
+      tc::mbar_arrive_expect_tx(bb[buf], 3 * BSTAGE_BYTES);
+      const int ls[3] = {lx, ly, lz};
 #pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = P == 3 ? (c2[j] + c1[j]) + c0[j] : (P == 2 ? c1[j] + c0[j] : c0[j]);
+      for (int st = 0; st < 3; ++st) {
+        int64_t blk = lbase + (int64_t)m * nl + ls[st] + Dop;
+        tc::bulk_g2s(tc::smem_u32(Bb + st * BSTAGE_BYTES), a.Bsplit + blk * BSTAGE_BYTES, BSTAGE_BYTES, bb[buf]);
+      }
     };
-    // element [contraction a][row (i, b, d)] for d = 0..k-1, pairs of rows per 32-bit store
-    auto store_run = [&](int i, int a_idx, int b_idx, const float *v) {
-      int mrow = i * k2 + b_idx * k;
+    // element [contraction a][row (i, b, d)] for d = 0..k-1 of this thread's rows
+    auto store_run = [&](int mrow, int a_idx, const float *v) {
       const int stride = T * TILE_BYTES;
 #pragma unroll
       for (int d = 0; d < K; d += 2) {
-        __nv_bfloat16 x0, x1, x2, y0, y1, y2;
-        split3f(v[d], x0, x1, x2);
-        split3f(v[d + 1], y0, y1, y2);
+        __nv_bfloat162 h0, h1, h2;
+        split_pair(v[d], v[d + 1], h0, h1, h2);
         uint32_t off = a_off(mrow + d, a_idx);
-        *(__nv_bfloat162 *)(A23 + off) = __halves2bfloat162(x0, y0);
-        *(__nv_bfloat162 *)(A23 + stride + off) = __halves2bfloat162(x1, y1);
-        if (P > 2) *(__nv_bfloat162 *)(A23 + 2 * stride + off) = __halves2bfloat162(x2, y2);
+        *(__nv_bfloat162 *)(A23 + off) = h0;
+        *(__nv_bfloat162 *)(A23 + stride + off) = h1;
+        if (P > 2) *(__nv_bfloat162 *)(A23 + 2 * stride + off) = h2;
       }
+    };
+    // tiles t0, t0+1 of D12 for this thread's lane, one wait for both loads
+    auto load_d12_pair = [&](int t0, float (*v)[16]) {
+      const uint32_t base = tmem + ((uint32_t)(32 * quarter) << 16);
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+        if (t0 + u < T) tc::tmem_ld16(base + (uint32_t)((t0 + u) * 16), v[u]);
+      tc::tmem_ld_wait();
     };
     for (int g = g0; g < g1 && !bad; ++g) {
       const int r0 = a.grp_start[g], r1 = a.grp_start[g + 1];
@@ -281,7 +307,21 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) apply_split_kernel(SplitArgs
         }
       }
       wg_sync(1);
-      // stage-1 operand: sources, rows (i, jy, jz), contraction jx; pairs of rows per store.
+      const int lev = g_level, lp = g_l;
+      const int Dop = a.Dlev[lev], nl = 2 * Dop + 1;
+      const int ldx = (lp & 255) - 128, ldy = ((lp >> 8) & 255) - 128, ldz = ((lp >> 16) & 255) - 128;
+      const int64_t lbase = a.level_off[lev];
+      uint64_t bits0 = uni[0], bits1 = uni[1];
+      auto next_term = [&](uint64_t &b0, uint64_t &b1) -> int {  // pop the lowest kept term
+        if (b0) { int m = __ffsll((long long)b0) - 1; b0 &= b0 - 1; return m; }
+        if (b1) { int m = 64 + __ffsll((long long)b1) - 1; b1 &= b1 - 1; return m; }
+        return -1;
+      };
+      int m = next_term(bits0, bits1);
+      // first term of the group: its blocks were not prefetched (buffer it&1 was last read by
+      // stage 3 of term it-2, complete since stage 1 of term it-1 completed)
+      if (tid == 0 && m >= 0) fetch_blocks(it & 1, m, lbase, nl, Dop, ldx, ldy, ldz);
+      // stage-1 operand: sources, rows (i, jy, jz), contraction jx (FP64 -> FP32 -> 3 BF16 pieces).
       // The previous group's stage-1 MMAs are complete (their stage 2 was waited for).
       for (int e = tid; e < G * k3 / 2; e += 128) {
         int e2 = 2 * e;
@@ -290,103 +330,95 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) apply_split_kernel(SplitArgs
         int src = slot_src[i];
         double2 xx = make_double2(0.0, 0.0);
         if (src >= 0) xx = *(const double2 *)(a.in_coeffs + (int64_t)src * k3 + rest);
-        __nv_bfloat16 x0, x1, x2, y0, y1, y2;
-        split3(xx.x, x0, x1, x2);
-        split3(xx.y, y0, y1, y2);
+        __nv_bfloat162 h0, h1, h2;
+        split_pair((float)xx.x, (float)xx.y, h0, h1, h2);
         uint32_t off = a_off(i * k2 + q, jx);
-        *(__nv_bfloat162 *)(A1 + off) = __halves2bfloat162(x0, y0);
-        *(__nv_bfloat162 *)(A1 + T * TILE_BYTES + off) = __halves2bfloat162(x1, y1);
-        if (P > 2) *(__nv_bfloat162 *)(A1 + 2 * T * TILE_BYTES + off) = __halves2bfloat162(x2, y2);
+        *(__nv_bfloat162 *)(A1 + off) = h0;
+        *(__nv_bfloat162 *)(A1 + T * TILE_BYTES + off) = h1;
+        if (P > 2) *(__nv_bfloat162 *)(A1 + 2 * T * TILE_BYTES + off) = h2;
       }
-      const int lev = g_level, lp = g_l;
-      const int Dop = a.Dlev[lev], nl = 2 * Dop + 1;
-      const int ldx = (lp & 255) - 128, ldy = ((lp >> 8) & 255) - 128, ldz = ((lp >> 16) & 255) - 128;
-      const int64_t lbase = a.level_off[lev];
-      for (int w = 0; w < 2 && !bad; ++w) {
-        uint64_t bits = uni[w];
-        while (bits && !bad) {
-          const int m = w * 64 + __ffsll((long long)bits) - 1;
-          bits &= bits - 1;
-          const int buf = it & 1;
-          unsigned char *Bb = Bt + buf * 3 * BSTAGE_BYTES;
-          // blocks of this term (buffer `buf` was last read by stage 3 of term it-2, which
-          // completed before stage 2 of term it-1)
-          for (int e = tid; e < 3 * (BSTAGE_BYTES / 16); e += 128) {
-            int st = e / (BSTAGE_BYTES / 16), q = e - st * (BSTAGE_BYTES / 16);
-            int ld = st == 0 ? ldx : (st == 1 ? ldy : ldz);
-            int64_t blk = lbase + (int64_t)m * nl + ld + Dop;
-            ((int4 *)(Bb + st * BSTAGE_BYTES))[q] = ((const int4 *)(a.Bsplit + blk * BSTAGE_BYTES))[q];
+      tc::fence_proxy_async_smem();
+      tc::fence_before_sync();
+      wg_sync(1);
+      while (m >= 0 && !bad) {
+        const int buf = it & 1;
+        const unsigned char *Bb = Bt + buf * 3 * BSTAGE_BYTES;
+        const int m_next = next_term(bits0, bits1);
+        if (tid == 0) {
+          // term info for warpgroup 1 (ring slot it&3 was read by its iteration it-4, which
+          // finished before the "D3 free" arrival that let stage 3 of term it-1 start)
+          uint32_t keep = 0;
+          const int w = m >> 6;
+          for (int i = 0; i < G; ++i) keep |= (uint32_t)((slot_mask[i][w] >> (m & 63)) & 1ull) << i;
+          ring_keep[it & 3] = keep;
+          ring_c[it & 3] = a.c[m];
+          bool ok = tc::mbar_wait(bb[buf], (uint32_t)((it >> 1) & 1), WAIT_CYCLES);
+          if (!ok) {
+            abort_flag = 1;
+          } else {
+            tc::fence_after_sync();
+            issue_stage(A1, Bb, 0);  // ---- stage 1: rows (i, jy, jz), contraction jx
+            tc::mma_commit(b12);
           }
-          if (tid == 0) {  // term info for warpgroup 1 (slot `buf` was consumed by term it-2)
-            uint32_t keep = 0;
-            for (int i = 0; i < G; ++i) keep |= (uint32_t)((slot_mask[i][w] >> (m & 63)) & 1ull) << i;
-            ring_keep[buf] = keep;
-            ring_c[buf] = a.c[m];
-          }
-          tc::fence_proxy_async_smem();
-          tc::fence_before_sync();
-          wg_sync(1);
-          // ---- stage 1: rows (i, jy, jz), contraction jx
-          if (tid == 0) issue_stacked(A1, Bb);
-          if (!wait12()) { bad = true; break; }
-          for (int t = 0; t < T; ++t) {
-            float v[16];
-            load_tile(t, v);
-            int m1 = t * 128 + quarter * 32 + lane;
-            if (m1 < rows) {
-              int i = m1 / k2, rem = m1 - i * k2, jy = rem / k, jz = rem - jy * k;
-              store_run(i, jy, jz, v);  // element [jy][(i, jz, ix)]
-            }
-          }
-          tc::fence_proxy_async_smem();
-          tc::fence_before_sync();
-          wg_sync(1);
-          // ---- stage 2: rows (i, jz, ix), contraction jy
-          if (tid == 0) issue_stacked(A23, Bb + BSTAGE_BYTES);
-          if (!wait12()) { bad = true; break; }
-          for (int t = 0; t < T; ++t) {
-            float v[16];
-            load_tile(t, v);
-            int m2 = t * 128 + quarter * 32 + lane;
-            if (m2 < rows) {
-              int i = m2 / k2, rem = m2 - i * k2, jz = rem / k, ix = rem - jz * k;
-              store_run(i, jz, ix, v);  // element [jz][(i, ix, iy)]
-            }
-          }
-          tc::fence_proxy_async_smem();
-          tc::fence_before_sync();
-          wg_sync(1);
-          // ---- stage 3: rows (i, ix, iy), contraction jz, into D3 once warpgroup 1 is done with it
-          if (tid == 0) {
-            bool ok = true;
-            if (it > 0) {
-              ok = tc::mbar_wait(bfree, pfree, WAIT_CYCLES);
-              pfree ^= 1u;
-            }
-            if (!ok) {
-              abort_flag = 1;
-              atomicExch(a.err, 1);
-            } else {
-              tc::fence_after_sync();
-              const unsigned char *B = Bb + 2 * BSTAGE_BYTES;
-              for (int t = 0; t < T; ++t) {
-                uint32_t d = tmem + d3col + (uint32_t)(t * 16);
-                bool first = true;
-                for (int s2 = P - 1; s2 >= 0; --s2)  // smaller products first
-                  for (int p = 0; p <= s2; ++p) {
-                    int q = s2 - p;
-                    uint64_t ad = tc::smem_desc(tc::smem_u32(A23 + (p * T + t) * TILE_BYTES), 128, MG_BYTES);
-                    uint64_t bd = tc::smem_desc(tc::smem_u32(B + q * BPIECE_BYTES), 128, 256);
-                    tc::mma_bf16(d, ad, bd, idesc_n[0], first ? 0u : 1u);
-                    first = false;
-                  }
-              }
-              tc::mma_commit(b3);
-            }
-          }
-          ++it;
-          if (wg_vote_or(1, abort_flag)) { bad = true; break; }
         }
+        if (!wait12()) { bad = true; break; }
+        // stage 1 done, hence also stage 3 of term it-1: buffer it+1 is free for the next term
+        if (tid == 0 && m_next >= 0) fetch_blocks((it + 1) & 1, m_next, lbase, nl, Dop, ldx, ldy, ldz);
+#pragma unroll
+        for (int t0 = 0; t0 < TM; t0 += 2) {
+          float v[2][16];
+          load_d12_pair(t0, v);
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int t = t0 + u;
+            int m1 = t * 128 + quarter * 32 + lane;
+            if (t < TM && t < T && m1 < rows) {
+              int i = m1 / k2, rem = m1 - i * k2, jy = rem / k, jz = rem - jy * k;
+              store_run(i * k2 + jz * k, jy, v[u]);  // element [jy][(i, jz, ix)]
+            }
+          }
+        }
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        wg_sync(1);
+        if (tid == 0) {  // ---- stage 2: rows (i, jz, ix), contraction jy
+          tc::fence_after_sync();
+          issue_stage(A23, Bb + BSTAGE_BYTES, 0);
+          tc::mma_commit(b12);
+        }
+        if (!wait12()) { bad = true; break; }
+#pragma unroll
+        for (int t0 = 0; t0 < TM; t0 += 2) {
+          float v[2][16];
+          load_d12_pair(t0, v);
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int t = t0 + u;
+            int m2 = t * 128 + quarter * 32 + lane;
+            if (t < TM && t < T && m2 < rows) {
+              int i = m2 / k2, rem = m2 - i * k2, jz = rem / k, ix = rem - jz * k;
+              store_run(i * k2 + ix * k, jz, v[u]);  // element [jz][(i, ix, iy)]
+            }
+          }
+        }
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        wg_sync(1);
+        if (tid == 0) {  // ---- stage 3 into D3 buffer it&1, once warpgroup 1 has read term it-2
+          const int db = it & 1;
+          bool ok = true;
+          if (it >= 2) ok = tc::mbar_wait(bfree[db], (uint32_t)(((it >> 1) - 1) & 1), WAIT_CYCLES);
+          if (!ok) {
+            abort_flag = 1;
+          } else {
+            tc::fence_after_sync();
+            issue_stage(A23, Bb + 2 * BSTAGE_BYTES, d3col + (uint32_t)(db * 16 * T));
+            tc::mma_commit(b3[db]);
+          }
+        }
+        ++it;
+        m = m_next;
+        if (wg_vote_or(1, abort_flag)) { bad = true; break; }
       }
       wg_sync(1);
     }
@@ -398,34 +430,39 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) apply_split_kernel(SplitArgs
     for (int t = 0; t < TM; ++t)
 #pragma unroll
       for (int j = 0; j < K; ++j) acc[t][j] = 0.0;
-    uint32_t p3 = 0;
     bool bad = false;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16) + d3col;
     for (int it = 0; it < nit; ++it) {
-      bool ok = tc::mbar_wait(b3, p3, WAIT_CYCLES);
-      p3 ^= 1u;
+      const int db = it & 1;
+      bool ok = tc::mbar_wait(b3[db], (uint32_t)((it >> 1) & 1), WAIT_CYCLES);
       if (wg_vote_or(2, !ok || abort_flag)) {
         bad = true;
         break;
       }
       tc::fence_after_sync();
-      const double cm = ring_c[it & 1];
-      const uint32_t keep = ring_keep[it & 1];
+      const double cm = ring_c[it & 3];
+      const uint32_t keep = ring_keep[it & 3];
+      const uint32_t base = lane_base + (uint32_t)(db * 16 * T);
 #pragma unroll
-      for (int t = 0; t < TM; ++t) {
-        if (t < T) {
-          float v[16];
-          tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + d3col + (uint32_t)(t * 16), v);
-          tc::tmem_ld_wait();
+      for (int t0 = 0; t0 < TM; t0 += 2) {  // two tiles per tensor-memory round trip
+        float v[2][16];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+          if (t0 + u < T) tc::tmem_ld16(base + (uint32_t)((t0 + u) * 16), v[u]);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int t = t0 + u;
           int m3 = t * 128 + quarter * 32 + lane;
-          if (m3 < rows && ((keep >> (m3 / k2)) & 1u)) {
+          if (t < TM && t < T && m3 < rows && ((keep >> (m3 / k2)) & 1u)) {
 #pragma unroll
-            for (int j = 0; j < K; ++j) acc[t][j] = fma(cm, widen(v[j]), acc[t][j]);
+            for (int j = 0; j < K; ++j) acc[t][j] = fma(cm, widen(v[u][j]), acc[t][j]);
           }
         }
       }
       tc::fence_before_sync();
       wg_sync(2);
-      if (tid == 128) mbar_arrive(bfree);
+      if (tid == 128) mbar_arrive(bfree[db]);  // D3 buffer db may take stage 3 of term it+2
     }
     if (bad) abort_flag = 1;
     // write the destinations: row (i, ix, iy), columns iz
@@ -439,8 +476,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) apply_split_kernel(SplitArgs
           if (dst < a.n_dest) {
             double *o = a.out_coeffs + dst * k3 + (int64_t)rem * k;
 #pragma unroll
-            for (int j = 0; j < K; ++j)
-              if (j < k) o[j] = acc[t][j];
+            for (int j = 0; j < K; ++j) o[j] = acc[t][j];
             if (rem == 0) a.out_keys[dst] = a.dest_key[dst];
           }
         }
@@ -451,16 +487,16 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) apply_split_kernel(SplitArgs
   __syncthreads();
   tc::fence_after_sync();
   if (abort_flag) {
-    if (tid == 0) atomicExch(a.err, 1);
-    // let any MMA still in flight finish before the tensor memory is released: a
+    // let any copy or MMA still in flight finish before the tensor memory is released: a
     // commit tracks every tcgen05 operation this thread issued before it
     if (tid == 0) {
+      atomicExch(a.err, 1);
       tc::mma_commit(tc::smem_u32(&bar_drain));
       tc::mbar_wait(tc::smem_u32(&bar_drain), 0, WAIT_CYCLES);
     }
     __syncthreads();
   }
-  if (warp == 0) tc::tmem_dealloc(tmem, TMEM_COLS);
+  if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols_for(K));
 }
 
 // ---------------------------------------------------------------- work-list kernels
@@ -547,6 +583,7 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
   if (k & 1) return fail(MRA_ERR_UNSUPPORTED, "split apply: odd k=%d not supported (use MRA_PREC_FP64)", k);
   const int G = g_for(k);
   const int T = (G * k * k + 127) / 128;
+  if (T > tm_for(k)) return fail(MRA_ERR_UNSUPPORTED, "split apply: tile shape for k=%d", k);
   const int64_t P = wk.P, nd = wk.n_dest;
   const int n_tiles = (int)((nd + G - 1) / G);
   // carve the split-path workspace
@@ -600,7 +637,7 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
   a.out_keys = out.keys;
   a.out_coeffs = out.coeffs;
   a.err = err;
-  size_t smem = (size_t)2 * a.P * T * TILE_BYTES + 6 * BSTAGE_BYTES + 1024;
+  size_t smem = (size_t)2 * a.P * T * TILE_BYTES + 6 * BSTAGE_BYTES;
   void (*kern)(SplitArgs) = nullptr;
   switch (k) {
     case 2: kern = apply_split_kernel<2>; break;
@@ -613,6 +650,7 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
     default: kern = apply_split_kernel<16>; break;
   }
   MRA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  MRA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   if (wk.ev0) MRA_CUDA_TRY(cudaEventRecord(wk.ev0, s));
   kern<<<(unsigned)n_tiles, SPLIT_THREADS, smem, s>>>(a);
   MRA_CUDA_TRY(cudaGetLastError());

@@ -79,6 +79,14 @@ def bsh_m60_adaptive_k10() -> Workload:
                     max_disp=1, tau=1e-8)
 
 
+def bsh_m60_uniform_k10() -> Workload:
+    """Small case with the BSH workload's k and M: uniform level 3 (512 boxes), 27 displacements,
+    no screen (used for profiling the apply kernels)."""
+    return Workload("bsh_m60_uniform_l3_k10", [gaussian_sum(8, 1.0, 1e4, seed=2)], k=10, L=L_CELL,
+                    thresh=0.0, uniform_level=3, kernel=BSH, mu=1.0, M=60, fit_eps=1e-6, stencil=1,
+                    max_disp=1, tau=0.0)
+
+
 def poisson_batched_64() -> Workload:
     """Batched Poisson apply: 64 functions (seeds 3000..3063) of 1-16 Gaussians a~logU[1,1e3],
     k=8, thresh 1e-5, 1/r as 40 Gaussians."""
@@ -106,6 +114,7 @@ def poisson_k14_large() -> Workload:
 WORKLOADS = {
     "poisson_m20_uniform_l3_k6": poisson_m20_uniform_k6,
     "bsh_m60_adaptive_k10": bsh_m60_adaptive_k10,
+    "bsh_m60_uniform_l3_k10": bsh_m60_uniform_k10,
     "poisson_batched64_k8": poisson_batched_64,
     "bsh_m80_adaptive_k10_learned": bsh_learned_k10,
     "poisson_m100_adaptive_k14": poisson_k14_large,
