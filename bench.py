@@ -334,7 +334,7 @@ def main():
                 "peak_source": f"bf16 dense burst, {pk_kind}", "kernel_ms": kms,
                 "flops": "algorithmic (6k^4+k^3 per kept term)"}
         dtype = f"bf16x{args.pieces}-split, f32 accumulate, f64 term sum"
-        launches_per_step = 8
+        launches_per_step = 10
 
     line = {"metric": METRIC, "value": value, "unit": "boxes/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -120,7 +120,8 @@ __host__ __device__ constexpr int minb_for(int k) { return k <= 10 ? 2 : 1; }
 __host__ __device__ constexpr int g_for(int k) {
   return (128 * tm_for(k)) / (k * k) > MAX_G ? MAX_G : (128 * tm_for(k)) / (k * k);
 }
-// tensor-memory columns: D12 (16 T) and two D3 buffers (2 x 16 T), rounded to a power of two
+// tensor-memory columns: D (48 T: three 16-column piece groups per tile), rounded to a
+// power of two
 __host__ __device__ constexpr uint32_t tmem_cols_for(int k) {
   return 48 * tm_for(k) <= 64 ? 64u : (48 * tm_for(k) <= 128 ? 128u : (48 * tm_for(k) <= 256 ? 256u : 512u));
 }
@@ -139,28 +140,31 @@ __device__ __forceinline__ void split_pair(float x, float y, __nv_bfloat162 &h0,
 // Warp roles: warpgroup 0 (warps 0-3) stages each group's sources, turns stage-1/2
 // outputs into the next stage's operands, and its thread 0 issues every MMA and every
 // block-tile copy (one term ahead); warpgroup 1 (warps 4-7) adds each term's stage-3
-// output into the FP64 accumulators while warpgroup 0 works on the next terms.  Every
-// stage accumulates all kept piece products in one 16-column FP32 group per tile:
-// D12 (stages 1 and 2) at columns [0, 16T), D3 (stage 3) double-buffered at
-// [16T, 32T) and [32T, 48T).  Each D3 buffer b has its own "done" (MMA commit) and
-// "free" (warpgroup 1 finished reading) barrier, so no barrier runs more than one
-// phase ahead of its waiter; term info goes through a 4-deep ring.
+// output into the FP64 accumulators while warpgroup 0 works on the next term.
+// An M=128 x K=16 MMA costs about the same for any N <= 128 (its A tile fetch bounds
+// it), so every stage stacks the B pieces along N: A piece p times [B0 .. B(P-1-p)]
+// into column groups p..P-1 of the tile's 48 columns of D ([0, 48T)).  Warpgroup 1
+// copies stage 3's result to registers (summing the groups) and releases D before
+// the next term's stage 1; the FP64 accumulation then runs alongside that term.
 template <int K>
 __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(K)) apply_split_kernel(SplitArgs a) {
   constexpr int TM = tm_for(K);
   extern __shared__ __align__(1024) unsigned char smem[];
-  const int k = a.k, k2 = k * k, k3 = k2 * k, P = a.P, G = a.G, T = a.T;
-  const int rows = G * k2;
+  // k, k^2, k^3, G, T are compile-time: the index arithmetic below has no runtime division
+  constexpr int k = K, k2 = K * K, k3 = K * K * K, G = g_for(K), T = (G * K * K + 127) / 128;
+  const int P = a.P;
+  constexpr int rows = G * k2;
   unsigned char *A1 = smem;                          // [P][T][TILE_BYTES] stage-1 operand (sources)
   unsigned char *A23 = A1 + P * T * TILE_BYTES;      // [P][T][TILE_BYTES] stage-2/3 operand
   unsigned char *Bt = A23 + P * T * TILE_BYTES;      // [2 buffers][3 stages][1536]
-  __shared__ __align__(8) uint64_t bar12, bar3[2], bar_free[2], bar_drain, bar_b[2];
+  __shared__ __align__(8) uint64_t bar12, bar3, bar_free, bar_drain, bar_b[2];
   __shared__ uint32_t tmem_holder;
   __shared__ int slot_src[MAX_G];
   __shared__ uint64_t slot_mask[MAX_G][2];
   __shared__ uint64_t uni[2];
   __shared__ int g_level, g_l, total_it;
   __shared__ double ring_c[4];
+  __shared__ double c_sh[MRA_MAX_TERMS];
   __shared__ uint32_t ring_keep[4];
   __shared__ volatile int abort_flag;
 
@@ -176,16 +180,15 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(K)) apply_split_kernel
   }
   if (tid == 0) {
     tc::mbar_init(tc::smem_u32(&bar12), 1);
-    tc::mbar_init(tc::smem_u32(&bar3[0]), 1);
-    tc::mbar_init(tc::smem_u32(&bar3[1]), 1);
-    tc::mbar_init(tc::smem_u32(&bar_free[0]), 1);
-    tc::mbar_init(tc::smem_u32(&bar_free[1]), 1);
+    tc::mbar_init(tc::smem_u32(&bar3), 1);
+    tc::mbar_init(tc::smem_u32(&bar_free), 1);
     tc::mbar_init(tc::smem_u32(&bar_drain), 1);
     tc::mbar_init(tc::smem_u32(&bar_b[0]), 1);
     tc::mbar_init(tc::smem_u32(&bar_b[1]), 1);
     abort_flag = 0;
     total_it = 0;
   }
+  for (int m = tid; m < a.M; m += SPLIT_THREADS) c_sh[m] = a.c[m];
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(&tmem_holder), tmem_cols_for(K));
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   tc::fence_proxy_async_smem();
@@ -211,28 +214,23 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(K)) apply_split_kernel
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_holder;
-  const uint32_t d3col = (uint32_t)(T * 16);
   const uint32_t b12 = tc::smem_u32(&bar12);
-  const uint32_t b3[2] = {tc::smem_u32(&bar3[0]), tc::smem_u32(&bar3[1])};
-  const uint32_t bfree[2] = {tc::smem_u32(&bar_free[0]), tc::smem_u32(&bar_free[1])};
+  const uint32_t b3 = tc::smem_u32(&bar3), bfree = tc::smem_u32(&bar_free);
   const uint32_t bb[2] = {tc::smem_u32(&bar_b[0]), tc::smem_u32(&bar_b[1])};
   const int nit = total_it;
   const uint32_t idesc16 = tc::idesc_bf16(128, 16, 1, 0);
+  const uint32_t idesc_n[3] = {idesc16, tc::idesc_bf16(128, 32, 1, 0), tc::idesc_bf16(128, 48, 1, 0)};
 
-  // one stage: for every tile, the products A_p B_q with p + q < P (smallest first) into
-  // the tile's 16 columns at `dcol`
-  auto issue_stage = [&](const unsigned char *A, const unsigned char *B, uint32_t dcol) {
+  // stages 1 and 2: A piece p times B pieces 0..P-1-p (stacked along N) into column
+  // groups p..P-1 of the tile's 48 columns of D12
+  auto issue_stacked = [&](const unsigned char *A, const unsigned char *B) {
     for (int t = 0; t < T; ++t) {
-      uint32_t d = tmem + dcol + (uint32_t)(t * 16);
-      bool first = true;
-      for (int s2 = P - 1; s2 >= 0; --s2)
-        for (int p = 0; p <= s2; ++p) {
-          int q = s2 - p;
-          uint64_t ad = tc::smem_desc(tc::smem_u32(A + (p * T + t) * TILE_BYTES), 128, MG_BYTES);
-          uint64_t bd = tc::smem_desc(tc::smem_u32(B + q * BPIECE_BYTES), 128, 256);
-          tc::mma_bf16(d, ad, bd, idesc16, first ? 0u : 1u);
-          first = false;
-        }
+      uint32_t d = tmem + (uint32_t)(t * 48);
+      for (int p = 0; p < P; ++p) {
+        uint64_t ad = tc::smem_desc(tc::smem_u32(A + (p * T + t) * TILE_BYTES), 128, MG_BYTES);
+        uint64_t bd = tc::smem_desc(tc::smem_u32(B), 128, 256);
+        tc::mma_bf16(d + 16 * p, ad, bd, idesc_n[P - 1 - p], p > 0 ? 1u : 0u);
+      }
     }
   };
 
@@ -272,13 +270,23 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(K)) apply_split_kernel
         if (P > 2) *(__nv_bfloat162 *)(A23 + 2 * stride + off) = h2;
       }
     };
-    // tiles t0, t0+1 of D12 for this thread's lane, one wait for both loads
+    // tiles t0, t0+1 of D12 for this thread's lane (first K columns of each of the P
+    // groups, summed smallest first), one wait for all loads
     auto load_d12_pair = [&](int t0, float (*v)[16]) {
       const uint32_t base = tmem + ((uint32_t)(32 * quarter) << 16);
 #pragma unroll
-      for (int u = 0; u < 2; ++u)
-        if (t0 + u < T) tc::tmem_ld16(base + (uint32_t)((t0 + u) * 16), v[u]);
-      tc::tmem_ld_wait();
+      for (int u = 0; u < 2; ++u) {
+        float c[3][K];
+        if (t0 + u < T) {
+#pragma unroll
+          for (int p = 0; p < 3; ++p)
+            if (p < P) tc::tmem_ldk<K>(base + (uint32_t)((t0 + u) * 48 + 16 * p), c[p]);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < K; ++j)
+            v[u][j] = P == 3 ? (c[2][j] + c[1][j]) + c[0][j] : (P == 2 ? c[1][j] + c[0][j] : c[0][j]);
+        }
+      }
     };
     for (int g = g0; g < g1 && !bad; ++g) {
       const int r0 = a.grp_start[g], r1 = a.grp_start[g + 1];
@@ -346,18 +354,20 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(K)) apply_split_kernel
         const int m_next = next_term(bits0, bits1);
         if (tid == 0) {
           // term info for warpgroup 1 (ring slot it&3 was read by its iteration it-4, which
-          // finished before the "D3 free" arrival that let stage 3 of term it-1 start)
+          // finished before the "D free" arrival that let stage 1 of term it-3 start)
           uint32_t keep = 0;
           const int w = m >> 6;
           for (int i = 0; i < G; ++i) keep |= (uint32_t)((slot_mask[i][w] >> (m & 63)) & 1ull) << i;
           ring_keep[it & 3] = keep;
-          ring_c[it & 3] = a.c[m];
+          ring_c[it & 3] = c_sh[m];
           bool ok = tc::mbar_wait(bb[buf], (uint32_t)((it >> 1) & 1), WAIT_CYCLES);
+          // D holds stage 3 of term it-1 until warpgroup 1 has copied it out
+          if (ok && it > 0) ok = tc::mbar_wait(bfree, (uint32_t)((it - 1) & 1), WAIT_CYCLES);
           if (!ok) {
             abort_flag = 1;
           } else {
             tc::fence_after_sync();
-            issue_stage(A1, Bb, 0);  // ---- stage 1: rows (i, jy, jz), contraction jx
+            issue_stacked(A1, Bb);  // ---- stage 1: rows (i, jy, jz), contraction jx
             tc::mma_commit(b12);
           }
         }
@@ -383,7 +393,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(K)) apply_split_kernel
         wg_sync(1);
         if (tid == 0) {  // ---- stage 2: rows (i, jz, ix), contraction jy
           tc::fence_after_sync();
-          issue_stage(A23, Bb + BSTAGE_BYTES, 0);
+          issue_stacked(A23, Bb + BSTAGE_BYTES);
           tc::mma_commit(b12);
         }
         if (!wait12()) { bad = true; break; }
@@ -404,17 +414,10 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(K)) apply_split_kernel
         tc::fence_proxy_async_smem();
         tc::fence_before_sync();
         wg_sync(1);
-        if (tid == 0) {  // ---- stage 3 into D3 buffer it&1, once warpgroup 1 has read term it-2
-          const int db = it & 1;
-          bool ok = true;
-          if (it >= 2) ok = tc::mbar_wait(bfree[db], (uint32_t)(((it >> 1) - 1) & 1), WAIT_CYCLES);
-          if (!ok) {
-            abort_flag = 1;
-          } else {
-            tc::fence_after_sync();
-            issue_stage(A23, Bb + 2 * BSTAGE_BYTES, d3col + (uint32_t)(db * 16 * T));
-            tc::mma_commit(b3[db]);
-          }
+        if (tid == 0) {  // ---- stage 3: rows (i, ix, iy), contraction jz
+          tc::fence_after_sync();
+          issue_stacked(A23, Bb + 2 * BSTAGE_BYTES);
+          tc::mma_commit(b3);
         }
         ++it;
         m = m_next;
@@ -431,10 +434,9 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(K)) apply_split_kernel
 #pragma unroll
       for (int j = 0; j < K; ++j) acc[t][j] = 0.0;
     bool bad = false;
-    const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16) + d3col;
+    const uint32_t base = tmem + ((uint32_t)(32 * quarter) << 16);
     for (int it = 0; it < nit; ++it) {
-      const int db = it & 1;
-      bool ok = tc::mbar_wait(b3[db], (uint32_t)((it >> 1) & 1), WAIT_CYCLES);
+      bool ok = tc::mbar_wait(b3, (uint32_t)(it & 1), WAIT_CYCLES);
       if (wg_vote_or(2, !ok || abort_flag)) {
         bad = true;
         break;
@@ -442,27 +444,31 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(K)) apply_split_kernel
       tc::fence_after_sync();
       const double cm = ring_c[it & 3];
       const uint32_t keep = ring_keep[it & 3];
-      const uint32_t base = lane_base + (uint32_t)(db * 16 * T);
+      float v[TM][K];
 #pragma unroll
-      for (int t0 = 0; t0 < TM; t0 += 2) {  // two tiles per tensor-memory round trip
-        float v[2][16];
+      for (int t = 0; t < TM; ++t) {
+        if (t < T) {
+          float c[3][K];
 #pragma unroll
-        for (int u = 0; u < 2; ++u)
-          if (t0 + u < T) tc::tmem_ld16(base + (uint32_t)((t0 + u) * 16), v[u]);
-        tc::tmem_ld_wait();
+          for (int p = 0; p < 3; ++p)
+            if (p < P) tc::tmem_ldk<K>(base + (uint32_t)(t * 48 + 16 * p), c[p]);
+          tc::tmem_ld_wait();
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int t = t0 + u;
-          int m3 = t * 128 + quarter * 32 + lane;
-          if (t < TM && t < T && m3 < rows && ((keep >> (m3 / k2)) & 1u)) {
-#pragma unroll
-            for (int j = 0; j < K; ++j) acc[t][j] = fma(cm, widen(v[u][j]), acc[t][j]);
-          }
+          for (int j = 0; j < K; ++j)
+            v[t][j] = P == 3 ? (c[2][j] + c[1][j]) + c[0][j] : (P == 2 ? c[1][j] + c[0][j] : c[0][j]);
         }
       }
       tc::fence_before_sync();
       wg_sync(2);
-      if (tid == 128) mbar_arrive(bfree[db]);  // D3 buffer db may take stage 3 of term it+2
+      if (tid == 128) mbar_arrive(bfree);  // D may take stage 1 of the next term
+#pragma unroll
+      for (int t = 0; t < TM; ++t) {
+        int m3 = t * 128 + quarter * 32 + lane;
+        if (t < T && m3 < rows && ((keep >> (m3 / k2)) & 1u)) {
+#pragma unroll
+          for (int j = 0; j < K; ++j) acc[t][j] = fma(cm, widen(v[t][j]), acc[t][j]);
+        }
+      }
     }
     if (bad) abort_flag = 1;
     // write the destinations: row (i, ix, iy), columns iz
