@@ -59,6 +59,8 @@ extern "C" {
 
 #define MRA_SCREEN_NONE 0 /* keep every term */
 #define MRA_SCREEN_NORM 1 /* keep a term iff |c| ||Rx|| ||Ry|| ||Rz|| ||s|| >= tau */
+#define MRA_SCREEN_LEARNED 2 /* the norm screen, then also skip a kept term when the learned
+                                 model predicts log10 ||term|| + delta < log10 tau */
 
 #define MRA_STENCIL_SHELLS 0  /* shells of |l|_inf = 0,1,..,max_disp, stop at the first empty shell */
 #define MRA_STENCIL_NEAREST 1 /* all 27 displacements with |l|_inf <= 1 */
@@ -67,6 +69,7 @@ extern "C" {
 #define MRA_MAX_K 16
 #define MRA_MAX_TERMS 128
 #define MRA_NOALLOC_MAX_BOXES (1 << 20) /* largest tree mra_norm_noalloc accepts */
+#define MRA_MLP_PARAMS 4555 /* floats of a learned-screen model (see mra_mlp_init) */
 
 /* ---- data types ----------------------------------------------------------- */
 
@@ -96,6 +99,8 @@ typedef struct {
   double tau;     /* screen threshold (ignored for MRA_SCREEN_NONE) */
   int stencil;    /* MRA_STENCIL_* */
   int max_disp;   /* largest |l|_inf for MRA_STENCIL_SHELLS (<= the operator's max_disp) */
+  const float *mlp; /* MRA_SCREEN_LEARNED: device model, MRA_MLP_PARAMS floats */
+  double delta;     /* MRA_SCREEN_LEARNED: safety margin in log10 units */
 } mra_apply_opts;
 
 typedef struct {
@@ -108,6 +113,8 @@ typedef struct {
   int64_t sources_truncated;  /* sources whose last allowed shell still kept terms */
   double skipped_bound;       /* sum of the screen bounds of dropped triples */
   double kernel_ms;           /* device time of the apply kernel (CUDA events on `stream`) */
+  int64_t terms_learned_skipped; /* triples the norm screen kept and the learned screen dropped */
+  double learned_skipped_bound;  /* sum of the norm-screen bounds of those triples */
 } mra_apply_stats;
 
 typedef struct {
@@ -200,6 +207,55 @@ int mra_apply_workspace_size(const mra_operator *op, const mra_tree_view *in,
 int mra_apply(const mra_operator *op, const mra_tree_view *in, const mra_apply_opts *opts,
               mra_tree_view *out, void *workspace, size_t workspace_bytes,
               mra_apply_stats *stats, void *stream);
+
+/* Learned screen (a 4 -> 64 -> 64 -> 1 tanh network in FP32, MRA_MLP_PARAMS floats on
+ * the device).  It predicts log10 of a term's norm ||c_m (R_x x R_y x R_z) s_b||_F from the
+ * features (level n, |l|_2, log10 t_m, log10 ||s_b||_F); MRA_SCREEN_LEARNED drops a term
+ * that passed the norm screen when prediction + delta < log10 tau.  The paper has no
+ * counterpart (its screen is the norm estimate of Sec. 2.2); the norm screen remains the
+ * fallback and a bound on what the learned one may drop (learned_skipped_bound).
+ * Parameter layout: W1[64][4], b1[64], W2[64][64], b2[64], W3[64], b3, x_mean[4], x_std[4],
+ * y_mean, y_std; inputs are standardised by (x_mean, x_std), the output is scaled by
+ * (y_std, y_mean). */
+
+/* Log training data from a plain apply: run the screen of mra_apply with `opts` (its
+ * precision is ignored), draw about max_terms of the kept terms with a counter-based
+ * hash of (seed, record, term) and write, for each, the features (device float[4]) and
+ * log10 of the term's true norm in FP64 (device float).  *n_logged <= max_terms.
+ * workspace: at least mra_apply_workspace_size bytes. */
+int mra_log_terms(const mra_operator *op, const mra_tree_view *in, const mra_apply_opts *opts,
+                  int64_t max_terms, uint64_t seed, float *features, float *log_norms,
+                  int64_t *n_logged, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Initialise a model: uniform(+-sqrt(6/(fan_in+fan_out))) weights from a counter-based
+ * generator of `seed`, zero biases, identity standardisation. */
+int mra_mlp_init(float *params, uint64_t seed, void *stream);
+
+/* Set the model's standardisation (mean and standard deviation of each feature and of
+ * the target) from n logged rows (device arrays). */
+int mra_mlp_standardize(float *params, const float *features, const float *targets, int64_t n,
+                        void *stream);
+
+/* Predictions (log10 term norms) for n rows of features; all device arrays. */
+int mra_mlp_forward(const float *params, const float *features, int64_t n, float *out, void *stream);
+
+/* Workspace bytes of mra_mlp_grad for n rows, or of mra_mlp_train for batches of n rows. */
+int mra_mlp_workspace_size(int64_t n, size_t *bytes);
+
+/* Full-batch gradient (device float[MRA_MLP_PARAMS], the trainable first 4545 entries
+ * written) of the mean squared error between the standardised output and the
+ * standardised targets, and that loss (host).  Deterministic. */
+int mra_mlp_grad(const float *params, const float *features, const float *targets, int64_t n,
+                 float *grad, double *loss, void *workspace, size_t workspace_bytes, void *stream);
+
+/* `steps` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, rate lr) on minibatches of
+ * `batch` rows drawn with replacement by a counter-based generator of (seed, step).
+ * adam_state: device float[2*MRA_MLP_PARAMS], zero before the first step; step0 = number
+ * of steps already taken with this state.  *final_loss (host, may be NULL) = loss of the
+ * last minibatch.  workspace: mra_mlp_workspace_size(batch) bytes. */
+int mra_mlp_train(float *params, float *adam_state, const float *features, const float *targets,
+                  int64_t n, int batch, int steps, int step0, float lr, uint64_t seed,
+                  double *final_loss, void *workspace, size_t workspace_bytes, void *stream);
 
 /* Per-box Frobenius norms (device array of tree->n doubles, may be NULL) and
  * the total L2 norm (host double, may be NULL).  Deterministic reduction. */

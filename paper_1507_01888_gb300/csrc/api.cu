@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "apply_internal.cuh"
+#include "mlp.cuh"
 
 namespace mra {
 
@@ -474,15 +475,17 @@ static int check_opts(const Operator *op, const mra_tree_view *in, const mra_app
   if (in->L != op->L) return fail(MRA_ERR_ARG, "mra_apply: tree L differs from operator L");
   if (o->precision != MRA_PREC_FP64 && o->precision != MRA_PREC_SPLIT_BF16)
     return fail(MRA_ERR_ARG, "mra_apply: unknown precision %d", o->precision);
-  if (o->screen != MRA_SCREEN_NONE && o->screen != MRA_SCREEN_NORM)
+  if (o->screen != MRA_SCREEN_NONE && o->screen != MRA_SCREEN_NORM && o->screen != MRA_SCREEN_LEARNED)
     return fail(MRA_ERR_ARG, "mra_apply: unknown screen %d", o->screen);
+  if (o->screen == MRA_SCREEN_LEARNED && (!o->mlp || !(o->tau > 0.0)))
+    return fail(MRA_ERR_ARG, "mra_apply: the learned screen needs a model and tau > 0");
   if (o->stencil != MRA_STENCIL_SHELLS && o->stencil != MRA_STENCIL_NEAREST)
     return fail(MRA_ERR_ARG, "mra_apply: unknown stencil %d", o->stencil);
   if (o->stencil == MRA_STENCIL_SHELLS && (o->max_disp < 0 || o->max_disp > op->max_disp))
     return fail(MRA_ERR_ARG, "mra_apply: max_disp %d outside 0..%d", o->max_disp, op->max_disp);
   if (o->stencil == MRA_STENCIL_NEAREST && op->max_disp < 1)
     return fail(MRA_ERR_ARG, "mra_apply: nearest stencil needs an operator with max_disp >= 1");
-  if (o->screen == MRA_SCREEN_NORM && !(o->tau >= 0.0)) return fail(MRA_ERR_ARG, "mra_apply: tau must be >= 0");
+  if (o->screen != MRA_SCREEN_NONE && !(o->tau >= 0.0)) return fail(MRA_ERR_ARG, "mra_apply: tau must be >= 0");
   if (o->precision == MRA_PREC_SPLIT_BF16 && (o->pieces < 2 || o->pieces > 3))
     return fail(MRA_ERR_ARG, "mra_apply: pieces must be 2 or 3");
   return MRA_OK;
@@ -511,6 +514,99 @@ int mra_apply(const mra_operator *h, const mra_tree_view *in, const mra_apply_op
   if (in->n >= (1LL << 31)) return fail(MRA_ERR_ARG, "mra_apply: more than 2^31 source boxes");
   out->L = op->L;
   return apply_run(*op, *in, *o, *out, workspace, workspace_bytes, stats, (cudaStream_t)stream);
+}
+
+int mra_log_terms(const mra_operator *h, const mra_tree_view *in, const mra_apply_opts *o, int64_t max_terms,
+                  uint64_t seed, float *features, float *log_norms, int64_t *n_logged, void *workspace,
+                  size_t workspace_bytes, void *stream) {
+  const Operator *op = reinterpret_cast<const Operator *>(h);
+  int rc = check_opts(op, in, o);
+  if (rc) return rc;
+  if (!n_logged || max_terms < 0 || (max_terms > 0 && (!features || !log_norms)))
+    return fail(MRA_ERR_ARG, "mra_log_terms: bad output arguments");
+  if (in->n > 0 && !workspace) return fail(MRA_ERR_ARG, "mra_log_terms: NULL workspace");
+  if (max_terms >= (1LL << 31)) return fail(MRA_ERR_ARG, "mra_log_terms: max_terms >= 2^31");
+  return log_terms_run(*op, *in, *o, max_terms, seed, features, log_norms, n_logged, workspace,
+                       workspace_bytes, (cudaStream_t)stream);
+}
+
+int mra_mlp_init(float *params, uint64_t seed, void *stream) {
+  if (!params) return fail(MRA_ERR_ARG, "mra_mlp_init: NULL params");
+  cudaStream_t s = (cudaStream_t)stream;
+  MRA_CUDA_TRY(cudaMemsetAsync(params, 0, MLP_NALL * sizeof(float), s));
+  MRA_CUDA_TRY(mlp_init(params, seed, s));
+  const float ident[10] = {0, 0, 0, 0, 1, 1, 1, 1, 0, 1};
+  MRA_CUDA_TRY(cudaMemcpyAsync(params + MLP_XMEAN, ident, sizeof(ident), cudaMemcpyHostToDevice, s));
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  return MRA_OK;
+}
+
+int mra_mlp_standardize(float *params, const float *x, const float *y, int64_t n, void *stream) {
+  if (!params || n < 1 || !x || !y) return fail(MRA_ERR_ARG, "mra_mlp_standardize: bad arguments");
+  MRA_CUDA_TRY(mlp_fit_norm(params, x, y, n, (cudaStream_t)stream));
+  return MRA_OK;
+}
+
+int mra_mlp_forward(const float *params, const float *x, int64_t n, float *out, void *stream) {
+  if (!params || n < 0 || (n > 0 && (!x || !out))) return fail(MRA_ERR_ARG, "mra_mlp_forward: bad arguments");
+  MRA_CUDA_TRY(mlp_forward(params, x, n, out, (cudaStream_t)stream));
+  return MRA_OK;
+}
+
+static size_t mlp_ws(int64_t n) {
+  size_t a = (mlp_grad_workspace(n) + 255) & ~(size_t)255;
+  size_t b = ((size_t)n * 5 * sizeof(float) + 255) & ~(size_t)255;
+  size_t c = ((size_t)MLP_NALL * sizeof(float) + 255) & ~(size_t)255;
+  return a + b + c + 256;
+}
+
+int mra_mlp_workspace_size(int64_t n, size_t *bytes) {
+  if (!bytes || n < 1) return fail(MRA_ERR_ARG, "mra_mlp_workspace_size: bad arguments");
+  *bytes = mlp_ws(n);
+  return MRA_OK;
+}
+
+int mra_mlp_grad(const float *params, const float *x, const float *y, int64_t n, float *grad, double *loss,
+                 void *ws, size_t ws_bytes, void *stream) {
+  if (!params || n < 1 || !x || !y || !grad || !ws) return fail(MRA_ERR_ARG, "mra_mlp_grad: bad arguments");
+  if (ws_bytes < mlp_ws(n)) return fail(MRA_ERR_CAPACITY, "mra_mlp_grad: workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  char *w = (char *)ws;
+  size_t a = (mlp_grad_workspace(n) + 255) & ~(size_t)255;
+  double *d_loss = (double *)(w + mlp_ws(n) - 256);
+  MRA_CUDA_TRY(mlp_grad(params, x, y, n, grad, d_loss, w, s));
+  (void)a;
+  double h = 0.0;
+  MRA_CUDA_TRY(cudaMemcpyAsync(&h, d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  if (loss) *loss = h;
+  return MRA_OK;
+}
+
+int mra_mlp_train(float *params, float *adam_state, const float *x, const float *y, int64_t n, int batch,
+                  int steps, int step0, float lr, uint64_t seed, double *final_loss, void *ws, size_t ws_bytes,
+                  void *stream) {
+  if (!params || !adam_state || !x || !y || n < 1 || batch < 1 || steps < 0 || step0 < 0 || !(lr > 0.f) || !ws)
+    return fail(MRA_ERR_ARG, "mra_mlp_train: bad arguments");
+  if (ws_bytes < mlp_ws(batch)) return fail(MRA_ERR_CAPACITY, "mra_mlp_train: workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  char *w = (char *)ws;
+  size_t a = (mlp_grad_workspace(batch) + 255) & ~(size_t)255;
+  float *bx = (float *)(w + a);
+  float *by = bx + (size_t)batch * 4;
+  size_t b = ((size_t)batch * 5 * sizeof(float) + 255) & ~(size_t)255;
+  float *grad = (float *)(w + a + b);
+  double *d_loss = (double *)(w + mlp_ws(batch) - 256);
+  for (int st = 0; st < steps; ++st) {
+    MRA_CUDA_TRY(mlp_gather_batch(x, y, n, batch, seed, step0 + st, bx, by, s));
+    MRA_CUDA_TRY(mlp_grad(params, bx, by, batch, grad, d_loss, w, s));
+    MRA_CUDA_TRY(mlp_adam(params, adam_state, adam_state + MLP_NALL, grad, lr, step0 + st + 1, s));
+  }
+  double h = 0.0;
+  MRA_CUDA_TRY(cudaMemcpyAsync(&h, d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  if (final_loss) *final_loss = h;
+  return MRA_OK;
 }
 
 int mra_norm(const mra_tree_view *t, double *per_box, double *total, void *stream) {

@@ -13,6 +13,7 @@
 #include <cub/cub.cuh>
 
 #include "apply_internal.cuh"
+#include "mlp.cuh"
 
 namespace mra {
 
@@ -83,10 +84,21 @@ struct ScreenArgs {
   double *box_skipped;
   int *box_trunc;
   int *err;
+  // learned screen (MRA_SCREEN_LEARNED): drop a kept term when mlp(features) < learned_cut
+  const float *mlp;
+  const double *t;            // Gaussian exponents (features)
+  float learned_cut;          // log10(tau) - delta
+  int64_t *box_learned;
+  double *box_lbound;
 };
 
 template <int PASS>
 __global__ void screen_kernel(ScreenArgs a) {
+  extern __shared__ float mlp_sh[];  // the learned screen's parameters, when used
+  if (a.mlp) {
+    for (int i = threadIdx.x; i < MLP_NALL; i += blockDim.x) mlp_sh[i] = a.mlp[i];
+    __syncthreads();
+  }
   int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   int lane = threadIdx.x & 31;
   if (b >= a.n_in) return;
@@ -105,8 +117,9 @@ __global__ void screen_kernel(ScreenArgs a) {
   int nl = 2 * Dop + 1;
   const double *Nl = a.N + a.level_off[n];
   double sn = a.snorm[b];
-  int64_t count = 0, kept = 0, screened = 0;
-  double skipped = 0.0;
+  int64_t count = 0, kept = 0, screened = 0, learned = 0;
+  double skipped = 0.0, lbound = 0.0;
+  const float log_sn = (float)log10(fmax(sn, 1e-300));
   int64_t wpos = PASS == 1 ? a.off[b] : 0;
   int d;
   for (d = 0; d <= D; ++d) {
@@ -124,15 +137,28 @@ __global__ void screen_kernel(ScreenArgs a) {
             int m = m0 + lane;
             bool keep = false;
             double B = 0.0;
+            bool dropped_by_model = false;
             if (m < a.M) {
               B = fabs(a.c[m]) * Nl[m * nl + lx + Dop] * Nl[m * nl + ly + Dop] *
                   Nl[m * nl + lz + Dop] * sn;
               keep = a.screen == MRA_SCREEN_NONE ? true : (B >= a.tau);
+              if (keep && a.mlp) {
+                float f[4] = {(float)n, sqrtf((float)(lx * lx + ly * ly + lz * lz)), (float)log10(a.t[m]), log_sn};
+                if (mlp_predict(mlp_sh, f) < a.learned_cut) {
+                  keep = false;
+                  dropped_by_model = true;
+                }
+              }
+            }
+            if (PASS == 0) {
+              unsigned lb = __ballot_sync(0xffffffffu, dropped_by_model);
+              learned += __popc(lb);
+              lbound += warp_sum(dropped_by_model ? B : 0.0);
             }
             unsigned bal = __ballot_sync(0xffffffffu, keep);
             mask[m0 >> 6] |= (uint64_t)bal << (m0 & 63);
             if (PASS == 0) {
-              double sk = (m < a.M && !keep) ? B : 0.0;
+              double sk = (m < a.M && !keep && !dropped_by_model) ? B : 0.0;
               skipped += warp_sum(sk);
             }
           }
@@ -163,6 +189,8 @@ __global__ void screen_kernel(ScreenArgs a) {
     a.box_screened[b] = screened;
     a.box_skipped[b] = skipped;
     a.box_trunc[b] = (a.stencil == MRA_STENCIL_SHELLS && d == D + 1) ? 1 : 0;
+    a.box_learned[b] = learned;
+    a.box_lbound[b] = lbound;
   }
 }
 
@@ -363,7 +391,7 @@ int64_t apply_max_records(const Operator &op, const mra_apply_opts &o, int64_t n
 //   per destination (<= records): dest key, seg (+1)
 //   CUB temp storage (max over scan / sort / reduce needs)
 struct Layout {
-  size_t snorm, dstop, cnt, off, kept, screened, skipped, trunc;
+  size_t snorm, dstop, cnt, off, kept, screened, skipped, trunc, learned, lbound;
   size_t rkey, rsrc, rl, rmask, skey, pin, pout, head, did, dkey, seg, ndest, split, tmp;
   size_t split_bytes, tmp_bytes, total;
 };
@@ -385,6 +413,8 @@ static Layout make_layout(int64_t n_in, int64_t P) {
   L.screened = take(nb * 8);
   L.skipped = take(nb * 8);
   L.trunc = take(nb * 4);
+  L.learned = take(nb * 8);
+  L.lbound = take(nb * 8);
   L.rkey = take(np * 8);
   L.rsrc = take(np * 4);
   L.rl = take(np * 4);
@@ -419,50 +449,68 @@ size_t apply_workspace_bytes(const Operator &op, const mra_apply_opts &o, int64_
   return make_layout(n_in, apply_max_records(op, o, n_in)).total;
 }
 
-int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts &o,
-              mra_tree_view &out, void *ws, size_t ws_bytes, mra_apply_stats *stats,
-              cudaStream_t s) {
+// Pointers into a carved workspace.
+struct WsPtrs {
+  double *snorm;
+  int *dstop;
+  int64_t *cnt, *off, *bkept, *bscr, *blearned;
+  double *bskip, *blbound;
+  int *btrunc;
+  uint64_t *rkey, *skey, *rmask, *dkey;
+  int *rsrc, *rl, *pin, *pout, *head, *did;
+  int64_t *seg, *ndest;
+  void *tmp;
+  size_t tmpb;
+};
+
+static WsPtrs carve(const Layout &L, void *ws) {
+  char *w = (char *)ws;
+  WsPtrs p{};
+  p.snorm = (double *)(w + L.snorm);
+  p.dstop = (int *)(w + L.dstop);
+  p.cnt = (int64_t *)(w + L.cnt);
+  p.off = (int64_t *)(w + L.off);
+  p.bkept = (int64_t *)(w + L.kept);
+  p.bscr = (int64_t *)(w + L.screened);
+  p.bskip = (double *)(w + L.skipped);
+  p.btrunc = (int *)(w + L.trunc);
+  p.blearned = (int64_t *)(w + L.learned);
+  p.blbound = (double *)(w + L.lbound);
+  p.rkey = (uint64_t *)(w + L.rkey);
+  p.skey = (uint64_t *)(w + L.skey);
+  p.rsrc = (int *)(w + L.rsrc);
+  p.rl = (int *)(w + L.rl);
+  p.rmask = (uint64_t *)(w + L.rmask);
+  p.pin = (int *)(w + L.pin);
+  p.pout = (int *)(w + L.pout);
+  p.head = (int *)(w + L.head);
+  p.did = (int *)(w + L.did);
+  p.dkey = (uint64_t *)(w + L.dkey);
+  p.seg = (int64_t *)(w + L.seg);
+  p.ndest = (int64_t *)(w + L.ndest);
+  p.tmp = w + L.tmp;
+  p.tmpb = L.tmp_bytes;
+  return p;
+}
+
+// Source norms, norm (and learned) screen, record counts, scan and record emission.
+// On return *P_out holds the number of records (written in source order).
+static int screen_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts &o, const WsPtrs &w,
+                      int64_t Pmax, mra_apply_stats *stats, int64_t *P_out, cudaStream_t s) {
   const int k = op.k, k3 = k * k * k;
   const int64_t n_in = in.n;
-  const int64_t Pmax = apply_max_records(op, o, n_in);
-  Layout L = make_layout(n_in, Pmax);
-  if (ws_bytes < L.total)
-    return fail(MRA_ERR_CAPACITY, "mra_apply: workspace of %zu bytes < %zu needed", ws_bytes, L.total);
-  char *w = (char *)ws;
-  double *snorm = (double *)(w + L.snorm);
-  int *dstop = (int *)(w + L.dstop);
-  int64_t *cnt = (int64_t *)(w + L.cnt), *off = (int64_t *)(w + L.off);
-  int64_t *bkept = (int64_t *)(w + L.kept), *bscr = (int64_t *)(w + L.screened);
-  double *bskip = (double *)(w + L.skipped);
-  int *btrunc = (int *)(w + L.trunc);
-  uint64_t *rkey = (uint64_t *)(w + L.rkey), *skey = (uint64_t *)(w + L.skey);
-  int *rsrc = (int *)(w + L.rsrc), *rl = (int *)(w + L.rl);
-  uint64_t *rmask = (uint64_t *)(w + L.rmask);
-  int *pin = (int *)(w + L.pin), *pout = (int *)(w + L.pout);
-  int *head = (int *)(w + L.head), *did = (int *)(w + L.did);
-  uint64_t *dkey = (uint64_t *)(w + L.dkey);
-  int64_t *seg = (int64_t *)(w + L.seg), *ndest = (int64_t *)(w + L.ndest);
-  void *tmp = w + L.tmp;
-  size_t tmpb = L.tmp_bytes;
-
-  if (n_in == 0) {
-    out.n = 0;
-    if (stats) *stats = mra_apply_stats{};
-    return MRA_OK;
-  }
   // error flag lives in the first word of the dest-count slot until it is used
-  int *d_err = (int *)ndest;
+  int *d_err = (int *)w.ndest;
   MRA_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int64_t), s));
-
   const int wpb = 8;  // warps per CTA for per-box kernels
   unsigned gboxes = (unsigned)((n_in + wpb - 1) / wpb);
-  box_norm_kernel<<<gboxes, 32 * wpb, 0, s>>>(n_in, k3, in.coeffs, snorm);
+  box_norm_kernel<<<gboxes, 32 * wpb, 0, s>>>(n_in, k3, in.coeffs, w.snorm);
   MRA_CUDA_TRY(cudaGetLastError());
 
   ScreenArgs a{};
   a.n_in = n_in;
   a.keys = in.keys;
-  a.snorm = snorm;
+  a.snorm = w.snorm;
   a.M = op.M;
   a.c = op.d_c;
   a.N = op.d_N;
@@ -470,42 +518,52 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
   a.level_off = op.d_level_off;
   a.stencil = o.stencil;
   a.dmax = apply_max_disp(op, o);
-  a.screen = o.screen;
+  a.screen = o.screen == MRA_SCREEN_LEARNED ? MRA_SCREEN_NORM : o.screen;
   a.tau = o.tau;
-  a.dstop = dstop;
-  a.cnt = cnt;
-  a.off = off;
-  a.rec_key = rkey;
-  a.rec_src = rsrc;
-  a.rec_l = rl;
-  a.rec_mask = rmask;
-  a.box_kept = bkept;
-  a.box_screened = bscr;
-  a.box_skipped = bskip;
-  a.box_trunc = btrunc;
+  a.dstop = w.dstop;
+  a.cnt = w.cnt;
+  a.off = w.off;
+  a.rec_key = w.rkey;
+  a.rec_src = w.rsrc;
+  a.rec_l = w.rl;
+  a.rec_mask = w.rmask;
+  a.box_kept = w.bkept;
+  a.box_screened = w.bscr;
+  a.box_skipped = w.bskip;
+  a.box_trunc = w.btrunc;
   a.err = d_err;
-  screen_kernel<0><<<gboxes, 32 * wpb, 0, s>>>(a);
+  a.mlp = o.screen == MRA_SCREEN_LEARNED ? o.mlp : nullptr;
+  a.t = op.d_t;
+  a.learned_cut = (float)(log10(o.tau) - o.delta);
+  a.box_learned = w.blearned;
+  a.box_lbound = w.blbound;
+  const size_t ssm = a.mlp ? (size_t)MLP_NALL * sizeof(float) : 0;
+  screen_kernel<0><<<gboxes, 32 * wpb, ssm, s>>>(a);
   MRA_CUDA_TRY(cudaGetLastError());
-  MRA_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, tmpb, cnt, off, (int)n_in, s));
+  void *tmp = w.tmp;
+  size_t tmpb = w.tmpb;
+  MRA_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, tmpb, w.cnt, w.off, (int)n_in, s));
   // statistics reduced on the device (deterministic), read with the record count
-  int64_t *red_i = (int64_t *)(seg);  // seg is free until the segments pass
-  double *red_d = (double *)(seg + 4);
+  int64_t *red_i = w.seg;  // seg is free until the segments pass
+  double *red_d = (double *)(w.seg + 4);
   if (stats) {
-    MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, bkept, red_i + 0, (int)n_in, s));
-    MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, bscr, red_i + 1, (int)n_in, s));
-    MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, btrunc, (int *)(red_i + 2), (int)n_in, s));
-    MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, bskip, red_d, (int)n_in, s));
+    MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, w.bkept, red_i + 0, (int)n_in, s));
+    MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, w.bscr, red_i + 1, (int)n_in, s));
+    MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, w.btrunc, (int *)(red_i + 2), (int)n_in, s));
+    MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, w.blearned, red_i + 3, (int)n_in, s));
+    MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, w.bskip, red_d, (int)n_in, s));
+    MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, w.blbound, red_d + 1, (int)n_in, s));
   }
   int64_t h_last[2] = {0, 0};
   int h_err = 0;
-  int64_t hs[3] = {0, 0, 0};
-  double hd = 0.0;
-  MRA_CUDA_TRY(cudaMemcpyAsync(&h_last[0], off + n_in - 1, 8, cudaMemcpyDeviceToHost, s));
-  MRA_CUDA_TRY(cudaMemcpyAsync(&h_last[1], cnt + n_in - 1, 8, cudaMemcpyDeviceToHost, s));
+  int64_t hs[4] = {0, 0, 0, 0};
+  double hd[2] = {0.0, 0.0};
+  MRA_CUDA_TRY(cudaMemcpyAsync(&h_last[0], w.off + n_in - 1, 8, cudaMemcpyDeviceToHost, s));
+  MRA_CUDA_TRY(cudaMemcpyAsync(&h_last[1], w.cnt + n_in - 1, 8, cudaMemcpyDeviceToHost, s));
   MRA_CUDA_TRY(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   if (stats) {
-    MRA_CUDA_TRY(cudaMemcpyAsync(hs, red_i, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    MRA_CUDA_TRY(cudaMemcpyAsync(&hd, red_d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MRA_CUDA_TRY(cudaMemcpyAsync(hs, red_i, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    MRA_CUDA_TRY(cudaMemcpyAsync(hd, red_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   }
   MRA_CUDA_TRY(cudaStreamSynchronize(s));
   if (h_err)
@@ -519,18 +577,50 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
     *stats = mra_apply_stats{};
     stats->n_in = n_in;
     stats->terms_kept = hs[0];
-    stats->terms_screened = hs[1];
+    stats->terms_screened = hs[1] - hs[3];  // the norm screen's drops; the model's are below
     stats->sources_truncated = ntr;
-    stats->skipped_bound = hd;
+    stats->skipped_bound = hd[0];
     stats->pairs = P;
     stats->terms_issued = hs[0];
+    stats->terms_learned_skipped = hs[3];
+    stats->learned_skipped_bound = hd[1];
   }
+  if (P > 0) {
+    screen_kernel<1><<<gboxes, 32 * wpb, ssm, s>>>(a);
+    MRA_CUDA_TRY(cudaGetLastError());
+  }
+  *P_out = P;
+  return MRA_OK;
+}
+
+int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts &o,
+              mra_tree_view &out, void *ws, size_t ws_bytes, mra_apply_stats *stats,
+              cudaStream_t s) {
+  const int k = op.k, k3 = k * k * k;
+  const int64_t n_in = in.n;
+  const int64_t Pmax = apply_max_records(op, o, n_in);
+  Layout L = make_layout(n_in, Pmax);
+  if (ws_bytes < L.total)
+    return fail(MRA_ERR_CAPACITY, "mra_apply: workspace of %zu bytes < %zu needed", ws_bytes, L.total);
+  WsPtrs W = carve(L, ws);
+  char *w = (char *)ws;
+  uint64_t *rkey = W.rkey, *skey = W.skey, *rmask = W.rmask, *dkey = W.dkey;
+  int *rsrc = W.rsrc, *rl = W.rl, *pin = W.pin, *pout = W.pout, *head = W.head, *did = W.did;
+  int64_t *seg = W.seg, *ndest = W.ndest;
+  void *tmp = W.tmp;
+  size_t tmpb = W.tmpb;
+  if (n_in == 0) {
+    out.n = 0;
+    if (stats) *stats = mra_apply_stats{};
+    return MRA_OK;
+  }
+  int64_t P = 0;
+  int rc0 = screen_run(op, in, o, W, Pmax, stats, &P, s);
+  if (rc0 != MRA_OK) return rc0;
   if (P == 0) {
     out.n = 0;
     return MRA_OK;
   }
-  screen_kernel<1><<<gboxes, 32 * wpb, 0, s>>>(a);
-  MRA_CUDA_TRY(cudaGetLastError());
   // sort record indices on the destination key
   {
     unsigned g = (unsigned)((P + 255) / 256);
@@ -601,6 +691,166 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
   return rc;
 }
 
+
+// ---------------------------------------------------------------- training-data logging
+namespace {
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ bool sampled(uint64_t seed, int64_t p, int m, uint64_t thr) {
+  return mix64(seed + 0x9E3779B97F4A7C15ull * (uint64_t)(p * 128 + m + 1)) <= thr;
+}
+
+__global__ void sample_count_kernel(int64_t P, const uint64_t *rmask, uint64_t seed, uint64_t thr,
+                                    int64_t *cnt) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  int64_t c = 0;
+  for (int w = 0; w < 2; ++w) {
+    uint64_t bits = rmask[2 * p + w];
+    while (bits) {
+      int m = w * 64 + __ffsll((long long)bits) - 1;
+      bits &= bits - 1;
+      c += sampled(seed, p, m, thr) ? 1 : 0;
+    }
+  }
+  cnt[p] = c;
+}
+
+// term list, stashed as ints in the feature rows until term_norm_kernel replaces them
+__global__ void sample_write_kernel(int64_t P, const uint64_t *rmask, const int *rsrc, const int *rl,
+                                    uint64_t seed, uint64_t thr, const int64_t *off, int64_t max_terms,
+                                    float *features) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  int64_t idx = off[p];
+  for (int w = 0; w < 2; ++w) {
+    uint64_t bits = rmask[2 * p + w];
+    while (bits) {
+      int m = w * 64 + __ffsll((long long)bits) - 1;
+      bits &= bits - 1;
+      if (!sampled(seed, p, m, thr)) continue;
+      if (idx < max_terms) {
+        int *row = (int *)(features + idx * 4);
+        row[0] = rsrc[p];
+        row[1] = rl[p];
+        row[2] = m;
+      }
+      ++idx;
+    }
+  }
+}
+
+// One CTA per logged term: its features and log10 ||c_m (Rx x Ry x Rz) s_b||_F in FP64.
+__global__ void term_norm_kernel(int k, const double *c, const double *t, const double *R, const int *Dlev,
+                                 const int64_t *level_off, const uint64_t *keys, const double *coeffs,
+                                 const double *snorm, float *features, float *log_norms) {
+  extern __shared__ double sm[];
+  __shared__ double red[32];
+  __shared__ int info[3];
+  const int k2 = k * k, k3 = k2 * k;
+  double *s = sm, *t1 = s + k3, *t2 = t1 + k3, *Rs = t2 + k3;
+  const int64_t q = blockIdx.x;
+  if (threadIdx.x < 3) info[threadIdx.x] = ((const int *)(features + q * 4))[threadIdx.x];
+  __syncthreads();
+  const int src = info[0], lp = info[1], m = info[2];
+  const int lx = (lp & 255) - 128, ly = ((lp >> 8) & 255) - 128, lz = ((lp >> 16) & 255) - 128;
+  const int n = key_level(keys[src]);
+  const int Dop = Dlev[n], nl = 2 * Dop + 1;
+  const double *Rlev = R + level_off[n] * k2;
+  const double *Rx = Rlev + ((int64_t)m * nl + lx + Dop) * k2;
+  const double *Ry = Rlev + ((int64_t)m * nl + ly + Dop) * k2;
+  const double *Rz = Rlev + ((int64_t)m * nl + lz + Dop) * k2;
+  for (int e = threadIdx.x; e < k3; e += blockDim.x) s[e] = coeffs[(int64_t)src * k3 + e];
+  for (int e = threadIdx.x; e < k2; e += blockDim.x) {
+    Rs[e] = Rx[e];
+    Rs[k2 + e] = Ry[e];
+    Rs[2 * k2 + e] = Rz[e];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < k3; e += blockDim.x) {
+    int ix = e / k2, rest = e % k2;
+    double v = 0.0;
+    for (int j = 0; j < k; ++j) v += Rs[ix * k + j] * s[j * k2 + rest];
+    t1[e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < k3; e += blockDim.x) {
+    int ix = e / k2, iy = (e / k) % k, jz = e % k;
+    double v = 0.0;
+    for (int j = 0; j < k; ++j) v += Rs[k2 + iy * k + j] * t1[ix * k2 + j * k + jz];
+    t2[e] = v;
+  }
+  __syncthreads();
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < k3; e += blockDim.x) {
+    int base = (e / k) * k, iz = e % k;
+    double v = 0.0;
+    for (int j = 0; j < k; ++j) v += Rs[2 * k2 + iz * k + j] * t2[base + j];
+    acc += v * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    double norm = fabs(c[m]) * sqrt(tot);
+    log_norms[q] = (float)log10(fmax(norm, 1e-300));
+    features[q * 4 + 0] = (float)n;
+    features[q * 4 + 1] = sqrtf((float)(lx * lx + ly * ly + lz * lz));
+    features[q * 4 + 2] = (float)log10(t[m]);
+    features[q * 4 + 3] = (float)log10(fmax(snorm[src], 1e-300));
+  }
+}
+
+}  // namespace
+
+int log_terms_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts &o, int64_t max_terms,
+                  uint64_t seed, float *features, float *log_norms, int64_t *n_logged, void *ws,
+                  size_t ws_bytes, cudaStream_t s) {
+  *n_logged = 0;
+  const int64_t n_in = in.n;
+  if (n_in == 0 || max_terms <= 0) return MRA_OK;
+  const int64_t Pmax = apply_max_records(op, o, n_in);
+  Layout L = make_layout(n_in, Pmax);
+  if (ws_bytes < L.total)
+    return fail(MRA_ERR_CAPACITY, "mra_log_terms: workspace of %zu bytes < %zu needed", ws_bytes, L.total);
+  WsPtrs W = carve(L, ws);
+  mra_apply_stats st{};
+  int64_t P = 0;
+  int rc = screen_run(op, in, o, W, Pmax, &st, &P, s);
+  if (rc != MRA_OK || P == 0) return rc;
+  const double frac = (double)max_terms / (double)(st.terms_kept > 0 ? st.terms_kept : 1);
+  const uint64_t thr = frac >= 1.0 ? ~0ull : (uint64_t)(frac * 18446744073709551615.0);
+  int64_t *cnt = (int64_t *)W.rkey, *off = (int64_t *)W.skey;  // free until a sort runs
+  unsigned g = (unsigned)((P + 255) / 256);
+  sample_count_kernel<<<g, 256, 0, s>>>(P, W.rmask, seed, thr, cnt);
+  MRA_CUDA_TRY(cudaGetLastError());
+  MRA_CUDA_TRY(cub::DeviceScan::ExclusiveSum(W.tmp, W.tmpb, cnt, off, (int)P, s));
+  int64_t last[2];
+  MRA_CUDA_TRY(cudaMemcpyAsync(&last[0], off + P - 1, 8, cudaMemcpyDeviceToHost, s));
+  MRA_CUDA_TRY(cudaMemcpyAsync(&last[1], cnt + P - 1, 8, cudaMemcpyDeviceToHost, s));
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  const int64_t total = last[0] + last[1];
+  const int64_t nlog = total < max_terms ? total : max_terms;
+  if (nlog == 0) return MRA_OK;
+  sample_write_kernel<<<g, 256, 0, s>>>(P, W.rmask, W.rsrc, W.rl, seed, thr, off, max_terms, features);
+  MRA_CUDA_TRY(cudaGetLastError());
+  const int k = op.k;
+  size_t smem = (size_t)(3 * k * k * k + 3 * k * k) * sizeof(double);
+  if (smem > 48 * 1024)
+    MRA_CUDA_TRY(cudaFuncSetAttribute(term_norm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  term_norm_kernel<<<(unsigned)nlog, 256, smem, s>>>(k, op.d_c, op.d_t, op.d_R, op.d_D, op.d_level_off, in.keys,
+                                                      in.coeffs, W.snorm, features, log_norms);
+  MRA_CUDA_TRY(cudaGetLastError());
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  *n_logged = nlog;
+  return MRA_OK;
+}
 
 // ---------------------------------------------------------------- norm / compare hosts
 

@@ -29,13 +29,16 @@ PREC_FP64 = 0
 PREC_SPLIT_BF16 = 1
 SCREEN_NONE = 0
 SCREEN_NORM = 1
+SCREEN_LEARNED = 2
+MLP_PARAMS = 4555
 STENCIL_SHELLS = 0
 STENCIL_NEAREST = 1
 
 EXPORTED = [
     "mra_last_error", "mra_version", "mra_project", "mra_operator_create", "mra_operator_fit",
     "mra_operator_info", "mra_operator_block", "mra_operator_free", "mra_apply_workspace_size",
-    "mra_apply", "mra_norm", "mra_norm_noalloc", "mra_compare",
+    "mra_apply", "mra_norm", "mra_norm_noalloc", "mra_compare", "mra_log_terms", "mra_mlp_init",
+    "mra_mlp_standardize", "mra_mlp_forward", "mra_mlp_workspace_size", "mra_mlp_grad", "mra_mlp_train",
 ]
 NOALLOC_MAX_BOXES = 1 << 20
 
@@ -59,14 +62,16 @@ class TreeView(ctypes.Structure):
 
 class ApplyOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("pieces", ctypes.c_int), ("screen", ctypes.c_int),
-                ("tau", ctypes.c_double), ("stencil", ctypes.c_int), ("max_disp", ctypes.c_int)]
+                ("tau", ctypes.c_double), ("stencil", ctypes.c_int), ("max_disp", ctypes.c_int),
+                ("mlp", ctypes.c_void_p), ("delta", ctypes.c_double)]
 
 
 class ApplyStats(ctypes.Structure):
     _fields_ = [("n_in", ctypes.c_int64), ("n_out", ctypes.c_int64), ("pairs", ctypes.c_int64),
                 ("terms_kept", ctypes.c_int64), ("terms_screened", ctypes.c_int64),
                 ("terms_issued", ctypes.c_int64), ("sources_truncated", ctypes.c_int64),
-                ("skipped_bound", ctypes.c_double), ("kernel_ms", ctypes.c_double)]
+                ("skipped_bound", ctypes.c_double), ("kernel_ms", ctypes.c_double),
+                ("terms_learned_skipped", ctypes.c_int64), ("learned_skipped_bound", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -116,6 +121,16 @@ def load(build_if_stale: bool = True):
         lib.mra_norm.argtypes = [P(TreeView), vp, P(d), vp]
         lib.mra_norm_noalloc.argtypes = [P(TreeView), vp, P(d), vp]
         lib.mra_compare.argtypes = [P(TreeView), P(TreeView), P(CompareResult), vp]
+        u64, i64 = ctypes.c_uint64, ctypes.c_int64
+        lib.mra_log_terms.argtypes = [vp, P(TreeView), P(ApplyOpts), i64, u64, vp, vp, P(i64), vp,
+                                      ctypes.c_size_t, vp]
+        lib.mra_mlp_init.argtypes = [vp, u64, vp]
+        lib.mra_mlp_standardize.argtypes = [vp, vp, vp, i64, vp]
+        lib.mra_mlp_forward.argtypes = [vp, vp, i64, vp, vp]
+        lib.mra_mlp_workspace_size.argtypes = [i64, P(ctypes.c_size_t)]
+        lib.mra_mlp_grad.argtypes = [vp, vp, vp, i64, vp, P(d), vp, ctypes.c_size_t, vp]
+        lib.mra_mlp_train.argtypes = [vp, vp, vp, vp, i64, i, i, i, ctypes.c_float, u64, P(d), vp,
+                                      ctypes.c_size_t, vp]
         _lib = lib
         return lib
 
@@ -244,9 +259,13 @@ class Operator:
             pass
 
 
-def make_opts(precision=PREC_FP64, pieces=2, screen=SCREEN_NONE, tau=0.0, stencil=STENCIL_NEAREST,
-              max_disp=1) -> ApplyOpts:
-    return ApplyOpts(precision, pieces, screen, tau, stencil, max_disp)
+def make_opts(precision=PREC_FP64, pieces=3, screen=SCREEN_NONE, tau=0.0, stencil=STENCIL_NEAREST,
+              max_disp=1, mlp: torch.Tensor | None = None, delta: float = 0.0) -> ApplyOpts:
+    o = ApplyOpts(precision, pieces, screen, tau, stencil, max_disp, None, delta)
+    if mlp is not None:
+        o.mlp = mlp.data_ptr()
+        o._mlp_ref = mlp  # keep the tensor alive with the options
+    return o
 
 
 def workspace_size(op: Operator, tree: Tree, opts: ApplyOpts) -> int:
@@ -317,3 +336,64 @@ def compare(test: Tree, ref: Tree, stream=None) -> dict:
     vt, vr = test.view(), ref.view()
     _check(load().mra_compare(ctypes.byref(vt), ctypes.byref(vr), ctypes.byref(res), _stream(stream)))
     return res.as_dict()
+
+
+# --------------------------------------------------------------------------- learned screen
+
+def _vp(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def log_terms(op: Operator, tree: Tree, opts: ApplyOpts, max_terms: int, seed: int = 0, stream=None):
+    """mra_log_terms: (features [n,4] float32, log10 term norms [n] float32) on the device."""
+    dev = tree.keys.device
+    feats = torch.empty((max(max_terms, 1), 4), dtype=torch.float32, device=dev)
+    targ = torch.empty(max(max_terms, 1), dtype=torch.float32, device=dev)
+    ws = torch.empty(max(workspace_size(op, tree, opts), 1), dtype=torch.uint8, device=dev)
+    n = ctypes.c_int64()
+    v = tree.view()
+    _check(load().mra_log_terms(op.handle, ctypes.byref(v), ctypes.byref(opts), int(max_terms), int(seed),
+                                _vp(feats), _vp(targ), ctypes.byref(n), _vp(ws), ws.numel(), _stream(stream)))
+    return feats[: n.value], targ[: n.value]
+
+
+def mlp_init(seed: int = 0, device="cuda", stream=None) -> torch.Tensor:
+    p = torch.empty(MLP_PARAMS, dtype=torch.float32, device=device)
+    _check(load().mra_mlp_init(_vp(p), int(seed), _stream(stream)))
+    return p
+
+
+def mlp_standardize(params, features, targets, stream=None):
+    _check(load().mra_mlp_standardize(_vp(params), _vp(features), _vp(targets), features.shape[0], _stream(stream)))
+
+
+def mlp_forward(params, features, stream=None) -> torch.Tensor:
+    out = torch.empty(features.shape[0], dtype=torch.float32, device=features.device)
+    _check(load().mra_mlp_forward(_vp(params), _vp(features), features.shape[0], _vp(out), _stream(stream)))
+    return out
+
+
+def _mlp_ws(n, device):
+    b = ctypes.c_size_t()
+    _check(load().mra_mlp_workspace_size(int(n), ctypes.byref(b)))
+    return torch.empty(b.value, dtype=torch.uint8, device=device)
+
+
+def mlp_grad(params, features, targets, stream=None):
+    """Full-batch gradient (first 4545 entries meaningful) and loss."""
+    g = torch.zeros(MLP_PARAMS, dtype=torch.float32, device=params.device)
+    ws = _mlp_ws(features.shape[0], params.device)
+    loss = ctypes.c_double()
+    _check(load().mra_mlp_grad(_vp(params), _vp(features), _vp(targets), features.shape[0], _vp(g),
+                               ctypes.byref(loss), _vp(ws), ws.numel(), _stream(stream)))
+    return g, loss.value
+
+
+def mlp_train(params, adam_state, features, targets, batch: int, steps: int, step0: int, lr: float,
+              seed: int = 0, stream=None) -> float:
+    ws = _mlp_ws(batch, params.device)
+    loss = ctypes.c_double()
+    _check(load().mra_mlp_train(_vp(params), _vp(adam_state), _vp(features), _vp(targets), features.shape[0],
+                                int(batch), int(steps), int(step0), float(lr), int(seed), ctypes.byref(loss),
+                                _vp(ws), ws.numel(), _stream(stream)))
+    return loss.value

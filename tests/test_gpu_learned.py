@@ -1,0 +1,120 @@
+"""The learned screen: hand-written CUDA forward/backward/Adam kernels checked against the
+oracle's FP64 network, logged training data checked against the oracle's own term norms,
+and the trained screen's gain and error on a held-out function."""
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle.mlp as OM
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mra():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1507_01888_gb300 import mra as m
+    m.load()
+    return m
+
+
+def random_params(rng):
+    p = np.concatenate([rng.standard_normal(OM.NP) * 0.3, [1.0, 0.5, 0.0, -2.0, 3.0, 0.6, 2.5, 1.5, -4.0, 2.0]])
+    return p.astype(np.float32)
+
+
+def test_mlp_forward_and_gradient_match_oracle(mra):
+    import torch
+    rng = np.random.default_rng(1)
+    p = random_params(rng)
+    x = (rng.standard_normal((1000, 4)) * [3, 0.5, 2, 2] + [6, 1, 0, -2]).astype(np.float32)
+    y = (rng.standard_normal(1000) * 2 - 5).astype(np.float32)
+    pt, xt, yt = (torch.from_numpy(a).cuda() for a in (p, x, y))
+    pred = mra.mlp_forward(pt, xt).cpu().numpy()
+    ref = OM.forward(p.astype(np.float64), x.astype(np.float64))
+    assert np.abs(pred - ref).max() <= 1e-5 * np.abs(ref).max()
+    g, loss = mra.mlp_grad(pt, xt, yt)
+    Lr, gr = OM.loss_and_grad(p.astype(np.float64), x.astype(np.float64), y.astype(np.float64))
+    assert loss == pytest.approx(Lr, rel=1e-5)
+    g = g.cpu().numpy()[: OM.NP]
+    assert np.abs(g - gr).max() <= 2e-5 * np.abs(gr).max()
+
+
+def test_logged_terms_match_oracle_exhaustively(mra):
+    """Every kept term of a tiny tree: the (features, log10 norm) multiset equals the oracle's."""
+    k, L, lev, M = 4, 16.0, 2, 6
+    keys, coeffs = W.random_tree_coeffs(12, k, lev, seed=31)
+    coeffs *= np.exp(np.random.default_rng(5).uniform(-6, 3, size=(len(keys), 1, 1, 1)))
+    op = mra.Operator(1, M, k, L, 0, lev, max_disp=1, mu=1.0, fit_eps=1e-6)
+    r_lo, r_hi = O.kernel_range(1, 1.0, L, 1e-6)
+    _, _, _, c, t = O.fit_search(1.0, M, r_lo, r_hi)
+    tau = 1e-3
+    opts = mra.make_opts(screen=mra.SCREEN_NORM, tau=tau, stencil=mra.STENCIL_NEAREST)
+    f, y = mra.log_terms(op, mra.Tree.from_host(keys, coeffs, L), opts, max_terms=100000, seed=3)
+    got = np.concatenate([f.cpu().numpy(), y.cpu().numpy()[:, None]], 1)
+    h = 2 * L / 2 ** lev
+    n_, x_, y_, z_ = O.split_keys(keys)
+    R = {(m, l): O.block(k, h, t[m] * h * h, l) for m in range(M) for l in (-1, 0, 1)}
+    rows = []
+    for b in range(len(keys)):
+        sn = np.linalg.norm(coeffs[b])
+        for lx in (-1, 0, 1):
+            for ly in (-1, 0, 1):
+                for lz in (-1, 0, 1):
+                    X, Y, Z = x_[b] + lx, y_[b] + ly, z_[b] + lz
+                    if not (0 <= X < 4 and 0 <= Y < 4 and 0 <= Z < 4):
+                        continue
+                    for m in range(M):
+                        B = abs(c[m]) * np.linalg.norm(R[m, lx]) * np.linalg.norm(R[m, ly]) * \
+                            np.linalg.norm(R[m, lz]) * sn
+                        if B < tau:
+                            continue
+                        term = c[m] * np.einsum("ai,bj,ck,ijk->abc", R[m, lx], R[m, ly], R[m, lz], coeffs[b])
+                        rows.append([lev, np.sqrt(lx * lx + ly * ly + lz * lz), np.log10(t[m]), np.log10(sn),
+                                     np.log10(np.linalg.norm(term))])
+    ref = np.array(rows)
+    assert len(got) == len(ref)
+    order = lambda a: np.lexsort(np.round(a[:, ::-1], 3).T)
+    g_s, r_s = got[order(got)], ref[order(ref)]
+    assert np.abs(g_s[:, :4] - r_s[:, :4]).max() < 1e-5
+    assert np.abs(g_s[:, 4] - r_s[:, 4]).max() < 1e-5
+
+
+def test_learned_screen_training_gain_and_error(mra):
+    """Train on terms logged from plain applies of several functions, calibrate the margin on
+    held-out terms, then apply with the learned screen to an unseen function: it drops terms the
+    norm screen kept, and the change of the result stays below the norm bound of what it drops."""
+    import torch
+    from paper_1507_01888_gb300 import learned
+    k, L, thresh, tau = 6, 32.0, 1e-4, 1e-6
+    funcs = [W.gaussian_sum(3, 1.0, 300.0, seed=700 + i, centre_box=15.0) for i in range(5)]
+    trees = [mra.project(f, k, L, thresh=thresh, init_level=2, max_level=10) for f in funcs]
+    op = mra.Operator(1, 30, k, L, 1, 10, max_disp=1, mu=1.0, fit_eps=1e-6)
+    base = mra.make_opts(screen=mra.SCREEN_NORM, tau=tau, stencil=mra.STENCIL_SHELLS, max_disp=1)
+    model, info = learned.train_screen(op, trees[:4], base, terms_per_tree=20000, steps=1500, batch=1024,
+                                       lr=3e-3, seed=11)
+    assert info["final_loss"] < 0.2 * info["initial_loss"]
+    test_tree = trees[4]
+    plain, st_plain = mra.apply(op, test_tree, base)
+    lopts = mra.make_opts(screen=mra.SCREEN_LEARNED, tau=tau, stencil=mra.STENCIL_SHELLS, max_disp=1,
+                          mlp=model, delta=info["delta"])
+    out, st = mra.apply(op, test_tree, lopts)
+    assert st["terms_learned_skipped"] > 0.05 * st_plain["terms_kept"]
+    assert st["terms_kept"] + st["terms_learned_skipped"] == st_plain["terms_kept"]
+    cmp = mra.compare(out, plain)
+    assert cmp["diff_norm"] <= st["learned_skipped_bound"] * (1 + 1e-9)
+    # judged by the oracle: the learned-screened result against the oracle's plain apply
+    ok, oc = test_tree.host()
+    r_lo, r_hi = O.kernel_range(1, 1.0, L, 1e-6)
+    _, _, _, c, t = O.fit_search(1.0, 30, r_lo, r_hi)
+    ref = O.apply(ok, oc, c, t, L, stencil=0, max_disp=1, tau=tau)
+    gk, gc = out.host()
+    common = np.isin(ref.keys, gk)
+    pos = np.searchsorted(gk, ref.keys[common])
+    diff2 = ((gc[pos] - ref.coeffs[common]) ** 2).sum() + (ref.coeffs[~common] ** 2).sum()
+    rel = np.sqrt(diff2 / (ref.coeffs ** 2).sum())
+    assert rel <= st["learned_skipped_bound"] / np.sqrt((ref.coeffs ** 2).sum()) + 1e-10
+    print(f"learned screen: dropped {st['terms_learned_skipped']} of {st_plain['terms_kept']} kept terms, "
+          f"rel. change {rel:.2e}")

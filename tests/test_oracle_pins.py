@@ -352,3 +352,25 @@ def test_screen_and_shells_on_adaptive_tree():
     assert r2.terms < r1.terms
     assert r1.terms > 0 and r1.screened > 0
     assert np.all(r1.bound > 0)
+
+
+# ----------------------------------------------------------------- learned-screen network (oracle side)
+
+def test_oracle_mlp_gradient_matches_finite_differences():
+    import oracle.mlp as M
+    rng = np.random.default_rng(0)
+    p = np.concatenate([rng.standard_normal(M.NP) * 0.3, [0.1, -0.2, 0.3, 0.0, 1.5, 0.7, 2.0, 1.1, -3.0, 2.0]])
+    x = rng.standard_normal((40, 4))
+    y = rng.standard_normal(40)
+    _, g = M.loss_and_grad(p, x, y)
+    idx = rng.choice(M.NP, 40, replace=False)
+    h = 1e-6
+    for i in idx:
+        e = np.zeros(M.NALL); e[i] = h
+        fd = (M.loss_and_grad(p + e, x, y)[0] - M.loss_and_grad(p - e, x, y)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-7 * max(1.0, abs(g[i]))
+    # forward is the documented composition
+    W1, b1, W2, b2, W3, b3, xm, xs, ym, ys = M.unpack(p)
+    z = (x[0] - xm) / xs
+    o = W3 @ np.tanh(W2 @ np.tanh(W1 @ z + b1) + b2) + b3
+    assert M.forward(p, x[:1])[0] == pytest.approx(o * ys + ym, rel=1e-14)
