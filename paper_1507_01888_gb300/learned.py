@@ -3,9 +3,12 @@
 Terms kept by the norm screen are logged from plain applies of several functions
 (mra_log_terms: features and the FP64 log10 norm of each sampled term), the
 network is standardised on them and trained with the library's Adam kernel, and
-the safety margin delta is set on held-out terms so that no held-out term whose
-true norm is at least tau would have been dropped:
-    delta = max over held-out rows of (true log10 norm - prediction) + margin.
+the safety margin delta is set on held-out terms from the residuals
+(true log10 norm - prediction):
+    delta = quantile(residuals, q) + margin.
+q = 1 (the default) takes the largest held-out residual, so that no held-out term
+whose true norm is at least tau would have been dropped; q < 1 trades accuracy
+for skipped terms (the apply then reports the norm bound of what it dropped).
 """
 from __future__ import annotations
 
@@ -24,7 +27,7 @@ def log_training_data(op, trees, opts, terms_per_tree: int, seed: int = 0):
 
 
 def train_screen(op, trees, opts, terms_per_tree: int = 20000, steps: int = 2000, batch: int = 1024,
-                 lr: float = 3e-3, seed: int = 0, margin: float = 0.1):
+                 lr: float = 3e-3, seed: int = 0, margin: float = 0.1, quantile: float = 1.0):
     """Returns (model parameters on the device, info dict)."""
     X, Y = log_training_data(op, trees, opts, terms_per_tree, seed)
     n = X.shape[0]
@@ -39,8 +42,9 @@ def train_screen(op, trees, opts, terms_per_tree: int = 20000, steps: int = 2000
     adam = torch.zeros(2 * mra.MLP_PARAMS, dtype=torch.float32, device=X.device)
     mra.mlp_train(params, adam, Xt, Yt, batch, steps, 0, lr, seed)
     _, loss1 = mra.mlp_grad(params, Xt, Yt)
-    pred_v = mra.mlp_forward(params, Xv)
-    delta = float((Yv - pred_v).max().item()) + margin
+    resid = Yv - mra.mlp_forward(params, Xv)
+    delta = float(torch.quantile(resid, quantile).item()) + margin
     info = {"initial_loss": loss0, "final_loss": loss1, "delta": delta, "n_train": int(Xt.shape[0]),
-            "n_val": int(Xv.shape[0]), "steps": steps}
+            "n_val": int(Xv.shape[0]), "steps": steps, "quantile": quantile,
+            "resid_max": float(resid.max().item()), "val_features": Xv, "val_targets": Yv}
     return params, info
