@@ -69,6 +69,7 @@ extern "C" {
 #define MRA_MAX_K 16
 #define MRA_MAX_TERMS 128
 #define MRA_NOALLOC_MAX_BOXES (1 << 20) /* largest tree mra_norm_noalloc accepts */
+#define MRA_MAX_FUNCS 2048 /* functions in one mra_apply_batched call */
 #define MRA_MLP_PARAMS 4555 /* floats of a learned-screen model (see mra_mlp_init) */
 
 /* ---- data types ----------------------------------------------------------- */
@@ -256,6 +257,20 @@ int mra_mlp_grad(const float *params, const float *features, const float *target
 int mra_mlp_train(float *params, float *adam_state, const float *features, const float *targets,
                   int64_t n, int batch, int steps, int step0, float lr, uint64_t seed,
                   double *final_loss, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Apply one operator to nfunc functions in one pass: every kernel of mra_apply runs once
+ * over all of them (the tensor-core tiles may mix functions, which share the operator's
+ * blocks).  in: one tree view holding the functions' boxes back to back, function f at
+ * [in_offsets[f], in_offsets[f+1]) (host array of nfunc+1, in_offsets[0] = 0,
+ * in_offsets[nfunc] = in->n), each function's keys sorted.  out: one tree view; on return
+ * function f's destination boxes are [out_offsets[f], out_offsets[f+1]) (host array of
+ * nfunc+1), keys sorted within each function.  Levels above 15 are not supported here
+ * (MRA_ERR_UNSUPPORTED); nfunc <= MRA_MAX_FUNCS.  Same workspace size query as mra_apply
+ * with in; same statistics, summed over the functions.  The paper applies each function
+ * separately; batching is this library's. */
+int mra_apply_batched(const mra_operator *op, int nfunc, const mra_tree_view *in, const int64_t *in_offsets,
+                      const mra_apply_opts *opts, mra_tree_view *out, int64_t *out_offsets, void *workspace,
+                      size_t workspace_bytes, mra_apply_stats *stats, void *stream);
 
 /* Per-box Frobenius norms (device array of tree->n doubles, may be NULL) and
  * the total L2 norm (host double, may be NULL).  Deterministic reduction. */

@@ -516,6 +516,28 @@ int mra_apply(const mra_operator *h, const mra_tree_view *in, const mra_apply_op
   return apply_run(*op, *in, *o, *out, workspace, workspace_bytes, stats, (cudaStream_t)stream);
 }
 
+int mra_apply_batched(const mra_operator *h, int nfunc, const mra_tree_view *in, const int64_t *in_offsets,
+                      const mra_apply_opts *o, mra_tree_view *out, int64_t *out_offsets, void *workspace,
+                      size_t workspace_bytes, mra_apply_stats *stats, void *stream) {
+  const Operator *op = reinterpret_cast<const Operator *>(h);
+  int rc = check_opts(op, in, o);
+  if (rc) return rc;
+  rc = check_view(out, "mra_apply_batched(out)", false);
+  if (rc) return rc;
+  if (nfunc < 1 || nfunc > MRA_MAX_FUNCS) return fail(MRA_ERR_ARG, "mra_apply_batched: nfunc=%d", nfunc);
+  if (!in_offsets || !out_offsets) return fail(MRA_ERR_ARG, "mra_apply_batched: NULL offsets");
+  if (in_offsets[0] != 0 || in_offsets[nfunc] != in->n)
+    return fail(MRA_ERR_ARG, "mra_apply_batched: offsets must run from 0 to in->n");
+  for (int f = 0; f < nfunc; ++f)
+    if (in_offsets[f + 1] < in_offsets[f]) return fail(MRA_ERR_ARG, "mra_apply_batched: offsets decrease");
+  if (out->k != op->k) return fail(MRA_ERR_ARG, "mra_apply_batched: output k differs");
+  if (in->n > 0 && !workspace) return fail(MRA_ERR_ARG, "mra_apply_batched: NULL workspace");
+  if (in->n >= (1LL << 31)) return fail(MRA_ERR_ARG, "mra_apply_batched: more than 2^31 source boxes");
+  out->L = op->L;
+  return apply_run(*op, *in, *o, *out, workspace, workspace_bytes, stats, (cudaStream_t)stream, nfunc, in_offsets,
+                   out_offsets);
+}
+
 int mra_log_terms(const mra_operator *h, const mra_tree_view *in, const mra_apply_opts *o, int64_t max_terms,
                   uint64_t seed, float *features, float *log_norms, int64_t *n_logged, void *workspace,
                   size_t workspace_bytes, void *stream) {

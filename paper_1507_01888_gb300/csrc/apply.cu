@@ -90,7 +90,20 @@ struct ScreenArgs {
   float learned_cut;          // log10(tau) - delta
   int64_t *box_learned;
   double *box_lbound;
+  // several functions in one apply: boxes [fn_off[f], fn_off[f+1]) belong to function f,
+  // and records sort on (f, level, x, y, z) packed as f<<53 | n<<48 | x<<32 | y<<16 | z
+  int nfunc;
+  const int64_t *fn_off;
 };
+
+// Sort key of a destination box of function f in a batched apply (levels <= 15).
+__device__ __forceinline__ uint64_t batched_key(int f, int n, int64_t x, int64_t y, int64_t z) {
+  return ((uint64_t)f << 53) | ((uint64_t)n << 48) | ((uint64_t)x << 32) | ((uint64_t)y << 16) | (uint64_t)z;
+}
+__device__ __forceinline__ uint64_t public_key(uint64_t bk) {
+  return make_key((int)((bk >> 48) & 31), (int64_t)((bk >> 32) & 0xFFFF), (int64_t)((bk >> 16) & 0xFFFF),
+                  (int64_t)(bk & 0xFFFF));
+}
 
 template <int PASS>
 __global__ void screen_kernel(ScreenArgs a) {
@@ -109,6 +122,19 @@ __global__ void screen_kernel(ScreenArgs a) {
   if (a.level_off[n] < 0) {
     if (lane == 0) atomicExch(a.err, 1);  // level outside the operator's table
     return;
+  }
+  int func = 0;
+  if (a.nfunc > 1) {
+    if (n > 15) {
+      if (lane == 0) atomicExch(a.err, 3);  // batched sort keys hold levels <= 15
+      return;
+    }
+    int lo = 0, hi = a.nfunc - 1;  // last f with fn_off[f] <= b
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (a.fn_off[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    func = lo;
   }
   int Dop = a.Dlev[n];
   int D = a.stencil == MRA_STENCIL_NEAREST ? 1 : a.dmax;
@@ -171,7 +197,8 @@ __global__ void screen_kernel(ScreenArgs a) {
           kept += pk;
           screened += a.M - pk;
           if (PASS == 1 && lane == 0) {
-            a.rec_key[wpos] = make_key(n, x + lx, y + ly, z + lz);
+            a.rec_key[wpos] = a.nfunc > 1 ? batched_key(func, n, x + lx, y + ly, z + lz)
+                                          : make_key(n, x + lx, y + ly, z + lz);
             a.rec_src[wpos] = (int)b;
             a.rec_l[wpos] = (lx + 128) | ((ly + 128) << 8) | ((lz + 128) << 16);
             a.rec_mask[2 * wpos] = mask[0];
@@ -203,17 +230,30 @@ __global__ void head_flags_kernel(int64_t P, const uint64_t *skey, int *head) {
 
 __global__ void segments_kernel(int64_t P, const uint64_t *skey, const int *head,
                                 const int *dest_id /*inclusive scan*/, uint64_t *dest_key,
-                                int64_t *seg, int64_t *n_dest) {
+                                int64_t *seg, int64_t *n_dest, int batched, int *dest_func) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P) return;
   if (head[i]) {
     int64_t d = dest_id[i] - 1;
-    dest_key[d] = skey[i];
+    dest_key[d] = batched ? public_key(skey[i]) : skey[i];
+    if (batched) dest_func[d] = (int)(skey[i] >> 53);
     seg[d] = i;
   }
   if (i == P - 1) {
     *n_dest = dest_id[i];
     seg[dest_id[i]] = P;
+  }
+}
+
+// offsets[f] = first destination of function f (dest_func is sorted), offsets[nfunc] = n
+__global__ void func_offsets_kernel(int64_t n, const int *dest_func, int nfunc, int64_t *offsets) {
+  for (int f = threadIdx.x; f <= nfunc; f += blockDim.x) {
+    int64_t lo = 0, hi = n;  // first index with dest_func >= f
+    while (lo < hi) {
+      int64_t mid = (lo + hi) >> 1;
+      if (dest_func[mid] < f) lo = mid + 1; else hi = mid;
+    }
+    offsets[f] = lo;
   }
 }
 
@@ -392,7 +432,7 @@ int64_t apply_max_records(const Operator &op, const mra_apply_opts &o, int64_t n
 //   CUB temp storage (max over scan / sort / reduce needs)
 struct Layout {
   size_t snorm, dstop, cnt, off, kept, screened, skipped, trunc, learned, lbound;
-  size_t rkey, rsrc, rl, rmask, skey, pin, pout, head, did, dkey, seg, ndest, split, tmp;
+  size_t rkey, rsrc, rl, rmask, skey, pin, pout, head, did, dkey, seg, ndest, dfunc, fnoff, split, tmp;
   size_t split_bytes, tmp_bytes, total;
 };
 
@@ -427,6 +467,8 @@ static Layout make_layout(int64_t n_in, int64_t P) {
   L.dkey = take(np * 8);
   L.seg = take((np + 1) * 8);
   L.ndest = take(8);
+  L.dfunc = take(np * 4);
+  L.fnoff = take((MRA_MAX_FUNCS + 1) * 8);
   L.split_bytes = split_workspace_bytes(np);
   L.split = take(L.split_bytes);
   // CUB temporary storage: the largest of the calls below
@@ -459,6 +501,8 @@ struct WsPtrs {
   uint64_t *rkey, *skey, *rmask, *dkey;
   int *rsrc, *rl, *pin, *pout, *head, *did;
   int64_t *seg, *ndest;
+  int *dfunc;
+  int64_t *fnoff;
   void *tmp;
   size_t tmpb;
 };
@@ -488,6 +532,8 @@ static WsPtrs carve(const Layout &L, void *ws) {
   p.dkey = (uint64_t *)(w + L.dkey);
   p.seg = (int64_t *)(w + L.seg);
   p.ndest = (int64_t *)(w + L.ndest);
+  p.dfunc = (int *)(w + L.dfunc);
+  p.fnoff = (int64_t *)(w + L.fnoff);
   p.tmp = w + L.tmp;
   p.tmpb = L.tmp_bytes;
   return p;
@@ -496,7 +542,7 @@ static WsPtrs carve(const Layout &L, void *ws) {
 // Source norms, norm (and learned) screen, record counts, scan and record emission.
 // On return *P_out holds the number of records (written in source order).
 static int screen_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts &o, const WsPtrs &w,
-                      int64_t Pmax, mra_apply_stats *stats, int64_t *P_out, cudaStream_t s) {
+                      int64_t Pmax, mra_apply_stats *stats, int64_t *P_out, cudaStream_t s, int nfunc = 1) {
   const int k = op.k, k3 = k * k * k;
   const int64_t n_in = in.n;
   // error flag lives in the first word of the dest-count slot until it is used
@@ -537,6 +583,8 @@ static int screen_run(const Operator &op, const mra_tree_view &in, const mra_app
   a.learned_cut = (float)(log10(o.tau) - o.delta);
   a.box_learned = w.blearned;
   a.box_lbound = w.blbound;
+  a.nfunc = nfunc;
+  a.fn_off = w.fnoff;
   const size_t ssm = a.mlp ? (size_t)MLP_NALL * sizeof(float) : 0;
   screen_kernel<0><<<gboxes, 32 * wpb, ssm, s>>>(a);
   MRA_CUDA_TRY(cudaGetLastError());
@@ -566,6 +614,8 @@ static int screen_run(const Operator &op, const mra_tree_view &in, const mra_app
     MRA_CUDA_TRY(cudaMemcpyAsync(hd, red_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   }
   MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h_err == 3)
+    return fail(MRA_ERR_UNSUPPORTED, "mra_apply_batched: levels above 15 are not supported");
   if (h_err)
     return fail(MRA_ERR_ARG, "mra_apply: an input box lies on a level the operator does not cover "
                 "(levels %d..%d)", op.min_level, op.max_level);
@@ -595,7 +645,7 @@ static int screen_run(const Operator &op, const mra_tree_view &in, const mra_app
 
 int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts &o,
               mra_tree_view &out, void *ws, size_t ws_bytes, mra_apply_stats *stats,
-              cudaStream_t s) {
+              cudaStream_t s, int nfunc, const int64_t *in_offsets, int64_t *out_offsets) {
   const int k = op.k, k3 = k * k * k;
   const int64_t n_in = in.n;
   const int64_t Pmax = apply_max_records(op, o, n_in);
@@ -609,13 +659,17 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
   int64_t *seg = W.seg, *ndest = W.ndest;
   void *tmp = W.tmp;
   size_t tmpb = W.tmpb;
+  if (out_offsets)
+    for (int f = 0; f <= nfunc; ++f) out_offsets[f] = 0;
   if (n_in == 0) {
     out.n = 0;
     if (stats) *stats = mra_apply_stats{};
     return MRA_OK;
   }
+  if (nfunc > 1)
+    MRA_CUDA_TRY(cudaMemcpyAsync(W.fnoff, in_offsets, (nfunc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   int64_t P = 0;
-  int rc0 = screen_run(op, in, o, W, Pmax, stats, &P, s);
+  int rc0 = screen_run(op, in, o, W, Pmax, stats, &P, s, nfunc);
   if (rc0 != MRA_OK) return rc0;
   if (P == 0) {
     out.n = 0;
@@ -630,7 +684,7 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
     head_flags_kernel<<<g, 256, 0, s>>>(P, skey, head);
     MRA_CUDA_TRY(cudaGetLastError());
     MRA_CUDA_TRY(cub::DeviceScan::InclusiveSum(tmp, tmpb, head, did, (int)P, s));
-    segments_kernel<<<g, 256, 0, s>>>(P, skey, head, did, dkey, seg, ndest);
+    segments_kernel<<<g, 256, 0, s>>>(P, skey, head, did, dkey, seg, ndest, nfunc > 1, W.dfunc);
     MRA_CUDA_TRY(cudaGetLastError());
   }
   int64_t nd = 0;
@@ -640,6 +694,15 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
     out.n = nd;
     return fail(MRA_ERR_CAPACITY, "mra_apply: output holds %lld boxes, %lld needed",
                 (long long)out.cap, (long long)nd);
+  }
+  if (nfunc > 1 && out_offsets) {  // first destination of each function (destinations sorted by function)
+    func_offsets_kernel<<<1, 256, 0, s>>>(nd, W.dfunc, nfunc, W.fnoff);
+    MRA_CUDA_TRY(cudaGetLastError());
+    MRA_CUDA_TRY(cudaMemcpyAsync(out_offsets, W.fnoff, (nfunc + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  } else if (out_offsets) {
+    out_offsets[0] = 0;
+    out_offsets[1] = nd;
   }
   int rc;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;

@@ -27,7 +27,7 @@ struct ApplyWork {
 size_t apply_workspace_bytes(const Operator &op, const mra_apply_opts &o, int64_t n_in);
 int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts &o,
               mra_tree_view &out, void *ws, size_t ws_bytes, mra_apply_stats *stats,
-              cudaStream_t s);
+              cudaStream_t s, int nfunc = 1, const int64_t *in_offsets = nullptr, int64_t *out_offsets = nullptr);
 int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts &o,
                     mra_tree_view &out, const ApplyWork &wk, mra_apply_stats *stats,
                     cudaStream_t s);

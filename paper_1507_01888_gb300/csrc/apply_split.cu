@@ -506,13 +506,13 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(K)) apply_split_kernel
 }
 
 // ---------------------------------------------------------------- work-list kernels
-__global__ void key2_kernel(int64_t P, int G, const int *perm, const int *did, const uint64_t *skey,
+__global__ void key2_kernel(int64_t P, int G, const int *perm, const int *did, const uint64_t *dest_key,
                             const int *rec_l, uint64_t *key2, int *val2) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P) return;
   int p = perm[i];
   uint64_t tile = (uint64_t)((did[i] - 1) / G);
-  uint64_t lev = (uint64_t)key_level(skey[i]);
+  uint64_t lev = (uint64_t)key_level(dest_key[did[i] - 1]);
   key2[i] = (tile << 32) | (lev << 24) | (uint64_t)(rec_l[p] & 0xFFFFFF);
   val2[i] = (int)i;
 }
@@ -610,7 +610,7 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
   size_t tmpb = wk.split_ws_bytes - (size_t)(q - w);
   unsigned g = (unsigned)((P + 255) / 256);
   MRA_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-  key2_kernel<<<g, 256, 0, s>>>(P, G, wk.perm, wk.did, wk.skey, wk.rec_l, key2, val2);
+  key2_kernel<<<g, 256, 0, s>>>(P, G, wk.perm, wk.did, wk.dest_key, wk.rec_l, key2, val2);
   MRA_CUDA_TRY(cudaGetLastError());
   MRA_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, tmpb, key2, key2s, val2, val2s, (int)P, 0, 64, s));
   groups_kernel<<<g, 256, 0, s>>>(P, key2s, head, n_tiles);

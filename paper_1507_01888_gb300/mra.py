@@ -37,7 +37,7 @@ STENCIL_NEAREST = 1
 EXPORTED = [
     "mra_last_error", "mra_version", "mra_project", "mra_operator_create", "mra_operator_fit",
     "mra_operator_info", "mra_operator_block", "mra_operator_free", "mra_apply_workspace_size",
-    "mra_apply", "mra_norm", "mra_norm_noalloc", "mra_compare", "mra_log_terms", "mra_mlp_init",
+    "mra_apply", "mra_apply_batched", "mra_norm", "mra_norm_noalloc", "mra_compare", "mra_log_terms", "mra_mlp_init",
     "mra_mlp_standardize", "mra_mlp_forward", "mra_mlp_workspace_size", "mra_mlp_grad", "mra_mlp_train",
 ]
 NOALLOC_MAX_BOXES = 1 << 20
@@ -118,6 +118,8 @@ def load(build_if_stale: bool = True):
         lib.mra_apply_workspace_size.argtypes = [vp, P(TreeView), P(ApplyOpts), P(ctypes.c_size_t)]
         lib.mra_apply.argtypes = [vp, P(TreeView), P(ApplyOpts), P(TreeView), vp, ctypes.c_size_t,
                                   P(ApplyStats), vp]
+        lib.mra_apply_batched.argtypes = [vp, i, P(TreeView), P(ctypes.c_int64), P(ApplyOpts), P(TreeView),
+                                          P(ctypes.c_int64), vp, ctypes.c_size_t, P(ApplyStats), vp]
         lib.mra_norm.argtypes = [P(TreeView), vp, P(d), vp]
         lib.mra_norm_noalloc.argtypes = [P(TreeView), vp, P(d), vp]
         lib.mra_compare.argtypes = [P(TreeView), P(TreeView), P(CompareResult), vp]
@@ -301,6 +303,45 @@ class Applier:
             _check(rc)
             self.out.n = int(vout.n)
             return self.out
+
+
+class BatchedApplier:
+    """mra_apply_batched over trees concatenated back to back (see concat_trees)."""
+
+    def __init__(self, op: Operator, tree: Tree, offsets, opts: ApplyOpts, out_cap: int | None = None,
+                 with_stats: bool = True):
+        self.op, self.opts, self.with_stats = op, opts, with_stats
+        self.nfunc = len(offsets) - 1
+        self.in_off = (ctypes.c_int64 * (self.nfunc + 1))(*[int(v) for v in offsets])
+        self.out_off = (ctypes.c_int64 * (self.nfunc + 1))()
+        self.ws = torch.empty(max(workspace_size(op, tree, opts), 1), dtype=torch.uint8, device=tree.keys.device)
+        self.out = Tree.empty(out_cap or max(2 * tree.n, 1), op.k, op.L, tree.keys.device)
+        self.stats = ApplyStats()
+
+    def __call__(self, tree: Tree, stream=None):
+        lib = load()
+        while True:
+            vin, vout = tree.view(), self.out.view()
+            rc = lib.mra_apply_batched(self.op.handle, self.nfunc, ctypes.byref(vin), self.in_off, ctypes.byref(self.opts),
+                                       ctypes.byref(vout), self.out_off, ctypes.c_void_p(self.ws.data_ptr()),
+                                       self.ws.numel(), ctypes.byref(self.stats) if self.with_stats else None,
+                                       _stream(stream))
+            if rc == MRA_ERR_CAPACITY and vout.n > self.out.cap:
+                self.out = Tree.empty(int(vout.n), self.op.k, self.op.L, tree.keys.device)
+                continue
+            _check(rc)
+            self.out.n = int(vout.n)
+            return self.out, [int(v) for v in self.out_off]
+
+
+def concat_trees(trees):
+    """One tree holding the given trees back to back, and the offsets of each."""
+    keys = torch.cat([t.keys[: t.n] for t in trees])
+    coeffs = torch.cat([t.coeffs[: t.n] for t in trees])
+    offs = [0]
+    for t in trees:
+        offs.append(offs[-1] + t.n)
+    return Tree(keys, coeffs, offs[-1], trees[0].k, trees[0].L), offs
 
 
 def apply(op: Operator, tree: Tree, opts: ApplyOpts, stream=None):
