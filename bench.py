@@ -210,9 +210,14 @@ def main():
         precision = "split"
     prec = mra.PREC_SPLIT_BF16 if precision == "split" else mra.PREC_FP64
 
-    # ---------------- setup (untimed): projection, operator, buffers
-    tree = mra.project(w.funcs[0], w.k, w.L, thresh=w.thresh, init_level=w.init_level, max_level=w.max_level,
-                       uniform_level=w.uniform_level)
+    # ---------------- setup (untimed): projection, operator, buffers, tile-width tuning
+    trees = [mra.project(f, w.k, w.L, thresh=w.thresh, init_level=w.init_level, max_level=w.max_level,
+                         uniform_level=w.uniform_level) for f in w.funcs]
+    batched = len(trees) > 1
+    if batched:
+        tree, offsets = mra.concat_trees(trees)
+    else:
+        tree, offsets = trees[0], [0, trees[0].n]
     keys_h, coeffs_h = tree.host()
     levels = (keys_h >> np.uint64(57)).astype(int)
     op = mra.Operator(w.kernel, w.M, w.k, w.L, int(levels.min()), int(levels.max()), max_disp=w.max_disp,
@@ -220,17 +225,24 @@ def main():
     screen = mra.SCREEN_NORM if w.tau > 0 else mra.SCREEN_NONE
     opts = mra.make_opts(precision=prec, pieces=args.pieces, screen=screen, tau=w.tau, stencil=w.stencil,
                          max_disp=w.max_disp)
-    try:
-        ap = mra.Applier(op, tree, opts)
-        ap(tree)
-    except mra.MraError as e:
-        if prec == mra.PREC_SPLIT_BF16 and e.code == mra.MRA_ERR_UNSUPPORTED and args.precision == "auto":
-            prec, precision = mra.PREC_FP64, "fp64"
-            opts = mra.make_opts(precision=prec, screen=screen, tau=w.tau, stencil=w.stencil, max_disp=w.max_disp)
-            ap = mra.Applier(op, tree, opts)
-            ap(tree)
-        else:
-            raise
+    tuning = {}
+    if prec == mra.PREC_SPLIT_BF16 and not batched:
+        from paper_1507_01888_gb300 import autotune
+        opts, table = autotune.tune(op, tree, opts)
+        tuning = {"tile_variant": opts.tile_variant, "candidates_ms": table}
+
+    def make_applier(o):
+        if batched:
+            ba = mra.BatchedApplier(op, tree, offsets, o)
+            return ba
+        return mra.Applier(op, tree, o)
+
+    ap = make_applier(opts)
+
+    def run(a, t):
+        return a(t)[0] if batched else a(t)
+
+    run(ap, tree)
     torch.cuda.synchronize()
     st0 = ap.stats.as_dict()
     k = w.k
@@ -238,12 +250,28 @@ def main():
     # accuracy of the timed path against the FP64 GPU apply (same screen)
     accuracy = {}
     if prec != mra.PREC_FP64:
-        ref_ap = mra.Applier(op, tree, mra.make_opts(precision=mra.PREC_FP64, screen=screen, tau=w.tau,
-                                                     stencil=w.stencil, max_disp=w.max_disp))
-        ref_out = ref_ap(tree)
-        cmp = mra.compare(ap.out, ref_out)
+        ref_ap = make_applier(mra.make_opts(precision=mra.PREC_FP64, screen=screen, tau=w.tau,
+                                            stencil=w.stencil, max_disp=w.max_disp))
+        if batched:  # keys are sorted within each function only: compare function by function
+            ref_out, ref_offs = ref_ap(tree)
+            _, offs_out = ap(tree)
+            d2 = r2 = mx = 0.0
+            for f in range(len(trees)):
+                def sl(t, o):
+                    return mra.Tree(t.keys[o[f]:o[f + 1]], t.coeffs[o[f]:o[f + 1]], o[f + 1] - o[f], t.k, t.L)
+                if offs_out[f + 1] == offs_out[f] and ref_offs[f + 1] == ref_offs[f]:
+                    continue
+                c = mra.compare(sl(ap.out, offs_out), sl(ref_out, ref_offs))
+                d2 += c["diff_norm"] ** 2
+                r2 += c["ref_norm"] ** 2
+                mx = max(mx, c["max_box_rel"])
+            cmp = {"rel_l2": (d2 / r2) ** 0.5 if r2 > 0 else 0.0, "max_box_rel": mx}
+        else:
+            ref_out = run(ref_ap, tree)
+            cmp = mra.compare(ap.out, ref_out)
         accuracy = {"rel_l2_vs_fp64_gpu": cmp["rel_l2"], "max_box_rel_vs_fp64_gpu": cmp["max_box_rel"],
-                    "fp64_gpu_apply_ms": ref_ap.stats.kernel_ms}
+                    "fp64_gpu_apply_ms": ref_ap.stats.kernel_ms,
+                    "speedup_vs_fp64_gpu_kernel": ref_ap.stats.kernel_ms / max(ap.stats.kernel_ms, 1e-9)}
         del ref_out, ref_ap
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -296,7 +324,7 @@ def main():
     def e2e_step():
         dev_tree.keys.copy_(keys_pin, non_blocking=True)
         dev_tree.coeffs.copy_(coeffs_pin, non_blocking=True)
-        out = ap(dev_tree, stream)
+        out = run(ap, dev_tree) if not batched else ap(dev_tree, stream)[0]
         out_keys_pin.copy_(out.keys[:n_out], non_blocking=True)
         out_coeffs_pin.copy_(out.coeffs[:n_out], non_blocking=True)
 
@@ -344,11 +372,12 @@ def main():
                        "stencil": "shells<=%d" % w.max_disp if w.stencil == 0 else "27-point",
                        "terms_kept": terms, "pairs": st0["pairs"], "n_out": st0["n_out"],
                        "precision": precision, "l2": "flushed by a 256 MB write before every step",
+                       "functions": len(trees), "tuning": tuning,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roof, "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
             "e2e": {"value": e2e_val, "unit": "boxes/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "accuracy": accuracy, "wall_s_timed": t_wall}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not batched:
         cb = cpu_baseline(w, args.cpu_seconds)
         t_job = cb["t_sample"] * cb["terms_total"] / max(cb["sample_terms"], 1)
         line["cpu_baseline"] = {"value": cb["n_in"] / t_job, "unit": "boxes/s", "cores": cb["cores"],

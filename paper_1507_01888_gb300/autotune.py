@@ -1,0 +1,49 @@
+"""Autotuner for the tensor-core apply: picks the tile shape by timing the library's apply
+kernel on the caller's own input.
+
+The library compiles, for k = 6, 8, 10, two tile shapes: four 128-row tiles per CTA with
+two CTAs per SM (variant 0) and seven tiles with one CTA per SM (variant 1).  Wider tiles
+fill more MMA rows per group; two CTAs per SM hide each other's MMA and tensor-memory
+latencies.  Which wins depends on the tree, so the tuner times each variant (device time
+of the apply kernel, CUDA events inside the library), keeps the fastest, and caches the
+choice per (k, pieces, number of boxes rounded to a power of two).
+"""
+from __future__ import annotations
+
+from . import mra
+
+_cache: dict = {}
+
+
+def candidates(k: int):
+    return [0, 1] if k in (6, 8, 10) else [0]
+
+
+def tune(op, tree, opts, repeats: int = 3, verbose: bool = False):
+    """Returns a copy of opts with tile_variant set, and the timing table (ms per variant)."""
+    key = (op.k, tree.n.bit_length(), opts.precision, opts.pieces)
+    table = {}
+    if key in _cache:
+        best = _cache[key]
+    else:
+        for v in candidates(op.k):
+            o = mra.ApplyOpts.from_buffer_copy(opts)
+            o.tile_variant = v
+            if getattr(opts, "_mlp_ref", None) is not None:
+                o._mlp_ref = opts._mlp_ref
+            ap = mra.Applier(op, tree, o)
+            ap(tree)  # warm-up
+            ms = []
+            for _ in range(repeats):
+                ap(tree)
+                ms.append(ap.stats.kernel_ms)
+            table[v] = min(ms)
+            if verbose:
+                print(f"tile_variant={v}: {table[v]:.3f} ms")
+        best = min(table, key=table.get)
+        _cache[key] = best
+    o = mra.ApplyOpts.from_buffer_copy(opts)
+    o.tile_variant = best
+    if getattr(opts, "_mlp_ref", None) is not None:
+        o._mlp_ref = opts._mlp_ref
+    return o, table

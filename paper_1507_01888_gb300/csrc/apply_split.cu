@@ -112,18 +112,22 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// Compile-time shape for an even k: TM tiles of 128 rows per stage and MINB CTAs per SM.
-// k <= 10: four tiles and two CTAs per SM (each CTA's serial chain of MMA waits and
-// tensor-memory loads hides behind the other's); k >= 12: one CTA with more tiles.
-__host__ __device__ constexpr int tm_for(int k) { return k <= 2 ? 1 : (k <= 10 ? 4 : (k <= 12 ? 6 : (k <= 14 ? 5 : 4))); }
-__host__ __device__ constexpr int minb_for(int k) { return k <= 10 ? 2 : 1; }
-__host__ __device__ constexpr int g_for(int k) {
-  return (128 * tm_for(k)) / (k * k) > MAX_G ? MAX_G : (128 * tm_for(k)) / (k * k);
+// Compile-time tile shapes for an even k: TM tiles of 128 rows per stage and MINB CTAs per
+// SM.  Variant 0 -- k <= 10: four tiles and two CTAs per SM (each CTA's serial chain of MMA
+// waits and tensor-memory loads hides behind the other's); k >= 12: one CTA with more tiles.
+// Variant 1 (k = 6, 8, 10): seven tiles, one CTA per SM (fewer, wider tiles).
+__host__ __device__ constexpr int tm_for(int k, int v = 0) {
+  return v == 1 ? 7 : (k <= 2 ? 1 : (k <= 10 ? 4 : (k <= 12 ? 6 : (k <= 14 ? 5 : 4))));
+}
+__host__ __device__ constexpr int minb_for(int k, int v = 0) { return v == 1 ? 1 : (k <= 10 ? 2 : 1); }
+__host__ __device__ constexpr int g_for(int k, int v = 0) {
+  return (128 * tm_for(k, v)) / (k * k) > MAX_G ? MAX_G : (128 * tm_for(k, v)) / (k * k);
 }
 // tensor-memory columns: D (48 T: three 16-column piece groups per tile), rounded to a
 // power of two
-__host__ __device__ constexpr uint32_t tmem_cols_for(int k) {
-  return 48 * tm_for(k) <= 64 ? 64u : (48 * tm_for(k) <= 128 ? 128u : (48 * tm_for(k) <= 256 ? 256u : 512u));
+__host__ __device__ constexpr uint32_t tmem_cols_for(int k, int v = 0) {
+  return 48 * tm_for(k, v) <= 64 ? 64u
+       : (48 * tm_for(k, v) <= 128 ? 128u : (48 * tm_for(k, v) <= 256 ? 256u : 512u));
 }
 
 // Split x and y into three BF16 pieces each (x = x0 + x1 + x2 to 24 bits), packed in pairs.
@@ -146,12 +150,12 @@ __device__ __forceinline__ void split_pair(float x, float y, __nv_bfloat162 &h0,
 // into column groups p..P-1 of the tile's 48 columns of D ([0, 48T)).  Warpgroup 1
 // copies stage 3's result to registers (summing the groups) and releases D before
 // the next term's stage 1; the FP64 accumulation then runs alongside that term.
-template <int K>
-__global__ void __launch_bounds__(SPLIT_THREADS, minb_for(K)) apply_split_kernel(SplitArgs a) {
-  constexpr int TM = tm_for(K);
+template <int K, int V>
+__global__ void __launch_bounds__(SPLIT_THREADS, minb_for(K, V)) apply_split_kernel(SplitArgs a) {
+  constexpr int TM = tm_for(K, V);
   extern __shared__ __align__(1024) unsigned char smem[];
   // k, k^2, k^3, G, T are compile-time: the index arithmetic below has no runtime division
-  constexpr int k = K, k2 = K * K, k3 = K * K * K, G = g_for(K), T = (G * K * K + 127) / 128;
+  constexpr int k = K, k2 = K * K, k3 = K * K * K, G = g_for(K, V), T = (G * K * K + 127) / 128;
   const int P = a.P;
   constexpr int rows = G * k2;
   unsigned char *A1 = smem;                          // [P][T][TILE_BYTES] stage-1 operand (sources)
@@ -189,7 +193,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(K)) apply_split_kernel
     total_it = 0;
   }
   for (int m = tid; m < a.M; m += SPLIT_THREADS) c_sh[m] = a.c[m];
-  if (warp == 0) tc::tmem_alloc(tc::smem_u32(&tmem_holder), tmem_cols_for(K));
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(&tmem_holder), tmem_cols_for(K, V));
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   tc::fence_proxy_async_smem();
   __syncthreads();
@@ -502,7 +506,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(K)) apply_split_kernel
     }
     __syncthreads();
   }
-  if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols_for(K));
+  if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols_for(K, V));
 }
 
 // ---------------------------------------------------------------- work-list kernels
@@ -587,9 +591,10 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
   if (!op.d_Rsplit) return fail(MRA_ERR_ARG, "mra_apply: operator has no split blocks");
   const int k = op.k;
   if (k & 1) return fail(MRA_ERR_UNSUPPORTED, "split apply: odd k=%d not supported (use MRA_PREC_FP64)", k);
-  const int G = g_for(k);
+  const int v = (o.tile_variant == 1 && (k == 6 || k == 8 || k == 10)) ? 1 : 0;
+  const int G = g_for(k, v);
   const int T = (G * k * k + 127) / 128;
-  if (T > tm_for(k)) return fail(MRA_ERR_UNSUPPORTED, "split apply: tile shape for k=%d", k);
+  if (T > tm_for(k, v)) return fail(MRA_ERR_UNSUPPORTED, "split apply: tile shape for k=%d", k);
   const int64_t P = wk.P, nd = wk.n_dest;
   const int n_tiles = (int)((nd + G - 1) / G);
   // carve the split-path workspace
@@ -645,15 +650,18 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
   a.err = err;
   size_t smem = (size_t)2 * a.P * T * TILE_BYTES + 6 * BSTAGE_BYTES;
   void (*kern)(SplitArgs) = nullptr;
-  switch (k) {
-    case 2: kern = apply_split_kernel<2>; break;
-    case 4: kern = apply_split_kernel<4>; break;
-    case 6: kern = apply_split_kernel<6>; break;
-    case 8: kern = apply_split_kernel<8>; break;
-    case 10: kern = apply_split_kernel<10>; break;
-    case 12: kern = apply_split_kernel<12>; break;
-    case 14: kern = apply_split_kernel<14>; break;
-    default: kern = apply_split_kernel<16>; break;
+  switch (k * 2 + v) {
+    case 4: kern = apply_split_kernel<2, 0>; break;
+    case 8: kern = apply_split_kernel<4, 0>; break;
+    case 12: kern = apply_split_kernel<6, 0>; break;
+    case 13: kern = apply_split_kernel<6, 1>; break;
+    case 16: kern = apply_split_kernel<8, 0>; break;
+    case 17: kern = apply_split_kernel<8, 1>; break;
+    case 20: kern = apply_split_kernel<10, 0>; break;
+    case 21: kern = apply_split_kernel<10, 1>; break;
+    case 24: kern = apply_split_kernel<12, 0>; break;
+    case 28: kern = apply_split_kernel<14, 0>; break;
+    default: kern = apply_split_kernel<16, 0>; break;
   }
   MRA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   MRA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));

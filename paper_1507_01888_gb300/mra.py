@@ -63,7 +63,7 @@ class TreeView(ctypes.Structure):
 class ApplyOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("pieces", ctypes.c_int), ("screen", ctypes.c_int),
                 ("tau", ctypes.c_double), ("stencil", ctypes.c_int), ("max_disp", ctypes.c_int),
-                ("mlp", ctypes.c_void_p), ("delta", ctypes.c_double)]
+                ("mlp", ctypes.c_void_p), ("delta", ctypes.c_double), ("tile_variant", ctypes.c_int)]
 
 
 class ApplyStats(ctypes.Structure):
@@ -262,8 +262,8 @@ class Operator:
 
 
 def make_opts(precision=PREC_FP64, pieces=3, screen=SCREEN_NONE, tau=0.0, stencil=STENCIL_NEAREST,
-              max_disp=1, mlp: torch.Tensor | None = None, delta: float = 0.0) -> ApplyOpts:
-    o = ApplyOpts(precision, pieces, screen, tau, stencil, max_disp, None, delta)
+              max_disp=1, mlp: torch.Tensor | None = None, delta: float = 0.0, tile_variant: int = 0) -> ApplyOpts:
+    o = ApplyOpts(precision, pieces, screen, tau, stencil, max_disp, None, delta, tile_variant)
     if mlp is not None:
         o.mlp = mlp.data_ptr()
         o._mlp_ref = mlp  # keep the tensor alive with the options

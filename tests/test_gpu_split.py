@@ -64,6 +64,23 @@ def test_split_random_trees_ragged(mra, k, lev, nbox, seed):
     assert cmp["rel_l2"] <= TOL_MIXED
 
 
+@pytest.mark.parametrize("k,lev,nbox,seed", [(6, 3, 200, 31), (8, 3, 150, 32), (10, 3, 90, 33)])
+def test_split_wide_tile_variant(mra, k, lev, nbox, seed):
+    """Tile variant 1 (seven 128-row tiles, one CTA per SM) equals the oracle like variant 0."""
+    keys, coeffs = W.random_tree_coeffs(nbox, k, lev, seed=seed)
+    op = mra.Operator(0, 16, k, 16.0, 0, lev, max_disp=1, fit_eps=1e-4)
+    fit = op.fit()
+    ref = O.apply(keys, coeffs, fit["c"], fit["t"], 16.0, stencil=1, tau=0.0)
+    tree = mra.Tree.from_host(keys, coeffs, 16.0)
+    for v in (0, 1):
+        o = split_opts(mra, stencil=mra.STENCIL_NEAREST)
+        o.tile_variant = v
+        out, _ = mra.apply(op, tree, o)
+        gk, gc = out.host()
+        assert (gk == ref.keys).all()
+        assert rel_l2(gc, ref.coeffs) <= TOL_MIXED
+
+
 def test_split_shells_and_screen_adaptive(mra):
     f = W.gaussian_sum(3, 1.0, 200.0, seed=23)
     ok, oc, _ = O.project(f, 6, 32.0, thresh=1e-4, init_level=2, max_level=10)
