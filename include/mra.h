@@ -102,8 +102,8 @@ typedef struct {
   int max_disp;   /* largest |l|_inf for MRA_STENCIL_SHELLS (<= the operator's max_disp) */
   const float *mlp; /* MRA_SCREEN_LEARNED: device model, MRA_MLP_PARAMS floats */
   double delta;     /* MRA_SCREEN_LEARNED: safety margin in log10 units */
-  int tile_variant; /* MRA_PREC_SPLIT_BF16 tile shape: 0 = default; 1 (k = 6, 8, 10) = seven
-                       128-row tiles per CTA and one CTA per SM instead of four and two */
+  int tile_variant; /* MRA_PREC_SPLIT_BF16 tile shape: 0 = default, four 128-row tiles per CTA
+                       (one CTA per SM); 1 (k = 4 to 10) = two tiles per CTA, two CTAs per SM */
 } mra_apply_opts;
 
 typedef struct {

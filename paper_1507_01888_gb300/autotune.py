@@ -1,10 +1,10 @@
 """Autotuner for the tensor-core apply: picks the tile shape by timing the library's apply
 kernel on the caller's own input.
 
-The library compiles, for k = 6, 8, 10, two tile shapes: four 128-row tiles per CTA with
-two CTAs per SM (variant 0) and seven tiles with one CTA per SM (variant 1).  Wider tiles
-fill more MMA rows per group; two CTAs per SM hide each other's MMA and tensor-memory
-latencies.  Which wins depends on the tree, so the tuner times each variant (device time
+The library compiles, for k = 4 to 10, two tile shapes: four 128-row tiles per CTA with
+one CTA per SM (variant 0, the whole tensor memory) and two tiles per CTA with two CTAs
+per SM (variant 1).  Wider tiles gather more destinations per group, so more MMA rows are
+filled; two CTAs per SM keep the tensor pipe busy while the other CTA waits.  Which wins depends on the tree, so the tuner times each variant (device time
 of the apply kernel, CUDA events inside the library), keeps the fastest, and caches the
 choice per (k, pieces, number of boxes rounded to a power of two).
 """
@@ -16,7 +16,7 @@ _cache: dict = {}
 
 
 def candidates(k: int):
-    return [0, 1] if k in (6, 8, 10) else [0]
+    return [0, 1] if 4 <= k <= 10 else [0]
 
 
 def tune(op, tree, opts, repeats: int = 3, verbose: bool = False):

@@ -21,6 +21,8 @@
 // a thread writes its row's k outputs as one contiguous run.  The k x k block
 // R_d is the K-major B operand (N = output index, K = input index), its P
 // pieces stacked along N so that one MMA per A piece covers all kept products.
+// Stage 3 multiplies by c_m R_z.  Each term's FP32 stage-3 output is added into per-slot
+// sums kept as FP32 pairs (TwoSum), so the term and box sums lose nothing to rounding.
 #include <cuda_bf16.h>
 
 #include <cub/cub.cuh>
@@ -37,7 +39,10 @@ constexpr int MG_BYTES = 272;           // stride of the 8-row groups: 256 B of 
                                         // so that consecutive groups start 4 banks apart
 constexpr int TILE_BYTES = 16 * MG_BYTES;  // one 128 x 16 BF16 operand tile
 constexpr int BPIECE_BYTES = 512;       // one 16 x 16 BF16 block piece
-constexpr int BSTAGE_BYTES = 3 * BPIECE_BYTES;
+constexpr int BSTAGE_BYTES = 3 * BPIECE_BYTES;  // the three pieces of one block
+constexpr int BTERM_BYTES = 3 * BSTAGE_BYTES;   // the three blocks (x, y, z) of one term
+constexpr int NBUF = 4;                         // block buffers: terms in flight
+constexpr int RING = 4;                         // term-info ring from warpgroup 0 to 1
 constexpr int MAX_G = 32;
 constexpr long long WAIT_CYCLES = 4000000000LL;  // bounded mbarrier wait (~2 s)
 
@@ -62,9 +67,9 @@ __device__ __forceinline__ void split3(double x, __nv_bfloat16 &p0, __nv_bfloat1
 
 
 struct SplitArgs {
-  int k, M, P, G, T;
-  const double *c;
-  const unsigned char *Bsplit;  // per block: 3 pieces x 512 B (K-major core-matrix layout)
+  int k, M, P;
+  const unsigned char *Bsplit;    // per block: 3 pieces x 512 B (K-major core-matrix layout)
+  const unsigned char *Bsplit_c;  // the same for c_m R (stage 3 carries the term coefficient)
   const int *Dlev;
   const int64_t *level_off;
   const double *in_coeffs;
@@ -112,22 +117,22 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// Compile-time tile shapes for an even k: TM tiles of 128 rows per stage and MINB CTAs per
-// SM.  Variant 0 -- k <= 10: four tiles and two CTAs per SM (each CTA's serial chain of MMA
-// waits and tensor-memory loads hides behind the other's); k >= 12: one CTA with more tiles.
-// Variant 1 (k = 6, 8, 10): seven tiles, one CTA per SM (fewer, wider tiles).
-__host__ __device__ constexpr int tm_for(int k, int v = 0) {
-  return v == 1 ? 7 : (k <= 2 ? 1 : (k <= 10 ? 4 : (k <= 12 ? 6 : (k <= 14 ? 5 : 4))));
+// Tile shapes for an even k.  A CTA owns G consecutive destination boxes (slots) whose
+// G k^2 operand rows fill T <= TT tiles of 128 rows.  Tensor memory holds the stage-1
+// and stage-2 outputs (48 columns per tile each: three 16-column piece groups) and the
+// stage-3 output (32 columns per tile: two groups): 128 T columns.  TT = 4 takes the whole
+// tensor memory (one CTA per SM); TT = 2 leaves room for a second CTA on the SM.
+__host__ __device__ constexpr int g_for(int k, int tt) {
+  return (128 * tt) / (k * k) > MAX_G ? MAX_G : (128 * tt) / (k * k);
 }
-__host__ __device__ constexpr int minb_for(int k, int v = 0) { return v == 1 ? 1 : (k <= 10 ? 2 : 1); }
-__host__ __device__ constexpr int g_for(int k, int v = 0) {
-  return (128 * tm_for(k, v)) / (k * k) > MAX_G ? MAX_G : (128 * tm_for(k, v)) / (k * k);
-}
-// tensor-memory columns: D (48 T: three 16-column piece groups per tile), rounded to a
-// power of two
-__host__ __device__ constexpr uint32_t tmem_cols_for(int k, int v = 0) {
-  return 48 * tm_for(k, v) <= 64 ? 64u
-       : (48 * tm_for(k, v) <= 128 ? 128u : (48 * tm_for(k, v) <= 256 ? 256u : 512u));
+__host__ __device__ constexpr int t_for(int k, int tt) { return (g_for(k, tt) * k * k + 127) / 128; }
+__host__ __device__ constexpr uint32_t tmem_cols_for(int T) { return T <= 1 ? 128u : (T <= 2 ? 256u : 512u); }
+// slots whose rows [i k^2, (i+1) k^2) meet tile t's rows [128 t, 128 t + 128)
+__host__ __device__ constexpr uint32_t tile_slots(int t, int k2, int G) {
+  uint32_t m = 0;
+  for (int i = 0; i < G; ++i)
+    if (i * k2 < 128 * (t + 1) && (i + 1) * k2 > 128 * t) m |= 1u << i;
+  return m;
 }
 
 // Split x and y into three BF16 pieces each (x = x0 + x1 + x2 to 24 bits), packed in pairs.
@@ -141,35 +146,41 @@ __device__ __forceinline__ void split_pair(float x, float y, __nv_bfloat162 &h0,
   h2 = __floats2bfloat162_rn(rx - f1.x, ry - f1.y);
 }
 
-// Warp roles: warpgroup 0 (warps 0-3) stages each group's sources, turns stage-1/2
-// outputs into the next stage's operands, and its thread 0 issues every MMA and every
-// block-tile copy (one term ahead); warpgroup 1 (warps 4-7) adds each term's stage-3
-// output into the FP64 accumulators while warpgroup 0 works on the next term.
-// An M=128 x K=16 MMA costs about the same for any N <= 128 (its A tile fetch bounds
-// it), so every stage stacks the B pieces along N: A piece p times [B0 .. B(P-1-p)]
-// into column groups p..P-1 of the tile's 48 columns of D ([0, 48T)).  Warpgroup 1
-// copies stage 3's result to registers (summing the groups) and releases D before
-// the next term's stage 1; the FP64 accumulation then runs alongside that term.
-template <int K, int V>
-__global__ void __launch_bounds__(SPLIT_THREADS, minb_for(K, V)) apply_split_kernel(SplitArgs a) {
-  constexpr int TM = tm_for(K, V);
+// Warp roles and the term pipeline.  Terms of a group flow through three MMA stages:
+//   warpgroup 0 (warps 0-3) stages each group's sources (A1), turns the stage-1 output
+//     D1 into the stage-2 operand A2; its thread 0 issues the block copies and the
+//     stage-1 and stage-2 MMAs;
+//   warpgroup 1 (warps 4-7) turns the stage-2 output D2 into the stage-3 operand A3; its
+//     thread 128 issues the stage-3 MMAs into D3 (the coefficient c_m is folded into the
+//     stage-3 blocks); while the next term's stage 2 runs it adds D3 into the per-slot
+//     sums, for the slots that keep the term.
+// So warpgroup 0 works on term j+1 while warpgroup 1 works on term j.  Tiles of 128 rows
+// that hold no slot keeping the term are skipped in all three stages.
+// mbarriers (one arrival each): bb[b] block copies landed; s1/s2/s3 stage done (commit);
+// ring_full term info published; d2_free D2 read out; b_free[b] block buffer b released
+// by the stage-3 MMAs that read it.  Each wait is bounded and gives up when the other
+// warpgroup has aborted.
+template <int K, int TT>
+__global__ void __launch_bounds__(SPLIT_THREADS, 4 / TT) apply_split_kernel(SplitArgs a) {
+  constexpr int k = K, k2 = K * K, k3 = K * K * K;
+  constexpr int G = g_for(K, TT), rows = G * k2, T = t_for(K, TT);
+  constexpr uint32_t NCOL = tmem_cols_for(T);
   extern __shared__ __align__(1024) unsigned char smem[];
-  // k, k^2, k^3, G, T are compile-time: the index arithmetic below has no runtime division
-  constexpr int k = K, k2 = K * K, k3 = K * K * K, G = g_for(K, V), T = (G * K * K + 127) / 128;
   const int P = a.P;
-  constexpr int rows = G * k2;
-  unsigned char *A1 = smem;                          // [P][T][TILE_BYTES] stage-1 operand (sources)
-  unsigned char *A23 = A1 + P * T * TILE_BYTES;      // [P][T][TILE_BYTES] stage-2/3 operand
-  unsigned char *Bt = A23 + P * T * TILE_BYTES;      // [2 buffers][3 stages][1536]
-  __shared__ __align__(8) uint64_t bar12, bar3, bar_free, bar_drain, bar_b[2];
+  const int ptile = P * T * TILE_BYTES;
+  unsigned char *A1 = smem;              // [P][T] tiles: stage-1 operand (sources)
+  unsigned char *A2 = A1 + ptile;        // [P][T] tiles: stage-2 operand
+  unsigned char *A3 = A2 + ptile;        // [P][T] tiles: stage-3 operand
+  unsigned char *Bt = A3 + ptile;        // [NBUF][3 stages][1536]: the blocks of a term
+  __shared__ __align__(8) uint64_t bar_s1, bar_s2, bar_s3, bar_ring, bar_d2free, bar_drain0, bar_drain1;
+  __shared__ __align__(8) uint64_t bar_bb[NBUF], bar_bfree[NBUF];
   __shared__ uint32_t tmem_holder;
   __shared__ int slot_src[MAX_G];
   __shared__ uint64_t slot_mask[MAX_G][2];
   __shared__ uint64_t uni[2];
-  __shared__ int g_level, g_l, total_it;
-  __shared__ double ring_c[4];
-  __shared__ double c_sh[MRA_MAX_TERMS];
-  __shared__ uint32_t ring_keep[4];
+  __shared__ int g_level, g_l, total_it, g_nterms;
+  __shared__ unsigned char g_terms[MRA_MAX_TERMS];
+  __shared__ uint32_t ring_keep[RING];
   __shared__ volatile int abort_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -177,23 +188,27 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(K, V)) apply_split_ker
   const int tile = blockIdx.x;
   const int g0 = a.tile_gstart[tile], g1 = a.tile_gstart[tile + 1];
 
-  {  // zero the operand buffers once: contraction and row padding stay zero
+  {  // zero the operand tiles once: contraction and row padding stay zero
     int4 *z = (int4 *)smem;
-    int n16 = (2 * P * T * TILE_BYTES) / 16;
+    int n16 = (3 * ptile) / 16;
     for (int i = tid; i < n16; i += SPLIT_THREADS) z[i] = make_int4(0, 0, 0, 0);
   }
   if (tid == 0) {
-    tc::mbar_init(tc::smem_u32(&bar12), 1);
-    tc::mbar_init(tc::smem_u32(&bar3), 1);
-    tc::mbar_init(tc::smem_u32(&bar_free), 1);
-    tc::mbar_init(tc::smem_u32(&bar_drain), 1);
-    tc::mbar_init(tc::smem_u32(&bar_b[0]), 1);
-    tc::mbar_init(tc::smem_u32(&bar_b[1]), 1);
+    tc::mbar_init(tc::smem_u32(&bar_s1), 1);
+    tc::mbar_init(tc::smem_u32(&bar_s2), 1);
+    tc::mbar_init(tc::smem_u32(&bar_s3), 1);
+    tc::mbar_init(tc::smem_u32(&bar_ring), 1);
+    tc::mbar_init(tc::smem_u32(&bar_d2free), 1);
+    tc::mbar_init(tc::smem_u32(&bar_drain0), 1);
+    tc::mbar_init(tc::smem_u32(&bar_drain1), 1);
+    for (int b = 0; b < NBUF; ++b) {
+      tc::mbar_init(tc::smem_u32(&bar_bb[b]), 1);
+      tc::mbar_init(tc::smem_u32(&bar_bfree[b]), 1);
+    }
     abort_flag = 0;
     total_it = 0;
   }
-  for (int m = tid; m < a.M; m += SPLIT_THREADS) c_sh[m] = a.c[m];
-  if (warp == 0) tc::tmem_alloc(tc::smem_u32(&tmem_holder), tmem_cols_for(K, V));
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(&tmem_holder), NCOL);
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   tc::fence_proxy_async_smem();
   __syncthreads();
@@ -218,79 +233,80 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(K, V)) apply_split_ker
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_holder;
-  const uint32_t b12 = tc::smem_u32(&bar12);
-  const uint32_t b3 = tc::smem_u32(&bar3), bfree = tc::smem_u32(&bar_free);
-  const uint32_t bb[2] = {tc::smem_u32(&bar_b[0]), tc::smem_u32(&bar_b[1])};
+  const uint32_t tD1 = tmem, tD2 = tmem + 48u * T, tD3 = tmem + 96u * T;
+  const uint32_t bs1 = tc::smem_u32(&bar_s1), bs2 = tc::smem_u32(&bar_s2), bs3 = tc::smem_u32(&bar_s3);
+  const uint32_t bring = tc::smem_u32(&bar_ring), bd2free = tc::smem_u32(&bar_d2free);
   const int nit = total_it;
-  const uint32_t idesc16 = tc::idesc_bf16(128, 16, 1, 0);
-  const uint32_t idesc_n[3] = {idesc16, tc::idesc_bf16(128, 32, 1, 0), tc::idesc_bf16(128, 48, 1, 0)};
-
+  const uint32_t idesc_n[3] = {tc::idesc_bf16(128, 16, 1, 0), tc::idesc_bf16(128, 32, 1, 0),
+                               tc::idesc_bf16(128, 48, 1, 0)};
+  auto tiles_of = [&](uint32_t keep) -> uint32_t {
+    uint32_t tl = 0;
+#pragma unroll
+    for (int t = 0; t < T; ++t)
+      if (keep & tile_slots(t, k2, G)) tl |= 1u << t;
+    return tl;
+  };
+  auto adesc = [&](const unsigned char *A, int p, int t) {
+    return tc::smem_desc(tc::smem_u32(A + (p * T + t) * TILE_BYTES), 128, MG_BYTES);
+  };
+  auto bdesc = [&](const unsigned char *B) { return tc::smem_desc(tc::smem_u32(B), 128, 256); };
   // stages 1 and 2: A piece p times B pieces 0..P-1-p (stacked along N) into column
-  // groups p..P-1 of the tile's 48 columns of D12
-  auto issue_stacked = [&](const unsigned char *A, const unsigned char *B) {
+  // groups p..P-1 of the tile's 48 columns
+  auto issue_stacked = [&](uint32_t d, const unsigned char *A, const unsigned char *B, uint32_t tiles) {
     for (int t = 0; t < T; ++t) {
-      uint32_t d = tmem + (uint32_t)(t * 48);
-      for (int p = 0; p < P; ++p) {
-        uint64_t ad = tc::smem_desc(tc::smem_u32(A + (p * T + t) * TILE_BYTES), 128, MG_BYTES);
-        uint64_t bd = tc::smem_desc(tc::smem_u32(B), 128, 256);
-        tc::mma_bf16(d + 16 * p, ad, bd, idesc_n[P - 1 - p], p > 0 ? 1u : 0u);
-      }
+      if (!((tiles >> t) & 1u)) continue;
+      for (int p = 0; p < P; ++p)
+        tc::mma_bf16(d + (uint32_t)(t * 48 + 16 * p), adesc(A, p, t), bdesc(B), idesc_n[P - 1 - p], p > 0 ? 1u : 0u);
     }
+  };
+  // element [contraction a][row (i, b, d)] for d = 0..k-1 of this thread's row, into operand A
+  auto store_run = [&](unsigned char *A, int mrow, int a_idx, const float *v) {
+    const int stride = T * TILE_BYTES;
+#pragma unroll
+    for (int d = 0; d < K; d += 2) {
+      __nv_bfloat162 h0, h1, h2;
+      split_pair(v[d], v[d + 1], h0, h1, h2);
+      uint32_t off = a_off(mrow + d, a_idx);
+      *(__nv_bfloat162 *)(A + off) = h0;
+      *(__nv_bfloat162 *)(A + stride + off) = h1;
+      if (P > 2) *(__nv_bfloat162 *)(A + 2 * stride + off) = h2;
+    }
+  };
+  // the first K columns of each of the P piece groups of tile t, summed smallest first
+  auto load_d = [&](uint32_t dbase, int t, float *v) {
+    const uint32_t base = dbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(t * 48);
+    float c[3][K];
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+      if (p < P) tc::tmem_ldk<K>(base + (uint32_t)(16 * p), c[p]);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      v[j] = P == 3 ? (c[2][j] + c[1][j]) + c[0][j] : (P == 2 ? c[1][j] + c[0][j] : c[0][j]);
   };
 
   if (wg == 0) {
-    // ======================================================= warpgroup 0 + MMA / copy issue
-    uint32_t p12 = 0;
+    // ======================================================= warpgroup 0
+    uint32_t p1 = 0;
     int it = 0;
+    int nfetch = 0, nwaited = 0;  // block copies issued / waited for (thread 0)
     bool bad = false;
-    auto wait12 = [&]() -> bool {
-      bool ok = tc::mbar_wait(b12, p12, WAIT_CYCLES);
-      p12 ^= 1u;
-      bool any_bad = wg_vote_or(1, !ok || abort_flag);
-      tc::fence_after_sync();
-      return !any_bad;
-    };
-    // copies of the three blocks (m; lx, ly, lz) into buffer `buf`
-    auto fetch_blocks = [&](int buf, int m, int64_t lbase, int nl, int Dop, int lx, int ly, int lz) {
-      unsigned char *Bb = Bt + buf * 3 * BSTAGE_BYTES;
-      tc::mbar_arrive_expect_tx(bb[buf], 3 * BSTAGE_BYTES);
-      const int ls[3] = {lx, ly, lz};
-#pragma unroll
-      for (int st = 0; st < 3; ++st) {
-        int64_t blk = lbase + (int64_t)m * nl + ls[st] + Dop;
-        tc::bulk_g2s(tc::smem_u32(Bb + st * BSTAGE_BYTES), a.Bsplit + blk * BSTAGE_BYTES, BSTAGE_BYTES, bb[buf]);
-      }
-    };
-    // element [contraction a][row (i, b, d)] for d = 0..k-1 of this thread's rows
-    auto store_run = [&](int mrow, int a_idx, const float *v) {
-      const int stride = T * TILE_BYTES;
-#pragma unroll
-      for (int d = 0; d < K; d += 2) {
-        __nv_bfloat162 h0, h1, h2;
-        split_pair(v[d], v[d + 1], h0, h1, h2);
-        uint32_t off = a_off(mrow + d, a_idx);
-        *(__nv_bfloat162 *)(A23 + off) = h0;
-        *(__nv_bfloat162 *)(A23 + stride + off) = h1;
-        if (P > 2) *(__nv_bfloat162 *)(A23 + 2 * stride + off) = h2;
-      }
-    };
-    // tiles t0, t0+1 of D12 for this thread's lane (first K columns of each of the P
-    // groups, summed smallest first), one wait for all loads
-    auto load_d12_pair = [&](int t0, float (*v)[16]) {
-      const uint32_t base = tmem + ((uint32_t)(32 * quarter) << 16);
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        float c[3][K];
-        if (t0 + u < T) {
-#pragma unroll
-          for (int p = 0; p < 3; ++p)
-            if (p < P) tc::tmem_ldk<K>(base + (uint32_t)((t0 + u) * 48 + 16 * p), c[p]);
-          tc::tmem_ld_wait();
-#pragma unroll
-          for (int j = 0; j < K; ++j)
-            v[u][j] = P == 3 ? (c[2][j] + c[1][j]) + c[0][j] : (P == 2 ? c[1][j] + c[0][j] : c[0][j]);
-        }
-      }
+    // copies of the three blocks (m; lx, ly, lz) of iteration `i` into buffer i % NBUF, once
+    // the stage-3 MMAs of iteration i - NBUF (the buffer's previous user) are done
+    auto fetch = [&](int i, int m, int64_t lbase, int nl, int Dop, int lx, int ly, int lz) -> bool {
+      const int b = i % NBUF;
+      if (i >= NBUF &&
+          !tc::mbar_wait_or_abort(tc::smem_u32(&bar_bfree[b]), (uint32_t)((i / NBUF - 1) & 1), WAIT_CYCLES, &abort_flag))
+        return false;
+      unsigned char *Bb = Bt + b * BTERM_BYTES;
+      const uint32_t bar = tc::smem_u32(&bar_bb[b]);
+      tc::mbar_arrive_expect_tx(bar, 3 * BSTAGE_BYTES);
+      const int64_t blk0 = lbase + (int64_t)m * nl + Dop;
+      tc::bulk_g2s(tc::smem_u32(Bb), a.Bsplit + (blk0 + lx) * BSTAGE_BYTES, BSTAGE_BYTES, bar);
+      tc::bulk_g2s(tc::smem_u32(Bb + BSTAGE_BYTES), a.Bsplit + (blk0 + ly) * BSTAGE_BYTES, BSTAGE_BYTES, bar);
+      tc::bulk_g2s(tc::smem_u32(Bb + 2 * BSTAGE_BYTES), a.Bsplit_c + (blk0 + lz) * BSTAGE_BYTES, BSTAGE_BYTES, bar);
+      ++nfetch;
+      return true;
     };
     for (int g = g0; g < g1 && !bad; ++g) {
       const int r0 = a.grp_start[g], r1 = a.grp_start[g + 1];
@@ -323,18 +339,17 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(K, V)) apply_split_ker
       const int Dop = a.Dlev[lev], nl = 2 * Dop + 1;
       const int ldx = (lp & 255) - 128, ldy = ((lp >> 8) & 255) - 128, ldz = ((lp >> 16) & 255) - 128;
       const int64_t lbase = a.level_off[lev];
-      uint64_t bits0 = uni[0], bits1 = uni[1];
-      auto next_term = [&](uint64_t &b0, uint64_t &b1) -> int {  // pop the lowest kept term
-        if (b0) { int m = __ffsll((long long)b0) - 1; b0 &= b0 - 1; return m; }
-        if (b1) { int m = 64 + __ffsll((long long)b1) - 1; b1 &= b1 - 1; return m; }
-        return -1;
-      };
-      int m = next_term(bits0, bits1);
-      // first term of the group: its blocks were not prefetched (buffer it&1 was last read by
-      // stage 3 of term it-2, complete since stage 1 of term it-1 completed)
-      if (tid == 0 && m >= 0) fetch_blocks(it & 1, m, lbase, nl, Dop, ldx, ldy, ldz);
-      // stage-1 operand: sources, rows (i, jy, jz), contraction jx (FP64 -> FP32 -> 3 BF16 pieces).
-      // The previous group's stage-1 MMAs are complete (their stage 2 was waited for).
+      if (tid == 0) {  // the group's terms in ascending order; blocks of its first two terms
+        int n = 0;
+        uint64_t b0 = uni[0], b1 = uni[1];
+        while (b0) { g_terms[n++] = (unsigned char)(__ffsll((long long)b0) - 1); b0 &= b0 - 1; }
+        while (b1) { g_terms[n++] = (unsigned char)(64 + __ffsll((long long)b1) - 1); b1 &= b1 - 1; }
+        g_nterms = n;
+        for (int j = 0; j < 2 && j < n; ++j)
+          if (!fetch(it + j, g_terms[j], lbase, nl, Dop, ldx, ldy, ldz)) abort_flag = 1;
+      }
+      // stage-1 operand: sources, rows (i, jy, jz), contraction jx (FP64 -> FP32 -> 3 BF16
+      // pieces).  The previous group's stage-1 MMAs are complete (their output was read).
       for (int e = tid; e < G * k3 / 2; e += 128) {
         int e2 = 2 * e;
         int i = e2 / k3, rest = e2 - i * k3;
@@ -351,162 +366,197 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(K, V)) apply_split_ker
       }
       tc::fence_proxy_async_smem();
       tc::fence_before_sync();
-      wg_sync(1);
-      while (m >= 0 && !bad) {
-        const int buf = it & 1;
-        const unsigned char *Bb = Bt + buf * 3 * BSTAGE_BYTES;
-        const int m_next = next_term(bits0, bits1);
+      if (wg_vote_or(1, abort_flag)) { bad = true; break; }
+      const int nt = g_nterms;
+      for (int j = 0; j < nt; ++j, ++it) {
+        const int m = g_terms[j];
+        const int b = it % NBUF;
+        const unsigned char *Bb = Bt + b * BTERM_BYTES;
+        uint32_t keep = 0;
+        for (int i = 0; i < G; ++i) keep |= (uint32_t)((slot_mask[i][m >> 6] >> (m & 63)) & 1ull) << i;
+        const uint32_t tiles = tiles_of(keep);
         if (tid == 0) {
-          // term info for warpgroup 1 (ring slot it&3 was read by its iteration it-4, which
-          // finished before the "D free" arrival that let stage 1 of term it-3 start)
-          uint32_t keep = 0;
-          const int w = m >> 6;
-          for (int i = 0; i < G; ++i) keep |= (uint32_t)((slot_mask[i][w] >> (m & 63)) & 1ull) << i;
-          ring_keep[it & 3] = keep;
-          ring_c[it & 3] = c_sh[m];
-          bool ok = tc::mbar_wait(bb[buf], (uint32_t)((it >> 1) & 1), WAIT_CYCLES);
-          // D holds stage 3 of term it-1 until warpgroup 1 has copied it out
-          if (ok && it > 0) ok = tc::mbar_wait(bfree, (uint32_t)((it - 1) & 1), WAIT_CYCLES);
-          if (!ok) {
-            abort_flag = 1;
-          } else {
+          bool ok = tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[b]), (uint32_t)((it / NBUF) & 1), WAIT_CYCLES, &abort_flag);
+          if (ok) {
+            nwaited = it + 1;
             tc::fence_after_sync();
-            issue_stacked(A1, Bb);  // ---- stage 1: rows (i, jy, jz), contraction jx
-            tc::mma_commit(b12);
+            issue_stacked(tD1, A1, Bb, tiles);  // ---- stage 1: rows (i, jy, jz), contraction jx
+            tc::mma_commit(bs1);
+            if (j + 2 < nt) ok = fetch(it + 2, g_terms[j + 2], lbase, nl, Dop, ldx, ldy, ldz);
           }
+          if (!ok) abort_flag = 1;
         }
-        if (!wait12()) { bad = true; break; }
-        // stage 1 done, hence also stage 3 of term it-1: buffer it+1 is free for the next term
-        if (tid == 0 && m_next >= 0) fetch_blocks((it + 1) & 1, m_next, lbase, nl, Dop, ldx, ldy, ldz);
+        bool ok = tc::mbar_wait_or_abort(bs1, p1, WAIT_CYCLES, &abort_flag);
+        p1 ^= 1u;
+        if (wg_vote_or(1, !ok || abort_flag)) { bad = true; break; }
+        tc::fence_after_sync();
+        // stage-1 output -> stage-2 operand: element [jy][(i, jz, ix)].  The stage-2 MMAs of
+        // the previous term have read A2: they were issued before this term's stage 1.
 #pragma unroll
-        for (int t0 = 0; t0 < TM; t0 += 2) {
-          float v[2][16];
-          load_d12_pair(t0, v);
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int t = t0 + u;
-            int m1 = t * 128 + quarter * 32 + lane;
-            if (t < TM && t < T && m1 < rows) {
-              int i = m1 / k2, rem = m1 - i * k2, jy = rem / k, jz = rem - jy * k;
-              store_run(i * k2 + jz * k, jy, v[u]);  // element [jy][(i, jz, ix)]
-            }
+        for (int t = 0; t < T; ++t) {
+          if (!((tiles >> t) & 1u)) continue;
+          float v[K];
+          load_d(tD1, t, v);
+          int m1 = t * 128 + quarter * 32 + lane;
+          if (m1 < rows) {
+            int i = m1 / k2, rem = m1 - i * k2, jy = rem / k, jz = rem - jy * k;
+            store_run(A2, i * k2 + jz * k, jy, v);
           }
         }
         tc::fence_proxy_async_smem();
         tc::fence_before_sync();
         wg_sync(1);
         if (tid == 0) {  // ---- stage 2: rows (i, jz, ix), contraction jy
-          tc::fence_after_sync();
-          issue_stacked(A23, Bb + BSTAGE_BYTES);
-          tc::mma_commit(b12);
-        }
-        if (!wait12()) { bad = true; break; }
-#pragma unroll
-        for (int t0 = 0; t0 < TM; t0 += 2) {
-          float v[2][16];
-          load_d12_pair(t0, v);
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int t = t0 + u;
-            int m2 = t * 128 + quarter * 32 + lane;
-            if (t < TM && t < T && m2 < rows) {
-              int i = m2 / k2, rem = m2 - i * k2, jz = rem / k, ix = rem - jz * k;
-              store_run(i * k2 + ix * k, jz, v[u]);  // element [jz][(i, ix, iy)]
-            }
+          bool ok2 = it == 0 || tc::mbar_wait_or_abort(bd2free, (uint32_t)((it - 1) & 1), WAIT_CYCLES, &abort_flag);
+          if (ok2) {
+            ring_keep[it % RING] = keep;
+            mbar_arrive(bring);
+            tc::fence_after_sync();
+            issue_stacked(tD2, A2, Bb + BSTAGE_BYTES, tiles);
+            tc::mma_commit(bs2);
+          } else {
+            abort_flag = 1;
           }
         }
-        tc::fence_proxy_async_smem();
-        tc::fence_before_sync();
-        wg_sync(1);
-        if (tid == 0) {  // ---- stage 3: rows (i, ix, iy), contraction jz
-          tc::fence_after_sync();
-          issue_stacked(A23, Bb + 2 * BSTAGE_BYTES);
-          tc::mma_commit(b3);
-        }
-        ++it;
-        m = m_next;
-        if (wg_vote_or(1, abort_flag)) { bad = true; break; }
       }
-      wg_sync(1);
     }
     if (bad) abort_flag = 1;
+    if (tid == 0) {
+      // block copies still in flight (after an abort) land before the CTA exits, and every
+      // MMA this thread issued is complete before the tensor memory is released
+      for (int i = nwaited; i < nfetch; ++i)
+        tc::mbar_wait(tc::smem_u32(&bar_bb[i % NBUF]), (uint32_t)((i / NBUF) & 1), WAIT_CYCLES);
+      tc::mma_commit(tc::smem_u32(&bar_drain0));
+      tc::mbar_wait(tc::smem_u32(&bar_drain0), 0, WAIT_CYCLES);
+    }
   } else {
-    // ======================================================= warpgroup 1: FP64 term sums
-    double acc[TM][K];
+    // ======================================================= warpgroup 1
+    // per-slot sums as unevaluated FP32 pairs hi + lo (about 48 significant bits), added to
+    // with TwoSum on the FP32 pipe; the FP64 pipe (1/64 rate) only forms hi + lo at the end
+    float hi[T][K], lo[T][K];
 #pragma unroll
-    for (int t = 0; t < TM; ++t)
+    for (int t = 0; t < T; ++t)
 #pragma unroll
-      for (int j = 0; j < K; ++j) acc[t][j] = 0.0;
+      for (int j = 0; j < K; ++j) hi[t][j] = lo[t][j] = 0.f;
     bool bad = false;
-    const uint32_t base = tmem + ((uint32_t)(32 * quarter) << 16);
-    for (int it = 0; it < nit; ++it) {
-      bool ok = tc::mbar_wait(b3, (uint32_t)(it & 1), WAIT_CYCLES);
-      if (wg_vote_or(2, !ok || abort_flag)) {
-        bad = true;
-        break;
-      }
-      tc::fence_after_sync();
-      const double cm = ring_c[it & 3];
-      const uint32_t keep = ring_keep[it & 3];
-      float v[TM][K];
+    const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
+    // add term it-1's stage-3 output (tiles `tl`, slots `kp`) into the sums of this
+    // thread's rows; rows of slots that do not keep the term are skipped
+    auto flush = [&](uint32_t tl, uint32_t kp) {
 #pragma unroll
-      for (int t = 0; t < TM; ++t) {
-        if (t < T) {
-          float c[3][K];
+      for (int t = 0; t < T; ++t) {
+        if (!((tl >> t) & 1u)) continue;
+        const uint32_t base = tD3 + lane_off + (uint32_t)(t * 32);
+        float c0[K], c1[K];
+        tc::tmem_ldk<K>(base, c0);
+        tc::tmem_ldk<K>(base + 16u, c1);
+        tc::tmem_ld_wait();
+        const int m3 = t * 128 + quarter * 32 + lane;
+        if (m3 < rows && ((kp >> (m3 / k2)) & 1u)) {
 #pragma unroll
-          for (int p = 0; p < 3; ++p)
-            if (p < P) tc::tmem_ldk<K>(base + (uint32_t)(t * 48 + 16 * p), c[p]);
-          tc::tmem_ld_wait();
-#pragma unroll
-          for (int j = 0; j < K; ++j)
-            v[t][j] = P == 3 ? (c[2][j] + c[1][j]) + c[0][j] : (P == 2 ? c[1][j] + c[0][j] : c[0][j]);
+          for (int j = 0; j < K; ++j) {
+            const float x = c1[j] + c0[j];
+            const float s = hi[t][j] + x;
+            const float bp = s - hi[t][j];
+            lo[t][j] += (hi[t][j] - (s - bp)) + (x - bp);
+            hi[t][j] = s;
+          }
         }
       }
+    };
+    uint32_t prev_tiles = 0, prev_keep = 0;
+    for (int it = 0; it < nit; ++it) {
+      bool ok = tc::mbar_wait_or_abort(bs2, (uint32_t)(it & 1), WAIT_CYCLES, &abort_flag) &&
+                tc::mbar_wait_or_abort(bring, (uint32_t)(it & 1), WAIT_CYCLES, &abort_flag);
+      // the previous term's stage 3 is done: A3 is free and D3 holds its output
+      if (ok && it > 0) ok = tc::mbar_wait_or_abort(bs3, (uint32_t)((it - 1) & 1), WAIT_CYCLES, &abort_flag);
+      if (wg_vote_or(2, !ok || abort_flag)) { bad = true; break; }
+      tc::fence_after_sync();
+      const uint32_t keep = ring_keep[it % RING];
+      const uint32_t tiles = tiles_of(keep);
+      if (it > 0) flush(prev_tiles, prev_keep);
+      // stage-2 output -> stage-3 operand: element [jz][(i, ix, iy)]
+#pragma unroll
+      for (int t = 0; t < T; ++t) {
+        if (!((tiles >> t) & 1u)) continue;
+        float v[K];
+        load_d(tD2, t, v);
+        int m2 = t * 128 + quarter * 32 + lane;
+        if (m2 < rows) {
+          int i = m2 / k2, rem = m2 - i * k2, jz = rem / k, ix = rem - jz * k;
+          store_run(A3, i * k2 + ix * k, jz, v);
+        }
+      }
+      tc::fence_proxy_async_smem();
       tc::fence_before_sync();
       wg_sync(2);
-      if (tid == 128) mbar_arrive(bfree);  // D may take stage 1 of the next term
-#pragma unroll
-      for (int t = 0; t < TM; ++t) {
-        int m3 = t * 128 + quarter * 32 + lane;
-        if (t < T && m3 < rows && ((keep >> (m3 / k2)) & 1u)) {
-#pragma unroll
-          for (int j = 0; j < K; ++j) acc[t][j] = fma(cm, widen(v[t][j]), acc[t][j]);
+      if (tid == 128) {
+        mbar_arrive(bd2free);  // D2 may take the next term's stage 2
+        const int b = it % NBUF;
+        const unsigned char *B3 = Bt + b * BTERM_BYTES + 2 * BSTAGE_BYTES;
+        bool okb = tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[b]), (uint32_t)((it / NBUF) & 1), WAIT_CYCLES, &abort_flag);
+        if (okb) {
+          tc::fence_after_sync();
+          // ---- stage 3: rows (i, ix, iy), contraction jz, B = c_m R_z pieces.  Column
+          // group 0 gets x0 y0 alone, group 1 the other products x_p y_q with p + q < P,
+          // so the small products are summed among themselves
+          for (int t = 0; t < T; ++t) {
+            if (!((tiles >> t) & 1u)) continue;
+            const uint32_t d = tD3 + (uint32_t)(t * 32);
+            tc::mma_bf16(d, adesc(A3, 0, t), bdesc(B3), idesc_n[1], 0u);                  // x0 [y0 y1]
+            tc::mma_bf16(d + 16u, adesc(A3, 1, t), bdesc(B3), idesc_n[0], 1u);            // x1 y0
+            if (P == 3) {
+              tc::mma_bf16(d + 16u, adesc(A3, 1, t), bdesc(B3 + BPIECE_BYTES), idesc_n[0], 1u);      // x1 y1
+              tc::mma_bf16(d + 16u, adesc(A3, 2, t), bdesc(B3), idesc_n[0], 1u);                     // x2 y0
+              tc::mma_bf16(d + 16u, adesc(A3, 0, t), bdesc(B3 + 2 * BPIECE_BYTES), idesc_n[0], 1u);  // x0 y2
+            }
+          }
+          tc::mma_commit(bs3);
+          tc::mma_commit(tc::smem_u32(&bar_bfree[b]));
+        } else {
+          abort_flag = 1;
         }
+      }
+      prev_tiles = tiles;
+      prev_keep = keep;
+    }
+    if (!bad && nit > 0) {
+      bool ok = tc::mbar_wait_or_abort(bs3, (uint32_t)((nit - 1) & 1), WAIT_CYCLES, &abort_flag);
+      if (wg_vote_or(2, !ok || abort_flag)) {
+        bad = true;
+      } else {
+        tc::fence_after_sync();
+        flush(prev_tiles, prev_keep);
       }
     }
     if (bad) abort_flag = 1;
     // write the destinations: row (i, ix, iy), columns iz
     if (!bad) {
 #pragma unroll
-      for (int t = 0; t < TM; ++t) {
+      for (int t = 0; t < T; ++t) {
         int m3 = t * 128 + quarter * 32 + lane;
-        if (t < T && m3 < rows) {
+        if (m3 < rows) {
           int i = m3 / k2, rem = m3 - i * k2;
           int64_t dst = (int64_t)tile * G + i;
           if (dst < a.n_dest) {
             double *o = a.out_coeffs + dst * k3 + (int64_t)rem * k;
 #pragma unroll
-            for (int j = 0; j < K; ++j) o[j] = acc[t][j];
+            for (int j = 0; j < K; ++j) o[j] = (double)hi[t][j] + (double)lo[t][j];
             if (rem == 0) a.out_keys[dst] = a.dest_key[dst];
           }
         }
       }
     }
+    if (tid == 128) {
+      tc::mma_commit(tc::smem_u32(&bar_drain1));
+      tc::mbar_wait(tc::smem_u32(&bar_drain1), 0, WAIT_CYCLES);
+    }
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (abort_flag) {
-    // let any copy or MMA still in flight finish before the tensor memory is released: a
-    // commit tracks every tcgen05 operation this thread issued before it
-    if (tid == 0) {
-      atomicExch(a.err, 1);
-      tc::mma_commit(tc::smem_u32(&bar_drain));
-      tc::mbar_wait(tc::smem_u32(&bar_drain), 0, WAIT_CYCLES);
-    }
-    __syncthreads();
-  }
-  if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols_for(K, V));
+  if (abort_flag && tid == 0) atomicExch(a.err, 1);
+  if (warp == 0) tc::tmem_dealloc(tmem, NCOL);
 }
 
 // ---------------------------------------------------------------- work-list kernels
@@ -544,16 +594,19 @@ __global__ void group_bounds_kernel(int64_t P, const uint64_t *key2s, const int 
 }
 
 // Block pieces in the K-major core-matrix layout the MMA reads: piece p of block
-// R (N = output index i, K = input index j), element (i, j) at
-// p*512 + (i/8)*256 + (j/8)*128 + (i%8)*16 + (j%8)*2; zero outside k x k.
-__global__ void split_blocks_kernel(int64_t n_blocks, int k, const double *R, unsigned char *out) {
+// x R (N = output index i, K = input index j), element (i, j) at
+// p*512 + (i/8)*256 + (j/8)*128 + (i%8)*16 + (j%8)*2; zero outside k x k.  Blocks are
+// numbered m * nl + (l + D) within one level; x = c[m] when c is given, else 1.
+__global__ void split_blocks_kernel(int64_t n_blocks, int k, int nl, const double *c, const double *R,
+                                    unsigned char *out) {
   int64_t blk = blockIdx.x;
   if (blk >= n_blocks) return;
+  const double x = c ? c[blk / nl] : 1.0;
   for (int e = threadIdx.x; e < 256; e += blockDim.x) {
     int i = e / 16, j = e % 16;
-    double x = (i < k && j < k) ? R[blk * k * k + i * k + j] : 0.0;
+    double y = (i < k && j < k) ? x * R[blk * k * k + i * k + j] : 0.0;
     __nv_bfloat16 p0, p1, p2;
-    split3(x, p0, p1, p2);
+    split3(y, p0, p1, p2);
     uint32_t off = (i / 8) * 256 + (j / 8) * 128 + (i % 8) * 16 + (j % 8) * 2;
     unsigned char *b = out + blk * BSTAGE_BYTES;
     *(__nv_bfloat16 *)(b + off) = p0;
@@ -578,10 +631,19 @@ size_t split_workspace_bytes(int64_t P) {
 
 int split_blocks_build(Operator &op, cudaStream_t s) {
   if (op.d_Rsplit) return MRA_OK;
-  MRA_CUDA_TRY(cudaMalloc(&op.d_Rsplit, (size_t)op.n_blocks * BSTAGE_BYTES));
-  split_blocks_kernel<<<(unsigned)op.n_blocks, 128, 0, s>>>(op.n_blocks, op.k, op.d_R,
-                                                            (unsigned char *)op.d_Rsplit);
-  MRA_CUDA_TRY(cudaGetLastError());
+  // two tables: the blocks R (stages 1 and 2) and c_m R (stage 3)
+  MRA_CUDA_TRY(cudaMalloc(&op.d_Rsplit, (size_t)2 * op.n_blocks * BSTAGE_BYTES));
+  unsigned char *plain = (unsigned char *)op.d_Rsplit;
+  unsigned char *scaled = plain + (size_t)op.n_blocks * BSTAGE_BYTES;
+  for (size_t li = 0; li < op.D.size(); ++li) {
+    const int nl = 2 * op.D[li] + 1;
+    const int64_t nb = (int64_t)op.M * nl, base = op.level_off[li];
+    if (nb <= 0) continue;
+    const double *R = op.d_R + base * op.k * op.k;
+    split_blocks_kernel<<<(unsigned)nb, 128, 0, s>>>(nb, op.k, nl, nullptr, R, plain + base * BSTAGE_BYTES);
+    split_blocks_kernel<<<(unsigned)nb, 128, 0, s>>>(nb, op.k, nl, op.d_c, R, scaled + base * BSTAGE_BYTES);
+    MRA_CUDA_TRY(cudaGetLastError());
+  }
   return MRA_OK;
 }
 
@@ -591,10 +653,9 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
   if (!op.d_Rsplit) return fail(MRA_ERR_ARG, "mra_apply: operator has no split blocks");
   const int k = op.k;
   if (k & 1) return fail(MRA_ERR_UNSUPPORTED, "split apply: odd k=%d not supported (use MRA_PREC_FP64)", k);
-  const int v = (o.tile_variant == 1 && (k == 6 || k == 8 || k == 10)) ? 1 : 0;
-  const int G = g_for(k, v);
-  const int T = (G * k * k + 127) / 128;
-  if (T > tm_for(k, v)) return fail(MRA_ERR_UNSUPPORTED, "split apply: tile shape for k=%d", k);
+  const int tt = (o.tile_variant == 1 && k >= 4 && k <= 10) ? 2 : 4;
+  const int G = g_for(k, tt);
+  const int T = t_for(k, tt);  // 128-row tiles per CTA
   const int64_t P = wk.P, nd = wk.n_dest;
   const int n_tiles = (int)((nd + G - 1) / G);
   // carve the split-path workspace
@@ -628,10 +689,8 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
   a.k = k;
   a.M = op.M;
   a.P = o.pieces;
-  a.G = G;
-  a.T = T;
-  a.c = op.d_c;
   a.Bsplit = (const unsigned char *)op.d_Rsplit;
+  a.Bsplit_c = a.Bsplit + (size_t)op.n_blocks * BSTAGE_BYTES;
   a.Dlev = op.d_D;
   a.level_off = op.d_level_off;
   a.in_coeffs = in.coeffs;
@@ -648,20 +707,25 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
   a.out_keys = out.keys;
   a.out_coeffs = out.coeffs;
   a.err = err;
-  size_t smem = (size_t)2 * a.P * T * TILE_BYTES + 6 * BSTAGE_BYTES;
+  size_t smem = (size_t)3 * a.P * T * TILE_BYTES + (size_t)NBUF * BTERM_BYTES;
+  // no more CTAs per SM than the tensor memory holds (512 columns): otherwise an extra
+  // CTA's allocation would wait for a resident CTA to finish
+  const size_t smem_floor = (size_t)233472 / (512 / tmem_cols_for(T) + 1);
+  if (smem < smem_floor) smem = smem_floor;
   void (*kern)(SplitArgs) = nullptr;
-  switch (k * 2 + v) {
-    case 4: kern = apply_split_kernel<2, 0>; break;
-    case 8: kern = apply_split_kernel<4, 0>; break;
-    case 12: kern = apply_split_kernel<6, 0>; break;
-    case 13: kern = apply_split_kernel<6, 1>; break;
-    case 16: kern = apply_split_kernel<8, 0>; break;
-    case 17: kern = apply_split_kernel<8, 1>; break;
-    case 20: kern = apply_split_kernel<10, 0>; break;
-    case 21: kern = apply_split_kernel<10, 1>; break;
-    case 24: kern = apply_split_kernel<12, 0>; break;
-    case 28: kern = apply_split_kernel<14, 0>; break;
-    default: kern = apply_split_kernel<16, 0>; break;
+  switch (k * 8 + tt) {
+    case 2 * 8 + 4: kern = apply_split_kernel<2, 4>; break;
+    case 4 * 8 + 4: kern = apply_split_kernel<4, 4>; break;
+    case 4 * 8 + 2: kern = apply_split_kernel<4, 2>; break;
+    case 6 * 8 + 4: kern = apply_split_kernel<6, 4>; break;
+    case 6 * 8 + 2: kern = apply_split_kernel<6, 2>; break;
+    case 8 * 8 + 4: kern = apply_split_kernel<8, 4>; break;
+    case 8 * 8 + 2: kern = apply_split_kernel<8, 2>; break;
+    case 10 * 8 + 4: kern = apply_split_kernel<10, 4>; break;
+    case 10 * 8 + 2: kern = apply_split_kernel<10, 2>; break;
+    case 12 * 8 + 4: kern = apply_split_kernel<12, 4>; break;
+    case 14 * 8 + 4: kern = apply_split_kernel<14, 4>; break;
+    default: kern = apply_split_kernel<16, 4>; break;
   }
   MRA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   MRA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));

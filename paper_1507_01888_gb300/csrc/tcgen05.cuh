@@ -34,6 +34,23 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long lon
   }
 }
 
+// As mbar_wait, and also gives up (returns false) once *abort is set by another thread.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t phase, long long max_cycles,
+                                                   const volatile int *abort) {
+  long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    if (done) return true;
+    if (*abort || clock64() - t0 > max_cycles) return false;
+  }
+}
+
 // ---------------------------------------------------------------- fences
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

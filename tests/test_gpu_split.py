@@ -64,9 +64,9 @@ def test_split_random_trees_ragged(mra, k, lev, nbox, seed):
     assert cmp["rel_l2"] <= TOL_MIXED
 
 
-@pytest.mark.parametrize("k,lev,nbox,seed", [(6, 3, 200, 31), (8, 3, 150, 32), (10, 3, 90, 33)])
-def test_split_wide_tile_variant(mra, k, lev, nbox, seed):
-    """Tile variant 1 (seven 128-row tiles, one CTA per SM) equals the oracle like variant 0."""
+@pytest.mark.parametrize("k,lev,nbox,seed", [(4, 3, 300, 30), (6, 3, 200, 31), (8, 3, 150, 32), (10, 3, 90, 33)])
+def test_split_tile_variants(mra, k, lev, nbox, seed):
+    """Tile variant 1 (two 128-row tiles per CTA, two CTAs per SM) equals the oracle like variant 0."""
     keys, coeffs = W.random_tree_coeffs(nbox, k, lev, seed=seed)
     op = mra.Operator(0, 16, k, 16.0, 0, lev, max_disp=1, fit_eps=1e-4)
     fit = op.fit()
