@@ -121,7 +121,8 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // G k^2 operand rows fill T <= TT tiles of 128 rows.  Tensor memory holds the stage-1
 // and stage-2 outputs (48 columns per tile each: three 16-column piece groups) and the
 // stage-3 output (32 columns per tile: two groups): 128 T columns.  TT = 4 takes the whole
-// tensor memory (one CTA per SM); TT = 2 leaves room for a second CTA on the SM.
+// tensor memory (one CTA per SM); TT = 2 leaves room for a second CTA on the SM and TT = 1
+// for three (then shared memory is the limit).
 __host__ __device__ constexpr int g_for(int k, int tt) {
   return (128 * tt) / (k * k) > MAX_G ? MAX_G : (128 * tt) / (k * k);
 }
@@ -161,7 +162,7 @@ __device__ __forceinline__ void split_pair(float x, float y, __nv_bfloat162 &h0,
 // by the stage-3 MMAs that read it.  Each wait is bounded and gives up when the other
 // warpgroup has aborted.
 template <int K, int TT>
-__global__ void __launch_bounds__(SPLIT_THREADS, 4 / TT) apply_split_kernel(SplitArgs a) {
+__global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_split_kernel(SplitArgs a) {
   constexpr int k = K, k2 = K * K, k3 = K * K * K;
   constexpr int G = g_for(K, TT), rows = G * k2, T = t_for(K, TT);
   constexpr uint32_t NCOL = tmem_cols_for(T);
@@ -653,7 +654,7 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
   if (!op.d_Rsplit) return fail(MRA_ERR_ARG, "mra_apply: operator has no split blocks");
   const int k = op.k;
   if (k & 1) return fail(MRA_ERR_UNSUPPORTED, "split apply: odd k=%d not supported (use MRA_PREC_FP64)", k);
-  const int tt = (o.tile_variant == 1 && k >= 4 && k <= 10) ? 2 : 4;
+  const int tt = (k >= 4 && k <= 10 && o.tile_variant == 1) ? 2 : (k >= 4 && k <= 10 && o.tile_variant == 2) ? 1 : 4;
   const int G = g_for(k, tt);
   const int T = t_for(k, tt);  // 128-row tiles per CTA
   const int64_t P = wk.P, nd = wk.n_dest;
@@ -717,12 +718,16 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
     case 2 * 8 + 4: kern = apply_split_kernel<2, 4>; break;
     case 4 * 8 + 4: kern = apply_split_kernel<4, 4>; break;
     case 4 * 8 + 2: kern = apply_split_kernel<4, 2>; break;
+    case 4 * 8 + 1: kern = apply_split_kernel<4, 1>; break;
     case 6 * 8 + 4: kern = apply_split_kernel<6, 4>; break;
     case 6 * 8 + 2: kern = apply_split_kernel<6, 2>; break;
+    case 6 * 8 + 1: kern = apply_split_kernel<6, 1>; break;
     case 8 * 8 + 4: kern = apply_split_kernel<8, 4>; break;
     case 8 * 8 + 2: kern = apply_split_kernel<8, 2>; break;
+    case 8 * 8 + 1: kern = apply_split_kernel<8, 1>; break;
     case 10 * 8 + 4: kern = apply_split_kernel<10, 4>; break;
     case 10 * 8 + 2: kern = apply_split_kernel<10, 2>; break;
+    case 10 * 8 + 1: kern = apply_split_kernel<10, 1>; break;
     case 12 * 8 + 4: kern = apply_split_kernel<12, 4>; break;
     case 14 * 8 + 4: kern = apply_split_kernel<14, 4>; break;
     default: kern = apply_split_kernel<16, 4>; break;
