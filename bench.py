@@ -226,9 +226,12 @@ def main():
     opts = mra.make_opts(precision=prec, pieces=args.pieces, screen=screen, tau=w.tau, stencil=w.stencil,
                          max_disp=w.max_disp)
     tuning = {}
-    if prec == mra.PREC_SPLIT_BF16 and not batched:
+    if prec == mra.PREC_SPLIT_BF16:
         from paper_1507_01888_gb300 import autotune
-        opts, table = autotune.tune(op, tree, opts)
+
+        def batched_applier(o):
+            return mra.BatchedApplier(op, tree, offsets, o)
+        opts, table = autotune.tune(op, tree, opts, make_applier=batched_applier if batched else None)
         tuning = {"tile_variant": opts.tile_variant, "candidates_ms": table}
 
     def make_applier(o):

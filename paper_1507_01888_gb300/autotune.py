@@ -20,9 +20,15 @@ def candidates(k: int):
     return [0, 1, 2] if 4 <= k <= 10 else [0]
 
 
-def tune(op, tree, opts, repeats: int = 3, verbose: bool = False):
-    """Returns a copy of opts with tile_variant set, and the timing table (ms per variant)."""
-    key = (op.k, tree.n.bit_length(), opts.precision, opts.pieces)
+def tune(op, tree, opts, repeats: int = 3, verbose: bool = False, make_applier=None):
+    """Returns a copy of opts with tile_variant set, and the timing table (ms per variant).
+
+    make_applier(opts) builds the applier to time (default: mra.Applier on `tree`; pass one
+    that builds a mra.BatchedApplier to tune a batched apply)."""
+    if make_applier is None:
+        def make_applier(o):
+            return mra.Applier(op, tree, o)
+    key = (op.k, tree.n.bit_length(), opts.precision, opts.pieces, make_applier.__name__)
     table = {}
     if key in _cache:
         best = _cache[key]
@@ -32,7 +38,7 @@ def tune(op, tree, opts, repeats: int = 3, verbose: bool = False):
             o.tile_variant = v
             if getattr(opts, "_mlp_ref", None) is not None:
                 o._mlp_ref = opts._mlp_ref
-            ap = mra.Applier(op, tree, o)
+            ap = make_applier(o)
             ap(tree)  # warm-up
             ms = []
             for _ in range(repeats):

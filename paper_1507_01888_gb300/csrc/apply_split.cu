@@ -238,8 +238,8 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
   const uint32_t bs1 = tc::smem_u32(&bar_s1), bs2 = tc::smem_u32(&bar_s2), bs3 = tc::smem_u32(&bar_s3);
   const uint32_t bring = tc::smem_u32(&bar_ring), bd2free = tc::smem_u32(&bar_d2free);
   const int nit = total_it;
-  const uint32_t idesc_n[3] = {tc::idesc_bf16(128, 16, 1, 0), tc::idesc_bf16(128, 32, 1, 0),
-                               tc::idesc_bf16(128, 48, 1, 0)};
+  // instruction descriptor of an M=128 x N x 16 MMA (A MN-major, B K-major), N = 16 n
+  auto idesc_n = [](int n) { return tc::idesc_bf16(128, 16 * n, 1, 0); };
   auto tiles_of = [&](uint32_t keep) -> uint32_t {
     uint32_t tl = 0;
 #pragma unroll
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
     for (int t = 0; t < T; ++t) {
       if (!((tiles >> t) & 1u)) continue;
       for (int p = 0; p < P; ++p)
-        tc::mma_bf16(d + (uint32_t)(t * 48 + 16 * p), adesc(A, p, t), bdesc(B), idesc_n[P - 1 - p], p > 0 ? 1u : 0u);
+        tc::mma_bf16(d + (uint32_t)(t * 48 + 16 * p), adesc(A, p, t), bdesc(B), idesc_n(P - p), p > 0 ? 1u : 0u);
     }
   };
   // element [contraction a][row (i, b, d)] for d = 0..k-1 of this thread's row, into operand A
@@ -387,7 +387,8 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
           }
           if (!ok) abort_flag = 1;
         }
-        bool ok = tc::mbar_wait_or_abort(bs1, p1, WAIT_CYCLES, &abort_flag);
+        // one warp polls the barrier; the others sleep in the vote
+        bool ok = quarter != 0 || tc::mbar_wait_or_abort(bs1, p1, WAIT_CYCLES, &abort_flag);
         p1 ^= 1u;
         if (wg_vote_or(1, !ok || abort_flag)) { bad = true; break; }
         tc::fence_after_sync();
@@ -467,10 +468,14 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
     };
     uint32_t prev_tiles = 0, prev_keep = 0;
     for (int it = 0; it < nit; ++it) {
-      bool ok = tc::mbar_wait_or_abort(bs2, (uint32_t)(it & 1), WAIT_CYCLES, &abort_flag) &&
-                tc::mbar_wait_or_abort(bring, (uint32_t)(it & 1), WAIT_CYCLES, &abort_flag);
-      // the previous term's stage 3 is done: A3 is free and D3 holds its output
-      if (ok && it > 0) ok = tc::mbar_wait_or_abort(bs3, (uint32_t)((it - 1) & 1), WAIT_CYCLES, &abort_flag);
+      // one warp polls the barriers; the others sleep in the vote.  Then the previous
+      // term's stage 3 is done too: A3 is free and D3 holds its output
+      bool ok = true;
+      if (quarter == 0) {
+        ok = tc::mbar_wait_or_abort(bs2, (uint32_t)(it & 1), WAIT_CYCLES, &abort_flag) &&
+             tc::mbar_wait_or_abort(bring, (uint32_t)(it & 1), WAIT_CYCLES, &abort_flag);
+        if (ok && it > 0) ok = tc::mbar_wait_or_abort(bs3, (uint32_t)((it - 1) & 1), WAIT_CYCLES, &abort_flag);
+      }
       if (wg_vote_or(2, !ok || abort_flag)) { bad = true; break; }
       tc::fence_after_sync();
       const uint32_t keep = ring_keep[it % RING];
@@ -504,12 +509,12 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
           for (int t = 0; t < T; ++t) {
             if (!((tiles >> t) & 1u)) continue;
             const uint32_t d = tD3 + (uint32_t)(t * 32);
-            tc::mma_bf16(d, adesc(A3, 0, t), bdesc(B3), idesc_n[1], 0u);                  // x0 [y0 y1]
-            tc::mma_bf16(d + 16u, adesc(A3, 1, t), bdesc(B3), idesc_n[0], 1u);            // x1 y0
+            tc::mma_bf16(d, adesc(A3, 0, t), bdesc(B3), idesc_n(2), 0u);                  // x0 [y0 y1]
+            tc::mma_bf16(d + 16u, adesc(A3, 1, t), bdesc(B3), idesc_n(1), 1u);            // x1 y0
             if (P == 3) {
-              tc::mma_bf16(d + 16u, adesc(A3, 1, t), bdesc(B3 + BPIECE_BYTES), idesc_n[0], 1u);      // x1 y1
-              tc::mma_bf16(d + 16u, adesc(A3, 2, t), bdesc(B3), idesc_n[0], 1u);                     // x2 y0
-              tc::mma_bf16(d + 16u, adesc(A3, 0, t), bdesc(B3 + 2 * BPIECE_BYTES), idesc_n[0], 1u);  // x0 y2
+              tc::mma_bf16(d + 16u, adesc(A3, 1, t), bdesc(B3 + BPIECE_BYTES), idesc_n(1), 1u);      // x1 y1
+              tc::mma_bf16(d + 16u, adesc(A3, 2, t), bdesc(B3), idesc_n(1), 1u);                     // x2 y0
+              tc::mma_bf16(d + 16u, adesc(A3, 0, t), bdesc(B3 + 2 * BPIECE_BYTES), idesc_n(1), 1u);  // x0 y2
             }
           }
           tc::mma_commit(bs3);
@@ -522,7 +527,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
       prev_keep = keep;
     }
     if (!bad && nit > 0) {
-      bool ok = tc::mbar_wait_or_abort(bs3, (uint32_t)((nit - 1) & 1), WAIT_CYCLES, &abort_flag);
+      bool ok = quarter != 0 || tc::mbar_wait_or_abort(bs3, (uint32_t)((nit - 1) & 1), WAIT_CYCLES, &abort_flag);
       if (wg_vote_or(2, !ok || abort_flag)) {
         bad = true;
       } else {
