@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU seconds of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--clocks-csv", default=None, help="also write the nvidia-smi samples here")
+    p.add_argument("--learned-quantile", type=float, default=1.0,
+                   help="learned-screen margin: this quantile of the held-out residuals (1 = largest)")
     return p.parse_args()
 
 
@@ -220,11 +222,26 @@ def main():
         tree, offsets = trees[0], [0, trees[0].n]
     keys_h, coeffs_h = tree.host()
     levels = (keys_h >> np.uint64(57)).astype(int)
-    op = mra.Operator(w.kernel, w.M, w.k, w.L, int(levels.min()), int(levels.max()), max_disp=w.max_disp,
-                      mu=w.mu, fit_eps=w.fit_eps)
+    train_trees = [mra.project(f, w.k, w.L, thresh=w.thresh, init_level=w.init_level, max_level=w.max_level,
+                               uniform_level=w.uniform_level) for f in w.extra.get("train_funcs", [])]
+    lev_lo, lev_hi = int(levels.min()), int(levels.max())
+    for t in train_trees:
+        tl = (t.host()[0] >> np.uint64(57)).astype(int)
+        lev_lo, lev_hi = min(lev_lo, int(tl.min())), max(lev_hi, int(tl.max()))
+    op = mra.Operator(w.kernel, w.M, w.k, w.L, lev_lo, lev_hi, max_disp=w.max_disp, mu=w.mu, fit_eps=w.fit_eps)
     screen = mra.SCREEN_NORM if w.tau > 0 else mra.SCREEN_NONE
     opts = mra.make_opts(precision=prec, pieces=args.pieces, screen=screen, tau=w.tau, stencil=w.stencil,
                          max_disp=w.max_disp)
+    learned_cfg = None
+    if train_trees:  # learned screen: train the network on terms logged from the training functions
+        from paper_1507_01888_gb300 import learned
+        model, linfo = learned.train_screen(op, train_trees, opts, terms_per_tree=20000, steps=2000,
+                                            batch=1024, lr=3e-3, seed=0, quantile=args.learned_quantile)
+        opts = mra.make_opts(precision=prec, pieces=args.pieces, screen=mra.SCREEN_LEARNED, tau=w.tau,
+                             stencil=w.stencil, max_disp=w.max_disp, mlp=model, delta=linfo["delta"])
+        learned_cfg = {"training_functions": len(train_trees), "logged_terms": linfo["n_train"] + linfo["n_val"],
+                       "final_loss": linfo["final_loss"], "delta": linfo["delta"], "quantile": args.learned_quantile}
+        del train_trees
     tuning = {}
     if prec == mra.PREC_SPLIT_BF16:
         from paper_1507_01888_gb300 import autotune
@@ -376,6 +393,9 @@ def main():
                        "terms_kept": terms, "pairs": st0["pairs"], "n_out": st0["n_out"],
                        "precision": precision, "l2": "flushed by a 256 MB write before every step",
                        "functions": len(trees), "tuning": tuning,
+                       **({"learned_screen": dict(learned_cfg, terms_skipped=st0["terms_learned_skipped"],
+                                                  skipped_bound=st0["learned_skipped_bound"])}
+                          if learned_cfg else {}),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roof, "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
             "e2e": {"value": e2e_val, "unit": "boxes/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -103,8 +103,8 @@ typedef struct {
   const float *mlp; /* MRA_SCREEN_LEARNED: device model, MRA_MLP_PARAMS floats */
   double delta;     /* MRA_SCREEN_LEARNED: safety margin in log10 units */
   int tile_variant; /* MRA_PREC_SPLIT_BF16 tile shape: 0 = four 128-row tiles per CTA (one CTA
-                       per SM); for k = 4 to 10 also 1 = two tiles per CTA (two CTAs per SM)
-                       and 2 = one tile per CTA (three CTAs per SM); others are taken as 0 */
+                       per SM); 1 (k >= 4) = two tiles per CTA (two CTAs per SM); 2 (k = 4 to
+                       10) = one tile per CTA (three CTAs per SM); others are taken as 0 */
 } mra_apply_opts;
 
 typedef struct {

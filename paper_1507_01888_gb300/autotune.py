@@ -1,9 +1,9 @@
 """Autotuner for the tensor-core apply: picks the tile shape by timing the library's apply
 kernel on the caller's own input.
 
-The library compiles, for k = 4 to 10, three tile shapes: four 128-row tiles per CTA with
-one CTA per SM (variant 0, the whole tensor memory), two tiles per CTA with two CTAs per
-SM (variant 1) and one tile per CTA with three CTAs per SM (variant 2).  Wider tiles gather
+The library compiles up to three tile shapes: four 128-row tiles per CTA with one CTA per
+SM (variant 0, the whole tensor memory), two tiles per CTA with two CTAs per SM (variant 1,
+k >= 4) and one tile per CTA with three CTAs per SM (variant 2, k = 4 to 10).  Wider tiles gather
 more destinations per group, so one MMA serves more boxes; more CTAs per SM keep the
 tensor pipe busy while a CTA waits on its own chain of stages.  Which wins depends on the tree, so the tuner times each variant (device time
 of the apply kernel, CUDA events inside the library), keeps the fastest, and caches the
@@ -17,7 +17,7 @@ _cache: dict = {}
 
 
 def candidates(k: int):
-    return [0, 1, 2] if 4 <= k <= 10 else [0]
+    return [0, 1, 2] if 4 <= k <= 10 else ([0, 1] if k >= 12 else [0])
 
 
 def tune(op, tree, opts, repeats: int = 3, verbose: bool = False, make_applier=None):

@@ -86,19 +86,6 @@ struct SplitArgs {
   int *err;
 };
 
-// Exact widening of an FP32 value to FP64 with integer operations (IEEE layouts:
-// 8-bit exponent bias 127 -> 11-bit bias 1023, 23-bit -> 52-bit fraction), so that
-// only the multiply-add of the term sum uses the FP64 pipe.  FP32 subnormals
-// (|x| < 1.2e-38) become zero.
-__device__ __forceinline__ double widen(float f) {
-  uint32_t u = __float_as_uint(f);
-  uint32_t e = (u >> 23) & 0xFFu;
-  uint64_t sign = (uint64_t)(u >> 31) << 63;
-  if (e == 0) return __longlong_as_double((long long)sign);
-  uint64_t ee = (e == 0xFFu) ? 2047u : (uint64_t)(e + 896u);
-  return __longlong_as_double((long long)(sign | (ee << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29)));
-}
-
 // Named barrier over one warpgroup (128 threads) with an OR vote.
 __device__ __forceinline__ bool wg_vote_or(int barrier_id, bool flag) {
   uint32_t out;
@@ -263,14 +250,35 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
   // element [contraction a][row (i, b, d)] for d = 0..k-1 of this thread's row, into operand A
   auto store_run = [&](unsigned char *A, int mrow, int a_idx, const float *v) {
     const int stride = T * TILE_BYTES;
+    if constexpr (K % 8 == 0) {
+      // mrow is a multiple of 8: each run of 8 rows is one 16-byte core-matrix row, written
+      // with one vector store per piece (lanes of a quarter warp then hit distinct banks)
 #pragma unroll
-    for (int d = 0; d < K; d += 2) {
-      __nv_bfloat162 h0, h1, h2;
-      split_pair(v[d], v[d + 1], h0, h1, h2);
-      uint32_t off = a_off(mrow + d, a_idx);
-      *(__nv_bfloat162 *)(A + off) = h0;
-      *(__nv_bfloat162 *)(A + stride + off) = h1;
-      if (P > 2) *(__nv_bfloat162 *)(A + 2 * stride + off) = h2;
+      for (int d0 = 0; d0 < K; d0 += 8) {
+        uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          __nv_bfloat162 h0, h1, h2;
+          split_pair(v[d0 + 2 * h], v[d0 + 2 * h + 1], h0, h1, h2);
+          w0[h] = *(uint32_t *)&h0;
+          w1[h] = *(uint32_t *)&h1;
+          w2[h] = *(uint32_t *)&h2;
+        }
+        uint32_t off = a_off(mrow + d0, a_idx);
+        *(uint4 *)(A + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+        *(uint4 *)(A + stride + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+        if (P > 2) *(uint4 *)(A + 2 * stride + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+      }
+    } else {
+#pragma unroll
+      for (int d = 0; d < K; d += 2) {
+        __nv_bfloat162 h0, h1, h2;
+        split_pair(v[d], v[d + 1], h0, h1, h2);
+        uint32_t off = a_off(mrow + d, a_idx);
+        *(__nv_bfloat162 *)(A + off) = h0;
+        *(__nv_bfloat162 *)(A + stride + off) = h1;
+        if (P > 2) *(__nv_bfloat162 *)(A + 2 * stride + off) = h2;
+      }
     }
   };
   // the first K columns of each of the P piece groups of tile t, summed smallest first
@@ -659,7 +667,7 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
   if (!op.d_Rsplit) return fail(MRA_ERR_ARG, "mra_apply: operator has no split blocks");
   const int k = op.k;
   if (k & 1) return fail(MRA_ERR_UNSUPPORTED, "split apply: odd k=%d not supported (use MRA_PREC_FP64)", k);
-  const int tt = (k >= 4 && k <= 10 && o.tile_variant == 1) ? 2 : (k >= 4 && k <= 10 && o.tile_variant == 2) ? 1 : 4;
+  const int tt = (k >= 4 && o.tile_variant == 1) ? 2 : (k >= 4 && k <= 10 && o.tile_variant == 2) ? 1 : 4;
   const int G = g_for(k, tt);
   const int T = t_for(k, tt);  // 128-row tiles per CTA
   const int64_t P = wk.P, nd = wk.n_dest;
@@ -733,8 +741,11 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
     case 10 * 8 + 4: kern = apply_split_kernel<10, 4>; break;
     case 10 * 8 + 2: kern = apply_split_kernel<10, 2>; break;
     case 10 * 8 + 1: kern = apply_split_kernel<10, 1>; break;
+    case 12 * 8 + 2: kern = apply_split_kernel<12, 2>; break;
     case 12 * 8 + 4: kern = apply_split_kernel<12, 4>; break;
+    case 14 * 8 + 2: kern = apply_split_kernel<14, 2>; break;
     case 14 * 8 + 4: kern = apply_split_kernel<14, 4>; break;
+    case 16 * 8 + 2: kern = apply_split_kernel<16, 2>; break;
     default: kern = apply_split_kernel<16, 4>; break;
   }
   MRA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -64,7 +64,8 @@ def test_split_random_trees_ragged(mra, k, lev, nbox, seed):
     assert cmp["rel_l2"] <= TOL_MIXED
 
 
-@pytest.mark.parametrize("k,lev,nbox,seed", [(4, 3, 300, 30), (6, 3, 200, 31), (8, 3, 150, 32), (10, 3, 90, 33)])
+@pytest.mark.parametrize("k,lev,nbox,seed", [(4, 3, 300, 30), (6, 3, 200, 31), (8, 3, 150, 32), (10, 3, 90, 33),
+                                              (12, 2, 40, 34), (14, 2, 30, 35), (16, 2, 20, 36)])
 def test_split_tile_variants(mra, k, lev, nbox, seed):
     """Tile variants 1 and 2 (two or one 128-row tiles per CTA) equal the oracle like variant 0."""
     keys, coeffs = W.random_tree_coeffs(nbox, k, lev, seed=seed)

@@ -98,10 +98,13 @@ def poisson_batched_64() -> Workload:
 
 
 def bsh_learned_k10() -> Workload:
-    """Learned-screen BSH apply: 32 Gaussians a~logU[1,1e4], k=10, thresh 1e-7, mu=0.5, M=80."""
+    """Learned-screen BSH apply: 32 Gaussians a~logU[1,1e4], k=10, thresh 1e-7, mu=0.5, M=80.
+    The screen's network is trained on terms logged from applies of functions of the same
+    family with seeds 4000, 4001, ... (extra["train_funcs"])."""
+    train = [gaussian_sum(32, 1.0, 1e4, seed=4000 + i) for i in range(4)]
     return Workload("bsh_m80_adaptive_k10_learned", [gaussian_sum(32, 1.0, 1e4, seed=4)], k=10, L=L_CELL,
                     thresh=1e-7, uniform_level=-1, kernel=BSH, mu=0.5, M=80, fit_eps=1e-7, stencil=0,
-                    max_disp=1, tau=1e-9)
+                    max_disp=1, tau=1e-9, extra={"train_funcs": train})
 
 
 def poisson_k14_large() -> Workload:
