@@ -136,10 +136,10 @@ __device__ __forceinline__ void split_pair(float x, float y, __nv_bfloat162 &h0,
 
 // Warp roles and the term pipeline.  Terms of a group flow through three MMA stages:
 //   warpgroup 0 (warps 0-3) stages each group's sources (A1), turns the stage-1 output
-//     D1 into the stage-2 operand A2; its thread 0 issues the block copies and the
-//     stage-1 and stage-2 MMAs;
+//     D1 into the stage-2 operand A2; its threads 0, 32 and 64 issue the stage-1 MMAs, the
+//     block copies and the stage-2 MMAs;
 //   warpgroup 1 (warps 4-7) turns the stage-2 output D2 into the stage-3 operand A3; its
-//     thread 128 issues the stage-3 MMAs into D3 (the coefficient c_m is folded into the
+//     thread 160 issues the stage-3 MMAs into D3 (the coefficient c_m is folded into the
 //     stage-3 blocks); while the next term's stage 2 runs it adds D3 into the per-slot
 //     sums, for the slots that keep the term.
 // So warpgroup 0 works on term j+1 while warpgroup 1 works on term j.  Tiles of 128 rows
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
   unsigned char *A2 = A1 + ptile;        // [P][T] tiles: stage-2 operand
   unsigned char *A3 = A2 + ptile;        // [P][T] tiles: stage-3 operand
   unsigned char *Bt = A3 + ptile;        // [NBUF][3 stages][1536]: the blocks of a term
-  __shared__ __align__(8) uint64_t bar_s1, bar_s2, bar_s3, bar_ring, bar_d2free, bar_drain0, bar_drain1;
+  __shared__ __align__(8) uint64_t bar_s1, bar_s2, bar_s3, bar_ring, bar_d2free, bar_drain0, bar_drain1, bar_drain2;
   __shared__ __align__(8) uint64_t bar_bb[NBUF], bar_bfree[NBUF];
   __shared__ uint32_t tmem_holder;
   __shared__ int slot_src[MAX_G];
@@ -189,6 +189,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
     tc::mbar_init(tc::smem_u32(&bar_d2free), 1);
     tc::mbar_init(tc::smem_u32(&bar_drain0), 1);
     tc::mbar_init(tc::smem_u32(&bar_drain1), 1);
+    tc::mbar_init(tc::smem_u32(&bar_drain2), 1);
     for (int b = 0; b < NBUF; ++b) {
       tc::mbar_init(tc::smem_u32(&bar_bb[b]), 1);
       tc::mbar_init(tc::smem_u32(&bar_bfree[b]), 1);
@@ -282,23 +283,31 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
     }
   };
   // the first K columns of each of the P piece groups of tile t, summed smallest first
+  // (groups P-1 and P-2 first, then group 0: two loads in flight at a time)
   auto load_d = [&](uint32_t dbase, int t, float *v) {
     const uint32_t base = dbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(t * 48);
-    float c[3][K];
+    float c[2][K];
+    if (P == 3) {
+      tc::tmem_ldk<K>(base + 32u, c[0]);
+      tc::tmem_ldk<K>(base + 16u, c[1]);
+      tc::tmem_ld_wait();
 #pragma unroll
-    for (int p = 0; p < 3; ++p)
-      if (p < P) tc::tmem_ldk<K>(base + (uint32_t)(16 * p), c[p]);
+      for (int j = 0; j < K; ++j) v[j] = c[0][j] + c[1][j];
+    } else {
+      tc::tmem_ldk<K>(base + 16u, v);
+      tc::tmem_ld_wait();
+    }
+    tc::tmem_ldk<K>(base, c[0]);
     tc::tmem_ld_wait();
 #pragma unroll
-    for (int j = 0; j < K; ++j)
-      v[j] = P == 3 ? (c[2][j] + c[1][j]) + c[0][j] : (P == 2 ? c[1][j] + c[0][j] : c[0][j]);
+    for (int j = 0; j < K; ++j) v[j] += c[0][j];
   };
 
   if (wg == 0) {
     // ======================================================= warpgroup 0
     uint32_t p1 = 0;
     int it = 0;
-    int nfetch = 0, nwaited = 0;  // block copies issued / waited for (thread 0)
+    int nfetch = 0;  // block copies issued (thread 32), for iterations 0 .. nfetch-1 in order
     bool bad = false;
     // copies of the three blocks (m; lx, ly, lz) of iteration `i` into buffer i % NBUF, once
     // the stage-3 MMAs of iteration i - NBUF (the buffer's previous user) are done
@@ -348,7 +357,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
       const int Dop = a.Dlev[lev], nl = 2 * Dop + 1;
       const int ldx = (lp & 255) - 128, ldy = ((lp >> 8) & 255) - 128, ldz = ((lp >> 16) & 255) - 128;
       const int64_t lbase = a.level_off[lev];
-      if (tid == 0) {  // the group's terms in ascending order; blocks of its first two terms
+      if (tid == 32) {  // the group's terms in ascending order; blocks of its first two terms
         int n = 0;
         uint64_t b0 = uni[0], b1 = uni[1];
         while (b0) { g_terms[n++] = (unsigned char)(__ffsll((long long)b0) - 1); b0 &= b0 - 1; }
@@ -384,24 +393,31 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
         uint32_t keep = 0;
         for (int i = 0; i < G; ++i) keep |= (uint32_t)((slot_mask[i][m >> 6] >> (m & 63)) & 1ull) << i;
         const uint32_t tiles = tiles_of(keep);
+        // asynchronous issue is spread over three threads of different warps, so that
+        // its latency overlaps: thread 0 stage 1, thread 32 the block copies two terms
+        // ahead, thread 64 stage 2
         if (tid == 0) {
           bool ok = tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[b]), (uint32_t)((it / NBUF) & 1), WAIT_CYCLES, &abort_flag);
           if (ok) {
-            nwaited = it + 1;
             tc::fence_after_sync();
             issue_stacked(tD1, A1, Bb, tiles);  // ---- stage 1: rows (i, jy, jz), contraction jx
             tc::mma_commit(bs1);
-            if (j + 2 < nt) ok = fetch(it + 2, g_terms[j + 2], lbase, nl, Dop, ldx, ldy, ldz);
+          } else {
+            abort_flag = 1;
           }
-          if (!ok) abort_flag = 1;
         }
-        // one warp polls the barrier; the others sleep in the vote
-        bool ok = quarter != 0 || tc::mbar_wait_or_abort(bs1, p1, WAIT_CYCLES, &abort_flag);
+        if (tid == 32 && j + 2 < nt && !fetch(it + 2, g_terms[j + 2], lbase, nl, Dop, ldx, ldy, ldz)) abort_flag = 1;
+        // one warp polls the barriers; the others sleep in the vote.  A2 is free once the
+        // previous term's stage 2 is done.
+        bool ok = true;
+        if (quarter == 0) {
+          ok = tc::mbar_wait_or_abort(bs1, p1, WAIT_CYCLES, &abort_flag);
+          if (ok && it > 0) ok = tc::mbar_wait_or_abort(bs2, (uint32_t)((it - 1) & 1), WAIT_CYCLES, &abort_flag);
+        }
         p1 ^= 1u;
         if (wg_vote_or(1, !ok || abort_flag)) { bad = true; break; }
         tc::fence_after_sync();
-        // stage-1 output -> stage-2 operand: element [jy][(i, jz, ix)].  The stage-2 MMAs of
-        // the previous term have read A2: they were issued before this term's stage 1.
+        // stage-1 output -> stage-2 operand: element [jy][(i, jz, ix)]
 #pragma unroll
         for (int t = 0; t < T; ++t) {
           if (!((tiles >> t) & 1u)) continue;
@@ -416,11 +432,14 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
         tc::fence_proxy_async_smem();
         tc::fence_before_sync();
         wg_sync(1);
-        if (tid == 0) {  // ---- stage 2: rows (i, jz, ix), contraction jy
+        if (tid == 64) {  // ---- stage 2: rows (i, jz, ix), contraction jy
           bool ok2 = it == 0 || tc::mbar_wait_or_abort(bd2free, (uint32_t)((it - 1) & 1), WAIT_CYCLES, &abort_flag);
           if (ok2) {
             ring_keep[it % RING] = keep;
             mbar_arrive(bring);
+            ok2 = tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[b]), (uint32_t)((it / NBUF) & 1), WAIT_CYCLES, &abort_flag);
+          }
+          if (ok2) {
             tc::fence_after_sync();
             issue_stacked(tD2, A2, Bb + BSTAGE_BYTES, tiles);
             tc::mma_commit(bs2);
@@ -431,13 +450,18 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
       }
     }
     if (bad) abort_flag = 1;
-    if (tid == 0) {
-      // block copies still in flight (after an abort) land before the CTA exits, and every
-      // MMA this thread issued is complete before the tensor memory is released
-      for (int i = nwaited; i < nfetch; ++i)
-        tc::mbar_wait(tc::smem_u32(&bar_bb[i % NBUF]), (uint32_t)((i / NBUF) & 1), WAIT_CYCLES);
-      tc::mma_commit(tc::smem_u32(&bar_drain0));
-      tc::mbar_wait(tc::smem_u32(&bar_drain0), 0, WAIT_CYCLES);
+    // block copies still in flight (after an abort) land before the CTA exits, and every
+    // MMA an issuing thread started is complete before the tensor memory is released
+    if (tid == 32) {
+      for (int b = 0; b < NBUF && b < nfetch; ++b) {
+        const int uses = (nfetch - 1 - b) / NBUF + 1;  // copies into buffer b
+        tc::mbar_wait(tc::smem_u32(&bar_bb[b]), (uint32_t)((uses - 1) & 1), WAIT_CYCLES);
+      }
+    }
+    if (tid == 0 || tid == 64) {
+      const uint32_t bd = tc::smem_u32(tid == 0 ? &bar_drain0 : &bar_drain2);
+      tc::mma_commit(bd);
+      tc::mbar_wait(bd, 0, WAIT_CYCLES);
     }
   } else {
     // ======================================================= warpgroup 1
@@ -488,24 +512,29 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
       tc::fence_after_sync();
       const uint32_t keep = ring_keep[it % RING];
       const uint32_t tiles = tiles_of(keep);
-      if (it > 0) flush(prev_tiles, prev_keep);
+      // D2 -> registers, then D2 is released for the next term's stage 2
+      float v[T][K];
+#pragma unroll
+      for (int t = 0; t < T; ++t)
+        if ((tiles >> t) & 1u) load_d(tD2, t, v[t]);
+      tc::fence_before_sync();
+      wg_sync(2);
+      if (tid == 128) mbar_arrive(bd2free);
       // stage-2 output -> stage-3 operand: element [jz][(i, ix, iy)]
 #pragma unroll
       for (int t = 0; t < T; ++t) {
         if (!((tiles >> t) & 1u)) continue;
-        float v[K];
-        load_d(tD2, t, v);
         int m2 = t * 128 + quarter * 32 + lane;
         if (m2 < rows) {
           int i = m2 / k2, rem = m2 - i * k2, jz = rem / k, ix = rem - jz * k;
-          store_run(A3, i * k2 + ix * k, jz, v);
+          store_run(A3, i * k2 + ix * k, jz, v[t]);
         }
       }
+      if (it > 0) flush(prev_tiles, prev_keep);  // before stage 3 of this term overwrites D3
       tc::fence_proxy_async_smem();
       tc::fence_before_sync();
       wg_sync(2);
-      if (tid == 128) {
-        mbar_arrive(bd2free);  // D2 may take the next term's stage 2
+      if (tid == 160) {  // a thread of another warp than the polling one issues stage 3
         const int b = it % NBUF;
         const unsigned char *B3 = Bt + b * BTERM_BYTES + 2 * BSTAGE_BYTES;
         bool okb = tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[b]), (uint32_t)((it / NBUF) & 1), WAIT_CYCLES, &abort_flag);
@@ -561,7 +590,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
         }
       }
     }
-    if (tid == 128) {
+    if (tid == 160) {
       tc::mma_commit(tc::smem_u32(&bar_drain1));
       tc::mbar_wait(tc::smem_u32(&bar_drain1), 0, WAIT_CYCLES);
     }
