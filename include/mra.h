@@ -104,7 +104,7 @@ typedef struct {
   double delta;     /* MRA_SCREEN_LEARNED: safety margin in log10 units */
   int tile_variant; /* MRA_PREC_SPLIT_BF16 tile shape: 0 = four 128-row tiles per CTA (one CTA
                        per SM); 1 (k >= 4) = two tiles per CTA (two CTAs per SM); 2 (k = 4 to
-                       10) = one tile per CTA (three CTAs per SM); others are taken as 0 */
+                       10) = one tile per CTA (four CTAs per SM); others are taken as 0 */
 } mra_apply_opts;
 
 typedef struct {

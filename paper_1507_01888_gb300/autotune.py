@@ -3,7 +3,7 @@ kernel on the caller's own input.
 
 The library compiles up to three tile shapes: four 128-row tiles per CTA with one CTA per
 SM (variant 0, the whole tensor memory), two tiles per CTA with two CTAs per SM (variant 1,
-k >= 4) and one tile per CTA with three CTAs per SM (variant 2, k = 4 to 10).  Wider tiles gather
+k >= 4) and one tile per CTA with four CTAs per SM (variant 2, k = 4 to 10).  Wider tiles gather
 more destinations per group, so one MMA serves more boxes; more CTAs per SM keep the
 tensor pipe busy while a CTA waits on its own chain of stages.  Which wins depends on the tree, so the tuner times each variant (device time
 of the apply kernel, CUDA events inside the library), keeps the fastest, and caches the

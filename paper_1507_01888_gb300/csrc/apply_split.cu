@@ -41,7 +41,7 @@ constexpr int TILE_BYTES = 16 * MG_BYTES;  // one 128 x 16 BF16 operand tile
 constexpr int BPIECE_BYTES = 512;       // one 16 x 16 BF16 block piece
 constexpr int BSTAGE_BYTES = 3 * BPIECE_BYTES;  // the three pieces of one block
 constexpr int BTERM_BYTES = 3 * BSTAGE_BYTES;   // the three blocks (x, y, z) of one term
-constexpr int NBUF = 4;                         // block buffers: terms in flight
+constexpr int NBUF = 4;                         // most block buffers a CTA uses
 constexpr int RING = 4;                         // term-info ring from warpgroup 0 to 1
 constexpr int MAX_G = 32;
 constexpr long long WAIT_CYCLES = 4000000000LL;  // bounded mbarrier wait (~2 s)
@@ -109,12 +109,18 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // and stage-2 outputs (48 columns per tile each: three 16-column piece groups) and the
 // stage-3 output (32 columns per tile: two groups): 128 T columns.  TT = 4 takes the whole
 // tensor memory (one CTA per SM); TT = 2 leaves room for a second CTA on the SM and TT = 1
-// for three (then shared memory is the limit).
+// for four.
 __host__ __device__ constexpr int g_for(int k, int tt) {
   return (128 * tt) / (k * k) > MAX_G ? MAX_G : (128 * tt) / (k * k);
 }
 __host__ __device__ constexpr int t_for(int k, int tt) { return (g_for(k, tt) * k * k + 127) / 128; }
 __host__ __device__ constexpr uint32_t tmem_cols_for(int T) { return T <= 1 ? 128u : (T <= 2 ? 256u : 512u); }
+// block buffers (terms whose blocks are in shared memory) and how many terms ahead the
+// copies run: the one-tile shape keeps three buffers so that four CTAs fit on an SM
+__host__ __device__ constexpr int nbuf_for(int tt) { return tt == 1 ? 3 : NBUF; }
+// CTAs per SM the launch bounds ask for: TT = 1 fills the 512 tensor-memory columns with
+// four CTAs of 128 columns each
+__host__ __device__ constexpr int minb_for(int tt) { return tt == 1 ? 4 : 4 / tt; }
 // slots whose rows [i k^2, (i+1) k^2) meet tile t's rows [128 t, 128 t + 128)
 __host__ __device__ constexpr uint32_t tile_slots(int t, int k2, int G) {
   uint32_t m = 0;
@@ -149,17 +155,18 @@ __device__ __forceinline__ void split_pair(float x, float y, __nv_bfloat162 &h0,
 // by the stage-3 MMAs that read it.  Each wait is bounded and gives up when the other
 // warpgroup has aborted.
 template <int K, int TT>
-__global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_split_kernel(SplitArgs a) {
+__global__ void __launch_bounds__(SPLIT_THREADS, minb_for(TT)) apply_split_kernel(SplitArgs a) {
   constexpr int k = K, k2 = K * K, k3 = K * K * K;
   constexpr int G = g_for(K, TT), rows = G * k2, T = t_for(K, TT);
   constexpr uint32_t NCOL = tmem_cols_for(T);
+  constexpr int NB = nbuf_for(TT), AHEAD = NB - 2;  // block buffers; copies run AHEAD terms ahead
   extern __shared__ __align__(1024) unsigned char smem[];
   const int P = a.P;
   const int ptile = P * T * TILE_BYTES;
   unsigned char *A1 = smem;              // [P][T] tiles: stage-1 operand (sources)
   unsigned char *A2 = A1 + ptile;        // [P][T] tiles: stage-2 operand
   unsigned char *A3 = A2 + ptile;        // [P][T] tiles: stage-3 operand
-  unsigned char *Bt = A3 + ptile;        // [NBUF][3 stages][1536]: the blocks of a term
+  unsigned char *Bt = A3 + ptile;        // [NB][3 stages][1536]: the blocks of a term
   __shared__ __align__(8) uint64_t bar_s1, bar_s2, bar_s3, bar_ring, bar_d2free, bar_drain0, bar_drain1, bar_drain2;
   __shared__ __align__(8) uint64_t bar_bb[NBUF], bar_bfree[NBUF];
   __shared__ uint32_t tmem_holder;
@@ -190,7 +197,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
     tc::mbar_init(tc::smem_u32(&bar_drain0), 1);
     tc::mbar_init(tc::smem_u32(&bar_drain1), 1);
     tc::mbar_init(tc::smem_u32(&bar_drain2), 1);
-    for (int b = 0; b < NBUF; ++b) {
+    for (int b = 0; b < NB; ++b) {
       tc::mbar_init(tc::smem_u32(&bar_bb[b]), 1);
       tc::mbar_init(tc::smem_u32(&bar_bfree[b]), 1);
     }
@@ -309,12 +316,12 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
     int it = 0;
     int nfetch = 0;  // block copies issued (thread 32), for iterations 0 .. nfetch-1 in order
     bool bad = false;
-    // copies of the three blocks (m; lx, ly, lz) of iteration `i` into buffer i % NBUF, once
-    // the stage-3 MMAs of iteration i - NBUF (the buffer's previous user) are done
+    // copies of the three blocks (m; lx, ly, lz) of iteration `i` into buffer i % NB, once
+    // the stage-3 MMAs of iteration i - NB (the buffer's previous user) are done
     auto fetch = [&](int i, int m, int64_t lbase, int nl, int Dop, int lx, int ly, int lz) -> bool {
-      const int b = i % NBUF;
-      if (i >= NBUF &&
-          !tc::mbar_wait_or_abort(tc::smem_u32(&bar_bfree[b]), (uint32_t)((i / NBUF - 1) & 1), WAIT_CYCLES, &abort_flag))
+      const int b = i % NB;
+      if (i >= NB &&
+          !tc::mbar_wait_or_abort(tc::smem_u32(&bar_bfree[b]), (uint32_t)((i / NB - 1) & 1), WAIT_CYCLES, &abort_flag))
         return false;
       unsigned char *Bb = Bt + b * BTERM_BYTES;
       const uint32_t bar = tc::smem_u32(&bar_bb[b]);
@@ -357,13 +364,13 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
       const int Dop = a.Dlev[lev], nl = 2 * Dop + 1;
       const int ldx = (lp & 255) - 128, ldy = ((lp >> 8) & 255) - 128, ldz = ((lp >> 16) & 255) - 128;
       const int64_t lbase = a.level_off[lev];
-      if (tid == 32) {  // the group's terms in ascending order; blocks of its first two terms
+      if (tid == 32) {  // the group's terms in ascending order; blocks of its first AHEAD terms
         int n = 0;
         uint64_t b0 = uni[0], b1 = uni[1];
         while (b0) { g_terms[n++] = (unsigned char)(__ffsll((long long)b0) - 1); b0 &= b0 - 1; }
         while (b1) { g_terms[n++] = (unsigned char)(64 + __ffsll((long long)b1) - 1); b1 &= b1 - 1; }
         g_nterms = n;
-        for (int j = 0; j < 2 && j < n; ++j)
+        for (int j = 0; j < AHEAD && j < n; ++j)
           if (!fetch(it + j, g_terms[j], lbase, nl, Dop, ldx, ldy, ldz)) abort_flag = 1;
       }
       // stage-1 operand: sources, rows (i, jy, jz), contraction jx (FP64 -> FP32 -> 3 BF16
@@ -388,16 +395,16 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
       const int nt = g_nterms;
       for (int j = 0; j < nt; ++j, ++it) {
         const int m = g_terms[j];
-        const int b = it % NBUF;
+        const int b = it % NB;
         const unsigned char *Bb = Bt + b * BTERM_BYTES;
         uint32_t keep = 0;
         for (int i = 0; i < G; ++i) keep |= (uint32_t)((slot_mask[i][m >> 6] >> (m & 63)) & 1ull) << i;
         const uint32_t tiles = tiles_of(keep);
         // asynchronous issue is spread over three threads of different warps, so that
-        // its latency overlaps: thread 0 stage 1, thread 32 the block copies two terms
+        // its latency overlaps: thread 0 stage 1, thread 32 the block copies AHEAD terms
         // ahead, thread 64 stage 2
         if (tid == 0) {
-          bool ok = tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[b]), (uint32_t)((it / NBUF) & 1), WAIT_CYCLES, &abort_flag);
+          bool ok = tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[b]), (uint32_t)((it / NB) & 1), WAIT_CYCLES, &abort_flag);
           if (ok) {
             tc::fence_after_sync();
             issue_stacked(tD1, A1, Bb, tiles);  // ---- stage 1: rows (i, jy, jz), contraction jx
@@ -406,7 +413,8 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
             abort_flag = 1;
           }
         }
-        if (tid == 32 && j + 2 < nt && !fetch(it + 2, g_terms[j + 2], lbase, nl, Dop, ldx, ldy, ldz)) abort_flag = 1;
+        if (tid == 32 && j + AHEAD < nt && !fetch(it + AHEAD, g_terms[j + AHEAD], lbase, nl, Dop, ldx, ldy, ldz))
+          abort_flag = 1;
         // one warp polls the barriers; the others sleep in the vote.  A2 is free once the
         // previous term's stage 2 is done.
         bool ok = true;
@@ -437,7 +445,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
           if (ok2) {
             ring_keep[it % RING] = keep;
             mbar_arrive(bring);
-            ok2 = tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[b]), (uint32_t)((it / NBUF) & 1), WAIT_CYCLES, &abort_flag);
+            ok2 = tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[b]), (uint32_t)((it / NB) & 1), WAIT_CYCLES, &abort_flag);
           }
           if (ok2) {
             tc::fence_after_sync();
@@ -453,8 +461,8 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
     // block copies still in flight (after an abort) land before the CTA exits, and every
     // MMA an issuing thread started is complete before the tensor memory is released
     if (tid == 32) {
-      for (int b = 0; b < NBUF && b < nfetch; ++b) {
-        const int uses = (nfetch - 1 - b) / NBUF + 1;  // copies into buffer b
+      for (int b = 0; b < NB && b < nfetch; ++b) {
+        const int uses = (nfetch - 1 - b) / NB + 1;  // copies into buffer b
         tc::mbar_wait(tc::smem_u32(&bar_bb[b]), (uint32_t)((uses - 1) & 1), WAIT_CYCLES);
       }
     }
@@ -535,9 +543,9 @@ __global__ void __launch_bounds__(SPLIT_THREADS, TT == 1 ? 3 : 4 / TT) apply_spl
       tc::fence_before_sync();
       wg_sync(2);
       if (tid == 160) {  // a thread of another warp than the polling one issues stage 3
-        const int b = it % NBUF;
+        const int b = it % NB;
         const unsigned char *B3 = Bt + b * BTERM_BYTES + 2 * BSTAGE_BYTES;
-        bool okb = tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[b]), (uint32_t)((it / NBUF) & 1), WAIT_CYCLES, &abort_flag);
+        bool okb = tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[b]), (uint32_t)((it / NB) & 1), WAIT_CYCLES, &abort_flag);
         if (okb) {
           tc::fence_after_sync();
           // ---- stage 3: rows (i, ix, iy), contraction jz, B = c_m R_z pieces.  Column
@@ -750,7 +758,7 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
   a.out_keys = out.keys;
   a.out_coeffs = out.coeffs;
   a.err = err;
-  size_t smem = (size_t)3 * a.P * T * TILE_BYTES + (size_t)NBUF * BTERM_BYTES;
+  size_t smem = (size_t)3 * a.P * T * TILE_BYTES + (size_t)nbuf_for(tt) * BTERM_BYTES;
   // no more CTAs per SM than the tensor memory holds (512 columns): otherwise an extra
   // CTA's allocation would wait for a resident CTA to finish
   const size_t smem_floor = (size_t)233472 / (512 / tmem_cols_for(T) + 1);
