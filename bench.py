@@ -33,6 +33,11 @@ sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
 
+# DRAM bytes (read + written) of one launch of the dominant kernel, from a one-pass ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of this bench's own command, keyed by
+# (workload, tile variant).  An entry is removed whenever the kernel changes.
+SPLIT_TRAFFIC = {("bsh_m60_adaptive_k10", 2): 71.26e6 + 77.45e6}
+
 METRIC = "3D operator-apply boxes/s & % roofline, mixed vs FP64 GPU at 1e-6 rel L2"
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no FP64 figure in the measured peaks)
 
@@ -378,7 +383,9 @@ def main():
     else:
         peak = pk.get("bf16_tflops", 1856.3)
         roof = {"bound": "tensor", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved_tflops / peak, "traffic": None, "kernel": "apply_split_kernel",
+                "frac": achieved_tflops / peak,
+                "traffic": SPLIT_TRAFFIC.get((w.name, int(opts.tile_variant))) if not batched else None,
+                "kernel": "apply_split_kernel",
                 "peak_source": f"bf16 dense burst, {pk_kind}", "kernel_ms": kms,
                 "flops": "algorithmic (6k^4+k^3 per kept term)"}
         dtype = f"bf16x{args.pieces}-split, f32 accumulate, f64 term sum"
