@@ -1,0 +1,68 @@
+"""The multi-rank host logic of the benchmark on CPU: two gloo ranks on 127.0.0.1.
+
+Each rank of a family of independent functions runs its own part (disjoint seeds, same
+size); a single-function workload is a replica on every rank; the job's value is the units
+summed over ranks divided by the slowest rank's time.
+"""
+import os
+import socket
+
+import pytest
+
+import workloads as W
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import bench
+        w = W.shard(W.poisson_batched_64(), rank, world)
+        ids = sorted(round(float(f["cx"][0]), 12) for f in w.funcs)  # identifies the functions
+        rep = W.shard(W.bsh_m60_adaptive_k10(), rank, world)
+        n_local = 1000 + 500 * rank
+        ms_local = 10.0 + 5.0 * rank
+        n_all, ms = bench.reduce_over_ranks(n_local, ms_local, world)
+        q.put((rank, len(w.funcs), ids, float(rep.funcs[0]["cx"][0]), n_all, ms))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_shard_and_reduce():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = {}
+    for _ in range(2):
+        r = q.get(timeout=120)
+        res[r[0]] = r
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (_, n0, s0, rep0, na0, ms0), (_, n1, s1, rep1, na1, ms1) = res[0], res[1]
+    assert n0 == n1 == 64                       # same amount of work per rank (weak scaling)
+    assert not set(s0) & set(s1)                # different functions on the two ranks
+    assert rep0 == rep1                         # single-function workload: a replica per rank
+    assert na0 == na1 == 1000 + 1500            # units summed over ranks
+    assert ms0 == ms1 == pytest.approx(15.0)    # slowest rank's time
+
+
+def test_shard_is_identity_for_one_rank():
+    w = W.poisson_batched_64()
+    assert W.shard(w, 0, 1) is w
+    w0 = W.shard(w, 0, 2)
+    assert [f["cx"][0] for f in w0.funcs] == [f["cx"][0] for f in w.funcs]  # rank 0 keeps part 0

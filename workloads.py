@@ -87,14 +87,21 @@ def bsh_m60_uniform_k10() -> Workload:
                     max_disp=1, tau=0.0)
 
 
+def _batched_funcs(part: int) -> list:
+    """Part p of the batched family: 64 functions of 1-16 Gaussians (counts from seed 3 + 1000 p),
+    a~logU[1,1e3], seeds 3000 + 64 p + i."""
+    rng = np.random.default_rng(3 + 1000 * part)
+    counts = rng.integers(1, 17, size=64)
+    return [gaussian_sum(int(counts[i]), 1.0, 1e3, seed=3000 + 64 * part + i) for i in range(64)]
+
+
 def poisson_batched_64() -> Workload:
     """Batched Poisson apply: 64 functions (seeds 3000..3063) of 1-16 Gaussians a~logU[1,1e3],
-    k=8, thresh 1e-5, 1/r as 40 Gaussians."""
-    rng = np.random.default_rng(3)
-    counts = rng.integers(1, 17, size=64)
-    funcs = [gaussian_sum(int(counts[i]), 1.0, 1e3, seed=3000 + i) for i in range(64)]
-    return Workload("poisson_batched64_k8", funcs, k=8, L=L_CELL, thresh=1e-5, uniform_level=-1,
-                    kernel=POISSON, mu=0.0, M=40, fit_eps=1e-5, stencil=0, max_disp=1, tau=1e-7)
+    k=8, thresh 1e-5, 1/r as 40 Gaussians.  Its functions are independent problems: with
+    several ranks, rank r takes part r of the family (extra["rank_funcs"])."""
+    return Workload("poisson_batched64_k8", _batched_funcs(0), k=8, L=L_CELL, thresh=1e-5, uniform_level=-1,
+                    kernel=POISSON, mu=0.0, M=40, fit_eps=1e-5, stencil=0, max_disp=1, tau=1e-7,
+                    extra={"rank_funcs": _batched_funcs})
 
 
 def bsh_learned_k10() -> Workload:
@@ -112,6 +119,16 @@ def poisson_k14_large() -> Workload:
     return Workload("poisson_m100_adaptive_k14", [gaussian_sum(64, 1.0, 1e6, seed=5)], k=14, L=L_CELL,
                     thresh=1e-8, uniform_level=-1, kernel=POISSON, mu=0.0, M=100, fit_eps=1e-8, stencil=0,
                     max_disp=1, tau=1e-10)
+
+
+def shard(w: Workload, rank: int, world: int) -> Workload:
+    """The workload rank `rank` of `world` runs.  Families of independent functions give every
+    rank its own part (same size: weak scaling, no exchange between ranks); a single-function
+    workload is run whole on every rank (replicas)."""
+    if world <= 1 or "rank_funcs" not in w.extra:
+        return w
+    return Workload(w.name, w.extra["rank_funcs"](rank), w.k, w.L, w.thresh, w.uniform_level, w.kernel, w.mu,
+                    w.M, w.fit_eps, w.stencil, w.max_disp, w.tau, w.init_level, w.max_level, dict(w.extra))
 
 
 WORKLOADS = {
