@@ -61,6 +61,7 @@ __global__ void box_norm_kernel(int64_t n, int k3, const double *coeffs, double 
 
 // ---------------------------------------------------------------- screen
 // One warp per source box.  pass 0 counts records, pass 1 writes them at off[b].
+constexpr int LD_Q = 13;  // |l|^2 classes with a stored learned-screen decision (|l|_inf <= 2)
 struct ScreenArgs {
   int64_t n_in;
   const uint64_t *keys;
@@ -90,6 +91,9 @@ struct ScreenArgs {
   float learned_cut;          // log10(tau) - delta
   int64_t *box_learned;
   double *box_lbound;
+  // the network's inputs depend on the displacement only through |l|^2: pass 0 evaluates it
+  // once per (box, class |l|^2 <= LD_Q - 1, term) and stores the drop bits, pass 1 reads them
+  uint64_t *learned_drop;     // [n_in][LD_Q][2]
   // several functions in one apply: boxes [fn_off[f], fn_off[f+1]) belong to function f,
   // and records sort on (f, level, x, y, z) packed as f<<53 | n<<48 | x<<32 | y<<16 | z
   int nfunc;
@@ -107,13 +111,15 @@ __device__ __forceinline__ uint64_t public_key(uint64_t bk) {
 
 template <int PASS>
 __global__ void screen_kernel(ScreenArgs a) {
-  extern __shared__ float mlp_sh[];  // the learned screen's parameters, when used
-  if (a.mlp) {
+  extern __shared__ __align__(16) float mlp_sh[];  // the learned screen's parameters, when used
+  __shared__ uint64_t drop_sh[8][LD_Q][2];  // per warp: learned-screen drop bits by |l|^2 class
+  if (a.mlp && PASS == 0) {
     for (int i = threadIdx.x; i < MLP_NALL; i += blockDim.x) mlp_sh[i] = a.mlp[i];
     __syncthreads();
   }
   int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
   if (b >= a.n_in) return;
   uint64_t key = a.keys[b];
   int n = key_level(key);
@@ -147,6 +153,41 @@ __global__ void screen_kernel(ScreenArgs a) {
   double skipped = 0.0, lbound = 0.0;
   const float log_sn = (float)log10(fmax(sn, 1e-300));
   int64_t wpos = PASS == 1 ? a.off[b] : 0;
+  // learned screen: drop bits of every (|l|^2 class, term) this box can meet, by the network
+  // in pass 0 (terms the norm screen would drop anyway are never looked up)
+  uint64_t(*drop)[2] = drop_sh[wib];
+  if (a.mlp && D <= 2) {
+    if (PASS == 0) {
+      for (int q = 0; q <= 3 * D * D; ++q) {
+        bool occurs = false;  // q = lx^2 + ly^2 + lz^2 with |l|_inf <= D
+        for (int u = 0; u <= D; ++u)
+          for (int v = 0; v <= D; ++v)
+            for (int w = 0; w <= D; ++w) occurs |= u * u + v * v + w * w == q;
+        uint64_t w0 = 0ull, w1 = 0ull;
+        if (occurs) {
+          for (int m0 = 0; m0 < a.M; m0 += 32) {
+            const int m = m0 + lane;
+            bool dr = false;
+            if (m < a.M) {
+              float f[4] = {(float)n, sqrtf((float)q), (float)log10(a.t[m]), log_sn};
+              dr = mlp_predict(mlp_sh, f) < a.learned_cut;
+            }
+            const uint64_t bal = (uint64_t)__ballot_sync(0xffffffffu, dr) << (m0 & 63);
+            if (m0 < 64) w0 |= bal; else w1 |= bal;
+          }
+        }
+        if (lane == 0) {
+          drop[q][0] = w0;
+          drop[q][1] = w1;
+          a.learned_drop[(b * LD_Q + q) * 2] = w0;
+          a.learned_drop[(b * LD_Q + q) * 2 + 1] = w1;
+        }
+      }
+    } else if (lane < 2 * (3 * D * D + 1)) {
+      drop[lane >> 1][lane & 1] = a.learned_drop[b * LD_Q * 2 + lane];
+    }
+    __syncwarp();
+  }
   int d;
   for (d = 0; d <= D; ++d) {
     int any = 0;
@@ -169,8 +210,16 @@ __global__ void screen_kernel(ScreenArgs a) {
                   Nl[m * nl + lz + Dop] * sn;
               keep = a.screen == MRA_SCREEN_NONE ? true : (B >= a.tau);
               if (keep && a.mlp) {
-                float f[4] = {(float)n, sqrtf((float)(lx * lx + ly * ly + lz * lz)), (float)log10(a.t[m]), log_sn};
-                if (mlp_predict(mlp_sh, f) < a.learned_cut) {
+                const int q = lx * lx + ly * ly + lz * lz;
+                bool dr;
+                if (D <= 2) {
+                  dr = (drop[q][m >> 6] >> (m & 63)) & 1ull;
+                } else {  // wide stencils: evaluate the network for this term (pass 0 only
+                          // sees the parameters in shared memory; pass 1 reads them from global)
+                  float f[4] = {(float)n, sqrtf((float)q), (float)log10(a.t[m]), log_sn};
+                  dr = mlp_predict(PASS == 0 ? (const float *)mlp_sh : a.mlp, f) < a.learned_cut;
+                }
+                if (dr) {
                   keep = false;
                   dropped_by_model = true;
                 }
@@ -431,12 +480,12 @@ int64_t apply_max_records(const Operator &op, const mra_apply_opts &o, int64_t n
 //   per destination (<= records): dest key, seg (+1)
 //   CUB temp storage (max over scan / sort / reduce needs)
 struct Layout {
-  size_t snorm, dstop, cnt, off, kept, screened, skipped, trunc, learned, lbound;
+  size_t snorm, dstop, cnt, off, kept, screened, skipped, trunc, learned, lbound, ldrop;
   size_t rkey, rsrc, rl, rmask, skey, pin, pout, head, did, dkey, seg, ndest, dfunc, fnoff, split, tmp;
   size_t split_bytes, tmp_bytes, total;
 };
 
-static Layout make_layout(int64_t n_in, int64_t P) {
+static Layout make_layout(int64_t n_in, int64_t P, bool learned) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -455,6 +504,7 @@ static Layout make_layout(int64_t n_in, int64_t P) {
   L.trunc = take(nb * 4);
   L.learned = take(nb * 8);
   L.lbound = take(nb * 8);
+  L.ldrop = take(learned ? nb * LD_Q * 16 : 0);
   L.rkey = take(np * 8);
   L.rsrc = take(np * 4);
   L.rl = take(np * 4);
@@ -488,7 +538,7 @@ static Layout make_layout(int64_t n_in, int64_t P) {
 }
 
 size_t apply_workspace_bytes(const Operator &op, const mra_apply_opts &o, int64_t n_in) {
-  return make_layout(n_in, apply_max_records(op, o, n_in)).total;
+  return make_layout(n_in, apply_max_records(op, o, n_in), o.screen == MRA_SCREEN_LEARNED).total;
 }
 
 // Pointers into a carved workspace.
@@ -497,6 +547,7 @@ struct WsPtrs {
   int *dstop;
   int64_t *cnt, *off, *bkept, *bscr, *blearned;
   double *bskip, *blbound;
+  uint64_t *ldrop;
   int *btrunc;
   uint64_t *rkey, *skey, *rmask, *dkey;
   int *rsrc, *rl, *pin, *pout, *head, *did;
@@ -520,6 +571,7 @@ static WsPtrs carve(const Layout &L, void *ws) {
   p.btrunc = (int *)(w + L.trunc);
   p.blearned = (int64_t *)(w + L.learned);
   p.blbound = (double *)(w + L.lbound);
+  p.ldrop = (uint64_t *)(w + L.ldrop);
   p.rkey = (uint64_t *)(w + L.rkey);
   p.skey = (uint64_t *)(w + L.skey);
   p.rsrc = (int *)(w + L.rsrc);
@@ -583,6 +635,7 @@ static int screen_run(const Operator &op, const mra_tree_view &in, const mra_app
   a.learned_cut = (float)(log10(o.tau) - o.delta);
   a.box_learned = w.blearned;
   a.box_lbound = w.blbound;
+  a.learned_drop = w.ldrop;
   a.nfunc = nfunc;
   a.fn_off = w.fnoff;
   const size_t ssm = a.mlp ? (size_t)MLP_NALL * sizeof(float) : 0;
@@ -649,7 +702,7 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
   const int k = op.k, k3 = k * k * k;
   const int64_t n_in = in.n;
   const int64_t Pmax = apply_max_records(op, o, n_in);
-  Layout L = make_layout(n_in, Pmax);
+  Layout L = make_layout(n_in, Pmax, o.screen == MRA_SCREEN_LEARNED);
   if (ws_bytes < L.total)
     return fail(MRA_ERR_CAPACITY, "mra_apply: workspace of %zu bytes < %zu needed", ws_bytes, L.total);
   WsPtrs W = carve(L, ws);
@@ -879,7 +932,7 @@ int log_terms_run(const Operator &op, const mra_tree_view &in, const mra_apply_o
   const int64_t n_in = in.n;
   if (n_in == 0 || max_terms <= 0) return MRA_OK;
   const int64_t Pmax = apply_max_records(op, o, n_in);
-  Layout L = make_layout(n_in, Pmax);
+  Layout L = make_layout(n_in, Pmax, o.screen == MRA_SCREEN_LEARNED);
   if (ws_bytes < L.total)
     return fail(MRA_ERR_CAPACITY, "mra_log_terms: workspace of %zu bytes < %zu needed", ws_bytes, L.total);
   WsPtrs W = carve(L, ws);

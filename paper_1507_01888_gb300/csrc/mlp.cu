@@ -82,9 +82,10 @@ __global__ void mlp_norm_kernel(float *p, const float *x, const float *y, int64_
 
 __global__ void mlp_forward_kernel(const float *__restrict__ p, const float *__restrict__ x, int64_t n,
                                    float *__restrict__ y) {
-  __shared__ float sp[MLP_NALL];
+  __shared__ __align__(16) float sp[MLP_NALL];
   for (int i = threadIdx.x; i < MLP_NALL; i += blockDim.x) sp[i] = p[i];
   __syncthreads();
+#pragma unroll 1
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
     float in[4] = {x[r * 4], x[r * 4 + 1], x[r * 4 + 2], x[r * 4 + 3]};
     y[r] = mlp_predict(sp, in);

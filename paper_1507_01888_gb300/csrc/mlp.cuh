@@ -16,25 +16,39 @@ constexpr int MLP_NP = MLP_B3 + 1;                  // trainable parameters (454
 constexpr int MLP_XMEAN = MLP_NP, MLP_XSTD = MLP_NP + 4, MLP_YMEAN = MLP_NP + 8, MLP_YSTD = MLP_NP + 9;
 constexpr int MLP_NALL = MLP_NP + 10;               // with the standardisation (4555)
 static_assert(MLP_NALL == MRA_MLP_PARAMS, "parameter count must match mra.h");
+static_assert(MLP_W1 % 4 == 0 && MLP_W2 % 4 == 0, "float4 rows of the network must be 16-byte aligned");
 
-// Predicted log10 of a term's norm for features x[4]; p in shared or global memory.
+// Predicted log10 of a term's norm for features x[4]; p in shared or global memory, 16-byte
+// aligned.  The hidden activations stay in registers (every index below is compile-time);
+// the 64 x 64 layer is read as float4 rows.
 __device__ __forceinline__ float mlp_predict(const float *p, const float *x) {
   float z[MLP_IN];
 #pragma unroll
   for (int f = 0; f < MLP_IN; ++f) z[f] = (x[f] - p[MLP_XMEAN + f]) / p[MLP_XSTD + f];
   float h1[MLP_H];
-#pragma unroll 8
-  for (int j = 0; j < MLP_H; ++j) {
-    float a = p[MLP_B1 + j];
 #pragma unroll
-    for (int f = 0; f < MLP_IN; ++f) a += p[MLP_W1 + j * MLP_IN + f] * z[f];
+  for (int j = 0; j < MLP_H; ++j) {
+    const float4 w = *(const float4 *)(p + MLP_W1 + j * MLP_IN);
+    float a = p[MLP_B1 + j];
+    a += w.x * z[0];
+    a += w.y * z[1];
+    a += w.z * z[2];
+    a += w.w * z[3];
     h1[j] = tanhf(a);
   }
   float o = p[MLP_B3];
+#pragma unroll 1
   for (int j = 0; j < MLP_H; ++j) {
+    const float4 *row = (const float4 *)(p + MLP_W2 + j * MLP_H);
     float a = p[MLP_B2 + j];
-#pragma unroll 16
-    for (int i = 0; i < MLP_H; ++i) a += p[MLP_W2 + j * MLP_H + i] * h1[i];
+#pragma unroll
+    for (int i4 = 0; i4 < MLP_H / 4; ++i4) {
+      const float4 w = row[i4];
+      a += w.x * h1[4 * i4];
+      a += w.y * h1[4 * i4 + 1];
+      a += w.z * h1[4 * i4 + 2];
+      a += w.w * h1[4 * i4 + 3];
+    }
     o += p[MLP_W3 + j] * tanhf(a);
   }
   return o * p[MLP_YSTD] + p[MLP_YMEAN];
