@@ -74,6 +74,9 @@ def _load():
         lib.orc_block.argtypes = [i, d, d, l, D]
         lib.orc_project.argtypes = [i, D, D, D, D, D, i, d, d, i, i, i, l, U64, D, L, D, i]
         lib.orc_apply.argtypes = [i, d, l, U64, D, i, D, D, i, i, d, l, U64, l, U64, D, D, D, L, L, i]
+        lib.orc_apply_ns.argtypes = [i, d, i, i, D, i, D, D, i, D, i]
+        lib.orc_unfilter3.argtypes = [i, D, D]
+        lib.orc_filter3.argtypes = [i, D, D]
         _lib = lib
         return lib
 
@@ -256,3 +259,38 @@ def apply(keys, coeffs, c, t, L: float, stencil: int = 1, max_disp: int = 1, tau
             raise RuntimeError(f"orc_apply failed ({rc})")
         m = n.value
         return ApplyResult(out_keys[:m].copy(), out[:m].copy(), bound[:m].copy(), marg[:m].copy(), stats)
+
+
+# --------------------------------------------------------------------------- non-standard form
+
+def unfilter3(k: int, v):
+    """(Ubar x Ubar x Ubar) v: a parent's k^3 coefficients as its children's (2k)^3 tensor (Sec. 2.2)."""
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(k, k, k)
+    S = np.zeros((2 * k, 2 * k, 2 * k))
+    _load().orc_unfilter3(int(k), _dp(v), _dp(S))
+    return S
+
+
+def filter3(k: int, S):
+    """(Ubar^T x Ubar^T x Ubar^T) S: the parent's k^3 scaling coefficients of a children tensor."""
+    S = np.ascontiguousarray(S, dtype=np.float64).reshape(2 * k, 2 * k, 2 * k)
+    v = np.zeros((k, k, k))
+    _load().orc_filter3(int(k), _dp(S), _dp(v))
+    return v
+
+
+def apply_ns(coeffs, k: int, L: float, N: int, n0: int, c, t, D: int, nthreads=None):
+    """Non-standard form apply (Sec. 2.2) on a uniform level-N tree: T^{n0} with every
+    displacement at level n0, the differences A^n + B^n + C^n = T2k^n - Ubar T^n Ubar^T with
+    |l|_inf <= D at levels n0..N-1, summed down to level N.  coeffs: [(2^N)^3, k, k, k] in key
+    order (x slowest).  With D >= 2^N - 1 it equals the plain level-N apply."""
+    nb = 1 << N
+    coeffs = np.ascontiguousarray(coeffs, dtype=np.float64).reshape(nb ** 3, k, k, k)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    out = np.zeros_like(coeffs)
+    rc = _load().orc_apply_ns(int(k), float(L), int(N), int(n0), _dp(coeffs), len(c), _dp(c), _dp(t), int(D),
+                              _dp(out), _threads(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"orc_apply_ns failed ({rc})")
+    return out

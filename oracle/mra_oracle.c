@@ -5,7 +5,7 @@
  * projection of a Gaussian sum onto the Legendre scaling-function basis,
  * the trapezoid Gaussian fit of 1/r and exp(-mu r)/r, the 1-D operator
  * blocks, the norm screen and the separated operator apply by direct
- * summation.  Every routine follows the paper (Harrison et al., "MADNESS: A
+ * summation, and the non-standard form apply on uniform trees.  Every routine follows the paper (Harrison et al., "MADNESS: A
  * Multiresolution, Adaptive Numerical Environment for Scientific Simulation",
  * arXiv 1507.01888) section or equation it cites.  It shares no code, header,
  * table or constant with the CUDA library; only the tests, the smoke check and
@@ -814,4 +814,289 @@ int orc_apply(int k, double L, long n_in, const uint64_t *keys, const double *co
     free(lb[n].N);
   }
   return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Non-standard form apply on a uniform tree (Sec. 2.2)                      */
+/* ------------------------------------------------------------------------ */
+
+/* Level-n boxes of a uniform level are stored densely: box (x, y, z) at ((x nb) + y) nb + z.
+ *
+ * Two-scale relation (Sec. 2.2, P^{n+1} = P^n + Q^n): with Ubar[(c,i)][j] = U^(c)[i][j]
+ * (orc_two_scale), the children of a box hold S = (Ubar x Ubar x Ubar) s for a function
+ * of the parent space, and the parent's scaling coefficients of any children tensor S are
+ * s = (Ubar^T x Ubar^T x Ubar^T) S.  S is stored as the (2k)^3 tensor with index (c, i) =
+ * c k + i in every dimension.
+ *
+ * The operator blocks of the 2k basis of level n are those of level n+1 between the
+ * children: R2k^n_{m,l}[(ci,i)][(cj,j)] = R^{n+1}_{m, 2l+ci-cj}[i][j].
+ *
+ * Non-standard form: T^{n+1} = T^n + A^n + B^n + C^n, so on a uniform level N
+ *   T^N s^N = T^{n0} s^{n0} + sum_{n=n0}^{N-1} (A^n + B^n + C^n) s,
+ * with (A + B + C)^n = T2k^n - Ubar T^n Ubar^T on level n's 2k basis.  The apply takes
+ * T^{n0} with every displacement of level n0 and the level-n differences with |l|_inf <= D,
+ * then sums down: r^{n+1} = Ubar (r^n - Z^n) + Y^n per box (Y^n = T2k^n S^n,
+ * Z^n = T^n s^n), split into the children.  With D covering every displacement the
+ * result equals the plain level-N apply T^N s^N. */
+
+/* out[target] = sum_{l, m} c_m (R_{m,lx} x R_{m,ly} x R_{m,lz}) in[target - l] on a dense level
+ * of nb^3 boxes of kk^3 coefficients; R holds [M][2D+1][kk*kk] blocks (index l + D). */
+static void apply_level_dense(int kk, long nb, const double *in, const double *R, const double *c, int M,
+                              int D, double *out) {
+  long nbox = nb * nb * nb;
+  int kk2 = kk * kk, kk3 = kk2 * kk, nl = 2 * D + 1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic)
+#endif
+  for (long tb = 0; tb < nbox; ++tb) {
+    long tx = tb / (nb * nb), ty = (tb / nb) % nb, tz = tb % nb;
+    double *o = out + tb * kk3;
+    double *t1 = (double *)malloc(sizeof(double) * kk3 * 3);
+    double *t2 = t1 + kk3, *t3 = t2 + kk3;
+    for (int i = 0; i < kk3; ++i) o[i] = 0.0;
+    for (int lx = -D; lx <= D; ++lx)
+      for (int ly = -D; ly <= D; ++ly)
+        for (int lz = -D; lz <= D; ++lz) {
+          long sx = tx - lx, sy = ty - ly, sz = tz - lz;
+          if (sx < 0 || sx >= nb || sy < 0 || sy >= nb || sz < 0 || sz >= nb) continue;
+          const double *s = in + ((sx * nb + sy) * nb + sz) * kk3;
+          for (int m = 0; m < M; ++m) {
+            const double *Rx = R + ((size_t)m * nl + lx + D) * kk2;
+            const double *Ry = R + ((size_t)m * nl + ly + D) * kk2;
+            const double *Rz = R + ((size_t)m * nl + lz + D) * kk2;
+            /* t1[ix][jy][jz] = sum_jx Rx[ix][jx] s[jx][jy][jz] */
+            for (int ix = 0; ix < kk; ++ix)
+              for (int q = 0; q < kk2; ++q) {
+                double a = 0.0;
+                for (int jx = 0; jx < kk; ++jx) a += Rx[ix * kk + jx] * s[jx * kk2 + q];
+                t1[ix * kk2 + q] = a;
+              }
+            /* t2[ix][iy][jz] = sum_jy Ry[iy][jy] t1[ix][jy][jz] */
+            for (int ix = 0; ix < kk; ++ix)
+              for (int iy = 0; iy < kk; ++iy)
+                for (int jz = 0; jz < kk; ++jz) {
+                  double a = 0.0;
+                  for (int jy = 0; jy < kk; ++jy) a += Ry[iy * kk + jy] * t1[(ix * kk + jy) * kk + jz];
+                  t2[(ix * kk + iy) * kk + jz] = a;
+                }
+            /* t3[ix][iy][iz] = sum_jz Rz[iz][jz] t2[ix][iy][jz] */
+            for (int q = 0; q < kk2; ++q)
+              for (int iz = 0; iz < kk; ++iz) {
+                double a = 0.0;
+                for (int jz = 0; jz < kk; ++jz) a += Rz[iz * kk + jz] * t2[q * kk + jz];
+                t3[q * kk + iz] = a;
+              }
+            for (int i = 0; i < kk3; ++i) o[i] += c[m] * t3[i];
+          }
+        }
+    free(t1);
+  }
+}
+
+/* k x k blocks of level n for l in [-D, D] (Sec. 2.2 Toeplitz blocks, Sec. 2.3 terms). */
+static double *blocks_level(int k, double L, int n, int M, const double *t, int D) {
+  int nl = 2 * D + 1, k2 = k * k;
+  double h = 2.0 * L / (double)(1L << n);
+  double *R = (double *)malloc(sizeof(double) * (size_t)M * nl * k2);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic)
+#endif
+  for (int q = 0; q < M * nl; ++q) orc_block(k, h, t[q / nl] * h * h, (long)(q % nl - D), R + (size_t)q * k2);
+  return R;
+}
+
+/* 2k x 2k blocks of level n from the level-(n+1) blocks between the children. */
+static double *blocks_level_2k(int k, double L, int n, int M, const double *t, int D) {
+  int Dc = 2 * D + 1, nlc = 2 * Dc + 1, nl = 2 * D + 1, kk = 2 * k, kk2 = kk * kk;
+  double *Rc = blocks_level(k, L, n + 1, M, t, Dc);
+  double *R = (double *)malloc(sizeof(double) * (size_t)M * nl * kk2);
+  for (int m = 0; m < M; ++m)
+    for (int li = 0; li < nl; ++li) {
+      int l = li - D;
+      double *B = R + ((size_t)m * nl + li) * kk2;
+      for (int ci = 0; ci < 2; ++ci)
+        for (int cj = 0; cj < 2; ++cj) {
+          const double *C = Rc + ((size_t)m * nlc + (2 * l + ci - cj) + Dc) * k * k;
+          for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j) B[(ci * k + i) * kk + cj * k + j] = C[i * k + j];
+        }
+    }
+  free(Rc);
+  return R;
+}
+
+/* (Ubar x Ubar x Ubar) v: k^3 -> (2k)^3, Ubar[(c,i)][j] = U^(c)[i][j]. */
+static void unfilter3(int k, const double *Ub, const double *v, double *S) {
+  int kk = 2 * k;
+  double *a = (double *)malloc(sizeof(double) * kk * k * k);
+  double *b = (double *)malloc(sizeof(double) * kk * kk * k);
+  for (int I = 0; I < kk; ++I)
+    for (int q = 0; q < k * k; ++q) {
+      double s = 0.0;
+      for (int j = 0; j < k; ++j) s += Ub[I * k + j] * v[j * k * k + q];
+      a[I * k * k + q] = s;
+    }
+  for (int I = 0; I < kk; ++I)
+    for (int J = 0; J < kk; ++J)
+      for (int l = 0; l < k; ++l) {
+        double s = 0.0;
+        for (int j = 0; j < k; ++j) s += Ub[J * k + j] * a[(I * k + j) * k + l];
+        b[(I * kk + J) * k + l] = s;
+      }
+  for (int q = 0; q < kk * kk; ++q)
+    for (int Lq = 0; Lq < kk; ++Lq) {
+      double s = 0.0;
+      for (int j = 0; j < k; ++j) s += Ub[Lq * k + j] * b[q * k + j];
+      S[q * kk + Lq] = s;
+    }
+  free(a);
+  free(b);
+}
+
+/* (Ubar^T x Ubar^T x Ubar^T) S: (2k)^3 -> k^3. */
+static void filter3(int k, const double *Ub, const double *S, double *v) {
+  int kk = 2 * k;
+  double *a = (double *)malloc(sizeof(double) * k * kk * kk);
+  double *b = (double *)malloc(sizeof(double) * k * k * kk);
+  for (int i = 0; i < k; ++i)
+    for (int q = 0; q < kk * kk; ++q) {
+      double s = 0.0;
+      for (int I = 0; I < kk; ++I) s += Ub[I * k + i] * S[I * kk * kk + q];
+      a[i * kk * kk + q] = s;
+    }
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j)
+      for (int Lq = 0; Lq < kk; ++Lq) {
+        double s = 0.0;
+        for (int J = 0; J < kk; ++J) s += Ub[J * k + j] * a[(i * kk + J) * kk + Lq];
+        b[(i * k + j) * kk + Lq] = s;
+      }
+  for (int q = 0; q < k * k; ++q)
+    for (int l = 0; l < k; ++l) {
+      double s = 0.0;
+      for (int Lq = 0; Lq < kk; ++Lq) s += Ub[Lq * k + l] * b[q * kk + Lq];
+      v[q * k + l] = s;
+    }
+  free(a);
+  free(b);
+}
+
+/* children of box (x,y,z) of level n (dense level n+1 array `fine`) as one (2k)^3 tensor */
+static void gather_children(int k, long nb, long x, long y, long z, const double *fine, double *S) {
+  int kk = 2 * k, k3 = k * k * k;
+  long nf = 2 * nb;
+  for (int cx = 0; cx < 2; ++cx)
+    for (int cy = 0; cy < 2; ++cy)
+      for (int cz = 0; cz < 2; ++cz) {
+        const double *s = fine + (((2 * x + cx) * nf + 2 * y + cy) * nf + 2 * z + cz) * k3;
+        for (int i = 0; i < k; ++i)
+          for (int j = 0; j < k; ++j)
+            for (int l = 0; l < k; ++l) S[((cx * k + i) * kk + cy * k + j) * kk + cz * k + l] = s[(i * k + j) * k + l];
+      }
+}
+
+int orc_apply_ns(int k, double L, int N, int n0, const double *s_in, int M, const double *c, const double *t,
+                 int D, double *r_out, int nthreads) {
+  if (k < 1 || 2 * k > ORC_MAXK || n0 < 0 || n0 > N || N > 10 || M < 1 || D < 0) return -1;
+  gl_init();
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+  int k3 = k * k * k, kk = 2 * k, kk3 = kk * kk * kk;
+  double U0[ORC_MAXK * ORC_MAXK], U1[ORC_MAXK * ORC_MAXK];
+  orc_two_scale(k, U0, U1);
+  double *Ub = (double *)malloc(sizeof(double) * kk * k);
+  for (int cc = 0; cc < 2; ++cc)
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) Ub[(cc * k + i) * k + j] = (cc == 0 ? U0 : U1)[i * k + j];
+  /* compress: s^n and S^n for n = N-1 .. n0 */
+  double *s[11], *S[11];
+  memset(s, 0, sizeof(s));
+  memset(S, 0, sizeof(S));
+  long nbN = 1L << N;
+  s[N] = (double *)malloc(sizeof(double) * nbN * nbN * nbN * k3);
+  memcpy(s[N], s_in, sizeof(double) * nbN * nbN * nbN * k3);
+  for (int n = N - 1; n >= n0; --n) {
+    long nb = 1L << n, nbox = nb * nb * nb;
+    s[n] = (double *)malloc(sizeof(double) * nbox * k3);
+    S[n] = (double *)malloc(sizeof(double) * nbox * kk3);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic)
+#endif
+    for (long b = 0; b < nbox; ++b) {
+      gather_children(k, nb, b / (nb * nb), (b / nb) % nb, b % nb, s[n + 1], S[n] + b * kk3);
+      filter3(k, Ub, S[n] + b * kk3, s[n] + b * k3);
+    }
+  }
+  /* coarsest level: T^{n0} with every displacement */
+  long nb0 = 1L << n0;
+  int D0 = (int)(nb0 - 1);
+  double *R0 = blocks_level(k, L, n0, M, t, D0);
+  double *r = (double *)malloc(sizeof(double) * nb0 * nb0 * nb0 * k3);
+  apply_level_dense(k, nb0, s[n0], R0, c, M, D0, r);
+  free(R0);
+  /* levels n0 .. N-1: r^{n+1} = Ubar (r^n - Z^n) + Y^n */
+  for (int n = n0; n < N; ++n) {
+    long nb = 1L << n, nbox = nb * nb * nb, nf = 2 * nb;
+    int Dn = D < nb - 1 ? D : (int)(nb - 1);
+    double *Rk = blocks_level(k, L, n, M, t, Dn);
+    double *R2 = blocks_level_2k(k, L, n, M, t, Dn);
+    double *Y = (double *)malloc(sizeof(double) * nbox * kk3);
+    double *Z = (double *)malloc(sizeof(double) * nbox * k3);
+    apply_level_dense(kk, nb, S[n], R2, c, M, Dn, Y);
+    apply_level_dense(k, nb, s[n], Rk, c, M, Dn, Z);
+    double *rn = (double *)malloc(sizeof(double) * nf * nf * nf * k3);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic)
+#endif
+    for (long b = 0; b < nbox; ++b) {
+      double *dv = (double *)malloc(sizeof(double) * (k3 + kk3));
+      double *U = dv + k3;
+      for (int i = 0; i < k3; ++i) dv[i] = r[b * k3 + i] - Z[b * k3 + i];
+      unfilter3(k, Ub, dv, U);
+      for (int i = 0; i < kk3; ++i) U[i] += Y[b * kk3 + i];
+      long x = b / (nb * nb), y = (b / nb) % nb, z = b % nb;
+      for (int cx = 0; cx < 2; ++cx)
+        for (int cy = 0; cy < 2; ++cy)
+          for (int cz = 0; cz < 2; ++cz) {
+            double *o = rn + (((2 * x + cx) * nf + 2 * y + cy) * nf + 2 * z + cz) * k3;
+            for (int i = 0; i < k; ++i)
+              for (int j = 0; j < k; ++j)
+                for (int l = 0; l < k; ++l) o[(i * k + j) * k + l] = U[((cx * k + i) * kk + cy * k + j) * kk + cz * k + l];
+          }
+      free(dv);
+    }
+    free(Rk);
+    free(R2);
+    free(Y);
+    free(Z);
+    free(r);
+    r = rn;
+  }
+  memcpy(r_out, r, sizeof(double) * nbN * nbN * nbN * k3);
+  free(r);
+  for (int n = 0; n <= 10; ++n) {
+    free(s[n]);
+    free(S[n]);
+  }
+  free(Ub);
+  return 0;
+}
+
+/* The two-scale transforms alone, for the pins: S = (Ubar x3) v and v = (Ubar^T x3) S. */
+void orc_unfilter3(int k, const double *v, double *S) {
+  double U0[ORC_MAXK * ORC_MAXK], U1[ORC_MAXK * ORC_MAXK], Ub[2 * ORC_MAXK * ORC_MAXK];
+  orc_two_scale(k, U0, U1);
+  for (int cc = 0; cc < 2; ++cc)
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) Ub[(cc * k + i) * k + j] = (cc == 0 ? U0 : U1)[i * k + j];
+  unfilter3(k, Ub, v, S);
+}
+void orc_filter3(int k, const double *S, double *v) {
+  double U0[ORC_MAXK * ORC_MAXK], U1[ORC_MAXK * ORC_MAXK], Ub[2 * ORC_MAXK * ORC_MAXK];
+  orc_two_scale(k, U0, U1);
+  for (int cc = 0; cc < 2; ++cc)
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) Ub[(cc * k + i) * k + j] = (cc == 0 ? U0 : U1)[i * k + j];
+  filter3(k, Ub, S, v);
 }

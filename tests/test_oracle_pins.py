@@ -374,3 +374,60 @@ def test_oracle_mlp_gradient_matches_finite_differences():
     z = (x[0] - xm) / xs
     o = W3 @ np.tanh(W2 @ np.tanh(W1 @ z + b1) + b2) + b3
     assert M.forward(p, x[:1])[0] == pytest.approx(o * ys + ym, rel=1e-14)
+
+
+# ----------------------------------------------------------------- non-standard form (Sec. 2.2)
+
+def test_two_scale_filter_is_projection_to_the_parent_level():
+    """The parent's scaling coefficients of its children's tensor equal the direct projection of
+    the function at the parent level (P^n = P^n P^{n+1}), and filtering undoes unfiltering."""
+    k, L = 4, 8.0
+    f = W.gaussian_sum(2, 0.5, 3.0, seed=41, centre_box=3.0)
+    _, c2, _ = O.project(f, k, L, uniform_level=2)
+    _, c3, _ = O.project(f, k, L, uniform_level=3)
+    nb = 4
+    for (x, y, z) in [(0, 0, 0), (1, 2, 3), (3, 3, 3), (2, 1, 0)]:
+        S = np.zeros((2 * k, 2 * k, 2 * k))
+        for cx in range(2):
+            for cy in range(2):
+                for cz in range(2):
+                    child = ((2 * x + cx) * 2 * nb + 2 * y + cy) * 2 * nb + 2 * z + cz
+                    S[cx * k:(cx + 1) * k, cy * k:(cy + 1) * k, cz * k:(cz + 1) * k] = c3[child]
+        parent = c2[(x * nb + y) * nb + z]
+        assert np.abs(O.filter3(k, S) - parent).max() <= 1e-13 * max(1.0, np.abs(parent).max())
+    v = np.random.default_rng(3).standard_normal((k, k, k))
+    assert np.abs(O.filter3(k, O.unfilter3(k, v)) - v).max() < 1e-14
+
+
+@pytest.mark.parametrize("kernel,mu,k", [(0, 0.0, 3), (1, 1.0, 4)])
+def test_ns_form_with_every_displacement_is_the_level_n_operator(kernel, mu, k):
+    """T^N = T^{n0} + sum_n (A^n + B^n + C^n): with every displacement at every level the
+    non-standard form apply equals the plain level-N apply."""
+    L, N = 8.0, 3
+    f = W.gaussian_sum(2, 1.0, 5.0, seed=7, centre_box=3.0)
+    keys, coeffs, _ = O.project(f, k, L, uniform_level=N)
+    r_lo, r_hi = O.kernel_range(kernel, mu, L, 1e-4)
+    _, _, _, c, t = O.fit_search(mu, 8, r_lo, r_hi)
+    plain = O.apply(keys, coeffs, c, t, L, stencil=0, max_disp=(1 << N) - 1, tau=0.0)
+    assert (plain.keys == keys).all()
+    for n0 in (1, 2):
+        ns = O.apply_ns(coeffs, k, L, N, n0, c, t, (1 << N) - 1)
+        assert np.sqrt(((ns - plain.coeffs) ** 2).sum() / (plain.coeffs ** 2).sum()) < 1e-13
+
+
+def test_ns_form_is_sparse_where_the_leaf_apply_is_not():
+    """Sec. 2.2: A^n decays as r^(-2k-1), B^n and C^n as r^(-k-1).  With |l|_inf <= D at every
+    level the non-standard form approaches T^N quickly in D, while the leaf-level apply with
+    the same stencil misses the operator's long range."""
+    k, L, N = 4, 8.0, 3
+    f = W.gaussian_sum(2, 1.0, 5.0, seed=7, centre_box=3.0)
+    keys, coeffs, _ = O.project(f, k, L, uniform_level=N)
+    r_lo, r_hi = O.kernel_range(0, 0.0, L, 1e-4)
+    _, _, _, c, t = O.fit_search(0.0, 8, r_lo, r_hi)
+    exact = O.apply(keys, coeffs, c, t, L, stencil=0, max_disp=(1 << N) - 1, tau=0.0).coeffs
+    rel = lambda a: np.sqrt(((a - exact) ** 2).sum() / (exact ** 2).sum())
+    e_ns = [rel(O.apply_ns(coeffs, k, L, N, 1, c, t, D)) for D in (1, 2)]
+    e_leaf = [rel(O.apply(keys, coeffs, c, t, L, stencil=0, max_disp=D, tau=0.0).coeffs) for D in (1, 2)]
+    assert e_ns[1] < e_ns[0] < 1e-2
+    assert e_ns[1] < 1e-5
+    assert min(e_leaf) > 0.1
