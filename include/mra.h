@@ -275,6 +275,39 @@ int mra_apply_batched(const mra_operator *op, int nfunc, const mra_tree_view *in
                       const mra_apply_opts *opts, mra_tree_view *out, int64_t *out_offsets, void *workspace,
                       size_t workspace_bytes, mra_apply_stats *stats, void *stream);
 
+/* ---- Non-standard form (Sec. 2.2).  With P^{n+1} = P^n + Q^n the level-N operator is
+ * T^N = T^{n0} + sum_{n=n0}^{N-1} (A^n + B^n + C^n), A^n = Q^n T Q^n, B^n = Q^n T P^n,
+ * C^n = P^n T Q^n, whose blocks decay with the displacement (A as r^(-2k-1), B and C as
+ * r^(-k-1)).  On level n's 2k basis (a box's children's coefficients side by side,
+ * index (c, i) = c k + i per dimension) the level-(n+1) operator has the blocks
+ *     R2k^n_{m,l}[(ci,i)][(cj,j)] = R^{n+1}_{m, 2l+ci-cj}[i][j].
+ *
+ * mra_operator_ns_create: the 2k-basis operator of levels op.min_level .. op.max_level-1
+ * with displacements |l| <= max_disp, assembled on the device from op's blocks (op needs
+ * max_disp >= 2 max_disp + 1 for that); its own norms and BF16 pieces.  2k <= MRA_MAX_K.
+ * Caller frees it with mra_operator_free.  It is an operator of order 2k: mra_apply can
+ * use it on trees of (2k)^3 coefficients. */
+int mra_operator_ns_create(const mra_operator *op, int max_disp, mra_operator **ns_op, void *stream);
+
+/* Workspace bytes of mra_apply_ns (device memory the caller provides, 256-byte aligned). */
+int mra_apply_ns_workspace_size(const mra_operator *op, const mra_operator *ns_op, const mra_tree_view *in,
+                                int n0, const mra_apply_opts *opts, size_t *bytes);
+
+/* Non-standard form apply on a uniform tree.  in: every box of one level N (1..10) in key
+ * order (keys sorted: x slowest), k^3 coefficients each; op: the operator (order k, levels
+ * n0..N, max_disp >= 2^n0 - 1); ns_op: mra_operator_ns_create(op, ...).  Steps: compress
+ * (s^n = filter of the children tensor S^n, n = N-1 .. n0); T^{n0} s^{n0} with every
+ * displacement of level n0; for n = n0 .. N-1, Y^n = T2k^n S^n and Z^n = T^n s^n with
+ * opts' stencil and screen (each an mra_apply on level n's boxes, in opts' precision),
+ * and the children of every box b get U^{x3} (r^n_b - Z^n_b) + Y^n_b as r^{n+1}.  out:
+ * the level-N result, same keys as in (cap >= in->n, else MRA_ERR_CAPACITY with out->n
+ * the size needed).  opts.screen: NONE or NORM.  With every displacement the result equals
+ * mra_apply's level-N result with every displacement.  stats: summed over the applies;
+ * kernel_ms is the apply kernels' time only.  Synchronises the stream. */
+int mra_apply_ns(const mra_operator *op, const mra_operator *ns_op, const mra_tree_view *in, int n0,
+                 const mra_apply_opts *opts, mra_tree_view *out, void *workspace, size_t workspace_bytes,
+                 mra_apply_stats *stats, void *stream);
+
 /* Per-box Frobenius norms (device array of tree->n doubles, may be NULL) and
  * the total L2 norm (host double, may be NULL).  Deterministic reduction. */
 int mra_norm(const mra_tree_view *tree, double *per_box, double *total, void *stream);

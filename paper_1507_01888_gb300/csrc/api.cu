@@ -64,7 +64,7 @@ void gauss_legendre(int n, double *x, double *w) {
 }
 
 // Two-scale matrices U^{(c)}[i][j] = 2^{-1/2} int_0^1 phi_i(y) phi_j((y+c)/2) dy (Sec. 2.2).
-static void two_scale(int k, double *U /* [2][k][k] */) {
+void two_scale(int k, double *U /* [2][k][k] */) {
   int nq = k + 2;
   std::vector<double> x(nq), w(nq);
   gauss_legendre(nq, x.data(), w.data());
@@ -93,7 +93,7 @@ static void two_scale(int k, double *U /* [2][k][k] */) {
   }
 }
 
-static void free_operator(Operator *op) {
+void free_operator(Operator *op) {
   if (!op) return;
   cudaFree(op->d_c);
   cudaFree(op->d_t);

@@ -58,6 +58,8 @@ struct Operator {
 
 // ---------------------------------------------------------------- host helpers
 void gauss_legendre(int n, double *x, double *w);  // nodes/weights on [-1,1]
+void two_scale(int k, double *U /* [2][k][k] */);  // U^(c)[i][j], Sec. 2.2
+void free_operator(Operator *op);
 
 // ---------------------------------------------------------------- launchers (setup)
 cudaError_t launch_fit_search(double mu, int M, double r_lo, double r_hi, double *d_err,

@@ -1,0 +1,460 @@
+// ns.cu -- the operator in non-standard form and its apply on uniform trees (Sec. 2.2).
+//
+// With P^{n+1} = P^n + Q^n the level-N operator T^N = P^N T P^N splits into
+//     T^N = T^{n0} + sum_{n=n0}^{N-1} (A^n + B^n + C^n),
+// A^n = Q^n T Q^n, B^n = Q^n T P^n, C^n = P^n T Q^n.  On level n's 2k basis -- a box's
+// children's k^3 coefficients side by side, S[(cx,i)][(cy,j)][(cz,l)] -- the level-(n+1)
+// operator has the blocks
+//     R2k^n_{m,l}[(ci,i)][(cj,j)] = R^{n+1}_{m, 2l+ci-cj}[i][j]
+// and A^n + B^n + C^n = T2k^n - Ubar T^n Ubar^T with Ubar[(c,i)][j] = U^(c)[i][j].  Its
+// blocks decay with the displacement (A as r^(-2k-1), B and C as r^(-k-1)), so a small
+// displacement range per level reaches the operator's long range through the coarse levels.
+//
+// The apply (uniform level N, every box present):
+//   compress   s^n = (Ubar^T)^{x3} S^n, S^n = children of level n, for n = N-1 .. n0;
+//   coarsest   r^{n0} = T^{n0} s^{n0} with every displacement of level n0;
+//   per level  Y^n = T2k^n S^n and Z^n = T^n s^n (the library's apply on level n's boxes,
+//              |l|_inf <= max_disp, FP64 or split BF16), then
+//              r^{n+1}(children of b) = (Ubar)^{x3} (r^n_b - Z^n_b) + Y^n_b;
+// r^N is the result.  With every displacement it equals the plain level-N apply.
+#include <algorithm>
+#include <vector>
+
+#include "apply_internal.cuh"
+
+namespace mra {
+
+namespace {
+
+// ---------------------------------------------------------------- 2k blocks
+// Blocks of one level of the non-standard operator from the level-(n+1) blocks of op.
+__global__ void ns_blocks_kernel(int k, int M, int D, const double *Rop, int64_t op_base, int Dc,
+                                 double *Rns, int64_t ns_base) {
+  const int nl = 2 * D + 1, nlc = 2 * Dc + 1, kk = 2 * k;
+  const int q = blockIdx.x;  // m * nl + (l + D)
+  if (q >= M * nl) return;
+  const int m = q / nl, l = q % nl - D;
+  double *B = Rns + (ns_base + q) * (int64_t)kk * kk;
+  for (int e = threadIdx.x; e < kk * kk; e += blockDim.x) {
+    const int I = e / kk, J = e % kk, ci = I / k, i = I % k, cj = J / k, j = J % k;
+    const int lc = 2 * l + ci - cj;
+    B[e] = Rop[(op_base + (int64_t)m * nlc + lc + Dc) * k * k + i * k + j];
+  }
+}
+
+// Frobenius norm of every block (for the norm screen).
+__global__ void block_norms_kernel(int64_t nblocks, int kk2, const double *R, double *N) {
+  const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= nblocks) return;
+  double s = 0.0;
+  for (int e = lane; e < kk2; e += 32) {
+    const double v = R[b * kk2 + e];
+    s += v * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) N[b] = sqrt(s);
+}
+
+// ---------------------------------------------------------------- uniform levels
+// Keys of every box of level n in key order (x slowest): box i at (i / nb^2, i / nb % nb, i % nb).
+__global__ void level_keys_kernel(int n, int64_t nbox, uint64_t *keys) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbox) return;
+  const int64_t nb = 1LL << n;
+  keys[i] = make_key(n, i / (nb * nb), (i / nb) % nb, i % nb);
+}
+
+__global__ void check_uniform_kernel(int n, int64_t nbox, const uint64_t *keys, int *err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbox) return;
+  const int64_t nb = 1LL << n;
+  if (keys[i] != make_key(n, i / (nb * nb), (i / nb) % nb, i % nb)) atomicExch(err, 1);
+}
+
+// Rows of an apply's output (keys of level n, any subset) into a zeroed dense level array.
+__global__ void scatter_dense_kernel(int64_t n_rows, const uint64_t *keys, const double *rows, int rowlen,
+                                     double *dense) {
+  const int64_t r = blockIdx.x;
+  if (r >= n_rows) return;
+  const uint64_t key = keys[r];
+  const int64_t nb = 1LL << key_level(key);
+  const int64_t d = (key_x(key) * nb + key_y(key)) * nb + key_z(key);
+  for (int e = threadIdx.x; e < rowlen; e += blockDim.x) dense[d * rowlen + e] = rows[r * rowlen + e];
+}
+
+// ---------------------------------------------------------------- two-scale transforms
+// One CTA per box of level n: S = the children (dense level n+1) as a (2k)^3 tensor, written
+// out, and s = (Ubar^T)^{x3} S.  Shared memory: S (2k)^3, a k (2k)^2, b k^2 (2k) doubles.
+__global__ void compress_kernel(int k, int n, const double *fine, const double *Ub, double *S_out,
+                                double *s_out) {
+  extern __shared__ double sh[];
+  const int kk = 2 * k, k3 = k * k * k, kk3 = kk * kk * kk;
+  double *S = sh, *a = S + kk3, *b = a + k * kk * kk;
+  const int64_t box = blockIdx.x, nb = 1LL << n, nf = 2 * nb;
+  const int64_t x = box / (nb * nb), y = (box / nb) % nb, z = box % nb;
+  for (int e = threadIdx.x; e < kk3; e += blockDim.x) {
+    const int I = e / (kk * kk), J = (e / kk) % kk, Lq = e % kk;
+    const int64_t child = ((2 * x + I / k) * nf + 2 * y + J / k) * nf + 2 * z + Lq / k;
+    const double v = fine[child * k3 + ((I % k) * k + J % k) * k + Lq % k];
+    S[e] = v;
+    S_out[box * kk3 + e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < k * kk * kk; e += blockDim.x) {  // a[i][J][L] = sum_I Ub[I][i] S[I][J][L]
+    const int i = e / (kk * kk), q = e % (kk * kk);
+    double v = 0.0;
+    for (int I = 0; I < kk; ++I) v += Ub[I * k + i] * S[I * kk * kk + q];
+    a[e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < k * k * kk; e += blockDim.x) {  // b[i][j][L] = sum_J Ub[J][j] a[i][J][L]
+    const int i = e / (k * kk), j = (e / kk) % k, Lq = e % kk;
+    double v = 0.0;
+    for (int J = 0; J < kk; ++J) v += Ub[J * k + j] * a[(i * kk + J) * kk + Lq];
+    b[e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < k3; e += blockDim.x) {  // s[i][j][l] = sum_L Ub[L][l] b[i][j][L]
+    const int q = e / k, l = e % k;
+    double v = 0.0;
+    for (int Lq = 0; Lq < kk; ++Lq) v += Ub[Lq * k + l] * b[q * kk + Lq];
+    s_out[box * k3 + e] = v;
+  }
+}
+
+// One CTA per box of level n: r^{n+1}(children) = (Ubar)^{x3} (r_b - Z_b) + Y_b, into the
+// dense level n+1 array.  Shared memory: d k^3, a (2k) k^2, b (2k)^2 k doubles.
+__global__ void sum_down_kernel(int k, int n, const double *r, const double *Z, const double *Y,
+                                const double *Ub, double *fine) {
+  extern __shared__ double sh[];
+  const int kk = 2 * k, k2 = k * k, k3 = k2 * k, kk3 = kk * kk * kk;
+  double *d = sh, *a = d + k3, *b = a + kk * k2;
+  const int64_t box = blockIdx.x, nb = 1LL << n, nf = 2 * nb;
+  const int64_t x = box / (nb * nb), y = (box / nb) % nb, z = box % nb;
+  for (int e = threadIdx.x; e < k3; e += blockDim.x) d[e] = r[box * k3 + e] - Z[box * k3 + e];
+  __syncthreads();
+  for (int e = threadIdx.x; e < kk * k2; e += blockDim.x) {  // a[I][j][l] = sum_i Ub[I][i] d[i][j][l]
+    const int I = e / k2, q = e % k2;
+    double v = 0.0;
+    for (int i = 0; i < k; ++i) v += Ub[I * k + i] * d[i * k2 + q];
+    a[e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kk * kk * k; e += blockDim.x) {  // b[I][J][l] = sum_j Ub[J][j] a[I][j][l]
+    const int I = e / (kk * k), J = (e / k) % kk, l = e % k;
+    double v = 0.0;
+    for (int j = 0; j < k; ++j) v += Ub[J * k + j] * a[(I * k + j) * k + l];
+    b[e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kk3; e += blockDim.x) {  // + sum_l Ub[L][l] b[I][J][l] + Y
+    const int I = e / (kk * kk), J = (e / kk) % kk, Lq = e % kk;
+    double v = Y[box * kk3 + e];
+    for (int l = 0; l < k; ++l) v += Ub[Lq * k + l] * b[(I * kk + J) * k + l];
+    const int64_t child = ((2 * x + I / k) * nf + 2 * y + J / k) * nf + 2 * z + Lq / k;
+    fine[child * k3 + ((I % k) * k + J % k) * k + Lq % k] = v;
+  }
+}
+
+inline size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
+inline int64_t boxes(int n) { return 1LL << (3 * n); }
+
+// Options of the per-level applies and of the coarsest level's complete apply.
+mra_apply_opts level_opts(const mra_apply_opts &o) { return o; }
+mra_apply_opts coarse_opts(const mra_apply_opts &o, int n0) {
+  mra_apply_opts c = o;
+  c.stencil = MRA_STENCIL_SHELLS;
+  c.max_disp = (int)((1LL << n0) - 1);
+  return c;
+}
+
+// Workspace of mra_apply_ns: dense s^n, S^n (n0 <= n < N), r ping-pong, Y, Z (level N-1
+// sizes), Ubar, an error word, one level's keys, the per-level apply outputs (keys +
+// coefficients of Y and of Z / the coarse r), and the largest per-level apply workspace.
+struct NsLayout {
+  std::vector<size_t> s, S;
+  size_t rA, rB, Yd, Zd, Ub, err, keys, yk, yc, zk, zc, apply, total;
+  size_t apply_bytes;
+};
+
+NsLayout ns_layout(const Operator &op, const Operator &ns, int N, int n0, const mra_apply_opts &o) {
+  NsLayout L{};
+  const int k = op.k, kk = 2 * k;
+  const size_t k3 = (size_t)k * k * k, kk3 = (size_t)kk * kk * kk;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off = al(off + (bytes ? bytes : 1));
+    return at;
+  };
+  L.s.assign(N + 1, 0);
+  L.S.assign(N + 1, 0);
+  for (int n = n0; n < N; ++n) {
+    L.s[n] = take(boxes(n) * k3 * 8);
+    L.S[n] = take(boxes(n) * kk3 * 8);
+  }
+  const int64_t nt = boxes(N - 1);
+  L.rA = take(nt * k3 * 8);
+  L.rB = take(nt * k3 * 8);
+  L.Yd = take(nt * kk3 * 8);
+  L.Zd = take(nt * k3 * 8);
+  L.Ub = take((size_t)kk * k * 8);
+  L.err = take(8);
+  L.keys = take(nt * 8);
+  L.yk = take(nt * 8);
+  L.yc = take(nt * kk3 * 8);
+  L.zk = take(nt * 8);
+  L.zc = take(nt * k3 * 8);
+  size_t ab = apply_workspace_bytes(op, coarse_opts(o, n0), boxes(n0));
+  for (int n = n0; n < N; ++n) {
+    ab = std::max(ab, apply_workspace_bytes(op, level_opts(o), boxes(n)));
+    ab = std::max(ab, apply_workspace_bytes(ns, level_opts(o), boxes(n)));
+  }
+  L.apply_bytes = ab;
+  L.apply = take(ab);
+  L.total = off;
+  return L;
+}
+
+int ns_check(const Operator *op, const Operator *ns, const mra_tree_view *in, int n0, const mra_apply_opts *o,
+             int *N_out) {
+  if (!op || !ns) return fail(MRA_ERR_ARG, "mra_apply_ns: NULL operator");
+  if (!in || !o) return fail(MRA_ERR_ARG, "mra_apply_ns: NULL argument");
+  if (ns->k != 2 * op->k || ns->M != op->M || ns->L != op->L)
+    return fail(MRA_ERR_ARG, "mra_apply_ns: the second operator is not the non-standard form of the first");
+  if (in->k != op->k || in->L != op->L) return fail(MRA_ERR_ARG, "mra_apply_ns: tree k or L differs from the operator");
+  if (in->n <= 0 || !in->keys || !in->coeffs) return fail(MRA_ERR_ARG, "mra_apply_ns: empty input tree");
+  int N = -1;
+  for (int n = 1; n <= 10; ++n)
+    if (in->n == boxes(n)) N = n;
+  if (N < 0) return fail(MRA_ERR_ARG, "mra_apply_ns: %lld boxes is not a whole level 1..10", (long long)in->n);
+  if (n0 < 0 || n0 >= N) return fail(MRA_ERR_ARG, "mra_apply_ns: coarsest level %d outside 0..%d", n0, N - 1);
+  if (n0 < op->min_level || N - 1 > op->max_level || n0 < ns->min_level || N - 1 > ns->max_level)
+    return fail(MRA_ERR_ARG, "mra_apply_ns: levels %d..%d outside the operators' tables", n0, N - 1);
+  if (o->precision != MRA_PREC_FP64 && o->precision != MRA_PREC_SPLIT_BF16)
+    return fail(MRA_ERR_ARG, "mra_apply_ns: unknown precision %d", o->precision);
+  if (o->precision == MRA_PREC_SPLIT_BF16 && (o->pieces < 2 || o->pieces > 3))
+    return fail(MRA_ERR_ARG, "mra_apply_ns: pieces must be 2 or 3");
+  if (o->screen != MRA_SCREEN_NONE && o->screen != MRA_SCREEN_NORM)
+    return fail(MRA_ERR_ARG, "mra_apply_ns: screen must be MRA_SCREEN_NONE or MRA_SCREEN_NORM");
+  if (o->screen == MRA_SCREEN_NORM && !(o->tau >= 0.0)) return fail(MRA_ERR_ARG, "mra_apply_ns: tau must be >= 0");
+  if (o->stencil != MRA_STENCIL_SHELLS && o->stencil != MRA_STENCIL_NEAREST)
+    return fail(MRA_ERR_ARG, "mra_apply_ns: unknown stencil %d", o->stencil);
+  const int D = o->stencil == MRA_STENCIL_NEAREST ? 1 : o->max_disp;
+  if (D < 0 || D > ns->max_disp || D > op->max_disp)
+    return fail(MRA_ERR_ARG, "mra_apply_ns: max_disp %d outside the operators' range", D);
+  if ((1LL << n0) - 1 > op->max_disp)
+    return fail(MRA_ERR_ARG, "mra_apply_ns: the complete level-%d apply needs an operator with max_disp >= %lld", n0,
+                (long long)((1LL << n0) - 1));
+  *N_out = N;
+  return MRA_OK;
+}
+
+}  // namespace
+
+}  // namespace mra
+
+using namespace mra;
+
+extern "C" int mra_operator_ns_create(const mra_operator *h, int max_disp, mra_operator **out, void *stream) {
+  const Operator *op = reinterpret_cast<const Operator *>(h);
+  if (!op || !out) return fail(MRA_ERR_ARG, "mra_operator_ns_create: NULL argument");
+  *out = nullptr;
+  if (2 * op->k > MRA_MAX_K) return fail(MRA_ERR_ARG, "mra_operator_ns_create: 2k=%d above %d", 2 * op->k, MRA_MAX_K);
+  if (op->max_level <= op->min_level)
+    return fail(MRA_ERR_ARG, "mra_operator_ns_create: the operator needs at least two levels");
+  if (max_disp < 0) return fail(MRA_ERR_ARG, "mra_operator_ns_create: max_disp < 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  Operator *ns = new Operator();
+  auto bail = [&](int code) {
+    free_operator(ns);
+    return code;
+  };
+  ns->kernel = op->kernel;
+  ns->mu = op->mu;
+  ns->M = op->M;
+  ns->k = 2 * op->k;
+  ns->L = op->L;
+  ns->min_level = op->min_level;
+  ns->max_level = op->max_level - 1;
+  ns->max_disp = max_disp;
+  ns->h_fit = op->h_fit;
+  ns->s_lo = op->s_lo;
+  ns->fit_err = op->fit_err;
+  ns->r_lo = op->r_lo;
+  ns->r_hi = op->r_hi;
+  ns->c = op->c;
+  ns->t = op->t;
+  std::vector<int> Dabs(20, 0);
+  std::vector<int64_t> off_abs(20, -1);
+  int64_t nb = 0;
+  for (int n = ns->min_level; n <= ns->max_level; ++n) {
+    const int D = (int)std::min<int64_t>(max_disp, (1LL << n) - 1);
+    if (2 * D + 1 > op->D[n + 1 - op->min_level])
+      return bail(fail(MRA_ERR_ARG, "mra_operator_ns_create: level %d needs the operator's max_disp >= %d", n + 1,
+                       2 * D + 1));
+    Dabs[n] = D;
+    off_abs[n] = nb;
+    ns->D.push_back(D);
+    ns->level_off.push_back(nb);
+    nb += (int64_t)ns->M * (2 * D + 1);
+  }
+  ns->n_blocks = nb;
+  const size_t kk2 = (size_t)ns->k * ns->k;
+  if (cudaMalloc((void **)&ns->d_c, ns->M * 8) != cudaSuccess || cudaMalloc((void **)&ns->d_t, ns->M * 8) != cudaSuccess ||
+      cudaMalloc((void **)&ns->d_R, nb * kk2 * 8) != cudaSuccess || cudaMalloc((void **)&ns->d_N, nb * 8) != cudaSuccess ||
+      cudaMalloc((void **)&ns->d_D, 20 * sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void **)&ns->d_level_off, 20 * sizeof(int64_t)) != cudaSuccess)
+    return bail(fail(MRA_ERR_CUDA, "mra_operator_ns_create: cudaMalloc failed"));
+  cudaError_t e = cudaMemcpyAsync(ns->d_c, ns->c.data(), ns->M * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ns->d_t, ns->t.data(), ns->M * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ns->d_D, Dabs.data(), 20 * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ns->d_level_off, off_abs.data(), 20 * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+  for (int n = ns->min_level; n <= ns->max_level && e == cudaSuccess; ++n) {
+    const int li = n - ns->min_level, lc = n + 1 - op->min_level;
+    const int D = ns->D[li];
+    ns_blocks_kernel<<<(unsigned)(ns->M * (2 * D + 1)), 256, 0, s>>>(op->k, ns->M, D, op->d_R, op->level_off[lc],
+                                                                       op->D[lc], ns->d_R, ns->level_off[li]);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    block_norms_kernel<<<(unsigned)((nb + 7) / 8), 256, 0, s>>>(nb, (int)kk2, ns->d_R, ns->d_N);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return bail(fail(MRA_ERR_CUDA, "mra_operator_ns_create: %s", cudaGetErrorString(e)));
+  int rc = split_blocks_build(*ns, s);  // BF16 pieces of the 2k blocks for the tensor-core path
+  if (rc != MRA_OK) return bail(rc);
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return bail(fail(MRA_ERR_CUDA, "mra_operator_ns_create: %s", cudaGetErrorString(e)));
+  *out = reinterpret_cast<mra_operator *>(ns);
+  return MRA_OK;
+}
+
+extern "C" int mra_apply_ns_workspace_size(const mra_operator *h, const mra_operator *hns, const mra_tree_view *in,
+                                           int n0, const mra_apply_opts *o, size_t *bytes) {
+  const Operator *op = reinterpret_cast<const Operator *>(h);
+  const Operator *ns = reinterpret_cast<const Operator *>(hns);
+  if (!bytes) return fail(MRA_ERR_ARG, "mra_apply_ns_workspace_size: NULL bytes");
+  int N = 0;
+  int rc = ns_check(op, ns, in, n0, o, &N);
+  if (rc) return rc;
+  *bytes = ns_layout(*op, *ns, N, n0, *o).total;
+  return MRA_OK;
+}
+
+extern "C" int mra_apply_ns(const mra_operator *h, const mra_operator *hns, const mra_tree_view *in, int n0,
+                            const mra_apply_opts *o, mra_tree_view *out, void *workspace, size_t workspace_bytes,
+                            mra_apply_stats *stats, void *stream) {
+  const Operator *op = reinterpret_cast<const Operator *>(h);
+  const Operator *ns = reinterpret_cast<const Operator *>(hns);
+  int N = 0;
+  int rc = ns_check(op, ns, in, n0, o, &N);
+  if (rc) return rc;
+  if (!out || !out->keys || !out->coeffs || out->k != op->k)
+    return fail(MRA_ERR_ARG, "mra_apply_ns: output view missing or of another k");
+  if (out->cap < in->n) {
+    out->n = in->n;
+    return fail(MRA_ERR_CAPACITY, "mra_apply_ns: output capacity %lld < %lld", (long long)out->cap,
+                (long long)in->n);
+  }
+  const NsLayout Lw = ns_layout(*op, *ns, N, n0, *o);
+  if (!workspace || workspace_bytes < Lw.total)
+    return fail(MRA_ERR_CAPACITY, "mra_apply_ns: workspace of %zu bytes < %zu needed", workspace_bytes, Lw.total);
+  cudaStream_t s = (cudaStream_t)stream;
+  char *w = (char *)workspace;
+  const int k = op->k, kk = 2 * k;
+  const int k3 = k * k * k, kk3 = kk * kk * kk;
+  double *Ub = (double *)(w + Lw.Ub);
+  int *d_err = (int *)(w + Lw.err);
+  uint64_t *keys = (uint64_t *)(w + Lw.keys);
+  // Ubar[(c,i)][j] = U^(c)[i][j]
+  std::vector<double> U(2 * k * k), Ubh(2 * k * k);
+  two_scale(k, U.data());
+  for (int c = 0; c < 2; ++c)
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) Ubh[(c * k + i) * k + j] = U[c * k * k + i * k + j];
+  MRA_CUDA_TRY(cudaMemcpyAsync(Ub, Ubh.data(), Ubh.size() * 8, cudaMemcpyHostToDevice, s));
+  MRA_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+  check_uniform_kernel<<<(unsigned)((in->n + 255) / 256), 256, 0, s>>>(N, in->n, in->keys, d_err);
+  MRA_CUDA_TRY(cudaGetLastError());
+  int herr = 0;
+  MRA_CUDA_TRY(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  if (herr) return fail(MRA_ERR_ARG, "mra_apply_ns: the input is not every box of level %d in key order", N);
+
+  // ---- compress: S^n and s^n for n = N-1 .. n0
+  const size_t sh_c = (size_t)(kk3 + k * kk * kk + k * k * kk) * 8;
+  const size_t sh_d = (size_t)(k3 + kk * k * k + kk * kk * k) * 8;
+  MRA_CUDA_TRY(cudaFuncSetAttribute(compress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_c));
+  MRA_CUDA_TRY(cudaFuncSetAttribute(sum_down_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_d));
+  for (int n = N - 1; n >= n0; --n) {
+    const double *fine = n == N - 1 ? in->coeffs : (const double *)(w + Lw.s[n + 1]);
+    compress_kernel<<<(unsigned)boxes(n), 256, sh_c, s>>>(k, n, fine, Ub, (double *)(w + Lw.S[n]),
+                                                          (double *)(w + Lw.s[n]));
+    MRA_CUDA_TRY(cudaGetLastError());
+  }
+
+  mra_apply_stats acc{};
+  auto add_stats = [&](const mra_apply_stats &st) {
+    acc.pairs += st.pairs;
+    acc.terms_kept += st.terms_kept;
+    acc.terms_screened += st.terms_screened;
+    acc.terms_issued += st.terms_issued;
+    acc.sources_truncated += st.sources_truncated;
+    acc.skipped_bound += st.skipped_bound;
+    acc.kernel_ms += st.kernel_ms;
+  };
+  void *aws = w + Lw.apply;
+  // one apply on every box of level n: its output rows scattered into a zeroed dense array
+  auto level_apply = [&](const Operator &opx, int n, const double *coeffs, const mra_apply_opts &oo,
+                         uint64_t *okeys, double *ocoeffs, double *dense) -> int {
+    const int64_t nbx = boxes(n);
+    const int rowlen = opx.k * opx.k * opx.k;
+    level_keys_kernel<<<(unsigned)((nbx + 255) / 256), 256, 0, s>>>(n, nbx, keys);
+    MRA_CUDA_TRY(cudaGetLastError());
+    mra_tree_view vin{nbx, nbx, keys, const_cast<double *>(coeffs), opx.k, opx.L};
+    mra_tree_view vout{0, nbx, okeys, ocoeffs, opx.k, opx.L};
+    mra_apply_stats st{};
+    int rc2 = apply_run(opx, vin, oo, vout, aws, Lw.apply_bytes, &st, s);
+    if (rc2 != MRA_OK) return rc2;
+    add_stats(st);
+    MRA_CUDA_TRY(cudaMemsetAsync(dense, 0, (size_t)nbx * rowlen * 8, s));
+    if (vout.n > 0) {
+      scatter_dense_kernel<<<(unsigned)vout.n, 128, 0, s>>>(vout.n, okeys, ocoeffs, rowlen, dense);
+      MRA_CUDA_TRY(cudaGetLastError());
+    }
+    return MRA_OK;
+  };
+  uint64_t *yk = (uint64_t *)(w + Lw.yk), *zk = (uint64_t *)(w + Lw.zk);
+  double *yc = (double *)(w + Lw.yc), *zc = (double *)(w + Lw.zc);
+  double *Yd = (double *)(w + Lw.Yd), *Zd = (double *)(w + Lw.Zd);
+  double *rcur = (double *)(w + Lw.rA), *rnext = (double *)(w + Lw.rB);
+
+  // ---- coarsest level: T^{n0} with every displacement
+  rc = level_apply(*op, n0, (const double *)(w + Lw.s[n0]), coarse_opts(*o, n0), zk, zc, rcur);
+  if (rc != MRA_OK) return rc;
+  // ---- levels n0 .. N-1
+  for (int n = n0; n < N; ++n) {
+    rc = level_apply(*ns, n, (const double *)(w + Lw.S[n]), level_opts(*o), yk, yc, Yd);
+    if (rc != MRA_OK) return rc;
+    rc = level_apply(*op, n, (const double *)(w + Lw.s[n]), level_opts(*o), zk, zc, Zd);
+    if (rc != MRA_OK) return rc;
+    double *fine = n == N - 1 ? out->coeffs : rnext;
+    sum_down_kernel<<<(unsigned)boxes(n), 256, sh_d, s>>>(k, n, rcur, Zd, Yd, Ub, fine);
+    MRA_CUDA_TRY(cudaGetLastError());
+    std::swap(rcur, rnext);
+  }
+  MRA_CUDA_TRY(cudaMemcpyAsync(out->keys, in->keys, (size_t)in->n * 8, cudaMemcpyDeviceToDevice, s));
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  out->n = in->n;
+  out->L = op->L;
+  if (stats) {
+    acc.n_in = in->n;
+    acc.n_out = in->n;
+    *stats = acc;
+  }
+  return MRA_OK;
+}

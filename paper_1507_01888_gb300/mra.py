@@ -39,6 +39,7 @@ EXPORTED = [
     "mra_operator_info", "mra_operator_block", "mra_operator_free", "mra_apply_workspace_size",
     "mra_apply", "mra_apply_batched", "mra_norm", "mra_norm_noalloc", "mra_compare", "mra_log_terms", "mra_mlp_init",
     "mra_mlp_standardize", "mra_mlp_forward", "mra_mlp_workspace_size", "mra_mlp_grad", "mra_mlp_train",
+    "mra_operator_ns_create", "mra_apply_ns_workspace_size", "mra_apply_ns",
 ]
 NOALLOC_MAX_BOXES = 1 << 20
 
@@ -120,6 +121,10 @@ def load(build_if_stale: bool = True):
                                   P(ApplyStats), vp]
         lib.mra_apply_batched.argtypes = [vp, i, P(TreeView), P(ctypes.c_int64), P(ApplyOpts), P(TreeView),
                                           P(ctypes.c_int64), vp, ctypes.c_size_t, P(ApplyStats), vp]
+        lib.mra_operator_ns_create.argtypes = [vp, i, P(vp), vp]
+        lib.mra_apply_ns_workspace_size.argtypes = [vp, vp, P(TreeView), i, P(ApplyOpts), P(ctypes.c_size_t)]
+        lib.mra_apply_ns.argtypes = [vp, vp, P(TreeView), i, P(ApplyOpts), P(TreeView), vp, ctypes.c_size_t,
+                                     P(ApplyStats), vp]
         lib.mra_norm.argtypes = [P(TreeView), vp, P(d), vp]
         lib.mra_norm_noalloc.argtypes = [P(TreeView), vp, P(d), vp]
         lib.mra_compare.argtypes = [P(TreeView), P(TreeView), P(CompareResult), vp]
@@ -259,6 +264,19 @@ class Operator:
             self.close()
         except Exception:
             pass
+
+
+class NSOperator(Operator):
+    """mra_operator_ns_create: the non-standard form (Sec. 2.2) of `op` -- order 2k, levels
+    op.min_level .. op.max_level - 1, displacements |l| <= max_disp."""
+
+    def __init__(self, op: "Operator", max_disp: int = 1, stream=None):
+        h = ctypes.c_void_p()
+        _check(load().mra_operator_ns_create(op.handle, int(max_disp), ctypes.byref(h), _stream(stream)))
+        self._h = h
+        self.kernel, self.M, self.k, self.L = op.kernel, op.M, 2 * op.k, op.L
+        self.min_level, self.max_level, self.max_disp = op.min_level, op.max_level - 1, max_disp
+        self.base = op  # the order-k operator stays alive with it
 
 
 def make_opts(precision=PREC_FP64, pieces=3, screen=SCREEN_NONE, tau=0.0, stencil=STENCIL_NEAREST,
@@ -438,3 +456,34 @@ def mlp_train(params, adam_state, features, targets, batch: int, steps: int, ste
                                 int(batch), int(steps), int(step0), float(lr), int(seed), ctypes.byref(loss),
                                 _vp(ws), ws.numel(), _stream(stream)))
     return loss.value
+
+
+# --------------------------------------------------------------------------- non-standard form
+
+class NSApplier:
+    """mra_apply_ns with its workspace and output allocated once (uniform level-N trees)."""
+
+    def __init__(self, op: Operator, ns_op: NSOperator, tree: "Tree", n0: int, opts: ApplyOpts):
+        self.op, self.ns_op, self.n0, self.opts = op, ns_op, int(n0), opts
+        v = tree.view()
+        nbytes = ctypes.c_size_t()
+        _check(load().mra_apply_ns_workspace_size(op.handle, ns_op.handle, ctypes.byref(v), self.n0,
+                                                  ctypes.byref(opts), ctypes.byref(nbytes)))
+        self.ws = torch.empty(max(nbytes.value, 1), dtype=torch.uint8, device=tree.keys.device)
+        self.out = Tree.empty(tree.n, op.k, op.L, tree.keys.device)
+        self.stats = ApplyStats()
+
+    def __call__(self, tree: "Tree", stream=None) -> "Tree":
+        vin, vout = tree.view(), self.out.view()
+        _check(load().mra_apply_ns(self.op.handle, self.ns_op.handle, ctypes.byref(vin), self.n0,
+                                   ctypes.byref(self.opts), ctypes.byref(vout), ctypes.c_void_p(self.ws.data_ptr()),
+                                   self.ws.numel(), ctypes.byref(self.stats), _stream(stream)))
+        self.out.n = int(vout.n)
+        return self.out
+
+
+def apply_ns(op: Operator, ns_op: NSOperator, tree: "Tree", n0: int, opts: ApplyOpts, stream=None):
+    """mra_apply_ns once; returns (output tree, stats dict)."""
+    ap = NSApplier(op, ns_op, tree, n0, opts)
+    out = ap(tree, stream)
+    return out, ap.stats.as_dict()

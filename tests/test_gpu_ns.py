@@ -1,0 +1,108 @@
+"""Non-standard form apply (Sec. 2.2) through the C ABI against the CPU oracle.
+
+FP64: relative L2 <= 1e-12 against the oracle's non-standard form with the same displacement
+range, and equality with the library's own plain level-N apply when every displacement is
+kept (the identity T^N = T^{n0} + sum (A^n + B^n + C^n)).  Split BF16x3: relative L2 <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mra():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1507_01888_gb300 import mra as m
+    m.load()
+    return m
+
+
+def rel(a, b):
+    return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
+
+
+def uniform_case(mra, k, N, kernel=0, mu=0.0, M=8, L=8.0, seed=7, op_disp=None):
+    f = W.gaussian_sum(2, 1.0, 5.0, seed=seed, centre_box=3.0)
+    keys, coeffs, _ = O.project(f, k, L, uniform_level=N)
+    op = mra.Operator(kernel, M, k, L, 0, N, max_disp=op_disp if op_disp is not None else (1 << N) - 1,
+                      mu=mu, fit_eps=1e-4)
+    fit = op.fit()
+    return keys, coeffs, op, fit
+
+
+@pytest.mark.parametrize("k,N,n0,D", [(3, 3, 1, 1), (4, 3, 1, 2), (4, 3, 2, 1), (6, 2, 1, 1), (8, 3, 1, 1)])
+def test_ns_fp64_matches_oracle(mra, k, N, n0, D):
+    keys, coeffs, op, fit = uniform_case(mra, k, N)
+    ns_op = mra.NSOperator(op, max_disp=D)
+    tree = mra.Tree.from_host(keys, coeffs, 8.0)
+    opts = mra.make_opts(stencil=mra.STENCIL_SHELLS, max_disp=D)
+    out, st = mra.apply_ns(op, ns_op, tree, n0, opts)
+    gk, gc = out.host()
+    assert (gk == keys).all()
+    ref = O.apply_ns(coeffs, k, 8.0, N, n0, fit["c"], fit["t"], D)
+    assert rel(gc, ref) <= 1e-12
+
+
+def test_ns_with_every_displacement_equals_the_plain_apply(mra):
+    k, N = 4, 3
+    keys, coeffs, op, fit = uniform_case(mra, k, N, kernel=1, mu=1.0)
+    D = (1 << N) - 1
+    ns_op = mra.NSOperator(op, max_disp=D)
+    tree = mra.Tree.from_host(keys, coeffs, 8.0)
+    out, _ = mra.apply_ns(op, ns_op, tree, 1, mra.make_opts(stencil=mra.STENCIL_SHELLS, max_disp=D))
+    plain, _ = mra.apply(op, tree, mra.make_opts(stencil=mra.STENCIL_SHELLS, max_disp=D))
+    pk, pc = plain.host()
+    assert (pk == keys).all()
+    assert rel(out.host()[1], pc) <= 1e-12
+
+
+def test_ns_is_accurate_where_the_leaf_apply_is_not(mra):
+    """With |l| <= 2 per level the NS form is within 1e-5 of T^N; the leaf-level apply with the
+    same stencil is not within 10%."""
+    k, N = 4, 3
+    keys, coeffs, op, fit = uniform_case(mra, k, N)
+    tree = mra.Tree.from_host(keys, coeffs, 8.0)
+    full = (1 << N) - 1
+    exact, _ = mra.apply(op, tree, mra.make_opts(stencil=mra.STENCIL_SHELLS, max_disp=full))
+    ex = exact.host()[1]
+    ns_op = mra.NSOperator(op, max_disp=2)
+    out, _ = mra.apply_ns(op, ns_op, tree, 1, mra.make_opts(stencil=mra.STENCIL_SHELLS, max_disp=2))
+    leaf, _ = mra.apply(op, tree, mra.make_opts(stencil=mra.STENCIL_SHELLS, max_disp=2))
+    assert rel(out.host()[1], ex) < 1e-5
+    assert rel(leaf.host()[1], ex) > 0.1
+
+
+@pytest.mark.parametrize("k,N,D", [(4, 4, 1), (6, 3, 1), (8, 3, 1)])
+def test_ns_split_matches_oracle(mra, k, N, D):
+    keys, coeffs, op, fit = uniform_case(mra, k, N, op_disp=3)
+    ns_op = mra.NSOperator(op, max_disp=D)
+    tree = mra.Tree.from_host(keys, coeffs, 8.0)
+    for v in (0, 1, 2):
+        opts = mra.make_opts(precision=mra.PREC_SPLIT_BF16, stencil=mra.STENCIL_SHELLS, max_disp=D)
+        opts.tile_variant = v
+        out, _ = mra.apply_ns(op, ns_op, tree, 1, opts)
+        ref = O.apply_ns(coeffs, k, 8.0, N, 1, fit["c"], fit["t"], D)
+        assert rel(out.host()[1], ref) <= 1e-6
+
+
+def test_ns_rejects_bad_inputs(mra):
+    k, N = 4, 3
+    keys, coeffs, op, fit = uniform_case(mra, k, N, op_disp=3)
+    ns_op = mra.NSOperator(op, max_disp=1)
+    opts = mra.make_opts(stencil=mra.STENCIL_SHELLS, max_disp=1)
+    tree = mra.Tree.from_host(keys, coeffs, 8.0)
+    with pytest.raises(mra.MraError):          # n0 must be below N
+        mra.apply_ns(op, ns_op, tree, N, opts)
+    with pytest.raises(mra.MraError):          # not a whole level
+        mra.apply_ns(op, ns_op, mra.Tree.from_host(keys[:-1], coeffs[:-1], 8.0), 1, opts)
+    shuffled = keys.copy()
+    shuffled[[0, 1]] = shuffled[[1, 0]]
+    with pytest.raises(mra.MraError):          # boxes out of key order
+        mra.apply_ns(op, ns_op, mra.Tree.from_host(shuffled, coeffs, 8.0), 1, opts)
+    with pytest.raises(mra.MraError):          # the operator's blocks must reach 2 D + 1 at level n+1
+        mra.NSOperator(mra.Operator(0, 8, k, 8.0, 0, N, max_disp=1, fit_eps=1e-4), max_disp=1)
