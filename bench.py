@@ -210,11 +210,134 @@ def reduce_over_ranks(n_local: int, ms_local: float, world: int, device=None):
     return int(round(n.item())), float(t.item())
 
 
+def ns_terms(N: int, n0: int, D: int, M: int):
+    """Kept terms of each apply of the non-standard form without a screen: (level, order factor,
+    terms) with order factor 1 for the k-basis applies and 2 for the 2k-basis applies."""
+    def pairs(n, d):  # in-cell (box, l) pairs of a whole level with |l|_inf <= d
+        nb = 1 << n
+        per_dim = sum(min(nb - 1, x + d) - max(0, x - d) + 1 for x in range(nb))
+        return per_dim ** 3
+    out = [(n0, 1, pairs(n0, (1 << n0) - 1) * M)]
+    for n in range(n0, N):
+        dn = min(D, (1 << n) - 1)
+        out += [(n, 2, pairs(n, dn) * M), (n, 1, pairs(n, dn) * M)]
+    return out
+
+
+def run_ns(args, w, rank, world):
+    """The non-standard form apply (mra_apply_ns) on a uniform tree; same JSON line."""
+    import torch
+    from paper_1507_01888_gb300 import mra, autotune
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    N, n0, D = w.uniform_level, w.extra["ns"]["n0"], w.max_disp
+    prec = mra.PREC_FP64 if args.precision == "fp64" else mra.PREC_SPLIT_BF16
+    tree = mra.project(w.funcs[0], w.k, w.L, uniform_level=N)
+    op = mra.Operator(w.kernel, w.M, w.k, w.L, 0, N, max_disp=max(2 * D + 1, (1 << n0) - 1), mu=w.mu,
+                      fit_eps=w.fit_eps)
+    ns_op = mra.NSOperator(op, max_disp=D)
+    opts = mra.make_opts(precision=prec, pieces=args.pieces, stencil=mra.STENCIL_SHELLS, max_disp=D)
+    tuning = {}
+    if prec == mra.PREC_SPLIT_BF16:
+        def make(o):
+            return mra.NSApplier(op, ns_op, tree, n0, o)
+        opts, table = autotune.tune(op, tree, opts, make_applier=make)
+        tuning = {"tile_variant": opts.tile_variant, "candidates_ms": table}
+    ap = mra.NSApplier(op, ns_op, tree, n0, opts)
+    ap(tree)
+    torch.cuda.synchronize()
+    accuracy = {}
+    if prec != mra.PREC_FP64:
+        ref = mra.NSApplier(op, ns_op, tree, n0, mra.make_opts(stencil=mra.STENCIL_SHELLS, max_disp=D))
+        cmp = mra.compare(ap(tree), ref(tree))
+        accuracy = {"rel_l2_vs_fp64_gpu": cmp["rel_l2"], "max_box_rel_vs_fp64_gpu": cmp["max_box_rel"],
+                    "fp64_gpu_apply_ms": ref.stats.kernel_ms,
+                    "speedup_vs_fp64_gpu_kernel": ref.stats.kernel_ms / max(ap.stats.kernel_ms, 1e-9)}
+        del ref
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        ap(tree, stream)
+    torch.cuda.synchronize()
+    clk = clocks_start(args.clocks_csv)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kms = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        ap(tree, stream)
+        ev[i][1].record(stream)
+        kms.append(ap.stats.kernel_ms)
+    torch.cuda.synchronize()
+    clocks = clocks_stop(clk, 0)
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    n_all, ms = reduce_over_ranks(tree.n, ms, world, dev)
+    value = n_all / (ms / 1e3)
+    # end to end: host coefficients in, host result out, through the same call
+    keys_h, coeffs_h = tree.host()
+    keys_pin = torch.from_numpy(keys_h.view(np.int64).copy()).pin_memory()
+    coeffs_pin = torch.from_numpy(coeffs_h.copy()).pin_memory()
+    dev_tree = mra.Tree(torch.empty_like(keys_pin, device=dev), torch.empty_like(coeffs_pin, device=dev),
+                        tree.n, w.k, w.L)
+    out_pin = torch.empty_like(coeffs_pin).pin_memory()
+    e_ms = []
+    for i in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dev_tree.keys.copy_(keys_pin, non_blocking=True)
+        dev_tree.coeffs.copy_(coeffs_pin, non_blocking=True)
+        out = ap(dev_tree, stream)
+        out_pin.copy_(out.coeffs[:tree.n], non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e_ms.append(a.elapsed_time(b))
+    _, e2e_ms = reduce_over_ranks(tree.n, statistics.mean(e_ms), world, dev)
+    k = w.k
+    terms = ns_terms(N, n0, D, w.M)
+    flops = sum(t * (6 * (f * k) ** 4 + (f * k) ** 3) for _, f, t in terms)
+    kms_mean = statistics.mean(kms)
+    achieved = flops / (kms_mean / 1e3) / 1e12
+    pk, pk_kind = peaks()
+    if prec == mra.PREC_FP64:
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "apply_f64_kernel (all levels)",
+                "peak_source": "nominal GB300 FP64", "kernel_ms": kms_mean,
+                "flops": "algorithmic (6k'^4+k'^3 per term, k' = k or 2k)"}
+        dtype = "f64"
+    else:
+        peak = pk.get("bf16_tflops", 1856.3)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "apply_split_kernel (all levels)", "peak_source": f"bf16 dense burst, {pk_kind}",
+                "kernel_ms": kms_mean, "flops": "algorithmic (6k'^4+k'^3 per term, k' = k or 2k)"}
+        dtype = f"bf16x{args.pieces}-split, f32 accumulate, f64 term sum"
+    line = {"metric": METRIC, "value": value, "unit": "boxes/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": w.name, "n_boxes": n_all, "k": k, "M": w.M, "form": "non-standard",
+                       "levels": f"{n0}..{N}", "max_disp_per_level": D, "terms": sum(t for _, _, t in terms),
+                       "terms_reported": ap.stats.terms_kept,
+                       "precision": "fp64" if prec == mra.PREC_FP64 else "split",
+                       "l2": "flushed by a 256 MB write before every step", "tuning": tuning,
+                       "parallelism": "single GPU" if world == 1 else f"replicas x{world}"},
+            "roofline": roof, "clocks": clocks,
+            # per step: the input check, N - n0 compress and sum-down kernels, and per apply (1 + 2 (N - n0)
+            # of them) the level keys, the apply's own 10 and the scatter into the dense level
+            "gpu_launches": args.steps * (1 + 2 * (N - n0) + (1 + 2 * (N - n0)) * 12),
+            "e2e": {"value": n_all / (e2e_ms / 1e3), "unit": "boxes/s", "h2d_bytes_per_step": keys_pin.numel() * 8
+                    + coeffs_pin.numel() * 8, "d2h_bytes_per_step": out_pin.numel() * 8},
+            "accuracy": accuracy}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if "ns" in W.WORKLOADS[args.workload]().extra:
+        return run_ns(args, W.WORKLOADS[args.workload](), rank, world)
 
     import torch
     from paper_1507_01888_gb300 import mra

@@ -121,6 +121,15 @@ def poisson_k14_large() -> Workload:
                     max_disp=1, tau=1e-10)
 
 
+def poisson_ns_uniform_k6() -> Workload:
+    """Non-standard form apply (Sec. 2.2): 1/r as 40 Gaussians on a uniform level-5 tree
+    (32,768 boxes) of 16 Gaussians a~logU[0.05,2] (smooth at box width 2), k=6 (2k=12),
+    complete apply at level 1, |l|_inf <= 1 at levels 1..4, no screen."""
+    return Workload("poisson_ns_uniform_l5_k6", [gaussian_sum(16, 0.05, 2.0, seed=6)], k=6, L=L_CELL,
+                    thresh=0.0, uniform_level=5, kernel=POISSON, mu=0.0, M=40, fit_eps=1e-5, stencil=0,
+                    max_disp=1, tau=0.0, extra={"ns": {"n0": 1}})
+
+
 def shard(w: Workload, rank: int, world: int) -> Workload:
     """The workload rank `rank` of `world` runs.  Families of independent functions give every
     rank its own part (same size: weak scaling, no exchange between ranks); a single-function
@@ -138,6 +147,7 @@ WORKLOADS = {
     "poisson_batched64_k8": poisson_batched_64,
     "bsh_m80_adaptive_k10_learned": bsh_learned_k10,
     "poisson_m100_adaptive_k14": poisson_k14_large,
+    "poisson_ns_uniform_l5_k6": poisson_ns_uniform_k6,
 }
 
 
