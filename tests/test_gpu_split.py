@@ -129,3 +129,39 @@ def test_split_two_pieces_is_coarser(mra):
     out3, _ = mra.apply(op, mra.Tree.from_host(keys, coeffs, 16.0), split_opts(mra, pieces=3, stencil=1))
     e3 = rel_l2(out3.host()[1], ref.coeffs)
     assert e3 < e2 < 1e-4
+
+
+def test_split_edge_cases(mra):
+    """Empty input, a lone level-0 box, boxes on the deepest level (19), and all 128 terms
+    (both words of the kept-term mask) on the tensor-core path."""
+    op = mra.Operator(0, 8, 4, 8.0, 0, 3, max_disp=1, fit_eps=1e-4)
+    opts = split_opts(mra, stencil=mra.STENCIL_NEAREST)
+    out, _ = mra.apply(op, mra.Tree.empty(1, 4, 8.0), opts)
+    assert out.n == 0
+    key = np.array([O.make_key(0, 0, 0, 0)], dtype=np.uint64)
+    s = np.random.default_rng(0).standard_normal((1, 4, 4, 4))
+    out, _ = mra.apply(op, mra.Tree.from_host(key, s, 8.0), opts)
+    fit = op.fit()
+    ref = O.apply(key, s, fit["c"], fit["t"], 8.0, stencil=1)
+    gk, gc = out.host()
+    assert (gk == ref.keys).all() and rel_l2(gc, ref.coeffs) <= TOL_MIXED
+    # deepest level: a corner pair and an interior pair of neighbours at level 19
+    top = (1 << 19) - 1
+    keys = np.sort(np.array([O.make_key(19, 0, 0, 0), O.make_key(19, 1, 0, 0),
+                             O.make_key(19, 4000, top - 1, 77), O.make_key(19, 4001, top - 1, 77)], dtype=np.uint64))
+    s = np.random.default_rng(1).standard_normal((4, 6, 6, 6))
+    op19 = mra.Operator(0, 12, 6, 32.0, 19, 19, max_disp=1, fit_eps=1e-4)
+    fit = op19.fit()
+    out, _ = mra.apply(op19, mra.Tree.from_host(keys, s, 32.0), split_opts(mra, stencil=mra.STENCIL_NEAREST))
+    ref = O.apply(keys, s, fit["c"], fit["t"], 32.0, stencil=1)
+    gk, gc = out.host()
+    assert (gk == ref.keys).all() and rel_l2(gc, ref.coeffs) <= TOL_MIXED
+    # every term slot: M = 128
+    keys, coeffs = W.random_tree_coeffs(40, 4, 3, seed=21)
+    op128 = mra.Operator(1, 128, 4, 16.0, 0, 3, max_disp=1, mu=1.0, fit_eps=1e-6)
+    fit = op128.fit()
+    out, st = mra.apply(op128, mra.Tree.from_host(keys, coeffs, 16.0), split_opts(mra, stencil=mra.STENCIL_NEAREST))
+    ref = O.apply(keys, coeffs, fit["c"], fit["t"], 16.0, stencil=1, tau=0.0)
+    gk, gc = out.host()
+    assert (gk == ref.keys).all() and rel_l2(gc, ref.coeffs) <= TOL_MIXED
+    assert st["terms_kept"] == ref.terms
