@@ -75,6 +75,7 @@ def _load():
         lib.orc_project.argtypes = [i, D, D, D, D, D, i, d, d, i, i, i, l, U64, D, L, D, i]
         lib.orc_apply.argtypes = [i, d, l, U64, D, i, D, D, i, i, d, l, U64, l, U64, D, D, D, L, L, i]
         lib.orc_apply_ns.argtypes = [i, d, i, i, D, i, D, D, i, D, i]
+        lib.orc_apply_ns_tree.argtypes = [i, d, l, U64, D, i, i, D, D, i, l, U64, D, L, i]
         lib.orc_unfilter3.argtypes = [i, D, D]
         lib.orc_filter3.argtypes = [i, D, D]
         _lib = lib
@@ -293,4 +294,50 @@ def apply_ns(coeffs, k: int, L: float, N: int, n0: int, c, t, D: int, nthreads=N
                               _dp(out), _threads(nthreads))
     if rc != 0:
         raise RuntimeError(f"orc_apply_ns failed ({rc})")
+    return out
+
+
+def apply_ns_tree(keys, coeffs, k: int, L: float, n0: int, c, t, D: int, nthreads=None):
+    """Non-standard form apply (Sec. 2.2) on an adaptive tree (complete octree partition, every
+    leaf below level n0); returns (result leaf keys, coefficients) of the result tree, which is
+    refined wherever a level's apply reaches.  See orc_apply_ns_tree."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    coeffs = np.ascontiguousarray(coeffs, dtype=np.float64).reshape(len(keys), k, k, k)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    cap = max(1, 8 * len(keys))
+    while True:
+        ok = np.zeros(cap, dtype=np.uint64)
+        oc = np.zeros((cap, k, k, k))
+        n = ctypes.c_long(0)
+        rc = _load().orc_apply_ns_tree(int(k), float(L), len(keys), _up(keys), _dp(coeffs), int(n0), len(c), _dp(c),
+                                       _dp(t), int(D), int(cap), _up(ok), _dp(oc), ctypes.byref(n), _threads(nthreads))
+        if rc == -4:
+            cap = int(n.value)
+            continue
+        if rc != 0:
+            raise RuntimeError(f"orc_apply_ns_tree failed ({rc})")
+        return ok[:n.value].copy(), oc[:n.value].copy()
+
+
+def evaluate(keys, coeffs, k: int, L: float, points):
+    """The function sum_b sum_ijl c_b[i,j,l] phi^n_{b,i}(x) phi^n_{b,j}(y) phi^n_{b,l}(z) at the
+    given points ([npts, 3] in the cell); boxes of any levels, overlapping or not (Sec. 2.1)."""
+    keys = np.asarray(keys, dtype=np.uint64)
+    coeffs = np.asarray(coeffs, dtype=np.float64).reshape(len(keys), k, k, k)
+    pts = np.asarray(points, dtype=np.float64)
+    lev = (keys >> np.uint64(57)).astype(np.int64)
+    out = np.zeros(len(pts))
+    for n in np.unique(lev):
+        h = 2.0 * L / (1 << int(n))
+        u = (pts + L) / h
+        b = np.clip(np.floor(u).astype(np.int64), 0, (1 << int(n)) - 1)
+        want = (np.uint64(n) << np.uint64(57)) | (b[:, 0].astype(np.uint64) << np.uint64(38)) | \
+            (b[:, 1].astype(np.uint64) << np.uint64(19)) | b[:, 2].astype(np.uint64)
+        pos = np.searchsorted(keys, want)
+        pos = np.minimum(pos, len(keys) - 1)
+        hit = keys[pos] == want
+        for p in np.nonzero(hit)[0]:
+            f = [phi(k, u[p, d] - b[p, d]) for d in range(3)]
+            out[p] += h ** -1.5 * np.einsum("ijl,i,j,l->", coeffs[pos[p]], f[0], f[1], f[2])
     return out

@@ -1100,3 +1100,309 @@ void orc_filter3(int k, const double *S, double *v) {
       for (int j = 0; j < k; ++j) Ub[(cc * k + i) * k + j] = (cc == 0 ? U0 : U1)[i * k + j];
   filter3(k, Ub, S, v);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Non-standard form apply on an adaptive tree (Sec. 2.2)                    */
+/* ------------------------------------------------------------------------ */
+
+/* The input is a complete octree partition of the cell: leaves (sorted keys, k^3
+ * coefficients each) at levels > n0, every interior node with its eight children.
+ * Sources of level n are the interior nodes I_n with S_b = their children's coefficients as
+ * one (2k)^3 tensor (a child is a leaf or an interior node, whose s = filter(S) comes from
+ * below) and s_b = (Ubar^T)^{x3} S_b.  The result tree is built from the top: R_{n0} = every
+ * box of level n0 with r = T^{n0} s^{n0} (every displacement); at level n the nodes of R_n
+ * that a level-n apply reaches (Y^n = T2k^n S^n, Z^n = T^n s^n, |l|_inf <= D) are refined,
+ * their children getting Ubar^{x3} (r_p - Z_p) + Y_p; the others are result leaves.  Every
+ * node of R at the deepest leaf level is a result leaf.  A leaf f_b of level n reaches the
+ * result through T^n (its parent's 2k apply telescopes T^{n0} + sum (T^{m+1} - T^m)), so with
+ * every displacement the result is, as a function, the leaf-level apply with every
+ * displacement. */
+
+typedef struct {
+  long n;
+  uint64_t *keys;
+  double *v; /* n x len */
+} orc_set;
+
+static int cmp_u64v(const void *a, const void *b) {
+  uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+  return x < y ? -1 : (x > y);
+}
+
+/* out[t] = sum_{l, m, src = t - l in the source set} c_m (R x R x R) in[src]; the targets are
+ * every in-cell box within |l|_inf <= D of a source (sorted). */
+static orc_set apply_level_sparse(int kk, int n, long ns, const uint64_t *skeys, const double *sin,
+                                  const double *R, const double *c, int M, int D) {
+  long nb = 1L << n;
+  int kk2 = kk * kk, kk3 = kk2 * kk, nl = 2 * D + 1;
+  long cap = ns * nl * nl * nl;
+  uint64_t *cand = (uint64_t *)malloc(sizeof(uint64_t) * (cap > 0 ? cap : 1));
+  long nc = 0;
+  for (long i = 0; i < ns; ++i) {
+    int lv;
+    long x, y, z;
+    split_key(skeys[i], &lv, &x, &y, &z);
+    for (int lx = -D; lx <= D; ++lx)
+      for (int ly = -D; ly <= D; ++ly)
+        for (int lz = -D; lz <= D; ++lz) {
+          long a = x + lx, b = y + ly, e = z + lz;
+          if (a < 0 || a >= nb || b < 0 || b >= nb || e < 0 || e >= nb) continue;
+          cand[nc++] = make_key(n, a, b, e);
+        }
+  }
+  qsort(cand, nc, sizeof(uint64_t), cmp_u64v);
+  long nt = 0;
+  for (long i = 0; i < nc; ++i)
+    if (i == 0 || cand[i] != cand[i - 1]) cand[nt++] = cand[i];
+  orc_set out;
+  out.n = nt;
+  out.keys = cand;
+  out.v = (double *)calloc((size_t)(nt > 0 ? nt : 1) * kk3, sizeof(double));
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic)
+#endif
+  for (long ti = 0; ti < nt; ++ti) {
+    int lv;
+    long tx, ty, tz;
+    split_key(cand[ti], &lv, &tx, &ty, &tz);
+    double *o = out.v + ti * kk3;
+    double *t1 = (double *)malloc(sizeof(double) * kk3 * 3);
+    double *t2 = t1 + kk3, *t3 = t2 + kk3;
+    for (int lx = -D; lx <= D; ++lx)
+      for (int ly = -D; ly <= D; ++ly)
+        for (int lz = -D; lz <= D; ++lz) {
+          long sx = tx - lx, sy = ty - ly, sz = tz - lz;
+          if (sx < 0 || sx >= nb || sy < 0 || sy >= nb || sz < 0 || sz >= nb) continue;
+          long si = find_key(skeys, ns, make_key(n, sx, sy, sz));
+          if (si < 0) continue;
+          const double *s = sin + si * kk3;
+          for (int m = 0; m < M; ++m) {
+            const double *Rx = R + ((size_t)m * nl + lx + D) * kk2;
+            const double *Ry = R + ((size_t)m * nl + ly + D) * kk2;
+            const double *Rz = R + ((size_t)m * nl + lz + D) * kk2;
+            for (int ix = 0; ix < kk; ++ix)
+              for (int q = 0; q < kk2; ++q) {
+                double a = 0.0;
+                for (int jx = 0; jx < kk; ++jx) a += Rx[ix * kk + jx] * s[jx * kk2 + q];
+                t1[ix * kk2 + q] = a;
+              }
+            for (int ix = 0; ix < kk; ++ix)
+              for (int iy = 0; iy < kk; ++iy)
+                for (int jz = 0; jz < kk; ++jz) {
+                  double a = 0.0;
+                  for (int jy = 0; jy < kk; ++jy) a += Ry[iy * kk + jy] * t1[(ix * kk + jy) * kk + jz];
+                  t2[(ix * kk + iy) * kk + jz] = a;
+                }
+            for (int q = 0; q < kk2; ++q)
+              for (int iz = 0; iz < kk; ++iz) {
+                double a = 0.0;
+                for (int jz = 0; jz < kk; ++jz) a += Rz[iz * kk + jz] * t2[q * kk + jz];
+                t3[q * kk + iz] = a;
+              }
+            for (int i = 0; i < kk3; ++i) o[i] += c[m] * t3[i];
+          }
+        }
+    free(t1);
+  }
+  return out;
+}
+
+int orc_apply_ns_tree(int k, double L, long n_leaf, const uint64_t *lkeys, const double *lcoeffs, int n0, int M,
+                      const double *c, const double *t, int D, long cap, uint64_t *out_keys, double *out_coeffs,
+                      long *n_out, int nthreads) {
+  if (k < 1 || 2 * k > ORC_MAXK || n0 < 0 || M < 1 || D < 0 || n_leaf < 1) return -1;
+  gl_init();
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+  for (long i = 1; i < n_leaf; ++i)
+    if (lkeys[i] <= lkeys[i - 1]) return -1;
+  int Nmax = 0;
+  for (long i = 0; i < n_leaf; ++i) {
+    int lv = (int)(lkeys[i] >> 57);
+    if (lv <= n0 || lv > 19) return -1; /* every leaf below the coarsest level */
+    if (lv > Nmax) Nmax = lv;
+  }
+  int k3 = k * k * k, kk = 2 * k, kk3 = kk * kk * kk;
+  double U0[ORC_MAXK * ORC_MAXK], U1[ORC_MAXK * ORC_MAXK];
+  orc_two_scale(k, U0, U1);
+  double *Ub = (double *)malloc(sizeof(double) * kk * k);
+  for (int cc = 0; cc < 2; ++cc)
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) Ub[(cc * k + i) * k + j] = (cc == 0 ? U0 : U1)[i * k + j];
+  /* interior nodes per level: the ancestors of the leaves */
+  orc_set I[20], Ssrc[20];
+  memset(I, 0, sizeof(I));
+  memset(Ssrc, 0, sizeof(Ssrc));
+  for (int n = n0; n < Nmax; ++n) {
+    uint64_t *a = (uint64_t *)malloc(sizeof(uint64_t) * n_leaf);
+    long na = 0;
+    for (long i = 0; i < n_leaf; ++i) {
+      int lv;
+      long x, y, z;
+      split_key(lkeys[i], &lv, &x, &y, &z);
+      if (lv <= n) continue;
+      a[na++] = make_key(n, x >> (lv - n), y >> (lv - n), z >> (lv - n));
+    }
+    qsort(a, na, sizeof(uint64_t), cmp_u64v);
+    long u = 0;
+    for (long i = 0; i < na; ++i)
+      if (i == 0 || a[i] != a[i - 1]) a[u++] = a[i];
+    I[n].n = u;
+    I[n].keys = a;
+    I[n].v = (double *)malloc(sizeof(double) * (u > 0 ? u : 1) * k3); /* s of interior nodes */
+    Ssrc[n].n = u;
+    Ssrc[n].keys = a;
+    Ssrc[n].v = (double *)malloc(sizeof(double) * (u > 0 ? u : 1) * kk3); /* S of interior nodes */
+  }
+  if (I[n0].n != (1L << (3 * n0))) return -2; /* level n0 must be complete */
+  int err = 0;
+  /* compress, from the deepest interior level up */
+  for (int n = Nmax - 1; n >= n0 && !err; --n) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic) reduction(| : err)
+#endif
+    for (long b = 0; b < I[n].n; ++b) {
+      int lv;
+      long x, y, z;
+      split_key(I[n].keys[b], &lv, &x, &y, &z);
+      double *S = Ssrc[n].v + b * kk3;
+      for (int cx = 0; cx < 2; ++cx)
+        for (int cy = 0; cy < 2; ++cy)
+          for (int cz = 0; cz < 2; ++cz) {
+            uint64_t ck = make_key(n + 1, 2 * x + cx, 2 * y + cy, 2 * z + cz);
+            const double *src = NULL;
+            long li = find_key(lkeys, n_leaf, ck);
+            if (li >= 0) src = lcoeffs + li * k3;
+            else if (n + 1 < Nmax) {
+              long ii = find_key(I[n + 1].keys, I[n + 1].n, ck);
+              if (ii >= 0) src = I[n + 1].v + ii * k3;
+            }
+            if (!src) {
+              err = 1; /* not a complete octree */
+              continue;
+            }
+            for (int i = 0; i < k; ++i)
+              for (int j = 0; j < k; ++j)
+                for (int l = 0; l < k; ++l) S[((cx * k + i) * kk + cy * k + j) * kk + cz * k + l] = src[(i * k + j) * k + l];
+          }
+      filter3(k, Ub, S, I[n].v + b * k3);
+    }
+  }
+  long nout = 0;
+  int rc = 0;
+  /* coarsest level: every box, T^{n0} with every displacement */
+  long nb0 = 1L << n0;
+  int D0 = (int)(nb0 - 1);
+  orc_set R;
+  R.n = I[n0].n;
+  R.keys = (uint64_t *)malloc(sizeof(uint64_t) * R.n);
+  memcpy(R.keys, I[n0].keys, sizeof(uint64_t) * R.n);
+  R.v = (double *)malloc(sizeof(double) * R.n * k3);
+  if (!err) {
+    double *R0 = blocks_level(k, L, n0, M, t, D0);
+    apply_level_dense(k, nb0, I[n0].v, R0, c, M, D0, R.v);
+    free(R0);
+  }
+  for (int n = n0; n < Nmax && !err; ++n) {
+    int Dn = D < (1L << n) - 1 ? D : (int)((1L << n) - 1);
+    double *Rk = blocks_level(k, L, n, M, t, Dn);
+    double *R2 = blocks_level_2k(k, L, n, M, t, Dn);
+    orc_set Y = apply_level_sparse(kk, n, Ssrc[n].n, Ssrc[n].keys, Ssrc[n].v, R2, c, M, Dn);
+    orc_set Z = apply_level_sparse(k, n, I[n].n, I[n].keys, I[n].v, Rk, c, M, Dn);
+    free(Rk);
+    free(R2);
+    /* every target must be a node of R_n */
+    for (long i = 0; i < Y.n; ++i)
+      if (find_key(R.keys, R.n, Y.keys[i]) < 0) err = 2;
+    /* refine the reached nodes, emit the others */
+    long nref = 0;
+    for (long p = 0; p < R.n; ++p)
+      if (find_key(Y.keys, Y.n, R.keys[p]) >= 0) ++nref;
+    orc_set Rn;
+    Rn.n = 8 * nref;
+    Rn.keys = (uint64_t *)malloc(sizeof(uint64_t) * (Rn.n > 0 ? Rn.n : 1));
+    Rn.v = (double *)malloc(sizeof(double) * (Rn.n > 0 ? Rn.n : 1) * k3);
+    long q = 0;
+    double *dv = (double *)malloc(sizeof(double) * (k3 + kk3));
+    double *U = dv + k3;
+    for (long p = 0; p < R.n && !err; ++p) {
+      long yi = find_key(Y.keys, Y.n, R.keys[p]);
+      if (yi < 0) {
+        if (nout < cap) {
+          out_keys[nout] = R.keys[p];
+          memcpy(out_coeffs + nout * k3, R.v + p * k3, sizeof(double) * k3);
+        }
+        ++nout;
+        continue;
+      }
+      long zi = find_key(Z.keys, Z.n, R.keys[p]);
+      for (int i = 0; i < k3; ++i) dv[i] = R.v[p * k3 + i] - (zi >= 0 ? Z.v[zi * k3 + i] : 0.0);
+      unfilter3(k, Ub, dv, U);
+      for (int i = 0; i < kk3; ++i) U[i] += Y.v[yi * kk3 + i];
+      int lv;
+      long x, y, z;
+      split_key(R.keys[p], &lv, &x, &y, &z);
+      for (int cx = 0; cx < 2; ++cx)
+        for (int cy = 0; cy < 2; ++cy)
+          for (int cz = 0; cz < 2; ++cz, ++q) {
+            Rn.keys[q] = make_key(n + 1, 2 * x + cx, 2 * y + cy, 2 * z + cz);
+            double *o = Rn.v + q * k3;
+            for (int i = 0; i < k; ++i)
+              for (int j = 0; j < k; ++j)
+                for (int l = 0; l < k; ++l) o[(i * k + j) * k + l] = U[((cx * k + i) * kk + cy * k + j) * kk + cz * k + l];
+          }
+    }
+    free(dv);
+    free(Y.keys);
+    free(Y.v);
+    free(Z.keys);
+    free(Z.v);
+    /* the children in key order */
+    long *perm = (long *)malloc(sizeof(long) * (Rn.n > 0 ? Rn.n : 1));
+    for (long i = 0; i < Rn.n; ++i) perm[i] = i;
+    for (long i = 1; i < Rn.n; ++i) { /* insertion sort by key (plain; sizes are small here) */
+      long pi = perm[i], j = i - 1;
+      while (j >= 0 && Rn.keys[perm[j]] > Rn.keys[pi]) {
+        perm[j + 1] = perm[j];
+        --j;
+      }
+      perm[j + 1] = pi;
+    }
+    orc_set Rs;
+    Rs.n = Rn.n;
+    Rs.keys = (uint64_t *)malloc(sizeof(uint64_t) * (Rs.n > 0 ? Rs.n : 1));
+    Rs.v = (double *)malloc(sizeof(double) * (Rs.n > 0 ? Rs.n : 1) * k3);
+    for (long i = 0; i < Rs.n; ++i) {
+      Rs.keys[i] = Rn.keys[perm[i]];
+      memcpy(Rs.v + i * k3, Rn.v + perm[i] * k3, sizeof(double) * k3);
+    }
+    free(perm);
+    free(Rn.keys);
+    free(Rn.v);
+    free(R.keys);
+    free(R.v);
+    R = Rs;
+  }
+  if (!err) {
+    for (long p = 0; p < R.n; ++p) { /* the deepest level: all leaves */
+      if (nout < cap) {
+        out_keys[nout] = R.keys[p];
+        memcpy(out_coeffs + nout * k3, R.v + p * k3, sizeof(double) * k3);
+      }
+      ++nout;
+    }
+  }
+  free(R.keys);
+  free(R.v);
+  for (int n = 0; n < 20; ++n) {
+    free(I[n].keys);
+    free(I[n].v);
+    free(Ssrc[n].v);
+  }
+  free(Ub);
+  *n_out = nout;
+  if (err) return -3;
+  if (nout > cap) rc = -4;
+  return rc;
+}

@@ -431,3 +431,64 @@ def test_ns_form_is_sparse_where_the_leaf_apply_is_not():
     assert e_ns[1] < e_ns[0] < 1e-2
     assert e_ns[1] < 1e-5
     assert min(e_leaf) > 0.1
+
+
+def _adaptive_case(k=3, thresh=3e-3, max_level=4):
+    L = 8.0
+    f = W.gaussian_sum(2, 1.0, 20.0, seed=11, centre_box=3.0)
+    keys, coeffs, _ = O.project(f, k, L, thresh=thresh, init_level=2, max_level=max_level)
+    r_lo, r_hi = O.kernel_range(0, 0.0, L, 1e-4)
+    _, _, _, c, t = O.fit_search(0.0, 8, r_lo, r_hi)
+    return keys, coeffs, c, t, L
+
+
+def test_evaluate_sums_every_box_containing_the_point():
+    """The pointwise evaluator is the basis expansion itself: a box's coefficient [0,0,0]
+    alone is the constant h^{-3/2} on that box, and overlapping boxes add."""
+    k, L = 3, 8.0
+    keys = np.array([O.make_key(1, 0, 1, 1), O.make_key(2, 1, 2, 3)], dtype=np.uint64)
+    coeffs = np.zeros((2, k, k, k))
+    coeffs[0, 0, 0, 0] = 2.0
+    coeffs[1, 0, 0, 0] = 3.0
+    pts = np.array([[-6.0, 1.0, 1.0], [-3.0, 1.0, 5.0], [6.0, 6.0, 6.0]])  # box 0 only; both; neither
+    v = O.evaluate(keys, coeffs, k, L, pts)
+    assert v == pytest.approx([2.0 * 8.0 ** -1.5, 2.0 * 8.0 ** -1.5 + 3.0 * 4.0 ** -1.5, 0.0], rel=1e-14)
+
+
+def test_ns_tree_with_every_displacement_is_the_leaf_level_apply():
+    """A leaf of level n enters through its parent's 2k apply, so the non-standard form on an
+    adaptive tree applies T^n to it: with every displacement the result is, as a function, the
+    leaf-level apply with every displacement (compared at 300 points)."""
+    keys, coeffs, c, t, L = _adaptive_case()
+    k = 3
+    leaf = O.apply(keys, coeffs, c, t, L, stencil=0, max_disp=15, tau=0.0)
+    nk, nc = O.apply_ns_tree(keys, coeffs, k, L, 1, c, t, 15)
+    assert (nk[1:] > nk[:-1]).all()  # result leaves in key order
+    pts = np.random.default_rng(0).uniform(-L, L, size=(300, 3))
+    a = O.evaluate(leaf.keys, leaf.coeffs, k, L, pts)
+    b = O.evaluate(nk, nc, k, L, pts)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+
+
+def test_ns_tree_on_a_uniform_tree_is_the_uniform_ns_form():
+    k, L = 4, 8.0
+    f = W.gaussian_sum(2, 1.0, 20.0, seed=11, centre_box=3.0)
+    uk, uc, _ = O.project(f, k, L, uniform_level=3)
+    r_lo, r_hi = O.kernel_range(0, 0.0, L, 1e-4)
+    _, _, _, c, t = O.fit_search(0.0, 8, r_lo, r_hi)
+    nk, nc = O.apply_ns_tree(uk, uc, k, L, 1, c, t, 1)
+    assert (nk == uk).all()
+    ref = O.apply_ns(uc, k, L, 3, 1, c, t, 1)
+    assert np.abs(nc - ref).max() <= 1e-14 * np.abs(ref).max()
+
+
+def test_ns_tree_is_accurate_where_the_leaf_apply_is_not():
+    keys, coeffs, c, t, L = _adaptive_case(k=4)
+    k = 4
+    pts = np.random.default_rng(1).uniform(-L, L, size=(300, 3))
+    exact = O.evaluate(*O.apply_ns_tree(keys, coeffs, k, L, 1, c, t, 15), k, L, pts)
+    nk, nc = O.apply_ns_tree(keys, coeffs, k, L, 1, c, t, 2)
+    leaf = O.apply(keys, coeffs, c, t, L, stencil=0, max_disp=2, tau=0.0)
+    e_ns = np.abs(O.evaluate(nk, nc, k, L, pts) - exact).max() / np.abs(exact).max()
+    e_leaf = np.abs(O.evaluate(leaf.keys, leaf.coeffs, k, L, pts) - exact).max() / np.abs(exact).max()
+    assert e_ns < 1e-3 and e_leaf > 0.1
