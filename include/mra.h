@@ -308,6 +308,20 @@ int mra_apply_ns(const mra_operator *op, const mra_operator *ns_op, const mra_tr
                  const mra_apply_opts *opts, mra_tree_view *out, void *workspace, size_t workspace_bytes,
                  mra_apply_stats *stats, void *stream);
 
+/* Non-standard form apply on an adaptive tree.  in: the leaves of a complete octree (every
+ * interior node has its eight children; keys sorted and unique), every leaf deeper than n0.
+ * Sources of level n are the interior nodes (S = the children's coefficients, s = their
+ * filter); the result tree starts with every box of level n0 (T^{n0} s^{n0}, every
+ * displacement) and at each level n refines the nodes that level's applies (T2k^n on S,
+ * T^n on s, opts' stencil and screen) reach: their children get U^{x3} (r_p - Z_p) + Y_p.
+ * out: the result's leaves in key order (boxes of several levels, disjoint); if out->cap is
+ * too small, MRA_ERR_CAPACITY with out->n the number needed.  A leaf of level n enters
+ * through T^n, so with every displacement the result is, as a function, mra_apply's
+ * leaf-level result with every displacement.  Allocates its temporaries on the stream
+ * (cudaMallocAsync) and releases them before returning; synchronises the stream. */
+int mra_apply_ns_tree(const mra_operator *op, const mra_operator *ns_op, const mra_tree_view *in, int n0,
+                      const mra_apply_opts *opts, mra_tree_view *out, mra_apply_stats *stats, void *stream);
+
 /* Per-box Frobenius norms (device array of tree->n doubles, may be NULL) and
  * the total L2 norm (host double, may be NULL).  Deterministic reduction. */
 int mra_norm(const mra_tree_view *tree, double *per_box, double *total, void *stream);

@@ -20,6 +20,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <cub/cub.cuh>
+
 #include "apply_internal.cuh"
 
 namespace mra {
@@ -155,6 +157,178 @@ __global__ void sum_down_kernel(int k, int n, const double *r, const double *Z, 
     const int64_t child = ((2 * x + I / k) * nf + 2 * y + J / k) * nf + 2 * z + Lq / k;
     fine[child * k3 + ((I % k) * k + J % k) * k + Lq % k] = v;
   }
+}
+
+// ---------------------------------------------------------------- adaptive trees
+__device__ __forceinline__ int64_t find_sorted(const uint64_t *keys, int64_t n, uint64_t key) {
+  int64_t lo = 0, hi = n - 1;
+  while (lo <= hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    const uint64_t v = keys[mid];
+    if (v == key) return mid;
+    if (v < key) lo = mid + 1; else hi = mid - 1;
+  }
+  return -1;
+}
+
+// Leaf checks: keys strictly increasing, every leaf deeper than n0; deepest level -> *maxlev.
+__global__ void leaf_check_kernel(int64_t n, const uint64_t *keys, int n0, int *err, int *maxlev) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int lv = key_level(keys[i]);
+  if (lv <= n0 || (i > 0 && keys[i] <= keys[i - 1])) atomicExch(err, 1);
+  atomicMax(maxlev, lv);
+}
+
+// Ancestor on level n of every leaf deeper than n (others: the largest key, dropped later).
+__global__ void ancestor_kernel(int64_t n_leaf, const uint64_t *keys, int n, uint64_t *anc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_leaf) return;
+  const uint64_t k = keys[i];
+  const int lv = key_level(k);
+  anc[i] = lv > n ? make_key(n, key_x(k) >> (lv - n), key_y(k) >> (lv - n), key_z(k) >> (lv - n)) : ~0ull;
+}
+
+// One CTA per interior node of level n: its children (leaves or interior nodes of level n+1)
+// as the (2k)^3 tensor S, and s = (Ubar^T)^{x3} S.  A missing child sets *err.
+__global__ void compress_tree_kernel(int k, int n, const uint64_t *ikeys, int64_t n_int, const uint64_t *lkeys,
+                                     const double *lcoeffs, int64_t n_leaf, const uint64_t *ckeys,
+                                     const double *ccoeffs, int64_t n_child_int, const double *Ub, double *S_out,
+                                     double *s_out, int *err) {
+  extern __shared__ double sh[];
+  __shared__ const double *src[8];
+  const int kk = 2 * k, k3 = k * k * k, kk3 = kk * kk * kk;
+  double *S = sh, *a = S + kk3, *b = a + k * kk * kk;
+  const int64_t box = blockIdx.x;
+  if (box >= n_int) return;
+  const uint64_t key = ikeys[box];
+  if (threadIdx.x < 8) {
+    const int cx = threadIdx.x >> 2, cy = (threadIdx.x >> 1) & 1, cz = threadIdx.x & 1;
+    const uint64_t ck = make_key(n + 1, 2 * key_x(key) + cx, 2 * key_y(key) + cy, 2 * key_z(key) + cz);
+    const int64_t li = find_sorted(lkeys, n_leaf, ck);
+    const double *p = nullptr;
+    if (li >= 0) {
+      p = lcoeffs + li * k3;
+    } else {
+      const int64_t ci = find_sorted(ckeys, n_child_int, ck);
+      if (ci >= 0) p = ccoeffs + ci * k3;
+    }
+    if (!p) atomicExch(err, 2);
+    src[threadIdx.x] = p;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kk3; e += blockDim.x) {
+    const int I = e / (kk * kk), J = (e / kk) % kk, Lq = e % kk;
+    const double *p = src[((I / k) << 2) | ((J / k) << 1) | (Lq / k)];
+    const double v = p ? p[((I % k) * k + J % k) * k + Lq % k] : 0.0;
+    S[e] = v;
+    S_out[box * kk3 + e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < k * kk * kk; e += blockDim.x) {
+    const int i = e / (kk * kk), q = e % (kk * kk);
+    double v = 0.0;
+    for (int I = 0; I < kk; ++I) v += Ub[I * k + i] * S[I * kk * kk + q];
+    a[e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < k * k * kk; e += blockDim.x) {
+    const int i = e / (k * kk), j = (e / kk) % k, Lq = e % kk;
+    double v = 0.0;
+    for (int J = 0; J < kk; ++J) v += Ub[J * k + j] * a[(i * kk + J) * kk + Lq];
+    b[e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < k3; e += blockDim.x) {
+    const int q = e / k, l = e % k;
+    double v = 0.0;
+    for (int Lq = 0; Lq < kk; ++Lq) v += Ub[Lq * k + l] * b[q * kk + Lq];
+    s_out[box * k3 + e] = v;
+  }
+}
+
+// Every node p of R_n: is it reached by the level's applies (Y or Z output row), and which.
+__global__ void reach_kernel(int64_t nr, const uint64_t *rkeys, const uint64_t *ykeys, int64_t ny,
+                             const uint64_t *zkeys, int64_t nz, int64_t *yi, int64_t *zi, int *refine, int *leaf) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nr) return;
+  const int64_t a = find_sorted(ykeys, ny, rkeys[p]), b = find_sorted(zkeys, nz, rkeys[p]);
+  yi[p] = a;
+  zi[p] = b;
+  refine[p] = (a >= 0 || b >= 0) ? 1 : 0;
+  leaf[p] = (a >= 0 || b >= 0) ? 0 : 1;
+}
+
+// Every target row of an apply must be a node of R_n.
+__global__ void targets_in_kernel(int64_t nt, const uint64_t *tkeys, const uint64_t *rkeys, int64_t nr, int *err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nt) return;
+  if (find_sorted(rkeys, nr, tkeys[i]) < 0) atomicExch(err, 3);
+}
+
+// Result leaves of this level: nodes of R_n that no apply reached, appended at out + base.
+__global__ void emit_leaves_kernel(int64_t nr, int k3, const uint64_t *rkeys, const double *r, const int *leaf,
+                                   const int *leaf_pos, int64_t base, int64_t cap, uint64_t *okeys, double *ocoeffs) {
+  const int64_t p = blockIdx.x;
+  if (p >= nr || !leaf[p]) return;
+  const int64_t o = base + leaf_pos[p];
+  if (o >= cap) return;
+  if (threadIdx.x == 0) okeys[o] = rkeys[p];
+  for (int e = threadIdx.x; e < k3; e += blockDim.x) ocoeffs[o * k3 + e] = r[p * k3 + e];
+}
+
+// One CTA per reached node p: its children get (Ubar)^{x3} (r_p - Z_p) + Y_p (absent rows as
+// zero), written at 8 ref_pos[p] + child in the unsorted level-(n+1) arrays.
+__global__ void sum_down_tree_kernel(int k, int64_t nr, const uint64_t *rkeys, const double *r, const int *refine,
+                                     const int *ref_pos, const int64_t *yi, const double *Y, const int64_t *zi,
+                                     const double *Z, const double *Ub, uint64_t *ckeys, double *cr) {
+  extern __shared__ double sh[];
+  const int64_t p = blockIdx.x;
+  if (p >= nr || !refine[p]) return;
+  const int kk = 2 * k, k2 = k * k, k3 = k2 * k, kk3 = kk * kk * kk;
+  double *d = sh, *a = d + k3, *b = a + kk * k2;
+  const int64_t y = yi[p], z = zi[p], base = 8 * (int64_t)ref_pos[p];
+  for (int e = threadIdx.x; e < k3; e += blockDim.x) d[e] = r[p * k3 + e] - (z >= 0 ? Z[z * k3 + e] : 0.0);
+  const uint64_t key = rkeys[p];
+  if (threadIdx.x < 8) {
+    const int cx = threadIdx.x >> 2, cy = (threadIdx.x >> 1) & 1, cz = threadIdx.x & 1;
+    ckeys[base + threadIdx.x] =
+        make_key(key_level(key) + 1, 2 * key_x(key) + cx, 2 * key_y(key) + cy, 2 * key_z(key) + cz);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kk * k2; e += blockDim.x) {
+    const int I = e / k2, q = e % k2;
+    double v = 0.0;
+    for (int i = 0; i < k; ++i) v += Ub[I * k + i] * d[i * k2 + q];
+    a[e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kk * kk * k; e += blockDim.x) {
+    const int I = e / (kk * k), J = (e / k) % kk, l = e % k;
+    double v = 0.0;
+    for (int j = 0; j < k; ++j) v += Ub[J * k + j] * a[(I * k + j) * k + l];
+    b[e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kk3; e += blockDim.x) {
+    const int I = e / (kk * kk), J = (e / kk) % kk, Lq = e % kk;
+    double v = y >= 0 ? Y[y * kk3 + e] : 0.0;
+    for (int l = 0; l < k; ++l) v += Ub[Lq * k + l] * b[(I * kk + J) * k + l];
+    const int child = ((I / k) << 2) | ((J / k) << 1) | (Lq / k);
+    cr[(base + child) * k3 + ((I % k) * k + J % k) * k + Lq % k] = v;
+  }
+}
+
+__global__ void gather_rows_ns_kernel(int64_t n, int rowlen, const int *perm, const double *src, double *dst) {
+  const int64_t i = blockIdx.x;
+  if (i >= n) return;
+  const int64_t from = perm[i];
+  for (int e = threadIdx.x; e < rowlen; e += blockDim.x) dst[i * rowlen + e] = src[from * rowlen + e];
+}
+
+__global__ void iota_ns_kernel(int64_t n, int *v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = (int)i;
 }
 
 inline size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -457,4 +631,289 @@ extern "C" int mra_apply_ns(const mra_operator *h, const mra_operator *hns, cons
     *stats = acc;
   }
   return MRA_OK;
+}
+
+// ---------------------------------------------------------------- adaptive trees
+// The non-standard form apply on an adaptive tree (leaves of a complete octree, every leaf
+// deeper than n0).  Sources of level n are the interior nodes I_n (S = children, s = filter);
+// the result tree starts with every box of level n0 (r = T^{n0} s^{n0}, every displacement)
+// and at each level refines the nodes the level's applies reach (children get
+// Ubar^{x3} (r_p - Z_p) + Y_p); the nodes they do not reach, and every node of the deepest
+// leaf level, are the result's leaves.
+extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns, const mra_tree_view *in, int n0,
+                                 const mra_apply_opts *o, mra_tree_view *out, mra_apply_stats *stats, void *stream) {
+  const Operator *op = reinterpret_cast<const Operator *>(h);
+  const Operator *ns = reinterpret_cast<const Operator *>(hns);
+  if (!op || !ns || !in || !o || !out) return fail(MRA_ERR_ARG, "mra_apply_ns_tree: NULL argument");
+  if (ns->k != 2 * op->k || ns->M != op->M || ns->L != op->L)
+    return fail(MRA_ERR_ARG, "mra_apply_ns_tree: the second operator is not the non-standard form of the first");
+  if (in->k != op->k || in->L != op->L) return fail(MRA_ERR_ARG, "mra_apply_ns_tree: tree k or L differs");
+  if (in->n <= 0 || !in->keys || !in->coeffs) return fail(MRA_ERR_ARG, "mra_apply_ns_tree: empty input tree");
+  if (in->n >= (1LL << 31)) return fail(MRA_ERR_ARG, "mra_apply_ns_tree: more than 2^31 leaves");
+  if (out->k != op->k || out->cap < 0 || (out->cap > 0 && (!out->keys || !out->coeffs)))
+    return fail(MRA_ERR_ARG, "mra_apply_ns_tree: bad output view");
+  if (o->precision != MRA_PREC_FP64 && o->precision != MRA_PREC_SPLIT_BF16)
+    return fail(MRA_ERR_ARG, "mra_apply_ns_tree: unknown precision %d", o->precision);
+  if (o->precision == MRA_PREC_SPLIT_BF16 && (o->pieces < 2 || o->pieces > 3))
+    return fail(MRA_ERR_ARG, "mra_apply_ns_tree: pieces must be 2 or 3");
+  if (o->screen != MRA_SCREEN_NONE && o->screen != MRA_SCREEN_NORM)
+    return fail(MRA_ERR_ARG, "mra_apply_ns_tree: screen must be MRA_SCREEN_NONE or MRA_SCREEN_NORM");
+  if (o->stencil != MRA_STENCIL_SHELLS && o->stencil != MRA_STENCIL_NEAREST)
+    return fail(MRA_ERR_ARG, "mra_apply_ns_tree: unknown stencil %d", o->stencil);
+  const int D = o->stencil == MRA_STENCIL_NEAREST ? 1 : o->max_disp;
+  if (D < 0 || D > ns->max_disp || D > op->max_disp)
+    return fail(MRA_ERR_ARG, "mra_apply_ns_tree: max_disp %d outside the operators' range", D);
+  if (n0 < 0 || (1LL << n0) - 1 > op->max_disp)
+    return fail(MRA_ERR_ARG, "mra_apply_ns_tree: the complete level-%d apply needs max_disp >= %lld", n0,
+                (long long)((1LL << n0) - 1));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int k = op->k, kk = 2 * k, k3 = k * k * k;
+  const int64_t n_leaf = in->n;
+  std::vector<void *> held;  // stream-ordered allocations, released on every return
+  struct Release {
+    std::vector<void *> &v;
+    cudaStream_t s;
+    ~Release() {
+      for (void *p : v) cudaFreeAsync(p, s);
+      cudaStreamSynchronize(s);
+    }
+  } release{held, s};
+  auto dalloc = [&](size_t bytes) -> void * {
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes ? bytes : 1, s) != cudaSuccess) return nullptr;
+    held.push_back(p);
+    return p;
+  };
+  auto drop = [&](void *p) {  // release one allocation early
+    auto it = std::find(held.begin(), held.end(), p);
+    if (it != held.end()) {
+      cudaFreeAsync(p, s);
+      held.erase(it);
+    }
+  };
+#define NS_ALLOC(var, type, count)                                                              \
+  type *var = (type *)dalloc((size_t)(count) * sizeof(type));                                   \
+  if (!var) return fail(MRA_ERR_CUDA, "mra_apply_ns_tree: out of device memory (%s)", #var);
+
+  // ---- leaves: order, depth
+  NS_ALLOC(d_int, int, 4);
+  MRA_CUDA_TRY(cudaMemsetAsync(d_int, 0, 4 * sizeof(int), s));
+  leaf_check_kernel<<<(unsigned)((n_leaf + 255) / 256), 256, 0, s>>>(n_leaf, in->keys, n0, d_int, d_int + 1);
+  MRA_CUDA_TRY(cudaGetLastError());
+  int hint[2] = {0, 0};
+  MRA_CUDA_TRY(cudaMemcpyAsync(hint, d_int, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  if (hint[0]) return fail(MRA_ERR_ARG, "mra_apply_ns_tree: leaves must be sorted, unique and deeper than level %d", n0);
+  const int Nmax = hint[1];
+  if (n0 < op->min_level || Nmax - 1 > op->max_level || n0 < ns->min_level || Nmax - 1 > ns->max_level)
+    return fail(MRA_ERR_ARG, "mra_apply_ns_tree: levels %d..%d outside the operators' tables", n0, Nmax - 1);
+  NS_ALLOC(Ub, double, kk * k);
+  std::vector<double> U(2 * k * k), Ubh(2 * k * k);
+  two_scale(k, U.data());
+  for (int c = 0; c < 2; ++c)
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) Ubh[(c * k + i) * k + j] = U[c * k * k + i * k + j];
+  MRA_CUDA_TRY(cudaMemcpyAsync(Ub, Ubh.data(), Ubh.size() * 8, cudaMemcpyHostToDevice, s));
+
+  // ---- interior nodes of every level: the leaves' ancestors, sorted and unique
+  std::vector<uint64_t *> Ik(Nmax + 1, nullptr);
+  std::vector<int64_t> In(Nmax + 1, 0);
+  {
+    NS_ALLOC(anc, uint64_t, n_leaf);
+    NS_ALLOC(anc_s, uint64_t, n_leaf);
+    NS_ALLOC(d_nsel, int64_t, 1);
+    size_t t1 = 0, t2 = 0;
+    MRA_CUDA_TRY(cub::DeviceRadixSort::SortKeys(nullptr, t1, anc, anc_s, (int)n_leaf, 0, 64, s));
+    MRA_CUDA_TRY(cub::DeviceSelect::Unique(nullptr, t2, anc_s, anc, d_nsel, (int)n_leaf, s));
+    const size_t tb = std::max(t1, t2);
+    NS_ALLOC(tmp, unsigned char, tb);
+    for (int n = n0; n < Nmax; ++n) {
+      ancestor_kernel<<<(unsigned)((n_leaf + 255) / 256), 256, 0, s>>>(n_leaf, in->keys, n, anc);
+      MRA_CUDA_TRY(cudaGetLastError());
+      size_t tt = tb;
+      MRA_CUDA_TRY(cub::DeviceRadixSort::SortKeys(tmp, tt, anc, anc_s, (int)n_leaf, 0, 64, s));
+      NS_ALLOC(ik, uint64_t, n_leaf);
+      tt = tb;
+      MRA_CUDA_TRY(cub::DeviceSelect::Unique(tmp, tt, anc_s, ik, d_nsel, (int)n_leaf, s));
+      int64_t nsel = 0;
+      uint64_t last = 0;
+      MRA_CUDA_TRY(cudaMemcpyAsync(&nsel, d_nsel, 8, cudaMemcpyDeviceToHost, s));
+      MRA_CUDA_TRY(cudaStreamSynchronize(s));
+      if (nsel > 0) {
+        MRA_CUDA_TRY(cudaMemcpyAsync(&last, ik + nsel - 1, 8, cudaMemcpyDeviceToHost, s));
+        MRA_CUDA_TRY(cudaStreamSynchronize(s));
+        if (last == ~0ull) --nsel;  // leaves not deeper than n
+      }
+      Ik[n] = ik;
+      In[n] = nsel;
+    }
+    drop(anc);
+    drop(anc_s);
+    drop(tmp);
+  }
+  if (In[n0] != boxes(n0)) return fail(MRA_ERR_ARG, "mra_apply_ns_tree: level %d is not complete", n0);
+
+  // ---- compress, from the deepest interior level up
+  const size_t sh_c = (size_t)(kk * kk * kk + k * kk * kk + k * k * kk) * 8;
+  const size_t sh_d = (size_t)(k3 + kk * k * k + kk * kk * k) * 8;
+  MRA_CUDA_TRY(cudaFuncSetAttribute(compress_tree_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_c));
+  MRA_CUDA_TRY(cudaFuncSetAttribute(sum_down_tree_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_d));
+  std::vector<double *> Sn(Nmax + 1, nullptr), sn(Nmax + 1, nullptr);
+  for (int n = Nmax - 1; n >= n0; --n) {
+    NS_ALLOC(S, double, In[n] * kk * kk * kk);
+    NS_ALLOC(sv, double, In[n] * k3);
+    Sn[n] = S;
+    sn[n] = sv;
+    const bool deeper = n + 1 < Nmax;
+    compress_tree_kernel<<<(unsigned)In[n], 256, sh_c, s>>>(k, n, Ik[n], In[n], in->keys, in->coeffs, n_leaf,
+                                                            deeper ? Ik[n + 1] : nullptr, deeper ? sn[n + 1] : nullptr,
+                                                            deeper ? In[n + 1] : 0, Ub, S, sv, d_int);
+    MRA_CUDA_TRY(cudaGetLastError());
+  }
+  MRA_CUDA_TRY(cudaMemcpyAsync(hint, d_int, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  if (hint[0]) return fail(MRA_ERR_ARG, "mra_apply_ns_tree: the leaves are not a complete octree");
+
+  mra_apply_stats acc{};
+  // one library apply on the given boxes of one level; its output allocated here
+  auto run_apply = [&](const Operator &opx, int64_t nsrc, uint64_t *skeys, double *scoeffs,
+                       const mra_apply_opts &oo, int64_t cap, uint64_t **okeys, double **ocoeffs,
+                       int64_t *nout) -> int {
+    const size_t wb = apply_workspace_bytes(opx, oo, nsrc);
+    void *ws = dalloc(wb);
+    *okeys = (uint64_t *)dalloc((size_t)cap * 8);
+    *ocoeffs = (double *)dalloc((size_t)cap * opx.k * opx.k * opx.k * 8);
+    if (!ws || !*okeys || !*ocoeffs) return fail(MRA_ERR_CUDA, "mra_apply_ns_tree: out of device memory");
+    mra_tree_view vin{nsrc, nsrc, skeys, scoeffs, opx.k, opx.L};
+    mra_tree_view vout{0, cap, *okeys, *ocoeffs, opx.k, opx.L};
+    mra_apply_stats st{};
+    const int rc2 = apply_run(opx, vin, oo, vout, ws, wb, &st, s);
+    drop(ws);
+    if (rc2 != MRA_OK) return rc2;
+    acc.pairs += st.pairs;
+    acc.terms_kept += st.terms_kept;
+    acc.terms_screened += st.terms_screened;
+    acc.terms_issued += st.terms_issued;
+    acc.skipped_bound += st.skipped_bound;
+    acc.kernel_ms += st.kernel_ms;
+    *nout = vout.n;
+    return MRA_OK;
+  };
+
+  // ---- coarsest level: every box, T^{n0} with every displacement
+  int64_t nR = boxes(n0);
+  uint64_t *Rk = Ik[n0];
+  NS_ALLOC(r0, double, nR * k3);
+  double *R = r0;
+  {
+    uint64_t *ok;
+    double *oc;
+    int64_t no = 0;
+    int rc = run_apply(*op, nR, Rk, sn[n0], coarse_opts(*o, n0), nR, &ok, &oc, &no);
+    if (rc != MRA_OK) return rc;
+    MRA_CUDA_TRY(cudaMemsetAsync(R, 0, (size_t)nR * k3 * 8, s));
+    if (no > 0) {
+      scatter_dense_kernel<<<(unsigned)no, 128, 0, s>>>(no, ok, oc, k3, R);  // level n0 is complete: dense order
+      MRA_CUDA_TRY(cudaGetLastError());
+    }
+    drop(ok);
+    drop(oc);
+  }
+  int64_t nout = 0;
+  const int64_t cap = out->cap;
+  const int64_t w3 = (int64_t)(2 * D + 1) * (2 * D + 1) * (2 * D + 1);
+  for (int n = n0; n < Nmax; ++n) {
+    const int64_t tcap = std::min<int64_t>(boxes(n), In[n] * w3);
+    uint64_t *yk, *zk;
+    double *yc, *zc;
+    int64_t ny = 0, nz = 0;
+    int rc = run_apply(*ns, In[n], Ik[n], Sn[n], level_opts(*o), tcap, &yk, &yc, &ny);
+    if (rc != MRA_OK) return rc;
+    rc = run_apply(*op, In[n], Ik[n], sn[n], level_opts(*o), tcap, &zk, &zc, &nz);
+    if (rc != MRA_OK) return rc;
+    MRA_CUDA_TRY(cudaMemsetAsync(d_int, 0, sizeof(int), s));
+    if (ny > 0) targets_in_kernel<<<(unsigned)((ny + 255) / 256), 256, 0, s>>>(ny, yk, Rk, nR, d_int);
+    if (nz > 0) targets_in_kernel<<<(unsigned)((nz + 255) / 256), 256, 0, s>>>(nz, zk, Rk, nR, d_int);
+    MRA_CUDA_TRY(cudaGetLastError());
+    NS_ALLOC(yi, int64_t, nR);
+    NS_ALLOC(zi, int64_t, nR);
+    NS_ALLOC(refine, int, nR + 1);
+    NS_ALLOC(leaf, int, nR + 1);
+    NS_ALLOC(ref_pos, int, nR + 1);
+    NS_ALLOC(leaf_pos, int, nR + 1);
+    reach_kernel<<<(unsigned)((nR + 255) / 256), 256, 0, s>>>(nR, Rk, yk, ny, zk, nz, yi, zi, refine, leaf);
+    MRA_CUDA_TRY(cudaGetLastError());
+    MRA_CUDA_TRY(cudaMemsetAsync(refine + nR, 0, sizeof(int), s));
+    MRA_CUDA_TRY(cudaMemsetAsync(leaf + nR, 0, sizeof(int), s));
+    size_t tb = 0;
+    MRA_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tb, refine, ref_pos, (int)(nR + 1), s));
+    NS_ALLOC(tmp, unsigned char, tb);
+    MRA_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, tb, refine, ref_pos, (int)(nR + 1), s));
+    MRA_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, tb, leaf, leaf_pos, (int)(nR + 1), s));
+    int hcount[2] = {0, 0};
+    MRA_CUDA_TRY(cudaMemcpyAsync(&hcount[0], ref_pos + nR, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MRA_CUDA_TRY(cudaMemcpyAsync(&hint[0], d_int, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MRA_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hint[0]) return fail(MRA_ERR_NUMERIC, "mra_apply_ns_tree: a level-%d apply reached a box outside the result tree", n);
+    const int64_t nref = hcount[0], nleaf_here = nR - nref;
+    if (nleaf_here > 0) {
+      emit_leaves_kernel<<<(unsigned)nR, 128, 0, s>>>(nR, k3, Rk, R, leaf, leaf_pos, nout, cap, out->keys, out->coeffs);
+      MRA_CUDA_TRY(cudaGetLastError());
+    }
+    nout += nleaf_here;
+    // children of the reached nodes, then in key order
+    const int64_t nC = 8 * nref;
+    NS_ALLOC(cku, uint64_t, nC);
+    NS_ALLOC(cru, double, nC * k3);
+    if (nref > 0) {
+      sum_down_tree_kernel<<<(unsigned)nR, 256, sh_d, s>>>(k, nR, Rk, R, refine, ref_pos, yi, yc, zi, zc, Ub, cku, cru);
+      MRA_CUDA_TRY(cudaGetLastError());
+    }
+    NS_ALLOC(cks, uint64_t, nC);
+    NS_ALLOC(crs, double, nC * k3);
+    NS_ALLOC(idx, int, nC);
+    NS_ALLOC(idx_s, int, nC);
+    if (nC > 0) {
+      iota_ns_kernel<<<(unsigned)((nC + 255) / 256), 256, 0, s>>>(nC, idx);
+      MRA_CUDA_TRY(cudaGetLastError());
+      size_t ts = 0;
+      MRA_CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, ts, cku, cks, idx, idx_s, (int)nC, 0, 64, s));
+      NS_ALLOC(tmp2, unsigned char, ts);
+      MRA_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp2, ts, cku, cks, idx, idx_s, (int)nC, 0, 64, s));
+      gather_rows_ns_kernel<<<(unsigned)nC, 128, 0, s>>>(nC, k3, idx_s, cru, crs);
+      MRA_CUDA_TRY(cudaGetLastError());
+      drop(tmp2);
+    }
+    for (void *p : {(void *)yk, (void *)yc, (void *)zk, (void *)zc, (void *)yi, (void *)zi, (void *)refine,
+                    (void *)leaf, (void *)ref_pos, (void *)leaf_pos, (void *)tmp, (void *)cku, (void *)cru,
+                    (void *)idx, (void *)idx_s})
+      drop(p);
+    if (Rk != Ik[n0]) drop(Rk);
+    drop(R);
+    Rk = cks;
+    R = crs;
+    nR = nC;
+  }
+  // the deepest level: every node is a result leaf
+  if (nR > 0 && nout < cap) {
+    const int64_t ncopy = std::min<int64_t>(nR, cap - nout);
+    MRA_CUDA_TRY(cudaMemcpyAsync(out->keys + nout, Rk, (size_t)ncopy * 8, cudaMemcpyDeviceToDevice, s));
+    MRA_CUDA_TRY(cudaMemcpyAsync(out->coeffs + nout * k3, R, (size_t)ncopy * k3 * 8, cudaMemcpyDeviceToDevice, s));
+  }
+  nout += nR;
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  if (stats) {
+    acc.n_in = n_leaf;
+    acc.n_out = nout;
+    *stats = acc;
+  }
+  out->L = op->L;
+  if (nout > cap) {
+    out->n = nout;
+    return fail(MRA_ERR_CAPACITY, "mra_apply_ns_tree: %lld result leaves, capacity %lld", (long long)nout,
+                (long long)cap);
+  }
+  out->n = nout;
+  return MRA_OK;
+#undef NS_ALLOC
 }

@@ -39,7 +39,7 @@ EXPORTED = [
     "mra_operator_info", "mra_operator_block", "mra_operator_free", "mra_apply_workspace_size",
     "mra_apply", "mra_apply_batched", "mra_norm", "mra_norm_noalloc", "mra_compare", "mra_log_terms", "mra_mlp_init",
     "mra_mlp_standardize", "mra_mlp_forward", "mra_mlp_workspace_size", "mra_mlp_grad", "mra_mlp_train",
-    "mra_operator_ns_create", "mra_apply_ns_workspace_size", "mra_apply_ns",
+    "mra_operator_ns_create", "mra_apply_ns_workspace_size", "mra_apply_ns", "mra_apply_ns_tree",
 ]
 NOALLOC_MAX_BOXES = 1 << 20
 
@@ -125,6 +125,7 @@ def load(build_if_stale: bool = True):
         lib.mra_apply_ns_workspace_size.argtypes = [vp, vp, P(TreeView), i, P(ApplyOpts), P(ctypes.c_size_t)]
         lib.mra_apply_ns.argtypes = [vp, vp, P(TreeView), i, P(ApplyOpts), P(TreeView), vp, ctypes.c_size_t,
                                      P(ApplyStats), vp]
+        lib.mra_apply_ns_tree.argtypes = [vp, vp, P(TreeView), i, P(ApplyOpts), P(TreeView), P(ApplyStats), vp]
         lib.mra_norm.argtypes = [P(TreeView), vp, P(d), vp]
         lib.mra_norm_noalloc.argtypes = [P(TreeView), vp, P(d), vp]
         lib.mra_compare.argtypes = [P(TreeView), P(TreeView), P(CompareResult), vp]
@@ -485,5 +486,36 @@ class NSApplier:
 def apply_ns(op: Operator, ns_op: NSOperator, tree: "Tree", n0: int, opts: ApplyOpts, stream=None):
     """mra_apply_ns once; returns (output tree, stats dict)."""
     ap = NSApplier(op, ns_op, tree, n0, opts)
+    out = ap(tree, stream)
+    return out, ap.stats.as_dict()
+
+
+class NSTreeApplier:
+    """mra_apply_ns_tree with an output tree that grows on MRA_ERR_CAPACITY (adaptive trees)."""
+
+    def __init__(self, op: Operator, ns_op: NSOperator, n0: int, opts: ApplyOpts, out_cap: int = 0,
+                 device="cuda"):
+        self.op, self.ns_op, self.n0, self.opts = op, ns_op, int(n0), opts
+        self.out = Tree.empty(max(out_cap, 1), op.k, op.L, device)
+        self.stats = ApplyStats()
+
+    def __call__(self, tree: "Tree", stream=None) -> "Tree":
+        lib = load()
+        while True:
+            vin, vout = tree.view(), self.out.view()
+            rc = lib.mra_apply_ns_tree(self.op.handle, self.ns_op.handle, ctypes.byref(vin), self.n0,
+                                       ctypes.byref(self.opts), ctypes.byref(vout), ctypes.byref(self.stats),
+                                       _stream(stream))
+            if rc == MRA_ERR_CAPACITY and vout.n > self.out.cap:
+                self.out = Tree.empty(int(vout.n), self.op.k, self.op.L, tree.keys.device)
+                continue
+            _check(rc)
+            self.out.n = int(vout.n)
+            return self.out
+
+
+def apply_ns_tree(op: Operator, ns_op: NSOperator, tree: "Tree", n0: int, opts: ApplyOpts, stream=None):
+    """mra_apply_ns_tree once; returns (result leaves as a tree, stats dict)."""
+    ap = NSTreeApplier(op, ns_op, n0, opts, out_cap=8 * tree.n, device=tree.keys.device)
     out = ap(tree, stream)
     return out, ap.stats.as_dict()

@@ -106,3 +106,82 @@ def test_ns_rejects_bad_inputs(mra):
         mra.apply_ns(op, ns_op, mra.Tree.from_host(shuffled, coeffs, 8.0), 1, opts)
     with pytest.raises(mra.MraError):          # the operator's blocks must reach 2 D + 1 at level n+1
         mra.NSOperator(mra.Operator(0, 8, k, 8.0, 0, N, max_disp=1, fit_eps=1e-4), max_disp=1)
+
+
+# ----------------------------------------------------------------- adaptive trees
+
+def adaptive_case(mra, k, thresh=3e-3, max_level=4, op_disp=15, M=8):
+    L = 8.0
+    f = W.gaussian_sum(2, 1.0, 20.0, seed=11, centre_box=3.0)
+    keys, coeffs, _ = O.project(f, k, L, thresh=thresh, init_level=2, max_level=max_level)
+    op = mra.Operator(0, M, k, L, 0, max_level, max_disp=op_disp, fit_eps=1e-4)
+    return keys, coeffs, op, op.fit(), L
+
+
+@pytest.mark.parametrize("k,D", [(3, 1), (4, 2), (6, 1), (8, 1)])
+def test_ns_tree_fp64_matches_oracle(mra, k, D):
+    keys, coeffs, op, fit, L = adaptive_case(mra, k)
+    ns_op = mra.NSOperator(op, max_disp=D)
+    out, st = mra.apply_ns_tree(op, ns_op, mra.Tree.from_host(keys, coeffs, L), 1,
+                                mra.make_opts(stencil=mra.STENCIL_SHELLS, max_disp=D))
+    gk, gc = out.host()
+    rk, rc = O.apply_ns_tree(keys, coeffs, k, L, 1, fit["c"], fit["t"], D)
+    assert (gk == rk).all()  # the same result tree
+    assert rel(gc, rc) <= 1e-12
+
+
+def test_ns_tree_with_every_displacement_is_the_leaf_level_apply(mra):
+    k = 3
+    keys, coeffs, op, fit, L = adaptive_case(mra, k)
+    tree = mra.Tree.from_host(keys, coeffs, L)
+    ns_op = mra.NSOperator(op, max_disp=7)
+    out, _ = mra.apply_ns_tree(op, ns_op, tree, 1, mra.make_opts(stencil=mra.STENCIL_SHELLS, max_disp=7))
+    leaf, _ = mra.apply(op, tree, mra.make_opts(stencil=mra.STENCIL_SHELLS, max_disp=15))
+    pts = np.random.default_rng(2).uniform(-L, L, size=(300, 3))
+    a = O.evaluate(*leaf.host(), k, L, pts)
+    b = O.evaluate(*out.host(), k, L, pts)
+    # levels 1..3 of the non-standard form reach |l| <= 7; level-4 leaves enter through
+    # level 3's 2k apply, whose children's displacements reach 15: every displacement
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+
+
+def test_ns_tree_on_a_uniform_tree_equals_the_uniform_apply(mra):
+    k, N = 4, 3
+    keys, coeffs, op, fit = uniform_case(mra, k, N, op_disp=3)
+    ns_op = mra.NSOperator(op, max_disp=1)
+    tree = mra.Tree.from_host(keys, coeffs, 8.0)
+    opts = mra.make_opts(stencil=mra.STENCIL_SHELLS, max_disp=1)
+    a, _ = mra.apply_ns(op, ns_op, tree, 1, opts)
+    b, _ = mra.apply_ns_tree(op, ns_op, tree, 1, opts)
+    ak, ac = a.host()
+    bk, bc = b.host()
+    assert (ak == bk).all() and np.array_equal(ac, bc)
+
+
+@pytest.mark.parametrize("k", [4, 6, 8])
+def test_ns_tree_split_matches_oracle(mra, k):
+    keys, coeffs, op, fit, L = adaptive_case(mra, k, op_disp=3)
+    ns_op = mra.NSOperator(op, max_disp=1)
+    rk, rc = O.apply_ns_tree(keys, coeffs, k, L, 1, fit["c"], fit["t"], 1)
+    for v in (0, 1, 2):
+        opts = mra.make_opts(precision=mra.PREC_SPLIT_BF16, stencil=mra.STENCIL_SHELLS, max_disp=1)
+        opts.tile_variant = v
+        out, _ = mra.apply_ns_tree(op, ns_op, mra.Tree.from_host(keys, coeffs, L), 1, opts)
+        gk, gc = out.host()
+        assert (gk == rk).all()
+        assert rel(gc, rc) <= 1e-6
+
+
+def test_ns_tree_rejects_bad_trees_and_grows_its_output(mra):
+    k = 4
+    keys, coeffs, op, fit, L = adaptive_case(mra, k, op_disp=3)
+    ns_op = mra.NSOperator(op, max_disp=1)
+    opts = mra.make_opts(stencil=mra.STENCIL_SHELLS, max_disp=1)
+    with pytest.raises(mra.MraError):   # a missing leaf: not a complete octree
+        mra.apply_ns_tree(op, ns_op, mra.Tree.from_host(np.delete(keys, 5), np.delete(coeffs, 5, 0), L), 1, opts)
+    with pytest.raises(mra.MraError):   # leaves must be deeper than the coarsest level
+        mra.apply_ns_tree(op, ns_op, mra.Tree.from_host(keys, coeffs, L), 2, opts)
+    ap = mra.NSTreeApplier(op, ns_op, 1, opts, out_cap=1)   # capacity error, then a retry
+    out = ap(mra.Tree.from_host(keys, coeffs, L))
+    rk, rc = O.apply_ns_tree(keys, coeffs, k, L, 1, fit["c"], fit["t"], 1)
+    assert out.n == len(rk) and rel(out.host()[1], rc) <= 1e-12
