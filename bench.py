@@ -225,30 +225,38 @@ def ns_terms(N: int, n0: int, D: int, M: int):
 
 
 def run_ns(args, w, rank, world):
-    """The non-standard form apply (mra_apply_ns) on a uniform tree; same JSON line."""
+    """The non-standard form apply (mra_apply_ns on a uniform tree, mra_apply_ns_tree on an adaptive
+    one); same JSON line."""
     import torch
     from paper_1507_01888_gb300 import mra, autotune
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    N, n0, D = w.uniform_level, w.extra["ns"]["n0"], w.max_disp
+    n0, D = w.extra["ns"]["n0"], w.max_disp
+    adaptive = w.uniform_level < 0
     prec = mra.PREC_FP64 if args.precision == "fp64" else mra.PREC_SPLIT_BF16
-    tree = mra.project(w.funcs[0], w.k, w.L, uniform_level=N)
+    tree = mra.project(w.funcs[0], w.k, w.L, thresh=w.thresh, init_level=w.init_level, max_level=w.max_level,
+                       uniform_level=w.uniform_level)
+    keys_h0 = tree.host()[0]
+    N = int((keys_h0 >> np.uint64(57)).max())
     op = mra.Operator(w.kernel, w.M, w.k, w.L, 0, N, max_disp=max(2 * D + 1, (1 << n0) - 1), mu=w.mu,
                       fit_eps=w.fit_eps)
     ns_op = mra.NSOperator(op, max_disp=D)
     opts = mra.make_opts(precision=prec, pieces=args.pieces, stencil=mra.STENCIL_SHELLS, max_disp=D)
+
+    def make(o):
+        if adaptive:
+            return mra.NSTreeApplier(op, ns_op, n0, o, out_cap=8 * tree.n, device=dev)
+        return mra.NSApplier(op, ns_op, tree, n0, o)
     tuning = {}
     if prec == mra.PREC_SPLIT_BF16:
-        def make(o):
-            return mra.NSApplier(op, ns_op, tree, n0, o)
         opts, table = autotune.tune(op, tree, opts, make_applier=make)
         tuning = {"tile_variant": opts.tile_variant, "candidates_ms": table}
-    ap = mra.NSApplier(op, ns_op, tree, n0, opts)
+    ap = make(opts)
     ap(tree)
     torch.cuda.synchronize()
     accuracy = {}
     if prec != mra.PREC_FP64:
-        ref = mra.NSApplier(op, ns_op, tree, n0, mra.make_opts(stencil=mra.STENCIL_SHELLS, max_disp=D))
+        ref = make(mra.make_opts(stencil=mra.STENCIL_SHELLS, max_disp=D))
         cmp = mra.compare(ap(tree), ref(tree))
         accuracy = {"rel_l2_vs_fp64_gpu": cmp["rel_l2"], "max_box_rel_vs_fp64_gpu": cmp["max_box_rel"],
                     "fp64_gpu_apply_ms": ref.stats.kernel_ms,
@@ -280,7 +288,7 @@ def run_ns(args, w, rank, world):
     coeffs_pin = torch.from_numpy(coeffs_h.copy()).pin_memory()
     dev_tree = mra.Tree(torch.empty_like(keys_pin, device=dev), torch.empty_like(coeffs_pin, device=dev),
                         tree.n, w.k, w.L)
-    out_pin = torch.empty_like(coeffs_pin).pin_memory()
+    out_pin = torch.empty((ap.out.n,) + tuple(coeffs_pin.shape[1:]), dtype=torch.float64).pin_memory()
     e_ms = []
     for i in range(args.steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -288,13 +296,18 @@ def run_ns(args, w, rank, world):
         dev_tree.keys.copy_(keys_pin, non_blocking=True)
         dev_tree.coeffs.copy_(coeffs_pin, non_blocking=True)
         out = ap(dev_tree, stream)
-        out_pin.copy_(out.coeffs[:tree.n], non_blocking=True)
+        out_pin.copy_(out.coeffs[:out.n], non_blocking=True)
         b.record(stream)
         b.synchronize()
         e_ms.append(a.elapsed_time(b))
     _, e2e_ms = reduce_over_ranks(tree.n, statistics.mean(e_ms), world, dev)
     k = w.k
-    terms = ns_terms(N, n0, D, w.M)
+    if adaptive:  # no screen: every level's 2k and k applies keep the same terms; the coarsest is T^{n0}
+        tc = ns_terms(n0, n0, D, w.M)[0][2]
+        t2 = (ap.stats.terms_kept - tc) // 2
+        terms = [(n0, 1, tc), (-1, 2, t2), (-1, 1, t2)]
+    else:
+        terms = ns_terms(N, n0, D, w.M)
     flops = sum(t * (6 * (f * k) ** 4 + (f * k) ** 3) for _, f, t in terms)
     kms_mean = statistics.mean(kms)
     achieved = flops / (kms_mean / 1e3) / 1e12
@@ -314,7 +327,8 @@ def run_ns(args, w, rank, world):
     line = {"metric": METRIC, "value": value, "unit": "boxes/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-            "config": {"workload": w.name, "n_boxes": n_all, "k": k, "M": w.M, "form": "non-standard",
+            "config": {"workload": w.name, "n_boxes": n_all, "result_leaves": ap.out.n, "k": k, "M": w.M,
+                       "form": "non-standard" + (", adaptive tree" if adaptive else ", uniform tree"),
                        "levels": f"{n0}..{N}", "max_disp_per_level": D, "terms": sum(t for _, _, t in terms),
                        "terms_reported": ap.stats.terms_kept,
                        "precision": "fp64" if prec == mra.PREC_FP64 else "split",

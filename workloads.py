@@ -130,6 +130,15 @@ def poisson_ns_uniform_k6() -> Workload:
                     max_disp=1, tau=0.0, extra={"ns": {"n0": 1}})
 
 
+def bsh_ns_adaptive_k8() -> Workload:
+    """Non-standard form apply on an adaptive tree: the mixed-precision BSH workload's function
+    (8 Gaussians a~logU[1,1e4], seed 2) at k=8 (2k=16), thresh 1e-6, exp(-r)/r as 60
+    Gaussians, complete apply at level 1, |l|_inf <= 1 at every finer level, no screen."""
+    return Workload("bsh_ns_adaptive_k8", [gaussian_sum(8, 1.0, 1e4, seed=2)], k=8, L=L_CELL, thresh=1e-6,
+                    uniform_level=-1, kernel=BSH, mu=1.0, M=60, fit_eps=1e-6, stencil=0, max_disp=1, tau=0.0,
+                    extra={"ns": {"n0": 1}})
+
+
 def shard(w: Workload, rank: int, world: int) -> Workload:
     """The workload rank `rank` of `world` runs.  Families of independent functions give every
     rank its own part (same size: weak scaling, no exchange between ranks); a single-function
@@ -148,6 +157,7 @@ WORKLOADS = {
     "bsh_m80_adaptive_k10_learned": bsh_learned_k10,
     "poisson_m100_adaptive_k14": poisson_k14_large,
     "poisson_ns_uniform_l5_k6": poisson_ns_uniform_k6,
+    "bsh_ns_adaptive_k8": bsh_ns_adaptive_k8,
 }
 
 
