@@ -76,6 +76,7 @@ def _load():
         lib.orc_apply.argtypes = [i, d, l, U64, D, i, D, D, i, i, d, l, U64, l, U64, D, D, D, L, L, i]
         lib.orc_apply_ns.argtypes = [i, d, i, i, D, i, D, D, i, D, i]
         lib.orc_apply_ns_tree.argtypes = [i, d, l, U64, D, i, i, D, D, i, l, U64, D, L, i]
+        lib.orc_reconstruct.argtypes = [i, l, U64, D, l, U64, D, L]
         lib.orc_unfilter3.argtypes = [i, D, D]
         lib.orc_filter3.argtypes = [i, D, D]
         _lib = lib
@@ -341,3 +342,24 @@ def evaluate(keys, coeffs, k: int, L: float, points):
             f = [phi(k, u[p, d] - b[p, d]) for d in range(3)]
             out[p] += h ** -1.5 * np.einsum("ijl,i,j,l->", coeffs[pos[p]], f[0], f[1], f[2])
     return out
+
+
+def reconstruct(keys, coeffs, k: int):
+    """Sum-down of a multi-level set of boxes (any levels, overlapping allowed) into disjoint
+    leaves holding the same function (Sec. 2.2, the fast wavelet transform's reconstruction).
+    Returns (leaf keys, coefficients) in key order."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    coeffs = np.ascontiguousarray(coeffs, dtype=np.float64).reshape(len(keys), k, k, k)
+    cap = max(1, 8 * len(keys))
+    while True:
+        ok = np.zeros(cap, dtype=np.uint64)
+        oc = np.zeros((cap, k, k, k))
+        n = ctypes.c_long(0)
+        rc = _load().orc_reconstruct(int(k), len(keys), _up(keys), _dp(coeffs), int(cap), _up(ok), _dp(oc),
+                                     ctypes.byref(n))
+        if rc == -4:
+            cap = int(n.value)
+            continue
+        if rc != 0:
+            raise RuntimeError(f"orc_reconstruct failed ({rc})")
+        return ok[:n.value].copy(), oc[:n.value].copy()

@@ -1406,3 +1406,164 @@ int orc_apply_ns_tree(int k, double L, long n_leaf, const uint64_t *lkeys, const
   if (nout > cap) rc = -4;
   return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Reconstruct: a multi-level sum of boxes as disjoint leaves (Sec. 2.2)     */
+/* ------------------------------------------------------------------------ */
+
+/* The input boxes (sorted, unique keys, any levels, a box and its descendants both allowed)
+ * represent f = sum_b f_b.  Sum-down (the reconstruction half of the fast wavelet transform):
+ * a box that has input boxes below it is interior; so is every box on the path from it to
+ * them; every interior box passes its accumulated coefficients to its eight children through
+ * the two-scale relation (S = Ubar^{x3} s), and the boxes that are not interior are the
+ * leaves of the result, which hold f restricted to them.  A box with no input box above it
+ * is a top of the result. */
+int orc_reconstruct(int k, long n_in, const uint64_t *keys, const double *coeffs, long cap, uint64_t *out_keys,
+                    double *out_coeffs, long *n_out) {
+  if (k < 1 || 2 * k > ORC_MAXK || n_in < 0) return -1;
+  for (long i = 1; i < n_in; ++i)
+    if (keys[i] <= keys[i - 1]) return -1;
+  int k3 = k * k * k, kk = 2 * k, kk3 = kk * kk * kk;
+  double U0[ORC_MAXK * ORC_MAXK], U1[ORC_MAXK * ORC_MAXK];
+  orc_two_scale(k, U0, U1);
+  double Ub[2 * ORC_MAXK * ORC_MAXK];
+  for (int cc = 0; cc < 2; ++cc)
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) Ub[(cc * k + i) * k + j] = (cc == 0 ? U0 : U1)[i * k + j];
+  /* top level of every input box: the shallowest input box above it or itself */
+  int *top = (int *)malloc(sizeof(int) * (n_in > 0 ? n_in : 1));
+  int nmin = 20, nmax = -1;
+  for (long b = 0; b < n_in; ++b) {
+    int lv;
+    long x, y, z;
+    split_key(keys[b], &lv, &x, &y, &z);
+    top[b] = lv;
+    for (int m = 0; m < lv; ++m)
+      if (find_key(keys, n_in, make_key(m, x >> (lv - m), y >> (lv - m), z >> (lv - m))) >= 0) {
+        top[b] = m;
+        break;
+      }
+    if (lv < nmin) nmin = lv;
+    if (lv > nmax) nmax = lv;
+  }
+  long nout = 0;
+  /* R: the result's boxes of the current level with their accumulated coefficients */
+  orc_set R = {0, NULL, NULL};
+  for (int n = nmin; n <= nmax; ++n) {
+    /* interior boxes of level n: ancestors (at level n) of deeper input boxes with top <= n */
+    uint64_t *I = (uint64_t *)malloc(sizeof(uint64_t) * (n_in > 0 ? n_in : 1));
+    long nI = 0;
+    for (long b = 0; b < n_in; ++b) {
+      int lv;
+      long x, y, z;
+      split_key(keys[b], &lv, &x, &y, &z);
+      if (lv > n && top[b] <= n) I[nI++] = make_key(n, x >> (lv - n), y >> (lv - n), z >> (lv - n));
+    }
+    qsort(I, nI, sizeof(uint64_t), cmp_u64v);
+    long u = 0;
+    for (long i = 0; i < nI; ++i)
+      if (i == 0 || I[i] != I[i - 1]) I[u++] = I[i];
+    nI = u;
+    /* R_n = children passed down from level n-1 (already in R) plus the tops of level n */
+    long ntop = 0;
+    for (long b = 0; b < n_in; ++b)
+      if ((int)(keys[b] >> 57) == n && top[b] == n) ++ntop;
+    orc_set Rn;
+    Rn.n = R.n + ntop;
+    Rn.keys = (uint64_t *)malloc(sizeof(uint64_t) * (Rn.n > 0 ? Rn.n : 1));
+    Rn.v = (double *)malloc(sizeof(double) * (Rn.n > 0 ? Rn.n : 1) * k3);
+    long q = 0;
+    for (long i = 0; i < R.n; ++i, ++q) {
+      Rn.keys[q] = R.keys[i];
+      memcpy(Rn.v + q * k3, R.v + i * k3, sizeof(double) * k3);
+    }
+    for (long b = 0; b < n_in; ++b)
+      if ((int)(keys[b] >> 57) == n && top[b] == n) {
+        Rn.keys[q] = keys[b];
+        memcpy(Rn.v + q * k3, coeffs + b * k3, sizeof(double) * k3);
+        ++q;
+      }
+    /* key order */
+    long *perm = (long *)malloc(sizeof(long) * (Rn.n > 0 ? Rn.n : 1));
+    for (long i = 0; i < Rn.n; ++i) perm[i] = i;
+    for (long i = 1; i < Rn.n; ++i) {
+      long pi = perm[i], j = i - 1;
+      while (j >= 0 && Rn.keys[perm[j]] > Rn.keys[pi]) {
+        perm[j + 1] = perm[j];
+        --j;
+      }
+      perm[j + 1] = pi;
+    }
+    orc_set Rs;
+    Rs.n = Rn.n;
+    Rs.keys = (uint64_t *)malloc(sizeof(uint64_t) * (Rs.n > 0 ? Rs.n : 1));
+    Rs.v = (double *)malloc(sizeof(double) * (Rs.n > 0 ? Rs.n : 1) * k3);
+    for (long i = 0; i < Rs.n; ++i) {
+      Rs.keys[i] = Rn.keys[perm[i]];
+      memcpy(Rs.v + i * k3, Rn.v + perm[i] * k3, sizeof(double) * k3);
+    }
+    free(perm);
+    free(Rn.keys);
+    free(Rn.v);
+    /* the input boxes of level n below a top add their own coefficients */
+    for (long b = 0; b < n_in; ++b)
+      if ((int)(keys[b] >> 57) == n && top[b] < n) {
+        long p = find_key(Rs.keys, Rs.n, keys[b]);
+        if (p < 0) { /* cannot happen: its parent is interior */
+          free(I);
+          free(Rs.keys);
+          free(Rs.v);
+          free(R.keys);
+          free(R.v);
+          free(top);
+          return -3;
+        }
+        for (int i = 0; i < k3; ++i) Rs.v[p * k3 + i] += coeffs[b * k3 + i];
+      }
+    /* leaves out, interior boxes down */
+    long nnext = 0;
+    for (long p = 0; p < Rs.n; ++p)
+      if (find_key(I, nI, Rs.keys[p]) >= 0) ++nnext;
+    orc_set Nx;
+    Nx.n = 8 * nnext;
+    Nx.keys = (uint64_t *)malloc(sizeof(uint64_t) * (Nx.n > 0 ? Nx.n : 1));
+    Nx.v = (double *)malloc(sizeof(double) * (Nx.n > 0 ? Nx.n : 1) * k3);
+    double *S = (double *)malloc(sizeof(double) * kk3);
+    long c = 0;
+    for (long p = 0; p < Rs.n; ++p) {
+      if (find_key(I, nI, Rs.keys[p]) < 0) {
+        if (nout < cap) {
+          out_keys[nout] = Rs.keys[p];
+          memcpy(out_coeffs + nout * k3, Rs.v + p * k3, sizeof(double) * k3);
+        }
+        ++nout;
+        continue;
+      }
+      unfilter3(k, Ub, Rs.v + p * k3, S);
+      int lv;
+      long x, y, z;
+      split_key(Rs.keys[p], &lv, &x, &y, &z);
+      for (int cx = 0; cx < 2; ++cx)
+        for (int cy = 0; cy < 2; ++cy)
+          for (int cz = 0; cz < 2; ++cz, ++c) {
+            Nx.keys[c] = make_key(n + 1, 2 * x + cx, 2 * y + cy, 2 * z + cz);
+            double *o = Nx.v + c * k3;
+            for (int i = 0; i < k; ++i)
+              for (int j = 0; j < k; ++j)
+                for (int l = 0; l < k; ++l) o[(i * k + j) * k + l] = S[((cx * k + i) * kk + cy * k + j) * kk + cz * k + l];
+          }
+    }
+    free(S);
+    free(I);
+    free(Rs.keys);
+    free(Rs.v);
+    free(R.keys);
+    free(R.v);
+    R = Nx;
+  }
+  free(R.keys);
+  free(R.v);
+  free(top);
+  *n_out = nout;
+  return nout > cap ? -4 : 0;
+}

@@ -492,3 +492,44 @@ def test_ns_tree_is_accurate_where_the_leaf_apply_is_not():
     e_ns = np.abs(O.evaluate(nk, nc, k, L, pts) - exact).max() / np.abs(exact).max()
     e_leaf = np.abs(O.evaluate(leaf.keys, leaf.coeffs, k, L, pts) - exact).max() / np.abs(exact).max()
     assert e_ns < 1e-3 and e_leaf > 0.1
+
+
+# ----------------------------------------------------------------- reconstruct (sum-down)
+
+def test_reconstruct_keeps_the_function_on_disjoint_leaves():
+    """The leaf-level apply's output (boxes of several levels, a box and its descendants both
+    present) summed down to disjoint leaves: the same function at 500 points, no leaf inside
+    another, and a tree that is already disjoint comes back unchanged."""
+    k, L = 4, 8.0
+    f = W.gaussian_sum(2, 1.0, 20.0, seed=11, centre_box=3.0)
+    keys, coeffs, _ = O.project(f, k, L, thresh=3e-3, init_level=2, max_level=4)
+    r_lo, r_hi = O.kernel_range(0, 0.0, L, 1e-4)
+    _, _, _, c, t = O.fit_search(0.0, 8, r_lo, r_hi)
+    multi = O.apply(keys, coeffs, c, t, L, stencil=0, max_disp=1, tau=0.0)
+    rk, rc = O.reconstruct(multi.keys, multi.coeffs, k)
+    pts = np.random.default_rng(0).uniform(-L, L, size=(500, 3))
+    a = O.evaluate(multi.keys, multi.coeffs, k, L, pts)
+    assert np.abs(O.evaluate(rk, rc, k, L, pts) - a).max() <= 1e-13 * np.abs(a).max()
+    assert (rk[1:] > rk[:-1]).all()
+    lev = (rk >> np.uint64(57)).astype(np.int64)
+    s = set(int(x) for x in rk)
+    for key, n in zip(rk, lev):  # no ancestor of a leaf is a leaf
+        x, y, z = (int(key) >> 38) & 0x7FFFF, (int(key) >> 19) & 0x7FFFF, int(key) & 0x7FFFF
+        for m in range(int(n)):
+            assert int(O.make_key(m, x >> (n - m), y >> (n - m), z >> (n - m))) not in s
+    same_k, same_c = O.reconstruct(keys, coeffs, k)
+    assert (same_k == keys).all() and np.array_equal(same_c, coeffs)
+
+
+def test_reconstruct_of_a_box_and_one_child():
+    """A level-2 box and one of its level-3 children: the result is the box's eight children;
+    their function equals the sum at every point."""
+    k, L = 3, 8.0
+    rng = np.random.default_rng(5)
+    keys = np.array([O.make_key(2, 1, 2, 3), O.make_key(3, 3, 4, 7)], dtype=np.uint64)
+    coeffs = rng.standard_normal((2, k, k, k))
+    rk, rc = O.reconstruct(keys, coeffs, k)
+    assert len(rk) == 8 and ((rk >> np.uint64(57)) == 3).all()
+    pts = np.column_stack([rng.uniform(-4, 0, 200), rng.uniform(0, 4, 200), rng.uniform(4, 8, 200)])
+    a = O.evaluate(keys, coeffs, k, L, pts)
+    assert np.abs(O.evaluate(rk, rc, k, L, pts) - a).max() <= 1e-13 * np.abs(a).max()
