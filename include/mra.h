@@ -322,6 +322,15 @@ int mra_apply_ns(const mra_operator *op, const mra_operator *ns_op, const mra_tr
 int mra_apply_ns_tree(const mra_operator *op, const mra_operator *ns_op, const mra_tree_view *in, int n0,
                       const mra_apply_opts *opts, mra_tree_view *out, mra_apply_stats *stats, void *stream);
 
+/* Reconstruct (sum-down, Sec. 2.2): boxes of any levels, keys sorted and unique, a box and
+ * boxes below it both allowed (as mra_apply returns them: every destination at its source's
+ * level), representing f = sum_b f_b; out: disjoint leaves holding the same function, keys
+ * sorted.  Every box with input boxes below it, and every box on the path down to them, passes
+ * its accumulated coefficients to its eight children through the two-scale relation; the
+ * others are the leaves.  k <= MRA_MAX_K / 2.  Capacity as mra_apply_ns_tree; temporaries
+ * stream-ordered; synchronises the stream. */
+int mra_reconstruct(const mra_tree_view *in, mra_tree_view *out, void *stream);
+
 /* Per-box Frobenius norms (device array of tree->n doubles, may be NULL) and
  * the total L2 norm (host double, may be NULL).  Deterministic reduction. */
 int mra_norm(const mra_tree_view *tree, double *per_box, double *total, void *stream);

@@ -331,6 +331,113 @@ __global__ void iota_ns_kernel(int64_t n, int *v) {
   if (i < n) v[i] = (int)i;
 }
 
+// ---------------------------------------------------------------- reconstruct
+// Level of the shallowest input box above box b or b itself (the input is sorted and unique).
+__global__ void top_level_kernel(int64_t n, const uint64_t *keys, int *top) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  const uint64_t k = keys[b];
+  const int lv = key_level(k);
+  int t = lv;
+  for (int m = 0; m < lv; ++m)
+    if (find_sorted(keys, n, make_key(m, key_x(k) >> (lv - m), key_y(k) >> (lv - m), key_z(k) >> (lv - m))) >= 0) {
+      t = m;
+      break;
+    }
+  top[b] = t;
+}
+
+// Interior boxes of level n: the level-n ancestors of deeper input boxes with an input box at
+// or above level n on their path (others: the largest key, dropped later).
+__global__ void interior_kernel(int64_t n_in, const uint64_t *keys, const int *top, int n, uint64_t *out) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_in) return;
+  const uint64_t k = keys[b];
+  const int lv = key_level(k);
+  out[b] = (lv > n && top[b] <= n) ? make_key(n, key_x(k) >> (lv - n), key_y(k) >> (lv - n), key_z(k) >> (lv - n))
+                                   : ~0ull;
+}
+
+// Input boxes of level n in [lo, hi): tops join the level's boxes (appended after `base`
+// passed-down boxes), the others add their coefficients to the passed-down box of the same key.
+__global__ void tops_kernel(int64_t lo, int64_t hi, int n, const int *top, const uint64_t *keys, const double *coeffs,
+                            int k3, const int *pos, int64_t base, uint64_t *rkeys, double *rv) {
+  const int64_t b = lo + blockIdx.x;
+  if (b >= hi || top[b] != n) return;
+  const int64_t o = base + pos[b - lo];
+  if (threadIdx.x == 0) rkeys[o] = keys[b];
+  for (int e = threadIdx.x; e < k3; e += blockDim.x) rv[o * k3 + e] = coeffs[b * k3 + e];
+}
+__global__ void top_flags_kernel(int64_t lo, int64_t hi, int n, const int *top, int *flag) {
+  const int64_t b = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= hi) return;
+  flag[b - lo] = top[b] == n ? 1 : 0;
+}
+__global__ void add_inputs_kernel(int64_t lo, int64_t hi, int n, const int *top, const uint64_t *keys,
+                                  const double *coeffs, int k3, const uint64_t *rkeys, int64_t nr, double *rv,
+                                  int *err) {
+  const int64_t b = lo + blockIdx.x;
+  if (b >= hi || top[b] == n) return;
+  __shared__ int64_t p;
+  if (threadIdx.x == 0) p = find_sorted(rkeys, nr, keys[b]);
+  __syncthreads();
+  if (p < 0) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    return;
+  }
+  for (int e = threadIdx.x; e < k3; e += blockDim.x) rv[p * k3 + e] += coeffs[b * k3 + e];
+}
+
+// Is box p of the level interior (passes down) or a leaf of the result?
+__global__ void classify_kernel(int64_t nr, const uint64_t *rkeys, const uint64_t *ikeys, int64_t ni, int *inner,
+                                int *leaf) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nr) return;
+  const bool in = find_sorted(ikeys, ni, rkeys[p]) >= 0;
+  inner[p] = in ? 1 : 0;
+  leaf[p] = in ? 0 : 1;
+}
+
+// One CTA per interior box: its eight children get Ubar^{x3} s (two-scale relation).
+__global__ void pass_down_kernel(int k, int64_t nr, const uint64_t *rkeys, const double *rv, const int *inner,
+                                 const int *pos, const double *Ub, uint64_t *ckeys, double *cv) {
+  extern __shared__ double sh[];
+  const int64_t p = blockIdx.x;
+  if (p >= nr || !inner[p]) return;
+  const int kk = 2 * k, k2 = k * k, k3 = k2 * k, kk3 = kk * kk * kk;
+  double *d = sh, *a = d + k3, *b = a + kk * k2;
+  const int64_t base = 8 * (int64_t)pos[p];
+  for (int e = threadIdx.x; e < k3; e += blockDim.x) d[e] = rv[p * k3 + e];
+  const uint64_t key = rkeys[p];
+  if (threadIdx.x < 8) {
+    const int cx = threadIdx.x >> 2, cy = (threadIdx.x >> 1) & 1, cz = threadIdx.x & 1;
+    ckeys[base + threadIdx.x] =
+        make_key(key_level(key) + 1, 2 * key_x(key) + cx, 2 * key_y(key) + cy, 2 * key_z(key) + cz);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kk * k2; e += blockDim.x) {
+    const int I = e / k2, q = e % k2;
+    double v = 0.0;
+    for (int i = 0; i < k; ++i) v += Ub[I * k + i] * d[i * k2 + q];
+    a[e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kk * kk * k; e += blockDim.x) {
+    const int I = e / (kk * k), J = (e / k) % kk, l = e % k;
+    double v = 0.0;
+    for (int j = 0; j < k; ++j) v += Ub[J * k + j] * a[(I * k + j) * k + l];
+    b[e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kk3; e += blockDim.x) {
+    const int I = e / (kk * kk), J = (e / kk) % kk, Lq = e % kk;
+    double v = 0.0;
+    for (int l = 0; l < k; ++l) v += Ub[Lq * k + l] * b[(I * kk + J) * k + l];
+    const int child = ((I / k) << 2) | ((J / k) << 1) | (Lq / k);
+    cv[(base + child) * k3 + ((I % k) * k + J % k) * k + Lq % k] = v;
+  }
+}
+
 inline size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
 inline int64_t boxes(int n) { return 1LL << (3 * n); }
 
@@ -916,4 +1023,206 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
   out->n = nout;
   return MRA_OK;
 #undef NS_ALLOC
+}
+
+
+// ---------------------------------------------------------------- reconstruct (host)
+extern "C" int mra_reconstruct(const mra_tree_view *in, mra_tree_view *out, void *stream) {
+  if (!in || !out) return fail(MRA_ERR_ARG, "mra_reconstruct: NULL argument");
+  if (in->n < 0 || (in->n > 0 && (!in->keys || !in->coeffs))) return fail(MRA_ERR_ARG, "mra_reconstruct: bad input");
+  if (in->k < 1 || 2 * in->k > MRA_MAX_K) return fail(MRA_ERR_ARG, "mra_reconstruct: k=%d outside 1..%d", in->k, MRA_MAX_K / 2);
+  if (in->n >= (1LL << 31)) return fail(MRA_ERR_ARG, "mra_reconstruct: more than 2^31 boxes");
+  if (out->k != in->k || out->cap < 0 || (out->cap > 0 && (!out->keys || !out->coeffs)))
+    return fail(MRA_ERR_ARG, "mra_reconstruct: bad output view");
+  out->L = in->L;
+  if (in->n == 0) {
+    out->n = 0;
+    return MRA_OK;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int k = in->k, kk = 2 * k, k3 = k * k * k;
+  const int64_t n_in = in->n;
+  std::vector<void *> held;
+  struct Release {
+    std::vector<void *> &v;
+    cudaStream_t s;
+    ~Release() {
+      for (void *p : v) cudaFreeAsync(p, s);
+      cudaStreamSynchronize(s);
+    }
+  } release{held, s};
+  auto dalloc = [&](size_t bytes) -> void * {
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes ? bytes : 1, s) != cudaSuccess) return nullptr;
+    held.push_back(p);
+    return p;
+  };
+  auto drop = [&](void *p) {
+    auto it = std::find(held.begin(), held.end(), p);
+    if (it != held.end()) {
+      cudaFreeAsync(p, s);
+      held.erase(it);
+    }
+  };
+#define RC_ALLOC(var, type, count)                                                              \
+  type *var = (type *)dalloc((size_t)(count) * sizeof(type));                                   \
+  if (!var) return fail(MRA_ERR_CUDA, "mra_reconstruct: out of device memory (%s)", #var);
+
+  // order and the level ranges of the sorted input
+  std::vector<uint64_t> hk(n_in);
+  MRA_CUDA_TRY(cudaMemcpyAsync(hk.data(), in->keys, (size_t)n_in * 8, cudaMemcpyDeviceToHost, s));
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<int64_t> lo(21, n_in), hi(21, n_in);
+  for (int64_t i = 0; i < n_in; ++i) {
+    if (i > 0 && hk[i] <= hk[i - 1]) return fail(MRA_ERR_ARG, "mra_reconstruct: keys must be sorted and unique");
+    const int lv = key_level(hk[i]);
+    if (lv > 19) return fail(MRA_ERR_ARG, "mra_reconstruct: level %d above 19", lv);
+  }
+  for (int n = 0; n <= 20; ++n) {
+    lo[n] = std::lower_bound(hk.begin(), hk.end(), (uint64_t)n << 57) - hk.begin();
+    hi[n] = n < 20 ? std::lower_bound(hk.begin(), hk.end(), (uint64_t)(n + 1) << 57) - hk.begin() : n_in;
+  }
+  const int nmin = key_level(hk.front()), nmax = key_level(hk.back());
+  RC_ALLOC(Ub, double, kk * k);
+  std::vector<double> U(2 * k * k), Ubh(2 * k * k);
+  two_scale(k, U.data());
+  for (int c = 0; c < 2; ++c)
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) Ubh[(c * k + i) * k + j] = U[c * k * k + i * k + j];
+  MRA_CUDA_TRY(cudaMemcpyAsync(Ub, Ubh.data(), Ubh.size() * 8, cudaMemcpyHostToDevice, s));
+  RC_ALLOC(top, int, n_in);
+  top_level_kernel<<<(unsigned)((n_in + 255) / 256), 256, 0, s>>>(n_in, in->keys, top);
+  MRA_CUDA_TRY(cudaGetLastError());
+  RC_ALLOC(d_err, int, 1);
+  MRA_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+  RC_ALLOC(anc, uint64_t, n_in);
+  RC_ALLOC(anc_s, uint64_t, n_in);
+  RC_ALLOC(d_nsel, int64_t, 1);
+  size_t tb = 0, t2 = 0;
+  MRA_CUDA_TRY(cub::DeviceRadixSort::SortKeys(nullptr, tb, anc, anc_s, (int)n_in, 0, 64, s));
+  MRA_CUDA_TRY(cub::DeviceSelect::Unique(nullptr, t2, anc_s, anc, d_nsel, (int)n_in, s));
+  tb = std::max(tb, t2);
+  RC_ALLOC(tmp, unsigned char, tb);
+  const size_t sh_d = (size_t)(k3 + kk * k * k + kk * kk * k) * 8;
+  MRA_CUDA_TRY(cudaFuncSetAttribute(pass_down_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_d));
+  uint64_t *Ck = nullptr;  // boxes passed down to the current level (unsorted) and their values
+  double *Cv = nullptr;
+  int64_t nC = 0, nout = 0;
+  const int64_t cap = out->cap;
+  for (int n = nmin; n <= nmax; ++n) {
+    // interior boxes of level n
+    interior_kernel<<<(unsigned)((n_in + 255) / 256), 256, 0, s>>>(n_in, in->keys, top, n, anc);
+    MRA_CUDA_TRY(cudaGetLastError());
+    size_t tt = tb;
+    MRA_CUDA_TRY(cub::DeviceRadixSort::SortKeys(tmp, tt, anc, anc_s, (int)n_in, 0, 64, s));
+    RC_ALLOC(ik, uint64_t, n_in);
+    tt = tb;
+    MRA_CUDA_TRY(cub::DeviceSelect::Unique(tmp, tt, anc_s, ik, d_nsel, (int)n_in, s));
+    int64_t ni = 0;
+    MRA_CUDA_TRY(cudaMemcpyAsync(&ni, d_nsel, 8, cudaMemcpyDeviceToHost, s));
+    MRA_CUDA_TRY(cudaStreamSynchronize(s));
+    if (ni > 0) {
+      uint64_t last = 0;
+      MRA_CUDA_TRY(cudaMemcpyAsync(&last, ik + ni - 1, 8, cudaMemcpyDeviceToHost, s));
+      MRA_CUDA_TRY(cudaStreamSynchronize(s));
+      if (last == ~0ull) --ni;
+    }
+    // the level's boxes: passed down, then the tops of this level; in key order
+    const int64_t nl = hi[n] - lo[n];
+    RC_ALLOC(tflag, int, nl + 1);
+    RC_ALLOC(tpos, int, nl + 1);
+    int ntop = 0;
+    if (nl > 0) {
+      top_flags_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, s>>>(lo[n], hi[n], n, top, tflag);
+      MRA_CUDA_TRY(cudaGetLastError());
+    }
+    MRA_CUDA_TRY(cudaMemsetAsync(tflag + nl, 0, sizeof(int), s));
+    size_t ts = 0;
+    MRA_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, ts, tflag, tpos, (int)(nl + 1), s));
+    RC_ALLOC(tmp3, unsigned char, ts);
+    MRA_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp3, ts, tflag, tpos, (int)(nl + 1), s));
+    MRA_CUDA_TRY(cudaMemcpyAsync(&ntop, tpos + nl, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MRA_CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t nr = nC + ntop;
+    RC_ALLOC(uk, uint64_t, nr);
+    RC_ALLOC(uv, double, nr * k3);
+    if (nC > 0) {
+      MRA_CUDA_TRY(cudaMemcpyAsync(uk, Ck, (size_t)nC * 8, cudaMemcpyDeviceToDevice, s));
+      MRA_CUDA_TRY(cudaMemcpyAsync(uv, Cv, (size_t)nC * k3 * 8, cudaMemcpyDeviceToDevice, s));
+    }
+    if (ntop > 0) {
+      tops_kernel<<<(unsigned)nl, 128, 0, s>>>(lo[n], hi[n], n, top, in->keys, in->coeffs, k3, tpos, nC, uk, uv);
+      MRA_CUDA_TRY(cudaGetLastError());
+    }
+    RC_ALLOC(rk, uint64_t, nr);
+    RC_ALLOC(rv, double, nr * k3);
+    RC_ALLOC(idx, int, nr);
+    RC_ALLOC(idx_s, int, nr);
+    if (nr > 0) {
+      iota_ns_kernel<<<(unsigned)((nr + 255) / 256), 256, 0, s>>>(nr, idx);
+      MRA_CUDA_TRY(cudaGetLastError());
+      size_t tsp = 0;
+      MRA_CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tsp, uk, rk, idx, idx_s, (int)nr, 0, 64, s));
+      RC_ALLOC(tmp4, unsigned char, tsp);
+      MRA_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp4, tsp, uk, rk, idx, idx_s, (int)nr, 0, 64, s));
+      gather_rows_ns_kernel<<<(unsigned)nr, 128, 0, s>>>(nr, k3, idx_s, uv, rv);
+      MRA_CUDA_TRY(cudaGetLastError());
+      drop(tmp4);
+    }
+    if (nl > 0) {  // input boxes below a top add their coefficients
+      add_inputs_kernel<<<(unsigned)nl, 128, 0, s>>>(lo[n], hi[n], n, top, in->keys, in->coeffs, k3, rk, nr, rv, d_err);
+      MRA_CUDA_TRY(cudaGetLastError());
+    }
+    // leaves out, interior boxes passed down
+    RC_ALLOC(inner, int, nr + 1);
+    RC_ALLOC(leaf, int, nr + 1);
+    RC_ALLOC(ipos, int, nr + 1);
+    RC_ALLOC(lpos, int, nr + 1);
+    MRA_CUDA_TRY(cudaMemsetAsync(inner + nr, 0, sizeof(int), s));
+    MRA_CUDA_TRY(cudaMemsetAsync(leaf + nr, 0, sizeof(int), s));
+    if (nr > 0) {
+      classify_kernel<<<(unsigned)((nr + 255) / 256), 256, 0, s>>>(nr, rk, ik, ni, inner, leaf);
+      MRA_CUDA_TRY(cudaGetLastError());
+    }
+    size_t tsc = 0;
+    MRA_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tsc, inner, ipos, (int)(nr + 1), s));
+    RC_ALLOC(tmp5, unsigned char, tsc);
+    MRA_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp5, tsc, inner, ipos, (int)(nr + 1), s));
+    MRA_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp5, tsc, leaf, lpos, (int)(nr + 1), s));
+    int ninner = 0, herr = 0;
+    MRA_CUDA_TRY(cudaMemcpyAsync(&ninner, ipos + nr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MRA_CUDA_TRY(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MRA_CUDA_TRY(cudaStreamSynchronize(s));
+    if (herr) return fail(MRA_ERR_NUMERIC, "mra_reconstruct: an input box has no place in the result");
+    if (nr - ninner > 0) {
+      emit_leaves_kernel<<<(unsigned)nr, 128, 0, s>>>(nr, k3, rk, rv, leaf, lpos, nout, cap, out->keys, out->coeffs);
+      MRA_CUDA_TRY(cudaGetLastError());
+    }
+    nout += nr - ninner;
+    const int64_t nnext = 8 * (int64_t)ninner;
+    RC_ALLOC(nk, uint64_t, nnext);
+    RC_ALLOC(nv, double, nnext * k3);
+    if (ninner > 0) {
+      pass_down_kernel<<<(unsigned)nr, 256, sh_d, s>>>(k, nr, rk, rv, inner, ipos, Ub, nk, nv);
+      MRA_CUDA_TRY(cudaGetLastError());
+    }
+    for (void *p : {(void *)ik, (void *)tflag, (void *)tpos, (void *)tmp3, (void *)uk, (void *)uv, (void *)rk,
+                    (void *)rv, (void *)idx, (void *)idx_s, (void *)inner, (void *)leaf, (void *)ipos, (void *)lpos,
+                    (void *)tmp5})
+      drop(p);
+    if (Ck) drop(Ck);
+    if (Cv) drop(Cv);
+    Ck = nk;
+    Cv = nv;
+    nC = nnext;
+  }
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  if (nC != 0) return fail(MRA_ERR_NUMERIC, "mra_reconstruct: boxes passed below the deepest level");
+  if (nout > cap) {
+    out->n = nout;
+    return fail(MRA_ERR_CAPACITY, "mra_reconstruct: %lld leaves, capacity %lld", (long long)nout, (long long)cap);
+  }
+  out->n = nout;
+  return MRA_OK;
+#undef RC_ALLOC
 }

@@ -40,6 +40,7 @@ EXPORTED = [
     "mra_apply", "mra_apply_batched", "mra_norm", "mra_norm_noalloc", "mra_compare", "mra_log_terms", "mra_mlp_init",
     "mra_mlp_standardize", "mra_mlp_forward", "mra_mlp_workspace_size", "mra_mlp_grad", "mra_mlp_train",
     "mra_operator_ns_create", "mra_apply_ns_workspace_size", "mra_apply_ns", "mra_apply_ns_tree",
+    "mra_reconstruct",
 ]
 NOALLOC_MAX_BOXES = 1 << 20
 
@@ -126,6 +127,7 @@ def load(build_if_stale: bool = True):
         lib.mra_apply_ns.argtypes = [vp, vp, P(TreeView), i, P(ApplyOpts), P(TreeView), vp, ctypes.c_size_t,
                                      P(ApplyStats), vp]
         lib.mra_apply_ns_tree.argtypes = [vp, vp, P(TreeView), i, P(ApplyOpts), P(TreeView), P(ApplyStats), vp]
+        lib.mra_reconstruct.argtypes = [P(TreeView), P(TreeView), vp]
         lib.mra_norm.argtypes = [P(TreeView), vp, P(d), vp]
         lib.mra_norm_noalloc.argtypes = [P(TreeView), vp, P(d), vp]
         lib.mra_compare.argtypes = [P(TreeView), P(TreeView), P(CompareResult), vp]
@@ -519,3 +521,19 @@ def apply_ns_tree(op: Operator, ns_op: NSOperator, tree: "Tree", n0: int, opts: 
     ap = NSTreeApplier(op, ns_op, n0, opts, out_cap=8 * tree.n, device=tree.keys.device)
     out = ap(tree, stream)
     return out, ap.stats.as_dict()
+
+
+def reconstruct(tree: "Tree", out_cap: int = 0, stream=None) -> "Tree":
+    """mra_reconstruct: the boxes of `tree` (any levels, overlapping allowed) summed down to
+    disjoint leaves; the output grows on MRA_ERR_CAPACITY."""
+    lib = load()
+    out = Tree.empty(max(out_cap, 4 * tree.n, 1), tree.k, tree.L, tree.keys.device)
+    while True:
+        vin, vout = tree.view(), out.view()
+        rc = lib.mra_reconstruct(ctypes.byref(vin), ctypes.byref(vout), _stream(stream))
+        if rc == MRA_ERR_CAPACITY and vout.n > out.cap:
+            out = Tree.empty(int(vout.n), tree.k, tree.L, tree.keys.device)
+            continue
+        _check(rc)
+        out.n = int(vout.n)
+        return out

@@ -1,0 +1,54 @@
+"""mra_reconstruct (sum-down into disjoint leaves) through the C ABI against the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mra():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1507_01888_gb300 import mra as m
+    m.load()
+    return m
+
+
+@pytest.mark.parametrize("k", [3, 6, 8])
+def test_reconstruct_of_the_leaf_level_apply(mra, k):
+    L = 8.0
+    f = W.gaussian_sum(2, 1.0, 20.0, seed=11, centre_box=3.0)
+    keys, coeffs, _ = O.project(f, k, L, thresh=3e-3, init_level=2, max_level=4)
+    op = mra.Operator(0, 8, k, L, 2, 4, max_disp=1, fit_eps=1e-4)
+    multi, _ = mra.apply(op, mra.Tree.from_host(keys, coeffs, L), mra.make_opts(stencil=mra.STENCIL_NEAREST))
+    mk, mc = multi.host()
+    out = mra.reconstruct(multi, out_cap=1)  # also exercises the capacity retry
+    gk, gc = out.host()
+    rk, rc = O.reconstruct(mk, mc, k)
+    assert (gk == rk).all()
+    assert np.abs(gc - rc).max() <= 1e-13 * np.abs(rc).max()
+    pts = np.random.default_rng(3).uniform(-L, L, size=(300, 3))
+    a = O.evaluate(mk, mc, k, L, pts)
+    assert np.abs(O.evaluate(gk, gc, k, L, pts) - a).max() <= 1e-12 * np.abs(a).max()
+
+
+def test_reconstruct_edge_cases(mra):
+    k, L = 4, 8.0
+    empty = mra.reconstruct(mra.Tree.empty(1, k, L))
+    assert empty.n == 0
+    f = W.gaussian_sum(2, 1.0, 20.0, seed=11, centre_box=3.0)
+    keys, coeffs, _ = O.project(f, k, L, thresh=3e-3, init_level=2, max_level=4)
+    same = mra.reconstruct(mra.Tree.from_host(keys, coeffs, L))  # already disjoint: unchanged
+    sk, sc = same.host()
+    assert (sk == keys).all() and np.array_equal(sc, coeffs)
+    one = np.array([O.make_key(2, 1, 2, 3), O.make_key(3, 3, 4, 7)], dtype=np.uint64)
+    c1 = np.random.default_rng(5).standard_normal((2, k, k, k))
+    gk, gc = mra.reconstruct(mra.Tree.from_host(one, c1, L)).host()
+    rk, rc = O.reconstruct(one, c1, k)
+    assert (gk == rk).all() and np.abs(gc - rc).max() <= 1e-13 * np.abs(rc).max()
+    bad = np.array([O.make_key(3, 0, 0, 1), O.make_key(3, 0, 0, 0)], dtype=np.uint64)
+    with pytest.raises(mra.MraError):  # keys out of order
+        mra.reconstruct(mra.Tree.from_host(bad, c1, L))
