@@ -77,6 +77,7 @@ def _load():
         lib.orc_apply_ns.argtypes = [i, d, i, i, D, i, D, D, i, D, i]
         lib.orc_apply_ns_tree.argtypes = [i, d, l, U64, D, i, i, D, D, i, l, U64, D, L, i]
         lib.orc_reconstruct.argtypes = [i, l, U64, D, l, U64, D, L]
+        lib.orc_truncate.argtypes = [i, l, U64, D, d, l, U64, D, L, D]
         lib.orc_unfilter3.argtypes = [i, D, D]
         lib.orc_filter3.argtypes = [i, D, D]
         _lib = lib
@@ -363,3 +364,21 @@ def reconstruct(keys, coeffs, k: int):
         if rc != 0:
             raise RuntimeError(f"orc_reconstruct failed ({rc})")
         return ok[:n.value].copy(), oc[:n.value].copy()
+
+
+def truncate(keys, coeffs, k: int, thresh: float):
+    """Coarsen disjoint leaves: from the deepest level up, eight sibling leaves whose detail
+    ||S - Ubar^{x3} filter(S)||_F <= thresh become their parent.  Returns (keys, coefficients,
+    sum of the squared dropped details = the squared L2 error)."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    coeffs = np.ascontiguousarray(coeffs, dtype=np.float64).reshape(len(keys), k, k, k)
+    cap = max(1, len(keys))
+    ok = np.zeros(cap, dtype=np.uint64)
+    oc = np.zeros((cap, k, k, k))
+    n = ctypes.c_long(0)
+    e2 = ctypes.c_double(0.0)
+    rc = _load().orc_truncate(int(k), len(keys), _up(keys), _dp(coeffs), float(thresh), int(cap), _up(ok), _dp(oc),
+                              ctypes.byref(n), ctypes.byref(e2))
+    if rc != 0:
+        raise RuntimeError(f"orc_truncate failed ({rc})")
+    return ok[:n.value].copy(), oc[:n.value].copy(), e2.value

@@ -1567,3 +1567,156 @@ int orc_reconstruct(int k, long n_in, const uint64_t *keys, const double *coeffs
   *n_out = nout;
   return nout > cap ? -4 : 0;
 }
+
+/* Truncate (Sec. 2.1 refinement test run backwards): on disjoint leaves, from the deepest level
+ * up, eight sibling leaves whose detail d = S - Ubar^{x3} s (s = the parent's filter of their
+ * tensor S) has ||d||_F <= thresh are replaced by their parent holding s.  A merged parent can
+ * merge again one level up.  Since d is orthogonal to the parent's space, the L2 error is
+ * sqrt(sum ||d||^2) over the merges, returned in *err2 as sum ||d||^2. */
+int orc_truncate(int k, long n_in, const uint64_t *keys, const double *coeffs, double thresh, long cap,
+                 uint64_t *out_keys, double *out_coeffs, long *n_out, double *err2) {
+  if (k < 1 || 2 * k > ORC_MAXK || n_in < 0) return -1;
+  for (long i = 1; i < n_in; ++i)
+    if (keys[i] <= keys[i - 1]) return -1;
+  int k3 = k * k * k, kk = 2 * k, kk3 = kk * kk * kk;
+  double U0[ORC_MAXK * ORC_MAXK], U1[ORC_MAXK * ORC_MAXK];
+  orc_two_scale(k, U0, U1);
+  double Ub[2 * ORC_MAXK * ORC_MAXK];
+  for (int cc = 0; cc < 2; ++cc)
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) Ub[(cc * k + i) * k + j] = (cc == 0 ? U0 : U1)[i * k + j];
+  /* leaves by level */
+  orc_set lev[20];
+  memset(lev, 0, sizeof(lev));
+  for (long i = 0; i < n_in; ++i) {
+    int n = (int)(keys[i] >> 57);
+    if (n > 19) return -1;
+    lev[n].n++;
+  }
+  for (int n = 0; n < 20; ++n) {
+    lev[n].keys = (uint64_t *)malloc(sizeof(uint64_t) * (lev[n].n + 1) * 2);
+    lev[n].v = (double *)malloc(sizeof(double) * (lev[n].n + 1) * 2 * k3);
+    lev[n].n = 0;
+  }
+  /* room for merged parents: at most one per eight leaves of the level below */
+  long room[20];
+  for (int n = 0; n < 20; ++n) room[n] = 0;
+  for (long i = 0; i < n_in; ++i) {
+    int n = (int)(keys[i] >> 57);
+    orc_set *L = &lev[n];
+    L->keys[L->n] = keys[i];
+    memcpy(L->v + L->n * k3, coeffs + i * k3, sizeof(double) * k3);
+    L->n++;
+  }
+  for (int n = 0; n < 20; ++n) room[n] = lev[n].n;
+  /* grow the parent levels' arrays to hold merges coming from below */
+  for (int n = 18; n >= 0; --n) {
+    long extra = 0;
+    for (int m = n + 1; m < 20; ++m) extra += room[m] / 8 + 1;
+    lev[n].keys = (uint64_t *)realloc(lev[n].keys, sizeof(uint64_t) * (room[n] + extra + 1));
+    lev[n].v = (double *)realloc(lev[n].v, sizeof(double) * (room[n] + extra + 1) * k3);
+  }
+  double e2 = 0.0;
+  double *S = (double *)malloc(sizeof(double) * kk3), *B = (double *)malloc(sizeof(double) * kk3);
+  double *s = (double *)malloc(sizeof(double) * k3);
+  char *gone = NULL;
+  for (int n = 19; n >= 1; --n) {
+    orc_set *L = &lev[n];
+    if (L->n == 0) continue;
+    /* the level's leaves in key order (merges from below were appended) */
+    long *perm = (long *)malloc(sizeof(long) * L->n);
+    for (long i = 0; i < L->n; ++i) perm[i] = i;
+    for (long i = 1; i < L->n; ++i) {
+      long pi = perm[i], j = i - 1;
+      while (j >= 0 && L->keys[perm[j]] > L->keys[pi]) {
+        perm[j + 1] = perm[j];
+        --j;
+      }
+      perm[j + 1] = pi;
+    }
+    uint64_t *sk = (uint64_t *)malloc(sizeof(uint64_t) * L->n);
+    double *sv = (double *)malloc(sizeof(double) * L->n * k3);
+    for (long i = 0; i < L->n; ++i) {
+      sk[i] = L->keys[perm[i]];
+      memcpy(sv + i * k3, L->v + perm[i] * k3, sizeof(double) * k3);
+    }
+    free(perm);
+    memcpy(L->keys, sk, sizeof(uint64_t) * L->n);
+    memcpy(L->v, sv, sizeof(double) * L->n * k3);
+    free(sk);
+    free(sv);
+    gone = (char *)calloc(L->n, 1);
+    for (long i = 0; i < L->n; ++i) {
+      int lv;
+      long x, y, z;
+      split_key(L->keys[i], &lv, &x, &y, &z);
+      if ((x & 1) || (y & 1) || (z & 1)) continue; /* each parent once, from its first child */
+      long idx[8];
+      int all = 1;
+      for (int c = 0; c < 8 && all; ++c) {
+        idx[c] = find_key(L->keys, L->n, make_key(n, x + (c >> 2), y + ((c >> 1) & 1), z + (c & 1)));
+        if (idx[c] < 0) all = 0;
+      }
+      if (!all) continue;
+      for (int c = 0; c < 8; ++c) {
+        int cx = c >> 2, cy = (c >> 1) & 1, cz = c & 1;
+        const double *v = L->v + idx[c] * k3;
+        for (int a = 0; a < k; ++a)
+          for (int b = 0; b < k; ++b)
+            for (int d = 0; d < k; ++d) S[((cx * k + a) * kk + cy * k + b) * kk + cz * k + d] = v[(a * k + b) * k + d];
+      }
+      filter3(k, Ub, S, s);
+      unfilter3(k, Ub, s, B);
+      double dn = 0.0;
+      for (int q = 0; q < kk3; ++q) dn += (S[q] - B[q]) * (S[q] - B[q]);
+      if (sqrt(dn) > thresh) continue;
+      e2 += dn;
+      for (int c = 0; c < 8; ++c) gone[idx[c]] = 1;
+      orc_set *P = &lev[n - 1];
+      P->keys[P->n] = make_key(n - 1, x >> 1, y >> 1, z >> 1);
+      memcpy(P->v + P->n * k3, s, sizeof(double) * k3);
+      P->n++;
+    }
+    long w = 0;
+    for (long i = 0; i < L->n; ++i)
+      if (!gone[i]) {
+        L->keys[w] = L->keys[i];
+        memmove(L->v + w * k3, L->v + i * k3, sizeof(double) * k3);
+        ++w;
+      }
+    L->n = w;
+    free(gone);
+  }
+  /* level 0 may also have received merges: sort it too */
+  {
+    orc_set *L = &lev[0];
+    for (long i = 1; i < L->n; ++i)
+      for (long j = i; j > 0 && L->keys[j - 1] > L->keys[j]; --j) {
+        uint64_t tk = L->keys[j];
+        L->keys[j] = L->keys[j - 1];
+        L->keys[j - 1] = tk;
+        for (int q = 0; q < k3; ++q) {
+          double tv = L->v[j * k3 + q];
+          L->v[j * k3 + q] = L->v[(j - 1) * k3 + q];
+          L->v[(j - 1) * k3 + q] = tv;
+        }
+      }
+  }
+  long nout = 0;
+  for (int n = 0; n < 20; ++n)
+    for (long i = 0; i < lev[n].n; ++i, ++nout)
+      if (nout < cap) {
+        out_keys[nout] = lev[n].keys[i];
+        memcpy(out_coeffs + nout * k3, lev[n].v + i * k3, sizeof(double) * k3);
+      }
+  for (int n = 0; n < 20; ++n) {
+    free(lev[n].keys);
+    free(lev[n].v);
+  }
+  free(S);
+  free(B);
+  free(s);
+  *n_out = nout;
+  *err2 = e2;
+  return nout > cap ? -4 : 0;
+}

@@ -533,3 +533,38 @@ def test_reconstruct_of_a_box_and_one_child():
     pts = np.column_stack([rng.uniform(-4, 0, 200), rng.uniform(0, 4, 200), rng.uniform(4, 8, 200)])
     a = O.evaluate(keys, coeffs, k, L, pts)
     assert np.abs(O.evaluate(rk, rc, k, L, pts) - a).max() <= 1e-13 * np.abs(a).max()
+
+
+def test_truncate_removes_exactly_the_dropped_details():
+    """Truncation is an orthogonal projection: ||f||^2 - ||trunc f||^2 equals the sum of the
+    dropped details' squares, each of which is below the threshold; a second truncation with
+    the same threshold changes nothing."""
+    k, L = 4, 8.0
+    f = W.gaussian_sum(3, 1.0, 30.0, seed=17, centre_box=3.0)
+    keys, coeffs, _ = O.project(f, k, L, uniform_level=4)
+    for thresh in (1e-5, 1e-3):
+        tk, tc, e2 = O.truncate(keys, coeffs, k, thresh)
+        assert len(tk) < len(keys) and (tk[1:] > tk[:-1]).all()
+        n2, t2 = (coeffs ** 2).sum(), (tc ** 2).sum()
+        assert abs((n2 - t2) - e2) <= 1e-12 * n2
+        merges = (len(keys) - len(tk)) // 7
+        assert e2 <= merges * thresh ** 2 * (1 + 1e-12)
+        again = O.truncate(tk, tc, k, thresh)
+        assert (again[0] == tk).all() and again[2] == 0.0
+
+
+def test_truncate_folds_a_parent_polynomial_back():
+    """Eight children made from one parent by the two-scale relation carry no detail: they fold
+    back into the parent's coefficients."""
+    k = 3
+    rng = np.random.default_rng(8)
+    parent = rng.standard_normal((k, k, k))
+    S = O.unfilter3(k, parent)
+    keys = np.array(sorted(O.make_key(3, 2 + cx, 4 + cy, 6 + cz) for cx in (0, 1) for cy in (0, 1) for cz in (0, 1)),
+                    dtype=np.uint64)
+    coeffs = np.array([S[((int(key) >> 38) & 1) * k:((int(key) >> 38) & 1) * k + k,
+                         ((int(key) >> 19) & 1) * k:((int(key) >> 19) & 1) * k + k,
+                         (int(key) & 1) * k:(int(key) & 1) * k + k] for key in keys])
+    tk, tc, e2 = O.truncate(keys, coeffs, k, 1e-12)
+    assert list(tk) == [O.make_key(2, 1, 2, 3)]
+    assert np.abs(tc[0] - parent).max() < 1e-14 and e2 < 1e-28
