@@ -331,6 +331,15 @@ int mra_apply_ns_tree(const mra_operator *op, const mra_operator *ns_op, const m
  * stream-ordered; synchronises the stream. */
 int mra_reconstruct(const mra_tree_view *in, mra_tree_view *out, void *stream);
 
+/* Truncate (the refinement test of Sec. 2.1 run backwards): on disjoint leaves (keys sorted and
+ * unique), from the deepest level up, eight sibling leaves whose detail d = S - U^{x3} s
+ * (S their coefficients as one (2k)^3 tensor, s = its filter, the parent's coefficients) has
+ * ||d||_F <= thresh are replaced by the parent holding s; a parent made so can merge again.
+ * out: the remaining leaves, keys sorted (capacity as mra_reconstruct).  *err2 (host, may be
+ * NULL): sum of ||d||^2 over the merges = the squared L2 change (d is orthogonal to the
+ * parent's space).  Temporaries stream-ordered; synchronises the stream. */
+int mra_truncate(const mra_tree_view *in, double thresh, mra_tree_view *out, double *err2, void *stream);
+
 /* Per-box Frobenius norms (device array of tree->n doubles, may be NULL) and
  * the total L2 norm (host double, may be NULL).  Deterministic reduction. */
 int mra_norm(const mra_tree_view *tree, double *per_box, double *total, void *stream);

@@ -438,6 +438,109 @@ __global__ void pass_down_kernel(int k, int64_t nr, const uint64_t *rkeys, const
   }
 }
 
+// ---------------------------------------------------------------- truncate
+// One CTA per leaf of level n (sorted keys): a leaf with even (x, y, z) whose seven siblings
+// are leaves too forms S from the eight, s = (Ubar^T)^{x3} S and the detail
+// d = S - Ubar^{x3} s; if ||d||_F <= thresh the eight are marked gone, the parent (key, s) is
+// appended at an atomic slot of the level above and ||d||^2 is kept at the first child's slot.
+__global__ void truncate_level_kernel(int k, int n, int64_t nl, const uint64_t *keys, const double *v, double thresh,
+                                      const double *Ub, int *gone, double *d2, uint64_t *pkeys, double *pv,
+                                      int *pcount) {
+  extern __shared__ double sh[];
+  __shared__ int64_t idx[8];
+  __shared__ int all;
+  __shared__ double red[8];
+  const int64_t i = blockIdx.x;
+  if (i >= nl) return;
+  const uint64_t key = keys[i];
+  const int64_t x = key_x(key), y = key_y(key), z = key_z(key);
+  if ((x & 1) || (y & 1) || (z & 1)) return;
+  const int kk = 2 * k, k3 = k * k * k, kk3 = kk * kk * kk;
+  double *S = sh, *a = S + kk3, *b = a + k * kk * kk, *sv = b + k * k * kk, *c = sv + k3, *e = c + kk * k * k;
+  if (threadIdx.x == 0) all = 1;
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    const int cx = threadIdx.x >> 2, cy = (threadIdx.x >> 1) & 1, cz = threadIdx.x & 1;
+    idx[threadIdx.x] = find_sorted(keys, nl, make_key(n, x + cx, y + cy, z + cz));
+    if (idx[threadIdx.x] < 0) atomicExch(&all, 0);
+  }
+  __syncthreads();
+  if (!all) return;
+  for (int q = threadIdx.x; q < kk3; q += blockDim.x) {
+    const int I = q / (kk * kk), J = (q / kk) % kk, Lq = q % kk;
+    const int64_t src = idx[((I / k) << 2) | ((J / k) << 1) | (Lq / k)];
+    S[q] = v[src * k3 + ((I % k) * k + J % k) * k + Lq % k];
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < k * kk * kk; q += blockDim.x) {  // filter
+    const int ii = q / (kk * kk), r = q % (kk * kk);
+    double t = 0.0;
+    for (int I = 0; I < kk; ++I) t += Ub[I * k + ii] * S[I * kk * kk + r];
+    a[q] = t;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < k * k * kk; q += blockDim.x) {
+    const int ii = q / (k * kk), j = (q / kk) % k, Lq = q % kk;
+    double t = 0.0;
+    for (int J = 0; J < kk; ++J) t += Ub[J * k + j] * a[(ii * kk + J) * kk + Lq];
+    b[q] = t;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < k3; q += blockDim.x) {
+    const int r = q / k, l = q % k;
+    double t = 0.0;
+    for (int Lq = 0; Lq < kk; ++Lq) t += Ub[Lq * k + l] * b[r * kk + Lq];
+    sv[q] = t;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < kk * k * k; q += blockDim.x) {  // unfilter of s
+    const int I = q / (k * k), r = q % (k * k);
+    double t = 0.0;
+    for (int ii = 0; ii < k; ++ii) t += Ub[I * k + ii] * sv[ii * k * k + r];
+    c[q] = t;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < kk * kk * k; q += blockDim.x) {
+    const int I = q / (kk * k), J = (q / k) % kk, l = q % k;
+    double t = 0.0;
+    for (int j = 0; j < k; ++j) t += Ub[J * k + j] * c[(I * k + j) * k + l];
+    e[q] = t;
+  }
+  __syncthreads();
+  double part = 0.0;
+  for (int q = threadIdx.x; q < kk3; q += blockDim.x) {
+    const int I = q / (kk * kk), J = (q / kk) % kk, Lq = q % kk;
+    double t = 0.0;
+    for (int l = 0; l < k; ++l) t += Ub[Lq * k + l] * e[(I * kk + J) * k + l];
+    const double dd = S[q] - t;
+    part += dd * dd;
+  }
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  __shared__ int slot;
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    const bool merge = sqrt(tot) <= thresh;
+    slot = -1;
+    if (merge) {
+      for (int cc = 0; cc < 8; ++cc) gone[idx[cc]] = 1;
+      d2[i] = tot;
+      slot = atomicAdd(pcount, 1);
+      pkeys[slot] = make_key(n - 1, x >> 1, y >> 1, z >> 1);
+    }
+  }
+  __syncthreads();
+  if (slot >= 0)
+    for (int q = threadIdx.x; q < k3; q += blockDim.x) pv[(int64_t)slot * k3 + q] = sv[q];
+}
+
+__global__ void keep_flags_kernel(int64_t n, const int *gone, int *keep) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) keep[i] = gone[i] ? 0 : 1;
+}
+
 inline size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
 inline int64_t boxes(int n) { return 1LL << (3 * n); }
 
@@ -1225,4 +1328,165 @@ extern "C" int mra_reconstruct(const mra_tree_view *in, mra_tree_view *out, void
   out->n = nout;
   return MRA_OK;
 #undef RC_ALLOC
+}
+
+
+// ---------------------------------------------------------------- truncate (host)
+extern "C" int mra_truncate(const mra_tree_view *in, double thresh, mra_tree_view *out, double *err2, void *stream) {
+  if (!in || !out) return fail(MRA_ERR_ARG, "mra_truncate: NULL argument");
+  if (in->n < 0 || (in->n > 0 && (!in->keys || !in->coeffs))) return fail(MRA_ERR_ARG, "mra_truncate: bad input");
+  if (in->k < 1 || 2 * in->k > MRA_MAX_K) return fail(MRA_ERR_ARG, "mra_truncate: k=%d outside 1..%d", in->k, MRA_MAX_K / 2);
+  if (in->n >= (1LL << 31)) return fail(MRA_ERR_ARG, "mra_truncate: more than 2^31 leaves");
+  if (!(thresh >= 0.0)) return fail(MRA_ERR_ARG, "mra_truncate: thresh must be >= 0");
+  if (out->k != in->k || out->cap < 0 || (out->cap > 0 && (!out->keys || !out->coeffs)))
+    return fail(MRA_ERR_ARG, "mra_truncate: bad output view");
+  out->L = in->L;
+  if (err2) *err2 = 0.0;
+  if (in->n == 0) {
+    out->n = 0;
+    return MRA_OK;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int k = in->k, kk = 2 * k, k3 = k * k * k;
+  const int64_t n_in = in->n;
+  std::vector<void *> held;
+  struct Release {
+    std::vector<void *> &v;
+    cudaStream_t s;
+    ~Release() {
+      for (void *p : v) cudaFreeAsync(p, s);
+      cudaStreamSynchronize(s);
+    }
+  } release{held, s};
+  auto dalloc = [&](size_t bytes) -> void * {
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes ? bytes : 1, s) != cudaSuccess) return nullptr;
+    held.push_back(p);
+    return p;
+  };
+#define TR_ALLOC(var, type, count)                                                              \
+  type *var = (type *)dalloc((size_t)(count) * sizeof(type));                                   \
+  if (!var) return fail(MRA_ERR_CUDA, "mra_truncate: out of device memory (%s)", #var);
+
+  std::vector<uint64_t> hk(n_in);
+  MRA_CUDA_TRY(cudaMemcpyAsync(hk.data(), in->keys, (size_t)n_in * 8, cudaMemcpyDeviceToHost, s));
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int64_t i = 1; i < n_in; ++i)
+    if (hk[i] <= hk[i - 1]) return fail(MRA_ERR_ARG, "mra_truncate: keys must be sorted and unique");
+  if (key_level(hk.back()) > 19) return fail(MRA_ERR_ARG, "mra_truncate: level above 19");
+  std::vector<int64_t> lo(21), hi(21);
+  for (int n = 0; n <= 20; ++n) {
+    lo[n] = std::lower_bound(hk.begin(), hk.end(), (uint64_t)n << 57) - hk.begin();
+    hi[n] = n < 20 ? std::lower_bound(hk.begin(), hk.end(), (uint64_t)(n + 1) << 57) - hk.begin() : n_in;
+  }
+  TR_ALLOC(Ub, double, kk * k);
+  std::vector<double> U(2 * k * k), Ubh(2 * k * k);
+  two_scale(k, U.data());
+  for (int c = 0; c < 2; ++c)
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) Ubh[(c * k + i) * k + j] = U[c * k * k + i * k + j];
+  MRA_CUDA_TRY(cudaMemcpyAsync(Ub, Ubh.data(), Ubh.size() * 8, cudaMemcpyHostToDevice, s));
+  const size_t sh = (size_t)(kk * kk * kk + k * kk * kk + k * k * kk + k3 + kk * k * k + kk * kk * k) * 8;
+  MRA_CUDA_TRY(cudaFuncSetAttribute(truncate_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+  TR_ALLOC(pcount, int, 1);
+  // the surviving leaves of each level (device arrays) and the merged parents carried up
+  std::vector<uint64_t *> keep_k(20, nullptr);
+  std::vector<double *> keep_v(20, nullptr);
+  std::vector<int64_t> keep_n(20, 0);
+  uint64_t *mk = nullptr;  // parents merged from the level below (unsorted)
+  double *mv = nullptr;
+  int64_t nm = 0;
+  double e2 = 0.0;
+  const int top = key_level(hk.back());
+  for (int n = top; n >= 0; --n) {
+    // this level's leaves: the input's, then the merged parents, in key order
+    const int64_t ni = hi[n] - lo[n], nl = ni + nm;
+    if (nl == 0) continue;
+    TR_ALLOC(uk, uint64_t, nl);
+    TR_ALLOC(uv, double, nl * k3);
+    if (ni > 0) {
+      MRA_CUDA_TRY(cudaMemcpyAsync(uk, in->keys + lo[n], (size_t)ni * 8, cudaMemcpyDeviceToDevice, s));
+      MRA_CUDA_TRY(cudaMemcpyAsync(uv, in->coeffs + lo[n] * k3, (size_t)ni * k3 * 8, cudaMemcpyDeviceToDevice, s));
+    }
+    if (nm > 0) {
+      MRA_CUDA_TRY(cudaMemcpyAsync(uk + ni, mk, (size_t)nm * 8, cudaMemcpyDeviceToDevice, s));
+      MRA_CUDA_TRY(cudaMemcpyAsync(uv + ni * k3, mv, (size_t)nm * k3 * 8, cudaMemcpyDeviceToDevice, s));
+    }
+    TR_ALLOC(lk, uint64_t, nl);
+    TR_ALLOC(lv, double, nl * k3);
+    TR_ALLOC(idx, int, nl);
+    TR_ALLOC(idx_s, int, nl);
+    iota_ns_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, s>>>(nl, idx);
+    MRA_CUDA_TRY(cudaGetLastError());
+    size_t tsp = 0;
+    MRA_CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tsp, uk, lk, idx, idx_s, (int)nl, 0, 64, s));
+    TR_ALLOC(tmp, unsigned char, tsp);
+    MRA_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, tsp, uk, lk, idx, idx_s, (int)nl, 0, 64, s));
+    gather_rows_ns_kernel<<<(unsigned)nl, 128, 0, s>>>(nl, k3, idx_s, uv, lv);
+    MRA_CUDA_TRY(cudaGetLastError());
+    // merges into level n-1
+    TR_ALLOC(gone, int, nl + 1);
+    TR_ALLOC(d2, double, nl);
+    MRA_CUDA_TRY(cudaMemsetAsync(gone, 0, (size_t)(nl + 1) * sizeof(int), s));
+    MRA_CUDA_TRY(cudaMemsetAsync(d2, 0, (size_t)nl * 8, s));
+    MRA_CUDA_TRY(cudaMemsetAsync(pcount, 0, sizeof(int), s));
+    TR_ALLOC(pk, uint64_t, nl / 8 + 1);
+    TR_ALLOC(pv, double, (nl / 8 + 1) * k3);
+    if (n > 0) {
+      truncate_level_kernel<<<(unsigned)nl, 256, sh, s>>>(k, n, nl, lk, lv, thresh, Ub, gone, d2, pk, pv, pcount);
+      MRA_CUDA_TRY(cudaGetLastError());
+    }
+    // survivors, compacted in key order
+    TR_ALLOC(keep, int, nl + 1);
+    TR_ALLOC(kpos, int, nl + 1);
+    keep_flags_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, s>>>(nl, gone, keep);
+    MRA_CUDA_TRY(cudaGetLastError());
+    MRA_CUDA_TRY(cudaMemsetAsync(keep + nl, 0, sizeof(int), s));
+    size_t tsc = 0;
+    MRA_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tsc, keep, kpos, (int)(nl + 1), s));
+    size_t tsr = 0;
+    double *dsum = nullptr;
+    MRA_CUDA_TRY(cub::DeviceReduce::Sum(nullptr, tsr, d2, dsum, (int)nl, s));
+    TR_ALLOC(tmp2, unsigned char, std::max(tsc, tsr));
+    TR_ALLOC(dsum_d, double, 1);
+    MRA_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp2, tsc, keep, kpos, (int)(nl + 1), s));
+    MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp2, tsr, d2, dsum_d, (int)nl, s));
+    int nkeep = 0, np = 0;
+    double dsum_h = 0.0;
+    MRA_CUDA_TRY(cudaMemcpyAsync(&nkeep, kpos + nl, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MRA_CUDA_TRY(cudaMemcpyAsync(&np, pcount, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MRA_CUDA_TRY(cudaMemcpyAsync(&dsum_h, dsum_d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MRA_CUDA_TRY(cudaStreamSynchronize(s));
+    e2 += dsum_h;
+    TR_ALLOC(kk_, uint64_t, nkeep);
+    TR_ALLOC(kv, double, (int64_t)nkeep * k3);
+    if (nkeep > 0) {
+      emit_leaves_kernel<<<(unsigned)nl, 128, 0, s>>>(nl, k3, lk, lv, keep, kpos, 0, nkeep, kk_, kv);
+      MRA_CUDA_TRY(cudaGetLastError());
+    }
+    keep_k[n] = kk_;
+    keep_v[n] = kv;
+    keep_n[n] = nkeep;
+    mk = pk;
+    mv = pv;
+    nm = np;
+  }
+  int64_t nout = 0;
+  for (int n = 0; n < 20; ++n) nout += keep_n[n];
+  if (nout > out->cap) {
+    out->n = nout;
+    return fail(MRA_ERR_CAPACITY, "mra_truncate: %lld leaves, capacity %lld", (long long)nout, (long long)out->cap);
+  }
+  int64_t o = 0;
+  for (int n = 0; n < 20; ++n) {
+    if (keep_n[n] == 0) continue;
+    MRA_CUDA_TRY(cudaMemcpyAsync(out->keys + o, keep_k[n], (size_t)keep_n[n] * 8, cudaMemcpyDeviceToDevice, s));
+    MRA_CUDA_TRY(cudaMemcpyAsync(out->coeffs + o * k3, keep_v[n], (size_t)keep_n[n] * k3 * 8, cudaMemcpyDeviceToDevice, s));
+    o += keep_n[n];
+  }
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  out->n = nout;
+  if (err2) *err2 = e2;
+  return MRA_OK;
+#undef TR_ALLOC
 }

@@ -40,7 +40,7 @@ EXPORTED = [
     "mra_apply", "mra_apply_batched", "mra_norm", "mra_norm_noalloc", "mra_compare", "mra_log_terms", "mra_mlp_init",
     "mra_mlp_standardize", "mra_mlp_forward", "mra_mlp_workspace_size", "mra_mlp_grad", "mra_mlp_train",
     "mra_operator_ns_create", "mra_apply_ns_workspace_size", "mra_apply_ns", "mra_apply_ns_tree",
-    "mra_reconstruct",
+    "mra_reconstruct", "mra_truncate",
 ]
 NOALLOC_MAX_BOXES = 1 << 20
 
@@ -128,6 +128,7 @@ def load(build_if_stale: bool = True):
                                      P(ApplyStats), vp]
         lib.mra_apply_ns_tree.argtypes = [vp, vp, P(TreeView), i, P(ApplyOpts), P(TreeView), P(ApplyStats), vp]
         lib.mra_reconstruct.argtypes = [P(TreeView), P(TreeView), vp]
+        lib.mra_truncate.argtypes = [P(TreeView), d, P(TreeView), P(d), vp]
         lib.mra_norm.argtypes = [P(TreeView), vp, P(d), vp]
         lib.mra_norm_noalloc.argtypes = [P(TreeView), vp, P(d), vp]
         lib.mra_compare.argtypes = [P(TreeView), P(TreeView), P(CompareResult), vp]
@@ -537,3 +538,19 @@ def reconstruct(tree: "Tree", out_cap: int = 0, stream=None) -> "Tree":
         _check(rc)
         out.n = int(vout.n)
         return out
+
+
+def truncate(tree: "Tree", thresh: float, out_cap: int = 0, stream=None):
+    """mra_truncate: returns (coarsened leaves, squared L2 change)."""
+    lib = load()
+    out = Tree.empty(max(out_cap, tree.n, 1), tree.k, tree.L, tree.keys.device)
+    e2 = ctypes.c_double()
+    while True:
+        vin, vout = tree.view(), out.view()
+        rc = lib.mra_truncate(ctypes.byref(vin), float(thresh), ctypes.byref(vout), ctypes.byref(e2), _stream(stream))
+        if rc == MRA_ERR_CAPACITY and vout.n > out.cap:
+            out = Tree.empty(int(vout.n), tree.k, tree.L, tree.keys.device)
+            continue
+        _check(rc)
+        out.n = int(vout.n)
+        return out, e2.value

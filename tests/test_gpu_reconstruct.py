@@ -52,3 +52,32 @@ def test_reconstruct_edge_cases(mra):
     bad = np.array([O.make_key(3, 0, 0, 1), O.make_key(3, 0, 0, 0)], dtype=np.uint64)
     with pytest.raises(mra.MraError):  # keys out of order
         mra.reconstruct(mra.Tree.from_host(bad, c1, L))
+
+
+@pytest.mark.parametrize("k,thresh", [(4, 1e-5), (4, 1e-3), (6, 1e-4), (8, 1e-4)])
+def test_truncate_matches_oracle(mra, k, thresh):
+    L = 8.0
+    f = W.gaussian_sum(3, 1.0, 30.0, seed=17, centre_box=3.0)
+    keys, coeffs, _ = O.project(f, k, L, uniform_level=4 if k <= 4 else 3)
+    out, e2 = mra.truncate(mra.Tree.from_host(keys, coeffs, L), thresh, out_cap=1)
+    gk, gc = out.host()
+    rk, rc, re2 = O.truncate(keys, coeffs, k, thresh)
+    assert (gk == rk).all()
+    assert np.abs(gc - rc).max() <= 1e-13 * np.abs(coeffs).max()
+    assert abs(e2 - re2) <= 1e-10 * max(re2, 1e-300)
+
+
+def test_reconstruct_then_truncate_keeps_the_error_bound(mra):
+    """The leaf-level apply's result, summed down and truncated: the function changes by
+    exactly sqrt(err2) in L2 (orthogonal projection)."""
+    k, L = 6, 8.0
+    f = W.gaussian_sum(2, 1.0, 20.0, seed=11, centre_box=3.0)
+    keys, coeffs, _ = O.project(f, k, L, thresh=1e-4, init_level=2, max_level=5)
+    op = mra.Operator(0, 12, k, L, 2, 5, max_disp=1, fit_eps=1e-4)
+    multi, _ = mra.apply(op, mra.Tree.from_host(keys, coeffs, L), mra.make_opts(stencil=mra.STENCIL_NEAREST))
+    leaves = mra.reconstruct(multi)
+    tr, e2 = mra.truncate(leaves, 1e-6)
+    assert tr.n < leaves.n
+    _, n_full = mra.norm(leaves)
+    _, n_tr = mra.norm(tr)
+    assert abs((n_full ** 2 - n_tr ** 2) - e2) <= 1e-10 * n_full ** 2
