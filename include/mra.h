@@ -340,6 +340,19 @@ int mra_reconstruct(const mra_tree_view *in, mra_tree_view *out, void *stream);
  * parent's space).  Temporaries stream-ordered; synchronises the stream. */
 int mra_truncate(const mra_tree_view *in, double thresh, mra_tree_view *out, double *err2, void *stream);
 
+/* Product of two functions held on trees of disjoint leaves (keys sorted and unique; same k
+ * and L).  Both are first summed down to their common refinement (each tree's leaves plus zero
+ * boxes at the other's keys, through mra_reconstruct); then, per leaf, the values at the k
+ * Gauss-Legendre points of each dimension (the third representation of Sec. 2.1) are
+ * multiplied and transformed back: s_ab = h^{-3/2} (V^T W)^{x3} [(V^{x3} s_a)(V^{x3} s_b)],
+ * V[q][i] = phi_i(x_q), W = diag(w_q) -- the product interpolated at the points.  out: the
+ * common leaves (capacity as mra_reconstruct).  k <= MRA_MAX_K / 2.  Synchronises. */
+int mra_multiply(const mra_tree_view *a, const mra_tree_view *b, mra_tree_view *out, void *stream);
+
+/* Inner product <a, b> = integral of a b, the coefficient dot product over the two trees'
+ * common leaves (orthonormal basis); deterministic reduction, *result on the host. */
+int mra_inner(const mra_tree_view *a, const mra_tree_view *b, double *result, void *stream);
+
 /* Per-box Frobenius norms (device array of tree->n doubles, may be NULL) and
  * the total L2 norm (host double, may be NULL).  Deterministic reduction. */
 int mra_norm(const mra_tree_view *tree, double *per_box, double *total, void *stream);

@@ -382,3 +382,41 @@ def truncate(keys, coeffs, k: int, thresh: float):
     if rc != 0:
         raise RuntimeError(f"orc_truncate failed ({rc})")
     return ok[:n.value].copy(), oc[:n.value].copy(), e2.value
+
+
+def _align(ka, ca, kb, cb, k):
+    """Both functions on their common leaves: each tree plus zero boxes at the other's keys,
+    summed down (reconstruct)."""
+    ka = np.asarray(ka, dtype=np.uint64)
+    kb = np.asarray(kb, dtype=np.uint64)
+    u = np.union1d(ka, kb)
+    ea = np.zeros((len(u), k, k, k))
+    eb = np.zeros((len(u), k, k, k))
+    ea[np.searchsorted(u, ka)] = ca
+    eb[np.searchsorted(u, kb)] = cb
+    ra, va = reconstruct(u, ea, k)
+    rb, vb = reconstruct(u, eb, k)
+    assert (ra == rb).all()
+    return ra, va, vb
+
+
+def multiply(ka, ca, kb, cb, k: int, L: float):
+    """Product in the values representation (Sec. 2.1): per common leaf, the values of both
+    functions at the k Gauss-Legendre points per dimension multiplied and transformed back."""
+    keys, va, vb = _align(ka, ca, kb, cb, k)
+    x, w = gauss_legendre(k)
+    xq, wq = 0.5 * (x + 1.0), 0.5 * w
+    V = np.array([phi(k, t) for t in xq])  # V[q][i]
+    lev = (keys >> np.uint64(57)).astype(np.int64)
+    h = 2.0 * L / np.left_shift(1, lev).astype(np.float64)
+    fa = np.einsum("pi,qj,rl,nijl->npqr", V, V, V, va)
+    fb = np.einsum("pi,qj,rl,nijl->npqr", V, V, V, vb)
+    VtW = (V * wq[:, None]).T  # [i][q]
+    out = np.einsum("ip,jq,lr,npqr->nijl", VtW, VtW, VtW, fa * fb) * (h ** -1.5)[:, None, None, None]
+    return keys, out
+
+
+def inner(ka, ca, kb, cb, k: int) -> float:
+    """<a, b>: coefficient dot product on the common leaves (orthonormal basis)."""
+    _, va, vb = _align(ka, ca, kb, cb, k)
+    return float((va * vb).sum())

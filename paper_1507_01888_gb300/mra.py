@@ -40,7 +40,7 @@ EXPORTED = [
     "mra_apply", "mra_apply_batched", "mra_norm", "mra_norm_noalloc", "mra_compare", "mra_log_terms", "mra_mlp_init",
     "mra_mlp_standardize", "mra_mlp_forward", "mra_mlp_workspace_size", "mra_mlp_grad", "mra_mlp_train",
     "mra_operator_ns_create", "mra_apply_ns_workspace_size", "mra_apply_ns", "mra_apply_ns_tree",
-    "mra_reconstruct", "mra_truncate",
+    "mra_reconstruct", "mra_truncate", "mra_multiply", "mra_inner",
 ]
 NOALLOC_MAX_BOXES = 1 << 20
 
@@ -129,6 +129,8 @@ def load(build_if_stale: bool = True):
         lib.mra_apply_ns_tree.argtypes = [vp, vp, P(TreeView), i, P(ApplyOpts), P(TreeView), P(ApplyStats), vp]
         lib.mra_reconstruct.argtypes = [P(TreeView), P(TreeView), vp]
         lib.mra_truncate.argtypes = [P(TreeView), d, P(TreeView), P(d), vp]
+        lib.mra_multiply.argtypes = [P(TreeView), P(TreeView), P(TreeView), vp]
+        lib.mra_inner.argtypes = [P(TreeView), P(TreeView), P(d), vp]
         lib.mra_norm.argtypes = [P(TreeView), vp, P(d), vp]
         lib.mra_norm_noalloc.argtypes = [P(TreeView), vp, P(d), vp]
         lib.mra_compare.argtypes = [P(TreeView), P(TreeView), P(CompareResult), vp]
@@ -554,3 +556,26 @@ def truncate(tree: "Tree", thresh: float, out_cap: int = 0, stream=None):
         _check(rc)
         out.n = int(vout.n)
         return out, e2.value
+
+
+def multiply(a: "Tree", b: "Tree", stream=None) -> "Tree":
+    """mra_multiply: the product on the two trees' common leaves."""
+    lib = load()
+    out = Tree.empty(max(a.n + b.n, 1), a.k, a.L, a.keys.device)
+    while True:
+        va, vb, vo = a.view(), b.view(), out.view()
+        rc = lib.mra_multiply(ctypes.byref(va), ctypes.byref(vb), ctypes.byref(vo), _stream(stream))
+        if rc == MRA_ERR_CAPACITY and vo.n > out.cap:
+            out = Tree.empty(int(vo.n), a.k, a.L, a.keys.device)
+            continue
+        _check(rc)
+        out.n = int(vo.n)
+        return out
+
+
+def inner(a: "Tree", b: "Tree", stream=None) -> float:
+    """mra_inner: <a, b>."""
+    r = ctypes.c_double()
+    va, vb = a.view(), b.view()
+    _check(load().mra_inner(ctypes.byref(va), ctypes.byref(vb), ctypes.byref(r), _stream(stream)))
+    return r.value

@@ -568,3 +568,54 @@ def test_truncate_folds_a_parent_polynomial_back():
     tk, tc, e2 = O.truncate(keys, coeffs, k, 1e-12)
     assert list(tk) == [O.make_key(2, 1, 2, 3)]
     assert np.abs(tc[0] - parent).max() < 1e-14 and e2 < 1e-28
+
+
+# ----------------------------------------------------------------- products and inner products
+
+def _poly_tree(k, L, keys, coef_fn):
+    """Coefficients of the polynomial p(x) = coef_fn(x, y, z) (degree < k per dimension) on the
+    given boxes, by projecting its values at the points with the oracle's own quadrature."""
+    x, w = O.gauss_legendre(k)
+    xq, wq = 0.5 * (x + 1.0), 0.5 * w
+    V = np.array([O.phi(k, t) for t in xq])
+    out = []
+    for key in keys:
+        n = int(key) >> 57
+        h = 2 * L / (1 << n)
+        bx, by, bz = (int(key) >> 38) & 0x7FFFF, (int(key) >> 19) & 0x7FFFF, int(key) & 0x7FFFF
+        X = -L + (bx + xq) * h
+        Y = -L + (by + xq) * h
+        Z = -L + (bz + xq) * h
+        vals = coef_fn(X[:, None, None], Y[None, :, None], Z[None, None, :])
+        s = np.einsum("p,q,r,pi,qj,rl,pqr->ijl", wq, wq, wq, V, V, V, vals) * h ** 1.5
+        out.append(s)
+    return np.array(out)
+
+
+def test_multiply_is_exact_for_low_degree_products():
+    """A product of degree < k per dimension is representable: the values-representation product
+    reproduces a(x) b(x) at random points, across two trees of different refinement."""
+    k, L = 4, 8.0
+    ka = np.array(sorted(O.make_key(1, x, y, z) for x in (0, 1) for y in (0, 1) for z in (0, 1)), dtype=np.uint64)
+    kb_list = [O.make_key(1, x, y, z) for x in (0, 1) for y in (0, 1) for z in (0, 1) if (x, y, z) != (1, 1, 1)]
+    kb_list += [O.make_key(2, 2 + x, 2 + y, 2 + z) for x in (0, 1) for y in (0, 1) for z in (0, 1)]
+    kb = np.array(sorted(kb_list), dtype=np.uint64)
+    fa = lambda x, y, z: 1.0 + 0.3 * x - 0.2 * y * z + 0.1 * x * y
+    fb = lambda x, y, z: 0.5 - 0.1 * z + 0.05 * x * x
+    ca, cb = _poly_tree(k, L, ka, fa), _poly_tree(k, L, kb, fb)
+    pk, pc = O.multiply(ka, ca, kb, cb, k, L)
+    pts = np.random.default_rng(0).uniform(-L, L, size=(200, 3))
+    want = fa(pts[:, 0], pts[:, 1], pts[:, 2]) * fb(pts[:, 0], pts[:, 1], pts[:, 2])
+    got = O.evaluate(pk, pc, k, L, pts)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_inner_with_one_is_the_charge():
+    """<f, 1> = integral of f: a unit-charge Gaussian against the constant 1 (one box per
+    level-1 octant) gives 1."""
+    k, L = 6, 8.0
+    f = W.gaussian_sum(1, 2.0, 2.0, seed=3, centre_box=2.0)
+    fk, fc, _ = O.project(f, k, L, thresh=1e-7, init_level=2, max_level=8)
+    ones_k = np.array(sorted(O.make_key(1, x, y, z) for x in (0, 1) for y in (0, 1) for z in (0, 1)), dtype=np.uint64)
+    ones_c = _poly_tree(k, L, ones_k, lambda x, y, z: np.ones_like(x * y * z))
+    assert O.inner(fk, fc, ones_k, ones_c, k) == pytest.approx(1.0, abs=1e-9)
