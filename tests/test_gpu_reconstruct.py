@@ -81,3 +81,23 @@ def test_reconstruct_then_truncate_keeps_the_error_bound(mra):
     _, n_full = mra.norm(leaves)
     _, n_tr = mra.norm(tr)
     assert abs((n_full ** 2 - n_tr ** 2) - e2) <= 1e-10 * n_full ** 2
+
+
+# ----------------------------------------------------------------- products and inner products
+
+@pytest.mark.parametrize("k", [4, 6, 8])
+def test_multiply_and_inner_match_oracle(mra, k):
+    L = 8.0
+    fa = W.gaussian_sum(2, 1.0, 20.0, seed=11, centre_box=3.0)
+    fb = W.gaussian_sum(3, 0.5, 5.0, seed=12, centre_box=3.0)
+    ka, ca, _ = O.project(fa, k, L, thresh=1e-3, init_level=2, max_level=5)
+    kb, cb, _ = O.project(fb, k, L, thresh=1e-4, init_level=2, max_level=5)
+    ta, tb = mra.Tree.from_host(ka, ca, L), mra.Tree.from_host(kb, cb, L)
+    prod = mra.multiply(ta, tb)
+    pk, pc = prod.host()
+    rk, rc = O.multiply(ka, ca, kb, cb, k, L)
+    assert (pk == rk).all()
+    assert np.abs(pc - rc).max() <= 1e-12 * np.abs(rc).max()
+    ip = mra.inner(ta, tb)
+    assert ip == pytest.approx(O.inner(ka, ca, kb, cb, k), rel=1e-12)
+    assert mra.inner(ta, ta) == pytest.approx(float((ca ** 2).sum()), rel=1e-12)
