@@ -247,16 +247,31 @@ __global__ void compress_tree_kernel(int k, int n, const uint64_t *ikeys, int64_
   }
 }
 
-// Every node p of R_n: is it reached by the level's applies (Y or Z output row), and which.
-__global__ void reach_kernel(int64_t nr, const uint64_t *rkeys, const uint64_t *ykeys, int64_t ny,
-                             const uint64_t *zkeys, int64_t nz, int64_t *yi, int64_t *zi, int *refine, int *leaf) {
+// The halo of the level's sources: every in-cell box within |l|_inf <= D of one (others: the
+// largest key, dropped later).
+__global__ void halo_kernel(int64_t ni, const uint64_t *ikeys, int D, uint64_t *out) {
+  const int w = 2 * D + 1, w3 = w * w * w;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ni * w3) return;
+  const uint64_t k = ikeys[e / w3];
+  const int l = (int)(e % w3), lx = l / (w * w) - D, ly = (l / w) % w - D, lz = l % w - D;
+  const int n = key_level(k);
+  const int64_t nb = 1LL << n, x = key_x(k) + lx, y = key_y(k) + ly, z = key_z(k) + lz;
+  out[e] = (x < 0 || x >= nb || y < 0 || y >= nb || z < 0 || z >= nb) ? ~0ull : make_key(n, x, y, z);
+}
+
+// Every node p of R_n: refined when it lies in the sources' halo (every box an unscreened apply
+// of the level would reach); its output rows of the level's two applies, if any.
+__global__ void reach_kernel(int64_t nr, const uint64_t *rkeys, const uint64_t *hkeys, int64_t nh,
+                             const uint64_t *ykeys, int64_t ny, const uint64_t *zkeys, int64_t nz, int64_t *yi,
+                             int64_t *zi, int *refine, int *leaf) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nr) return;
-  const int64_t a = find_sorted(ykeys, ny, rkeys[p]), b = find_sorted(zkeys, nz, rkeys[p]);
-  yi[p] = a;
-  zi[p] = b;
-  refine[p] = (a >= 0 || b >= 0) ? 1 : 0;
-  leaf[p] = (a >= 0 || b >= 0) ? 0 : 1;
+  yi[p] = find_sorted(ykeys, ny, rkeys[p]);
+  zi[p] = find_sorted(zkeys, nz, rkeys[p]);
+  const bool in = find_sorted(hkeys, nh, rkeys[p]) >= 0;
+  refine[p] = in ? 1 : 0;
+  leaf[p] = in ? 0 : 1;
 }
 
 // Every target row of an apply must be a node of R_n.
@@ -847,9 +862,11 @@ extern "C" int mra_apply_ns(const mra_operator *h, const mra_operator *hns, cons
 // The non-standard form apply on an adaptive tree (leaves of a complete octree, every leaf
 // deeper than n0).  Sources of level n are the interior nodes I_n (S = children, s = filter);
 // the result tree starts with every box of level n0 (r = T^{n0} s^{n0}, every displacement)
-// and at each level refines the nodes the level's applies reach (children get
-// Ubar^{x3} (r_p - Z_p) + Y_p); the nodes they do not reach, and every node of the deepest
-// leaf level, are the result's leaves.
+// and at each level refines the nodes in the halo of the level's sources -- every box an
+// unscreened apply reaches, |l|_inf <= D (children get Ubar^{x3} (r_p - Z_p) + Y_p, absent
+// rows of screened applies as zero); the other nodes, and every node of the deepest leaf
+// level, are the result's leaves.  The halo keeps every later level's targets inside the
+// result: a target's parent lies in the previous level's halo.
 extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns, const mra_tree_view *in, int n0,
                                  const mra_apply_opts *o, mra_tree_view *out, mra_apply_stats *stats, void *stream) {
   const Operator *op = reinterpret_cast<const Operator *>(h);
@@ -1045,14 +1062,43 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
     if (ny > 0) targets_in_kernel<<<(unsigned)((ny + 255) / 256), 256, 0, s>>>(ny, yk, Rk, nR, d_int);
     if (nz > 0) targets_in_kernel<<<(unsigned)((nz + 255) / 256), 256, 0, s>>>(nz, zk, Rk, nR, d_int);
     MRA_CUDA_TRY(cudaGetLastError());
+    // the halo of the level's sources, sorted and unique
+    const int64_t nh_all = In[n] * w3;
+    NS_ALLOC(hal, uint64_t, nh_all);
+    NS_ALLOC(hal_s, uint64_t, nh_all);
+    NS_ALLOC(hk, uint64_t, nh_all);
+    NS_ALLOC(d_nh, int64_t, 1);
+    MRA_CUDA_TRY(cudaMemsetAsync(d_nh, 0, 8, s));
+    if (nh_all > 0) {
+      halo_kernel<<<(unsigned)((nh_all + 255) / 256), 256, 0, s>>>(In[n], Ik[n], D, hal);
+      MRA_CUDA_TRY(cudaGetLastError());
+      size_t t1 = 0, t2 = 0;
+      MRA_CUDA_TRY(cub::DeviceRadixSort::SortKeys(nullptr, t1, hal, hal_s, (int)nh_all, 0, 64, s));
+      MRA_CUDA_TRY(cub::DeviceSelect::Unique(nullptr, t2, hal_s, hk, d_nh, (int)nh_all, s));
+      NS_ALLOC(tmph, unsigned char, std::max(t1, t2));
+      MRA_CUDA_TRY(cub::DeviceRadixSort::SortKeys(tmph, t1, hal, hal_s, (int)nh_all, 0, 64, s));
+      MRA_CUDA_TRY(cub::DeviceSelect::Unique(tmph, t2, hal_s, hk, d_nh, (int)nh_all, s));
+      drop(tmph);
+    }
+    int64_t nh = 0;
+    MRA_CUDA_TRY(cudaMemcpyAsync(&nh, d_nh, 8, cudaMemcpyDeviceToHost, s));
+    MRA_CUDA_TRY(cudaStreamSynchronize(s));
+    if (nh > 0) {
+      uint64_t last = 0;
+      MRA_CUDA_TRY(cudaMemcpyAsync(&last, hk + nh - 1, 8, cudaMemcpyDeviceToHost, s));
+      MRA_CUDA_TRY(cudaStreamSynchronize(s));
+      if (last == ~0ull) --nh;
+    }
     NS_ALLOC(yi, int64_t, nR);
     NS_ALLOC(zi, int64_t, nR);
     NS_ALLOC(refine, int, nR + 1);
     NS_ALLOC(leaf, int, nR + 1);
     NS_ALLOC(ref_pos, int, nR + 1);
     NS_ALLOC(leaf_pos, int, nR + 1);
-    reach_kernel<<<(unsigned)((nR + 255) / 256), 256, 0, s>>>(nR, Rk, yk, ny, zk, nz, yi, zi, refine, leaf);
-    MRA_CUDA_TRY(cudaGetLastError());
+    if (nR > 0) {
+      reach_kernel<<<(unsigned)((nR + 255) / 256), 256, 0, s>>>(nR, Rk, hk, nh, yk, ny, zk, nz, yi, zi, refine, leaf);
+      MRA_CUDA_TRY(cudaGetLastError());
+    }
     MRA_CUDA_TRY(cudaMemsetAsync(refine + nR, 0, sizeof(int), s));
     MRA_CUDA_TRY(cudaMemsetAsync(leaf + nR, 0, sizeof(int), s));
     size_t tb = 0;
@@ -1066,7 +1112,7 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
     MRA_CUDA_TRY(cudaStreamSynchronize(s));
     if (hint[0]) return fail(MRA_ERR_NUMERIC, "mra_apply_ns_tree: a level-%d apply reached a box outside the result tree", n);
     const int64_t nref = hcount[0], nleaf_here = nR - nref;
-    if (nleaf_here > 0) {
+    if (nleaf_here > 0 && nR > 0) {
       emit_leaves_kernel<<<(unsigned)nR, 128, 0, s>>>(nR, k3, Rk, R, leaf, leaf_pos, nout, cap, out->keys, out->coeffs);
       MRA_CUDA_TRY(cudaGetLastError());
     }
@@ -1096,7 +1142,7 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
     }
     for (void *p : {(void *)yk, (void *)yc, (void *)zk, (void *)zc, (void *)yi, (void *)zi, (void *)refine,
                     (void *)leaf, (void *)ref_pos, (void *)leaf_pos, (void *)tmp, (void *)cku, (void *)cru,
-                    (void *)idx, (void *)idx_s})
+                    (void *)idx, (void *)idx_s, (void *)hal, (void *)hal_s, (void *)hk, (void *)d_nh})
       drop(p);
     if (Rk != Ik[n0]) drop(Rk);
     drop(R);
