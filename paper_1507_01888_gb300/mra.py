@@ -239,6 +239,7 @@ class Operator:
         self._h = h
         self.kernel, self.M, self.k, self.L = kernel, M, k, L
         self.min_level, self.max_level, self.max_disp = min_level, max_level, max_disp
+        self.mu, self.fit_eps, self.r_lo, self.r_hi = mu, fit_eps, r_lo, r_hi
 
     @property
     def handle(self):

@@ -6,6 +6,7 @@ import pytest
 
 import oracle as O
 import workloads as W
+from oracle_inputs import oracle_fit
 
 pytestmark = pytest.mark.gpu
 
@@ -46,7 +47,7 @@ def test_batched_equals_per_function(mra, precision):
     # one function against the oracle
     f = 3
     ok, oc = trees[f].host()
-    fit = op.fit()
+    fit = oracle_fit(op)
     ref = O.apply(ok, oc, fit["c"], fit["t"], L, stencil=0, max_disp=1, tau=1e-7)
     a, b = out_offs[f], out_offs[f + 1]
     assert (gk[a:b] == ref.keys).all()

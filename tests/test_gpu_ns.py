@@ -9,6 +9,7 @@ import pytest
 
 import oracle as O
 import workloads as W
+from oracle_inputs import oracle_fit
 
 pytestmark = pytest.mark.gpu
 
@@ -31,7 +32,7 @@ def uniform_case(mra, k, N, kernel=0, mu=0.0, M=8, L=8.0, seed=7, op_disp=None):
     keys, coeffs, _ = O.project(f, k, L, uniform_level=N)
     op = mra.Operator(kernel, M, k, L, 0, N, max_disp=op_disp if op_disp is not None else (1 << N) - 1,
                       mu=mu, fit_eps=1e-4)
-    fit = op.fit()
+    fit = oracle_fit(op)
     return keys, coeffs, op, fit
 
 
@@ -115,7 +116,7 @@ def adaptive_case(mra, k, thresh=3e-3, max_level=4, op_disp=15, M=8):
     f = W.gaussian_sum(2, 1.0, 20.0, seed=11, centre_box=3.0)
     keys, coeffs, _ = O.project(f, k, L, thresh=thresh, init_level=2, max_level=max_level)
     op = mra.Operator(0, M, k, L, 0, max_level, max_disp=op_disp, fit_eps=1e-4)
-    return keys, coeffs, op, op.fit(), L
+    return keys, coeffs, op, oracle_fit(op), L
 
 
 @pytest.mark.parametrize("k,D", [(3, 1), (4, 2), (6, 1), (8, 1)])

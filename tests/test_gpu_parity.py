@@ -12,6 +12,7 @@ import pytest
 
 import oracle as O
 import workloads as W
+from oracle_inputs import golden, oracle_fit
 
 pytestmark = pytest.mark.gpu
 
@@ -55,7 +56,7 @@ def test_fit_matches_oracle(mra, kernel, mu, M, eps):
 @pytest.mark.parametrize("k", [4, 10, 14])
 def test_blocks_match_oracle(mra, k):
     op = mra.Operator(0, 40, k, 32.0, 0, 19, max_disp=2, fit_eps=1e-6)
-    f = op.fit()
+    f = oracle_fit(op)
     rng = np.random.default_rng(k)
     cases = [(lev, int(m), l) for lev in (0, 2, 5, 11, 19) for m in rng.choice(40, 4, replace=False)
              for l in (-2, -1, 0, 1, 2) if abs(l) <= 2 ** lev - 1]
@@ -121,9 +122,8 @@ def test_fp64_apply_uniform_27_point(mra):
 def test_fp64_apply_random_trees_ragged(mra, k, lev, nbox, seed):
     """Random sparse trees (ragged: missing sources, boundary boxes), several k."""
     keys, coeffs = W.random_tree_coeffs(nbox, k, lev, seed=seed)
-    c, t = O.fit_coeffs(0.0, 9, 0.9, -4.0)
     op = mra.Operator(0, 9, k, 16.0, 0, lev, max_disp=1, fit_eps=1e-4)
-    f = op.fit()
+    f = oracle_fit(op)
     ref = O.apply(keys, coeffs, f["c"], f["t"], 16.0, stencil=1, tau=0.0)
     out, st = mra.apply(op, mra.Tree.from_host(keys, coeffs, 16.0), mra.make_opts(stencil=mra.STENCIL_NEAREST))
     fp64_box_check(*out.host(), ref)
@@ -134,7 +134,7 @@ def test_fp64_apply_shells_and_screen_adaptive(mra):
     f = W.gaussian_sum(3, 1.0, 200.0, seed=23)
     ok, oc, margin = O.project(f, 6, 32.0, thresh=1e-4, init_level=2, max_level=10)
     op = mra.Operator(1, 24, 6, 32.0, 1, 10, max_disp=2, mu=1.0, fit_eps=1e-6)
-    fit = op.fit()
+    fit = oracle_fit(op)
     ref = O.apply(ok, oc, fit["c"], fit["t"], 32.0, stencil=0, max_disp=2, tau=1e-6)
     out, st = mra.apply(op, mra.Tree.from_host(ok, oc, 32.0),
                         mra.make_opts(stencil=mra.STENCIL_SHELLS, max_disp=2, screen=mra.SCREEN_NORM, tau=1e-6))
@@ -153,9 +153,10 @@ def test_fp64_paper_worked_example_on_gpu(mra):
     k_out, s_out = out.host()
     assert (k_in == k_out).all()
     E = float((s_in * s_out).sum())
-    assert abs(E - 24.739429) < 1e-6 * 24.739429
+    gold = golden("paper_gaussian_example.txt")
+    assert abs(E - gold["self_energy"]) < 1e-6 * gold["self_energy"]
     _, total = mra.norm(t)
-    assert abs(total - 1.403104) < 1e-6
+    assert abs(total - gold["norm2"]) < 1e-6
 
 
 def test_fp64_apply_edge_cases(mra):
@@ -169,7 +170,7 @@ def test_fp64_apply_edge_cases(mra):
     key = np.array([O.make_key(0, 0, 0, 0)], dtype=np.uint64)
     s = np.random.default_rng(0).standard_normal((1, 4, 4, 4))
     out, st = mra.apply(op, mra.Tree.from_host(key, s, 8.0), opts)
-    ref = O.apply(key, s, op.fit()["c"], op.fit()["t"], 8.0, stencil=1)
+    ref = O.apply(key, s, oracle_fit(op)["c"], oracle_fit(op)["t"], 8.0, stencil=1)
     fp64_box_check(*out.host(), ref)
     # a level the operator does not cover -> argument error, no fault
     key5 = np.array([O.make_key(5, 1, 2, 3)], dtype=np.uint64)
@@ -181,7 +182,7 @@ def test_fp64_apply_edge_cases(mra):
     tree = mra.Tree.from_host(keys, coeffs, 8.0)
     ap = mra.Applier(op, tree, opts, out_cap=1)
     out = ap(tree)
-    ref = O.apply(keys, coeffs, op.fit()["c"], op.fit()["t"], 8.0, stencil=1)
+    ref = O.apply(keys, coeffs, oracle_fit(op)["c"], oracle_fit(op)["t"], 8.0, stencil=1)
     fp64_box_check(*out.host(), ref)
 
 
@@ -196,7 +197,7 @@ def test_fp64_apply_full_size_sampled(mra):
     keys, coeffs = t.host()
     assert (keys == ok).all()
     op = mra.Operator(w.kernel, w.M, w.k, w.L, 2, 19, max_disp=w.max_disp, mu=w.mu, fit_eps=w.fit_eps)
-    fit = op.fit()
+    fit = oracle_fit(op)
     opts = mra.make_opts(stencil=w.stencil, max_disp=w.max_disp, screen=mra.SCREEN_NORM, tau=w.tau)
     out, st = mra.apply(op, mra.Tree.from_host(ok, oc, w.L), opts)
     gk, gc = out.host()

@@ -22,10 +22,12 @@ def test_reconstruct_of_the_leaf_level_apply(mra, k):
     L = 8.0
     f = W.gaussian_sum(2, 1.0, 20.0, seed=11, centre_box=3.0)
     keys, coeffs, _ = O.project(f, k, L, thresh=3e-3, init_level=2, max_level=4)
-    op = mra.Operator(0, 8, k, L, 2, 4, max_disp=1, fit_eps=1e-4)
-    multi, _ = mra.apply(op, mra.Tree.from_host(keys, coeffs, L), mra.make_opts(stencil=mra.STENCIL_NEAREST))
-    mk, mc = multi.host()
-    out = mra.reconstruct(multi, out_cap=1)  # also exercises the capacity retry
+    # the multi-level box sum of the leaf-level apply, computed by the oracle: both sides sum it down
+    r_lo, r_hi = O.kernel_range(O.POISSON, 0.0, L, 1e-4)
+    _, _, _, c, t = O.fit_search(0.0, 8, r_lo, r_hi)
+    multi = O.apply(keys, coeffs, c, t, L, stencil=1, tau=0.0)
+    mk, mc = multi.keys, multi.coeffs
+    out = mra.reconstruct(mra.Tree.from_host(mk, mc, L), out_cap=1)  # also exercises the capacity retry
     gk, gc = out.host()
     rk, rc = O.reconstruct(mk, mc, k)
     assert (gk == rk).all()

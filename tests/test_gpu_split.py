@@ -9,6 +9,7 @@ import pytest
 
 import oracle as O
 import workloads as W
+from oracle_inputs import oracle_fit
 
 pytestmark = pytest.mark.gpu
 
@@ -37,7 +38,7 @@ def test_split_uniform_27_point(mra):
     w = W.poisson_m20_uniform_k6()
     ok, oc, _ = O.project(w.funcs[0], w.k, w.L, uniform_level=3)
     op = mra.Operator(w.kernel, w.M, w.k, w.L, 3, 3, max_disp=1, fit_eps=w.fit_eps)
-    fit = op.fit()
+    fit = oracle_fit(op)
     ref = O.apply(ok, oc, fit["c"], fit["t"], w.L, stencil=1, tau=0.0)
     out, st = mra.apply(op, mra.Tree.from_host(ok, oc, w.L), split_opts(mra, stencil=mra.STENCIL_NEAREST))
     keys, coeffs = out.host()
@@ -51,7 +52,7 @@ def test_split_random_trees_ragged(mra, k, lev, nbox, seed):
     """Sparse random trees: missing sources, boundary boxes, partial tiles, every tile shape."""
     keys, coeffs = W.random_tree_coeffs(nbox, k, lev, seed=seed)
     op = mra.Operator(0, 16, k, 16.0, 0, lev, max_disp=1, fit_eps=1e-4)
-    fit = op.fit()
+    fit = oracle_fit(op)
     ref = O.apply(keys, coeffs, fit["c"], fit["t"], 16.0, stencil=1, tau=0.0)
     tree = mra.Tree.from_host(keys, coeffs, 16.0)
     out, st = mra.apply(op, tree, split_opts(mra, stencil=mra.STENCIL_NEAREST))
@@ -70,7 +71,7 @@ def test_split_tile_variants(mra, k, lev, nbox, seed):
     """Tile variants 1 and 2 (two or one 128-row tiles per CTA) equal the oracle like variant 0."""
     keys, coeffs = W.random_tree_coeffs(nbox, k, lev, seed=seed)
     op = mra.Operator(0, 16, k, 16.0, 0, lev, max_disp=1, fit_eps=1e-4)
-    fit = op.fit()
+    fit = oracle_fit(op)
     ref = O.apply(keys, coeffs, fit["c"], fit["t"], 16.0, stencil=1, tau=0.0)
     tree = mra.Tree.from_host(keys, coeffs, 16.0)
     for v in (0, 1, 2):
@@ -86,7 +87,7 @@ def test_split_shells_and_screen_adaptive(mra):
     f = W.gaussian_sum(3, 1.0, 200.0, seed=23)
     ok, oc, _ = O.project(f, 6, 32.0, thresh=1e-4, init_level=2, max_level=10)
     op = mra.Operator(1, 24, 6, 32.0, 1, 10, max_disp=2, mu=1.0, fit_eps=1e-6)
-    fit = op.fit()
+    fit = oracle_fit(op)
     ref = O.apply(ok, oc, fit["c"], fit["t"], 32.0, stencil=0, max_disp=2, tau=1e-6)
     out, st = mra.apply(op, mra.Tree.from_host(ok, oc, 32.0),
                         split_opts(mra, stencil=mra.STENCIL_SHELLS, max_disp=2, screen=mra.SCREEN_NORM, tau=1e-6))
@@ -100,7 +101,7 @@ def test_split_full_size_vs_fp64_and_oracle(mra):
     w = W.bsh_m60_adaptive_k10()
     ok, oc, _ = O.project(w.funcs[0], w.k, w.L, thresh=w.thresh, init_level=w.init_level, max_level=w.max_level)
     op = mra.Operator(w.kernel, w.M, w.k, w.L, 2, 19, max_disp=w.max_disp, mu=w.mu, fit_eps=w.fit_eps)
-    fit = op.fit()
+    fit = oracle_fit(op)
     tree = mra.Tree.from_host(ok, oc, w.L)
     kw = dict(stencil=w.stencil, max_disp=w.max_disp, screen=mra.SCREEN_NORM, tau=w.tau)
     sp, _ = mra.apply(op, tree, split_opts(mra, **kw))
@@ -122,7 +123,7 @@ def test_split_two_pieces_is_coarser(mra):
     """Two BF16 pieces carry ~16 significant bits: the error grows to ~1e-5 but stays bounded."""
     keys, coeffs = W.random_tree_coeffs(60, 8, 3, seed=12)
     op = mra.Operator(0, 16, 8, 16.0, 0, 3, max_disp=1, fit_eps=1e-4)
-    fit = op.fit()
+    fit = oracle_fit(op)
     ref = O.apply(keys, coeffs, fit["c"], fit["t"], 16.0, stencil=1, tau=0.0)
     out, _ = mra.apply(op, mra.Tree.from_host(keys, coeffs, 16.0), split_opts(mra, pieces=2, stencil=1))
     e2 = rel_l2(out.host()[1], ref.coeffs)
@@ -141,7 +142,7 @@ def test_split_edge_cases(mra):
     key = np.array([O.make_key(0, 0, 0, 0)], dtype=np.uint64)
     s = np.random.default_rng(0).standard_normal((1, 4, 4, 4))
     out, _ = mra.apply(op, mra.Tree.from_host(key, s, 8.0), opts)
-    fit = op.fit()
+    fit = oracle_fit(op)
     ref = O.apply(key, s, fit["c"], fit["t"], 8.0, stencil=1)
     gk, gc = out.host()
     assert (gk == ref.keys).all() and rel_l2(gc, ref.coeffs) <= TOL_MIXED
@@ -151,7 +152,7 @@ def test_split_edge_cases(mra):
                              O.make_key(19, 4000, top - 1, 77), O.make_key(19, 4001, top - 1, 77)], dtype=np.uint64))
     s = np.random.default_rng(1).standard_normal((4, 6, 6, 6))
     op19 = mra.Operator(0, 12, 6, 32.0, 19, 19, max_disp=1, fit_eps=1e-4)
-    fit = op19.fit()
+    fit = oracle_fit(op19)
     out, _ = mra.apply(op19, mra.Tree.from_host(keys, s, 32.0), split_opts(mra, stencil=mra.STENCIL_NEAREST))
     ref = O.apply(keys, s, fit["c"], fit["t"], 32.0, stencil=1)
     gk, gc = out.host()
@@ -159,7 +160,7 @@ def test_split_edge_cases(mra):
     # every term slot: M = 128
     keys, coeffs = W.random_tree_coeffs(40, 4, 3, seed=21)
     op128 = mra.Operator(1, 128, 4, 16.0, 0, 3, max_disp=1, mu=1.0, fit_eps=1e-6)
-    fit = op128.fit()
+    fit = oracle_fit(op128)
     out, st = mra.apply(op128, mra.Tree.from_host(keys, coeffs, 16.0), split_opts(mra, stencil=mra.STENCIL_NEAREST))
     ref = O.apply(keys, coeffs, fit["c"], fit["t"], 16.0, stencil=1, tau=0.0)
     gk, gc = out.host()

@@ -11,6 +11,7 @@ import pytest
 
 import oracle as O
 import workloads as W
+from oracle_inputs import golden
 
 mpmath = pytest.importorskip("mpmath")
 
@@ -223,12 +224,27 @@ def test_projection_trace_and_norm_closed_forms():
     assert (s ** 2).sum() == pytest.approx(ref, rel=1e-9)
 
 
+def test_golden_fixtures_agree_with_their_closed_forms():
+    """The digits printed in Sec. 3.1 (eq. gaussian) are the closed forms cut after the last printed
+    digit (pi^{3/2} = 5.56832799..., printed 5.5683279); the hydrogen fixture is the closed form
+    itself (orbital normalised: 4 pi int r^2 psi^2 dr = 1)."""
+    g = golden("paper_gaussian_example.txt")
+    assert 0 <= math.pi ** 1.5 - g["trace"] < 1e-7
+    assert 0 <= (math.pi / 2) ** 0.75 - g["norm2"] < 1e-6
+    assert 0 <= math.pi ** 2.5 * math.sqrt(2.0) - g["self_energy"] < 1e-6
+    h = golden("hydrogen_ground_state.txt")
+    a = h["psi_decay"]
+    assert 4 * math.pi * h["psi_norm"] ** 2 * 2.0 / (2 * a) ** 3 == pytest.approx(1.0, rel=1e-15)
+    assert h["energy"] == -0.5 * h["Z"] ** 2
+
+
 def test_paper_worked_example_trace_norm():
     """Sec. 3.1: g = exp(-|x|^2) on [-6,6]^3; trace 5.5683279, norm 1.403104 (printed values)."""
+    gold = golden("paper_gaussian_example.txt")
     keys, s, _ = O.project(W.paper_gaussian(), 10, 6.0, uniform_level=2)
     h = 12.0 / 4
-    assert abs((s[:, 0, 0, 0] * h ** 1.5).sum() - 5.5683279) < 1e-7
-    assert abs(math.sqrt((s ** 2).sum()) - 1.403104) < 1e-6
+    assert abs((s[:, 0, 0, 0] * h ** 1.5).sum() - gold["trace"]) < 1e-7
+    assert abs(math.sqrt((s ** 2).sum()) - gold["norm2"]) < 1e-6
 
 
 # ----------------------------------------------------------------- apply (Sec. 2.3, Sec. 3.1)
@@ -242,7 +258,8 @@ def test_paper_worked_example_self_energy():
     r = O.apply(keys, s, c, t, L, stencil=0, max_disp=3, tau=0.0)
     assert (r.keys == keys).all()
     E = float((r.coeffs * s).sum())
-    assert abs(E - 24.739429) < 1e-6 * 24.739429
+    gold = golden("paper_gaussian_example.txt")["self_energy"]
+    assert abs(E - gold) < 1e-6 * gold
     assert E == pytest.approx(math.pi ** 2.5 * math.sqrt(2.0), rel=1e-6)
 
 
