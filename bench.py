@@ -176,6 +176,18 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     w = W.WORKLOADS[args.workload]()
+    if "post" in w.extra or "solver" in w.extra:  # whole steps of the oracle, no sampling
+        runs = [oracle_post_step(w) if "post" in w.extra else oracle_solver_step(w)
+                for _ in range(args.warmup + args.steps)][args.warmup:]
+        value = statistics.mean(r["value"] for r in runs)
+        line = {"metric": METRIC, "value": value, "unit": "boxes/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": {"workload": w.name, "k": w.k},
+                "cpu_baseline": dict(runs[-1], value=value),
+                "e2e": {"value": value, "unit": "boxes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     times = []
     info = None
     for i in range(args.warmup + args.steps):
@@ -271,6 +283,7 @@ def run_ns(args, w, rank, world):
     clk = clocks_start(args.clocks_csv)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     kms = []
+    launches0 = mra.launch_count()
     for i in range(args.steps):
         flush.fill_(float(i))
         ev[i][0].record(stream)
@@ -278,6 +291,7 @@ def run_ns(args, w, rank, world):
         ev[i][1].record(stream)
         kms.append(ap.stats.kernel_ms)
     torch.cuda.synchronize()
+    launches = mra.launch_count() - launches0
     clocks = clocks_stop(clk, 0)
     ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
     n_all, ms = reduce_over_ranks(tree.n, ms, world, dev)
@@ -309,6 +323,7 @@ def run_ns(args, w, rank, world):
     else:
         terms = ns_terms(N, n0, D, w.M)
     flops = sum(t * (6 * (f * k) ** 4 + (f * k) ** 3) for _, f, t in terms)
+    assert abs(flops - ap.stats.algo_flops) <= 1e-9 * flops, "term count differs from the library's"
     kms_mean = statistics.mean(kms)
     achieved = flops / (kms_mean / 1e3) / 1e12
     pk, pk_kind = peaks()
@@ -335,9 +350,7 @@ def run_ns(args, w, rank, world):
                        "l2": "flushed by a 256 MB write before every step", "tuning": tuning,
                        "parallelism": "single GPU" if world == 1 else f"replicas x{world}"},
             "roofline": roof, "clocks": clocks,
-            # per step: the input check, N - n0 compress and sum-down kernels, and per apply (1 + 2 (N - n0)
-            # of them) the level keys, the apply's own 10 and the scatter into the dense level
-            "gpu_launches": args.steps * (1 + 2 * (N - n0) + (1 + 2 * (N - n0)) * 12),
+            "gpu_launches": launches,
             "e2e": {"value": n_all / (e2e_ms / 1e3), "unit": "boxes/s", "h2d_bytes_per_step": keys_pin.numel() * 8
                     + coeffs_pin.numel() * 8, "d2h_bytes_per_step": out_pin.numel() * 8},
             "accuracy": accuracy}
@@ -345,13 +358,257 @@ def run_ns(args, w, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def _timed(args, step, dev):
+    """W untimed steps, then K steps each after an L2 flush, CUDA events on the current stream.
+    Returns (mean ms per step, clocks, kernel launches of the library inside the timed region)."""
+    import torch
+    from paper_1507_01888_gb300 import mra
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    clk = clocks_start(args.clocks_csv)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = mra.launch_count()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    launches = mra.launch_count() - launches0
+    clocks = clocks_stop(clk, 0)
+    return statistics.mean(a.elapsed_time(b) for a, b in ev), clocks, launches
+
+
+def run_post(args, w, rank, world):
+    """Sum-down and truncation of the leaf-level apply's multi-level result: a step is
+    mra_reconstruct followed by mra_truncate, timed as whole calls (their per-level kernels,
+    CUB sorts and scans and host synchronisations).  Units: input boxes of the sum-down."""
+    import torch
+    from paper_1507_01888_gb300 import mra
+    import oracle as O
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    th = w.extra["post"]["truncate_thresh"]
+    tree = mra.project(w.funcs[0], w.k, w.L, thresh=w.thresh, init_level=w.init_level, max_level=w.max_level)
+    lv = (tree.host()[0] >> np.uint64(57)).astype(int)
+    op = mra.Operator(w.kernel, w.M, w.k, w.L, int(lv.min()), int(lv.max()), max_disp=w.max_disp, mu=w.mu,
+                      fit_eps=w.fit_eps)
+    multi, _ = mra.apply(op, tree, mra.make_opts(screen=mra.SCREEN_NORM, tau=w.tau, stencil=w.stencil,
+                                                 max_disp=w.max_disp))
+    k3 = w.k ** 3
+    res = {}
+
+    def step(src=multi):
+        leaves = mra.reconstruct(src, out_cap=4 * src.n)
+        tr, e2 = mra.truncate(leaves, th, out_cap=leaves.n)
+        res.update(leaves=leaves, tr=tr, e2=e2)
+        return tr
+
+    ms, clocks, launches = _timed(args, step, dev)
+    n_in, n_leaves, n_tr = multi.n, res["leaves"].n, res["tr"].n
+    n_all, ms = reduce_over_ranks(n_in, ms, world, dev)
+    box_bytes = k3 * 8 + 8
+    algo_bytes = box_bytes * (n_in + 2 * n_leaves + n_tr)
+    pk, pk_kind = peaks()
+    achieved = algo_bytes / (ms / 1e3) / 1e9
+    # end to end: host multi-level tree in, host truncated tree out
+    mk, mc = multi.host()
+    keys_pin = torch.from_numpy(mk.view(np.int64).copy()).pin_memory()
+    coeffs_pin = torch.from_numpy(mc.copy()).pin_memory()
+    dev_tree = mra.Tree(torch.empty_like(keys_pin, device=dev), torch.empty_like(coeffs_pin, device=dev),
+                        n_in, w.k, w.L)
+    out_k = torch.empty(n_tr, dtype=torch.int64).pin_memory()
+    out_c = torch.empty((n_tr, w.k, w.k, w.k), dtype=torch.float64).pin_memory()
+    stream = torch.cuda.current_stream()
+    e_ms = []
+    for i in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dev_tree.keys.copy_(keys_pin, non_blocking=True)
+        dev_tree.coeffs.copy_(coeffs_pin, non_blocking=True)
+        tr = step(dev_tree)
+        out_k.copy_(tr.keys[:n_tr], non_blocking=True)
+        out_c.copy_(tr.coeffs[:n_tr], non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e_ms.append(a.elapsed_time(b))
+    _, e2e_ms = reduce_over_ranks(n_in, statistics.mean(e_ms), world, dev)
+    line = {"metric": METRIC, "value": n_all / (ms / 1e3), "unit": "boxes/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n_boxes": n_all, "k": w.k, "input": "leaf-level FP64 apply result of "
+                       "the BSH M=60 k=10 workload (boxes on several levels)", "result_leaves": n_leaves,
+                       "truncated_leaves": n_tr, "truncate_thresh": th, "l2_change": res["e2"] ** 0.5,
+                       "l2": "flushed by a 256 MB write before every step",
+                       "parallelism": "single GPU" if world == 1 else f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                         "kernel": "mra_reconstruct + mra_truncate, whole calls",
+                         "peak_source": f"HBM copy, {pk_kind}",
+                         "bytes": "algorithmic: (k^3 + 1) x 8 B per box read or written: input, leaves written "
+                                  "and read back, truncated leaves"},
+            "clocks": clocks, "gpu_launches": launches,
+            "e2e": {"value": n_all / (e2e_ms / 1e3), "unit": "boxes/s",
+                    "h2d_bytes_per_step": keys_pin.numel() * 8 + coeffs_pin.numel() * 8,
+                    "d2h_bytes_per_step": out_k.numel() * 8 + out_c.numel() * 8}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_post_step(w)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def oracle_post_step(w):
+    """The oracle's own multi-level result of the same workload (untimed), then its sum-down and
+    truncation, timed as one whole step."""
+    import oracle as O
+    ok, oc, _ = O.project(w.funcs[0], w.k, w.L, thresh=w.thresh, init_level=w.init_level, max_level=w.max_level)
+    _, _, _, c, t = oracle_fit(w)
+    r = O.apply(ok, oc, c, t, w.L, stencil=w.stencil, max_disp=w.max_disp, tau=w.tau)
+    t0 = time.perf_counter()
+    lk, lc = O.reconstruct(r.keys, r.coeffs, w.k)
+    O.truncate(lk, lc, w.k, w.extra["post"]["truncate_thresh"])
+    t_cpu = time.perf_counter() - t0
+    return {"value": len(r.keys) / t_cpu, "unit": "boxes/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+            "sample": f"the whole job: {len(r.keys)} input boxes, {t_cpu:.2f} s"}
+
+
+def run_solver(args, w, rank, world):
+    """The bound-state Helmholtz fixed-point solve for Z = 1: converged first (untimed), then a
+    step is one whole iteration (product, non-standard apply, truncation, inner products, energy
+    update) at the converged state.  Units: leaves of V psi entering the non-standard apply."""
+    import math
+    import torch
+    from paper_1507_01888_gb300 import mra, solvers
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    cfg = w.extra["solver"]
+    prec = mra.PREC_FP64 if args.precision == "fp64" else mra.PREC_SPLIT_BF16
+    t0 = time.perf_counter()
+    V, vfit = solvers.project_potential(cfg["Z"], w.k, w.L, w.thresh, M=cfg["M_potential"])
+    psi = solvers.gaussian_start(cfg["Z"], w.k, w.L, w.thresh)
+    E, hist = cfg["E0"], []
+    for _ in range(40):
+        E, psi, dE = solvers.bsh_step(V, psi, E, w.thresh, w.M, w.fit_eps, prec)
+        hist.append(E)
+        if abs(dE) < 1e-3 * w.thresh:
+            break
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    info = {}
+    state = {"E": E}
+
+    def step(p=psi):
+        E1, new, _ = solvers.bsh_step(V, p, state["E"], w.thresh, w.M, w.fit_eps, prec, info=info)
+        return new
+
+    ms, clocks, launches = _timed(args, step, dev)
+    st = info["apply_stats"]
+    n_all, ms = reduce_over_ranks(info["n_vpsi"], ms, world, dev)
+    # the non-standard apply inside a step, alone, for the roofline of its tensor-core kernel
+    kms = st["kernel_ms"]
+    achieved = st["algo_flops"] / (kms / 1e3) / 1e12
+    pk, pk_kind = peaks()
+    peak = pk.get("bf16_tflops_sustained", 1688.5) if prec != mra.PREC_FP64 else FP64_PEAK_TFLOPS
+    # end to end: psi from the host, the new psi back to the host
+    pk_h, pc_h = psi.host()
+    keys_pin = torch.from_numpy(pk_h.view(np.int64).copy()).pin_memory()
+    coeffs_pin = torch.from_numpy(pc_h.copy()).pin_memory()
+    dev_psi = mra.Tree(torch.empty_like(keys_pin, device=dev), torch.empty_like(coeffs_pin, device=dev),
+                       psi.n, w.k, w.L)
+    stream = torch.cuda.current_stream()
+    e_ms, d2h = [], 0
+    for i in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dev_psi.keys.copy_(keys_pin, non_blocking=True)
+        dev_psi.coeffs.copy_(coeffs_pin, non_blocking=True)
+        new = step(dev_psi)
+        ok_ = torch.empty(new.n, dtype=torch.int64).pin_memory()
+        oc_ = torch.empty((new.n, w.k, w.k, w.k), dtype=torch.float64).pin_memory()
+        ok_.copy_(new.keys[:new.n], non_blocking=True)
+        oc_.copy_(new.coeffs[:new.n], non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e_ms.append(a.elapsed_time(b))
+        d2h = ok_.numel() * 8 + oc_.numel() * 8
+    _, e2e_ms = reduce_over_ranks(info["n_vpsi"], statistics.mean(e_ms), world, dev)
+    line = {"metric": METRIC, "value": n_all / (ms / 1e3), "unit": "boxes/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == mra.PREC_FP64 else "bf16x3-split apply, f64 elsewhere", "data": "synthetic",
+            "config": {"workload": w.name, "n_boxes": n_all, "k": w.k, "L": w.L, "thresh": w.thresh,
+                       "Z": cfg["Z"], "psi_leaves": info["n_psi"], "apply_result_leaves": info["n_result"],
+                       "bsh_terms": w.M, "potential_terms": cfg["M_potential"], "potential_fit_err": vfit,
+                       "iterations_to_converge": len(hist), "solve_s": t_solve, "energy": E,
+                       "energy_error": E + 0.5 * cfg["Z"] ** 2, "terms_kept": st["terms_kept"],
+                       "precision": "fp64" if prec == mra.PREC_FP64 else "split",
+                       "l2": "flushed by a 256 MB write before every step",
+                       "parallelism": "single GPU" if world == 1 else f"replicas x{world}"},
+            "roofline": {"bound": "alu" if prec == mra.PREC_FP64 else "tensor", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "kernel": "apply kernels of the non-standard apply (all levels)",
+                         "peak_source": ("nominal GB300 FP64" if prec == mra.PREC_FP64 else
+                                         f"bf16 dense sustained, {pk_kind}"), "kernel_ms": kms,
+                         "flops": "algorithmic (6k'^4+k'^3 per kept term, k' = k or 2k)",
+                         "share_of_step": kms / ms},
+            "clocks": clocks, "gpu_launches": launches,
+            "e2e": {"value": n_all / (e2e_ms / 1e3), "unit": "boxes/s",
+                    "h2d_bytes_per_step": keys_pin.numel() * 8 + coeffs_pin.numel() * 8,
+                    "d2h_bytes_per_step": d2h}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_solver_step(w)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def oracle_solver_step(w):
+    """One iteration of the solve composed from the oracle's functions (product, non-standard
+    apply with every term, truncation, inner products) on the oracle's own projections of -Z/r
+    and the Gaussian start; the whole step is timed."""
+    import math
+    import oracle as O
+    cfg = w.extra["solver"]
+    Mv = cfg["M_potential"]
+    _, _, _, c, t = O.fit_search(0.0, Mv, 1e-4, 2 * w.L)
+    g = {"coef": -cfg["Z"] * c, "expnt": t, "cx": np.zeros(Mv), "cy": np.zeros(Mv), "cz": np.zeros(Mv)}
+    Vk, Vc, _ = O.project(g, w.k, w.L, thresh=w.thresh, init_level=2, max_level=19)
+    a = cfg["Z"] ** 2
+    gp = {"coef": np.array([(2 * a / math.pi) ** 0.75]), "expnt": np.array([a]), "cx": np.zeros(1),
+          "cy": np.zeros(1), "cz": np.zeros(1)}
+    pk, pc, _ = O.project(gp, w.k, w.L, thresh=w.thresh, init_level=2, max_level=19)
+    t0 = time.perf_counter()
+    vk, vc = O.multiply(Vk, Vc, pk, pc, w.k, w.L)
+    E = cfg["E0"]
+    mu = math.sqrt(-2 * E)
+    r_lo, r_hi = O.kernel_range(O.BSH, mu, w.L, w.fit_eps)
+    _, _, _, cb, tb = O.fit_search(mu, w.M, r_lo, r_hi)
+    rk, rc = O.apply_ns_tree(vk, vc, w.k, w.L, 1, cb, tb, w.max_disp)
+    rc = rc * (-1.0 / (2.0 * math.pi))
+    nk, nc, _ = O.truncate(rk, rc, w.k, w.thresh)
+    O.inner(vk, vc, pk, pc, w.k)
+    O.inner(vk, vc, nk, nc, w.k)
+    O.inner(nk, nc, nk, nc, w.k)
+    t_cpu = time.perf_counter() - t0
+    return {"value": len(vk) / t_cpu, "unit": "boxes/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+            "sample": f"one whole iteration from the Gaussian start ({len(vk)} leaves of V psi), {t_cpu:.1f} s"}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
-    if "ns" in W.WORKLOADS[args.workload]().extra:
+    extra = W.WORKLOADS[args.workload]().extra
+    if "ns" in extra:
         return run_ns(args, W.WORKLOADS[args.workload](), rank, world)
+    if "post" in extra:
+        return run_post(args, W.WORKLOADS[args.workload](), rank, world)
+    if "solver" in extra:
+        return run_solver(args, W.WORKLOADS[args.workload](), rank, world)
 
     import torch
     from paper_1507_01888_gb300 import mra
@@ -465,6 +722,7 @@ def main():
     clk = clocks_start(args.clocks_csv)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     kernel_ms = []
+    launches0 = mra.launch_count()
     t_wall = time.perf_counter()
     for i in range(args.steps):
         flush.fill_(float(i))
@@ -474,6 +732,7 @@ def main():
         kernel_ms.append(ap.stats.kernel_ms)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
+    launches = mra.launch_count() - launches0
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -526,7 +785,6 @@ def main():
                 "kernel": "apply_f64_kernel", "peak_source": "nominal GB300 FP64 rate (recipe table)",
                 "kernel_ms": kms}
         dtype = "f64"
-        launches_per_step = 7
     else:
         peak = pk.get("bf16_tflops", 1856.3)
         roof = {"bound": "tensor", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
@@ -536,7 +794,6 @@ def main():
                 "peak_source": f"bf16 dense burst, {pk_kind}", "kernel_ms": kms,
                 "flops": "algorithmic (6k^4+k^3 per kept term)"}
         dtype = f"bf16x{args.pieces}-split, f32 accumulate, f64 term sum"
-        launches_per_step = 10
 
     line = {"metric": METRIC, "value": value, "unit": "boxes/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -553,7 +810,7 @@ def main():
                        "parallelism": ("single GPU" if world == 1 else
                                        f"{world} ranks, own functions each" if "rank_funcs" in w.extra
                                        else f"replicas x{world}")},
-            "roofline": roof, "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
+            "roofline": roof, "clocks": clocks, "gpu_launches": launches,
             "e2e": {"value": e2e_val, "unit": "boxes/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "accuracy": accuracy, "wall_s_timed": t_wall}
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not batched:

@@ -119,6 +119,8 @@ typedef struct {
   double kernel_ms;           /* device time of the apply kernel (CUDA events on `stream`) */
   int64_t terms_learned_skipped; /* triples the norm screen kept and the learned screen dropped */
   double learned_skipped_bound;  /* sum of the norm-screen bounds of those triples */
+  double algo_flops;  /* algorithmic flops of the kept triples: 6 k^4 + k^3 each, k the order
+                         of the operator that applied them (k or 2k in the non-standard form) */
 } mra_apply_stats;
 
 typedef struct {
@@ -132,6 +134,11 @@ typedef struct {
 } mra_compare_result;
 
 /* ---- calls ---------------------------------------------------------------- */
+
+/* Number of kernels the library has launched in this process so far (every launch of every
+ * entry point, counted on the host when it is issued; library routines the calls use, such as
+ * the CUB sorts and scans, are not counted).  Take the difference around a region of calls. */
+long long mra_launch_count(void);
 
 /* Thread-local description of the last error (never NULL). */
 const char *mra_last_error(void);

@@ -1,4 +1,5 @@
 // api.cu -- the extern "C" entry points declared in include/mra.h.
+#include <atomic>
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -128,6 +129,9 @@ __global__ void iota32(int64_t n, int *p) {
 }
 }  // namespace
 
+std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 }  // namespace mra
 
 using namespace mra;
@@ -137,6 +141,8 @@ extern "C" {
 const char *mra_last_error(void) { return g_err; }
 
 const char *mra_version(void) { return "mra-gb300 0.1 (sm_103a)"; }
+
+long long mra_launch_count(void) { return mra::g_launches.load(std::memory_order_relaxed); }
 
 int mra_operator_create(int kernel, double mu, int M, double fit_eps, double r_lo, double r_hi,
                         int k, double L, int min_level, int max_level, int max_disp,
@@ -412,7 +418,7 @@ int mra_project(const mra_gauss_sum *f, int k, double L, double thresh, int init
         leaf_cap = nc;
       }
       MRA_CUDA_TRY(cudaMemcpyAsync(d_from, from.data(), nf * 8, cudaMemcpyHostToDevice, s));
-      gather_rows_kernel<<<(unsigned)nf, 128, 0, s>>>(nf, k3, d_box, d_from, d_leaf, n_leaf);
+      gather_rows_kernel<<<counted((unsigned)nf), 128, 0, s>>>(nf, k3, d_box, d_from, d_leaf, n_leaf);
       MRA_CUDA_TRY(cudaGetLastError());
       n_leaf += nf;
       MRA_CUDA_TRY(cudaStreamSynchronize(s));  // ck/from are reused by the next chunk
@@ -436,9 +442,9 @@ int mra_project(const mra_gauss_sum *f, int k, double L, double thresh, int init
     MRA_CUDA_TRY(cudaMallocAsync((void **)&d_po, n_leaf * 4, s));
     MRA_CUDA_TRY(cudaMallocAsync(&tmp, tb, s));
     MRA_CUDA_TRY(cudaMemcpyAsync(d_lk, leaf_keys.data(), n_leaf * 8, cudaMemcpyHostToDevice, s));
-    iota32<<<(unsigned)((n_leaf + 255) / 256), 256, 0, s>>>(n_leaf, d_pi);
+    iota32<<<counted((unsigned)((n_leaf + 255) / 256)), 256, 0, s>>>(n_leaf, d_pi);
     MRA_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, tb, d_lk, out->keys, d_pi, d_po, (int)n_leaf, 0, 64, s));
-    gather_sorted_kernel<<<(unsigned)n_leaf, 128, 0, s>>>(n_leaf, k3, d_leaf, d_po, out->coeffs);
+    gather_sorted_kernel<<<counted((unsigned)n_leaf), 128, 0, s>>>(n_leaf, k3, d_leaf, d_po, out->coeffs);
     MRA_CUDA_TRY(cudaGetLastError());
     MRA_CUDA_TRY(cudaFreeAsync(d_lk, s));
     MRA_CUDA_TRY(cudaFreeAsync(d_pi, s));

@@ -602,7 +602,7 @@ static int screen_run(const Operator &op, const mra_tree_view &in, const mra_app
   MRA_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int64_t), s));
   const int wpb = 8;  // warps per CTA for per-box kernels
   unsigned gboxes = (unsigned)((n_in + wpb - 1) / wpb);
-  box_norm_kernel<<<gboxes, 32 * wpb, 0, s>>>(n_in, k3, in.coeffs, w.snorm);
+  box_norm_kernel<<<counted(gboxes), 32 * wpb, 0, s>>>(n_in, k3, in.coeffs, w.snorm);
   MRA_CUDA_TRY(cudaGetLastError());
 
   ScreenArgs a{};
@@ -639,7 +639,7 @@ static int screen_run(const Operator &op, const mra_tree_view &in, const mra_app
   a.nfunc = nfunc;
   a.fn_off = w.fnoff;
   const size_t ssm = a.mlp ? (size_t)MLP_NALL * sizeof(float) : 0;
-  screen_kernel<0><<<gboxes, 32 * wpb, ssm, s>>>(a);
+  screen_kernel<0><<<counted(gboxes), 32 * wpb, ssm, s>>>(a);
   MRA_CUDA_TRY(cudaGetLastError());
   void *tmp = w.tmp;
   size_t tmpb = w.tmpb;
@@ -687,9 +687,10 @@ static int screen_run(const Operator &op, const mra_tree_view &in, const mra_app
     stats->terms_issued = hs[0];
     stats->terms_learned_skipped = hs[3];
     stats->learned_skipped_bound = hd[1];
+    stats->algo_flops = (double)hs[0] * (6.0 * op.k * op.k * op.k * op.k + (double)op.k * op.k * op.k);
   }
   if (P > 0) {
-    screen_kernel<1><<<gboxes, 32 * wpb, ssm, s>>>(a);
+    screen_kernel<1><<<counted(gboxes), 32 * wpb, ssm, s>>>(a);
     MRA_CUDA_TRY(cudaGetLastError());
   }
   *P_out = P;
@@ -731,13 +732,13 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
   // sort record indices on the destination key
   {
     unsigned g = (unsigned)((P + 255) / 256);
-    iota_kernel<<<g, 256, 0, s>>>(P, pin);
+    iota_kernel<<<counted(g), 256, 0, s>>>(P, pin);
     MRA_CUDA_TRY(cudaGetLastError());
     MRA_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, tmpb, rkey, skey, pin, pout, (int)P, 0, 64, s));
-    head_flags_kernel<<<g, 256, 0, s>>>(P, skey, head);
+    head_flags_kernel<<<counted(g), 256, 0, s>>>(P, skey, head);
     MRA_CUDA_TRY(cudaGetLastError());
     MRA_CUDA_TRY(cub::DeviceScan::InclusiveSum(tmp, tmpb, head, did, (int)P, s));
-    segments_kernel<<<g, 256, 0, s>>>(P, skey, head, did, dkey, seg, ndest, nfunc > 1, W.dfunc);
+    segments_kernel<<<counted(g), 256, 0, s>>>(P, skey, head, did, dkey, seg, ndest, nfunc > 1, W.dfunc);
     MRA_CUDA_TRY(cudaGetLastError());
   }
   int64_t nd = 0;
@@ -749,7 +750,7 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
                 (long long)out.cap, (long long)nd);
   }
   if (nfunc > 1 && out_offsets) {  // first destination of each function (destinations sorted by function)
-    func_offsets_kernel<<<1, 256, 0, s>>>(nd, W.dfunc, nfunc, W.fnoff);
+    func_offsets_kernel<<<counted(1), 256, 0, s>>>(nd, W.dfunc, nfunc, W.fnoff);
     MRA_CUDA_TRY(cudaGetLastError());
     MRA_CUDA_TRY(cudaMemcpyAsync(out_offsets, W.fnoff, (nfunc + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     MRA_CUDA_TRY(cudaStreamSynchronize(s));
@@ -784,7 +785,7 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
     if (smem > 48 * 1024)
       MRA_CUDA_TRY(cudaFuncSetAttribute(apply_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem));
-    apply_f64_kernel<<<(unsigned)nd, F64_THREADS, smem, s>>>(
+    apply_f64_kernel<<<counted((unsigned)nd), F64_THREADS, smem, s>>>(
         k, op.M, op.d_c, op.d_R, op.d_D, op.d_level_off, in.keys, in.coeffs, seg, pout, rsrc, rl,
         rmask, dkey, out.keys, out.coeffs);
     MRA_CUDA_TRY(cudaGetLastError());
@@ -944,7 +945,7 @@ int log_terms_run(const Operator &op, const mra_tree_view &in, const mra_apply_o
   const uint64_t thr = frac >= 1.0 ? ~0ull : (uint64_t)(frac * 18446744073709551615.0);
   int64_t *cnt = (int64_t *)W.rkey, *off = (int64_t *)W.skey;  // free until a sort runs
   unsigned g = (unsigned)((P + 255) / 256);
-  sample_count_kernel<<<g, 256, 0, s>>>(P, W.rmask, seed, thr, cnt);
+  sample_count_kernel<<<counted(g), 256, 0, s>>>(P, W.rmask, seed, thr, cnt);
   MRA_CUDA_TRY(cudaGetLastError());
   MRA_CUDA_TRY(cub::DeviceScan::ExclusiveSum(W.tmp, W.tmpb, cnt, off, (int)P, s));
   int64_t last[2];
@@ -954,13 +955,13 @@ int log_terms_run(const Operator &op, const mra_tree_view &in, const mra_apply_o
   const int64_t total = last[0] + last[1];
   const int64_t nlog = total < max_terms ? total : max_terms;
   if (nlog == 0) return MRA_OK;
-  sample_write_kernel<<<g, 256, 0, s>>>(P, W.rmask, W.rsrc, W.rl, seed, thr, off, max_terms, features);
+  sample_write_kernel<<<counted(g), 256, 0, s>>>(P, W.rmask, W.rsrc, W.rl, seed, thr, off, max_terms, features);
   MRA_CUDA_TRY(cudaGetLastError());
   const int k = op.k;
   size_t smem = (size_t)(3 * k * k * k + 3 * k * k) * sizeof(double);
   if (smem > 48 * 1024)
     MRA_CUDA_TRY(cudaFuncSetAttribute(term_norm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  term_norm_kernel<<<(unsigned)nlog, 256, smem, s>>>(k, op.d_c, op.d_t, op.d_R, op.d_D, op.d_level_off, in.keys,
+  term_norm_kernel<<<counted((unsigned)nlog), 256, smem, s>>>(k, op.d_c, op.d_t, op.d_R, op.d_D, op.d_level_off, in.keys,
                                                       in.coeffs, W.snorm, features, log_norms);
   MRA_CUDA_TRY(cudaGetLastError());
   MRA_CUDA_TRY(cudaStreamSynchronize(s));
@@ -987,8 +988,8 @@ int norm_run(const mra_tree_view &t, double *per_box, double *total, cudaStream_
   tmp = (void *)(((uintptr_t)(dsum + 1) + 255) & ~(uintptr_t)255);
   double *norms = per_box ? per_box : buf;
   const int wpb = 8;
-  box_norm_kernel<<<(unsigned)((n + wpb - 1) / wpb), 32 * wpb, 0, s>>>(n, k3, t.coeffs, norms);
-  square_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, norms, sq);
+  box_norm_kernel<<<counted((unsigned)((n + wpb - 1) / wpb)), 32 * wpb, 0, s>>>(n, k3, t.coeffs, norms);
+  square_kernel<<<counted((unsigned)((n + 255) / 256)), 256, 0, s>>>(n, norms, sq);
   MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, sq, dsum, (int)n, s));
   double h = 0.0;
   MRA_CUDA_TRY(cudaMemcpyAsync(&h, dsum, 8, cudaMemcpyDeviceToHost, s));
@@ -1023,16 +1024,16 @@ int compare_run(const mra_tree_view &t, const mra_tree_view &r, mra_compare_resu
   const int wpb = 8;
   MRA_CUDA_TRY(cudaMemsetAsync(sums, 0, 8 * sizeof(double), s));
   if (nt > 0) {
-    compare_kernel<<<(unsigned)((nt + wpb - 1) / wpb), 32 * wpb, 0, s>>>(
+    compare_kernel<<<counted((unsigned)((nt + wpb - 1) / wpb)), 32 * wpb, 0, s>>>(
         nt, t.keys, t.coeffs, nr, r.keys, r.coeffs, k3, d2, t2, r2, rel, match);
     MRA_CUDA_TRY(cudaGetLastError());
     MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, d2, sums + 0, (int)nt, s));
     MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, t2, sums + 1, (int)nt, s));
     MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, match, (int *)(sums + 4), (int)nt, s));
-    max_kernel_single<<<1, 1024, 0, s>>>(nt, rel, sums + 5);
+    max_kernel_single<<<counted(1), 1024, 0, s>>>(nt, rel, sums + 5);
   }
   if (nr > 0) {
-    ref_only_kernel<<<(unsigned)((nr + wpb - 1) / wpb), 32 * wpb, 0, s>>>(nr, r.keys, r.coeffs, nt,
+    ref_only_kernel<<<counted((unsigned)((nr + wpb - 1) / wpb)), 32 * wpb, 0, s>>>(nr, r.keys, r.coeffs, nt,
                                                                            t.keys, k3, ra, ro, only);
     MRA_CUDA_TRY(cudaGetLastError());
     MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, ra, sums + 2, (int)nr, s));

@@ -691,8 +691,8 @@ int split_blocks_build(Operator &op, cudaStream_t s) {
     const int64_t nb = (int64_t)op.M * nl, base = op.level_off[li];
     if (nb <= 0) continue;
     const double *R = op.d_R + base * op.k * op.k;
-    split_blocks_kernel<<<(unsigned)nb, 128, 0, s>>>(nb, op.k, nl, nullptr, R, plain + base * BSTAGE_BYTES);
-    split_blocks_kernel<<<(unsigned)nb, 128, 0, s>>>(nb, op.k, nl, op.d_c, R, scaled + base * BSTAGE_BYTES);
+    split_blocks_kernel<<<counted((unsigned)nb), 128, 0, s>>>(nb, op.k, nl, nullptr, R, plain + base * BSTAGE_BYTES);
+    split_blocks_kernel<<<counted((unsigned)nb), 128, 0, s>>>(nb, op.k, nl, op.d_c, R, scaled + base * BSTAGE_BYTES);
     MRA_CUDA_TRY(cudaGetLastError());
   }
   return MRA_OK;
@@ -727,13 +727,13 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
   size_t tmpb = wk.split_ws_bytes - (size_t)(q - w);
   unsigned g = (unsigned)((P + 255) / 256);
   MRA_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-  key2_kernel<<<g, 256, 0, s>>>(P, G, wk.perm, wk.did, wk.dest_key, wk.rec_l, key2, val2);
+  key2_kernel<<<counted(g), 256, 0, s>>>(P, G, wk.perm, wk.did, wk.dest_key, wk.rec_l, key2, val2);
   MRA_CUDA_TRY(cudaGetLastError());
   MRA_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, tmpb, key2, key2s, val2, val2s, (int)P, 0, 64, s));
-  groups_kernel<<<g, 256, 0, s>>>(P, key2s, head, n_tiles);
+  groups_kernel<<<counted(g), 256, 0, s>>>(P, key2s, head, n_tiles);
   MRA_CUDA_TRY(cudaGetLastError());
   MRA_CUDA_TRY(cub::DeviceScan::InclusiveSum(tmp, tmpb, head, gid, (int)P, s));
-  group_bounds_kernel<<<g, 256, 0, s>>>(P, key2s, head, gid, grp_start, tile_gstart, n_tiles);
+  group_bounds_kernel<<<counted(g), 256, 0, s>>>(P, key2s, head, gid, grp_start, tile_gstart, n_tiles);
   MRA_CUDA_TRY(cudaGetLastError());
 
   SplitArgs a{};
@@ -788,7 +788,7 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
   MRA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   MRA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   if (wk.ev0) MRA_CUDA_TRY(cudaEventRecord(wk.ev0, s));
-  kern<<<(unsigned)n_tiles, SPLIT_THREADS, smem, s>>>(a);
+  kern<<<counted((unsigned)n_tiles), SPLIT_THREADS, smem, s>>>(a);
   MRA_CUDA_TRY(cudaGetLastError());
   if (wk.ev1) MRA_CUDA_TRY(cudaEventRecord(wk.ev1, s));
   int herr = 0;

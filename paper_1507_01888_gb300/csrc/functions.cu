@@ -121,7 +121,7 @@ struct Pool {
 int check_leaf_view(const mra_tree_view *v, const char *what) {
   if (!v) return fail(MRA_ERR_ARG, "%s: NULL tree", what);
   if (v->n < 0 || (v->n > 0 && (!v->keys || !v->coeffs))) return fail(MRA_ERR_ARG, "%s: bad tree view", what);
-  if (v->k < 1 || 2 * v->k > MRA_MAX_K) return fail(MRA_ERR_ARG, "%s: k=%d outside 1..%d", what, v->k, MRA_MAX_K / 2);
+  if (v->k < 1 || v->k > MRA_MAX_K) return fail(MRA_ERR_ARG, "%s: k=%d outside 1..%d", what, v->k, MRA_MAX_K);
   return MRA_OK;
 }
 
@@ -155,8 +155,8 @@ int align(const mra_tree_view &a, const mra_tree_view &b, Pool &pool, cudaStream
   MRA_CUDA_TRY(cudaMemcpyAsync(dia, ia.data(), nu * 8, cudaMemcpyHostToDevice, s));
   MRA_CUDA_TRY(cudaMemcpyAsync(dib, ib.data(), nu * 8, cudaMemcpyHostToDevice, s));
   if (nu > 0) {
-    ext_rows_kernel<<<(unsigned)nu, 128, 0, s>>>(nu, k3, dia, a.coeffs, ea);
-    ext_rows_kernel<<<(unsigned)nu, 128, 0, s>>>(nu, k3, dib, b.coeffs, eb);
+    ext_rows_kernel<<<counted((unsigned)nu), 128, 0, s>>>(nu, k3, dia, a.coeffs, ea);
+    ext_rows_kernel<<<counted((unsigned)nu), 128, 0, s>>>(nu, k3, dib, b.coeffs, eb);
     MRA_CUDA_TRY(cudaGetLastError());
   }
   // sum both down to the common leaves
@@ -247,7 +247,9 @@ extern "C" int mra_multiply(const mra_tree_view *a, const mra_tree_view *b, mra_
   double *dVW = (double *)pool.get(VW.size() * 8);
   if (!dVW) return fail(MRA_ERR_CUDA, "mra_multiply: out of device memory");
   MRA_CUDA_TRY(cudaMemcpyAsync(dVW, VW.data(), VW.size() * 8, cudaMemcpyHostToDevice, s));
-  product_kernel<<<(unsigned)n, 128, 4 * k3 * sizeof(double), s>>>(k, a->L, n, keys, ca, cb, dVW, out->coeffs);
+  MRA_CUDA_TRY(cudaFuncSetAttribute(product_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(4 * k3 * sizeof(double))));
+  product_kernel<<<counted((unsigned)n), 128, 4 * k3 * sizeof(double), s>>>(k, a->L, n, keys, ca, cb, dVW, out->coeffs);
   MRA_CUDA_TRY(cudaGetLastError());
   MRA_CUDA_TRY(cudaMemcpyAsync(out->keys, keys, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
   MRA_CUDA_TRY(cudaStreamSynchronize(s));
@@ -274,7 +276,7 @@ extern "C" int mra_inner(const mra_tree_view *a, const mra_tree_view *b, double 
   const int k3 = a->k * a->k * a->k;
   double *d = (double *)pool.get(n * 8), *sum = (double *)pool.get(8);
   if (!d || !sum) return fail(MRA_ERR_CUDA, "mra_inner: out of device memory");
-  dot_rows_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(n, k3, ca, cb, d);
+  dot_rows_kernel<<<counted((unsigned)((n + 7) / 8)), 256, 0, s>>>(n, k3, ca, cb, d);
   MRA_CUDA_TRY(cudaGetLastError());
   size_t tb = 0;
   MRA_CUDA_TRY(cub::DeviceReduce::Sum(nullptr, tb, d, sum, (int)n, s));

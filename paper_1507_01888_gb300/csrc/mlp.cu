@@ -253,12 +253,12 @@ size_t mlp_grad_workspace(int64_t n) {
 }
 
 cudaError_t mlp_init(float *p, uint64_t seed, cudaStream_t s) {
-  mlp_init_kernel<<<(MLP_NP + 255) / 256, 256, 0, s>>>(p, seed);
+  mlp_init_kernel<<<counted((MLP_NP + 255) / 256), 256, 0, s>>>(p, seed);
   return cudaGetLastError();
 }
 
 cudaError_t mlp_fit_norm(float *p, const float *x, const float *y, int64_t n, cudaStream_t s) {
-  mlp_norm_kernel<<<1, 256, 0, s>>>(p, x, y, n);
+  mlp_norm_kernel<<<counted(1), 256, 0, s>>>(p, x, y, n);
   return cudaGetLastError();
 }
 
@@ -266,7 +266,7 @@ cudaError_t mlp_forward(const float *p, const float *x, int64_t n, float *y, cud
   if (n <= 0) return cudaSuccess;
   int64_t blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
-  mlp_forward_kernel<<<(unsigned)blocks, 256, 0, s>>>(p, x, n, y);
+  mlp_forward_kernel<<<counted((unsigned)blocks), 256, 0, s>>>(p, x, n, y);
   return cudaGetLastError();
 }
 
@@ -276,21 +276,21 @@ cudaError_t mlp_grad(const float *p, const float *x, const float *y, int64_t n, 
   int64_t chunk = (n + nb - 1) / nb;
   float *part = (float *)ws;
   double *lpart = (double *)(((uintptr_t)(part + (size_t)nb * MLP_NP) + 15) & ~(uintptr_t)15);
-  mlp_grad_partial_kernel<<<nb, 256, 0, s>>>(p, x, y, n, chunk, part, lpart);
+  mlp_grad_partial_kernel<<<counted(nb), 256, 0, s>>>(p, x, y, n, chunk, part, lpart);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  grad_reduce_kernel<<<(MLP_NP + 255) / 256, 256, 0, s>>>(part, nb, grad, lpart, n, d_loss);
+  grad_reduce_kernel<<<counted((MLP_NP + 255) / 256), 256, 0, s>>>(part, nb, grad, lpart, n, d_loss);
   return cudaGetLastError();
 }
 
 cudaError_t mlp_adam(float *p, float *m, float *v, const float *g, float lr, int step, cudaStream_t s) {
-  adam_kernel<<<(MLP_NP + 255) / 256, 256, 0, s>>>(p, m, v, g, lr, 0.9f, 0.999f, 1e-8f, step);
+  adam_kernel<<<counted((MLP_NP + 255) / 256), 256, 0, s>>>(p, m, v, g, lr, 0.9f, 0.999f, 1e-8f, step);
   return cudaGetLastError();
 }
 
 cudaError_t mlp_gather_batch(const float *x, const float *y, int64_t n, int batch, uint64_t seed, int step,
                              float *bx, float *by, cudaStream_t s) {
-  gather_batch_kernel<<<(batch + 255) / 256, 256, 0, s>>>(x, y, n, batch, seed, step, bx, by);
+  gather_batch_kernel<<<counted((batch + 255) / 256), 256, 0, s>>>(x, y, n, batch, seed, step, bx, by);
   return cudaGetLastError();
 }
 

@@ -23,6 +23,16 @@ int fail(int code, const char *fmt, ...);
                          cudaGetErrorString(e_));                                   \
   } while (0)
 
+// ---------------------------------------------------------------- launch count
+// Every kernel launch of the library takes its grid through counted(), so that
+// mra_launch_count reports how many kernels the library has launched.
+void note_launch();
+template <class G>
+inline G counted(G grid) {
+  note_launch();
+  return grid;
+}
+
 // ---------------------------------------------------------------- keys
 __host__ __device__ inline uint64_t make_key(int n, int64_t x, int64_t y, int64_t z) {
   return ((uint64_t)n << 57) | ((uint64_t)x << 38) | ((uint64_t)y << 19) | (uint64_t)z;

@@ -93,10 +93,10 @@ extern "C" int mra_norm_noalloc(const mra_tree_view *t, double *per_box, double 
   double *sq = scratch, *tot = scratch + MRA_NOALLOC_MAX_BOXES;
   if (n > 0) {
     const int wpb = 8;
-    sq_norm_kernel<<<(unsigned)((n + wpb - 1) / wpb), 32 * wpb, 0, s>>>(n, k3, t->coeffs, sq, per_box);
+    sq_norm_kernel<<<counted((unsigned)((n + wpb - 1) / wpb)), 32 * wpb, 0, s>>>(n, k3, t->coeffs, sq, per_box);
     MRA_CUDA_TRY(cudaGetLastError());
   }
-  sum_kernel<<<1, 1024, 0, s>>>(n, sq, tot);
+  sum_kernel<<<counted(1), 1024, 0, s>>>(n, sq, tot);
   MRA_CUDA_TRY(cudaGetLastError());
   double h = 0.0;
   MRA_CUDA_TRY(cudaMemcpyAsync(&h, tot, sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -458,9 +458,12 @@ __global__ void pass_down_kernel(int k, int64_t nr, const uint64_t *rkeys, const
 // are leaves too forms S from the eight, s = (Ubar^T)^{x3} S and the detail
 // d = S - Ubar^{x3} s; if ||d||_F <= thresh the eight are marked gone, the parent (key, s) is
 // appended at an atomic slot of the level above and ||d||^2 is kept at the first child's slot.
+// Shared memory: the filter's two intermediates (4k^3, 2k^3) and s (k^3), the unfilter's
+// intermediates reusing the filter's; S itself (8k^3) is staged too when s_smem is set, and
+// read from the children's rows otherwise (k > 12, where it does not fit).
 __global__ void truncate_level_kernel(int k, int n, int64_t nl, const uint64_t *keys, const double *v, double thresh,
                                       const double *Ub, int *gone, double *d2, uint64_t *pkeys, double *pv,
-                                      int *pcount) {
+                                      int *pcount, int s_smem) {
   extern __shared__ double sh[];
   __shared__ int64_t idx[8];
   __shared__ int all;
@@ -471,7 +474,8 @@ __global__ void truncate_level_kernel(int k, int n, int64_t nl, const uint64_t *
   const int64_t x = key_x(key), y = key_y(key), z = key_z(key);
   if ((x & 1) || (y & 1) || (z & 1)) return;
   const int kk = 2 * k, k3 = k * k * k, kk3 = kk * kk * kk;
-  double *S = sh, *a = S + kk3, *b = a + k * kk * kk, *sv = b + k * k * kk, *c = sv + k3, *e = c + kk * k * k;
+  double *a = sh, *b = a + k * kk * kk, *sv = b + k * k * kk, *S = sv + k3;
+  double *c = b, *e = a;  // the unfilter's intermediates (kk k^2 and kk^2 k) once a and b are consumed
   if (threadIdx.x == 0) all = 1;
   __syncthreads();
   if (threadIdx.x < 8) {
@@ -481,16 +485,20 @@ __global__ void truncate_level_kernel(int k, int n, int64_t nl, const uint64_t *
   }
   __syncthreads();
   if (!all) return;
-  for (int q = threadIdx.x; q < kk3; q += blockDim.x) {
+  // S[(I, J, L)] = child (I/k, J/k, L/k)'s coefficient (I%k, J%k, L%k)
+  auto s_at = [&](int q) {
     const int I = q / (kk * kk), J = (q / kk) % kk, Lq = q % kk;
     const int64_t src = idx[((I / k) << 2) | ((J / k) << 1) | (Lq / k)];
-    S[q] = v[src * k3 + ((I % k) * k + J % k) * k + Lq % k];
+    return v[src * k3 + ((I % k) * k + J % k) * k + Lq % k];
+  };
+  if (s_smem) {
+    for (int q = threadIdx.x; q < kk3; q += blockDim.x) S[q] = s_at(q);
+    __syncthreads();
   }
-  __syncthreads();
   for (int q = threadIdx.x; q < k * kk * kk; q += blockDim.x) {  // filter
     const int ii = q / (kk * kk), r = q % (kk * kk);
     double t = 0.0;
-    for (int I = 0; I < kk; ++I) t += Ub[I * k + ii] * S[I * kk * kk + r];
+    for (int I = 0; I < kk; ++I) t += Ub[I * k + ii] * (s_smem ? S[I * kk * kk + r] : s_at(I * kk * kk + r));
     a[q] = t;
   }
   __syncthreads();
@@ -527,7 +535,7 @@ __global__ void truncate_level_kernel(int k, int n, int64_t nl, const uint64_t *
     const int I = q / (kk * kk), J = (q / kk) % kk, Lq = q % kk;
     double t = 0.0;
     for (int l = 0; l < k; ++l) t += Ub[Lq * k + l] * e[(I * kk + J) * k + l];
-    const double dd = S[q] - t;
+    const double dd = (s_smem ? S[q] : s_at(q)) - t;
     part += dd * dd;
   }
   for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
@@ -714,12 +722,12 @@ extern "C" int mra_operator_ns_create(const mra_operator *h, int max_disp, mra_o
   for (int n = ns->min_level; n <= ns->max_level && e == cudaSuccess; ++n) {
     const int li = n - ns->min_level, lc = n + 1 - op->min_level;
     const int D = ns->D[li];
-    ns_blocks_kernel<<<(unsigned)(ns->M * (2 * D + 1)), 256, 0, s>>>(op->k, ns->M, D, op->d_R, op->level_off[lc],
+    ns_blocks_kernel<<<counted((unsigned)(ns->M * (2 * D + 1))), 256, 0, s>>>(op->k, ns->M, D, op->d_R, op->level_off[lc],
                                                                        op->D[lc], ns->d_R, ns->level_off[li]);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
-    block_norms_kernel<<<(unsigned)((nb + 7) / 8), 256, 0, s>>>(nb, (int)kk2, ns->d_R, ns->d_N);
+    block_norms_kernel<<<counted((unsigned)((nb + 7) / 8)), 256, 0, s>>>(nb, (int)kk2, ns->d_R, ns->d_N);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -777,7 +785,7 @@ extern "C" int mra_apply_ns(const mra_operator *h, const mra_operator *hns, cons
       for (int j = 0; j < k; ++j) Ubh[(c * k + i) * k + j] = U[c * k * k + i * k + j];
   MRA_CUDA_TRY(cudaMemcpyAsync(Ub, Ubh.data(), Ubh.size() * 8, cudaMemcpyHostToDevice, s));
   MRA_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), s));
-  check_uniform_kernel<<<(unsigned)((in->n + 255) / 256), 256, 0, s>>>(N, in->n, in->keys, d_err);
+  check_uniform_kernel<<<counted((unsigned)((in->n + 255) / 256)), 256, 0, s>>>(N, in->n, in->keys, d_err);
   MRA_CUDA_TRY(cudaGetLastError());
   int herr = 0;
   MRA_CUDA_TRY(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -791,7 +799,7 @@ extern "C" int mra_apply_ns(const mra_operator *h, const mra_operator *hns, cons
   MRA_CUDA_TRY(cudaFuncSetAttribute(sum_down_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_d));
   for (int n = N - 1; n >= n0; --n) {
     const double *fine = n == N - 1 ? in->coeffs : (const double *)(w + Lw.s[n + 1]);
-    compress_kernel<<<(unsigned)boxes(n), 256, sh_c, s>>>(k, n, fine, Ub, (double *)(w + Lw.S[n]),
+    compress_kernel<<<counted((unsigned)boxes(n)), 256, sh_c, s>>>(k, n, fine, Ub, (double *)(w + Lw.S[n]),
                                                           (double *)(w + Lw.s[n]));
     MRA_CUDA_TRY(cudaGetLastError());
   }
@@ -805,6 +813,7 @@ extern "C" int mra_apply_ns(const mra_operator *h, const mra_operator *hns, cons
     acc.sources_truncated += st.sources_truncated;
     acc.skipped_bound += st.skipped_bound;
     acc.kernel_ms += st.kernel_ms;
+    acc.algo_flops += st.algo_flops;
   };
   void *aws = w + Lw.apply;
   // one apply on every box of level n: its output rows scattered into a zeroed dense array
@@ -812,7 +821,7 @@ extern "C" int mra_apply_ns(const mra_operator *h, const mra_operator *hns, cons
                          uint64_t *okeys, double *ocoeffs, double *dense) -> int {
     const int64_t nbx = boxes(n);
     const int rowlen = opx.k * opx.k * opx.k;
-    level_keys_kernel<<<(unsigned)((nbx + 255) / 256), 256, 0, s>>>(n, nbx, keys);
+    level_keys_kernel<<<counted((unsigned)((nbx + 255) / 256)), 256, 0, s>>>(n, nbx, keys);
     MRA_CUDA_TRY(cudaGetLastError());
     mra_tree_view vin{nbx, nbx, keys, const_cast<double *>(coeffs), opx.k, opx.L};
     mra_tree_view vout{0, nbx, okeys, ocoeffs, opx.k, opx.L};
@@ -822,7 +831,7 @@ extern "C" int mra_apply_ns(const mra_operator *h, const mra_operator *hns, cons
     add_stats(st);
     MRA_CUDA_TRY(cudaMemsetAsync(dense, 0, (size_t)nbx * rowlen * 8, s));
     if (vout.n > 0) {
-      scatter_dense_kernel<<<(unsigned)vout.n, 128, 0, s>>>(vout.n, okeys, ocoeffs, rowlen, dense);
+      scatter_dense_kernel<<<counted((unsigned)vout.n), 128, 0, s>>>(vout.n, okeys, ocoeffs, rowlen, dense);
       MRA_CUDA_TRY(cudaGetLastError());
     }
     return MRA_OK;
@@ -842,7 +851,7 @@ extern "C" int mra_apply_ns(const mra_operator *h, const mra_operator *hns, cons
     rc = level_apply(*op, n, (const double *)(w + Lw.s[n]), level_opts(*o), zk, zc, Zd);
     if (rc != MRA_OK) return rc;
     double *fine = n == N - 1 ? out->coeffs : rnext;
-    sum_down_kernel<<<(unsigned)boxes(n), 256, sh_d, s>>>(k, n, rcur, Zd, Yd, Ub, fine);
+    sum_down_kernel<<<counted((unsigned)boxes(n)), 256, sh_d, s>>>(k, n, rcur, Zd, Yd, Ub, fine);
     MRA_CUDA_TRY(cudaGetLastError());
     std::swap(rcur, rnext);
   }
@@ -925,7 +934,7 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
   // ---- leaves: order, depth
   NS_ALLOC(d_int, int, 4);
   MRA_CUDA_TRY(cudaMemsetAsync(d_int, 0, 4 * sizeof(int), s));
-  leaf_check_kernel<<<(unsigned)((n_leaf + 255) / 256), 256, 0, s>>>(n_leaf, in->keys, n0, d_int, d_int + 1);
+  leaf_check_kernel<<<counted((unsigned)((n_leaf + 255) / 256)), 256, 0, s>>>(n_leaf, in->keys, n0, d_int, d_int + 1);
   MRA_CUDA_TRY(cudaGetLastError());
   int hint[2] = {0, 0};
   MRA_CUDA_TRY(cudaMemcpyAsync(hint, d_int, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -955,7 +964,7 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
     const size_t tb = std::max(t1, t2);
     NS_ALLOC(tmp, unsigned char, tb);
     for (int n = n0; n < Nmax; ++n) {
-      ancestor_kernel<<<(unsigned)((n_leaf + 255) / 256), 256, 0, s>>>(n_leaf, in->keys, n, anc);
+      ancestor_kernel<<<counted((unsigned)((n_leaf + 255) / 256)), 256, 0, s>>>(n_leaf, in->keys, n, anc);
       MRA_CUDA_TRY(cudaGetLastError());
       size_t tt = tb;
       MRA_CUDA_TRY(cub::DeviceRadixSort::SortKeys(tmp, tt, anc, anc_s, (int)n_leaf, 0, 64, s));
@@ -992,7 +1001,7 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
     Sn[n] = S;
     sn[n] = sv;
     const bool deeper = n + 1 < Nmax;
-    compress_tree_kernel<<<(unsigned)In[n], 256, sh_c, s>>>(k, n, Ik[n], In[n], in->keys, in->coeffs, n_leaf,
+    compress_tree_kernel<<<counted((unsigned)In[n]), 256, sh_c, s>>>(k, n, Ik[n], In[n], in->keys, in->coeffs, n_leaf,
                                                             deeper ? Ik[n + 1] : nullptr, deeper ? sn[n + 1] : nullptr,
                                                             deeper ? In[n + 1] : 0, Ub, S, sv, d_int);
     MRA_CUDA_TRY(cudaGetLastError());
@@ -1023,6 +1032,7 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
     acc.terms_issued += st.terms_issued;
     acc.skipped_bound += st.skipped_bound;
     acc.kernel_ms += st.kernel_ms;
+    acc.algo_flops += st.algo_flops;
     *nout = vout.n;
     return MRA_OK;
   };
@@ -1040,7 +1050,7 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
     if (rc != MRA_OK) return rc;
     MRA_CUDA_TRY(cudaMemsetAsync(R, 0, (size_t)nR * k3 * 8, s));
     if (no > 0) {
-      scatter_dense_kernel<<<(unsigned)no, 128, 0, s>>>(no, ok, oc, k3, R);  // level n0 is complete: dense order
+      scatter_dense_kernel<<<counted((unsigned)no), 128, 0, s>>>(no, ok, oc, k3, R);  // level n0 is complete: dense order
       MRA_CUDA_TRY(cudaGetLastError());
     }
     drop(ok);
@@ -1059,8 +1069,8 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
     rc = run_apply(*op, In[n], Ik[n], sn[n], level_opts(*o), tcap, &zk, &zc, &nz);
     if (rc != MRA_OK) return rc;
     MRA_CUDA_TRY(cudaMemsetAsync(d_int, 0, sizeof(int), s));
-    if (ny > 0) targets_in_kernel<<<(unsigned)((ny + 255) / 256), 256, 0, s>>>(ny, yk, Rk, nR, d_int);
-    if (nz > 0) targets_in_kernel<<<(unsigned)((nz + 255) / 256), 256, 0, s>>>(nz, zk, Rk, nR, d_int);
+    if (ny > 0) targets_in_kernel<<<counted((unsigned)((ny + 255) / 256)), 256, 0, s>>>(ny, yk, Rk, nR, d_int);
+    if (nz > 0) targets_in_kernel<<<counted((unsigned)((nz + 255) / 256)), 256, 0, s>>>(nz, zk, Rk, nR, d_int);
     MRA_CUDA_TRY(cudaGetLastError());
     // the halo of the level's sources, sorted and unique
     const int64_t nh_all = In[n] * w3;
@@ -1070,7 +1080,7 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
     NS_ALLOC(d_nh, int64_t, 1);
     MRA_CUDA_TRY(cudaMemsetAsync(d_nh, 0, 8, s));
     if (nh_all > 0) {
-      halo_kernel<<<(unsigned)((nh_all + 255) / 256), 256, 0, s>>>(In[n], Ik[n], D, hal);
+      halo_kernel<<<counted((unsigned)((nh_all + 255) / 256)), 256, 0, s>>>(In[n], Ik[n], D, hal);
       MRA_CUDA_TRY(cudaGetLastError());
       size_t t1 = 0, t2 = 0;
       MRA_CUDA_TRY(cub::DeviceRadixSort::SortKeys(nullptr, t1, hal, hal_s, (int)nh_all, 0, 64, s));
@@ -1096,7 +1106,7 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
     NS_ALLOC(ref_pos, int, nR + 1);
     NS_ALLOC(leaf_pos, int, nR + 1);
     if (nR > 0) {
-      reach_kernel<<<(unsigned)((nR + 255) / 256), 256, 0, s>>>(nR, Rk, hk, nh, yk, ny, zk, nz, yi, zi, refine, leaf);
+      reach_kernel<<<counted((unsigned)((nR + 255) / 256)), 256, 0, s>>>(nR, Rk, hk, nh, yk, ny, zk, nz, yi, zi, refine, leaf);
       MRA_CUDA_TRY(cudaGetLastError());
     }
     MRA_CUDA_TRY(cudaMemsetAsync(refine + nR, 0, sizeof(int), s));
@@ -1113,7 +1123,7 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
     if (hint[0]) return fail(MRA_ERR_NUMERIC, "mra_apply_ns_tree: a level-%d apply reached a box outside the result tree", n);
     const int64_t nref = hcount[0], nleaf_here = nR - nref;
     if (nleaf_here > 0 && nR > 0) {
-      emit_leaves_kernel<<<(unsigned)nR, 128, 0, s>>>(nR, k3, Rk, R, leaf, leaf_pos, nout, cap, out->keys, out->coeffs);
+      emit_leaves_kernel<<<counted((unsigned)nR), 128, 0, s>>>(nR, k3, Rk, R, leaf, leaf_pos, nout, cap, out->keys, out->coeffs);
       MRA_CUDA_TRY(cudaGetLastError());
     }
     nout += nleaf_here;
@@ -1122,7 +1132,7 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
     NS_ALLOC(cku, uint64_t, nC);
     NS_ALLOC(cru, double, nC * k3);
     if (nref > 0) {
-      sum_down_tree_kernel<<<(unsigned)nR, 256, sh_d, s>>>(k, nR, Rk, R, refine, ref_pos, yi, yc, zi, zc, Ub, cku, cru);
+      sum_down_tree_kernel<<<counted((unsigned)nR), 256, sh_d, s>>>(k, nR, Rk, R, refine, ref_pos, yi, yc, zi, zc, Ub, cku, cru);
       MRA_CUDA_TRY(cudaGetLastError());
     }
     NS_ALLOC(cks, uint64_t, nC);
@@ -1130,13 +1140,13 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
     NS_ALLOC(idx, int, nC);
     NS_ALLOC(idx_s, int, nC);
     if (nC > 0) {
-      iota_ns_kernel<<<(unsigned)((nC + 255) / 256), 256, 0, s>>>(nC, idx);
+      iota_ns_kernel<<<counted((unsigned)((nC + 255) / 256)), 256, 0, s>>>(nC, idx);
       MRA_CUDA_TRY(cudaGetLastError());
       size_t ts = 0;
       MRA_CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, ts, cku, cks, idx, idx_s, (int)nC, 0, 64, s));
       NS_ALLOC(tmp2, unsigned char, ts);
       MRA_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp2, ts, cku, cks, idx, idx_s, (int)nC, 0, 64, s));
-      gather_rows_ns_kernel<<<(unsigned)nC, 128, 0, s>>>(nC, k3, idx_s, cru, crs);
+      gather_rows_ns_kernel<<<counted((unsigned)nC), 128, 0, s>>>(nC, k3, idx_s, cru, crs);
       MRA_CUDA_TRY(cudaGetLastError());
       drop(tmp2);
     }
@@ -1179,7 +1189,7 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
 extern "C" int mra_reconstruct(const mra_tree_view *in, mra_tree_view *out, void *stream) {
   if (!in || !out) return fail(MRA_ERR_ARG, "mra_reconstruct: NULL argument");
   if (in->n < 0 || (in->n > 0 && (!in->keys || !in->coeffs))) return fail(MRA_ERR_ARG, "mra_reconstruct: bad input");
-  if (in->k < 1 || 2 * in->k > MRA_MAX_K) return fail(MRA_ERR_ARG, "mra_reconstruct: k=%d outside 1..%d", in->k, MRA_MAX_K / 2);
+  if (in->k < 1 || in->k > MRA_MAX_K) return fail(MRA_ERR_ARG, "mra_reconstruct: k=%d outside 1..%d", in->k, MRA_MAX_K);
   if (in->n >= (1LL << 31)) return fail(MRA_ERR_ARG, "mra_reconstruct: more than 2^31 boxes");
   if (out->k != in->k || out->cap < 0 || (out->cap > 0 && (!out->keys || !out->coeffs)))
     return fail(MRA_ERR_ARG, "mra_reconstruct: bad output view");
@@ -1240,7 +1250,7 @@ extern "C" int mra_reconstruct(const mra_tree_view *in, mra_tree_view *out, void
       for (int j = 0; j < k; ++j) Ubh[(c * k + i) * k + j] = U[c * k * k + i * k + j];
   MRA_CUDA_TRY(cudaMemcpyAsync(Ub, Ubh.data(), Ubh.size() * 8, cudaMemcpyHostToDevice, s));
   RC_ALLOC(top, int, n_in);
-  top_level_kernel<<<(unsigned)((n_in + 255) / 256), 256, 0, s>>>(n_in, in->keys, top);
+  top_level_kernel<<<counted((unsigned)((n_in + 255) / 256)), 256, 0, s>>>(n_in, in->keys, top);
   MRA_CUDA_TRY(cudaGetLastError());
   RC_ALLOC(d_err, int, 1);
   MRA_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), s));
@@ -1260,7 +1270,7 @@ extern "C" int mra_reconstruct(const mra_tree_view *in, mra_tree_view *out, void
   const int64_t cap = out->cap;
   for (int n = nmin; n <= nmax; ++n) {
     // interior boxes of level n
-    interior_kernel<<<(unsigned)((n_in + 255) / 256), 256, 0, s>>>(n_in, in->keys, top, n, anc);
+    interior_kernel<<<counted((unsigned)((n_in + 255) / 256)), 256, 0, s>>>(n_in, in->keys, top, n, anc);
     MRA_CUDA_TRY(cudaGetLastError());
     size_t tt = tb;
     MRA_CUDA_TRY(cub::DeviceRadixSort::SortKeys(tmp, tt, anc, anc_s, (int)n_in, 0, 64, s));
@@ -1282,7 +1292,7 @@ extern "C" int mra_reconstruct(const mra_tree_view *in, mra_tree_view *out, void
     RC_ALLOC(tpos, int, nl + 1);
     int ntop = 0;
     if (nl > 0) {
-      top_flags_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, s>>>(lo[n], hi[n], n, top, tflag);
+      top_flags_kernel<<<counted((unsigned)((nl + 255) / 256)), 256, 0, s>>>(lo[n], hi[n], n, top, tflag);
       MRA_CUDA_TRY(cudaGetLastError());
     }
     MRA_CUDA_TRY(cudaMemsetAsync(tflag + nl, 0, sizeof(int), s));
@@ -1300,7 +1310,7 @@ extern "C" int mra_reconstruct(const mra_tree_view *in, mra_tree_view *out, void
       MRA_CUDA_TRY(cudaMemcpyAsync(uv, Cv, (size_t)nC * k3 * 8, cudaMemcpyDeviceToDevice, s));
     }
     if (ntop > 0) {
-      tops_kernel<<<(unsigned)nl, 128, 0, s>>>(lo[n], hi[n], n, top, in->keys, in->coeffs, k3, tpos, nC, uk, uv);
+      tops_kernel<<<counted((unsigned)nl), 128, 0, s>>>(lo[n], hi[n], n, top, in->keys, in->coeffs, k3, tpos, nC, uk, uv);
       MRA_CUDA_TRY(cudaGetLastError());
     }
     RC_ALLOC(rk, uint64_t, nr);
@@ -1308,18 +1318,18 @@ extern "C" int mra_reconstruct(const mra_tree_view *in, mra_tree_view *out, void
     RC_ALLOC(idx, int, nr);
     RC_ALLOC(idx_s, int, nr);
     if (nr > 0) {
-      iota_ns_kernel<<<(unsigned)((nr + 255) / 256), 256, 0, s>>>(nr, idx);
+      iota_ns_kernel<<<counted((unsigned)((nr + 255) / 256)), 256, 0, s>>>(nr, idx);
       MRA_CUDA_TRY(cudaGetLastError());
       size_t tsp = 0;
       MRA_CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tsp, uk, rk, idx, idx_s, (int)nr, 0, 64, s));
       RC_ALLOC(tmp4, unsigned char, tsp);
       MRA_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp4, tsp, uk, rk, idx, idx_s, (int)nr, 0, 64, s));
-      gather_rows_ns_kernel<<<(unsigned)nr, 128, 0, s>>>(nr, k3, idx_s, uv, rv);
+      gather_rows_ns_kernel<<<counted((unsigned)nr), 128, 0, s>>>(nr, k3, idx_s, uv, rv);
       MRA_CUDA_TRY(cudaGetLastError());
       drop(tmp4);
     }
     if (nl > 0) {  // input boxes below a top add their coefficients
-      add_inputs_kernel<<<(unsigned)nl, 128, 0, s>>>(lo[n], hi[n], n, top, in->keys, in->coeffs, k3, rk, nr, rv, d_err);
+      add_inputs_kernel<<<counted((unsigned)nl), 128, 0, s>>>(lo[n], hi[n], n, top, in->keys, in->coeffs, k3, rk, nr, rv, d_err);
       MRA_CUDA_TRY(cudaGetLastError());
     }
     // leaves out, interior boxes passed down
@@ -1330,7 +1340,7 @@ extern "C" int mra_reconstruct(const mra_tree_view *in, mra_tree_view *out, void
     MRA_CUDA_TRY(cudaMemsetAsync(inner + nr, 0, sizeof(int), s));
     MRA_CUDA_TRY(cudaMemsetAsync(leaf + nr, 0, sizeof(int), s));
     if (nr > 0) {
-      classify_kernel<<<(unsigned)((nr + 255) / 256), 256, 0, s>>>(nr, rk, ik, ni, inner, leaf);
+      classify_kernel<<<counted((unsigned)((nr + 255) / 256)), 256, 0, s>>>(nr, rk, ik, ni, inner, leaf);
       MRA_CUDA_TRY(cudaGetLastError());
     }
     size_t tsc = 0;
@@ -1344,7 +1354,7 @@ extern "C" int mra_reconstruct(const mra_tree_view *in, mra_tree_view *out, void
     MRA_CUDA_TRY(cudaStreamSynchronize(s));
     if (herr) return fail(MRA_ERR_NUMERIC, "mra_reconstruct: an input box has no place in the result");
     if (nr - ninner > 0) {
-      emit_leaves_kernel<<<(unsigned)nr, 128, 0, s>>>(nr, k3, rk, rv, leaf, lpos, nout, cap, out->keys, out->coeffs);
+      emit_leaves_kernel<<<counted((unsigned)nr), 128, 0, s>>>(nr, k3, rk, rv, leaf, lpos, nout, cap, out->keys, out->coeffs);
       MRA_CUDA_TRY(cudaGetLastError());
     }
     nout += nr - ninner;
@@ -1352,7 +1362,7 @@ extern "C" int mra_reconstruct(const mra_tree_view *in, mra_tree_view *out, void
     RC_ALLOC(nk, uint64_t, nnext);
     RC_ALLOC(nv, double, nnext * k3);
     if (ninner > 0) {
-      pass_down_kernel<<<(unsigned)nr, 256, sh_d, s>>>(k, nr, rk, rv, inner, ipos, Ub, nk, nv);
+      pass_down_kernel<<<counted((unsigned)nr), 256, sh_d, s>>>(k, nr, rk, rv, inner, ipos, Ub, nk, nv);
       MRA_CUDA_TRY(cudaGetLastError());
     }
     for (void *p : {(void *)ik, (void *)tflag, (void *)tpos, (void *)tmp3, (void *)uk, (void *)uv, (void *)rk,
@@ -1381,7 +1391,7 @@ extern "C" int mra_reconstruct(const mra_tree_view *in, mra_tree_view *out, void
 extern "C" int mra_truncate(const mra_tree_view *in, double thresh, mra_tree_view *out, double *err2, void *stream) {
   if (!in || !out) return fail(MRA_ERR_ARG, "mra_truncate: NULL argument");
   if (in->n < 0 || (in->n > 0 && (!in->keys || !in->coeffs))) return fail(MRA_ERR_ARG, "mra_truncate: bad input");
-  if (in->k < 1 || 2 * in->k > MRA_MAX_K) return fail(MRA_ERR_ARG, "mra_truncate: k=%d outside 1..%d", in->k, MRA_MAX_K / 2);
+  if (in->k < 1 || in->k > MRA_MAX_K) return fail(MRA_ERR_ARG, "mra_truncate: k=%d outside 1..%d", in->k, MRA_MAX_K);
   if (in->n >= (1LL << 31)) return fail(MRA_ERR_ARG, "mra_truncate: more than 2^31 leaves");
   if (!(thresh >= 0.0)) return fail(MRA_ERR_ARG, "mra_truncate: thresh must be >= 0");
   if (out->k != in->k || out->cap < 0 || (out->cap > 0 && (!out->keys || !out->coeffs)))
@@ -1432,7 +1442,9 @@ extern "C" int mra_truncate(const mra_tree_view *in, double thresh, mra_tree_vie
     for (int i = 0; i < k; ++i)
       for (int j = 0; j < k; ++j) Ubh[(c * k + i) * k + j] = U[c * k * k + i * k + j];
   MRA_CUDA_TRY(cudaMemcpyAsync(Ub, Ubh.data(), Ubh.size() * 8, cudaMemcpyHostToDevice, s));
-  const size_t sh = (size_t)(kk * kk * kk + k * kk * kk + k * k * kk + k3 + kk * k * k + kk * kk * k) * 8;
+  // S stays in shared memory up to k = 12 (120 k^3 bytes); above, only the filter's pieces (56 k^3)
+  const int s_smem = k <= 12 ? 1 : 0;
+  const size_t sh = (size_t)(k * kk * kk + k * k * kk + k3 + (s_smem ? kk * kk * kk : 0)) * 8;
   MRA_CUDA_TRY(cudaFuncSetAttribute(truncate_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
   TR_ALLOC(pcount, int, 1);
   // the surviving leaves of each level (device arrays) and the merged parents carried up
@@ -1462,13 +1474,13 @@ extern "C" int mra_truncate(const mra_tree_view *in, double thresh, mra_tree_vie
     TR_ALLOC(lv, double, nl * k3);
     TR_ALLOC(idx, int, nl);
     TR_ALLOC(idx_s, int, nl);
-    iota_ns_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, s>>>(nl, idx);
+    iota_ns_kernel<<<counted((unsigned)((nl + 255) / 256)), 256, 0, s>>>(nl, idx);
     MRA_CUDA_TRY(cudaGetLastError());
     size_t tsp = 0;
     MRA_CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tsp, uk, lk, idx, idx_s, (int)nl, 0, 64, s));
     TR_ALLOC(tmp, unsigned char, tsp);
     MRA_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, tsp, uk, lk, idx, idx_s, (int)nl, 0, 64, s));
-    gather_rows_ns_kernel<<<(unsigned)nl, 128, 0, s>>>(nl, k3, idx_s, uv, lv);
+    gather_rows_ns_kernel<<<counted((unsigned)nl), 128, 0, s>>>(nl, k3, idx_s, uv, lv);
     MRA_CUDA_TRY(cudaGetLastError());
     // merges into level n-1
     TR_ALLOC(gone, int, nl + 1);
@@ -1479,13 +1491,14 @@ extern "C" int mra_truncate(const mra_tree_view *in, double thresh, mra_tree_vie
     TR_ALLOC(pk, uint64_t, nl / 8 + 1);
     TR_ALLOC(pv, double, (nl / 8 + 1) * k3);
     if (n > 0) {
-      truncate_level_kernel<<<(unsigned)nl, 256, sh, s>>>(k, n, nl, lk, lv, thresh, Ub, gone, d2, pk, pv, pcount);
+      truncate_level_kernel<<<counted((unsigned)nl), 256, sh, s>>>(k, n, nl, lk, lv, thresh, Ub, gone, d2, pk, pv, pcount,
+                                                                   s_smem);
       MRA_CUDA_TRY(cudaGetLastError());
     }
     // survivors, compacted in key order
     TR_ALLOC(keep, int, nl + 1);
     TR_ALLOC(kpos, int, nl + 1);
-    keep_flags_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, s>>>(nl, gone, keep);
+    keep_flags_kernel<<<counted((unsigned)((nl + 255) / 256)), 256, 0, s>>>(nl, gone, keep);
     MRA_CUDA_TRY(cudaGetLastError());
     MRA_CUDA_TRY(cudaMemsetAsync(keep + nl, 0, sizeof(int), s));
     size_t tsc = 0;
@@ -1507,7 +1520,7 @@ extern "C" int mra_truncate(const mra_tree_view *in, double thresh, mra_tree_vie
     TR_ALLOC(kk_, uint64_t, nkeep);
     TR_ALLOC(kv, double, (int64_t)nkeep * k3);
     if (nkeep > 0) {
-      emit_leaves_kernel<<<(unsigned)nl, 128, 0, s>>>(nl, k3, lk, lv, keep, kpos, 0, nkeep, kk_, kv);
+      emit_leaves_kernel<<<counted((unsigned)nl), 128, 0, s>>>(nl, k3, lk, lv, keep, kpos, 0, nkeep, kk_, kv);
       MRA_CUDA_TRY(cudaGetLastError());
     }
     keep_k[n] = kk_;

@@ -300,7 +300,7 @@ cudaError_t upload_gl() {
 
 cudaError_t launch_fit_search(double mu, int M, double r_lo, double r_hi, double *d_err,
                               cudaStream_t s) {
-  fit_search_kernel<<<FIT_NH * FIT_NS, 256, 2 * M * sizeof(double), s>>>(mu, M, r_lo, r_hi, d_err);
+  fit_search_kernel<<<counted(FIT_NH * FIT_NS), 256, 2 * M * sizeof(double), s>>>(mu, M, r_lo, r_hi, d_err);
   return cudaGetLastError();
 }
 
@@ -312,7 +312,7 @@ cudaError_t launch_blocks(const Operator &op, const double *d_glxk, const double
   size_t smem = (size_t)(2 * ZB * kq * op.k + ZB * kq) * sizeof(double);
   int threads = 256;
   int nlev = op.max_level - op.min_level + 1;
-  blocks_kernel<<<(unsigned)op.n_blocks, threads, smem, s>>>(op.k, op.L, op.min_level, nlev, op.d_D,
+  blocks_kernel<<<counted((unsigned)op.n_blocks), threads, smem, s>>>(op.k, op.L, op.min_level, nlev, op.d_D,
                                                              op.d_level_off, op.d_t, op.M, d_glxk,
                                                              d_glwk, op.d_R, op.d_N);
   return cudaGetLastError();
@@ -328,7 +328,7 @@ cudaError_t launch_project_boxes(int ng, const double *d_g, int k, double L, int
     e = cudaFuncSetAttribute(project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  project_kernel<<<(unsigned)nbox, 256, smem, s>>>(ng, d_g, k, L, d_keys, d_out);
+  project_kernel<<<counted((unsigned)nbox), 256, smem, s>>>(ng, d_g, k, L, d_keys, d_out);
   return cudaGetLastError();
 }
 
@@ -342,7 +342,7 @@ cudaError_t launch_refine_test(int k, int64_t nparent, const double *d_parent,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  refine_test_kernel<<<(unsigned)nparent, 256, smem, s>>>(k, d_parent, d_child, d_U, d_dnorm);
+  refine_test_kernel<<<counted((unsigned)nparent), 256, smem, s>>>(k, d_parent, d_child, d_U, d_dnorm);
   return cudaGetLastError();
 }
 

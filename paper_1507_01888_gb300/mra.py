@@ -40,7 +40,7 @@ EXPORTED = [
     "mra_apply", "mra_apply_batched", "mra_norm", "mra_norm_noalloc", "mra_compare", "mra_log_terms", "mra_mlp_init",
     "mra_mlp_standardize", "mra_mlp_forward", "mra_mlp_workspace_size", "mra_mlp_grad", "mra_mlp_train",
     "mra_operator_ns_create", "mra_apply_ns_workspace_size", "mra_apply_ns", "mra_apply_ns_tree",
-    "mra_reconstruct", "mra_truncate", "mra_multiply", "mra_inner",
+    "mra_reconstruct", "mra_truncate", "mra_multiply", "mra_inner", "mra_launch_count",
 ]
 NOALLOC_MAX_BOXES = 1 << 20
 
@@ -73,7 +73,8 @@ class ApplyStats(ctypes.Structure):
                 ("terms_kept", ctypes.c_int64), ("terms_screened", ctypes.c_int64),
                 ("terms_issued", ctypes.c_int64), ("sources_truncated", ctypes.c_int64),
                 ("skipped_bound", ctypes.c_double), ("kernel_ms", ctypes.c_double),
-                ("terms_learned_skipped", ctypes.c_int64), ("learned_skipped_bound", ctypes.c_double)]
+                ("terms_learned_skipped", ctypes.c_int64), ("learned_skipped_bound", ctypes.c_double),
+                ("algo_flops", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -111,6 +112,7 @@ def load(build_if_stale: bool = True):
         vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
         lib.mra_last_error.restype = ctypes.c_char_p
         lib.mra_version.restype = ctypes.c_char_p
+        lib.mra_launch_count.restype = ctypes.c_longlong
         lib.mra_project.argtypes = [P(GaussSum), i, d, d, i, i, i, P(TreeView), vp]
         lib.mra_operator_create.argtypes = [i, d, i, d, d, d, i, d, i, i, i, P(vp), vp]
         lib.mra_operator_fit.argtypes = [vp, P(d), P(d), P(d), P(d), P(d)]
@@ -572,6 +574,11 @@ def multiply(a: "Tree", b: "Tree", stream=None) -> "Tree":
         _check(rc)
         out.n = int(vo.n)
         return out
+
+
+def launch_count() -> int:
+    """mra_launch_count: kernels the library has launched in this process so far."""
+    return int(load().mra_launch_count())
 
 
 def inner(a: "Tree", b: "Tree", stream=None) -> float:

@@ -27,9 +27,10 @@ def project_potential(Z: float, k: int, L: float, thresh: float, M: int = 100, d
 
 
 def bsh_step(V, psi, E: float, thresh: float, M_bsh: int = 60, fit_eps: float = 1e-6,
-             precision: int = mra.PREC_SPLIT_BF16, screen: bool = True, max_disp: int = 1):
+             precision: int = mra.PREC_SPLIT_BF16, screen: bool = True, max_disp: int = 1, info=None):
     """One step of the fixed-point iteration: psi~ = -2 G_E (V psi) on the adaptive tree, truncated
-    at `thresh`; returns (E + dE, psi~ normalised, dE) with dE = -<V psi, psi - psi~> / <psi~, psi~>."""
+    at `thresh`; returns (E + dE, psi~ normalised, dE) with dE = -<V psi, psi - psi~> / <psi~, psi~>.
+    If `info` is a dict it receives the non-standard apply's statistics and the tree sizes."""
     k, L = psi.k, psi.L
     Vpsi = mra.multiply(V, psi)
     top = int((Vpsi.keys[: Vpsi.n] >> 57).max().item())
@@ -41,7 +42,7 @@ def bsh_step(V, psi, E: float, thresh: float, M_bsh: int = 60, fit_eps: float = 
                              screen=mra.SCREEN_NORM, tau=0.01 * thresh)
     else:
         opts = mra.make_opts(precision=precision, stencil=mra.STENCIL_SHELLS, max_disp=max_disp)
-    r, _ = mra.apply_ns_tree(op, ns, Vpsi, 1, opts)
+    r, st = mra.apply_ns_tree(op, ns, Vpsi, 1, opts)
     r.coeffs[: r.n] *= -1.0 / (2.0 * math.pi)
     new, _ = mra.truncate(r, thresh)
     vp = mra.inner(Vpsi, psi)
@@ -49,6 +50,8 @@ def bsh_step(V, psi, E: float, thresh: float, M_bsh: int = 60, fit_eps: float = 
     nn = mra.inner(new, new)
     dE = -(vp - vn) / nn
     new.coeffs[: new.n] /= math.sqrt(nn)
+    if info is not None:
+        info.update(apply_stats=st, n_vpsi=Vpsi.n, n_result=r.n, n_psi=new.n)
     return E + dE, new, dE
 
 

@@ -17,7 +17,7 @@ def mra():
     return m
 
 
-@pytest.mark.parametrize("k", [3, 6, 8])
+@pytest.mark.parametrize("k", [3, 6, 8, 10, 14])
 def test_reconstruct_of_the_leaf_level_apply(mra, k):
     L = 8.0
     f = W.gaussian_sum(2, 1.0, 20.0, seed=11, centre_box=3.0)
@@ -56,7 +56,8 @@ def test_reconstruct_edge_cases(mra):
         mra.reconstruct(mra.Tree.from_host(bad, c1, L))
 
 
-@pytest.mark.parametrize("k,thresh", [(4, 1e-5), (4, 1e-3), (6, 1e-4), (8, 1e-4)])
+@pytest.mark.parametrize("k,thresh", [(4, 1e-5), (4, 1e-3), (6, 1e-4), (8, 1e-4), (10, 1e-4), (12, 1e-5),
+                                      (14, 1e-5)])
 def test_truncate_matches_oracle(mra, k, thresh):
     L = 8.0
     f = W.gaussian_sum(3, 1.0, 30.0, seed=17, centre_box=3.0)
@@ -87,7 +88,7 @@ def test_reconstruct_then_truncate_keeps_the_error_bound(mra):
 
 # ----------------------------------------------------------------- products and inner products
 
-@pytest.mark.parametrize("k", [4, 6, 8])
+@pytest.mark.parametrize("k", [4, 6, 8, 10])
 def test_multiply_and_inner_match_oracle(mra, k):
     L = 8.0
     fa = W.gaussian_sum(2, 1.0, 20.0, seed=11, centre_box=3.0)

@@ -139,6 +139,26 @@ def bsh_ns_adaptive_k8() -> Workload:
                     extra={"ns": {"n0": 1}})
 
 
+def bsh_k10_reconstruct_truncate() -> Workload:
+    """Sum-down and truncation (Sec. 2.1-2.2) of the mixed-precision BSH workload's leaf-level
+    apply result: the multi-level box sum is summed down into disjoint leaves (mra_reconstruct)
+    and coarsened where the detail is below the projection threshold 1e-6 (mra_truncate)."""
+    w = bsh_m60_adaptive_k10()
+    w.name = "bsh_m60_k10_reconstruct_truncate"
+    w.extra = {"post": {"truncate_thresh": 1e-6}}
+    return w
+
+
+def hydrogen_bsh_k6() -> Workload:
+    """The bound-state Helmholtz fixed-point solve (Sec. 3.2) for Z = 1 in [-20, 20]^3: k=6,
+    thresh 1e-4, -1/r as the 100-term 1/r fit, exp(-mu r)/r as 60 Gaussians (fit 1e-6), the
+    non-standard apply with |l|_inf <= 1 per level and the norm screen at thresh/100.  A step
+    is one iteration at the converged state."""
+    return Workload("hydrogen_bsh_k6", [], k=6, L=20.0, thresh=1e-4, uniform_level=-1, kernel=BSH, mu=1.0,
+                    M=60, fit_eps=1e-6, stencil=0, max_disp=1, tau=1e-6,
+                    extra={"solver": {"Z": 1.0, "E0": -0.4, "M_potential": 100}})
+
+
 def shard(w: Workload, rank: int, world: int) -> Workload:
     """The workload rank `rank` of `world` runs.  Families of independent functions give every
     rank its own part (same size: weak scaling, no exchange between ranks); a single-function
@@ -158,6 +178,8 @@ WORKLOADS = {
     "poisson_m100_adaptive_k14": poisson_k14_large,
     "poisson_ns_uniform_l5_k6": poisson_ns_uniform_k6,
     "bsh_ns_adaptive_k8": bsh_ns_adaptive_k8,
+    "bsh_m60_k10_reconstruct_truncate": bsh_k10_reconstruct_truncate,
+    "hydrogen_bsh_k6": hydrogen_bsh_k6,
 }
 
 
