@@ -271,6 +271,7 @@ def run_ns(args, w, rank, world):
         ref = make(mra.make_opts(stencil=mra.STENCIL_SHELLS, max_disp=D))
         cmp = mra.compare(ap(tree), ref(tree))
         accuracy = {"rel_l2_vs_fp64_gpu": cmp["rel_l2"], "max_box_rel_vs_fp64_gpu": cmp["max_box_rel"],
+                    "per_level_rel_l2_vs_fp64_gpu": {str(x["level"]): x["rel_l2"] for x in cmp["levels"]},
                     "fp64_gpu_apply_ms": ref.stats.kernel_ms,
                     "speedup_vs_fp64_gpu_kernel": ref.stats.kernel_ms / max(ap.stats.kernel_ms, 1e-9)}
         del ref
@@ -650,9 +651,12 @@ def main():
         model, linfo = learned.train_screen(op, train_trees, opts, terms_per_tree=20000, steps=2000,
                                             batch=1024, lr=3e-3, seed=0, quantile=args.learned_quantile)
         opts = mra.make_opts(precision=prec, pieces=args.pieces, screen=mra.SCREEN_LEARNED, tau=w.tau,
-                             stencil=w.stencil, max_disp=w.max_disp, mlp=model, delta=linfo["delta"])
+                             stencil=w.stencil, max_disp=w.max_disp, mlp=model, delta=linfo["delta"],
+                             delta_level=linfo["delta_level"])
         learned_cfg = {"training_functions": len(train_trees), "logged_terms": linfo["n_train"] + linfo["n_val"],
-                       "final_loss": linfo["final_loss"], "delta": linfo["delta"], "quantile": args.learned_quantile}
+                       "final_loss": linfo["final_loss"], "delta": linfo["delta"], "quantile": args.learned_quantile,
+                       "delta_level": {str(n): d for n, d in enumerate(linfo["delta_level"]) if d != float("inf")},
+                       "held_out_terms_per_level": {str(n): c for n, c in linfo["val_per_level"].items()}}
         del train_trees
     tuning = {}
     if prec == mra.PREC_SPLIT_BF16:
@@ -688,6 +692,7 @@ def main():
             ref_out, ref_offs = ref_ap(tree)
             _, offs_out = ap(tree)
             d2 = r2 = mx = 0.0
+            lev = {}
             for f in range(len(trees)):
                 def sl(t, o):
                     return mra.Tree(t.keys[o[f]:o[f + 1]], t.coeffs[o[f]:o[f + 1]], o[f + 1] - o[f], t.k, t.L)
@@ -697,20 +702,34 @@ def main():
                 d2 += c["diff_norm"] ** 2
                 r2 += c["ref_norm"] ** 2
                 mx = max(mx, c["max_box_rel"])
-            cmp = {"rel_l2": (d2 / r2) ** 0.5 if r2 > 0 else 0.0, "max_box_rel": mx}
+                for x in c["levels"]:
+                    a_ = lev.setdefault(x["level"], [0.0, 0.0, 0])
+                    a_[0] += x["diff_norm"] ** 2
+                    a_[1] += x["ref_norm"] ** 2
+                    a_[2] += x["ref_boxes"]
+            cmp = {"rel_l2": (d2 / r2) ** 0.5 if r2 > 0 else 0.0, "max_box_rel": mx,
+                   "levels": [{"level": n, "rel_l2": (v[0] / v[1]) ** 0.5 if v[1] > 0 else v[0] ** 0.5,
+                               "ref_boxes": v[2]} for n, v in sorted(lev.items())]}
         else:
             ref_out = run(ref_ap, tree)
             cmp = mra.compare(ap.out, ref_out)
         accuracy = {"rel_l2_vs_fp64_gpu": cmp["rel_l2"], "max_box_rel_vs_fp64_gpu": cmp["max_box_rel"],
+                    "per_level_rel_l2_vs_fp64_gpu": {str(x["level"]): x["rel_l2"] for x in cmp["levels"]},
                     "fp64_gpu_apply_ms": ref_ap.stats.kernel_ms,
                     "speedup_vs_fp64_gpu_kernel": ref_ap.stats.kernel_ms / max(ap.stats.kernel_ms, 1e-9)}
         del ref_out, ref_ap
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    graph = None
+    if batched:  # the whole batched apply recorded once as a CUDA graph, one launch per step
+        graph = mra.ApplyGraph(op, tree, opts, offsets=offsets, stream=stream)
 
     def step():
-        ap(tree, stream)
+        if graph is not None:
+            graph.launch(stream)
+        else:
+            ap(tree, stream)
 
     for _ in range(args.warmup):
         flush.fill_(1.0)
@@ -729,10 +748,16 @@ def main():
         ev[i][0].record(stream)
         step()
         ev[i][1].record(stream)
-        kernel_ms.append(ap.stats.kernel_ms)
+        if graph is None:
+            kernel_ms.append(ap.stats.kernel_ms)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
     launches = mra.launch_count() - launches0
+    if graph is not None:
+        graph.status(stream)  # every replay kept the recorded sizes
+        for _ in range(3):  # the apply kernel's own time, from plain applies of the same input
+            ap(tree, stream)
+            kernel_ms.append(ap.stats.kernel_ms)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -752,9 +777,14 @@ def main():
     out_coeffs_pin = torch.empty((n_out, k, k, k), dtype=torch.float64).pin_memory()
 
     def e2e_step():
-        dev_tree.keys.copy_(keys_pin, non_blocking=True)
-        dev_tree.coeffs.copy_(coeffs_pin, non_blocking=True)
-        out = run(ap, dev_tree) if not batched else ap(dev_tree, stream)[0]
+        if graph is not None:  # the graph reads the tree's own buffers
+            tree.keys[:n_in].copy_(keys_pin, non_blocking=True)
+            tree.coeffs[:n_in].copy_(coeffs_pin, non_blocking=True)
+            out = graph.launch(stream)
+        else:
+            dev_tree.keys.copy_(keys_pin, non_blocking=True)
+            dev_tree.coeffs.copy_(coeffs_pin, non_blocking=True)
+            out = run(ap, dev_tree)
         out_keys_pin.copy_(out.keys[:n_out], non_blocking=True)
         out_coeffs_pin.copy_(out.coeffs[:n_out], non_blocking=True)
 
@@ -769,6 +799,8 @@ def main():
         b.record(stream)
         b.synchronize()
         e_ms.append(a.elapsed_time(b))
+    if graph is not None:
+        graph.status(stream)
     _, e2e_ms = reduce_over_ranks(n_in, statistics.mean(e_ms), world, dev)
     e2e_val = n_all / (e2e_ms / 1e3)
     h2d = keys_pin.numel() * 8 + coeffs_pin.numel() * 8
@@ -804,6 +836,8 @@ def main():
                        "terms_kept": terms, "pairs": st0["pairs"], "n_out": st0["n_out"],
                        "precision": precision, "l2": "flushed by a 256 MB write before every step",
                        "functions": len(trees), "tuning": tuning,
+                       **({"launch": f"one CUDA graph per step ({graph.kernels_per_launch} library kernels "
+                                     "recorded: norms, screen, sorts, apply)"} if graph is not None else {}),
                        **({"learned_screen": dict(learned_cfg, terms_skipped=st0["terms_learned_skipped"],
                                                   skipped_bound=st0["learned_skipped_bound"])}
                           if learned_cfg else {}),

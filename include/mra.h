@@ -105,6 +105,9 @@ typedef struct {
   int tile_variant; /* MRA_PREC_SPLIT_BF16 tile shape: 0 = four 128-row tiles per CTA (one CTA
                        per SM); 1 (k >= 4) = two tiles per CTA (two CTAs per SM); 2 (k = 4 to
                        10) = one tile per CTA (four CTAs per SM); others are taken as 0 */
+  const double *delta_level; /* MRA_SCREEN_LEARNED, optional (NULL = delta at every level): host
+                                array of MRA_MAX_LEVEL + 1 margins, one per source level, read
+                                during the call; +inf keeps every term of that level */
 } mra_apply_opts;
 
 typedef struct {
@@ -131,6 +134,12 @@ typedef struct {
   double max_box_rel;/* max over common boxes of ||test_b - ref_b|| / ||ref_b|| */
   int64_t n_common;  /* boxes present in both trees */
   int64_t n_only_test, n_only_ref;
+  /* per level n = 0..MRA_MAX_LEVEL: || test - ref ||_2 and || ref ||_2 over the boxes of level n
+     (boxes present in only one tree count with the other side as zero) and the number of boxes
+     of level n in ref */
+  double level_diff_norm[MRA_MAX_LEVEL + 1];
+  double level_ref_norm[MRA_MAX_LEVEL + 1];
+  int64_t level_ref_boxes[MRA_MAX_LEVEL + 1];
 } mra_compare_result;
 
 /* ---- calls ---------------------------------------------------------------- */
@@ -359,6 +368,29 @@ int mra_multiply(const mra_tree_view *a, const mra_tree_view *b, mra_tree_view *
 /* Inner product <a, b> = integral of a b, the coefficient dot product over the two trees'
  * common leaves (orthonormal basis); deterministic reduction, *result on the host. */
 int mra_inner(const mra_tree_view *a, const mra_tree_view *b, double *result, void *stream);
+
+/* ---- graph-captured apply --------------------------------------------------------------
+ * An apply (nfunc == 1: as mra_apply; nfunc > 1: as mra_apply_batched, in_offsets and
+ * out_offsets as there) recorded once as a CUDA graph and replayed with one launch.  Create
+ * runs the apply once (its result is in `out` on return), learns its sizes (records after the
+ * screen, destination boxes) and records the whole sequence -- norms, screen, sorts, the apply
+ * kernel -- in a fixed-size mode without host synchronisation.  A replay reads in->keys and
+ * in->coeffs and writes out->keys and out->coeffs at the addresses given here, so the caller
+ * may change the input coefficients between replays (same in->n).  The workspace stays owned
+ * by the graph until mra_apply_graph_free.  Every replay checks on the device that its record
+ * and destination counts equal the recorded ones; mra_apply_graph_status synchronises the
+ * stream, returns MRA_ERR_CAPACITY if any replay since the last call needed other sizes (its
+ * output is then not valid: create the graph again), MRA_ERR_TIMEOUT if a tensor-core wait
+ * gave up, and clears the record.  Statistics are not gathered by replays. */
+typedef struct mra_apply_graph mra_apply_graph; /* opaque */
+int mra_apply_graph_create(const mra_operator *op, int nfunc, const mra_tree_view *in, const int64_t *in_offsets,
+                           const mra_apply_opts *opts, mra_tree_view *out, int64_t *out_offsets, void *workspace,
+                           size_t workspace_bytes, mra_apply_graph **graph, void *stream);
+int mra_apply_graph_launch(mra_apply_graph *graph, void *stream);
+int mra_apply_graph_status(mra_apply_graph *graph, void *stream);
+/* Destination boxes of the recorded apply and the library kernels one replay launches. */
+int mra_apply_graph_info(const mra_apply_graph *graph, int64_t *n_out, long long *kernels_per_launch);
+int mra_apply_graph_free(mra_apply_graph *graph);
 
 /* Per-box Frobenius norms (device array of tree->n doubles, may be NULL) and
  * the total L2 norm (host double, may be NULL).  Deterministic reduction. */

@@ -34,10 +34,8 @@ def tune(op, tree, opts, repeats: int = 3, verbose: bool = False, make_applier=N
         best = _cache[key]
     else:
         for v in candidates(op.k):
-            o = mra.ApplyOpts.from_buffer_copy(opts)
+            o = mra.copy_opts(opts)
             o.tile_variant = v
-            if getattr(opts, "_mlp_ref", None) is not None:
-                o._mlp_ref = opts._mlp_ref
             ap = make_applier(o)
             ap(tree)  # warm-up
             ms = []
@@ -49,8 +47,6 @@ def tune(op, tree, opts, repeats: int = 3, verbose: bool = False, make_applier=N
                 print(f"tile_variant={v}: {table[v]:.3f} ms")
         best = min(table, key=table.get)
         _cache[key] = best
-    o = mra.ApplyOpts.from_buffer_copy(opts)
+    o = mra.copy_opts(opts)
     o.tile_variant = best
-    if getattr(opts, "_mlp_ref", None) is not None:
-        o._mlp_ref = opts._mlp_ref
     return o, table

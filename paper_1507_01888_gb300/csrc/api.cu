@@ -131,6 +131,7 @@ __global__ void iota32(int64_t n, int *p) {
 
 std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_total() { return g_launches.load(std::memory_order_relaxed); }
 
 }  // namespace mra
 

@@ -88,7 +88,7 @@ struct ScreenArgs {
   // learned screen (MRA_SCREEN_LEARNED): drop a kept term when mlp(features) < learned_cut
   const float *mlp;
   const double *t;            // Gaussian exponents (features)
-  float learned_cut;          // log10(tau) - delta
+  float learned_cut[MRA_MAX_LEVEL + 1];  // per source level: log10(tau) - delta (-inf: keep all)
   int64_t *box_learned;
   double *box_lbound;
   // the network's inputs depend on the displacement only through |l|^2: pass 0 evaluates it
@@ -170,7 +170,7 @@ __global__ void screen_kernel(ScreenArgs a) {
             bool dr = false;
             if (m < a.M) {
               float f[4] = {(float)n, sqrtf((float)q), (float)log10(a.t[m]), log_sn};
-              dr = mlp_predict(mlp_sh, f) < a.learned_cut;
+              dr = mlp_predict(mlp_sh, f) < a.learned_cut[n];
             }
             const uint64_t bal = (uint64_t)__ballot_sync(0xffffffffu, dr) << (m0 & 63);
             if (m0 < 64) w0 |= bal; else w1 |= bal;
@@ -217,7 +217,7 @@ __global__ void screen_kernel(ScreenArgs a) {
                 } else {  // wide stencils: evaluate the network for this term (pass 0 only
                           // sees the parameters in shared memory; pass 1 reads them from global)
                   float f[4] = {(float)n, sqrtf((float)q), (float)log10(a.t[m]), log_sn};
-                  dr = mlp_predict(PASS == 0 ? (const float *)mlp_sh : a.mlp, f) < a.learned_cut;
+                  dr = mlp_predict(PASS == 0 ? (const float *)mlp_sh : a.mlp, f) < a.learned_cut[n];
                 }
                 if (dr) {
                   keep = false;
@@ -430,6 +430,47 @@ __global__ void compare_kernel(int64_t nt, const uint64_t *tk, const double *tc,
   }
 }
 
+// Fixed-size (graph) mode: the record count the screen computed against the captured one.
+__global__ void fixed_count_check_kernel(const int64_t *off, const int64_t *cnt, int64_t n_in, int64_t P,
+                                         const int *d_err, int *status) {
+  int st = 0;
+  if (off[n_in - 1] + cnt[n_in - 1] != P) st |= 1;
+  if (*d_err) st |= 4;
+  if (st) atomicOr(status, st);
+}
+__global__ void fixed_dest_check_kernel(const int64_t *ndest, int64_t nd, int *status) {
+  if (*ndest != nd) atomicOr(status, 2);
+}
+
+// One CTA per level n: the sum of v over the boxes of level n (keys sorted, so the level's boxes
+// are contiguous), reduced in a fixed order (deterministic).
+__global__ void level_sum_kernel(int64_t n, const uint64_t *keys, const double *v, double *out,
+                                 int64_t *count) {
+  __shared__ double red[32];
+  const int lev = blockIdx.x;
+  auto lower = [&](uint64_t key) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (keys[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+  };
+  const int64_t b0 = lower((uint64_t)lev << 57);
+  const int64_t b1 = lev >= MRA_MAX_LEVEL ? n : lower((uint64_t)(lev + 1) << 57);
+  double s = 0.0;
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += v[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    out[lev] = t;
+    if (count) count[lev] = b1 - b0;
+  }
+}
+
 __global__ void ref_only_kernel(int64_t nr, const uint64_t *rk, const double *rc, int64_t nt,
                                 const uint64_t *tk, int k3, double *r2_all, double *r2_only,
                                 int *only) {
@@ -594,7 +635,8 @@ static WsPtrs carve(const Layout &L, void *ws) {
 // Source norms, norm (and learned) screen, record counts, scan and record emission.
 // On return *P_out holds the number of records (written in source order).
 static int screen_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts &o, const WsPtrs &w,
-                      int64_t Pmax, mra_apply_stats *stats, int64_t *P_out, cudaStream_t s, int nfunc = 1) {
+                      int64_t Pmax, mra_apply_stats *stats, int64_t *P_out, cudaStream_t s, int nfunc = 1,
+                      const FixedSizes *fx = nullptr) {
   const int k = op.k, k3 = k * k * k;
   const int64_t n_in = in.n;
   // error flag lives in the first word of the dest-count slot until it is used
@@ -632,7 +674,10 @@ static int screen_run(const Operator &op, const mra_tree_view &in, const mra_app
   a.err = d_err;
   a.mlp = o.screen == MRA_SCREEN_LEARNED ? o.mlp : nullptr;
   a.t = op.d_t;
-  a.learned_cut = (float)(log10(o.tau) - o.delta);
+  for (int n = 0; n <= MRA_MAX_LEVEL; ++n) {
+    const double dl = o.delta_level ? o.delta_level[n] : o.delta;
+    a.learned_cut[n] = isinf(dl) && dl > 0 ? -INFINITY : (float)(log10(o.tau) - dl);
+  }
   a.box_learned = w.blearned;
   a.box_lbound = w.blbound;
   a.learned_drop = w.ldrop;
@@ -644,6 +689,16 @@ static int screen_run(const Operator &op, const mra_tree_view &in, const mra_app
   void *tmp = w.tmp;
   size_t tmpb = w.tmpb;
   MRA_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, tmpb, w.cnt, w.off, (int)n_in, s));
+  if (fx) {  // graph mode: the captured record count, checked on the device
+    fixed_count_check_kernel<<<counted(1), 1, 0, s>>>(w.off, w.cnt, n_in, fx->P, d_err, fx->status);
+    MRA_CUDA_TRY(cudaGetLastError());
+    if (fx->P > 0) {
+      screen_kernel<1><<<counted(gboxes), 32 * wpb, ssm, s>>>(a);
+      MRA_CUDA_TRY(cudaGetLastError());
+    }
+    *P_out = fx->P;
+    return MRA_OK;
+  }
   // statistics reduced on the device (deterministic), read with the record count
   int64_t *red_i = w.seg;  // seg is free until the segments pass
   double *red_d = (double *)(w.seg + 4);
@@ -699,7 +754,8 @@ static int screen_run(const Operator &op, const mra_tree_view &in, const mra_app
 
 int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts &o,
               mra_tree_view &out, void *ws, size_t ws_bytes, mra_apply_stats *stats,
-              cudaStream_t s, int nfunc, const int64_t *in_offsets, int64_t *out_offsets) {
+              cudaStream_t s, int nfunc, const int64_t *in_offsets, int64_t *out_offsets,
+              const FixedSizes *fx) {
   const int k = op.k, k3 = k * k * k;
   const int64_t n_in = in.n;
   const int64_t Pmax = apply_max_records(op, o, n_in);
@@ -713,17 +769,22 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
   int64_t *seg = W.seg, *ndest = W.ndest;
   void *tmp = W.tmp;
   size_t tmpb = W.tmpb;
-  if (out_offsets)
+  if (fx) stats = nullptr;  // graph mode: nothing is read back
+  if (out_offsets && !fx)
     for (int f = 0; f <= nfunc; ++f) out_offsets[f] = 0;
   if (n_in == 0) {
     out.n = 0;
     if (stats) *stats = mra_apply_stats{};
     return MRA_OK;
   }
-  if (nfunc > 1)
-    MRA_CUDA_TRY(cudaMemcpyAsync(W.fnoff, in_offsets, (nfunc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  if (nfunc > 1) {
+    if (fx)
+      MRA_CUDA_TRY(cudaMemcpyAsync(W.fnoff, fx->d_in_offsets, (nfunc + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    else
+      MRA_CUDA_TRY(cudaMemcpyAsync(W.fnoff, in_offsets, (nfunc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  }
   int64_t P = 0;
-  int rc0 = screen_run(op, in, o, W, Pmax, stats, &P, s, nfunc);
+  int rc0 = screen_run(op, in, o, W, Pmax, stats, &P, s, nfunc, fx);
   if (rc0 != MRA_OK) return rc0;
   if (P == 0) {
     out.n = 0;
@@ -742,14 +803,22 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
     MRA_CUDA_TRY(cudaGetLastError());
   }
   int64_t nd = 0;
-  MRA_CUDA_TRY(cudaMemcpyAsync(&nd, ndest, 8, cudaMemcpyDeviceToHost, s));
-  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  if (fx) {
+    fixed_dest_check_kernel<<<counted(1), 1, 0, s>>>(ndest, fx->nd, fx->status);
+    MRA_CUDA_TRY(cudaGetLastError());
+    nd = fx->nd;
+  } else {
+    MRA_CUDA_TRY(cudaMemcpyAsync(&nd, ndest, 8, cudaMemcpyDeviceToHost, s));
+    MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  }
   if (nd > out.cap) {
     out.n = nd;
     return fail(MRA_ERR_CAPACITY, "mra_apply: output holds %lld boxes, %lld needed",
                 (long long)out.cap, (long long)nd);
   }
-  if (nfunc > 1 && out_offsets) {  // first destination of each function (destinations sorted by function)
+  if (fx) {
+    // graph mode: the output offsets of the sizing run stand
+  } else if (nfunc > 1 && out_offsets) {  // first destination of each function (destinations sorted by function)
     func_offsets_kernel<<<counted(1), 256, 0, s>>>(nd, W.dfunc, nfunc, W.fnoff);
     MRA_CUDA_TRY(cudaGetLastError());
     MRA_CUDA_TRY(cudaMemcpyAsync(out_offsets, W.fnoff, (nfunc + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -779,6 +848,7 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
   wk.split_ws_bytes = L.split_bytes;
   wk.ev0 = ev0;
   wk.ev1 = ev1;
+  wk.fx = fx;
   if (o.precision == MRA_PREC_FP64) {
     if (ev0) MRA_CUDA_TRY(cudaEventRecord(ev0, s));
     size_t smem = (size_t)(3 * k3 + 3 * k * k) * sizeof(double);
@@ -1021,6 +1091,10 @@ int compare_run(const mra_tree_view &t, const mra_tree_view &r, mra_compare_resu
   int *match = (int *)(buf + 6 * per), *only = (int *)(buf + 7 * per);
   void *tmp = buf + 8 * per;
   double *sums = (double *)(buf + 8 * per + align_up(tmpb));  // 8 doubles
+  constexpr int NLEV = MRA_MAX_LEVEL + 1;
+  double *lev = nullptr;  // per level: test diff^2, ref-only diff^2, ref^2; ref box counts
+  MRA_CUDA_TRY(cudaMallocAsync((void **)&lev, 4 * NLEV * sizeof(double), s));
+  MRA_CUDA_TRY(cudaMemsetAsync(lev, 0, 4 * NLEV * sizeof(double), s));
   const int wpb = 8;
   MRA_CUDA_TRY(cudaMemsetAsync(sums, 0, 8 * sizeof(double), s));
   if (nt > 0) {
@@ -1031,6 +1105,8 @@ int compare_run(const mra_tree_view &t, const mra_tree_view &r, mra_compare_resu
     MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, t2, sums + 1, (int)nt, s));
     MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, match, (int *)(sums + 4), (int)nt, s));
     max_kernel_single<<<counted(1), 1024, 0, s>>>(nt, rel, sums + 5);
+    level_sum_kernel<<<counted(NLEV), 256, 0, s>>>(nt, t.keys, d2, lev, nullptr);
+    MRA_CUDA_TRY(cudaGetLastError());
   }
   if (nr > 0) {
     ref_only_kernel<<<counted((unsigned)((nr + wpb - 1) / wpb)), 32 * wpb, 0, s>>>(nr, r.keys, r.coeffs, nt,
@@ -1039,11 +1115,25 @@ int compare_run(const mra_tree_view &t, const mra_tree_view &r, mra_compare_resu
     MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, ra, sums + 2, (int)nr, s));
     MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, ro, sums + 3, (int)nr, s));
     MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, only, (int *)(sums + 6), (int)nr, s));
+    level_sum_kernel<<<counted(NLEV), 256, 0, s>>>(nr, r.keys, ro, lev + NLEV, nullptr);
+    MRA_CUDA_TRY(cudaGetLastError());
+    level_sum_kernel<<<counted(NLEV), 256, 0, s>>>(nr, r.keys, ra, lev + 2 * NLEV, (int64_t *)(lev + 3 * NLEV));
+    MRA_CUDA_TRY(cudaGetLastError());
   }
   double h[8];
+  double hl[4 * NLEV];
   MRA_CUDA_TRY(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s));
+  MRA_CUDA_TRY(cudaMemcpyAsync(hl, lev, sizeof(hl), cudaMemcpyDeviceToHost, s));
   MRA_CUDA_TRY(cudaFreeAsync(buf, s));
+  MRA_CUDA_TRY(cudaFreeAsync(lev, s));
   MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int n = 0; n < NLEV; ++n) {
+    res->level_diff_norm[n] = sqrt(hl[n] + hl[NLEV + n]);
+    res->level_ref_norm[n] = sqrt(hl[2 * NLEV + n]);
+    int64_t c = 0;
+    memcpy(&c, &hl[3 * NLEV + n], sizeof(int64_t));
+    res->level_ref_boxes[n] = c;
+  }
   int n_common = 0, n_only_ref = 0;
   memcpy(&n_common, &h[4], sizeof(int));
   memcpy(&n_only_ref, &h[6], sizeof(int));

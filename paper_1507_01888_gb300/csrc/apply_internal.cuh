@@ -5,6 +5,17 @@
 
 namespace mra {
 
+// Fixed-size mode, used when an apply is recorded into a CUDA graph: no host synchronisation;
+// the record count P and destination count nd of an earlier run of the same input are used as
+// the sizes, and kernels compare the counts the device computes with them, OR-ing into *status:
+// 1 = record count differs, 2 = destination count differs, 4 = a box on a level the operator
+// does not cover, 8 = a tensor-core wait gave up, 16 = inconsistent split work list.
+struct FixedSizes {
+  int64_t P = 0, nd = 0;
+  int *status = nullptr;                  // device word
+  const int64_t *d_in_offsets = nullptr;  // device copy of the batched input offsets (nfunc + 1)
+};
+
 // The sorted work list handed from the screen/sort stage to an apply kernel.
 // Destination d gathers records perm[seg[d]] .. perm[seg[d+1]-1]; record p names
 // a source box rec_src[p], a displacement rec_l[p] (three biased bytes) and the
@@ -22,12 +33,14 @@ struct ApplyWork {
   void *split_ws;             // scratch for the tensor-core path's grouping
   size_t split_ws_bytes;
   cudaEvent_t ev0, ev1;       // recorded around the apply kernel when non-null
+  const FixedSizes *fx;       // fixed-size (graph) mode when non-null
 };
 
 size_t apply_workspace_bytes(const Operator &op, const mra_apply_opts &o, int64_t n_in);
 int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts &o,
               mra_tree_view &out, void *ws, size_t ws_bytes, mra_apply_stats *stats,
-              cudaStream_t s, int nfunc = 1, const int64_t *in_offsets = nullptr, int64_t *out_offsets = nullptr);
+              cudaStream_t s, int nfunc = 1, const int64_t *in_offsets = nullptr, int64_t *out_offsets = nullptr,
+              const FixedSizes *fx = nullptr);
 int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts &o,
                     mra_tree_view &out, const ApplyWork &wk, mra_apply_stats *stats,
                     cudaStream_t s);

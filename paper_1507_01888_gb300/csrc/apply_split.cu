@@ -611,6 +611,12 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(TT)) apply_split_kerne
 }
 
 // ---------------------------------------------------------------- work-list kernels
+// Fixed-size (graph) mode: the kernel's error word into the graph's status.
+__global__ void fixed_err_kernel(const int *err, int *status) {
+  if (*err == 1) atomicOr(status, 8);
+  else if (*err) atomicOr(status, 16);
+}
+
 __global__ void key2_kernel(int64_t P, int G, const int *perm, const int *did, const uint64_t *dest_key,
                             const int *rec_l, uint64_t *key2, int *val2) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -791,6 +797,11 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
   kern<<<counted((unsigned)n_tiles), SPLIT_THREADS, smem, s>>>(a);
   MRA_CUDA_TRY(cudaGetLastError());
   if (wk.ev1) MRA_CUDA_TRY(cudaEventRecord(wk.ev1, s));
+  if (wk.fx) {
+    fixed_err_kernel<<<counted(1), 1, 0, s>>>(err, wk.fx->status);
+    MRA_CUDA_TRY(cudaGetLastError());
+    return MRA_OK;
+  }
   int herr = 0;
   MRA_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   MRA_CUDA_TRY(cudaStreamSynchronize(s));

@@ -27,6 +27,7 @@ int fail(int code, const char *fmt, ...);
 // Every kernel launch of the library takes its grid through counted(), so that
 // mra_launch_count reports how many kernels the library has launched.
 void note_launch();
+long long launch_total();
 template <class G>
 inline G counted(G grid) {
   note_launch();

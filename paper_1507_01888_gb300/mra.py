@@ -41,6 +41,8 @@ EXPORTED = [
     "mra_mlp_standardize", "mra_mlp_forward", "mra_mlp_workspace_size", "mra_mlp_grad", "mra_mlp_train",
     "mra_operator_ns_create", "mra_apply_ns_workspace_size", "mra_apply_ns", "mra_apply_ns_tree",
     "mra_reconstruct", "mra_truncate", "mra_multiply", "mra_inner", "mra_launch_count",
+    "mra_apply_graph_create", "mra_apply_graph_launch", "mra_apply_graph_status", "mra_apply_graph_info",
+    "mra_apply_graph_free",
 ]
 NOALLOC_MAX_BOXES = 1 << 20
 
@@ -65,7 +67,8 @@ class TreeView(ctypes.Structure):
 class ApplyOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("pieces", ctypes.c_int), ("screen", ctypes.c_int),
                 ("tau", ctypes.c_double), ("stencil", ctypes.c_int), ("max_disp", ctypes.c_int),
-                ("mlp", ctypes.c_void_p), ("delta", ctypes.c_double), ("tile_variant", ctypes.c_int)]
+                ("mlp", ctypes.c_void_p), ("delta", ctypes.c_double), ("tile_variant", ctypes.c_int),
+                ("delta_level", ctypes.c_void_p)]
 
 
 class ApplyStats(ctypes.Structure):
@@ -84,10 +87,18 @@ class CompareResult(ctypes.Structure):
     _fields_ = [("diff_norm", ctypes.c_double), ("ref_norm", ctypes.c_double),
                 ("test_norm", ctypes.c_double), ("rel_l2", ctypes.c_double),
                 ("max_box_rel", ctypes.c_double), ("n_common", ctypes.c_int64),
-                ("n_only_test", ctypes.c_int64), ("n_only_ref", ctypes.c_int64)]
+                ("n_only_test", ctypes.c_int64), ("n_only_ref", ctypes.c_int64),
+                ("level_diff_norm", ctypes.c_double * 20), ("level_ref_norm", ctypes.c_double * 20),
+                ("level_ref_boxes", ctypes.c_int64 * 20)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {f: getattr(self, f) for f, _ in self._fields_[:8]}
+        d["levels"] = [{"level": n, "rel_l2": (self.level_diff_norm[n] / self.level_ref_norm[n]
+                                               if self.level_ref_norm[n] > 0 else self.level_diff_norm[n]),
+                        "diff_norm": self.level_diff_norm[n], "ref_norm": self.level_ref_norm[n],
+                        "ref_boxes": self.level_ref_boxes[n]}
+                       for n in range(20) if self.level_ref_boxes[n] > 0 or self.level_diff_norm[n] > 0]
+        return d
 
 
 _lib = None
@@ -129,6 +140,12 @@ def load(build_if_stale: bool = True):
         lib.mra_apply_ns.argtypes = [vp, vp, P(TreeView), i, P(ApplyOpts), P(TreeView), vp, ctypes.c_size_t,
                                      P(ApplyStats), vp]
         lib.mra_apply_ns_tree.argtypes = [vp, vp, P(TreeView), i, P(ApplyOpts), P(TreeView), P(ApplyStats), vp]
+        lib.mra_apply_graph_create.argtypes = [vp, i, P(TreeView), P(ctypes.c_int64), P(ApplyOpts), P(TreeView),
+                                               P(ctypes.c_int64), vp, ctypes.c_size_t, P(vp), vp]
+        lib.mra_apply_graph_launch.argtypes = [vp, vp]
+        lib.mra_apply_graph_status.argtypes = [vp, vp]
+        lib.mra_apply_graph_info.argtypes = [vp, P(ctypes.c_int64), P(ctypes.c_longlong)]
+        lib.mra_apply_graph_free.argtypes = [vp]
         lib.mra_reconstruct.argtypes = [P(TreeView), P(TreeView), vp]
         lib.mra_truncate.argtypes = [P(TreeView), d, P(TreeView), P(d), vp]
         lib.mra_multiply.argtypes = [P(TreeView), P(TreeView), P(TreeView), vp]
@@ -289,11 +306,30 @@ class NSOperator(Operator):
 
 
 def make_opts(precision=PREC_FP64, pieces=3, screen=SCREEN_NONE, tau=0.0, stencil=STENCIL_NEAREST,
-              max_disp=1, mlp: torch.Tensor | None = None, delta: float = 0.0, tile_variant: int = 0) -> ApplyOpts:
-    o = ApplyOpts(precision, pieces, screen, tau, stencil, max_disp, None, delta, tile_variant)
+              max_disp=1, mlp: torch.Tensor | None = None, delta: float = 0.0, tile_variant: int = 0,
+              delta_level=None) -> ApplyOpts:
+    """delta_level: optional per-source-level margins (MAX_LEVEL + 1 values; inf keeps every term
+    of a level) replacing delta for the learned screen."""
+    o = ApplyOpts(precision, pieces, screen, tau, stencil, max_disp, None, delta, tile_variant, None)
     if mlp is not None:
         o.mlp = mlp.data_ptr()
         o._mlp_ref = mlp  # keep the tensor alive with the options
+    if delta_level is not None:
+        import numpy as np
+        dl = np.ascontiguousarray(delta_level, dtype=np.float64)
+        if dl.shape != (20,):
+            raise ValueError("delta_level needs one margin per level 0..19")
+        o.delta_level = dl.ctypes.data
+        o._dl_ref = dl
+    return o
+
+
+def copy_opts(opts: ApplyOpts) -> ApplyOpts:
+    """A copy of the options that keeps the buffers they point to alive."""
+    o = ApplyOpts.from_buffer_copy(opts)
+    for ref in ("_mlp_ref", "_dl_ref"):
+        if getattr(opts, ref, None) is not None:
+            setattr(o, ref, getattr(opts, ref))
     return o
 
 
@@ -359,6 +395,59 @@ class BatchedApplier:
             _check(rc)
             self.out.n = int(vout.n)
             return self.out, [int(v) for v in self.out_off]
+
+
+class ApplyGraph:
+    """mra_apply_graph_*: the apply of `tree` (one function, or several back to back with
+    `offsets`) recorded once as a CUDA graph; launch() replays it with one graph launch, reading
+    tree's buffers and writing self.out.  The output buffer is sized by a first plain apply."""
+
+    def __init__(self, op: Operator, tree: Tree, opts: ApplyOpts, offsets=None, stream=None):
+        lib = load()
+        self.op, self.opts, self.tree = op, opts, tree
+        offsets = offsets if offsets is not None else [0, tree.n]
+        self.nfunc = len(offsets) - 1
+        self.in_off = (ctypes.c_int64 * (self.nfunc + 1))(*[int(v) for v in offsets])
+        self.out_off = (ctypes.c_int64 * (self.nfunc + 1))()
+        self.ws = torch.empty(max(workspace_size(op, tree, opts), 1), dtype=torch.uint8, device=tree.keys.device)
+        cap = max(2 * tree.n, 1)
+        self._h = ctypes.c_void_p()
+        while True:
+            self.out = Tree.empty(cap, op.k, op.L, tree.keys.device)
+            vin, vout = tree.view(), self.out.view()
+            rc = lib.mra_apply_graph_create(op.handle, self.nfunc, ctypes.byref(vin), self.in_off,
+                                            ctypes.byref(opts), ctypes.byref(vout), self.out_off,
+                                            ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(),
+                                            ctypes.byref(self._h), _stream(stream))
+            if rc == MRA_ERR_CAPACITY and vout.n > cap:
+                cap = int(vout.n)
+                continue
+            _check(rc)
+            break
+        n_out, kern = ctypes.c_int64(), ctypes.c_longlong()
+        _check(lib.mra_apply_graph_info(self._h, ctypes.byref(n_out), ctypes.byref(kern)))
+        self.out.n = int(n_out.value)
+        self.kernels_per_launch = int(kern.value)
+        self.out_offsets = [int(v) for v in self.out_off]
+
+    def launch(self, stream=None):
+        _check(load().mra_apply_graph_launch(self._h, _stream(stream)))
+        return self.out
+
+    def status(self, stream=None):
+        """MRA_OK, or raises MraError (MRA_ERR_CAPACITY when a replay needed other sizes)."""
+        _check(load().mra_apply_graph_status(self._h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().mra_apply_graph_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def concat_trees(trees):

@@ -123,3 +123,24 @@ def test_learned_screen_training_gain_and_error(mra):
         print(f"learned screen delta={delta:.2f}: dropped {st['terms_learned_skipped']} of "
               f"{st_plain['terms_kept']} kept terms, rel. change {err / rn:.2e}")
     assert st["terms_learned_skipped"] > 0
+    # per-level margins: calibrated levels get at least the global margin, uncalibrated ones keep
+    # every term; a level with an infinite margin gives exactly the plain apply's boxes
+    dl = info["delta_level"]
+    assert all(d >= info["delta"] for d in dl)
+    lv_src = (ok >> np.uint64(57)).astype(int)
+    busiest = int(np.bincount(lv_src).argmax())
+    one = [float("inf")] * 20
+    one[busiest] = 0.5
+    lopts = mra.make_opts(screen=mra.SCREEN_LEARNED, tau=tau, stencil=mra.STENCIL_SHELLS, max_disp=1,
+                          mlp=model, delta=0.5, delta_level=one)
+    out, st = mra.apply(op, test_tree, lopts)
+    assert st["terms_learned_skipped"] > 0
+    gk, gc = out.host()
+    pk, pc = plain.host()
+    assert (gk == pk).all()
+    other = (gk >> np.uint64(57)).astype(int) != busiest
+    assert np.array_equal(gc[other], pc[other])
+    none = mra.make_opts(screen=mra.SCREEN_LEARNED, tau=tau, stencil=mra.STENCIL_SHELLS, max_disp=1,
+                         mlp=model, delta=0.5, delta_level=[float("inf")] * 20)
+    out, st = mra.apply(op, test_tree, none)
+    assert st["terms_learned_skipped"] == 0 and np.array_equal(out.host()[1], pc)

@@ -227,3 +227,19 @@ def test_norm_and_compare(mra):
     assert r["diff_norm"] == pytest.approx(diff, rel=1e-12)
     assert r["n_common"] == 49 and r["n_only_ref"] == 1 and r["n_only_test"] == 0
     assert r["max_box_rel"] == pytest.approx(1e-3, rel=1e-9)
+    assert [lv["level"] for lv in r["levels"]] == [3]
+    assert r["levels"][0]["diff_norm"] == pytest.approx(diff, rel=1e-12)
+    assert r["levels"][0]["ref_boxes"] == 50
+    # two levels: the breakdown splits the difference and the reference norm by level
+    k2, c2b = W.random_tree_coeffs(20, 5, 2, seed=9)
+    ka, ca = np.concatenate([k2, keys]), np.concatenate([c2b, coeffs])
+    tb = ca.copy()
+    tb[2] *= 1.01  # a level-2 box
+    tb[20 + 5] *= 0.99  # a level-3 box
+    r2 = mra.compare(mra.Tree.from_host(ka, tb, 8.0), mra.Tree.from_host(ka, ca, 8.0))
+    lv = {x["level"]: x for x in r2["levels"]}
+    assert sorted(lv) == [2, 3] and lv[2]["ref_boxes"] == 20 and lv[3]["ref_boxes"] == 50
+    for n, sl in ((2, slice(0, 20)), (3, slice(20, 70))):
+        assert lv[n]["diff_norm"] == pytest.approx(np.sqrt(((tb[sl] - ca[sl]) ** 2).sum()), rel=1e-12)
+        assert lv[n]["ref_norm"] == pytest.approx(np.sqrt((ca[sl] ** 2).sum()), rel=1e-12)
+    assert sum(x["diff_norm"] ** 2 for x in r2["levels"]) == pytest.approx(r2["diff_norm"] ** 2, rel=1e-12)

@@ -115,10 +115,12 @@ def bsh_learned_k10() -> Workload:
 
 
 def poisson_k14_large() -> Workload:
-    """Full-size Poisson apply: 64 Gaussians a~logU[1,1e6], k=14, thresh 1e-8, M=100."""
+    """Full-size Poisson apply: 64 Gaussians a~logU[1,1e6], k=14, thresh 1e-8, M=100, with the
+    learned screen trained on two more functions of the family (seeds 5000, 5001)."""
     return Workload("poisson_m100_adaptive_k14", [gaussian_sum(64, 1.0, 1e6, seed=5)], k=14, L=L_CELL,
                     thresh=1e-8, uniform_level=-1, kernel=POISSON, mu=0.0, M=100, fit_eps=1e-8, stencil=0,
-                    max_disp=1, tau=1e-10)
+                    max_disp=1, tau=1e-10,
+                    extra={"train_funcs": [gaussian_sum(64, 1.0, 1e6, seed=s) for s in (5000, 5001)]})
 
 
 def poisson_ns_uniform_k6() -> Workload:
