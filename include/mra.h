@@ -149,6 +149,12 @@ typedef struct {
  * the CUB sorts and scans, are not counted).  Take the difference around a region of calls. */
 long long mra_launch_count(void);
 
+/* Test hook for the failure path: the next MRA_PREC_SPLIT_BF16 apply in this process has its
+ * first CTA skip the block copies of its first term, so that the kernel's bounded waits on them
+ * run out (about two seconds each); that apply returns MRA_ERR_TIMEOUT with the device context
+ * intact, and later calls run normally.  One-shot; nothing else is changed. */
+int mra_debug_inject_stall(void);
+
 /* Thread-local description of the last error (never NULL). */
 const char *mra_last_error(void);
 

@@ -23,6 +23,8 @@
 // pieces stacked along N so that one MMA per A piece covers all kept products.
 // Stage 3 multiplies by c_m R_z.  Each term's FP32 stage-3 output is added into per-slot
 // sums kept as FP32 pairs (TwoSum), so the term and box sums lose nothing to rounding.
+#include <atomic>
+
 #include <cuda_bf16.h>
 
 #include <cub/cub.cuh>
@@ -84,6 +86,7 @@ struct SplitArgs {
   uint64_t *out_keys;
   double *out_coeffs;
   int *err;
+  int inject_stall;  // test hook: CTA 0 never issues the block copies of its first term
 };
 
 // Named barrier over one warpgroup (128 threads) with an OR vote.
@@ -325,6 +328,10 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(TT)) apply_split_kerne
         return false;
       unsigned char *Bb = Bt + b * BTERM_BYTES;
       const uint32_t bar = tc::smem_u32(&bar_bb[b]);
+      if (a.inject_stall && blockIdx.x == 0 && i == 0) {  // the copies never land: the waits run out
+        ++nfetch;
+        return true;
+      }
       tc::mbar_arrive_expect_tx(bar, 3 * BSTAGE_BYTES);
       const int64_t blk0 = lbase + (int64_t)m * nl + Dop;
       tc::bulk_g2s(tc::smem_u32(Bb), a.Bsplit + (blk0 + lx) * BSTAGE_BYTES, BSTAGE_BYTES, bar);
@@ -610,6 +617,10 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(TT)) apply_split_kerne
   if (warp == 0) tc::tmem_dealloc(tmem, NCOL);
 }
 
+// ---------------------------------------------------------------- failure-path test hook
+std::atomic<int> g_inject_stall{0};
+bool take_injected_stall() { return g_inject_stall.exchange(0) != 0; }
+
 // ---------------------------------------------------------------- work-list kernels
 // Fixed-size (graph) mode: the kernel's error word into the graph's status.
 __global__ void fixed_err_kernel(const int *err, int *status) {
@@ -764,6 +775,7 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
   a.out_keys = out.keys;
   a.out_coeffs = out.coeffs;
   a.err = err;
+  a.inject_stall = take_injected_stall() ? 1 : 0;
   size_t smem = (size_t)3 * a.P * T * TILE_BYTES + (size_t)nbuf_for(tt) * BTERM_BYTES;
   // no more CTAs per SM than the tensor memory holds (512 columns): otherwise an extra
   // CTA's allocation would wait for a resident CTA to finish
@@ -812,3 +824,8 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
 }
 
 }  // namespace mra
+
+extern "C" int mra_debug_inject_stall(void) {
+  mra::g_inject_stall.store(1);
+  return MRA_OK;
+}

@@ -42,7 +42,7 @@ EXPORTED = [
     "mra_operator_ns_create", "mra_apply_ns_workspace_size", "mra_apply_ns", "mra_apply_ns_tree",
     "mra_reconstruct", "mra_truncate", "mra_multiply", "mra_inner", "mra_launch_count",
     "mra_apply_graph_create", "mra_apply_graph_launch", "mra_apply_graph_status", "mra_apply_graph_info",
-    "mra_apply_graph_free",
+    "mra_apply_graph_free", "mra_debug_inject_stall",
 ]
 NOALLOC_MAX_BOXES = 1 << 20
 
@@ -663,6 +663,11 @@ def multiply(a: "Tree", b: "Tree", stream=None) -> "Tree":
         _check(rc)
         out.n = int(vo.n)
         return out
+
+
+def debug_inject_stall():
+    """mra_debug_inject_stall: the next split-precision apply's waits run out (MRA_ERR_TIMEOUT)."""
+    _check(load().mra_debug_inject_stall())
 
 
 def launch_count() -> int:
