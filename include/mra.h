@@ -67,6 +67,8 @@ extern "C" {
 
 #define MRA_MAX_LEVEL 19
 #define MRA_MAX_K 16
+#define MRA_MAX_NS_K 20 /* largest order 2k of a non-standard-form operator (k <= 10); orders
+                           above MRA_MAX_K are applied with MRA_PREC_FP64 only */
 #define MRA_MAX_TERMS 128
 #define MRA_NOALLOC_MAX_BOXES (1 << 20) /* largest tree mra_norm_noalloc accepts */
 #define MRA_MAX_FUNCS 2048 /* functions in one mra_apply_batched call */

@@ -310,9 +310,11 @@ __global__ void func_offsets_kernel(int64_t n, const int *dest_func, int nfunc, 
 // One CTA per destination box.  For each of its records (source b, l, mask)
 // and each kept term m:  t1 = s x_1 Rx, t2 = t1 x_2 Ry, t3 = t2 x_3 Rz,
 // acc += c_m t3 (Sec. 2.3), acc held in registers across all records.
+// PT accumulators per thread: k^3 <= 256 PT (PT = 16 up to k = 16, 32 for the non-standard
+// form's orders up to 20).
 constexpr int F64_THREADS = 256;
-constexpr int F64_PER_THREAD = (MRA_MAX_K * MRA_MAX_K * MRA_MAX_K + F64_THREADS - 1) / F64_THREADS;
 
+template <int PT>
 __global__ void __launch_bounds__(F64_THREADS) apply_f64_kernel(
     int k, int M, const double *c, const double *R, const int *Dlev, const int64_t *level_off,
     const uint64_t *in_keys, const double *in_coeffs, const int64_t *seg, const int *perm,
@@ -327,9 +329,9 @@ __global__ void __launch_bounds__(F64_THREADS) apply_f64_kernel(
   int Dop = Dlev[n];
   int nl = 2 * Dop + 1;
   const double *Rlev = R + level_off[n] * k2;
-  double acc[F64_PER_THREAD];
+  double acc[PT];
 #pragma unroll
-  for (int q = 0; q < F64_PER_THREAD; ++q) acc[q] = 0.0;
+  for (int q = 0; q < PT; ++q) acc[q] = 0.0;
   int64_t r0 = seg[dst], r1 = seg[dst + 1];
   for (int64_t r = r0; r < r1; ++r) {
     int p = perm[r];
@@ -371,7 +373,7 @@ __global__ void __launch_bounds__(F64_THREADS) apply_f64_kernel(
         __syncthreads();
         double cm = c[m];
 #pragma unroll
-        for (int q = 0; q < F64_PER_THREAD; ++q) {  // acc += c_m t3[ix][iy][iz]
+        for (int q = 0; q < PT; ++q) {  // acc += c_m t3[ix][iy][iz]
           int e = threadIdx.x + q * F64_THREADS;
           if (e < k3) {
             int base = (e / k) * k, iz = e % k;
@@ -385,7 +387,7 @@ __global__ void __launch_bounds__(F64_THREADS) apply_f64_kernel(
   }
   double *o = out_coeffs + dst * k3;
 #pragma unroll
-  for (int q = 0; q < F64_PER_THREAD; ++q) {
+  for (int q = 0; q < PT; ++q) {
     int e = threadIdx.x + q * F64_THREADS;
     if (e < k3) o[e] = acc[q];
   }
@@ -852,10 +854,10 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
   if (o.precision == MRA_PREC_FP64) {
     if (ev0) MRA_CUDA_TRY(cudaEventRecord(ev0, s));
     size_t smem = (size_t)(3 * k3 + 3 * k * k) * sizeof(double);
+    auto kern = k3 <= 16 * F64_THREADS ? apply_f64_kernel<16> : apply_f64_kernel<32>;
     if (smem > 48 * 1024)
-      MRA_CUDA_TRY(cudaFuncSetAttribute(apply_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
-    apply_f64_kernel<<<counted((unsigned)nd), F64_THREADS, smem, s>>>(
+      MRA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<counted((unsigned)nd), F64_THREADS, smem, s>>>(
         k, op.M, op.d_c, op.d_R, op.d_D, op.d_level_off, in.keys, in.coeffs, seg, pout, rsrc, rl,
         rmask, dkey, out.keys, out.coeffs);
     MRA_CUDA_TRY(cudaGetLastError());

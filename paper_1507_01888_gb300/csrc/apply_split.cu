@@ -718,8 +718,9 @@ int split_blocks_build(Operator &op, cudaStream_t s) {
 int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts &o,
                     mra_tree_view &out, const ApplyWork &wk, mra_apply_stats *stats,
                     cudaStream_t s) {
-  if (!op.d_Rsplit) return fail(MRA_ERR_ARG, "mra_apply: operator has no split blocks");
   const int k = op.k;
+  if (k > MRA_MAX_K) return fail(MRA_ERR_UNSUPPORTED, "split apply: order %d above %d (use MRA_PREC_FP64)", k, MRA_MAX_K);
+  if (!op.d_Rsplit) return fail(MRA_ERR_ARG, "mra_apply: operator has no split blocks");
   if (k & 1) return fail(MRA_ERR_UNSUPPORTED, "split apply: odd k=%d not supported (use MRA_PREC_FP64)", k);
   const int tt = (k >= 4 && o.tile_variant == 1) ? 2 : (k >= 4 && k <= 10 && o.tile_variant == 2) ? 1 : 4;
   const int G = g_for(k, tt);

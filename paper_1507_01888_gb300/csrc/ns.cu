@@ -643,6 +643,9 @@ int ns_check(const Operator *op, const Operator *ns, const mra_tree_view *in, in
     return fail(MRA_ERR_ARG, "mra_apply_ns: unknown precision %d", o->precision);
   if (o->precision == MRA_PREC_SPLIT_BF16 && (o->pieces < 2 || o->pieces > 3))
     return fail(MRA_ERR_ARG, "mra_apply_ns: pieces must be 2 or 3");
+  if (o->precision == MRA_PREC_SPLIT_BF16 && ns->k > MRA_MAX_K)
+    return fail(MRA_ERR_UNSUPPORTED, "mra_apply_ns: order 2k=%d is applied in FP64 only (split precision to %d)",
+                ns->k, MRA_MAX_K);
   if (o->screen != MRA_SCREEN_NONE && o->screen != MRA_SCREEN_NORM)
     return fail(MRA_ERR_ARG, "mra_apply_ns: screen must be MRA_SCREEN_NONE or MRA_SCREEN_NORM");
   if (o->screen == MRA_SCREEN_NORM && !(o->tau >= 0.0)) return fail(MRA_ERR_ARG, "mra_apply_ns: tau must be >= 0");
@@ -668,7 +671,8 @@ extern "C" int mra_operator_ns_create(const mra_operator *h, int max_disp, mra_o
   const Operator *op = reinterpret_cast<const Operator *>(h);
   if (!op || !out) return fail(MRA_ERR_ARG, "mra_operator_ns_create: NULL argument");
   *out = nullptr;
-  if (2 * op->k > MRA_MAX_K) return fail(MRA_ERR_ARG, "mra_operator_ns_create: 2k=%d above %d", 2 * op->k, MRA_MAX_K);
+  if (2 * op->k > MRA_MAX_NS_K)
+    return fail(MRA_ERR_ARG, "mra_operator_ns_create: 2k=%d above %d", 2 * op->k, MRA_MAX_NS_K);
   if (op->max_level <= op->min_level)
     return fail(MRA_ERR_ARG, "mra_operator_ns_create: the operator needs at least two levels");
   if (max_disp < 0) return fail(MRA_ERR_ARG, "mra_operator_ns_create: max_disp < 0");
@@ -732,8 +736,10 @@ extern "C" int mra_operator_ns_create(const mra_operator *h, int max_disp, mra_o
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return bail(fail(MRA_ERR_CUDA, "mra_operator_ns_create: %s", cudaGetErrorString(e)));
-  int rc = split_blocks_build(*ns, s);  // BF16 pieces of the 2k blocks for the tensor-core path
-  if (rc != MRA_OK) return bail(rc);
+  if (ns->k <= MRA_MAX_K) {  // BF16 pieces of the 2k blocks for the tensor-core path
+    int rc = split_blocks_build(*ns, s);
+    if (rc != MRA_OK) return bail(rc);
+  }
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return bail(fail(MRA_ERR_CUDA, "mra_operator_ns_create: %s", cudaGetErrorString(e)));
   *out = reinterpret_cast<mra_operator *>(ns);

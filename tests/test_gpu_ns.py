@@ -36,7 +36,8 @@ def uniform_case(mra, k, N, kernel=0, mu=0.0, M=8, L=8.0, seed=7, op_disp=None):
     return keys, coeffs, op, fit
 
 
-@pytest.mark.parametrize("k,N,n0,D", [(3, 3, 1, 1), (4, 3, 1, 2), (4, 3, 2, 1), (6, 2, 1, 1), (8, 3, 1, 1)])
+@pytest.mark.parametrize("k,N,n0,D", [(3, 3, 1, 1), (4, 3, 1, 2), (4, 3, 2, 1), (6, 2, 1, 1), (8, 3, 1, 1),
+                                     (10, 2, 1, 1)])
 def test_ns_fp64_matches_oracle(mra, k, N, n0, D):
     keys, coeffs, op, fit = uniform_case(mra, k, N)
     ns_op = mra.NSOperator(op, max_disp=D)
@@ -47,6 +48,19 @@ def test_ns_fp64_matches_oracle(mra, k, N, n0, D):
     assert (gk == keys).all()
     ref = O.apply_ns(coeffs, k, 8.0, N, n0, fit["c"], fit["t"], D)
     assert rel(gc, ref) <= 1e-12
+
+
+def test_ns_order_above_16_is_fp64_only(mra):
+    """k = 10: the non-standard operator has order 20, applied in FP64; split precision is refused."""
+    keys, coeffs, op, fit = uniform_case(mra, 10, 2)
+    ns_op = mra.NSOperator(op, max_disp=1)
+    tree = mra.Tree.from_host(keys, coeffs, 8.0)
+    with pytest.raises(mra.MraError) as e:
+        mra.apply_ns(op, ns_op, tree, 1, mra.make_opts(precision=mra.PREC_SPLIT_BF16, stencil=mra.STENCIL_SHELLS,
+                                                       max_disp=1))
+    assert e.value.code == mra.MRA_ERR_UNSUPPORTED
+    with pytest.raises(mra.MraError):  # order 22 is above the largest non-standard order
+        mra.NSOperator(mra.Operator(0, 8, 11, 8.0, 0, 2, max_disp=3, fit_eps=1e-4), max_disp=1)
 
 
 def test_ns_with_every_displacement_equals_the_plain_apply(mra):
@@ -119,7 +133,7 @@ def adaptive_case(mra, k, thresh=3e-3, max_level=4, op_disp=15, M=8):
     return keys, coeffs, op, oracle_fit(op), L
 
 
-@pytest.mark.parametrize("k,D", [(3, 1), (4, 2), (6, 1), (8, 1)])
+@pytest.mark.parametrize("k,D", [(3, 1), (4, 2), (6, 1), (8, 1), (10, 1)])
 def test_ns_tree_fp64_matches_oracle(mra, k, D):
     keys, coeffs, op, fit, L = adaptive_case(mra, k)
     ns_op = mra.NSOperator(op, max_disp=D)
