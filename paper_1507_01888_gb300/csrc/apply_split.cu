@@ -46,6 +46,7 @@ constexpr int BTERM_BYTES = 3 * BSTAGE_BYTES;   // the three blocks (x, y, z) of
 constexpr int NBUF = 4;                         // most block buffers a CTA uses
 constexpr int RING = 4;                         // term-info ring from warpgroup 0 to 1
 constexpr int MAX_G = 32;
+constexpr int JOIN = 2;                         // terms summed in tensor memory per flush
 constexpr long long WAIT_CYCLES = 4000000000LL;  // bounded mbarrier wait (~2 s)
 
 
@@ -480,8 +481,10 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(TT)) apply_split_kerne
     }
   } else {
     // ======================================================= warpgroup 1
-    // per-slot sums as unevaluated FP32 pairs hi + lo (about 48 significant bits), added to
-    // with TwoSum on the FP32 pipe; the FP64 pipe (1/64 rate) only forms hi + lo at the end
+    // per-slot sums as FP32 pairs hi + lo, added to with compensated (Kahan) summation on the
+    // FP32 pipe; the FP64 pipe (1/64 rate) only forms hi + lo at the end.  Up to JOIN
+    // consecutive terms kept by the same slots are summed in D3 by the stage-3 MMAs before
+    // one flush adds them in.
     float hi[T][K], lo[T][K];
 #pragma unroll
     for (int t = 0; t < T; ++t)
@@ -489,8 +492,8 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(TT)) apply_split_kerne
       for (int j = 0; j < K; ++j) hi[t][j] = lo[t][j] = 0.f;
     bool bad = false;
     const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
-    // add term it-1's stage-3 output (tiles `tl`, slots `kp`) into the sums of this
-    // thread's rows; rows of slots that do not keep the term are skipped
+    // add the terms summed in D3 (tiles `tl`, kept by slots `kp`) into the sums of this
+    // thread's rows; rows of slots that do not keep them are skipped
     auto flush = [&](uint32_t tl, uint32_t kp) {
 #pragma unroll
       for (int t = 0; t < T; ++t) {
@@ -503,17 +506,17 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(TT)) apply_split_kerne
         const int m3 = t * 128 + quarter * 32 + lane;
         if (m3 < rows && ((kp >> (m3 / k2)) & 1u)) {
 #pragma unroll
-          for (int j = 0; j < K; ++j) {
-            const float x = c1[j] + c0[j];
-            const float s = hi[t][j] + x;
-            const float bp = s - hi[t][j];
-            lo[t][j] += (hi[t][j] - (s - bp)) + (x - bp);
+          for (int j = 0; j < K; ++j) {  // lo holds minus the running compensation
+            const float y = (c1[j] + c0[j]) + lo[t][j];
+            const float s = hi[t][j] + y;
+            lo[t][j] = y - (s - hi[t][j]);
             hi[t][j] = s;
           }
         }
       }
     };
     uint32_t prev_tiles = 0, prev_keep = 0;
+    int joined = 0;  // terms summed in D3 since its last flush
     for (int it = 0; it < nit; ++it) {
       // one warp polls the barriers; the others sleep in the vote.  Then the previous
       // term's stage 3 is done too: A3 is free and D3 holds its output
@@ -545,7 +548,13 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(TT)) apply_split_kerne
           store_run(A3, i * k2 + ix * k, jz, v[t]);
         }
       }
-      if (it > 0) flush(prev_tiles, prev_keep);  // before stage 3 of this term overwrites D3
+      // this term's stage 3 adds onto D3 when the previous term's sum there has the same slots
+      // and room; otherwise D3 is flushed first and overwritten
+      const bool join = joined > 0 && joined < JOIN && keep == prev_keep;
+      if (joined > 0 && !join) {
+        flush(prev_tiles, prev_keep);
+        joined = 0;
+      }
       tc::fence_proxy_async_smem();
       tc::fence_before_sync();
       wg_sync(2);
@@ -561,7 +570,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(TT)) apply_split_kerne
           for (int t = 0; t < T; ++t) {
             if (!((tiles >> t) & 1u)) continue;
             const uint32_t d = tD3 + (uint32_t)(t * 32);
-            tc::mma_bf16(d, adesc(A3, 0, t), bdesc(B3), idesc_n(2), 0u);                  // x0 [y0 y1]
+            tc::mma_bf16(d, adesc(A3, 0, t), bdesc(B3), idesc_n(2), join ? 1u : 0u);      // x0 [y0 y1]
             tc::mma_bf16(d + 16u, adesc(A3, 1, t), bdesc(B3), idesc_n(1), 1u);            // x1 y0
             if (P == 3) {
               tc::mma_bf16(d + 16u, adesc(A3, 1, t), bdesc(B3 + BPIECE_BYTES), idesc_n(1), 1u);      // x1 y1
@@ -577,6 +586,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(TT)) apply_split_kerne
       }
       prev_tiles = tiles;
       prev_keep = keep;
+      ++joined;
     }
     if (!bad && nit > 0) {
       bool ok = quarter != 0 || tc::mbar_wait_or_abort(bs3, (uint32_t)((nit - 1) & 1), WAIT_CYCLES, &abort_flag);
