@@ -482,9 +482,8 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(TT)) apply_split_kerne
   } else {
     // ======================================================= warpgroup 1
     // per-slot sums as FP32 pairs hi + lo, added to with compensated (Kahan) summation on the
-    // FP32 pipe; the FP64 pipe (1/64 rate) only forms hi + lo at the end.  Up to JOIN
-    // consecutive terms kept by the same slots are summed in D3 by the stage-3 MMAs before
-    // one flush adds them in.
+    // FP32 pipe; the FP64 pipe (1/64 rate) only forms hi + lo at the end.  In one-slot tiles up
+    // to JOIN consecutive terms are summed in D3 by the stage-3 MMAs before one flush adds them.
     float hi[T][K], lo[T][K];
 #pragma unroll
     for (int t = 0; t < T; ++t)
@@ -548,9 +547,11 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(TT)) apply_split_kerne
           store_run(A3, i * k2 + ix * k, jz, v[t]);
         }
       }
-      // this term's stage 3 adds onto D3 when the previous term's sum there has the same slots
-      // and room; otherwise D3 is flushed first and overwritten
-      const bool join = joined > 0 && joined < JOIN && keep == prev_keep;
+      // this term's stage 3 adds onto D3 when the tile holds one slot and D3 has room;
+      // otherwise D3 is flushed first and overwritten.  With several slots the rounding of a
+      // slot's sum would depend on which other slots share its tile (joins need equal keep
+      // masks), and a destination's result would change with how its function is batched.
+      const bool join = G == 1 && joined > 0 && joined < JOIN && keep == prev_keep;
       if (joined > 0 && !join) {
         flush(prev_tiles, prev_keep);
         joined = 0;
