@@ -1,0 +1,114 @@
+"""Full-size parity of the split-BF16 apply on the large workloads, in the launch shape the
+benchmark times (its tuned tile variant), against the oracle on seeded samples of destinations.
+
+For each workload the library's projection must give the oracle's tree key for key (the
+refinement decisions are all away from the threshold), the split apply runs on the whole
+tree, and the oracle computes the sampled destinations one by one from its own projection and
+its own Gaussian fit.  Bar: relative L2 over the sample <= 1e-6 (the mixed-precision threshold),
+same destination keys.  The learned screen is off here (the norm screen is its fallback and
+the reference its error is judged against); it is tested in test_gpu_learned.py.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from oracle_inputs import oracle_fit
+
+pytestmark = pytest.mark.gpu
+
+TOL_MIXED = 1e-6
+
+
+@pytest.fixture(scope="module")
+def mra():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1507_01888_gb300 import mra as m
+    m.load()
+    return m
+
+
+def rel_l2(a, b):
+    return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
+
+
+def project_both(mra, w, f):
+    ok, oc, margin = O.project(f, w.k, w.L, thresh=w.thresh, init_level=w.init_level, max_level=w.max_level)
+    assert margin > 1e-8
+    t = mra.project(f, w.k, w.L, thresh=w.thresh, init_level=w.init_level, max_level=w.max_level)
+    gk, _ = t.host()
+    assert (gk == ok).all()
+    return t, ok, oc
+
+
+def check_sample(w, fit, ok, oc, gk, gc, n, seed):
+    rng = np.random.default_rng(seed)
+    sample = np.sort(rng.choice(gk, min(n, len(gk)), replace=False))
+    ref = O.apply(ok, oc, fit["c"], fit["t"], w.L, stencil=w.stencil, max_disp=w.max_disp, tau=w.tau,
+                  sample_keys=sample)
+    assert len(ref.keys) == len(sample)
+    pos = np.searchsorted(gk, ref.keys)
+    assert (gk[pos] == ref.keys).all()
+    assert rel_l2(gc[pos], ref.coeffs) <= TOL_MIXED
+
+
+def test_batched_64_functions_full_size(mra):
+    """Poisson M=40 k=8, 64 functions (1,057,400 boxes) in one batched apply, one-tile shape."""
+    w = W.poisson_batched_64()
+    rng = np.random.default_rng(3)
+    picked = sorted(int(f) for f in rng.choice(len(w.funcs), 3, replace=False))
+    trees, host = [], {}
+    for i, f in enumerate(w.funcs):
+        if i in picked:
+            t, ok, oc = project_both(mra, w, f)
+            host[i] = (ok, oc)
+        else:
+            t = mra.project(f, w.k, w.L, thresh=w.thresh, init_level=w.init_level, max_level=w.max_level)
+        trees.append(t)
+    big, offs = mra.concat_trees(trees)
+    lv = (big.host()[0] >> np.uint64(57)).astype(int)
+    op = mra.Operator(w.kernel, w.M, w.k, w.L, int(lv.min()), int(lv.max()), max_disp=w.max_disp, mu=w.mu,
+                      fit_eps=w.fit_eps)
+    fit = oracle_fit(op)
+    opts = mra.make_opts(precision=mra.PREC_SPLIT_BF16, screen=mra.SCREEN_NORM, tau=w.tau, stencil=w.stencil,
+                         max_disp=w.max_disp, tile_variant=2)
+    g = mra.ApplyGraph(op, big, opts, offsets=offs)  # the benchmark's launch: one graph per step
+    g.launch()
+    g.status()
+    gk_all, gc_all = g.out.host()
+    oo = g.out_offsets
+    for i in picked:
+        ok, oc = host[i]
+        a, b = oo[i], oo[i + 1]
+        check_sample(w, fit, ok, oc, gk_all[a:b], gc_all[a:b], 16, seed=100 + i)
+
+
+def test_learned_workload_tree_full_size(mra):
+    """BSH mu=0.5 M=80 k=10, 133,456 boxes (the learned-screen workload's tree), one-tile shape."""
+    w = W.bsh_learned_k10()
+    t, ok, oc = project_both(mra, w, w.funcs[0])
+    lv = (ok >> np.uint64(57)).astype(int)
+    op = mra.Operator(w.kernel, w.M, w.k, w.L, int(lv.min()), int(lv.max()), max_disp=w.max_disp, mu=w.mu,
+                      fit_eps=w.fit_eps)
+    fit = oracle_fit(op)
+    opts = mra.make_opts(precision=mra.PREC_SPLIT_BF16, screen=mra.SCREEN_NORM, tau=w.tau, stencil=w.stencil,
+                         max_disp=w.max_disp, tile_variant=2)
+    out, _ = mra.apply(op, t, opts)
+    gk, gc = out.host()
+    check_sample(w, fit, ok, oc, gk, gc, 24, seed=7)
+
+
+def test_k14_full_size(mra):
+    """Poisson M=100 k=14, 171,592 boxes (2,744 coefficients each), two-tile shape."""
+    w = W.poisson_k14_large()
+    t, ok, oc = project_both(mra, w, w.funcs[0])
+    lv = (ok >> np.uint64(57)).astype(int)
+    op = mra.Operator(w.kernel, w.M, w.k, w.L, int(lv.min()), int(lv.max()), max_disp=w.max_disp, mu=w.mu,
+                      fit_eps=w.fit_eps)
+    fit = oracle_fit(op)
+    opts = mra.make_opts(precision=mra.PREC_SPLIT_BF16, screen=mra.SCREEN_NORM, tau=w.tau, stencil=w.stencil,
+                         max_disp=w.max_disp, tile_variant=1)
+    out, _ = mra.apply(op, t, opts)
+    gk, gc = out.host()
+    check_sample(w, fit, ok, oc, gk, gc, 16, seed=9)

@@ -96,15 +96,17 @@ def test_split_shells_and_screen_adaptive(mra):
     assert rel_l2(gc, ref.coeffs) <= TOL_MIXED
 
 
-def test_split_full_size_vs_fp64_and_oracle(mra):
-    """BSH M=60 adaptive k=10 (17,200 boxes): split vs FP64 GPU on every box, vs the oracle on a sample."""
+@pytest.mark.parametrize("tile_variant", [0, 2])
+def test_split_full_size_vs_fp64_and_oracle(mra, tile_variant):
+    """BSH M=60 adaptive k=10 (17,200 boxes): split vs FP64 GPU on every box, vs the oracle on a
+    sample; the four-tile shape and the one-tile shape the benchmark's tuner picks."""
     w = W.bsh_m60_adaptive_k10()
     ok, oc, _ = O.project(w.funcs[0], w.k, w.L, thresh=w.thresh, init_level=w.init_level, max_level=w.max_level)
     op = mra.Operator(w.kernel, w.M, w.k, w.L, 2, 19, max_disp=w.max_disp, mu=w.mu, fit_eps=w.fit_eps)
     fit = oracle_fit(op)
     tree = mra.Tree.from_host(ok, oc, w.L)
     kw = dict(stencil=w.stencil, max_disp=w.max_disp, screen=mra.SCREEN_NORM, tau=w.tau)
-    sp, _ = mra.apply(op, tree, split_opts(mra, **kw))
+    sp, _ = mra.apply(op, tree, split_opts(mra, tile_variant=tile_variant, **kw))
     f64, _ = mra.apply(op, tree, mra.make_opts(**kw))
     cmp = mra.compare(sp, f64)
     assert cmp["n_only_test"] == 0 and cmp["n_only_ref"] == 0
