@@ -33,14 +33,18 @@ __device__ __forceinline__ void legendre_phi(int k, double x01, double *out) {
 
 // --------------------------------------------------------------------------- fit search
 // One CTA per candidate (h, s_lo) of the grid h = (5+i)/100, s_lo = (j-100)/4:
-// max over 3000 log-spaced r of |sum_m c_m exp(-t_m r^2) - K(r)| / K(r).
+// max over the log-spaced points p = 0, stride, 2 stride, ... < 3000 of
+// |sum_m c_m exp(-t_m r_p^2) - K(r_p)| / K(r_p).  With stride 1 this is the candidate's error;
+// with a larger stride it is a lower bound of it (a maximum over a subset of the same values).
+// `cands` lists the candidates to evaluate (NULL: every candidate, in grid order).
 constexpr int FIT_NS = 113, FIT_NH = 116, FIT_NP = 3000;
 
-__global__ void fit_search_kernel(double mu, int M, double r_lo, double r_hi, double *err) {
+__global__ void fit_search_kernel(double mu, int M, double r_lo, double r_hi, int stride, const int *cands,
+                                  double *err) {
   extern __shared__ double sh[];
   double *c = sh, *t = sh + M;
   __shared__ double red[32];
-  int cand = blockIdx.x;
+  const int cand = cands ? cands[blockIdx.x] : (int)blockIdx.x;
   int i = cand / FIT_NS, j = cand % FIT_NS;
   double h = (5.0 + i) / 100.0, s_lo = (j - 100.0) / 4.0;
   const double two_over_sqrtpi = 2.0 / sqrt(3.14159265358979323846264338327950288);
@@ -51,7 +55,7 @@ __global__ void fit_search_kernel(double mu, int M, double r_lo, double r_hi, do
   }
   __syncthreads();
   double worst = 0.0;
-  for (int p = threadIdx.x; p < FIT_NP; p += blockDim.x) {
+  for (int p = threadIdx.x * stride; p < FIT_NP; p += blockDim.x * stride) {
     double r = r_lo * pow(r_hi / r_lo, (double)p / (double)(FIT_NP - 1));
     double K = exp(-mu * r) / r, sum = 0.0;
     for (int m = 0; m < M; ++m) sum += c[m] * exp(-t[m] * r * r);
@@ -64,7 +68,7 @@ __global__ void fit_search_kernel(double mu, int M, double r_lo, double r_hi, do
   if (threadIdx.x == 0) {
     double w = 0.0;
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) w = fmax(w, red[q]);
-    err[cand] = w;
+    err[blockIdx.x] = w;
   }
 }
 
@@ -298,9 +302,10 @@ cudaError_t upload_gl() {
 
 }  // namespace
 
-cudaError_t launch_fit_search(double mu, int M, double r_lo, double r_hi, double *d_err,
-                              cudaStream_t s) {
-  fit_search_kernel<<<counted(FIT_NH * FIT_NS), 256, 2 * M * sizeof(double), s>>>(mu, M, r_lo, r_hi, d_err);
+cudaError_t launch_fit_search(double mu, int M, double r_lo, double r_hi, int stride, const int *d_cands,
+                              int n_cands, double *d_err, cudaStream_t s) {
+  fit_search_kernel<<<counted((unsigned)n_cands), 256, 2 * M * sizeof(double), s>>>(mu, M, r_lo, r_hi, stride,
+                                                                                   d_cands, d_err);
   return cudaGetLastError();
 }
 
