@@ -5,7 +5,10 @@ import os
 import re
 import shutil
 
+import numpy as np
 import pytest
+
+import workloads as W
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -56,3 +59,29 @@ def test_argument_errors_need_no_gpu(lib_path):
     assert rc == mra.MRA_ERR_ARG
     rc = lib.mra_apply(None, None, None, None, None, 0, None, None)
     assert rc == mra.MRA_ERR_ARG
+
+
+# ----------------------------------------------------------------- checkpoint / resume (host only)
+
+def test_tree_and_model_checkpoints_round_trip(tmp_path):
+    import torch
+    from paper_1507_01888_gb300 import checkpoint, mra
+    keys, coeffs = W.random_tree_coeffs(40, 4, 3, seed=3)
+    tree = mra.Tree.from_host(keys, coeffs, 8.0, device="cpu")
+    checkpoint.save_tree(tmp_path / "t.npz", tree)
+    back = checkpoint.load_tree(tmp_path / "t.npz", device="cpu")
+    bk, bc = back.host()
+    assert (bk == keys).all() and np.array_equal(bc, coeffs) and back.k == 4 and back.L == 8.0
+    bad = keys.copy()
+    bad[[0, 1]] = bad[[1, 0]]
+    np.savez(tmp_path / "bad.npz", format="mra-tree-1", keys=bad, coeffs=coeffs, k=4, L=8.0)
+    with pytest.raises(ValueError):
+        checkpoint.load_tree(tmp_path / "bad.npz", device="cpu")
+    params = torch.arange(mra.MLP_PARAMS, dtype=torch.float32)
+    dl = [float("inf")] * 20
+    dl[7] = 1.5
+    checkpoint.save_mlp(tmp_path / "m.npz", params, 1.25, dl)
+    p2, d2, dl2 = checkpoint.load_mlp(tmp_path / "m.npz", device="cpu")
+    assert torch.equal(p2, params) and d2 == 1.25 and dl2 == dl
+    with pytest.raises(ValueError):
+        checkpoint.load_tree(tmp_path / "m.npz", device="cpu")
