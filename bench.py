@@ -834,6 +834,7 @@ def main():
                        "kernel": "bsh" if w.kernel == W.BSH else "poisson", "mu": w.mu, "tau": w.tau,
                        "stencil": "shells<=%d" % w.max_disp if w.stencil == 0 else "27-point",
                        "terms_kept": terms, "pairs": st0["pairs"], "n_out": st0["n_out"],
+                       "per_level": {str(n): [c["sources"], c["terms_kept"]] for n, c in st0["levels"].items()},
                        "precision": precision, "l2": "flushed by a 256 MB write before every step",
                        "functions": len(trees), "tuning": tuning,
                        **({"launch": f"one CUDA graph per step ({graph.kernels_per_launch} library kernels "

@@ -126,6 +126,8 @@ typedef struct {
   double learned_skipped_bound;  /* sum of the norm-screen bounds of those triples */
   double algo_flops;  /* algorithmic flops of the kept triples: 6 k^4 + k^3 each, k the order
                          of the operator that applied them (k or 2k in the non-standard form) */
+  int64_t level_sources[MRA_MAX_LEVEL + 1];    /* source boxes per level */
+  int64_t level_terms_kept[MRA_MAX_LEVEL + 1]; /* kept triples per source level */
 } mra_apply_stats;
 
 typedef struct {

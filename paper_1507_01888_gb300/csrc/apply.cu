@@ -432,6 +432,24 @@ __global__ void compare_kernel(int64_t nt, const uint64_t *tk, const double *tc,
   }
 }
 
+// Per source level: boxes and kept triples (a shared-memory histogram per CTA, then one
+// integer atomic per level: the sums are exact whatever the order).
+__global__ void level_counts_kernel(int64_t n, const uint64_t *keys, const int64_t *kept, int64_t *lev) {
+  __shared__ unsigned long long hb[MRA_MAX_LEVEL + 1], ht[MRA_MAX_LEVEL + 1];
+  if (threadIdx.x <= MRA_MAX_LEVEL) hb[threadIdx.x] = ht[threadIdx.x] = 0ull;
+  __syncthreads();
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+    const int l = key_level(keys[b]);
+    atomicAdd(&hb[l], 1ull);
+    atomicAdd(&ht[l], (unsigned long long)kept[b]);
+  }
+  __syncthreads();
+  if (threadIdx.x <= MRA_MAX_LEVEL) {
+    if (hb[threadIdx.x]) atomicAdd((unsigned long long *)&lev[threadIdx.x], hb[threadIdx.x]);
+    if (ht[threadIdx.x]) atomicAdd((unsigned long long *)&lev[MRA_MAX_LEVEL + 1 + threadIdx.x], ht[threadIdx.x]);
+  }
+}
+
 // Fixed-size (graph) mode: the record count the screen computed against the captured one.
 __global__ void fixed_count_check_kernel(const int64_t *off, const int64_t *cnt, int64_t n_in, int64_t P,
                                          const int *d_err, int *status) {
@@ -524,7 +542,7 @@ int64_t apply_max_records(const Operator &op, const mra_apply_opts &o, int64_t n
 //   CUB temp storage (max over scan / sort / reduce needs)
 struct Layout {
   size_t snorm, dstop, cnt, off, kept, screened, skipped, trunc, learned, lbound, ldrop;
-  size_t rkey, rsrc, rl, rmask, skey, pin, pout, head, did, dkey, seg, ndest, dfunc, fnoff, split, tmp;
+  size_t rkey, rsrc, rl, rmask, skey, pin, pout, head, did, dkey, seg, ndest, dfunc, fnoff, lev, split, tmp;
   size_t split_bytes, tmp_bytes, total;
 };
 
@@ -562,6 +580,7 @@ static Layout make_layout(int64_t n_in, int64_t P, bool learned) {
   L.ndest = take(8);
   L.dfunc = take(np * 4);
   L.fnoff = take((MRA_MAX_FUNCS + 1) * 8);
+  L.lev = take(2 * (MRA_MAX_LEVEL + 1) * 8);
   L.split_bytes = split_workspace_bytes(np);
   L.split = take(L.split_bytes);
   // CUB temporary storage: the largest of the calls below
@@ -597,6 +616,7 @@ struct WsPtrs {
   int64_t *seg, *ndest;
   int *dfunc;
   int64_t *fnoff;
+  int64_t *lev;  // per level: source boxes, kept triples
   void *tmp;
   size_t tmpb;
 };
@@ -629,6 +649,7 @@ static WsPtrs carve(const Layout &L, void *ws) {
   p.ndest = (int64_t *)(w + L.ndest);
   p.dfunc = (int *)(w + L.dfunc);
   p.fnoff = (int64_t *)(w + L.fnoff);
+  p.lev = (int64_t *)(w + L.lev);
   p.tmp = w + L.tmp;
   p.tmpb = L.tmp_bytes;
   return p;
@@ -711,17 +732,23 @@ static int screen_run(const Operator &op, const mra_tree_view &in, const mra_app
     MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, w.blearned, red_i + 3, (int)n_in, s));
     MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, w.bskip, red_d, (int)n_in, s));
     MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tmpb, w.blbound, red_d + 1, (int)n_in, s));
+    MRA_CUDA_TRY(cudaMemsetAsync(w.lev, 0, 2 * (MRA_MAX_LEVEL + 1) * sizeof(int64_t), s));
+    level_counts_kernel<<<counted((unsigned)std::min<int64_t>((n_in + 255) / 256, 1024)), 256, 0, s>>>(
+        n_in, in.keys, w.bkept, w.lev);
+    MRA_CUDA_TRY(cudaGetLastError());
   }
   int64_t h_last[2] = {0, 0};
   int h_err = 0;
   int64_t hs[4] = {0, 0, 0, 0};
   double hd[2] = {0.0, 0.0};
+  int64_t hl[2 * (MRA_MAX_LEVEL + 1)] = {};
   MRA_CUDA_TRY(cudaMemcpyAsync(&h_last[0], w.off + n_in - 1, 8, cudaMemcpyDeviceToHost, s));
   MRA_CUDA_TRY(cudaMemcpyAsync(&h_last[1], w.cnt + n_in - 1, 8, cudaMemcpyDeviceToHost, s));
   MRA_CUDA_TRY(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   if (stats) {
     MRA_CUDA_TRY(cudaMemcpyAsync(hs, red_i, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     MRA_CUDA_TRY(cudaMemcpyAsync(hd, red_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MRA_CUDA_TRY(cudaMemcpyAsync(hl, w.lev, sizeof(hl), cudaMemcpyDeviceToHost, s));
   }
   MRA_CUDA_TRY(cudaStreamSynchronize(s));
   if (h_err == 3)
@@ -745,6 +772,10 @@ static int screen_run(const Operator &op, const mra_tree_view &in, const mra_app
     stats->terms_learned_skipped = hs[3];
     stats->learned_skipped_bound = hd[1];
     stats->algo_flops = (double)hs[0] * (6.0 * op.k * op.k * op.k * op.k + (double)op.k * op.k * op.k);
+    for (int n = 0; n <= MRA_MAX_LEVEL; ++n) {
+      stats->level_sources[n] = hl[n];
+      stats->level_terms_kept[n] = hl[MRA_MAX_LEVEL + 1 + n];
+    }
   }
   if (P > 0) {
     screen_kernel<1><<<counted(gboxes), 32 * wpb, ssm, s>>>(a);

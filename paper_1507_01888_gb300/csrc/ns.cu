@@ -820,6 +820,10 @@ extern "C" int mra_apply_ns(const mra_operator *h, const mra_operator *hns, cons
     acc.skipped_bound += st.skipped_bound;
     acc.kernel_ms += st.kernel_ms;
     acc.algo_flops += st.algo_flops;
+    for (int q = 0; q <= MRA_MAX_LEVEL; ++q) {
+      acc.level_sources[q] += st.level_sources[q];
+      acc.level_terms_kept[q] += st.level_terms_kept[q];
+    }
   };
   void *aws = w + Lw.apply;
   // one apply on every box of level n: its output rows scattered into a zeroed dense array
@@ -1039,6 +1043,10 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
     acc.skipped_bound += st.skipped_bound;
     acc.kernel_ms += st.kernel_ms;
     acc.algo_flops += st.algo_flops;
+    for (int q = 0; q <= MRA_MAX_LEVEL; ++q) {
+      acc.level_sources[q] += st.level_sources[q];
+      acc.level_terms_kept[q] += st.level_terms_kept[q];
+    }
     *nout = vout.n;
     return MRA_OK;
   };

@@ -77,10 +77,14 @@ class ApplyStats(ctypes.Structure):
                 ("terms_issued", ctypes.c_int64), ("sources_truncated", ctypes.c_int64),
                 ("skipped_bound", ctypes.c_double), ("kernel_ms", ctypes.c_double),
                 ("terms_learned_skipped", ctypes.c_int64), ("learned_skipped_bound", ctypes.c_double),
-                ("algo_flops", ctypes.c_double)]
+                ("algo_flops", ctypes.c_double), ("level_sources", ctypes.c_int64 * 20),
+                ("level_terms_kept", ctypes.c_int64 * 20)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {f: getattr(self, f) for f, _ in self._fields_[:-2]}
+        d["levels"] = {n: {"sources": int(self.level_sources[n]), "terms_kept": int(self.level_terms_kept[n])}
+                       for n in range(20) if self.level_sources[n] > 0}
+        return d
 
 
 class CompareResult(ctypes.Structure):

@@ -141,6 +141,10 @@ def test_fp64_apply_shells_and_screen_adaptive(mra):
     fp64_box_check(*out.host(), ref)
     assert st["terms_kept"] == ref.terms
     assert st["sources_truncated"] == ref.truncated
+    # per-level statistics: boxes by level, and kept terms summing to the total
+    lv = (ok >> np.uint64(57)).astype(int)
+    assert {n: c["sources"] for n, c in st["levels"].items()} == {int(n): int((lv == n).sum()) for n in np.unique(lv)}
+    assert sum(c["terms_kept"] for c in st["levels"].values()) == st["terms_kept"]
 
 
 def test_fp64_paper_worked_example_on_gpu(mra):
