@@ -259,37 +259,46 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(TT)) apply_split_kerne
         tc::mma_bf16(d + (uint32_t)(t * 48 + 16 * p), adesc(A, p, t), bdesc(B), idesc_n(P - p), p > 0 ? 1u : 0u);
     }
   };
-  // element [contraction a][row (i, b, d)] for d = 0..k-1 of this thread's row, into operand A
-  auto store_run = [&](unsigned char *A, int mrow, int a_idx, const float *v) {
-    const int stride = T * TILE_BYTES;
-    if constexpr (K % 8 == 0) {
-      // mrow is a multiple of 8: each run of 8 rows is one 16-byte core-matrix row, written
-      // with one vector store per piece (lanes of a quarter warp then hit distinct banks)
+  // store units of a thread's run: 16-byte core-matrix rows when 8 divides k, else 4-byte pairs
+  constexpr int U = K % 8 == 0 ? K / 8 : K / 2;
+  // shared-memory addresses of the store units of element [contraction a][rows (i, b, 0..k-1)]
+  // in the first piece of operand A (the others follow at T * TILE_BYTES): fixed per thread
+  auto run_addrs = [&](const unsigned char *A, int mrow, int a_idx, uint32_t *addr) {
+    const uint32_t a0 = tc::smem_u32(A);
 #pragma unroll
-      for (int d0 = 0; d0 < K; d0 += 8) {
+    for (int u = 0; u < U; ++u) addr[u] = a0 + a_off(mrow + (K % 8 == 0 ? 8 : 2) * u, a_idx);
+  };
+  auto st32 = [](uint32_t addr, uint32_t v) { asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory"); };
+  auto st128 = [](uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+  };
+  // a thread's k values split into P pieces, stored at its precomputed unit addresses
+  auto store_units = [&](const uint32_t *addr, const float *v) {
+    const uint32_t stride = T * TILE_BYTES;
+    if constexpr (K % 8 == 0) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
         uint32_t w0[4], w1[4], w2[4];
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
           __nv_bfloat162 h0, h1, h2;
-          split_pair(v[d0 + 2 * h], v[d0 + 2 * h + 1], h0, h1, h2);
+          split_pair(v[8 * u + 2 * h], v[8 * u + 2 * h + 1], h0, h1, h2);
           w0[h] = *(uint32_t *)&h0;
           w1[h] = *(uint32_t *)&h1;
           w2[h] = *(uint32_t *)&h2;
         }
-        uint32_t off = a_off(mrow + d0, a_idx);
-        *(uint4 *)(A + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-        *(uint4 *)(A + stride + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-        if (P > 2) *(uint4 *)(A + 2 * stride + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+        st128(addr[u], w0[0], w0[1], w0[2], w0[3]);
+        st128(addr[u] + stride, w1[0], w1[1], w1[2], w1[3]);
+        if (P > 2) st128(addr[u] + 2 * stride, w2[0], w2[1], w2[2], w2[3]);
       }
     } else {
 #pragma unroll
-      for (int d = 0; d < K; d += 2) {
+      for (int u = 0; u < U; ++u) {
         __nv_bfloat162 h0, h1, h2;
-        split_pair(v[d], v[d + 1], h0, h1, h2);
-        uint32_t off = a_off(mrow + d, a_idx);
-        *(__nv_bfloat162 *)(A + off) = h0;
-        *(__nv_bfloat162 *)(A + stride + off) = h1;
-        if (P > 2) *(__nv_bfloat162 *)(A + 2 * stride + off) = h2;
+        split_pair(v[2 * u], v[2 * u + 1], h0, h1, h2);
+        st32(addr[u], *(uint32_t *)&h0);
+        st32(addr[u] + stride, *(uint32_t *)&h1);
+        if (P > 2) st32(addr[u] + 2 * stride, *(uint32_t *)&h2);
       }
     }
   };
@@ -316,6 +325,15 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(TT)) apply_split_kerne
 
   if (wg == 0) {
     // ======================================================= warpgroup 0
+    // where this thread's stage-1 output row (i, jy, jz) goes in the stage-2 operand:
+    // element [jy][(i, jz, 0..k-1)]
+    uint32_t a2_addr[T][U];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+      const int m1 = min(t * 128 + quarter * 32 + lane, rows - 1);
+      const int i = m1 / k2, rem = m1 - i * k2, jy = rem / k, jz = rem - jy * k;
+      run_addrs(A2, i * k2 + jz * k, jy, a2_addr[t]);
+    }
     uint32_t p1 = 0;
     int it = 0;
     int nfetch = 0;  // block copies issued (thread 32), for iterations 0 .. nfetch-1 in order
@@ -439,11 +457,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(TT)) apply_split_kerne
           if (!((tiles >> t) & 1u)) continue;
           float v[K];
           load_d(tD1, t, v);
-          int m1 = t * 128 + quarter * 32 + lane;
-          if (m1 < rows) {
-            int i = m1 / k2, rem = m1 - i * k2, jy = rem / k, jz = rem - jy * k;
-            store_run(A2, i * k2 + jz * k, jy, v);
-          }
+          if (t * 128 + quarter * 32 + lane < rows) store_units(a2_addr[t], v);
         }
         tc::fence_proxy_async_smem();
         tc::fence_before_sync();
@@ -481,6 +495,15 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(TT)) apply_split_kerne
     }
   } else {
     // ======================================================= warpgroup 1
+    // where this thread's stage-2 output row (i, jz, ix) goes in the stage-3 operand:
+    // element [jz][(i, ix, 0..k-1)]
+    uint32_t a3_addr[T][U];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+      const int m2 = min(t * 128 + quarter * 32 + lane, rows - 1);
+      const int i = m2 / k2, rem = m2 - i * k2, jz = rem / k, ix = rem - jz * k;
+      run_addrs(A3, i * k2 + ix * k, jz, a3_addr[t]);
+    }
     // per-slot sums as FP32 pairs hi + lo, added to with compensated (Kahan) summation on the
     // FP32 pipe; the FP64 pipe (1/64 rate) only forms hi + lo at the end.  In one-slot tiles up
     // to JOIN consecutive terms are summed in D3 by the stage-3 MMAs before one flush adds them.
@@ -541,11 +564,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(TT)) apply_split_kerne
 #pragma unroll
       for (int t = 0; t < T; ++t) {
         if (!((tiles >> t) & 1u)) continue;
-        int m2 = t * 128 + quarter * 32 + lane;
-        if (m2 < rows) {
-          int i = m2 / k2, rem = m2 - i * k2, jz = rem / k, ix = rem - jz * k;
-          store_run(A3, i * k2 + ix * k, jz, v[t]);
-        }
+        if (t * 128 + quarter * 32 + lane < rows) store_units(a3_addr[t], v[t]);
       }
       // this term's stage 3 adds onto D3 when the tile holds one slot and D3 has room;
       // otherwise D3 is flushed first and overwritten.  With several slots the rounding of a
