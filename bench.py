@@ -245,7 +245,8 @@ def run_ns(args, w, rank, world):
     dev = torch.device("cuda", 0)
     n0, D = w.extra["ns"]["n0"], w.max_disp
     adaptive = w.uniform_level < 0
-    prec = mra.PREC_FP64 if args.precision == "fp64" else mra.PREC_SPLIT_BF16
+    # orders 2k above 16 are applied in FP64 only
+    prec = mra.PREC_FP64 if args.precision == "fp64" or 2 * w.k > 16 else mra.PREC_SPLIT_BF16
     tree = mra.project(w.funcs[0], w.k, w.L, thresh=w.thresh, init_level=w.init_level, max_level=w.max_level,
                        uniform_level=w.uniform_level)
     keys_h0 = tree.host()[0]

@@ -141,6 +141,14 @@ def bsh_ns_adaptive_k8() -> Workload:
                     extra={"ns": {"n0": 1}})
 
 
+def bsh_ns_adaptive_k10() -> Workload:
+    """Non-standard form apply of the mixed-precision BSH workload's function at its own k=10
+    (2k = 20, applied in FP64), thresh 1e-6, |l|_inf <= 1 at every level below level 1."""
+    return Workload("bsh_ns_adaptive_k10", [gaussian_sum(8, 1.0, 1e4, seed=2)], k=10, L=L_CELL, thresh=1e-6,
+                    uniform_level=-1, kernel=BSH, mu=1.0, M=60, fit_eps=1e-6, stencil=0, max_disp=1, tau=0.0,
+                    extra={"ns": {"n0": 1}})
+
+
 def bsh_k10_reconstruct_truncate() -> Workload:
     """Sum-down and truncation (Sec. 2.1-2.2) of the mixed-precision BSH workload's leaf-level
     apply result: the multi-level box sum is summed down into disjoint leaves (mra_reconstruct)
@@ -180,6 +188,7 @@ WORKLOADS = {
     "poisson_m100_adaptive_k14": poisson_k14_large,
     "poisson_ns_uniform_l5_k6": poisson_ns_uniform_k6,
     "bsh_ns_adaptive_k8": bsh_ns_adaptive_k8,
+    "bsh_ns_adaptive_k10": bsh_ns_adaptive_k10,
     "bsh_m60_k10_reconstruct_truncate": bsh_k10_reconstruct_truncate,
     "hydrogen_bsh_k6": hydrogen_bsh_k6,
 }
