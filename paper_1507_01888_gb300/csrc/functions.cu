@@ -137,6 +137,13 @@ int align(const mra_tree_view &a, const mra_tree_view &b, Pool &pool, cudaStream
     if (ka[i] <= ka[i - 1]) return fail(MRA_ERR_ARG, "mra_multiply/inner: first tree's keys not sorted and unique");
   for (size_t i = 1; i < kb.size(); ++i)
     if (kb[i] <= kb[i - 1]) return fail(MRA_ERR_ARG, "mra_multiply/inner: second tree's keys not sorted and unique");
+  if (ka == kb) {  // already on the same leaves
+    *n_out = a.n;
+    *keys_out = a.keys;
+    *ca = a.coeffs;
+    *cb = b.coeffs;
+    return MRA_OK;
+  }
   std::vector<uint64_t> u;
   std::set_union(ka.begin(), ka.end(), kb.begin(), kb.end(), std::back_inserter(u));
   const int64_t nu = (int64_t)u.size();
@@ -159,11 +166,31 @@ int align(const mra_tree_view &a, const mra_tree_view &b, Pool &pool, cudaStream
     ext_rows_kernel<<<counted((unsigned)nu), 128, 0, s>>>(nu, k3, dib, b.coeffs, eb);
     MRA_CUDA_TRY(cudaGetLastError());
   }
-  // sum both down to the common leaves
+  // sum both down to the common leaves; a tree whose own leaves turn out to be the common
+  // leaves (the other tree's are all at or above them) is used as it is
   uint64_t *rk[2] = {nullptr, nullptr};
   double *rc[2] = {nullptr, nullptr};
   int64_t rn[2] = {0, 0};
-  for (int w = 0; w < 2; ++w) {
+  const bool b_finer = b.n >= a.n;  // reconstruct the coarser tree first
+  for (int pass = 0; pass < 2; ++pass) {
+    const int w = (pass == 0) == b_finer ? 0 : 1;
+    if (pass == 1) {
+      const std::vector<uint64_t> &own = w == 0 ? ka : kb;
+      const int o = 1 - w;
+      if (rn[o] == (int64_t)own.size()) {
+        std::vector<uint64_t> got(rn[o]);
+        if (rn[o]) {
+          MRA_CUDA_TRY(cudaMemcpyAsync(got.data(), rk[o], rn[o] * 8, cudaMemcpyDeviceToHost, s));
+          MRA_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+        if (got == own) {
+          rk[w] = w == 0 ? a.keys : b.keys;
+          rc[w] = w == 0 ? a.coeffs : b.coeffs;
+          rn[w] = rn[o];
+          break;
+        }
+      }
+    }
     int64_t cap = std::max<int64_t>(8 * nu, 1);
     while (true) {
       rk[w] = (uint64_t *)pool.get(cap * 8);
