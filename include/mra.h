@@ -159,6 +159,16 @@ long long mra_launch_count(void);
  * intact, and later calls run normally.  One-shot; nothing else is changed. */
 int mra_debug_inject_stall(void);
 
+/* The checking build (libmra_debug.so, compiled with MRA_DEBUG): the hot kernels' gather and
+ * scatter indices (records, sources, operator blocks) are checked against their ranges; an
+ * index out of range is replaced by 0, so the access stays in bounds, and the first failing
+ * source line is kept.  mra_debug_status synchronises `stream`, writes that line (0: no
+ * failure since the last call) to *line and clears it; the release build always writes 0.
+ * mra_debug_selftest sends one out-of-range index through the check (a test of the checking
+ * path itself; a no-op in the release build). */
+int mra_debug_status(int *line, void *stream);
+int mra_debug_selftest(void *stream);
+
 /* Thread-local description of the last error (never NULL). */
 const char *mra_last_error(void);
 

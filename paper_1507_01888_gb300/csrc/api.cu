@@ -145,6 +145,17 @@ const char *mra_version(void) { return "mra-gb300 0.1 (sm_103a)"; }
 
 long long mra_launch_count(void) { return mra::g_launches.load(std::memory_order_relaxed); }
 
+int mra_debug_status(int *line, void *stream) {
+  if (!line) return fail(MRA_ERR_ARG, "mra_debug_status: NULL line");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int a = debug_line_apply(s), b = debug_line_split(s);
+  if (a < 0 || b < 0) return fail(MRA_ERR_CUDA, "mra_debug_status: reading the check words failed");
+  *line = a ? a : b;
+  return MRA_OK;
+}
+
+int mra_debug_selftest(void *stream) { return debug_selftest_run((cudaStream_t)stream); }
+
 int mra_operator_create(int kernel, double mu, int M, double fit_eps, double r_lo, double r_hi,
                         int k, double L, int min_level, int max_level, int max_disp,
                         mra_operator **out, void *stream) {

@@ -85,6 +85,7 @@ struct ScreenArgs {
   double *box_skipped;
   int *box_trunc;
   int *err;
+  int64_t rec_cap;            // records the workspace holds (index checks of the checking build)
   // learned screen (MRA_SCREEN_LEARNED): drop a kept term when mlp(features) < learned_cut
   const float *mlp;
   const double *t;            // Gaussian exponents (features)
@@ -246,12 +247,13 @@ __global__ void screen_kernel(ScreenArgs a) {
           kept += pk;
           screened += a.M - pk;
           if (PASS == 1 && lane == 0) {
-            a.rec_key[wpos] = a.nfunc > 1 ? batched_key(func, n, x + lx, y + ly, z + lz)
-                                          : make_key(n, x + lx, y + ly, z + lz);
-            a.rec_src[wpos] = (int)b;
-            a.rec_l[wpos] = (lx + 128) | ((ly + 128) << 8) | ((lz + 128) << 16);
-            a.rec_mask[2 * wpos] = mask[0];
-            a.rec_mask[2 * wpos + 1] = mask[1];
+            const int64_t wp = MRA_IDX(wpos, a.rec_cap);
+            a.rec_key[wp] = a.nfunc > 1 ? batched_key(func, n, x + lx, y + ly, z + lz)
+                                        : make_key(n, x + lx, y + ly, z + lz);
+            a.rec_src[wp] = (int)b;
+            a.rec_l[wp] = (lx + 128) | ((ly + 128) << 8) | ((lz + 128) << 16);
+            a.rec_mask[2 * wp] = mask[0];
+            a.rec_mask[2 * wp + 1] = mask[1];
           }
           ++wpos;
           ++count;
@@ -319,7 +321,7 @@ __global__ void __launch_bounds__(F64_THREADS) apply_f64_kernel(
     int k, int M, const double *c, const double *R, const int *Dlev, const int64_t *level_off,
     const uint64_t *in_keys, const double *in_coeffs, const int64_t *seg, const int *perm,
     const int *rec_src, const int *rec_l, const uint64_t *rec_mask, const uint64_t *dest_key,
-    uint64_t *out_keys, double *out_coeffs) {
+    uint64_t *out_keys, double *out_coeffs, int64_t n_src, int64_t n_rec, int64_t n_blocks) {
   extern __shared__ double sm[];
   int k2 = k * k, k3 = k2 * k;
   double *s = sm, *t1 = s + k3, *t2 = t1 + k3, *Rs = t2 + k3;  // Rs: 3 * k2
@@ -328,14 +330,13 @@ __global__ void __launch_bounds__(F64_THREADS) apply_f64_kernel(
   int n = key_level(dkey);
   int Dop = Dlev[n];
   int nl = 2 * Dop + 1;
-  const double *Rlev = R + level_off[n] * k2;
   double acc[PT];
 #pragma unroll
   for (int q = 0; q < PT; ++q) acc[q] = 0.0;
   int64_t r0 = seg[dst], r1 = seg[dst + 1];
   for (int64_t r = r0; r < r1; ++r) {
-    int p = perm[r];
-    int src = rec_src[p];
+    int p = MRA_IDX(perm[MRA_IDX(r, n_rec)], n_rec);
+    int src = MRA_IDX(rec_src[p], n_src);
     int lp = rec_l[p];
     int lx = (lp & 255) - 128, ly = ((lp >> 8) & 255) - 128, lz = ((lp >> 16) & 255) - 128;
     uint64_t mk[2] = {rec_mask[2 * (int64_t)p], rec_mask[2 * (int64_t)p + 1]};
@@ -348,9 +349,10 @@ __global__ void __launch_bounds__(F64_THREADS) apply_f64_kernel(
         int m = w * 64 + __ffsll((long long)bits) - 1;
         bits &= bits - 1;
         __syncthreads();
-        const double *Rx = Rlev + ((int64_t)m * nl + lx + Dop) * k2;
-        const double *Ry = Rlev + ((int64_t)m * nl + ly + Dop) * k2;
-        const double *Rz = Rlev + ((int64_t)m * nl + lz + Dop) * k2;
+        const int64_t lo = level_off[n];
+        const double *Rx = R + MRA_IDX(lo + (int64_t)m * nl + lx + Dop, n_blocks) * k2;
+        const double *Ry = R + MRA_IDX(lo + (int64_t)m * nl + ly + Dop, n_blocks) * k2;
+        const double *Rz = R + MRA_IDX(lo + (int64_t)m * nl + lz + Dop, n_blocks) * k2;
         for (int e = threadIdx.x; e < k2; e += blockDim.x) {
           Rs[e] = Rx[e];
           Rs[k2 + e] = Ry[e];
@@ -448,6 +450,12 @@ __global__ void level_counts_kernel(int64_t n, const uint64_t *keys, const int64
     if (hb[threadIdx.x]) atomicAdd((unsigned long long *)&lev[threadIdx.x], hb[threadIdx.x]);
     if (ht[threadIdx.x]) atomicAdd((unsigned long long *)&lev[MRA_MAX_LEVEL + 1 + threadIdx.x], ht[threadIdx.x]);
   }
+}
+
+// The checking build's self test: one index outside its range through MRA_IDX.
+__global__ void debug_selftest_kernel(int *sink) {
+  const int i = MRA_IDX(5, 3);
+  sink[i] = 1;
 }
 
 // Fixed-size (graph) mode: the record count the screen computed against the captured one.
@@ -695,6 +703,7 @@ static int screen_run(const Operator &op, const mra_tree_view &in, const mra_app
   a.box_skipped = w.bskip;
   a.box_trunc = w.btrunc;
   a.err = d_err;
+  a.rec_cap = Pmax;
   a.mlp = o.screen == MRA_SCREEN_LEARNED ? o.mlp : nullptr;
   a.t = op.d_t;
   for (int n = 0; n <= MRA_MAX_LEVEL; ++n) {
@@ -890,7 +899,7 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
       MRA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<counted((unsigned)nd), F64_THREADS, smem, s>>>(
         k, op.M, op.d_c, op.d_R, op.d_D, op.d_level_off, in.keys, in.coeffs, seg, pout, rsrc, rl,
-        rmask, dkey, out.keys, out.coeffs);
+        rmask, dkey, out.keys, out.coeffs, n_in, P, op.n_blocks);
     MRA_CUDA_TRY(cudaGetLastError());
     if (ev1) MRA_CUDA_TRY(cudaEventRecord(ev1, s));
     rc = MRA_OK;
@@ -1103,6 +1112,18 @@ int norm_run(const mra_tree_view &t, double *per_box, double *total, cudaStream_
 }
 
 
+
+int debug_line_apply(cudaStream_t s) { return debug_take_line(s); }
+
+int debug_selftest_run(cudaStream_t s) {
+  int *sink = nullptr;
+  MRA_CUDA_TRY(cudaMallocAsync((void **)&sink, sizeof(int), s));
+  debug_selftest_kernel<<<counted(1), 1, 0, s>>>(sink);
+  MRA_CUDA_TRY(cudaGetLastError());
+  MRA_CUDA_TRY(cudaFreeAsync(sink, s));
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  return MRA_OK;
+}
 
 int compare_run(const mra_tree_view &t, const mra_tree_view &r, mra_compare_result *res,
                 cudaStream_t s) {

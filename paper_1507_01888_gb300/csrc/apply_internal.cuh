@@ -50,6 +50,7 @@ int log_terms_run(const Operator &op, const mra_tree_view &in, const mra_apply_o
                   uint64_t seed, float *features, float *log_norms, int64_t *n_logged, void *ws,
                   size_t ws_bytes, cudaStream_t s);
 int norm_run(const mra_tree_view &t, double *per_box, double *total, cudaStream_t s);
+int debug_selftest_run(cudaStream_t s);
 int compare_run(const mra_tree_view &t, const mra_tree_view &r, mra_compare_result *res,
                 cudaStream_t s);
 

@@ -88,6 +88,7 @@ struct SplitArgs {
   double *out_coeffs;
   int *err;
   int inject_stall;  // test hook: CTA 0 never issues the block copies of its first term
+  int64_t n_src, n_rec, n_blocks;  // sizes for the index checks of the checking build
 };
 
 // Named barrier over one warpgroup (128 threads) with an OR vote.
@@ -353,9 +354,11 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(TT)) apply_split_kerne
       }
       tc::mbar_arrive_expect_tx(bar, 3 * BSTAGE_BYTES);
       const int64_t blk0 = lbase + (int64_t)m * nl + Dop;
-      tc::bulk_g2s(tc::smem_u32(Bb), a.Bsplit + (blk0 + lx) * BSTAGE_BYTES, BSTAGE_BYTES, bar);
-      tc::bulk_g2s(tc::smem_u32(Bb + BSTAGE_BYTES), a.Bsplit + (blk0 + ly) * BSTAGE_BYTES, BSTAGE_BYTES, bar);
-      tc::bulk_g2s(tc::smem_u32(Bb + 2 * BSTAGE_BYTES), a.Bsplit_c + (blk0 + lz) * BSTAGE_BYTES, BSTAGE_BYTES, bar);
+      const int64_t bx = MRA_IDX(blk0 + lx, a.n_blocks), by = MRA_IDX(blk0 + ly, a.n_blocks),
+                    bz = MRA_IDX(blk0 + lz, a.n_blocks);
+      tc::bulk_g2s(tc::smem_u32(Bb), a.Bsplit + bx * BSTAGE_BYTES, BSTAGE_BYTES, bar);
+      tc::bulk_g2s(tc::smem_u32(Bb + BSTAGE_BYTES), a.Bsplit + by * BSTAGE_BYTES, BSTAGE_BYTES, bar);
+      tc::bulk_g2s(tc::smem_u32(Bb + 2 * BSTAGE_BYTES), a.Bsplit_c + bz * BSTAGE_BYTES, BSTAGE_BYTES, bar);
       ++nfetch;
       return true;
     };
@@ -368,8 +371,8 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(TT)) apply_split_kerne
       if (tid == 0) uni[0] = uni[1] = 0ull;
       wg_sync(1);
       for (int r = r0 + tid; r < r1; r += 128) {
-        int i = a.val2[r];
-        int p = a.perm[i];
+        int i = MRA_IDX(a.val2[MRA_IDX(r, a.n_rec)], a.n_rec);
+        int p = MRA_IDX(a.perm[i], a.n_rec);
         int slot = (a.did[i] - 1) - tile * G;
         if (slot < 0 || slot >= G) {
           atomicExch(a.err, 2);
@@ -407,7 +410,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(TT)) apply_split_kerne
         int jx = rest / k2, q = rest - jx * k2;
         int src = slot_src[i];
         double2 xx = make_double2(0.0, 0.0);
-        if (src >= 0) xx = *(const double2 *)(a.in_coeffs + (int64_t)src * k3 + rest);
+        if (src >= 0) xx = *(const double2 *)(a.in_coeffs + (int64_t)MRA_IDX(src, a.n_src) * k3 + rest);
         __nv_bfloat162 h0, h1, h2;
         split_pair((float)xx.x, (float)xx.y, h0, h1, h2);
         uint32_t off = a_off(i * k2 + q, jx);
@@ -807,6 +810,9 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
   a.out_coeffs = out.coeffs;
   a.err = err;
   a.inject_stall = take_injected_stall() ? 1 : 0;
+  a.n_src = in.n;
+  a.n_rec = P;
+  a.n_blocks = op.n_blocks;
   size_t smem = (size_t)3 * a.P * T * TILE_BYTES + (size_t)nbuf_for(tt) * BTERM_BYTES;
   // no more CTAs per SM than the tensor memory holds (512 columns): otherwise an extra
   // CTA's allocation would wait for a resident CTA to finish
@@ -854,6 +860,10 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
   return MRA_OK;
 }
 
+}  // namespace mra
+
+namespace mra {
+int debug_line_split(cudaStream_t s) { return debug_take_line(s); }
 }  // namespace mra
 
 extern "C" int mra_debug_inject_stall(void) {

@@ -34,6 +34,37 @@ inline G counted(G grid) {
   return grid;
 }
 
+// ---------------------------------------------------------------- index checks
+// The checking build (-DMRA_DEBUG) routes indices of the hot kernels' gathers and scatters
+// through MRA_IDX(i, n): an index outside [0, n) is replaced by 0, so the access stays in
+// bounds, and the first failing source line is kept in a device word of the translation unit,
+// which mra_debug_status reads.  In the release build MRA_IDX(i, n) is i.
+#ifdef MRA_DEBUG
+static __device__ int g_debug_line;
+template <class I, class N>
+__device__ __forceinline__ I debug_idx(I i, N n, int line) {
+  if (i < 0 || (long long)i >= (long long)n) {
+    atomicCAS(&g_debug_line, 0, line);
+    return (I)0;
+  }
+  return i;
+}
+#define MRA_IDX(i, n) ::mra::debug_idx((i), (n), __LINE__)
+// the translation unit's first failing line since the last read (0: none), cleared
+static inline int debug_take_line(cudaStream_t s) {
+  int h = 0, z = 0;
+  if (cudaMemcpyFromSymbolAsync(&h, g_debug_line, sizeof(int), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess) return -1;
+  if (cudaMemcpyToSymbolAsync(g_debug_line, &z, sizeof(int), 0, cudaMemcpyHostToDevice, s) != cudaSuccess) return -1;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+  return h;
+}
+#else
+#define MRA_IDX(i, n) (i)
+static inline int debug_take_line(cudaStream_t) { return 0; }
+#endif
+int debug_line_apply(cudaStream_t s);
+int debug_line_split(cudaStream_t s);
+
 // ---------------------------------------------------------------- keys
 __host__ __device__ inline uint64_t make_key(int n, int64_t x, int64_t y, int64_t z) {
   return ((uint64_t)n << 57) | ((uint64_t)x << 38) | ((uint64_t)y << 19) | (uint64_t)z;

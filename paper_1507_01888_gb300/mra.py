@@ -42,7 +42,7 @@ EXPORTED = [
     "mra_operator_ns_create", "mra_apply_ns_workspace_size", "mra_apply_ns", "mra_apply_ns_tree",
     "mra_reconstruct", "mra_truncate", "mra_multiply", "mra_inner", "mra_launch_count",
     "mra_apply_graph_create", "mra_apply_graph_launch", "mra_apply_graph_status", "mra_apply_graph_info",
-    "mra_apply_graph_free", "mra_debug_inject_stall",
+    "mra_apply_graph_free", "mra_debug_inject_stall", "mra_debug_status", "mra_debug_selftest",
 ]
 NOALLOC_MAX_BOXES = 1 << 20
 
@@ -114,12 +114,17 @@ def library_path() -> str:
 
 
 def load(build_if_stale: bool = True):
-    """Load libmra.so, compiling it first if it is missing or older than its sources."""
+    """Load libmra.so, compiling it first if it is missing or older than its sources.  With
+    MRA_DEBUG=1 in the environment the checking build libmra_debug.so is loaded instead."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.build() if build_if_stale else _build.LIB
+        debug = os.environ.get("MRA_DEBUG", "0") == "1"
+        if build_if_stale:
+            path = _build.build(debug=debug)
+        else:
+            path = _build.DEBUG_LIB if debug else _build.LIB
         if not os.path.exists(path):
             raise RuntimeError(f"libmra.so not found at {path}; run __graft_entry__.build()")
         lib = ctypes.CDLL(path)
@@ -128,6 +133,7 @@ def load(build_if_stale: bool = True):
         lib.mra_last_error.restype = ctypes.c_char_p
         lib.mra_version.restype = ctypes.c_char_p
         lib.mra_launch_count.restype = ctypes.c_longlong
+        lib.mra_debug_status.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]
         lib.mra_project.argtypes = [P(GaussSum), i, d, d, i, i, i, P(TreeView), vp]
         lib.mra_operator_create.argtypes = [i, d, i, d, d, d, i, d, i, i, i, P(vp), vp]
         lib.mra_operator_fit.argtypes = [vp, P(d), P(d), P(d), P(d), P(d)]
@@ -667,6 +673,19 @@ def multiply(a: "Tree", b: "Tree", stream=None) -> "Tree":
         _check(rc)
         out.n = int(vo.n)
         return out
+
+
+def debug_status(stream=None) -> int:
+    """mra_debug_status: 0, or the source line of the first failed index check since the last
+    call (checking build only; the release build always reports 0)."""
+    line = ctypes.c_int()
+    _check(load().mra_debug_status(ctypes.byref(line), _stream(stream)))
+    return int(line.value)
+
+
+def debug_selftest(stream=None):
+    """mra_debug_selftest: one out-of-range index through the checking path (checking build)."""
+    _check(load().mra_debug_selftest(_stream(stream)))
 
 
 def debug_inject_stall():
