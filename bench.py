@@ -56,6 +56,12 @@ def parse():
     p.add_argument("--clocks-csv", default=None, help="also write the nvidia-smi samples here")
     p.add_argument("--learned-quantile", type=float, default=1.0,
                    help="learned-screen margin: this quantile of the held-out residuals (1 = largest)")
+    p.add_argument("--dist-backend", default="nccl", choices=["nccl", "gloo"],
+                   help="torch.distributed backend for N > 1 (gloo: host-side exchange, for tests)")
+    p.add_argument("--partition", action="store_true",
+                   help="N > 1, one function: each rank computes a destination key range (owner "
+                        "computes) after an all-gather of the input parts (strong scaling) instead "
+                        "of running a replica")
     return p.parse_args()
 
 
@@ -463,6 +469,92 @@ def run_post(args, w, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def run_partitioned(args, w, rank, world, local):
+    """One function over N ranks by destination key ranges (owner computes).  Each rank holds
+    its key range of the input tree; a step is the all-gather of the parts (NCCL) and the
+    rank's apply on its halo of sources with its destination range.  value = the function's
+    boxes / the slowest rank's step time (strong scaling: the total work is fixed)."""
+    import torch
+    import torch.distributed as dist
+    from paper_1507_01888_gb300 import mra, partition as PT
+    dev = torch.device("cuda", local)
+    prec = mra.PREC_FP64 if args.precision == "fp64" else mra.PREC_SPLIT_BF16
+    tree = mra.project(w.funcs[0], w.k, w.L, thresh=w.thresh, init_level=w.init_level, max_level=w.max_level,
+                       uniform_level=w.uniform_level)
+    keys_h, coeffs_h = tree.host()
+    lv = (keys_h >> np.uint64(57)).astype(int)
+    lo, hi = PT.split_ranges(keys_h, world)[rank]
+    own = PT.in_range(keys_h, lo, hi)
+    halo_idx = torch.from_numpy(np.nonzero(PT.halo_mask(keys_h, lo, hi, w.max_disp))[0]).to(dev)
+    local_keys = tree.keys[: tree.n][torch.from_numpy(own).to(dev)].contiguous()
+    local_coeffs = tree.coeffs[: tree.n][torch.from_numpy(own).to(dev)].contiguous()
+    op = mra.Operator(w.kernel, w.M, w.k, w.L, int(lv.min()), int(lv.max()), max_disp=w.max_disp, mu=w.mu,
+                      fit_eps=w.fit_eps)
+    screen = mra.SCREEN_NORM if w.tau > 0 else mra.SCREEN_NONE
+    opts = mra.make_opts(precision=prec, pieces=args.pieces, screen=screen, tau=w.tau, stencil=w.stencil,
+                         max_disp=w.max_disp, tile_variant=2 if prec == mra.PREC_SPLIT_BF16 and 4 <= w.k <= 10 else 0,
+                         dest_range=(lo, hi))
+    sub = mra.Tree(tree.keys[halo_idx].contiguous(), tree.coeffs[halo_idx].contiguous(), int(halo_idx.numel()),
+                   w.k, w.L)
+    ap = mra.Applier(op, sub, opts)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        keys_all, coeffs_all = PT.exchange(local_keys, local_coeffs)
+        torch.index_select(keys_all, 0, halo_idx, out=sub.keys)
+        torch.index_select(coeffs_all, 0, halo_idx, out=sub.coeffs)
+        ap(sub, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks_start(args.clocks_csv)
+    launches0 = mra.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kms = []
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        kms.append(ap.stats.kernel_ms)
+    torch.cuda.synchronize()
+    launches = mra.launch_count() - launches0
+    dist.barrier()
+    clocks = clocks_stop(clk, local)
+    ms_local = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    t = torch.tensor([ms_local], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    terms = torch.tensor([float(ap.stats.terms_kept)], dtype=torch.float64, device=dev)
+    dist.all_reduce(terms, op=dist.ReduceOp.SUM)
+    kmax = torch.tensor([statistics.mean(kms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(kmax, op=dist.ReduceOp.MAX)
+    pk, pk_kind = peaks()
+    k = w.k
+    achieved = terms.item() * (6 * k ** 4 + k ** 3) / (kmax.item() / 1e3) / 1e12
+    peak = pk.get("bf16_tflops", 1856.3) * world if prec == mra.PREC_SPLIT_BF16 else FP64_PEAK_TFLOPS * world
+    line = {"metric": METRIC, "value": tree.n / (ms / 1e3), "unit": "boxes/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None,
+            "dtype": "f64" if prec == mra.PREC_FP64 else f"bf16x{args.pieces}-split, f32 accumulate, f64 term sum",
+            "data": "synthetic",
+            "config": {"workload": w.name, "n_boxes": tree.n, "k": k, "M": w.M,
+                       "parallelism": f"{world} ranks, destination key ranges (owner computes), "
+                                      f"{args.dist_backend} all-gather of the input parts every step",
+                       "l2": "inputs gathered anew every step"},
+            "roofline": {"bound": "tensor" if prec == mra.PREC_SPLIT_BF16 else "alu", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "kernel": "apply kernel, slowest rank", "peak_source": f"{world} x per-GPU peak, {pk_kind}"},
+            "clocks": clocks, "gpu_launches": launches,
+            "e2e": {"value": None, "unit": "boxes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                    "note": "not measured in the partitioned mode (inputs are exchanged between devices)"}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+
+
 def oracle_post_step(w):
     """The oracle's own multi-level result of the same workload (untimed), then its sum-down and
     truncation, timed as one whole step."""
@@ -615,12 +707,15 @@ def main():
     import torch
     from paper_1507_01888_gb300 import mra
 
+    local = local % max(torch.cuda.device_count(), 1)
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group(args.dist_backend)
     dev = torch.device("cuda", local)
     w = W.shard(W.WORKLOADS[args.workload](), rank, world)
+    if args.partition and world > 1 and len(w.funcs) == 1:
+        return run_partitioned(args, w, rank, world, local)
     precision = args.precision
     if precision == "auto":
         precision = "split"

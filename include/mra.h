@@ -110,6 +110,10 @@ typedef struct {
   const double *delta_level; /* MRA_SCREEN_LEARNED, optional (NULL = delta at every level): host
                                 array of MRA_MAX_LEVEL + 1 margins, one per source level, read
                                 during the call; +inf keeps every term of that level */
+  uint64_t dest_lo, dest_hi; /* destination partition (owner computes): only destinations whose
+                                key lies in [dest_lo, dest_hi) are computed and written, with the
+                                screen's shell decisions of the whole apply; dest_hi = 0 keeps all.
+                                mra_apply only (not batched, not the non-standard form) */
 } mra_apply_opts;
 
 typedef struct {

@@ -535,6 +535,8 @@ static int check_opts(const Operator *op, const mra_tree_view *in, const mra_app
   if (o->screen != MRA_SCREEN_NONE && !(o->tau >= 0.0)) return fail(MRA_ERR_ARG, "mra_apply: tau must be >= 0");
   if (o->precision == MRA_PREC_SPLIT_BF16 && (o->pieces < 2 || o->pieces > 3))
     return fail(MRA_ERR_ARG, "mra_apply: pieces must be 2 or 3");
+  if (o->dest_hi != 0 && o->dest_lo >= o->dest_hi)
+    return fail(MRA_ERR_ARG, "mra_apply: empty destination range");
   return MRA_OK;
 }
 
@@ -572,6 +574,7 @@ int mra_apply_batched(const mra_operator *h, int nfunc, const mra_tree_view *in,
   rc = check_view(out, "mra_apply_batched(out)", false);
   if (rc) return rc;
   if (nfunc < 1 || nfunc > MRA_MAX_FUNCS) return fail(MRA_ERR_ARG, "mra_apply_batched: nfunc=%d", nfunc);
+  if (o->dest_hi != 0) return fail(MRA_ERR_ARG, "mra_apply_batched: no destination range with several functions");
   if (!in_offsets || !out_offsets) return fail(MRA_ERR_ARG, "mra_apply_batched: NULL offsets");
   if (in_offsets[0] != 0 || in_offsets[nfunc] != in->n)
     return fail(MRA_ERR_ARG, "mra_apply_batched: offsets must run from 0 to in->n");

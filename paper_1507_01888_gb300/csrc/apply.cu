@@ -86,6 +86,7 @@ struct ScreenArgs {
   int *box_trunc;
   int *err;
   int64_t rec_cap;            // records the workspace holds (index checks of the checking build)
+  uint64_t dest_lo, dest_hi;  // keep destinations with keys in [dest_lo, dest_hi); dest_hi = 0: all
   // learned screen (MRA_SCREEN_LEARNED): drop a kept term when mlp(features) < learned_cut
   const float *mlp;
   const double *t;            // Gaussian exponents (features)
@@ -200,6 +201,10 @@ __global__ void screen_kernel(ScreenArgs a) {
           if (x + lx < 0 || x + lx >= nb || y + ly < 0 || y + ly >= nb || z + lz < 0 ||
               z + lz >= nb)
             continue;
+          // destinations outside the caller's key range are screened (so that the shell logic
+          // is that of the whole apply) but neither counted nor emitted
+          const uint64_t tkey = make_key(n, x + lx, y + ly, z + lz);
+          const bool owned = a.dest_hi == 0 || (tkey >= a.dest_lo && tkey < a.dest_hi);
           uint64_t mask[2] = {0ull, 0ull};
           for (int m0 = 0; m0 < a.M; m0 += 32) {
             int m = m0 + lane;
@@ -226,24 +231,25 @@ __global__ void screen_kernel(ScreenArgs a) {
                 }
               }
             }
-            if (PASS == 0) {
+            if (PASS == 0 && owned) {
               unsigned lb = __ballot_sync(0xffffffffu, dropped_by_model);
               learned += __popc(lb);
               lbound += warp_sum(dropped_by_model ? B : 0.0);
             }
             unsigned bal = __ballot_sync(0xffffffffu, keep);
             mask[m0 >> 6] |= (uint64_t)bal << (m0 & 63);
-            if (PASS == 0) {
+            if (PASS == 0 && owned) {
               double sk = (m < a.M && !keep && !dropped_by_model) ? B : 0.0;
               skipped += warp_sum(sk);
             }
           }
           int pk = __popcll(mask[0]) + __popcll(mask[1]);
           if (pk == 0) {
-            screened += a.M;
+            if (owned) screened += a.M;
             continue;
           }
           any = 1;
+          if (!owned) continue;
           kept += pk;
           screened += a.M - pk;
           if (PASS == 1 && lane == 0) {
@@ -704,6 +710,8 @@ static int screen_run(const Operator &op, const mra_tree_view &in, const mra_app
   a.box_trunc = w.btrunc;
   a.err = d_err;
   a.rec_cap = Pmax;
+  a.dest_lo = o.dest_lo;
+  a.dest_hi = o.dest_hi;
   a.mlp = o.screen == MRA_SCREEN_LEARNED ? o.mlp : nullptr;
   a.t = op.d_t;
   for (int n = 0; n <= MRA_MAX_LEVEL; ++n) {

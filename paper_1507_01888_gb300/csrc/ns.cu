@@ -643,6 +643,7 @@ int ns_check(const Operator *op, const Operator *ns, const mra_tree_view *in, in
     return fail(MRA_ERR_ARG, "mra_apply_ns: unknown precision %d", o->precision);
   if (o->precision == MRA_PREC_SPLIT_BF16 && (o->pieces < 2 || o->pieces > 3))
     return fail(MRA_ERR_ARG, "mra_apply_ns: pieces must be 2 or 3");
+  if (o->dest_hi != 0) return fail(MRA_ERR_ARG, "mra_apply_ns: no destination range in the non-standard form");
   if (o->precision == MRA_PREC_SPLIT_BF16 && ns->k > MRA_MAX_K)
     return fail(MRA_ERR_UNSUPPORTED, "mra_apply_ns: order 2k=%d is applied in FP64 only (split precision to %d)",
                 ns->k, MRA_MAX_K);
@@ -898,6 +899,7 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
   if (in->n >= (1LL << 31)) return fail(MRA_ERR_ARG, "mra_apply_ns_tree: more than 2^31 leaves");
   if (out->k != op->k || out->cap < 0 || (out->cap > 0 && (!out->keys || !out->coeffs)))
     return fail(MRA_ERR_ARG, "mra_apply_ns_tree: bad output view");
+  if (o->dest_hi != 0) return fail(MRA_ERR_ARG, "mra_apply_ns_tree: no destination range in the non-standard form");
   if (o->precision != MRA_PREC_FP64 && o->precision != MRA_PREC_SPLIT_BF16)
     return fail(MRA_ERR_ARG, "mra_apply_ns_tree: unknown precision %d", o->precision);
   if (o->precision == MRA_PREC_SPLIT_BF16 && (o->pieces < 2 || o->pieces > 3))

@@ -66,3 +66,78 @@ def test_shard_is_identity_for_one_rank():
     assert W.shard(w, 0, 1) is w
     w0 = W.shard(w, 0, 2)
     assert [f["cx"][0] for f in w0.funcs] == [f["cx"][0] for f in w.funcs]  # rank 0 keeps part 0
+
+
+# ----------------------------------------------------------------- destination partition
+
+def _partition_rank(rank, world, port, q):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1507_01888_gb300 import partition as PT
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        keys, coeffs = W.random_tree_coeffs(300, 3, 4, seed=5)
+        ranges = PT.split_ranges(keys, world)
+        lo, hi = ranges[rank]
+        own = PT.in_range(keys, lo, hi)
+        k_all, c_all = PT.exchange(torch.from_numpy(keys[own].view(np.int64).copy()),
+                                   torch.from_numpy(coeffs[own].copy()))
+        q.put((rank, k_all.numpy().view(np.uint64).copy(), c_all.numpy().copy(), lo, hi))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_partition_exchange_gives_every_rank_the_whole_tree():
+    """Three gloo ranks hold disjoint key ranges of a tree; the all-gather gives each the whole
+    tree in key order."""
+    import numpy as np
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    world = 3
+    procs = [ctx.Process(target=_partition_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = {}
+    for _ in range(world):
+        r = q.get(timeout=120)
+        res[r[0]] = r
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    keys, coeffs = W.random_tree_coeffs(300, 3, 4, seed=5)
+    for r in range(world):
+        assert (res[r][1] == keys).all() and np.array_equal(res[r][2], coeffs)
+    # the ranges tile the key space in order
+    assert res[0][3] == 0 and res[world - 1][4] == int(np.uint64(0xFFFFFFFFFFFFFFFF))
+    for r in range(world - 1):
+        assert res[r][4] == res[r + 1][3]
+
+
+def test_partition_ranges_and_halo_by_brute_force():
+    import numpy as np
+    from paper_1507_01888_gb300 import partition as PT
+    keys, _ = W.random_tree_coeffs(200, 3, 3, seed=7)
+    ranges = PT.split_ranges(keys, 4)
+    owned = sum(PT.in_range(keys, lo, hi).astype(int) for lo, hi in ranges)
+    assert (owned == 1).all()                      # every box owned by exactly one rank
+    counts = [int(PT.in_range(keys, lo, hi).sum()) for lo, hi in ranges]
+    assert max(counts) - min(counts) <= 1          # balanced by box count
+    n, x, y, z = PT._split_key(keys)
+    for lo, hi in ranges:
+        halo = PT.halo_mask(keys, lo, hi, 1)
+        for i in range(len(keys)):                 # brute force: some in-cell neighbour key in range
+            nb = 1 << int(n[i])
+            want = False
+            for lx in (-1, 0, 1):
+                for ly in (-1, 0, 1):
+                    for lz in (-1, 0, 1):
+                        a, b, c = x[i] + lx, y[i] + ly, z[i] + lz
+                        if 0 <= a < nb and 0 <= b < nb and 0 <= c < nb:
+                            t = (int(n[i]) << 57) | (int(a) << 38) | (int(b) << 19) | int(c)
+                            want |= lo <= t < hi
+            assert bool(halo[i]) == want
