@@ -36,7 +36,7 @@ import workloads as W  # noqa: E402
 # DRAM bytes (read + written) of one launch of the dominant kernel, from a one-pass ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of this bench's own command, keyed by
 # (workload, tile variant).  An entry is removed whenever the kernel changes.
-SPLIT_TRAFFIC = {("bsh_m60_adaptive_k10", 2): 71.32e6 + 77.84e6}
+SPLIT_TRAFFIC = {("bsh_m60_adaptive_k10", 2): 70.93e6 + 77.63e6}
 
 METRIC = "3D operator-apply boxes/s & % roofline, mixed vs FP64 GPU at 1e-6 rel L2"
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no FP64 figure in the measured peaks)
