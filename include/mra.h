@@ -324,9 +324,9 @@ int mra_apply_batched(const mra_operator *op, int nfunc, const mra_tree_view *in
  *
  * mra_operator_ns_create: the 2k-basis operator of levels op.min_level .. op.max_level-1
  * with displacements |l| <= max_disp, assembled on the device from op's blocks (op needs
- * max_disp >= 2 max_disp + 1 for that); its own norms and BF16 pieces.  2k <= MRA_MAX_K.
- * Caller frees it with mra_operator_free.  It is an operator of order 2k: mra_apply can
- * use it on trees of (2k)^3 coefficients. */
+ * max_disp >= 2 max_disp + 1 for that); its own norms, and its BF16 pieces when 2k <=
+ * MRA_MAX_K.  2k <= MRA_MAX_NS_K; orders above MRA_MAX_K are applied with MRA_PREC_FP64 only
+ * (a split request returns MRA_ERR_UNSUPPORTED).  Caller frees it with mra_operator_free. */
 int mra_operator_ns_create(const mra_operator *op, int max_disp, mra_operator **ns_op, void *stream);
 
 /* Workspace bytes of mra_apply_ns (device memory the caller provides, 256-byte aligned). */
