@@ -45,7 +45,7 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no FP64 figure in the measur
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="bsh_m60_adaptive_k10", choices=sorted(W.WORKLOADS))
