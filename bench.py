@@ -104,20 +104,27 @@ def _candidate_dests(keys):
     return np.unique(np.concatenate(out))
 
 
-def cpu_baseline(w, target_s=12.0, seed=12345):
-    """The oracle, as it stands, on a seeded sample of destination boxes sized for about
-    target_s seconds of work; whole-job time is extrapolated by the sample's share of kept
-    terms (the oracle's own whole-job term count).  Returns a dict."""
+def cpu_prepare(w):
+    """The oracle's projection and fit of the workload, and the time of its per-apply set-up
+    (blocks, norms, screen, destination set), measured once."""
     import oracle as O
     keys, coeffs, _ = O.project(w.funcs[0], w.k, w.L, thresh=w.thresh, init_level=w.init_level,
                                 max_level=w.max_level, uniform_level=w.uniform_level)
     _, _, _, c, t = oracle_fit(w)
-    cores = os.cpu_count() or 1
-    kw = dict(stencil=w.stencil, max_disp=w.max_disp, tau=w.tau)
     never = np.array([np.uint64(0xFFFFFFFFFFFFFFFF)], dtype=np.uint64)
     t0 = time.perf_counter()
-    O.apply(keys, coeffs, c, t, w.L, sample_keys=never, **kw)  # blocks, norms, screen, destination set
-    t_setup = time.perf_counter() - t0
+    O.apply(keys, coeffs, c, t, w.L, sample_keys=never, stencil=w.stencil, max_disp=w.max_disp, tau=w.tau)
+    return keys, coeffs, c, t, time.perf_counter() - t0
+
+
+def cpu_baseline(w, target_s=12.0, seed=12345, prepared=None):
+    """The oracle, as it stands, on a seeded sample of destination boxes sized for about
+    target_s seconds of work; whole-job time is extrapolated by the sample's share of kept
+    terms (the oracle's own whole-job term count).  Returns a dict."""
+    import oracle as O
+    keys, coeffs, c, t, t_setup = prepared if prepared is not None else cpu_prepare(w)
+    cores = os.cpu_count() or 1
+    kw = dict(stencil=w.stencil, max_disp=w.max_disp, tau=w.tau)
     cand = _candidate_dests(keys) if w.stencil == 1 or w.max_disp <= 1 else keys
     rng = np.random.default_rng(seed)
     n_try = min(64, len(cand))
@@ -196,8 +203,10 @@ def run_reference(args, rank, world):
         return
     times = []
     info = None
+    prepared = cpu_prepare(w)  # projection and fit once; every step is a sampled apply
     for i in range(args.warmup + args.steps):
-        info = cpu_baseline(w, args.cpu_seconds / max(args.steps + args.warmup, 1) * 2, seed=1000 + i)
+        info = cpu_baseline(w, args.cpu_seconds / max(args.steps + args.warmup, 1) * 2, seed=1000 + i,
+                            prepared=prepared)
         if i >= args.warmup:
             times.append(info)
     per = [x["t_sample"] * x["terms_total"] / max(x["sample_terms"], 1) for x in times]
