@@ -100,7 +100,7 @@ def test_fit_error_matches_extended_precision(mu, M, r_hi):
     ref = _mp_maxerr(mu, c, t, 1e-4, r_hi)
     # 3000-point FP64 estimate and a 1430-point extended-precision estimate agree
     assert 0.8 * err <= ref <= 1.05 * err
-    # the surveyed error level at the literal term counts
+    # the error level the trapezoid fit reaches at these term counts (M = 20 and 60)
     assert err < {20: 2.5e-2, 60: 1e-4}[M] if M in (20, 60) and mu in (0.0, 1.0) and r_hi > 12 else True
 
 
