@@ -930,6 +930,13 @@ def main():
                 "kernel": "apply_split_kernel",
                 "peak_source": f"bf16 dense burst, {pk_kind}", "kernel_ms": kms,
                 "flops": "algorithmic (6k^4+k^3 per kept term)"}
+        if int(opts.tile_variant) == 2 and k * k <= 128 and 128 // (k * k) == 1 and args.pieces == 3:
+            # one slot per 128-row tile: each kept term issues 3 + 3 + 5 MMAs of M=128, K=16 with
+            # N = 48, 32, 16 | 48, 32, 16 | 32, 16, 16, 16, 16 -- the tensor core's own work
+            issued = terms * 2 * 128 * 16 * (96 + 96 + 96) / (kms / 1e3) / 1e12
+            roof["issued"] = {"tflops": issued, "frac": issued / peak,
+                              "note": "BF16 flops the MMAs issue (padding to 128x16x16 tiles and the six "
+                                      "piece products included); context only, not the algorithmic rate"}
         dtype = f"bf16x{args.pieces}-split, f32 accumulate, f64 term sum"
 
     line = {"metric": METRIC, "value": value, "unit": "boxes/s", "n_gpus": world, "steps": args.steps,
