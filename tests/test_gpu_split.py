@@ -168,3 +168,21 @@ def test_split_edge_cases(mra):
     gk, gc = out.host()
     assert (gk == ref.keys).all() and rel_l2(gc, ref.coeffs) <= TOL_MIXED
     assert st["terms_kept"] == ref.terms
+
+
+def test_zero_function_and_screen_that_keeps_nothing(mra):
+    """Degenerate inputs: an all-zero tree (the norm screen drops every term: no destination, no
+    error; without a screen every destination is exactly zero), and a tau above every bound."""
+    keys, coeffs = W.random_tree_coeffs(30, 6, 3, seed=31)
+    op = mra.Operator(0, 10, 6, 16.0, 0, 3, max_disp=1, fit_eps=1e-4)
+    zero = mra.Tree.from_host(keys, np.zeros_like(coeffs), 16.0)
+    for prec in (0, 1):
+        out, st = mra.apply(op, zero, mra.make_opts(precision=prec, stencil=mra.STENCIL_NEAREST,
+                                                    screen=mra.SCREEN_NORM, tau=1e-30))
+        assert out.n == 0 and st["terms_kept"] == 0
+        out, st = mra.apply(op, zero, mra.make_opts(precision=prec, stencil=mra.STENCIL_NEAREST))
+        assert out.n > 0 and not out.host()[1].any()
+        out, st = mra.apply(op, mra.Tree.from_host(keys, coeffs, 16.0),
+                            mra.make_opts(precision=prec, stencil=mra.STENCIL_NEAREST, screen=mra.SCREEN_NORM,
+                                          tau=1e300))
+        assert out.n == 0 and st["terms_kept"] == 0 and st["terms_screened"] > 0
