@@ -594,8 +594,9 @@ def run_solver(args, w, rank, world):
     V, vfit = solvers.project_potential(cfg["Z"], w.k, w.L, w.thresh, M=cfg["M_potential"])
     psi = solvers.gaussian_start(cfg["Z"], w.k, w.L, w.thresh)
     E, hist = cfg["E0"], []
+    cache = {}
     for _ in range(40):
-        E, psi, dE = solvers.bsh_step(V, psi, E, w.thresh, w.M, w.fit_eps, prec)
+        E, psi, dE = solvers.bsh_step(V, psi, E, w.thresh, w.M, w.fit_eps, prec, cache=cache)
         hist.append(E)
         if abs(dE) < 1e-3 * w.thresh:
             break
@@ -605,7 +606,7 @@ def run_solver(args, w, rank, world):
     state = {"E": E}
 
     def step(p=psi):
-        E1, new, _ = solvers.bsh_step(V, p, state["E"], w.thresh, w.M, w.fit_eps, prec, info=info)
+        E1, new, _ = solvers.bsh_step(V, p, state["E"], w.thresh, w.M, w.fit_eps, prec, info=info, cache=cache)
         return new
 
     ms, clocks, launches = _timed(args, step, dev)

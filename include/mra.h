@@ -213,6 +213,14 @@ int mra_operator_create(int kernel, double mu, int M, double fit_eps, double r_l
                         mra_operator **op, void *stream);
 
 /* Copy the fit out of an operator (host arrays of length M; any may be NULL). */
+/* The BSH operator refitted in place for a new mu (an iteration whose energy changed): the
+ * Gaussian fit is searched again; when it lands on the same grid point (h, s_lo) the exponents
+ * t_m, and so every block, are unchanged and only c_m and the c_m-scaled tensor-core pieces are
+ * recomputed (*blocks_reused = 1), otherwise the blocks are computed again (0).  The result is
+ * the operator mra_operator_create would make for mu.  Non-standard-form operators built from
+ * op must be created again. */
+int mra_operator_refit(mra_operator *op, double mu, int *blocks_reused, void *stream);
+
 int mra_operator_fit(const mra_operator *op, double *c, double *t, double *h, double *s_lo,
                      double *max_rel_err);
 

@@ -135,6 +135,69 @@ long long launch_total() { return g_launches.load(std::memory_order_relaxed); }
 
 }  // namespace mra
 
+namespace mra {
+// The Gaussian fit of the operator's kernel (mu_fit = 0: 1/r) on [r_lo, r_hi]: op->h_fit, s_lo,
+// fit_err, c, t (host copies).
+static int fit_operator(Operator *op, double mu_fit, int M, double r_lo, double r_hi, cudaStream_t s) {
+  // The grid's argmin of the max relative error over the 3000 points, the first (lowest
+  // index) of equal minima.  Exact with far fewer evaluations: the maximum over every tenth
+  // point is a lower bound of each candidate's error, so candidates are evaluated in full in
+  // increasing order of that bound until the bound exceeds the best full error found; no
+  // candidate left out can reach it.
+  const int NC = 116 * 113, SUB = 10, BATCH = 256;
+  double *d_err = nullptr;
+  int *d_cand = nullptr;
+  if (cudaMalloc((void **)&d_err, NC * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void **)&d_cand, BATCH * sizeof(int)) != cudaSuccess) {
+    cudaFree(d_err);
+    return fail(MRA_ERR_CUDA, "fit search: cudaMalloc failed");
+  }
+  std::vector<double> lower(NC), full(NC, -1.0);
+  cudaError_t e = launch_fit_search(mu_fit, M, r_lo, r_hi, SUB, nullptr, NC, d_err, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(lower.data(), d_err, NC * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  std::vector<int> order(NC);
+  for (int q = 0; q < NC; ++q) order[q] = q;
+  // NaN bounds (never produced by the finite grid) sort last and are evaluated like the rest
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const bool na = std::isnan(lower[a]), nb = std::isnan(lower[b]);
+    return na != nb ? nb : (!na && lower[a] < lower[b]);
+  });
+  int best = -1, pos = 0;
+  while (e == cudaSuccess && pos < NC && (best < 0 || !(lower[order[pos]] > full[best]))) {
+    const int nb = std::min(BATCH, NC - pos);
+    std::vector<double> part(nb);
+    e = cudaMemcpyAsync(d_cand, order.data() + pos, nb * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_fit_search(mu_fit, M, r_lo, r_hi, 1, d_cand, nb, d_err, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(part.data(), d_err, nb * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (int q = 0; q < nb && e == cudaSuccess; ++q) {
+      const int c = order[pos + q];
+      full[c] = part[q];
+      if (best < 0 || part[q] < full[best] || (part[q] == full[best] && c < best)) best = c;
+    }
+    pos += nb;
+  }
+  cudaFree(d_err);
+  cudaFree(d_cand);
+  if (e != cudaSuccess) return fail(MRA_ERR_CUDA, "fit search: %s", cudaGetErrorString(e));
+  op->h_fit = (5.0 + best / 113) / 100.0;
+  op->s_lo = (best % 113 - 100.0) / 4.0;
+  op->fit_err = full[best];
+  if (!std::isfinite(op->fit_err)) return fail(MRA_ERR_NUMERIC, "fit search produced a non-finite error");
+  op->c.resize(M);
+  op->t.resize(M);
+  const double pi = 3.14159265358979323846264338327950288;
+  for (int m = 0; m < M; ++m) {
+    double sm = op->s_lo + m * op->h_fit;
+    op->c[m] = 2.0 / sqrt(pi) * op->h_fit * exp(sm - mu_fit * mu_fit * exp(-2.0 * sm) / 4.0);
+    op->t[m] = exp(2.0 * sm);
+  }
+  return MRA_OK;
+}
+
+}  // namespace mra
+
 using namespace mra;
 
 extern "C" {
@@ -172,7 +235,8 @@ int mra_operator_create(int kernel, double mu, int M, double fit_eps, double r_l
   if (max_disp < 0 || max_disp > 127) return fail(MRA_ERR_ARG, "mra_operator_create: max_disp outside 0..127");
   if (!(r_lo > 0.0)) return fail(MRA_ERR_ARG, "mra_operator_create: r_lo must be > 0");
   cudaStream_t s = (cudaStream_t)stream;
-  if (!(r_hi > 0.0)) {
+  const bool r_hi_auto = !(r_hi > 0.0);
+  if (r_hi_auto) {
     r_hi = 2.0 * L;
     if (kernel == MRA_BSH) {
       if (!(fit_eps > 0.0 && fit_eps < 1.0)) return fail(MRA_ERR_ARG, "mra_operator_create: fit_eps in (0,1) needed");
@@ -192,63 +256,13 @@ int mra_operator_create(int kernel, double mu, int M, double fit_eps, double r_l
   op->max_disp = max_disp;
   op->r_lo = r_lo;
   op->r_hi = r_hi;
+  op->r_hi_auto = r_hi_auto;
+  op->fit_eps = fit_eps;
   auto bail = [&](int code) { free_operator(op); return code; };
   // ---- fit: grid search on the device, argmin on the host (first strict minimum)
   {
-    // The grid's argmin of the max relative error over the 3000 points, the first (lowest
-    // index) of equal minima.  Exact with far fewer evaluations: the maximum over every tenth
-    // point is a lower bound of each candidate's error, so candidates are evaluated in full in
-    // increasing order of that bound until the bound exceeds the best full error found; no
-    // candidate left out can reach it.
-    const int NC = 116 * 113, SUB = 10, BATCH = 256;
-    double *d_err = nullptr;
-    int *d_cand = nullptr;
-    if (cudaMalloc((void **)&d_err, NC * sizeof(double)) != cudaSuccess ||
-        cudaMalloc((void **)&d_cand, BATCH * sizeof(int)) != cudaSuccess) {
-      cudaFree(d_err);
-      return bail(fail(MRA_ERR_CUDA, "mra_operator_create: cudaMalloc failed"));
-    }
-    std::vector<double> lower(NC), full(NC, -1.0);
-    cudaError_t e = launch_fit_search(mu_fit, M, r_lo, r_hi, SUB, nullptr, NC, d_err, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(lower.data(), d_err, NC * sizeof(double), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    std::vector<int> order(NC);
-    for (int q = 0; q < NC; ++q) order[q] = q;
-    // NaN bounds (never produced by the finite grid) sort last and are evaluated like the rest
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-      const bool na = std::isnan(lower[a]), nb = std::isnan(lower[b]);
-      return na != nb ? nb : (!na && lower[a] < lower[b]);
-    });
-    int best = -1, pos = 0;
-    while (e == cudaSuccess && pos < NC && (best < 0 || !(lower[order[pos]] > full[best]))) {
-      const int nb = std::min(BATCH, NC - pos);
-      std::vector<double> part(nb);
-      e = cudaMemcpyAsync(d_cand, order.data() + pos, nb * sizeof(int), cudaMemcpyHostToDevice, s);
-      if (e == cudaSuccess) e = launch_fit_search(mu_fit, M, r_lo, r_hi, 1, d_cand, nb, d_err, s);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(part.data(), d_err, nb * sizeof(double), cudaMemcpyDeviceToHost, s);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-      for (int q = 0; q < nb && e == cudaSuccess; ++q) {
-        const int c = order[pos + q];
-        full[c] = part[q];
-        if (best < 0 || part[q] < full[best] || (part[q] == full[best] && c < best)) best = c;
-      }
-      pos += nb;
-    }
-    cudaFree(d_err);
-    cudaFree(d_cand);
-    if (e != cudaSuccess) return bail(fail(MRA_ERR_CUDA, "fit search: %s", cudaGetErrorString(e)));
-    op->h_fit = (5.0 + best / 113) / 100.0;
-    op->s_lo = (best % 113 - 100.0) / 4.0;
-    op->fit_err = full[best];
-    if (!std::isfinite(op->fit_err)) return bail(fail(MRA_ERR_NUMERIC, "fit search produced a non-finite error"));
-    op->c.resize(M);
-    op->t.resize(M);
-    const double pi = 3.14159265358979323846264338327950288;
-    for (int m = 0; m < M; ++m) {
-      double sm = op->s_lo + m * op->h_fit;
-      op->c[m] = 2.0 / sqrt(pi) * op->h_fit * exp(sm - mu_fit * mu_fit * exp(-2.0 * sm) / 4.0);
-      op->t[m] = exp(2.0 * sm);
-    }
+    const int rcf = fit_operator(op, mu_fit, M, r_lo, r_hi, s);
+    if (rcf != MRA_OK) return bail(rcf);
   }
   // ---- block table layout
   std::vector<int> Dabs(20, 0);
@@ -295,6 +309,48 @@ int mra_operator_create(int kernel, double mu, int M, double fit_eps, double r_l
     if (e != cudaSuccess) return bail(fail(MRA_ERR_CUDA, "split blocks: %s", cudaGetErrorString(e)));
   }
   *out = reinterpret_cast<mra_operator *>(op);
+  return MRA_OK;
+}
+
+int mra_operator_refit(mra_operator *h, double mu, int *blocks_reused, void *stream) {
+  Operator *op = reinterpret_cast<Operator *>(h);
+  if (!op) return fail(MRA_ERR_ARG, "mra_operator_refit: NULL operator");
+  if (op->kernel != MRA_BSH) return fail(MRA_ERR_ARG, "mra_operator_refit: only the BSH kernel depends on mu");
+  if (!(mu > 0.0)) return fail(MRA_ERR_ARG, "mra_operator_refit: mu must be > 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  const double r_hi = op->r_hi_auto ? std::min(2.0 * op->L, log(1.0 / op->fit_eps) / mu) : op->r_hi;
+  if (!(r_hi > op->r_lo)) return fail(MRA_ERR_ARG, "mra_operator_refit: empty fit range");
+  Operator fitted;
+  const int rc = fit_operator(&fitted, mu, op->M, op->r_lo, r_hi, s);
+  if (rc != MRA_OK) return rc;
+  // the exponents t_m depend on (h, s_lo) only: equal grid points give the same blocks
+  const bool same = fitted.h_fit == op->h_fit && fitted.s_lo == op->s_lo;
+  op->mu = mu;
+  op->r_hi = r_hi;
+  op->h_fit = fitted.h_fit;
+  op->s_lo = fitted.s_lo;
+  op->fit_err = fitted.fit_err;
+  op->c = fitted.c;
+  op->t = fitted.t;
+  MRA_CUDA_TRY(cudaMemcpyAsync(op->d_c, op->c.data(), op->M * 8, cudaMemcpyHostToDevice, s));
+  MRA_CUDA_TRY(cudaMemcpyAsync(op->d_t, op->t.data(), op->M * 8, cudaMemcpyHostToDevice, s));
+  if (!same) {
+    const int k = op->k;
+    double *d_gl = nullptr;
+    std::vector<double> glx(k + 1), glw(k + 1);
+    gauss_legendre(k + 1, glx.data(), glw.data());
+    cudaError_t e = cudaMalloc((void **)&d_gl, 2 * (k + 1) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_gl, glx.data(), (k + 1) * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_gl + k + 1, glw.data(), (k + 1) * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_blocks(*op, d_gl, d_gl + k + 1, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_gl);
+    if (e != cudaSuccess) return fail(MRA_ERR_CUDA, "operator blocks: %s", cudaGetErrorString(e));
+  }
+  const int rc2 = split_blocks_build(*op, s, true);  // the c_m-scaled pieces change with c_m
+  if (rc2 != MRA_OK) return rc2;
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  if (blocks_reused) *blocks_reused = same ? 1 : 0;
   return MRA_OK;
 }
 

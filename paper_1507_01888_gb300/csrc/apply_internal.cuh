@@ -45,7 +45,9 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
                     mra_tree_view &out, const ApplyWork &wk, mra_apply_stats *stats,
                     cudaStream_t s);
 size_t split_workspace_bytes(int64_t P);
-int split_blocks_build(Operator &op, cudaStream_t s);
+// BF16 pieces of the operator's blocks and of c_m times them (allocated once; rebuild = true
+// recomputes them, after the blocks or the coefficients changed)
+int split_blocks_build(Operator &op, cudaStream_t s, bool rebuild = false);
 int log_terms_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts &o, int64_t max_terms,
                   uint64_t seed, float *features, float *log_norms, int64_t *n_logged, void *ws,
                   size_t ws_bytes, cudaStream_t s);

@@ -730,10 +730,10 @@ size_t split_workspace_bytes(int64_t P) {
   return al(np * 8) * 2 + al(np * 4) * 5 + al((np + 2) * 4) * 2 + al(t) + 256;
 }
 
-int split_blocks_build(Operator &op, cudaStream_t s) {
-  if (op.d_Rsplit) return MRA_OK;
+int split_blocks_build(Operator &op, cudaStream_t s, bool rebuild) {
+  if (op.d_Rsplit && !rebuild) return MRA_OK;
   // two tables: the blocks R (stages 1 and 2) and c_m R (stage 3)
-  MRA_CUDA_TRY(cudaMalloc(&op.d_Rsplit, (size_t)2 * op.n_blocks * BSTAGE_BYTES));
+  if (!op.d_Rsplit) MRA_CUDA_TRY(cudaMalloc(&op.d_Rsplit, (size_t)2 * op.n_blocks * BSTAGE_BYTES));
   unsigned char *plain = (unsigned char *)op.d_Rsplit;
   unsigned char *scaled = plain + (size_t)op.n_blocks * BSTAGE_BYTES;
   for (size_t li = 0; li < op.D.size(); ++li) {

@@ -43,6 +43,7 @@ EXPORTED = [
     "mra_reconstruct", "mra_truncate", "mra_multiply", "mra_inner", "mra_launch_count",
     "mra_apply_graph_create", "mra_apply_graph_launch", "mra_apply_graph_status", "mra_apply_graph_info",
     "mra_apply_graph_free", "mra_debug_inject_stall", "mra_debug_status", "mra_debug_selftest",
+    "mra_operator_refit",
 ]
 NOALLOC_MAX_BOXES = 1 << 20
 
@@ -150,6 +151,7 @@ def load(build_if_stale: bool = True):
         lib.mra_apply_ns.argtypes = [vp, vp, P(TreeView), i, P(ApplyOpts), P(TreeView), vp, ctypes.c_size_t,
                                      P(ApplyStats), vp]
         lib.mra_apply_ns_tree.argtypes = [vp, vp, P(TreeView), i, P(ApplyOpts), P(TreeView), P(ApplyStats), vp]
+        lib.mra_operator_refit.argtypes = [vp, d, P(i), vp]
         lib.mra_apply_graph_create.argtypes = [vp, i, P(TreeView), P(ctypes.c_int64), P(ApplyOpts), P(TreeView),
                                                P(ctypes.c_int64), vp, ctypes.c_size_t, P(vp), vp]
         lib.mra_apply_graph_launch.argtypes = [vp, vp]
@@ -282,6 +284,14 @@ class Operator:
         _check(load().mra_operator_fit(self._h, _dptr(c), _dptr(t), ctypes.byref(h), ctypes.byref(s),
                                        ctypes.byref(e)))
         return {"c": c, "t": t, "h": h.value, "s_lo": s.value, "max_rel_err": e.value}
+
+    def refit(self, mu: float, stream=None) -> bool:
+        """mra_operator_refit: the BSH operator for a new mu, in place; True if the blocks were
+        kept (the fit landed on the same grid point)."""
+        reused = ctypes.c_int()
+        _check(load().mra_operator_refit(self._h, float(mu), ctypes.byref(reused), _stream(stream)))
+        self.mu = mu
+        return bool(reused.value)
 
     def block(self, level: int, m: int, l: int):
         import numpy as np

@@ -27,15 +27,27 @@ def project_potential(Z: float, k: int, L: float, thresh: float, M: int = 100, d
 
 
 def bsh_step(V, psi, E: float, thresh: float, M_bsh: int = 60, fit_eps: float = 1e-6,
-             precision: int = mra.PREC_SPLIT_BF16, screen: bool = True, max_disp: int = 1, info=None):
+             precision: int = mra.PREC_SPLIT_BF16, screen: bool = True, max_disp: int = 1, info=None,
+             cache=None):
     """One step of the fixed-point iteration: psi~ = -2 G_E (V psi) on the adaptive tree, truncated
     at `thresh`; returns (E + dE, psi~ normalised, dE) with dE = -<V psi, psi - psi~> / <psi~, psi~>.
-    If `info` is a dict it receives the non-standard apply's statistics and the tree sizes."""
+    If `info` is a dict it receives the non-standard apply's statistics and the tree sizes.  If
+    `cache` is a dict, the BSH operator of the previous step kept there is refitted to the new
+    energy (its blocks are kept when the fit lands on the same grid point) instead of made anew."""
     k, L = psi.k, psi.L
     Vpsi = mra.multiply(V, psi)
     top = int((Vpsi.keys[: Vpsi.n] >> 57).max().item())
     mu = math.sqrt(-2.0 * E)
-    op = mra.Operator(mra.BSH, M_bsh, k, L, 0, top, max_disp=2 * max_disp + 1, mu=mu, fit_eps=fit_eps)
+    op = cache.get("op") if cache is not None else None
+    if op is not None and (op.k, op.L, op.M, op.max_level, op.fit_eps) == (k, L, M_bsh, top, fit_eps):
+        reused = op.refit(mu)
+    else:
+        op = mra.Operator(mra.BSH, M_bsh, k, L, 0, top, max_disp=2 * max_disp + 1, mu=mu, fit_eps=fit_eps)
+        reused = False
+        if cache is not None:
+            cache["op"] = op
+    if info is not None:
+        info["blocks_reused"] = reused
     ns = mra.NSOperator(op, max_disp=max_disp)
     if screen:
         opts = mra.make_opts(precision=precision, stencil=mra.STENCIL_SHELLS, max_disp=max_disp,
@@ -74,8 +86,9 @@ def hydrogen(Z: float = 1.0, k: int = 8, L: float = 20.0, thresh: float = 1e-5, 
     psi = gaussian_start(Z, k, L, thresh, device=device)
     E = E0
     hist = []
+    cache = {}
     for it in range(iters):
-        E, psi, dE = bsh_step(V, psi, E, thresh, M_bsh, fit_eps, precision)
+        E, psi, dE = bsh_step(V, psi, E, thresh, M_bsh, fit_eps, precision, cache=cache)
         hist.append(E)
         if log:
             log(f"iter {it:2d}  E {E:.10f}  dE {dE:+.3e}  leaves {psi.n}")
