@@ -218,7 +218,8 @@ int mra_operator_create(int kernel, double mu, int M, double fit_eps, double r_l
  * t_m, and so every block, are unchanged and only c_m and the c_m-scaled tensor-core pieces are
  * recomputed (*blocks_reused = 1), otherwise the blocks are computed again (0).  The result is
  * the operator mra_operator_create would make for mu.  Non-standard-form operators built from
- * op must be created again. */
+ * op must be created again (refitting one of them is refused).  After an error the operator
+ * may be half updated: free it. */
 int mra_operator_refit(mra_operator *op, double mu, int *blocks_reused, void *stream);
 
 int mra_operator_fit(const mra_operator *op, double *c, double *t, double *h, double *s_lo,

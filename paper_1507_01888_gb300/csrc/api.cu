@@ -316,6 +316,8 @@ int mra_operator_refit(mra_operator *h, double mu, int *blocks_reused, void *str
   Operator *op = reinterpret_cast<Operator *>(h);
   if (!op) return fail(MRA_ERR_ARG, "mra_operator_refit: NULL operator");
   if (op->kernel != MRA_BSH) return fail(MRA_ERR_ARG, "mra_operator_refit: only the BSH kernel depends on mu");
+  if (op->non_standard)
+    return fail(MRA_ERR_ARG, "mra_operator_refit: refit the operator it was made from and create it again");
   if (!(mu > 0.0)) return fail(MRA_ERR_ARG, "mra_operator_refit: mu must be > 0");
   cudaStream_t s = (cudaStream_t)stream;
   const double r_hi = op->r_hi_auto ? std::min(2.0 * op->L, log(1.0 / op->fit_eps) / mu) : op->r_hi;

@@ -85,6 +85,7 @@ struct Operator {
   int min_level = 0, max_level = 0, max_disp = 0;
   double h_fit = 0.0, s_lo = 0.0, fit_err = 0.0, r_lo = 0.0, r_hi = 0.0, fit_eps = 0.0;
   bool r_hi_auto = false;                 // r_hi derived from (L, fit_eps, mu) at creation
+  bool non_standard = false;              // made by mra_operator_ns_create (blocks gathered, not fitted)
   std::vector<double> c, t;               // host copies of the fit
   std::vector<int> D;                     // per level (index n - min_level)
   std::vector<int64_t> level_off;         // first block index of each level

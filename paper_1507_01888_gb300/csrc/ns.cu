@@ -684,6 +684,7 @@ extern "C" int mra_operator_ns_create(const mra_operator *h, int max_disp, mra_o
     return code;
   };
   ns->kernel = op->kernel;
+  ns->non_standard = true;
   ns->mu = op->mu;
   ns->M = op->M;
   ns->k = 2 * op->k;
