@@ -144,7 +144,7 @@ static int fit_operator(Operator *op, double mu_fit, int M, double r_lo, double 
   // point is a lower bound of each candidate's error, so candidates are evaluated in full in
   // increasing order of that bound until the bound exceeds the best full error found; no
   // candidate left out can reach it.
-  const int NC = 116 * 113, SUB = 10, BATCH = 256;
+  const int NC = 116 * 113, SUB = 30, BATCH = 256;
   double *d_err = nullptr;
   int *d_cand = nullptr;
   if (cudaMalloc((void **)&d_err, NC * sizeof(double)) != cudaSuccess ||
