@@ -140,7 +140,7 @@ namespace mra {
 // fit_err, c, t (host copies).
 static int fit_operator(Operator *op, double mu_fit, int M, double r_lo, double r_hi, cudaStream_t s) {
   // The grid's argmin of the max relative error over the 3000 points, the first (lowest
-  // index) of equal minima.  Exact with far fewer evaluations: the maximum over every tenth
+  // index) of equal minima.  Exact with far fewer evaluations: the maximum over every 30th
   // point is a lower bound of each candidate's error, so candidates are evaluated in full in
   // increasing order of that bound until the bound exceeds the best full error found; no
   // candidate left out can reach it.
