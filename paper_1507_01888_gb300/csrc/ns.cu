@@ -362,31 +362,54 @@ __global__ void top_level_kernel(int64_t n, const uint64_t *keys, int *top) {
   top[b] = t;
 }
 
-// Interior boxes of level n: the level-n ancestors of deeper input boxes with an input box at
-// or above level n on their path (others: the largest key, dropped later).
-__global__ void interior_kernel(int64_t n_in, const uint64_t *keys, const int *top, int n, uint64_t *out) {
-  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= n_in) return;
+// Interior boxes of levels n0 .. n0+nlev-1 at once: entry (j, b) is the level-(n0+j) ancestor of
+// input box b when b is deeper and has an input box at or above that level on its path, else
+// the largest key (dropped after the sort: its level field is beyond every level).
+__global__ void interior_all_kernel(int64_t n_in, const uint64_t *keys, const int *top, int n0, int nlev,
+                                    uint64_t *out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_in * nlev) return;
+  const int64_t b = e % n_in;
+  const int n = n0 + (int)(e / n_in);
   const uint64_t k = keys[b];
   const int lv = key_level(k);
-  out[b] = (lv > n && top[b] <= n) ? make_key(n, key_x(k) >> (lv - n), key_y(k) >> (lv - n), key_z(k) >> (lv - n))
+  out[e] = (lv > n && top[b] <= n) ? make_key(n, key_x(k) >> (lv - n), key_y(k) >> (lv - n), key_z(k) >> (lv - n))
                                    : ~0ull;
+}
+// off[l] = first position of level l (0 <= l <= 20) in the sorted keys[0 .. *n)
+__global__ void level_offsets_kernel(const uint64_t *keys, const int64_t *n, int64_t *off) {
+  const int l = threadIdx.x;
+  if (l > 20) return;
+  const uint64_t x = (uint64_t)l << 57;
+  int64_t a = 0, b = *n;
+  while (a < b) {
+    const int64_t m = (a + b) / 2;
+    if (keys[m] < x) a = m + 1;
+    else b = m;
+  }
+  off[l] = a;
 }
 
 // Input boxes of level n in [lo, hi): tops join the level's boxes (appended after `base`
-// passed-down boxes), the others add their coefficients to the passed-down box of the same key.
+// passed-down boxes, at their rank pos[b] - pos0 among the level's tops), the others add their
+// coefficients to the passed-down box of the same key.
 __global__ void tops_kernel(int64_t lo, int64_t hi, int n, const int *top, const uint64_t *keys, const double *coeffs,
-                            int k3, const int *pos, int64_t base, uint64_t *rkeys, double *rv) {
+                            int k3, const int *pos, int pos0, int64_t base, uint64_t *rkeys, double *rv) {
   const int64_t b = lo + blockIdx.x;
   if (b >= hi || top[b] != n) return;
-  const int64_t o = base + pos[b - lo];
+  const int64_t o = base + (pos[b] - pos0);
   if (threadIdx.x == 0) rkeys[o] = keys[b];
   for (int e = threadIdx.x; e < k3; e += blockDim.x) rv[o * k3 + e] = coeffs[b * k3 + e];
 }
-__global__ void top_flags_kernel(int64_t lo, int64_t hi, int n, const int *top, int *flag) {
-  const int64_t b = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= hi) return;
-  flag[b - lo] = top[b] == n ? 1 : 0;
+// flag[b] = 1 for the input boxes that are tops (no input box above them), flag[n] = 0
+__global__ void top_flags_kernel(int64_t n, const uint64_t *keys, const int *top, int *flag) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b > n) return;
+  flag[b] = b < n && top[b] == key_level(keys[b]) ? 1 : 0;
+}
+// the level's interior boxes found among its boxes must be all of them (a consistent tree)
+__global__ void inner_count_check_kernel(const int *ipos, int64_t nr, int64_t ni, int *err) {
+  if (ipos[nr] != ni) atomicExch(err, 2);
 }
 __global__ void add_inputs_kernel(int64_t lo, int64_t hi, int n, const int *top, const uint64_t *keys,
                                   const double *coeffs, int k3, const uint64_t *rkeys, int64_t nr, double *rv,
@@ -415,10 +438,15 @@ __global__ void classify_kernel(int64_t nr, const uint64_t *rkeys, const uint64_
 
 // One CTA per interior box: its eight children get Ubar^{x3} s (two-scale relation).
 __global__ void pass_down_kernel(int k, int64_t nr, const uint64_t *rkeys, const double *rv, const int *inner,
-                                 const int *pos, const double *Ub, uint64_t *ckeys, double *cv) {
+                                 const int *pos, int64_t ninner, const double *Ub, uint64_t *ckeys, double *cv,
+                                 int *err) {
   extern __shared__ double sh[];
   const int64_t p = blockIdx.x;
   if (p >= nr || !inner[p]) return;
+  if (pos[p] >= ninner) {  // more interior boxes than the level has room for: inconsistent tree
+    if (threadIdx.x == 0) atomicExch(err, 2);
+    return;
+  }
   const int kk = 2 * k, k2 = k * k, k3 = k2 * k, kk3 = kk * kk * kk;
   double *d = sh, *a = d + k3, *b = a + kk * k2;
   const int64_t base = 8 * (int64_t)pos[p];
@@ -559,9 +587,14 @@ __global__ void truncate_level_kernel(int k, int n, int64_t nl, const uint64_t *
     for (int q = threadIdx.x; q < k3; q += blockDim.x) pv[(int64_t)slot * k3 + q] = sv[q];
 }
 
-__global__ void keep_flags_kernel(int64_t n, const int *gone, int *keep) {
+__global__ void keep_flags_kernel(int64_t n, const uint64_t *keys, const int *gone, int *keep) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) keep[i] = gone[i] ? 0 : 1;
+  if (i < n) keep[i] = gone[i] || keys[i] == ~0ull ? 0 : 1;  // the largest key pads the level
+}
+// the level's survivor count and merged squared detail into per-level slots
+__global__ void level_totals_kernel(const int *kpos, int64_t nl, const double *dsum, int n, int *cnt, double *d2l) {
+  cnt[n] = kpos[nl];
+  d2l[n] = *dsum;
 }
 
 inline size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -1271,14 +1304,48 @@ extern "C" int mra_reconstruct(const mra_tree_view *in, mra_tree_view *out, void
   MRA_CUDA_TRY(cudaGetLastError());
   RC_ALLOC(d_err, int, 1);
   MRA_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), s));
-  RC_ALLOC(anc, uint64_t, n_in);
-  RC_ALLOC(anc_s, uint64_t, n_in);
+  // Every size of the level loop is known in advance, so the loop runs without a host
+  // synchronisation: the interior boxes of all levels (one sort), the tops of all levels
+  // (one scan), one copy to the host.  A level's boxes are the 8 children of the previous
+  // level's interior boxes and its tops; its interior boxes are exactly the interior keys of
+  // the level (checked on the device), the others are leaves of the result.
+  const int nlev = std::max(nmax - nmin, 1);
+  if (n_in * nlev >= (int64_t)INT32_MAX) return fail(MRA_ERR_ARG, "mra_reconstruct: too many boxes x levels");
+  const int64_t na = n_in * nlev;
+  RC_ALLOC(anc, uint64_t, na);
+  RC_ALLOC(iall, uint64_t, na);
   RC_ALLOC(d_nsel, int64_t, 1);
-  size_t tb = 0, t2 = 0;
-  MRA_CUDA_TRY(cub::DeviceRadixSort::SortKeys(nullptr, tb, anc, anc_s, (int)n_in, 0, 64, s));
-  MRA_CUDA_TRY(cub::DeviceSelect::Unique(nullptr, t2, anc_s, anc, d_nsel, (int)n_in, s));
-  tb = std::max(tb, t2);
-  RC_ALLOC(tmp, unsigned char, tb);
+  RC_ALLOC(d_ioff, int64_t, 21);
+  RC_ALLOC(tflag, int, n_in + 1);
+  RC_ALLOC(tpos, int, n_in + 1);
+  interior_all_kernel<<<counted((unsigned)((na + 255) / 256)), 256, 0, s>>>(n_in, in->keys, top, nmin, nlev, anc);
+  MRA_CUDA_TRY(cudaGetLastError());
+  top_flags_kernel<<<counted((unsigned)((n_in + 256) / 256)), 256, 0, s>>>(n_in, in->keys, top, tflag);
+  MRA_CUDA_TRY(cudaGetLastError());
+  {
+    size_t tb = 0, t2 = 0, t3 = 0;
+    MRA_CUDA_TRY(cub::DeviceRadixSort::SortKeys(nullptr, tb, anc, iall, (int)na, 0, 64, s));
+    MRA_CUDA_TRY(cub::DeviceSelect::Unique(nullptr, t2, iall, anc, d_nsel, (int)na, s));
+    MRA_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, t3, tflag, tpos, (int)(n_in + 1), s));
+    tb = std::max(tb, std::max(t2, t3));
+    RC_ALLOC(tmp, unsigned char, tb);
+    size_t tt = tb;
+    MRA_CUDA_TRY(cub::DeviceRadixSort::SortKeys(tmp, tt, anc, iall, (int)na, 0, 64, s));
+    tt = tb;
+    MRA_CUDA_TRY(cub::DeviceSelect::Unique(tmp, tt, iall, anc, d_nsel, (int)na, s));
+    tt = tb;
+    MRA_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, tt, tflag, tpos, (int)(n_in + 1), s));
+    drop(tmp);
+  }
+  uint64_t *ik_all = anc;  // the unique interior keys, in key order (so level by level)
+  level_offsets_kernel<<<counted(1), 32, 0, s>>>(ik_all, d_nsel, d_ioff);
+  MRA_CUDA_TRY(cudaGetLastError());
+  std::vector<int64_t> ioff(21);
+  std::vector<int> tposh(n_in + 1);
+  MRA_CUDA_TRY(cudaMemcpyAsync(ioff.data(), d_ioff, 21 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  MRA_CUDA_TRY(cudaMemcpyAsync(tposh.data(), tpos, (size_t)(n_in + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  drop(iall);
   const size_t sh_d = (size_t)(k3 + kk * k * k + kk * kk * k) * 8;
   MRA_CUDA_TRY(cudaFuncSetAttribute(pass_down_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_d));
   uint64_t *Ck = nullptr;  // boxes passed down to the current level (unsorted) and their values
@@ -1286,39 +1353,11 @@ extern "C" int mra_reconstruct(const mra_tree_view *in, mra_tree_view *out, void
   int64_t nC = 0, nout = 0;
   const int64_t cap = out->cap;
   for (int n = nmin; n <= nmax; ++n) {
-    // interior boxes of level n
-    interior_kernel<<<counted((unsigned)((n_in + 255) / 256)), 256, 0, s>>>(n_in, in->keys, top, n, anc);
-    MRA_CUDA_TRY(cudaGetLastError());
-    size_t tt = tb;
-    MRA_CUDA_TRY(cub::DeviceRadixSort::SortKeys(tmp, tt, anc, anc_s, (int)n_in, 0, 64, s));
-    RC_ALLOC(ik, uint64_t, n_in);
-    tt = tb;
-    MRA_CUDA_TRY(cub::DeviceSelect::Unique(tmp, tt, anc_s, ik, d_nsel, (int)n_in, s));
-    int64_t ni = 0;
-    MRA_CUDA_TRY(cudaMemcpyAsync(&ni, d_nsel, 8, cudaMemcpyDeviceToHost, s));
-    MRA_CUDA_TRY(cudaStreamSynchronize(s));
-    if (ni > 0) {
-      uint64_t last = 0;
-      MRA_CUDA_TRY(cudaMemcpyAsync(&last, ik + ni - 1, 8, cudaMemcpyDeviceToHost, s));
-      MRA_CUDA_TRY(cudaStreamSynchronize(s));
-      if (last == ~0ull) --ni;
-    }
+    const int64_t ni = ioff[n + 1] - ioff[n];  // interior boxes of level n
+    const uint64_t *ik = ik_all + ioff[n];
     // the level's boxes: passed down, then the tops of this level; in key order
     const int64_t nl = hi[n] - lo[n];
-    RC_ALLOC(tflag, int, nl + 1);
-    RC_ALLOC(tpos, int, nl + 1);
-    int ntop = 0;
-    if (nl > 0) {
-      top_flags_kernel<<<counted((unsigned)((nl + 255) / 256)), 256, 0, s>>>(lo[n], hi[n], n, top, tflag);
-      MRA_CUDA_TRY(cudaGetLastError());
-    }
-    MRA_CUDA_TRY(cudaMemsetAsync(tflag + nl, 0, sizeof(int), s));
-    size_t ts = 0;
-    MRA_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, ts, tflag, tpos, (int)(nl + 1), s));
-    RC_ALLOC(tmp3, unsigned char, ts);
-    MRA_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp3, ts, tflag, tpos, (int)(nl + 1), s));
-    MRA_CUDA_TRY(cudaMemcpyAsync(&ntop, tpos + nl, sizeof(int), cudaMemcpyDeviceToHost, s));
-    MRA_CUDA_TRY(cudaStreamSynchronize(s));
+    const int ntop = tposh[hi[n]] - tposh[lo[n]];
     const int64_t nr = nC + ntop;
     RC_ALLOC(uk, uint64_t, nr);
     RC_ALLOC(uv, double, nr * k3);
@@ -1327,7 +1366,8 @@ extern "C" int mra_reconstruct(const mra_tree_view *in, mra_tree_view *out, void
       MRA_CUDA_TRY(cudaMemcpyAsync(uv, Cv, (size_t)nC * k3 * 8, cudaMemcpyDeviceToDevice, s));
     }
     if (ntop > 0) {
-      tops_kernel<<<counted((unsigned)nl), 128, 0, s>>>(lo[n], hi[n], n, top, in->keys, in->coeffs, k3, tpos, nC, uk, uv);
+      tops_kernel<<<counted((unsigned)nl), 128, 0, s>>>(lo[n], hi[n], n, top, in->keys, in->coeffs, k3, tpos,
+                                                        tposh[lo[n]], nC, uk, uv);
       MRA_CUDA_TRY(cudaGetLastError());
     }
     RC_ALLOC(rk, uint64_t, nr);
@@ -1365,26 +1405,22 @@ extern "C" int mra_reconstruct(const mra_tree_view *in, mra_tree_view *out, void
     RC_ALLOC(tmp5, unsigned char, tsc);
     MRA_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp5, tsc, inner, ipos, (int)(nr + 1), s));
     MRA_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp5, tsc, leaf, lpos, (int)(nr + 1), s));
-    int ninner = 0, herr = 0;
-    MRA_CUDA_TRY(cudaMemcpyAsync(&ninner, ipos + nr, sizeof(int), cudaMemcpyDeviceToHost, s));
-    MRA_CUDA_TRY(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    MRA_CUDA_TRY(cudaStreamSynchronize(s));
-    if (herr) return fail(MRA_ERR_NUMERIC, "mra_reconstruct: an input box has no place in the result");
-    if (nr - ninner > 0) {
+    inner_count_check_kernel<<<counted(1), 1, 0, s>>>(ipos, nr, ni, d_err);
+    MRA_CUDA_TRY(cudaGetLastError());
+    if (nr - ni > 0) {
       emit_leaves_kernel<<<counted((unsigned)nr), 128, 0, s>>>(nr, k3, rk, rv, leaf, lpos, nout, cap, out->keys, out->coeffs);
       MRA_CUDA_TRY(cudaGetLastError());
     }
-    nout += nr - ninner;
-    const int64_t nnext = 8 * (int64_t)ninner;
+    nout += std::max<int64_t>(nr - ni, 0);
+    const int64_t nnext = 8 * ni;
     RC_ALLOC(nk, uint64_t, nnext);
     RC_ALLOC(nv, double, nnext * k3);
-    if (ninner > 0) {
-      pass_down_kernel<<<counted((unsigned)nr), 256, sh_d, s>>>(k, nr, rk, rv, inner, ipos, Ub, nk, nv);
+    if (ni > 0 && nr > 0) {
+      pass_down_kernel<<<counted((unsigned)nr), 256, sh_d, s>>>(k, nr, rk, rv, inner, ipos, ni, Ub, nk, nv, d_err);
       MRA_CUDA_TRY(cudaGetLastError());
     }
-    for (void *p : {(void *)ik, (void *)tflag, (void *)tpos, (void *)tmp3, (void *)uk, (void *)uv, (void *)rk,
-                    (void *)rv, (void *)idx, (void *)idx_s, (void *)inner, (void *)leaf, (void *)ipos, (void *)lpos,
-                    (void *)tmp5})
+    for (void *p : {(void *)uk, (void *)uv, (void *)rk, (void *)rv, (void *)idx, (void *)idx_s, (void *)inner,
+                    (void *)leaf, (void *)ipos, (void *)lpos, (void *)tmp5})
       drop(p);
     if (Ck) drop(Ck);
     if (Cv) drop(Cv);
@@ -1392,7 +1428,11 @@ extern "C" int mra_reconstruct(const mra_tree_view *in, mra_tree_view *out, void
     Cv = nv;
     nC = nnext;
   }
+  int herr = 0;
+  MRA_CUDA_TRY(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  if (herr == 1) return fail(MRA_ERR_NUMERIC, "mra_reconstruct: an input box has no place in the result");
+  if (herr) return fail(MRA_ERR_NUMERIC, "mra_reconstruct: the interior boxes of a level are inconsistent");
   if (nC != 0) return fail(MRA_ERR_NUMERIC, "mra_reconstruct: boxes passed below the deepest level");
   if (nout > cap) {
     out->n = nout;
@@ -1464,14 +1504,20 @@ extern "C" int mra_truncate(const mra_tree_view *in, double thresh, mra_tree_vie
   const size_t sh = (size_t)(k * kk * kk + k * k * kk + k3 + (s_smem ? kk * kk * kk : 0)) * 8;
   MRA_CUDA_TRY(cudaFuncSetAttribute(truncate_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
   TR_ALLOC(pcount, int, 1);
-  // the surviving leaves of each level (device arrays) and the merged parents carried up
+  TR_ALLOC(d_cnt, int, 20);
+  TR_ALLOC(d_d2l, double, 20);
+  MRA_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, 20 * sizeof(int), s));
+  MRA_CUDA_TRY(cudaMemsetAsync(d_d2l, 0, 20 * sizeof(double), s));
+  // The level loop runs without a host synchronisation.  The parents merged from level n+1
+  // are at most a eighth of that level's leaves, so every array is sized by that bound; the
+  // merged parents are written at atomic slots of an array prefilled with the largest key,
+  // which sorts after every real key, is never a leaf of a sibling group and is not kept.
+  // The survivors of each level stay on the device until the counts are read at the end.
   std::vector<uint64_t *> keep_k(20, nullptr);
   std::vector<double *> keep_v(20, nullptr);
-  std::vector<int64_t> keep_n(20, 0);
-  uint64_t *mk = nullptr;  // parents merged from the level below (unsorted)
+  uint64_t *mk = nullptr;  // parents merged from the level below (unsorted, padded)
   double *mv = nullptr;
-  int64_t nm = 0;
-  double e2 = 0.0;
+  int64_t nm = 0;  // bound on their number
   const int top = key_level(hk.back());
   for (int n = top; n >= 0; --n) {
     // this level's leaves: the input's, then the merged parents, in key order
@@ -1505,8 +1551,10 @@ extern "C" int mra_truncate(const mra_tree_view *in, double thresh, mra_tree_vie
     MRA_CUDA_TRY(cudaMemsetAsync(gone, 0, (size_t)(nl + 1) * sizeof(int), s));
     MRA_CUDA_TRY(cudaMemsetAsync(d2, 0, (size_t)nl * 8, s));
     MRA_CUDA_TRY(cudaMemsetAsync(pcount, 0, sizeof(int), s));
-    TR_ALLOC(pk, uint64_t, nl / 8 + 1);
-    TR_ALLOC(pv, double, (nl / 8 + 1) * k3);
+    const int64_t np_max = n > 0 ? nl / 8 : 0;
+    TR_ALLOC(pk, uint64_t, np_max + 1);
+    TR_ALLOC(pv, double, (np_max + 1) * k3);
+    MRA_CUDA_TRY(cudaMemsetAsync(pk, 0xFF, (size_t)(np_max + 1) * 8, s));
     if (n > 0) {
       truncate_level_kernel<<<counted((unsigned)nl), 256, sh, s>>>(k, n, nl, lk, lv, thresh, Ub, gone, d2, pk, pv, pcount,
                                                                    s_smem);
@@ -1515,7 +1563,7 @@ extern "C" int mra_truncate(const mra_tree_view *in, double thresh, mra_tree_vie
     // survivors, compacted in key order
     TR_ALLOC(keep, int, nl + 1);
     TR_ALLOC(kpos, int, nl + 1);
-    keep_flags_kernel<<<counted((unsigned)((nl + 255) / 256)), 256, 0, s>>>(nl, gone, keep);
+    keep_flags_kernel<<<counted((unsigned)((nl + 255) / 256)), 256, 0, s>>>(nl, lk, gone, keep);
     MRA_CUDA_TRY(cudaGetLastError());
     MRA_CUDA_TRY(cudaMemsetAsync(keep + nl, 0, sizeof(int), s));
     size_t tsc = 0;
@@ -1527,26 +1575,25 @@ extern "C" int mra_truncate(const mra_tree_view *in, double thresh, mra_tree_vie
     TR_ALLOC(dsum_d, double, 1);
     MRA_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp2, tsc, keep, kpos, (int)(nl + 1), s));
     MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp2, tsr, d2, dsum_d, (int)nl, s));
-    int nkeep = 0, np = 0;
-    double dsum_h = 0.0;
-    MRA_CUDA_TRY(cudaMemcpyAsync(&nkeep, kpos + nl, sizeof(int), cudaMemcpyDeviceToHost, s));
-    MRA_CUDA_TRY(cudaMemcpyAsync(&np, pcount, sizeof(int), cudaMemcpyDeviceToHost, s));
-    MRA_CUDA_TRY(cudaMemcpyAsync(&dsum_h, dsum_d, sizeof(double), cudaMemcpyDeviceToHost, s));
-    MRA_CUDA_TRY(cudaStreamSynchronize(s));
-    e2 += dsum_h;
-    TR_ALLOC(kk_, uint64_t, nkeep);
-    TR_ALLOC(kv, double, (int64_t)nkeep * k3);
-    if (nkeep > 0) {
-      emit_leaves_kernel<<<counted((unsigned)nl), 128, 0, s>>>(nl, k3, lk, lv, keep, kpos, 0, nkeep, kk_, kv);
-      MRA_CUDA_TRY(cudaGetLastError());
-    }
+    level_totals_kernel<<<counted(1), 1, 0, s>>>(kpos, nl, dsum_d, n, d_cnt, d_d2l);
+    MRA_CUDA_TRY(cudaGetLastError());
+    TR_ALLOC(kk_, uint64_t, nl);
+    TR_ALLOC(kv, double, nl * k3);
+    emit_leaves_kernel<<<counted((unsigned)nl), 128, 0, s>>>(nl, k3, lk, lv, keep, kpos, 0, nl, kk_, kv);
+    MRA_CUDA_TRY(cudaGetLastError());
     keep_k[n] = kk_;
     keep_v[n] = kv;
-    keep_n[n] = nkeep;
     mk = pk;
     mv = pv;
-    nm = np;
+    nm = np_max;
   }
+  std::vector<int> keep_n(20);
+  std::vector<double> d2l(20);
+  MRA_CUDA_TRY(cudaMemcpyAsync(keep_n.data(), d_cnt, 20 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  MRA_CUDA_TRY(cudaMemcpyAsync(d2l.data(), d_d2l, 20 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  double e2 = 0.0;
+  for (int n = top; n >= 0; --n) e2 += d2l[n];
   int64_t nout = 0;
   for (int n = 0; n < 20; ++n) nout += keep_n[n];
   if (nout > out->cap) {
