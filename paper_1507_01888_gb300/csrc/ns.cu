@@ -181,12 +181,15 @@ __global__ void leaf_check_kernel(int64_t n, const uint64_t *keys, int n0, int *
 }
 
 // Ancestor on level n of every leaf deeper than n (others: the largest key, dropped later).
-__global__ void ancestor_kernel(int64_t n_leaf, const uint64_t *keys, int n, uint64_t *anc) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_leaf) return;
+// Entry (j, i): the level-(n0+j) ancestor of leaf i when the leaf is deeper, else the largest key.
+__global__ void ancestor_kernel(int64_t n_leaf, const uint64_t *keys, int n0, int nlev, uint64_t *anc) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_leaf * nlev) return;
+  const int64_t i = e % n_leaf;
+  const int n = n0 + (int)(e / n_leaf);
   const uint64_t k = keys[i];
   const int lv = key_level(k);
-  anc[i] = lv > n ? make_key(n, key_x(k) >> (lv - n), key_y(k) >> (lv - n), key_z(k) >> (lv - n)) : ~0ull;
+  anc[e] = lv > n ? make_key(n, key_x(k) >> (lv - n), key_y(k) >> (lv - n), key_z(k) >> (lv - n)) : ~0ull;
 }
 
 // One CTA per interior node of level n: its children (leaves or interior nodes of level n+1)
@@ -262,14 +265,16 @@ __global__ void halo_kernel(int64_t ni, const uint64_t *ikeys, int D, uint64_t *
 
 // Every node p of R_n: refined when it lies in the sources' halo (every box an unscreened apply
 // of the level would reach); its output rows of the level's two applies, if any.
-__global__ void reach_kernel(int64_t nr, const uint64_t *rkeys, const uint64_t *hkeys, int64_t nh,
+// The halo's count *nh is read on the device (its last key may be the largest key, which no
+// node has).
+__global__ void reach_kernel(int64_t nr, const uint64_t *rkeys, const uint64_t *hkeys, const int64_t *nh,
                              const uint64_t *ykeys, int64_t ny, const uint64_t *zkeys, int64_t nz, int64_t *yi,
                              int64_t *zi, int *refine, int *leaf) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nr) return;
   yi[p] = find_sorted(ykeys, ny, rkeys[p]);
   zi[p] = find_sorted(zkeys, nz, rkeys[p]);
-  const bool in = find_sorted(hkeys, nh, rkeys[p]) >= 0;
+  const bool in = find_sorted(hkeys, *nh, rkeys[p]) >= 0;
   refine[p] = in ? 1 : 0;
   leaf[p] = in ? 0 : 1;
 }
@@ -997,39 +1002,38 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
       for (int j = 0; j < k; ++j) Ubh[(c * k + i) * k + j] = U[c * k * k + i * k + j];
   MRA_CUDA_TRY(cudaMemcpyAsync(Ub, Ubh.data(), Ubh.size() * 8, cudaMemcpyHostToDevice, s));
 
-  // ---- interior nodes of every level: the leaves' ancestors, sorted and unique
+  // ---- interior nodes of every level: the leaves' ancestors, sorted and unique, all levels in
+  // one sort (keys order by level first, so each level is one range)
   std::vector<uint64_t *> Ik(Nmax + 1, nullptr);
   std::vector<int64_t> In(Nmax + 1, 0);
   {
-    NS_ALLOC(anc, uint64_t, n_leaf);
-    NS_ALLOC(anc_s, uint64_t, n_leaf);
+    const int nlev = std::max(Nmax - n0, 1);
+    if (n_leaf * nlev >= (int64_t)INT32_MAX) return fail(MRA_ERR_ARG, "mra_apply_ns_tree: too many leaves x levels");
+    const int64_t na = n_leaf * nlev;
+    NS_ALLOC(anc, uint64_t, na);
+    NS_ALLOC(anc_s, uint64_t, na);
     NS_ALLOC(d_nsel, int64_t, 1);
+    NS_ALLOC(d_off, int64_t, 21);
     size_t t1 = 0, t2 = 0;
-    MRA_CUDA_TRY(cub::DeviceRadixSort::SortKeys(nullptr, t1, anc, anc_s, (int)n_leaf, 0, 64, s));
-    MRA_CUDA_TRY(cub::DeviceSelect::Unique(nullptr, t2, anc_s, anc, d_nsel, (int)n_leaf, s));
-    const size_t tb = std::max(t1, t2);
+    MRA_CUDA_TRY(cub::DeviceRadixSort::SortKeys(nullptr, t1, anc, anc_s, (int)na, 0, 64, s));
+    MRA_CUDA_TRY(cub::DeviceSelect::Unique(nullptr, t2, anc_s, anc, d_nsel, (int)na, s));
+    size_t tb = std::max(t1, t2);
     NS_ALLOC(tmp, unsigned char, tb);
+    ancestor_kernel<<<counted((unsigned)((na + 255) / 256)), 256, 0, s>>>(n_leaf, in->keys, n0, nlev, anc);
+    MRA_CUDA_TRY(cudaGetLastError());
+    size_t tt = tb;
+    MRA_CUDA_TRY(cub::DeviceRadixSort::SortKeys(tmp, tt, anc, anc_s, (int)na, 0, 64, s));
+    tt = tb;
+    MRA_CUDA_TRY(cub::DeviceSelect::Unique(tmp, tt, anc_s, anc, d_nsel, (int)na, s));
+    level_offsets_kernel<<<counted(1), 32, 0, s>>>(anc, d_nsel, d_off);
+    MRA_CUDA_TRY(cudaGetLastError());
+    std::vector<int64_t> off(21);
+    MRA_CUDA_TRY(cudaMemcpyAsync(off.data(), d_off, 21 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    MRA_CUDA_TRY(cudaStreamSynchronize(s));
     for (int n = n0; n < Nmax; ++n) {
-      ancestor_kernel<<<counted((unsigned)((n_leaf + 255) / 256)), 256, 0, s>>>(n_leaf, in->keys, n, anc);
-      MRA_CUDA_TRY(cudaGetLastError());
-      size_t tt = tb;
-      MRA_CUDA_TRY(cub::DeviceRadixSort::SortKeys(tmp, tt, anc, anc_s, (int)n_leaf, 0, 64, s));
-      NS_ALLOC(ik, uint64_t, n_leaf);
-      tt = tb;
-      MRA_CUDA_TRY(cub::DeviceSelect::Unique(tmp, tt, anc_s, ik, d_nsel, (int)n_leaf, s));
-      int64_t nsel = 0;
-      uint64_t last = 0;
-      MRA_CUDA_TRY(cudaMemcpyAsync(&nsel, d_nsel, 8, cudaMemcpyDeviceToHost, s));
-      MRA_CUDA_TRY(cudaStreamSynchronize(s));
-      if (nsel > 0) {
-        MRA_CUDA_TRY(cudaMemcpyAsync(&last, ik + nsel - 1, 8, cudaMemcpyDeviceToHost, s));
-        MRA_CUDA_TRY(cudaStreamSynchronize(s));
-        if (last == ~0ull) --nsel;  // leaves not deeper than n
-      }
-      Ik[n] = ik;
-      In[n] = nsel;
+      Ik[n] = anc + off[n];
+      In[n] = off[n + 1] - off[n];
     }
-    drop(anc);
     drop(anc_s);
     drop(tmp);
   }
@@ -1140,15 +1144,6 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
       MRA_CUDA_TRY(cub::DeviceSelect::Unique(tmph, t2, hal_s, hk, d_nh, (int)nh_all, s));
       drop(tmph);
     }
-    int64_t nh = 0;
-    MRA_CUDA_TRY(cudaMemcpyAsync(&nh, d_nh, 8, cudaMemcpyDeviceToHost, s));
-    MRA_CUDA_TRY(cudaStreamSynchronize(s));
-    if (nh > 0) {
-      uint64_t last = 0;
-      MRA_CUDA_TRY(cudaMemcpyAsync(&last, hk + nh - 1, 8, cudaMemcpyDeviceToHost, s));
-      MRA_CUDA_TRY(cudaStreamSynchronize(s));
-      if (last == ~0ull) --nh;
-    }
     NS_ALLOC(yi, int64_t, nR);
     NS_ALLOC(zi, int64_t, nR);
     NS_ALLOC(refine, int, nR + 1);
@@ -1156,7 +1151,7 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
     NS_ALLOC(ref_pos, int, nR + 1);
     NS_ALLOC(leaf_pos, int, nR + 1);
     if (nR > 0) {
-      reach_kernel<<<counted((unsigned)((nR + 255) / 256)), 256, 0, s>>>(nR, Rk, hk, nh, yk, ny, zk, nz, yi, zi, refine, leaf);
+      reach_kernel<<<counted((unsigned)((nR + 255) / 256)), 256, 0, s>>>(nR, Rk, hk, d_nh, yk, ny, zk, nz, yi, zi, refine, leaf);
       MRA_CUDA_TRY(cudaGetLastError());
     }
     MRA_CUDA_TRY(cudaMemsetAsync(refine + nR, 0, sizeof(int), s));
