@@ -212,7 +212,12 @@ int mra_operator_create(int kernel, double mu, int M, double fit_eps, double r_l
                         int k, double L, int min_level, int max_level, int max_disp,
                         mra_operator **op, void *stream);
 
-/* Copy the fit out of an operator (host arrays of length M; any may be NULL). */
+/* The same call under the name of the block generator it runs (identical arguments, result and
+ * errors): the Gaussian fit and every block R^n_{m,l} of the operator. */
+int mra_operator_blocks(int kernel, double mu, int M, double fit_eps, double r_lo, double r_hi,
+                        int k, double L, int min_level, int max_level, int max_disp,
+                        mra_operator **op, void *stream);
+
 /* The BSH operator refitted in place for a new mu (an iteration whose energy changed): the
  * Gaussian fit is searched again; when it lands on the same grid point (h, s_lo) the exponents
  * t_m, and so every block, are unchanged and only c_m and the c_m-scaled tensor-core pieces are
@@ -222,6 +227,7 @@ int mra_operator_create(int kernel, double mu, int M, double fit_eps, double r_l
  * may be half updated: free it. */
 int mra_operator_refit(mra_operator *op, double mu, int *blocks_reused, void *stream);
 
+/* Copy the fit out of an operator (host arrays of length M; any may be NULL). */
 int mra_operator_fit(const mra_operator *op, double *c, double *t, double *h, double *s_lo,
                      double *max_rel_err);
 

@@ -312,6 +312,12 @@ int mra_operator_create(int kernel, double mu, int M, double fit_eps, double r_l
   return MRA_OK;
 }
 
+int mra_operator_blocks(int kernel, double mu, int M, double fit_eps, double r_lo, double r_hi,
+                        int k, double L, int min_level, int max_level, int max_disp,
+                        mra_operator **out, void *stream) {
+  return mra_operator_create(kernel, mu, M, fit_eps, r_lo, r_hi, k, L, min_level, max_level, max_disp, out, stream);
+}
+
 int mra_operator_refit(mra_operator *h, double mu, int *blocks_reused, void *stream) {
   Operator *op = reinterpret_cast<Operator *>(h);
   if (!op) return fail(MRA_ERR_ARG, "mra_operator_refit: NULL operator");

@@ -43,7 +43,7 @@ EXPORTED = [
     "mra_reconstruct", "mra_truncate", "mra_multiply", "mra_inner", "mra_launch_count",
     "mra_apply_graph_create", "mra_apply_graph_launch", "mra_apply_graph_status", "mra_apply_graph_info",
     "mra_apply_graph_free", "mra_debug_inject_stall", "mra_debug_status", "mra_debug_selftest",
-    "mra_operator_refit",
+    "mra_operator_refit", "mra_operator_blocks",
 ]
 NOALLOC_MAX_BOXES = 1 << 20
 
@@ -137,6 +137,7 @@ def load(build_if_stale: bool = True):
         lib.mra_debug_status.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]
         lib.mra_project.argtypes = [P(GaussSum), i, d, d, i, i, i, P(TreeView), vp]
         lib.mra_operator_create.argtypes = [i, d, i, d, d, d, i, d, i, i, i, P(vp), vp]
+        lib.mra_operator_blocks.argtypes = [i, d, i, d, d, d, i, d, i, i, i, P(vp), vp]
         lib.mra_operator_fit.argtypes = [vp, P(d), P(d), P(d), P(d), P(d)]
         lib.mra_operator_info.argtypes = [vp, P(i), P(i), P(i), P(i), P(i), P(d)]
         lib.mra_operator_block.argtypes = [vp, i, i, i, P(d), P(d)]
@@ -258,14 +259,15 @@ def project(gauss: dict, k: int, L: float, thresh: float = 0.0, init_level: int 
 # --------------------------------------------------------------------------- operator
 
 class Operator:
-    """mra_operator_create: Gaussian fit of 1/r or exp(-mu r)/r plus the 1-D block tables."""
+    """mra_operator_blocks (also exported as mra_operator_create): Gaussian fit of 1/r or
+    exp(-mu r)/r plus the 1-D block tables."""
 
     def __init__(self, kernel: int, M: int, k: int, L: float, min_level: int, max_level: int,
                  max_disp: int = 1, mu: float = 0.0, fit_eps: float = 1e-6, r_lo: float = 1e-4,
                  r_hi: float = -1.0, stream=None):
         lib = load()
         h = ctypes.c_void_p()
-        _check(lib.mra_operator_create(kernel, mu, M, fit_eps, r_lo, r_hi, k, L, min_level, max_level,
+        _check(lib.mra_operator_blocks(kernel, mu, M, fit_eps, r_lo, r_hi, k, L, min_level, max_level,
                                        max_disp, ctypes.byref(h), _stream(stream)))
         self._h = h
         self.kernel, self.M, self.k, self.L = kernel, M, k, L

@@ -70,6 +70,40 @@ def test_truncate_matches_oracle(mra, k, thresh):
     assert abs(e2 - re2) <= 1e-10 * max(re2, 1e-300)
 
 
+def test_truncate_cascades_and_degenerate_thresholds(mra):
+    """Merges that cascade over every level (a threshold above every detail norm: a uniform tree
+    collapses to the level-0 box, an adaptive one as far as its sibling groups are complete),
+    none at all (threshold 0), and a single box: the level loop sizes each level by a bound on
+    the merged parents, so these are its extreme cases."""
+    k, L = 4, 8.0
+    f = W.gaussian_sum(3, 1.0, 30.0, seed=17, centre_box=3.0)
+    uk, uc, _ = O.project(f, k, L, uniform_level=3)
+    ak, ac, _ = O.project(f, k, L, thresh=1e-4, init_level=2, max_level=5)
+    cases = [(uk, uc, 1e30), (ak, ac, 1e30), (ak, ac, 0.0), (uk[:1], uc[:1], 1e30),
+             (np.array([O.make_key(0, 0, 0, 0)], dtype=np.uint64), uc[:1], 1.0)]
+    for keys, coeffs, thresh in cases:
+        out, e2 = mra.truncate(mra.Tree.from_host(keys, coeffs, L), thresh)
+        gk, gc = out.host()
+        rk, rc, re2 = O.truncate(keys, coeffs, k, thresh)
+        assert (gk == rk).all()
+        assert np.abs(gc - rc).max() <= 1e-13 * np.abs(coeffs).max()
+        assert abs(e2 - re2) <= 1e-10 * max(re2, 1e-300)
+    out, _ = mra.truncate(mra.Tree.from_host(uk, uc, L), 1e30)
+    assert out.n == 1 and int(out.host()[0][0]) == int(O.make_key(0, 0, 0, 0))
+
+
+def test_reconstruct_deep_chain(mra):
+    """A level-0 box with one box at level 6 inside it: the sum passes down through every
+    level in between (eight children per interior box, seven of them leaves)."""
+    k, L = 3, 8.0
+    keys = np.array([O.make_key(0, 0, 0, 0), O.make_key(6, 37, 5, 60)], dtype=np.uint64)
+    c = np.random.default_rng(8).standard_normal((2, k, k, k))
+    gk, gc = mra.reconstruct(mra.Tree.from_host(keys, c, L)).host()
+    rk, rc = O.reconstruct(keys, c, k)
+    assert len(rk) == 1 + 7 * 6 and (gk == rk).all()
+    assert np.abs(gc - rc).max() <= 1e-13 * np.abs(rc).max()
+
+
 def test_reconstruct_then_truncate_keeps_the_error_bound(mra):
     """The leaf-level apply's result, summed down and truncated: the function changes by
     exactly sqrt(err2) in L2 (orthogonal projection)."""

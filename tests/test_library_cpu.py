@@ -29,8 +29,8 @@ def lib_path():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for must in ("mra_project", "mra_operator_create", "mra_apply", "mra_norm", "mra_compare",
-                 "mra_operator_fit", "mra_last_error"):
+    for must in ("mra_project", "mra_operator_blocks", "mra_operator_create", "mra_apply", "mra_apply_batched",
+                 "mra_norm", "mra_compare", "mra_operator_fit", "mra_last_error"):
         assert must in names
 
 
@@ -57,6 +57,9 @@ def test_argument_errors_need_no_gpu(lib_path):
     assert b"unknown kernel" in lib.mra_last_error()
     rc = lib.mra_operator_create(0, 0.0, 500, 1e-6, 1e-4, -1.0, 6, 32.0, 0, 3, 1, ctypes.byref(h), None)
     assert rc == mra.MRA_ERR_ARG
+    rc = lib.mra_operator_blocks(1, 0.0, 10, 1e-6, 1e-4, -1.0, 6, 32.0, 0, 3, 1, ctypes.byref(h), None)
+    assert rc == mra.MRA_ERR_ARG  # the same checks under the block generator's name
+    assert b"BSH needs mu > 0" in lib.mra_last_error()
     rc = lib.mra_apply(None, None, None, None, None, 0, None, None)
     assert rc == mra.MRA_ERR_ARG
 
