@@ -231,17 +231,15 @@ __global__ void screen_kernel(ScreenArgs a) {
                 }
               }
             }
-            if (PASS == 0 && owned) {
-              unsigned lb = __ballot_sync(0xffffffffu, dropped_by_model);
-              learned += __popc(lb);
-              lbound += warp_sum(dropped_by_model ? B : 0.0);
+            if (PASS == 0 && owned) {  // per-lane sums, reduced over the warp once per box
+              if (a.mlp) {
+                learned += __popc(__ballot_sync(0xffffffffu, dropped_by_model));
+                if (dropped_by_model) lbound += B;
+              }
+              if (m < a.M && !keep && !dropped_by_model) skipped += B;
             }
             unsigned bal = __ballot_sync(0xffffffffu, keep);
             mask[m0 >> 6] |= (uint64_t)bal << (m0 & 63);
-            if (PASS == 0 && owned) {
-              double sk = (m < a.M && !keep && !dropped_by_model) ? B : 0.0;
-              skipped += warp_sum(sk);
-            }
           }
           int pk = __popcll(mask[0]) + __popcll(mask[1]);
           if (pk == 0) {
@@ -265,6 +263,10 @@ __global__ void screen_kernel(ScreenArgs a) {
           ++count;
         }
     if (a.stencil == MRA_STENCIL_SHELLS && !any) break;
+  }
+  if (PASS == 0) {
+    skipped = warp_sum(skipped);
+    lbound = warp_sum(lbound);
   }
   if (PASS == 0 && lane == 0) {
     a.cnt[b] = count;
