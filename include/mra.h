@@ -157,6 +157,13 @@ typedef struct {
  * the CUB sorts and scans, are not counted).  Take the difference around a region of calls. */
 long long mra_launch_count(void);
 
+/* Device memory the library keeps for reuse: the scratch of the calls that allocate it
+ * themselves (projection, norms and comparisons, reconstruction, truncation, products, the
+ * non-standard applies) comes from a stream-ordered pool per device that holds on to freed
+ * memory between calls.  This returns the pool's unused memory to the driver.  Memory of
+ * allocations still in flight on a stream is not affected. */
+int mra_release_memory(void);
+
 /* Test hook for the failure path: the next MRA_PREC_SPLIT_BF16 apply in this process has its
  * first CTA skip the block copies of its first term, so that the kernel's bounded waits on them
  * run out (about two seconds each); that apply returns MRA_ERR_TIMEOUT with the device context

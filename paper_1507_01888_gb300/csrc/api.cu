@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cub/cub.cuh>
 #include <vector>
 
@@ -133,6 +134,37 @@ std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launch_total() { return g_launches.load(std::memory_order_relaxed); }
 
+constexpr int MAX_POOL_DEVICES = 64;
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[MAX_POOL_DEVICES] = {};
+
+cudaError_t pool_malloc(void **p, size_t bytes, cudaStream_t s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= MAX_POOL_DEVICES) return cudaMallocAsync(p, bytes, s);
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pools[dev]) {
+      cudaMemPoolProps props{};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      e = cudaMemPoolCreate(&g_pools[dev], &props);
+      if (e != cudaSuccess) {
+        g_pools[dev] = nullptr;
+        return e;
+      }
+      uint64_t keep = UINT64_MAX;  // never released at a synchronisation; trimmed on request
+      e = cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+      if (e != cudaSuccess) return e;
+    }
+    pool = g_pools[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
 }  // namespace mra
 
 namespace mra {
@@ -207,6 +239,16 @@ const char *mra_last_error(void) { return g_err; }
 const char *mra_version(void) { return "mra-gb300 0.1 (sm_103a)"; }
 
 long long mra_launch_count(void) { return mra::g_launches.load(std::memory_order_relaxed); }
+
+int mra_release_memory(void) {
+  std::lock_guard<std::mutex> lock(mra::g_pool_mu);
+  for (int d = 0; d < mra::MAX_POOL_DEVICES; ++d) {
+    if (!mra::g_pools[d]) continue;
+    const cudaError_t e = cudaMemPoolTrimTo(mra::g_pools[d], 0);
+    if (e != cudaSuccess) return fail(MRA_ERR_CUDA, "mra_release_memory: %s", cudaGetErrorString(e));
+  }
+  return MRA_OK;
+}
 
 int mra_debug_status(int *line, void *stream) {
   if (!line) return fail(MRA_ERR_ARG, "mra_debug_status: NULL line");
@@ -427,7 +469,7 @@ int mra_project(const mra_gauss_sum *f, int k, double L, double thresh, int init
     hg[4 * ng + g] = f->cz[g];
   }
   double *d_g = nullptr;
-  MRA_CUDA_TRY(cudaMallocAsync((void **)&d_g, hg.size() * 8, s));
+  MRA_CUDA_TRY(pool_malloc((void **)&d_g, hg.size() * 8, s));
   MRA_CUDA_TRY(cudaMemcpyAsync(d_g, hg.data(), hg.size() * 8, cudaMemcpyHostToDevice, s));
   out->k = k;
   out->L = L;
@@ -456,7 +498,7 @@ int mra_project(const mra_gauss_sum *f, int k, double L, double thresh, int init
   std::vector<double> U(2 * k * k);
   two_scale(k, U.data());
   double *d_U = nullptr;
-  MRA_CUDA_TRY(cudaMallocAsync((void **)&d_U, U.size() * 8, s));
+  MRA_CUDA_TRY(pool_malloc((void **)&d_U, U.size() * 8, s));
   MRA_CUDA_TRY(cudaMemcpyAsync(d_U, U.data(), U.size() * 8, cudaMemcpyHostToDevice, s));
   int pl = init_level - 1;
   std::vector<uint64_t> parents;
@@ -468,14 +510,14 @@ int mra_project(const mra_gauss_sum *f, int k, double L, double thresh, int init
   uint64_t *d_keys = nullptr;
   double *d_box = nullptr, *d_dn = nullptr;
   int64_t *d_from = nullptr;
-  MRA_CUDA_TRY(cudaMallocAsync((void **)&d_keys, CH * 9 * 8, s));
-  MRA_CUDA_TRY(cudaMallocAsync((void **)&d_box, (size_t)CH * 9 * k3 * 8, s));
-  MRA_CUDA_TRY(cudaMallocAsync((void **)&d_dn, CH * 8, s));
-  MRA_CUDA_TRY(cudaMallocAsync((void **)&d_from, CH * 8 * 8, s));
+  MRA_CUDA_TRY(pool_malloc((void **)&d_keys, CH * 9 * 8, s));
+  MRA_CUDA_TRY(pool_malloc((void **)&d_box, (size_t)CH * 9 * k3 * 8, s));
+  MRA_CUDA_TRY(pool_malloc((void **)&d_dn, CH * 8, s));
+  MRA_CUDA_TRY(pool_malloc((void **)&d_from, CH * 8 * 8, s));
   // leaves accumulate in a growing device buffer
   int64_t leaf_cap = 1 << 14, n_leaf = 0;
   double *d_leaf = nullptr;
-  MRA_CUDA_TRY(cudaMallocAsync((void **)&d_leaf, (size_t)leaf_cap * k3 * 8, s));
+  MRA_CUDA_TRY(pool_malloc((void **)&d_leaf, (size_t)leaf_cap * k3 * 8, s));
   std::vector<uint64_t> leaf_keys;
   std::vector<double> dn(CH);
   std::vector<uint64_t> ck(CH * 9);
@@ -516,7 +558,7 @@ int mra_project(const mra_gauss_sum *f, int k, double L, double thresh, int init
       if (n_leaf + nf > leaf_cap) {
         int64_t nc = std::max(leaf_cap * 2, n_leaf + nf);
         double *grown = nullptr;
-        MRA_CUDA_TRY(cudaMallocAsync((void **)&grown, (size_t)nc * k3 * 8, s));
+        MRA_CUDA_TRY(pool_malloc((void **)&grown, (size_t)nc * k3 * 8, s));
         MRA_CUDA_TRY(cudaMemcpyAsync(grown, d_leaf, (size_t)n_leaf * k3 * 8, cudaMemcpyDeviceToDevice, s));
         MRA_CUDA_TRY(cudaFreeAsync(d_leaf, s));
         d_leaf = grown;
@@ -542,10 +584,10 @@ int mra_project(const mra_gauss_sum *f, int k, double L, double thresh, int init
     size_t tb = 0;
     cub::DeviceRadixSort::SortPairs(nullptr, tb, (uint64_t *)nullptr, (uint64_t *)nullptr, (int *)nullptr,
                                     (int *)nullptr, (int)n_leaf);
-    MRA_CUDA_TRY(cudaMallocAsync((void **)&d_lk, n_leaf * 8, s));
-    MRA_CUDA_TRY(cudaMallocAsync((void **)&d_pi, n_leaf * 4, s));
-    MRA_CUDA_TRY(cudaMallocAsync((void **)&d_po, n_leaf * 4, s));
-    MRA_CUDA_TRY(cudaMallocAsync(&tmp, tb, s));
+    MRA_CUDA_TRY(pool_malloc((void **)&d_lk, n_leaf * 8, s));
+    MRA_CUDA_TRY(pool_malloc((void **)&d_pi, n_leaf * 4, s));
+    MRA_CUDA_TRY(pool_malloc((void **)&d_po, n_leaf * 4, s));
+    MRA_CUDA_TRY(pool_malloc(&tmp, tb, s));
     MRA_CUDA_TRY(cudaMemcpyAsync(d_lk, leaf_keys.data(), n_leaf * 8, cudaMemcpyHostToDevice, s));
     iota32<<<counted((unsigned)((n_leaf + 255) / 256)), 256, 0, s>>>(n_leaf, d_pi);
     MRA_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, tb, d_lk, out->keys, d_pi, d_po, (int)n_leaf, 0, 64, s));

@@ -1104,7 +1104,7 @@ int norm_run(const mra_tree_view &t, double *per_box, double *total, cudaStream_
   void *tmp = nullptr;
   size_t tmpb = 0;
   MRA_CUDA_TRY(cub::DeviceReduce::Sum(nullptr, tmpb, (double *)nullptr, (double *)nullptr, (int)n));
-  MRA_CUDA_TRY(cudaMallocAsync((void **)&buf, n * 8 * 2 + 8 + tmpb + 512, s));
+  MRA_CUDA_TRY(pool_malloc((void **)&buf, n * 8 * 2 + 8 + tmpb + 512, s));
   sq = buf + n;
   dsum = sq + n;
   tmp = (void *)(((uintptr_t)(dsum + 1) + 255) & ~(uintptr_t)255);
@@ -1127,7 +1127,7 @@ int debug_line_apply(cudaStream_t s) { return debug_take_line(s); }
 
 int debug_selftest_run(cudaStream_t s) {
   int *sink = nullptr;
-  MRA_CUDA_TRY(cudaMallocAsync((void **)&sink, sizeof(int), s));
+  MRA_CUDA_TRY(pool_malloc((void **)&sink, sizeof(int), s));
   debug_selftest_kernel<<<counted(1), 1, 0, s>>>(sink);
   MRA_CUDA_TRY(cudaGetLastError());
   MRA_CUDA_TRY(cudaFreeAsync(sink, s));
@@ -1148,7 +1148,7 @@ int compare_run(const mra_tree_view &t, const mra_tree_view &r, mra_compare_resu
   char *buf = nullptr;
   size_t per = align_up(nmax * 8);
   size_t total = per * 8 + align_up(tmpb) + 256;
-  MRA_CUDA_TRY(cudaMallocAsync((void **)&buf, total, s));
+  MRA_CUDA_TRY(pool_malloc((void **)&buf, total, s));
   double *d2 = (double *)buf, *t2 = (double *)(buf + per), *r2 = (double *)(buf + 2 * per);
   double *rel = (double *)(buf + 3 * per), *ra = (double *)(buf + 4 * per);
   double *ro = (double *)(buf + 5 * per);
@@ -1157,7 +1157,7 @@ int compare_run(const mra_tree_view &t, const mra_tree_view &r, mra_compare_resu
   double *sums = (double *)(buf + 8 * per + align_up(tmpb));  // 8 doubles
   constexpr int NLEV = MRA_MAX_LEVEL + 1;
   double *lev = nullptr;  // per level: test diff^2, ref-only diff^2, ref^2; ref box counts
-  MRA_CUDA_TRY(cudaMallocAsync((void **)&lev, 4 * NLEV * sizeof(double), s));
+  MRA_CUDA_TRY(pool_malloc((void **)&lev, 4 * NLEV * sizeof(double), s));
   MRA_CUDA_TRY(cudaMemsetAsync(lev, 0, 4 * NLEV * sizeof(double), s));
   const int wpb = 8;
   MRA_CUDA_TRY(cudaMemsetAsync(sums, 0, 8 * sizeof(double), s));

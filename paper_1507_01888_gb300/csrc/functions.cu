@@ -112,7 +112,7 @@ struct Pool {
   }
   void *get(size_t bytes) {
     void *p = nullptr;
-    if (cudaMallocAsync(&p, bytes ? bytes : 1, s) != cudaSuccess) return nullptr;
+    if (pool_malloc(&p, bytes ? bytes : 1, s) != cudaSuccess) return nullptr;
     held.push_back(p);
     return p;
   }

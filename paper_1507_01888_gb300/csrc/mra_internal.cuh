@@ -34,6 +34,12 @@ inline G counted(G grid) {
   return grid;
 }
 
+// ---------------------------------------------------------------- device memory
+// Scratch of the host-orchestrated calls comes from a stream-ordered pool of the library's
+// own (one per device) that keeps freed memory for the next call instead of returning it to
+// the driver at every synchronisation, as the default pool does; mra_release_memory trims it.
+cudaError_t pool_malloc(void **p, size_t bytes, cudaStream_t s);
+
 // ---------------------------------------------------------------- index checks
 // The checking build (-DMRA_DEBUG) routes indices of the hot kernels' gathers and scatters
 // through MRA_IDX(i, n): an index outside [0, n) is replaced by 0, so the access stays in

@@ -967,7 +967,7 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
   } release{held, s};
   auto dalloc = [&](size_t bytes) -> void * {
     void *p = nullptr;
-    if (cudaMallocAsync(&p, bytes ? bytes : 1, s) != cudaSuccess) return nullptr;
+    if (pool_malloc(&p, bytes ? bytes : 1, s) != cudaSuccess) return nullptr;
     held.push_back(p);
     return p;
   };
@@ -1257,7 +1257,7 @@ extern "C" int mra_reconstruct(const mra_tree_view *in, mra_tree_view *out, void
   } release{held, s};
   auto dalloc = [&](size_t bytes) -> void * {
     void *p = nullptr;
-    if (cudaMallocAsync(&p, bytes ? bytes : 1, s) != cudaSuccess) return nullptr;
+    if (pool_malloc(&p, bytes ? bytes : 1, s) != cudaSuccess) return nullptr;
     held.push_back(p);
     return p;
   };
@@ -1468,7 +1468,7 @@ extern "C" int mra_truncate(const mra_tree_view *in, double thresh, mra_tree_vie
   } release{held, s};
   auto dalloc = [&](size_t bytes) -> void * {
     void *p = nullptr;
-    if (cudaMallocAsync(&p, bytes ? bytes : 1, s) != cudaSuccess) return nullptr;
+    if (pool_malloc(&p, bytes ? bytes : 1, s) != cudaSuccess) return nullptr;
     held.push_back(p);
     return p;
   };

@@ -43,7 +43,7 @@ EXPORTED = [
     "mra_reconstruct", "mra_truncate", "mra_multiply", "mra_inner", "mra_launch_count",
     "mra_apply_graph_create", "mra_apply_graph_launch", "mra_apply_graph_status", "mra_apply_graph_info",
     "mra_apply_graph_free", "mra_debug_inject_stall", "mra_debug_status", "mra_debug_selftest",
-    "mra_operator_refit", "mra_operator_blocks",
+    "mra_operator_refit", "mra_operator_blocks", "mra_release_memory",
 ]
 NOALLOC_MAX_BOXES = 1 << 20
 
@@ -705,6 +705,11 @@ def debug_selftest(stream=None):
 def debug_inject_stall():
     """mra_debug_inject_stall: the next split-precision apply's waits run out (MRA_ERR_TIMEOUT)."""
     _check(load().mra_debug_inject_stall())
+
+
+def release_memory():
+    """mra_release_memory: return the library's cached device scratch to the driver."""
+    _check(load().mra_release_memory())
 
 
 def launch_count() -> int:

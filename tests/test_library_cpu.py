@@ -62,6 +62,7 @@ def test_argument_errors_need_no_gpu(lib_path):
     assert b"BSH needs mu > 0" in lib.mra_last_error()
     rc = lib.mra_apply(None, None, None, None, None, 0, None, None)
     assert rc == mra.MRA_ERR_ARG
+    assert lib.mra_release_memory() == mra.MRA_OK  # nothing cached yet: no CUDA call
 
 
 # ----------------------------------------------------------------- checkpoint / resume (host only)
