@@ -876,8 +876,6 @@ def main():
     # ---------------- end to end through the public API with host buffers
     keys_pin = torch.from_numpy(keys_h.view(np.int64).copy()).pin_memory()
     coeffs_pin = torch.from_numpy(coeffs_h.copy()).pin_memory()
-    dev_tree = mra.Tree(torch.empty_like(keys_pin, device=dev), torch.empty_like(coeffs_pin, device=dev),
-                        n_in, k, w.L)
     n_out = ap.out.n
     out_keys_pin = torch.empty(n_out, dtype=torch.int64).pin_memory()
     out_coeffs_pin = torch.empty((n_out, k, k, k), dtype=torch.float64).pin_memory()
@@ -887,10 +885,10 @@ def main():
             tree.keys[:n_in].copy_(keys_pin, non_blocking=True)
             tree.coeffs[:n_in].copy_(coeffs_pin, non_blocking=True)
             out = graph.launch(stream)
-        else:
-            dev_tree.keys.copy_(keys_pin, non_blocking=True)
-            dev_tree.coeffs.copy_(coeffs_pin, non_blocking=True)
-            out = run(ap, dev_tree)
+        else:  # one C-ABI call on host buffers: copies in, apply, copies out
+            n_got, _ = mra.apply_host(op, keys_pin, coeffs_pin, opts, out_keys_pin, out_coeffs_pin, stream)
+            assert n_got == n_out
+            return
         out_keys_pin.copy_(out.keys[:n_out], non_blocking=True)
         out_coeffs_pin.copy_(out.coeffs[:n_out], non_blocking=True)
 

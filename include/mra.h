@@ -284,6 +284,18 @@ int mra_apply(const mra_operator *op, const mra_tree_view *in, const mra_apply_o
  * y_mean, y_std; inputs are standardised by (x_mean, x_std), the output is scaled by
  * (y_std, y_mean). */
 
+/* mra_apply on a tree in HOST memory: in->keys and in->coeffs, out->keys and out->coeffs are
+ * host pointers (page-locked memory gives the full copy rate; pageable memory works but the
+ * copies then block the calling thread).  The library copies the tree to the device, runs the
+ * same apply as mra_apply (same kernels, same result bit for bit), copies the result boxes
+ * into out (out->cap boxes at most) and synchronises the stream before returning; its device
+ * scratch comes from the library's memory pool (see mra_release_memory).  When the result has
+ * more than out->cap boxes nothing is copied, out->n receives the count and MRA_ERR_CAPACITY
+ * is returned.  Every host<->device copy of the apply is inside this one call, which is what
+ * an end-to-end measurement times. */
+int mra_apply_host(const mra_operator *op, const mra_tree_view *in, const mra_apply_opts *opts,
+                   mra_tree_view *out, mra_apply_stats *stats, void *stream);
+
 /* Log training data from a plain apply: run the screen of mra_apply with `opts` (its
  * precision is ignored), draw about max_terms of the kept terms with a counter-based
  * hash of (seed, record, term) and write, for each, the features (device float[4]) and

@@ -671,6 +671,53 @@ int mra_apply(const mra_operator *h, const mra_tree_view *in, const mra_apply_op
   return apply_run(*op, *in, *o, *out, workspace, workspace_bytes, stats, (cudaStream_t)stream);
 }
 
+int mra_apply_host(const mra_operator *h, const mra_tree_view *in, const mra_apply_opts *o, mra_tree_view *out,
+                   mra_apply_stats *stats, void *stream) {
+  const Operator *op = reinterpret_cast<const Operator *>(h);
+  int rc = check_opts(op, in, o);
+  if (rc) return rc;
+  rc = check_view(out, "mra_apply_host(out)", false);
+  if (rc) return rc;
+  if (out->k != op->k) return fail(MRA_ERR_ARG, "mra_apply_host: output k=%d, operator k=%d", out->k, op->k);
+  if (out->cap > 0 && (!out->keys || !out->coeffs)) return fail(MRA_ERR_ARG, "mra_apply_host: NULL output buffers");
+  if (in->n >= (1LL << 31)) return fail(MRA_ERR_ARG, "mra_apply_host: more than 2^31 source boxes");
+  out->L = op->L;
+  if (in->n == 0) {
+    out->n = 0;
+    if (stats) *stats = mra_apply_stats{};
+    return MRA_OK;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = in->n, cap = out->cap, k3 = (int64_t)op->k * op->k * op->k;
+  const size_t wb = apply_workspace_bytes(*op, *o, n);
+  void *d_ik = nullptr, *d_ic = nullptr, *d_ok = nullptr, *d_oc = nullptr, *ws = nullptr;
+  cudaError_t e = pool_malloc(&d_ik, (size_t)n * 8, s);
+  if (e == cudaSuccess) e = pool_malloc(&d_ic, (size_t)(n * k3) * 8, s);
+  if (e == cudaSuccess) e = pool_malloc(&d_ok, (size_t)std::max<int64_t>(cap, 1) * 8, s);
+  if (e == cudaSuccess) e = pool_malloc(&d_oc, (size_t)(std::max<int64_t>(cap, 1) * k3) * 8, s);
+  if (e == cudaSuccess) e = pool_malloc(&ws, wb, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_ik, in->keys, (size_t)n * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_ic, in->coeffs, (size_t)(n * k3) * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    mra_tree_view din{n, n, (uint64_t *)d_ik, (double *)d_ic, op->k, op->L};
+    mra_tree_view dout{0, cap, (uint64_t *)d_ok, (double *)d_oc, op->k, op->L};
+    rc = apply_run(*op, din, *o, dout, ws, wb, stats, s);
+    out->n = dout.n;
+    if (rc == MRA_OK && dout.n > 0) {
+      e = cudaMemcpyAsync(out->keys, d_ok, (size_t)dout.n * 8, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out->coeffs, d_oc, (size_t)(dout.n * k3) * 8, cudaMemcpyDeviceToHost, s);
+    }
+  }
+  for (void *p : {d_ik, d_ic, d_ok, d_oc, ws})
+    if (p) cudaFreeAsync(p, s);
+  const cudaError_t es = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(MRA_ERR_CUDA, "mra_apply_host: %s", cudaGetErrorString(e));
+  if (rc != MRA_OK) return rc;
+  if (es != cudaSuccess) return fail(MRA_ERR_CUDA, "mra_apply_host: %s", cudaGetErrorString(es));
+  return MRA_OK;
+}
+
 int mra_apply_batched(const mra_operator *h, int nfunc, const mra_tree_view *in, const int64_t *in_offsets,
                       const mra_apply_opts *o, mra_tree_view *out, int64_t *out_offsets, void *workspace,
                       size_t workspace_bytes, mra_apply_stats *stats, void *stream) {

@@ -43,7 +43,7 @@ EXPORTED = [
     "mra_reconstruct", "mra_truncate", "mra_multiply", "mra_inner", "mra_launch_count",
     "mra_apply_graph_create", "mra_apply_graph_launch", "mra_apply_graph_status", "mra_apply_graph_info",
     "mra_apply_graph_free", "mra_debug_inject_stall", "mra_debug_status", "mra_debug_selftest",
-    "mra_operator_refit", "mra_operator_blocks", "mra_release_memory",
+    "mra_operator_refit", "mra_operator_blocks", "mra_release_memory", "mra_apply_host",
 ]
 NOALLOC_MAX_BOXES = 1 << 20
 
@@ -143,6 +143,7 @@ def load(build_if_stale: bool = True):
         lib.mra_operator_block.argtypes = [vp, i, i, i, P(d), P(d)]
         lib.mra_operator_free.argtypes = [vp]
         lib.mra_apply_workspace_size.argtypes = [vp, P(TreeView), P(ApplyOpts), P(ctypes.c_size_t)]
+        lib.mra_apply_host.argtypes = [vp, P(TreeView), P(ApplyOpts), P(TreeView), P(ApplyStats), vp]
         lib.mra_apply.argtypes = [vp, P(TreeView), P(ApplyOpts), P(TreeView), vp, ctypes.c_size_t,
                                   P(ApplyStats), vp]
         lib.mra_apply_batched.argtypes = [vp, i, P(TreeView), P(ctypes.c_int64), P(ApplyOpts), P(TreeView),
@@ -489,6 +490,23 @@ def apply(op: Operator, tree: Tree, opts: ApplyOpts, stream=None):
     ap = Applier(op, tree, opts)
     out = ap(tree, stream)
     return out, ap.stats.as_dict()
+
+
+def apply_host(op: Operator, keys: torch.Tensor, coeffs: torch.Tensor, opts: ApplyOpts,
+               out_keys: torch.Tensor, out_coeffs: torch.Tensor, stream=None):
+    """mra_apply_host: the apply of a tree held in host memory (CPU tensors, page-locked for the
+    full copy rate: keys int64 [n], coeffs float64 [n, k, k, k]) into host tensors out_keys
+    [cap] and out_coeffs [cap, k, k, k].  Returns (number of result boxes, stats dict)."""
+    for t in (keys, coeffs, out_keys, out_coeffs):
+        if t.device.type != "cpu" or not t.is_contiguous():
+            raise ValueError("apply_host takes contiguous CPU tensors")
+    k = op.k
+    vin = TreeView(keys.shape[0], keys.shape[0], keys.data_ptr(), coeffs.data_ptr(), k, op.L)
+    vout = TreeView(0, out_keys.shape[0], out_keys.data_ptr(), out_coeffs.data_ptr(), k, op.L)
+    st = ApplyStats()
+    _check(load().mra_apply_host(op.handle, ctypes.byref(vin), ctypes.byref(opts), ctypes.byref(vout),
+                                 ctypes.byref(st), _stream(stream)))
+    return vout.n, st.as_dict()
 
 
 def norm(tree: Tree, stream=None):

@@ -186,3 +186,41 @@ def test_zero_function_and_screen_that_keeps_nothing(mra):
                             mra.make_opts(precision=prec, stencil=mra.STENCIL_NEAREST, screen=mra.SCREEN_NORM,
                                           tau=1e300))
         assert out.n == 0 and st["terms_kept"] == 0 and st["terms_screened"] > 0
+
+
+@pytest.mark.parametrize("precision", ["split", "fp64"])
+def test_apply_host_buffers(mra, precision):
+    """mra_apply_host (host buffers in and out, the call the end-to-end benchmark times) gives
+    the device apply's result bit for bit, and the oracle's to the parity bar; a too-small
+    output reports the count without copying."""
+    import torch
+    w = W.bsh_m60_adaptive_k10()
+    f = W.gaussian_sum(3, 1.0, 300.0, seed=21)
+    ok, oc, _ = O.project(f, w.k, w.L, thresh=1e-4, init_level=2, max_level=19)
+    lv = (ok >> np.uint64(57)).astype(int)
+    op = mra.Operator(w.kernel, w.M, w.k, w.L, int(lv.min()), int(lv.max()), max_disp=1, mu=w.mu,
+                      fit_eps=w.fit_eps)
+    prec = mra.PREC_SPLIT_BF16 if precision == "split" else mra.PREC_FP64
+    opts = mra.make_opts(precision=prec, screen=mra.SCREEN_NORM, tau=1e-6, stencil=mra.STENCIL_SHELLS,
+                         max_disp=1)
+    dev_out, dev_st = mra.apply(op, mra.Tree.from_host(ok, oc, w.L), opts)
+    dk, dc = dev_out.host()
+    keys = torch.from_numpy(ok.view(np.int64).copy()).pin_memory()
+    coeffs = torch.from_numpy(oc.copy()).pin_memory()
+    n = len(dk)
+    out_k = torch.empty(n, dtype=torch.int64).pin_memory()
+    out_c = torch.empty((n, w.k, w.k, w.k), dtype=torch.float64).pin_memory()
+    n_got, st = mra.apply_host(op, keys, coeffs, opts, out_k, out_c)
+    assert n_got == n and st["terms_kept"] == dev_st["terms_kept"]
+    assert (out_k.numpy().view(np.uint64) == dk).all() and np.array_equal(out_c.numpy(), dc)
+    fit = oracle_fit(op)  # the oracle on seeded sampled destinations
+    sample = np.sort(np.random.default_rng(4).choice(dk, 12, replace=False))
+    ref = O.apply(ok, oc, fit["c"], fit["t"], w.L, stencil=0, max_disp=1, tau=1e-6, sample_keys=sample)
+    pos = np.searchsorted(dk, ref.keys)
+    assert len(ref.keys) == len(sample) and (dk[pos] == ref.keys).all()
+    assert rel_l2(out_c.numpy()[pos], ref.coeffs) <= (TOL_MIXED if precision == "split" else 1e-12)
+    small_k, small_c = torch.zeros(n - 1, dtype=torch.int64), torch.zeros((n - 1, w.k, w.k, w.k), dtype=torch.float64)
+    with pytest.raises(mra.MraError) as e:
+        mra.apply_host(op, keys, coeffs, opts, small_k, small_c)
+    assert e.value.code == mra.MRA_ERR_CAPACITY
+    assert not small_k.any() and not small_c.any()
