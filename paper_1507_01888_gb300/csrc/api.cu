@@ -172,20 +172,34 @@ namespace mra {
 // fit_err, c, t (host copies).
 static int fit_operator(Operator *op, double mu_fit, int M, double r_lo, double r_hi, cudaStream_t s) {
   // The grid's argmin of the max relative error over the 3000 points, the first (lowest
-  // index) of equal minima.  Exact with far fewer evaluations: the maximum over every 30th
-  // point is a lower bound of each candidate's error, so candidates are evaluated in full in
-  // increasing order of that bound until the bound exceeds the best full error found; no
-  // candidate left out can reach it.
-  const int NC = 116 * 113, SUB = 30, BATCH = 256;
+  // index) of equal minima.  Exact with far fewer evaluations: the maximum over 16 of the
+  // points (the three at each end of the range, where the truncation of the Gaussian sum shows,
+  // and twelve spread over it) is a lower bound of each candidate's error, so candidates are
+  // evaluated in full in increasing order of that bound until the bound exceeds the best full
+  // error found; no candidate left out can reach it.  The batches of full evaluations grow
+  // from 16 (a handful are usually enough), and a full evaluation stops once it exceeds the
+  // best error found before its batch (such a candidate can neither win nor tie).
+  const int NC = 116 * 113, NP = 3000, BATCH = 256;
+  std::vector<int> sub;
+  for (int q = 0; q < 3; ++q) {
+    sub.push_back(q);
+    sub.push_back(NP - 1 - q);
+  }
+  for (int q = 0; q < 12; ++q) sub.push_back((int)lround(q * (NP - 1) / 11.0));
+  std::sort(sub.begin(), sub.end());
+  sub.erase(std::unique(sub.begin(), sub.end()), sub.end());
   double *d_err = nullptr;
   int *d_cand = nullptr;
   if (cudaMalloc((void **)&d_err, NC * sizeof(double)) != cudaSuccess ||
-      cudaMalloc((void **)&d_cand, BATCH * sizeof(int)) != cudaSuccess) {
+      cudaMalloc((void **)&d_cand, (BATCH + 256) * sizeof(int)) != cudaSuccess) {
     cudaFree(d_err);
     return fail(MRA_ERR_CUDA, "fit search: cudaMalloc failed");
   }
+  int *d_pts = d_cand + BATCH;
   std::vector<double> lower(NC), full(NC, -1.0);
-  cudaError_t e = launch_fit_search(mu_fit, M, r_lo, r_hi, SUB, nullptr, NC, d_err, s);
+  cudaError_t e = cudaMemcpyAsync(d_pts, sub.data(), sub.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = launch_fit_search(mu_fit, M, r_lo, r_hi, 1, d_pts, (int)sub.size(), nullptr, NC, INFINITY, d_err, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(lower.data(), d_err, NC * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   std::vector<int> order(NC);
@@ -195,12 +209,14 @@ static int fit_operator(Operator *op, double mu_fit, int M, double r_lo, double 
     const bool na = std::isnan(lower[a]), nb = std::isnan(lower[b]);
     return na != nb ? nb : (!na && lower[a] < lower[b]);
   });
-  int best = -1, pos = 0;
+  int best = -1, pos = 0, batch = 16;
   while (e == cudaSuccess && pos < NC && (best < 0 || !(lower[order[pos]] > full[best]))) {
-    const int nb = std::min(BATCH, NC - pos);
+    const int nb = std::min(batch, NC - pos);
+    batch = std::min(2 * batch, BATCH);
     std::vector<double> part(nb);
     e = cudaMemcpyAsync(d_cand, order.data() + pos, nb * sizeof(int), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = launch_fit_search(mu_fit, M, r_lo, r_hi, 1, d_cand, nb, d_err, s);
+    const double stop = best < 0 ? INFINITY : full[best];
+    if (e == cudaSuccess) e = launch_fit_search(mu_fit, M, r_lo, r_hi, 1, nullptr, 0, d_cand, nb, stop, d_err, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(part.data(), d_err, nb * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     for (int q = 0; q < nb && e == cudaSuccess; ++q) {

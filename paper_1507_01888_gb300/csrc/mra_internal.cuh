@@ -112,8 +112,8 @@ void two_scale(int k, double *U /* [2][k][k] */);  // U^(c)[i][j], Sec. 2.2
 void free_operator(Operator *op);
 
 // ---------------------------------------------------------------- launchers (setup)
-cudaError_t launch_fit_search(double mu, int M, double r_lo, double r_hi, int stride, const int *d_cands,
-                              int n_cands, double *d_err, cudaStream_t s);
+cudaError_t launch_fit_search(double mu, int M, double r_lo, double r_hi, int stride, const int *d_pts, int npts,
+                              const int *d_cands, int n_cands, double stop, double *d_err, cudaStream_t s);
 cudaError_t launch_blocks(const Operator &op, const double *d_glx, const double *d_glw,
                           cudaStream_t s);
 cudaError_t launch_project_boxes(int ng, const double *d_g /*[5][ng]*/, int k, double L,

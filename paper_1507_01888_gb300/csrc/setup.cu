@@ -33,14 +33,18 @@ __device__ __forceinline__ void legendre_phi(int k, double x01, double *out) {
 
 // --------------------------------------------------------------------------- fit search
 // One CTA per candidate (h, s_lo) of the grid h = (5+i)/100, s_lo = (j-100)/4:
-// max over the log-spaced points p = 0, stride, 2 stride, ... < 3000 of
-// |sum_m c_m exp(-t_m r_p^2) - K(r_p)| / K(r_p).  With stride 1 this is the candidate's error;
-// with a larger stride it is a lower bound of it (a maximum over a subset of the same values).
-// `cands` lists the candidates to evaluate (NULL: every candidate, in grid order).
-constexpr int FIT_NS = 113, FIT_NH = 116, FIT_NP = 3000;
+// max over the log-spaced points p = 0, stride, 2 stride, ... < 3000 (or, when `pts` is given,
+// over the npts points pts[0..npts), npts <= blockDim) of
+// |sum_m c_m exp(-t_m r_p^2) - K(r_p)| / K(r_p).  Over all points this is the candidate's
+// error; over a subset it is a lower bound of it (a maximum over some of the same values).
+// `cands` lists the candidates to evaluate (NULL: every candidate, in grid order).  A CTA
+// stops early once its running maximum exceeds `stop` (a full error found already; +inf:
+// never) and then writes that partial maximum, which exceeds `stop` too; errors at or below
+// `stop` are exact.
+constexpr int FIT_NS = 113, FIT_NP = 3000;  // s_lo values per h (116 h values), points
 
-__global__ void fit_search_kernel(double mu, int M, double r_lo, double r_hi, int stride, const int *cands,
-                                  double *err) {
+__global__ void fit_search_kernel(double mu, int M, double r_lo, double r_hi, int stride, const int *pts,
+                                  int npts, const int *cands, double stop, double *err) {
   extern __shared__ double sh[];
   double *c = sh, *t = sh + M;
   __shared__ double red[32];
@@ -55,12 +59,17 @@ __global__ void fit_search_kernel(double mu, int M, double r_lo, double r_hi, in
   }
   __syncthreads();
   double worst = 0.0;
-  for (int p = threadIdx.x * stride; p < FIT_NP; p += blockDim.x * stride) {
-    double r = r_lo * pow(r_hi / r_lo, (double)p / (double)(FIT_NP - 1));
-    double K = exp(-mu * r) / r, sum = 0.0;
-    for (int m = 0; m < M; ++m) sum += c[m] * exp(-t[m] * r * r);
-    double e = fabs(sum - K) / K;
-    worst = e > worst ? e : worst;
+  const int span = pts ? (int)blockDim.x : FIT_NP;
+  for (int p0 = 0; p0 < span; p0 += blockDim.x * stride) {  // block-uniform trip count
+    const int p = pts ? (threadIdx.x < npts ? pts[threadIdx.x] : FIT_NP) : p0 + threadIdx.x * stride;
+    if (p < FIT_NP) {
+      double r = r_lo * pow(r_hi / r_lo, (double)p / (double)(FIT_NP - 1));
+      double K = exp(-mu * r) / r, sum = 0.0;
+      for (int m = 0; m < M; ++m) sum += c[m] * exp(-t[m] * r * r);
+      double e = fabs(sum - K) / K;
+      worst = e > worst ? e : worst;
+    }
+    if (__syncthreads_or(worst > stop)) break;
   }
   for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = worst;
@@ -302,10 +311,11 @@ cudaError_t upload_gl() {
 
 }  // namespace
 
-cudaError_t launch_fit_search(double mu, int M, double r_lo, double r_hi, int stride, const int *d_cands,
-                              int n_cands, double *d_err, cudaStream_t s) {
-  fit_search_kernel<<<counted((unsigned)n_cands), 256, 2 * M * sizeof(double), s>>>(mu, M, r_lo, r_hi, stride,
-                                                                                   d_cands, d_err);
+cudaError_t launch_fit_search(double mu, int M, double r_lo, double r_hi, int stride, const int *d_pts, int npts,
+                              const int *d_cands, int n_cands, double stop, double *d_err, cudaStream_t s) {
+  if (d_pts && (npts < 1 || npts > 256)) return cudaErrorInvalidValue;
+  fit_search_kernel<<<counted((unsigned)n_cands), 256, 2 * M * sizeof(double), s>>>(
+      mu, M, r_lo, r_hi, stride, d_pts, npts, d_cands, stop, d_err);
   return cudaGetLastError();
 }
 
