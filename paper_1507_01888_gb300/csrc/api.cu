@@ -190,10 +190,11 @@ static int fit_operator(Operator *op, double mu_fit, int M, double r_lo, double 
   sub.erase(std::unique(sub.begin(), sub.end()), sub.end());
   double *d_err = nullptr;
   int *d_cand = nullptr;
-  if (cudaMalloc((void **)&d_err, NC * sizeof(double)) != cudaSuccess ||
-      cudaMalloc((void **)&d_cand, (BATCH + 256) * sizeof(int)) != cudaSuccess) {
-    cudaFree(d_err);
-    return fail(MRA_ERR_CUDA, "fit search: cudaMalloc failed");
+  if (pool_malloc((void **)&d_err, NC * sizeof(double), s) != cudaSuccess ||
+      pool_malloc((void **)&d_cand, (BATCH + 256) * sizeof(int), s) != cudaSuccess) {
+    if (d_err) cudaFreeAsync(d_err, s);
+    cudaStreamSynchronize(s);
+    return fail(MRA_ERR_CUDA, "fit search: out of device memory");
   }
   int *d_pts = d_cand + BATCH;
   std::vector<double> lower(NC), full(NC, -1.0);
@@ -226,8 +227,10 @@ static int fit_operator(Operator *op, double mu_fit, int M, double r_lo, double 
     }
     pos += nb;
   }
-  cudaFree(d_err);
-  cudaFree(d_cand);
+  cudaFreeAsync(d_err, s);
+  cudaFreeAsync(d_cand, s);
+  const cudaError_t ef = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = ef;
   if (e != cudaSuccess) return fail(MRA_ERR_CUDA, "fit search: %s", cudaGetErrorString(e));
   op->h_fit = (5.0 + best / 113) / 100.0;
   op->s_lo = (best % 113 - 100.0) / 4.0;
