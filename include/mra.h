@@ -46,7 +46,7 @@ extern "C" {
 #define MRA_ERR_CUDA (-3)     /* a CUDA runtime call or kernel launch failed */
 #define MRA_ERR_TIMEOUT (-4)  /* a bounded device-side wait gave up */
 #define MRA_ERR_NUMERIC (-5)  /* a non-finite value was produced */
-#define MRA_ERR_UNSUPPORTED (-6)
+#define MRA_ERR_UNSUPPORTED (-6) /* valid, but outside what this path supports (e.g. a split order above 16) */
 
 /* ---- enumerations --------------------------------------------------------- */
 #define MRA_POISSON 0 /* K(r) = 1/r                          (Sec. 2.3) */
