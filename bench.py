@@ -828,8 +828,15 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     graph = None
-    if batched:  # the whole batched apply recorded once as a CUDA graph, one launch per step
-        graph = mra.ApplyGraph(op, tree, opts, offsets=offsets, stream=stream)
+    if batched or (prec == mra.PREC_SPLIT_BF16 and not learned_cfg):
+        # the whole apply recorded once as a CUDA graph, one launch per step (no host
+        # synchronisation between its kernels); the plain apply above gave the same result
+        graph = mra.ApplyGraph(op, tree, opts, offsets=offsets if batched else None, stream=stream)
+        if not batched:  # a replay is the plain apply, bit for bit
+            g_out = graph.launch(stream)
+            graph.status(stream)
+            assert g_out.n == ap.out.n and torch.equal(g_out.keys[:g_out.n], ap.out.keys[:ap.out.n]) and \
+                torch.equal(g_out.coeffs[:g_out.n], ap.out.coeffs[:ap.out.n]), "graph replay differs from the apply"
 
     def step():
         if graph is not None:
@@ -881,7 +888,7 @@ def main():
     out_coeffs_pin = torch.empty((n_out, k, k, k), dtype=torch.float64).pin_memory()
 
     def e2e_step():
-        if graph is not None:  # the graph reads the tree's own buffers
+        if batched:  # the graph reads the tree's own buffers
             tree.keys[:n_in].copy_(keys_pin, non_blocking=True)
             tree.coeffs[:n_in].copy_(coeffs_pin, non_blocking=True)
             out = graph.launch(stream)
