@@ -1504,7 +1504,7 @@ extern "C" int mra_truncate(const mra_tree_view *in, double thresh, mra_tree_vie
   MRA_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, 20 * sizeof(int), s));
   MRA_CUDA_TRY(cudaMemsetAsync(d_d2l, 0, 20 * sizeof(double), s));
   // The level loop runs without a host synchronisation.  The parents merged from level n+1
-  // are at most a eighth of that level's leaves, so every array is sized by that bound; the
+  // are at most an eighth of that level's leaves, so every array is sized by that bound; the
   // merged parents are written at atomic slots of an array prefilled with the largest key,
   // which sorts after every real key, is never a leaf of a sibling group and is not kept.
   // The survivors of each level stay on the device until the counts are read at the end.
