@@ -141,3 +141,55 @@ def test_partition_ranges_and_halo_by_brute_force():
                             t = (int(n[i]) << 57) | (int(a) << 38) | (int(b) << 19) | int(c)
                             want |= lo <= t < hi
             assert bool(halo[i]) == want
+
+
+def _lost_rank(rank, world, port, q):
+    import datetime
+    import time
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1507_01888_gb300 import partition as PT
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    keys, coeffs = W.random_tree_coeffs(100, 2, 3, seed=7)
+    lo, hi = PT.split_ranges(keys, world)[rank]
+    own = PT.in_range(keys, lo, hi)
+    if rank == world - 1:  # this rank leaves between steps, before the exchange, without a word
+        q.put((rank, "left", 0.0))
+        q.close()
+        q.join_thread()  # the message is sent before the process ends
+        os._exit(0)
+    t0 = time.monotonic()
+    try:
+        PT.exchange(torch.from_numpy(keys[own].view(np.int64).copy()), torch.from_numpy(coeffs[own].copy()))
+        q.put((rank, "completed", time.monotonic() - t0))
+    except Exception as e:  # the survivors learn of it on the host: the collective fails
+        q.put((rank, type(e).__name__, time.monotonic() - t0))
+    q.close()
+    q.join_thread()
+    os._exit(0)  # no orderly shutdown of a process group that lost a member
+
+
+def test_exchange_fails_loudly_when_a_rank_is_lost():
+    """Failure detection on the host: one of three gloo ranks exits before the halo exchange.
+    The others do not hang: their all-gather raises within the process group's timeout."""
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    world = 3
+    procs = [ctx.Process(target=_lost_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = {}
+    for _ in range(world):
+        r = q.get(timeout=120)
+        res[r[0]] = r
+    for p in procs:
+        p.join(timeout=60)
+    assert res[world - 1][1] == "left"
+    for r in range(world - 1):
+        assert res[r][1] != "completed", res[r]
+        assert res[r][2] < 60.0
