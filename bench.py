@@ -39,7 +39,32 @@ import workloads as W  # noqa: E402
 SPLIT_TRAFFIC = {("bsh_m60_adaptive_k10", 2): 70.93e6 + 77.63e6}
 
 METRIC = "3D operator-apply boxes/s & % roofline, mixed vs FP64 GPU at 1e-6 rel L2"
-FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no FP64 figure in the measured peaks)
+def split_dtype(pieces):
+    """What the split-precision apply computes in (the label of its JSON line)."""
+    return (f"bf16x{pieces}-split MMAs with f32 accumulation; Gaussian-term sums in compensated f32 "
+            f"(sum + Kahan correction); f64 per-destination sums")
+
+
+_FP64 = {}
+
+
+def fp64_peak(dev_index=0):
+    """FP64 rate of this GPU, measured by the library's probe (mra_measure_fp64_peak: a DFMA loop
+    and an FP64 MMA loop over the whole device, ~2 s, before any timed region), with the clocks
+    sampled while it ran.  The FP64 apply kernel issues DFMA, so its roofline peak is the DFMA rate."""
+    if "v" not in _FP64:
+        from paper_1507_01888_gb300 import mra
+        clk = clocks_start(None)
+        dfma, dmma = mra.measure_fp64_peak(2.0)
+        clocks = clocks_stop(clk, dev_index)
+        _FP64["v"] = {"dfma_tflops": dfma, "dmma_tflops": dmma, "clocks": clocks}
+    return _FP64["v"]
+
+
+def fp64_peak_source(dev_index=0):
+    f = fp64_peak(dev_index)
+    return (f"measured DFMA loop (mra_measure_fp64_peak; DMMA {f['dmma_tflops']:.3f} TFLOP/s), "
+            f"SM clock median {f['clocks'].get('sm_mhz')} MHz, reasons {f['clocks'].get('reasons')}")
 
 
 def parse():
@@ -78,6 +103,22 @@ def peaks():
             return json.load(f), "measured"
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+L2_NOTE = "a 256 MB buffer is written before every timed step (device memory on the GPU arm, host memory on the oracle arm)"
+
+
+def workload_config(w):
+    """The workload's identifying parameters, printed as `config` by every arm (run results go to `run`)."""
+    return {"workload": w.name, "k": w.k, "M": w.M, "kernel": "bsh" if w.kernel == W.BSH else "poisson",
+            "mu": w.mu, "thresh": w.thresh, "tau": w.tau, "functions": len(w.funcs),
+            "tree": "adaptive" if w.uniform_level < 0 else f"uniform level {w.uniform_level}",
+            "stencil": "shells<=%d" % w.max_disp if w.stencil == 0 else "27-point", "l2": L2_NOTE}
+
+
+def host_flush(buf):
+    """Write a 256 MB host buffer (the oracle arm's counterpart of the GPU arm's L2 flush)."""
+    buf.fill(np.random.default_rng().integers(1, 1 << 30))
 
 
 def oracle_fit(w):
@@ -186,40 +227,66 @@ def clocks_stop(handle, gpu_index):
 
 
 def run_reference(args, rank, world):
+    """The oracle as it stands on this machine's cores.  Every step is one whole oracle job when
+    a job takes at most about 15 s (the headline workload: ~4.4 s on 16 cores), else a seeded
+    sample of destination boxes with the job time extrapolated by kept terms (said in `sample`)."""
     if rank != 0:
         return
     w = W.WORKLOADS[args.workload]()
+    buf = np.empty(256 * 1024 * 1024 // 8)
     if "post" in w.extra or "solver" in w.extra:  # whole steps of the oracle, no sampling
-        runs = [oracle_post_step(w) if "post" in w.extra else oracle_solver_step(w)
-                for _ in range(args.warmup + args.steps)][args.warmup:]
+        runs = []
+        for i in range(args.warmup + args.steps):
+            host_flush(buf)
+            runs.append(oracle_post_step(w) if "post" in w.extra else oracle_solver_step(w))
+        runs = runs[args.warmup:]
         value = statistics.mean(r["value"] for r in runs)
         line = {"metric": METRIC, "value": value, "unit": "boxes/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-                "config": {"workload": w.name, "k": w.k},
+                "config": workload_config(w), "run": {"parallelism": f"{os.cpu_count()} host cores"},
                 "cpu_baseline": dict(runs[-1], value=value),
                 "e2e": {"value": value, "unit": "boxes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
-    times = []
-    info = None
-    prepared = cpu_prepare(w)  # projection and fit once; every step is a sampled apply
+    import oracle as O
+    prepared = cpu_prepare(w)  # the oracle's projection and fit, once
+    keys, coeffs, c, t, t_setup = prepared
+    probe = cpu_baseline(w, 2.0, seed=999, prepared=prepared)
+    t_est = probe["t_sample"] * probe["terms_total"] / max(probe["sample_terms"], 1) + t_setup
+    whole = t_est <= 15.0
+    kw = dict(stencil=w.stencil, max_disp=w.max_disp, tau=w.tau)
+    times, info = [], None
     for i in range(args.warmup + args.steps):
-        info = cpu_baseline(w, args.cpu_seconds / max(args.steps + args.warmup, 1) * 2, seed=1000 + i,
-                            prepared=prepared)
+        host_flush(buf)
+        if whole:
+            t0 = time.perf_counter()
+            r = O.apply(keys, coeffs, c, t, w.L, **kw)
+            dt = time.perf_counter() - t0
+            info = {"terms": r.terms, "dest": len(r.keys)}
+        else:
+            cb = cpu_baseline(w, args.cpu_seconds / max(args.steps + args.warmup, 1) * 2, seed=1000 + i,
+                              prepared=prepared)
+            dt = cb["t_sample"] * cb["terms_total"] / max(cb["sample_terms"], 1)
+            info = cb
         if i >= args.warmup:
-            times.append(info)
-    per = [x["t_sample"] * x["terms_total"] / max(x["sample_terms"], 1) for x in times]
-    t_job = statistics.mean(per)
-    value = info["n_in"] / t_job
+            times.append(dt)
+    t_job = statistics.mean(times)
+    value = len(keys) / t_job
+    cores = os.cpu_count() or 1
+    if whole:
+        sample = (f"the whole job every step: {len(keys)} source boxes, {info['terms']} kept terms, "
+                  f"{info['dest']} destination boxes (the oracle's own block generation and screen included, "
+                  f"{t_setup:.2f} s of each step)")
+    else:
+        sample = (f"{info['sample_dest']} seeded destination boxes per step ({info['sample_terms']} of "
+                  f"{info['terms_total']} kept terms); job time extrapolated by kept terms")
     line = {"metric": METRIC, "value": value, "unit": "boxes/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_job * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": w.name, "n_boxes": info["n_in"], "k": w.k, "M": w.M},
-            "cpu_baseline": {"value": value, "unit": "boxes/s", "cores": info["cores"], "kind": "oracle",
-                             "sample": f"{info['sample_dest']} seeded destination boxes per step "
-                                       f"({info['sample_terms']} of {info['terms_total']} kept terms); job "
-                                       "time extrapolated by kept terms"},
+            "config": workload_config(w),
+            "run": {"n_boxes": len(keys), "parallelism": f"{cores} host cores (OpenMP over destinations)"},
+            "cpu_baseline": {"value": value, "unit": "boxes/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "boxes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -345,9 +412,10 @@ def run_ns(args, w, rank, world):
     achieved = flops / (kms_mean / 1e3) / 1e12
     pk, pk_kind = peaks()
     if prec == mra.PREC_FP64:
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "apply_f64_kernel (all levels)",
-                "peak_source": "nominal GB300 FP64", "kernel_ms": kms_mean,
+        p64 = fp64_peak()["dfma_tflops"]
+        roof = {"bound": "alu", "achieved": achieved, "peak": p64, "unit": "TFLOP/s",
+                "frac": achieved / p64, "traffic": None, "kernel": "apply_f64_kernel (all levels)",
+                "peak_source": fp64_peak_source(), "kernel_ms": kms_mean,
                 "flops": "algorithmic (6k'^4+k'^3 per term, k' = k or 2k)"}
         dtype = "f64"
     else:
@@ -355,11 +423,11 @@ def run_ns(args, w, rank, world):
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None, "kernel": "apply_split_kernel (all levels)", "peak_source": f"bf16 dense burst, {pk_kind}",
                 "kernel_ms": kms_mean, "flops": "algorithmic (6k'^4+k'^3 per term, k' = k or 2k)"}
-        dtype = f"bf16x{args.pieces}-split, f32 accumulate, f64 term sum"
+        dtype = split_dtype(args.pieces)
     line = {"metric": METRIC, "value": value, "unit": "boxes/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-            "config": {"workload": w.name, "n_boxes": n_all, "result_leaves": ap.out.n, "k": k, "M": w.M,
+            "config": workload_config(w), "run": {"n_boxes": n_all, "result_leaves": ap.out.n, "k": k, "M": w.M,
                        "form": "non-standard" + (", adaptive tree" if adaptive else ", uniform tree"),
                        "levels": f"{n0}..{N}", "max_disp_per_level": D, "terms": sum(t for _, _, t in terms),
                        "terms_reported": ap.stats.terms_kept,
@@ -457,7 +525,7 @@ def run_post(args, w, rank, world):
     line = {"metric": METRIC, "value": n_all / (ms / 1e3), "unit": "boxes/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "n_boxes": n_all, "k": w.k, "input": "leaf-level FP64 apply result of "
+            "config": workload_config(w), "run": {"n_boxes": n_all, "k": w.k, "input": "leaf-level FP64 apply result of "
                        "the BSH M=60 k=10 workload (boxes on several levels)", "result_leaves": n_leaves,
                        "truncated_leaves": n_tr, "truncate_thresh": th, "l2_change": res["e2"] ** 0.5,
                        "l2": "flushed by a 256 MB write before every step",
@@ -543,13 +611,14 @@ def run_partitioned(args, w, rank, world, local):
     pk, pk_kind = peaks()
     k = w.k
     achieved = terms.item() * (6 * k ** 4 + k ** 3) / (kmax.item() / 1e3) / 1e12
-    peak = pk.get("bf16_tflops", 1856.3) * world if prec == mra.PREC_SPLIT_BF16 else FP64_PEAK_TFLOPS * world
+    peak = pk.get("bf16_tflops", 1856.3) * world if prec == mra.PREC_SPLIT_BF16 else \
+        fp64_peak(local)["dfma_tflops"] * world
     line = {"metric": METRIC, "value": tree.n / (ms / 1e3), "unit": "boxes/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None,
-            "dtype": "f64" if prec == mra.PREC_FP64 else f"bf16x{args.pieces}-split, f32 accumulate, f64 term sum",
+            "dtype": "f64" if prec == mra.PREC_FP64 else split_dtype(args.pieces),
             "data": "synthetic",
-            "config": {"workload": w.name, "n_boxes": tree.n, "k": k, "M": w.M,
+            "config": workload_config(w), "run": {"n_boxes": tree.n, "k": k, "M": w.M,
                        "parallelism": f"{world} ranks, destination key ranges (owner computes), "
                                       f"{args.dist_backend} all-gather of the input parts every step",
                        "l2": "inputs gathered anew every step"},
@@ -616,7 +685,7 @@ def run_solver(args, w, rank, world):
     kms = st["kernel_ms"]
     achieved = st["algo_flops"] / (kms / 1e3) / 1e12
     pk, pk_kind = peaks()
-    peak = pk.get("bf16_tflops_sustained", 1688.5) if prec != mra.PREC_FP64 else FP64_PEAK_TFLOPS
+    peak = pk.get("bf16_tflops_sustained", 1688.5) if prec != mra.PREC_FP64 else fp64_peak()["dfma_tflops"]
     # end to end: psi from the host, the new psi back to the host
     pk_h, pc_h = psi.host()
     keys_pin = torch.from_numpy(pk_h.view(np.int64).copy()).pin_memory()
@@ -644,7 +713,7 @@ def run_solver(args, w, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == mra.PREC_FP64 else "bf16x3-split apply, f64 elsewhere", "data": "synthetic",
-            "config": {"workload": w.name, "n_boxes": n_all, "k": w.k, "L": w.L, "thresh": w.thresh,
+            "config": workload_config(w), "run": {"n_boxes": n_all, "k": w.k, "L": w.L, "thresh": w.thresh,
                        "Z": cfg["Z"], "psi_leaves": info["n_psi"], "apply_result_leaves": info["n_result"],
                        "bsh_terms": w.M, "potential_terms": cfg["M_potential"], "potential_fit_err": vfit,
                        "iterations_to_converge": len(hist), "solve_s": t_solve, "energy": E,
@@ -655,7 +724,7 @@ def run_solver(args, w, rank, world):
             "roofline": {"bound": "alu" if prec == mra.PREC_FP64 else "tensor", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                          "kernel": "apply kernels of the non-standard apply (all levels)",
-                         "peak_source": ("nominal GB300 FP64" if prec == mra.PREC_FP64 else
+                         "peak_source": (fp64_peak_source() if prec == mra.PREC_FP64 else
                                          f"bf16 dense sustained, {pk_kind}"), "kernel_ms": kms,
                          "flops": "algorithmic (6k'^4+k'^3 per kept term, k' = k or 2k)",
                          "share_of_step": kms / ms},
@@ -923,9 +992,10 @@ def main():
     terms = st0["terms_kept"]
     achieved_tflops = terms * flops_per_term / (kms / 1e3) / 1e12
     if prec == mra.PREC_FP64:
-        roof = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
-                "kernel": "apply_f64_kernel", "peak_source": "nominal GB300 FP64 rate (recipe table)",
+        p64 = fp64_peak(local)["dfma_tflops"]
+        roof = {"bound": "alu", "achieved": achieved_tflops, "peak": p64, "unit": "TFLOP/s",
+                "frac": achieved_tflops / p64, "traffic": None,
+                "kernel": "apply_f64_kernel", "peak_source": fp64_peak_source(local),
                 "kernel_ms": kms}
         dtype = "f64"
     else:
@@ -943,12 +1013,12 @@ def main():
             roof["issued"] = {"tflops": issued, "frac": issued / peak,
                               "note": "BF16 flops the MMAs issue (padding to 128x16x16 tiles and the six "
                                       "piece products included); context only, not the algorithmic rate"}
-        dtype = f"bf16x{args.pieces}-split, f32 accumulate, f64 term sum"
+        dtype = split_dtype(args.pieces)
 
     line = {"metric": METRIC, "value": value, "unit": "boxes/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-            "config": {"workload": w.name, "n_boxes": n_all, "k": k, "M": w.M,
+            "config": workload_config(w), "run": {"n_boxes": n_all, "k": k, "M": w.M,
                        "kernel": "bsh" if w.kernel == W.BSH else "poisson", "mu": w.mu, "tau": w.tau,
                        "stencil": "shells<=%d" % w.max_disp if w.stencil == 0 else "27-point",
                        "terms_kept": terms, "pairs": st0["pairs"], "n_out": st0["n_out"],

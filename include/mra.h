@@ -54,8 +54,14 @@ extern "C" {
                          without its 1/(4 pi), which the caller applies) */
 
 #define MRA_PREC_FP64 0       /* all arithmetic in FP64 */
-#define MRA_PREC_SPLIT_BF16 1 /* mode products as split-BF16 tcgen05 MMAs with FP32
-                                 accumulation; Gaussian-term and box sums in FP64 */
+#define MRA_PREC_SPLIT_BF16 1 /* mode products as split-BF16 tcgen05 MMAs: every operand is
+                                 split into `pieces` BF16 pieces and the piece products p + q <
+                                 pieces are accumulated in FP32 in tensor memory.  Gaussian-term
+                                 sums are compensated FP32 sums (a sum and its Kahan correction);
+                                 the per-destination sum is FP64.  Operator blocks, fit, norms and
+                                 screen stay FP64.  Measured error: about 1e-7 relative L2 against
+                                 MRA_PREC_FP64 with 3 pieces; use MRA_PREC_FP64 for thresholds
+                                 below that */
 
 #define MRA_SCREEN_NONE 0 /* keep every term */
 #define MRA_SCREEN_NORM 1 /* keep a term iff |c| ||Rx|| ||Ry|| ||Rz|| ||s|| >= tau */
@@ -179,6 +185,15 @@ int mra_debug_inject_stall(void);
  * path itself; a no-op in the release build). */
 int mra_debug_status(int *line, void *stream);
 int mra_debug_selftest(void *stream);
+
+/* FP64 throughput of the current device, measured (the paper has no counterpart; this is the
+ * denominator of the FP64 apply's roofline).  Two probes over the whole device (eight CTAs of
+ * 256 threads per SM), each timed with CUDA events as the best of three launches of about
+ * seconds/8 each after a calibration launch: *dfma_tflops, independent DFMA chains (the
+ * instructions apply_f64 uses); *dmma_tflops, mma.sync m16n8k16 FP64 warp MMAs.  Either
+ * pointer may be NULL.  Takes about `seconds` (0 < seconds <= 60) of GPU time on `stream` and
+ * synchronises it; allocates nothing. */
+int mra_measure_fp64_peak(double seconds, double *dfma_tflops, double *dmma_tflops, void *stream);
 
 /* Thread-local description of the last error (never NULL). */
 const char *mra_last_error(void);
@@ -427,6 +442,12 @@ int mra_multiply(const mra_tree_view *a, const mra_tree_view *b, mra_tree_view *
  * common leaves (orthonormal basis); deterministic reduction, *result on the host. */
 int mra_inner(const mra_tree_view *a, const mra_tree_view *b, double *result, void *stream);
 
+/* Multiply a function by a constant in place: every coefficient of tree->n boxes times alpha
+ * (the basis is linear, so the coefficients of alpha f are alpha times those of f, Sec. 2.1).
+ * The bound-state Helmholtz iteration of Sec. 3.2 uses it for the Green's function factor
+ * -2 * 1/(4 pi) and for normalising psi.  Stream-ordered, no synchronisation; alpha finite. */
+int mra_scale(mra_tree_view *tree, double alpha, void *stream);
+
 /* ---- graph-captured apply --------------------------------------------------------------
  * An apply (nfunc == 1: as mra_apply; nfunc > 1: as mra_apply_batched, in_offsets and
  * out_offsets as there) recorded once as a CUDA graph and replayed with one launch.  Create
@@ -450,8 +471,14 @@ int mra_apply_graph_status(mra_apply_graph *graph, void *stream);
 int mra_apply_graph_info(const mra_apply_graph *graph, int64_t *n_out, long long *kernels_per_launch);
 int mra_apply_graph_free(mra_apply_graph *graph);
 
-/* Per-box Frobenius norms (device array of tree->n doubles, may be NULL) and
- * the total L2 norm (host double, may be NULL).  Deterministic reduction. */
+/* Norm of a function on a tree (the L2 norm the worked example of Sec. 3.1 prints, next to
+ * eq. gaussian, for the projected Gaussian).  The scaling functions are orthonormal (Sec. 2.1,
+ * eq. scalingfunc), so the L2 norm of f restricted to a box is the Frobenius norm of the box's
+ * coefficient tensor and ||f||_2^2 is the sum of their squares over disjoint boxes.  Writes the
+ * per-box norms (device array of tree->n doubles, may be NULL) and the total
+ * sqrt(sum_b ||s_b||_F^2) (host double, may be NULL); with boxes that overlap (a box and boxes
+ * below it, as mra_apply returns them) the total is the coefficient norm, not ||f||_2.
+ * Deterministic reduction; synchronises `stream`. */
 int mra_norm(const mra_tree_view *tree, double *per_box, double *total, void *stream);
 
 /* mra_norm without any device allocation.  The paper has no counterpart: this
@@ -463,19 +490,25 @@ int mra_norm(const mra_tree_view *tree, double *per_box, double *total, void *st
  * Same results as mra_norm (per-box norms into the caller's device array
  * per_box, may be NULL; total into the host double, may be NULL).
  * Scratch is one fixed array of MRA_NOALLOC_MAX_BOXES + 32 doubles (8 MiB) in
- * the library's device memory, present on every GPU that loads the library
- * until the process exits; trees with more boxes are rejected with
- * MRA_ERR_CAPACITY before any GPU work.  The first call on each device looks up
- * the array's device address (with that device current); make that first call
- * before any stream capture.  All calls share the array and nothing carries
+ * the library's device memory.  It is resident on a device from the first call
+ * there (the library's device code, and the array with it, is loaded into a
+ * context on first use) until the process exits; trees with more boxes are
+ * rejected with MRA_ERR_CAPACITY before any GPU work.  Every call looks up the
+ * array's address in the current device's context (cudaGetSymbolAddress); the
+ * first call on a device loads the code there, so make it before any stream
+ * capture.  All calls share the array and nothing carries
  * over between calls (every slot read is written earlier in the same call), but
  * calls that overlap on the GPU (e.g. on two streams) race on it.  The call
  * allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
  * Synchronises `stream`. */
 int mra_norm_noalloc(const mra_tree_view *tree, double *per_box, double *total, void *stream);
 
-/* Compare two trees with the same k: boxes are matched by key; a box present
- * in one tree only counts in full.  Host result; synchronises `stream`. */
+/* Relative L2 error of `test` against `ref` (the error measure the apply's accuracy is stated
+ * in: || test - ref ||_2 / || ref ||_2, also per level).  Both trees have the same k; boxes are
+ * matched by key and a box present in one tree only counts in full (the other side as zero).
+ * By the orthonormality of the basis (Sec. 2.1, eq. scalingfunc) coefficient differences are
+ * function differences, so on trees of the same boxes diff_norm is the L2 norm of the difference
+ * of the two functions.  Host result; synchronises `stream`. */
 int mra_compare(const mra_tree_view *test, const mra_tree_view *ref, mra_compare_result *res,
                 void *stream);
 

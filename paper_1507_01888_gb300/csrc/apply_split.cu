@@ -4,8 +4,9 @@
 //     t1 = s x_1 Rx,  t2 = t1 x_2 Ry,  t3 = t2 x_3 Rz,  r += c_m t3,
 // run as BF16 tcgen05 MMAs with FP32 accumulation in tensor memory; every FP64
 // or FP32 operand x is split into P BF16 pieces x = x0 + x1 (+ x2) and the
-// products x_p y_q with p + q < P are kept.  The Gaussian-term sum and the
-// per-box accumulation are FP64, in registers.
+// products x_p y_q with p + q < P are kept.  The Gaussian-term sums and the
+// per-box accumulation are compensated FP32 sums in registers (a sum and its Kahan
+// correction per coefficient), formed into FP64 at the end.
 //
 // Work decomposition (destination-stationary, no atomics): a CTA owns a tile of
 // G consecutive destination boxes (slot i = 0..G-1).  Their records are grouped
@@ -22,7 +23,8 @@
 // R_d is the K-major B operand (N = output index, K = input index), its P
 // pieces stacked along N so that one MMA per A piece covers all kept products.
 // Stage 3 multiplies by c_m R_z.  Each term's FP32 stage-3 output is added into per-slot
-// sums kept as FP32 pairs (TwoSum), so the term and box sums lose nothing to rounding.
+// compensated FP32 sums (Kahan); in one-slot tiles two consecutive terms are first summed in
+// the tensor-memory accumulator (JOIN).
 #include <atomic>
 
 #include <cuda_bf16.h>

@@ -10,6 +10,7 @@
 // the product interpolated at the points.  The inner product is the coefficient dot product
 // over the common leaves (the basis is orthonormal).
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include <cub/cub.cuh>
@@ -18,6 +19,12 @@
 
 namespace mra {
 namespace {
+
+// c <- alpha c over n * k3 coefficients (grid-stride).
+__global__ void scale_kernel(int64_t n, double alpha, double *c) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    c[i] *= alpha;
+}
 
 // Coefficients of the union leaves: the tree's own where the key is its, zero elsewhere.
 __global__ void ext_rows_kernel(int64_t n, int k3, const int64_t *src, const double *coeffs, double *out) {
@@ -312,5 +319,20 @@ extern "C" int mra_inner(const mra_tree_view *a, const mra_tree_view *b, double 
   MRA_CUDA_TRY(cub::DeviceReduce::Sum(tmp, tb, d, sum, (int)n, s));
   MRA_CUDA_TRY(cudaMemcpyAsync(result, sum, 8, cudaMemcpyDeviceToHost, s));
   MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  return MRA_OK;
+}
+
+extern "C" int mra_scale(mra_tree_view *t, double alpha, void *stream) {
+  if (!t) return fail(MRA_ERR_ARG, "mra_scale: NULL tree view");
+  if (t->n < 0 || t->n > t->cap) return fail(MRA_ERR_ARG, "mra_scale: bad n/cap");
+  if (t->k < 1 || t->k > MRA_MAX_NS_K) return fail(MRA_ERR_ARG, "mra_scale: k=%d invalid", t->k);
+  if (!std::isfinite(alpha)) return fail(MRA_ERR_ARG, "mra_scale: alpha is not finite");
+  if (t->n == 0) return MRA_OK;
+  if (!t->coeffs) return fail(MRA_ERR_ARG, "mra_scale: NULL coefficients");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = t->n * (int64_t)t->k * t->k * t->k;
+  const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  scale_kernel<<<counted(grid), 256, 0, s>>>(n, alpha, t->coeffs);
+  MRA_CUDA_TRY(cudaGetLastError());
   return MRA_OK;
 }

@@ -2,11 +2,11 @@
 // allocation, for callers that cannot allocate device memory (see include/mra.h).
 //
 // Scratch lives in one file-scope __device__ array of fixed size, shared by every
-// call on a device.  Host code never uses the array's name as an address: on the
-// first call on each device (with that device current) it asks the runtime for
-// the array's device address with cudaGetSymbolAddress and passes that pointer
-// to the kernels.
-#include <mutex>
+// call on a device.  Host code never uses the array's name as an address: every
+// call asks the runtime for the array's device address in the current device's
+// context with cudaGetSymbolAddress and passes that pointer to the kernels.  The
+// lookup is not cached, so a new primary context (after cudaDeviceReset) gets its
+// own address; once the module is loaded in a context the lookup allocates nothing.
 
 #include "mra_internal.cuh"
 
@@ -17,9 +17,6 @@ namespace {
 // [0, MAX) per-box squared norms, [MAX] the total.  Every slot a call reads is
 // written earlier in the same call, so nothing needs clearing between calls.
 static __device__ __align__(256) double g_norm_scratch[MRA_NOALLOC_MAX_BOXES + 32];
-
-std::mutex g_setup_mutex;
-double *g_scratch_ptr[64] = {nullptr};
 
 __global__ void sq_norm_kernel(int64_t n, int k3, const double *coeffs, double *sq,
                                double *per_box) {
@@ -50,21 +47,18 @@ __global__ void sum_kernel(int64_t n, const double *sq, double *total) {
   if (threadIdx.x == 0) *total = red[0];
 }
 
-// Device address of the scratch array on the current device (set up once per device).
+// Device address of the scratch array in the current device's context.  The first lookup in a
+// context loads the library's device code there (lazy module loading), which brings the array
+// into that device's memory; later lookups only read the address.
 int scratch_for_current_device(double **out) {
   int dev = 0;
   MRA_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return fail(MRA_ERR_UNSUPPORTED, "mra_norm_noalloc: device %d >= 64", dev);
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[dev]) {
-    double *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress((void **)&p, g_norm_scratch);
-    if (e != cudaSuccess || !p)
-      return fail(MRA_ERR_CUDA, "mra_norm_noalloc: cudaGetSymbolAddress failed on device %d: %s", dev,
-                  cudaGetErrorString(e));
-    g_scratch_ptr[dev] = p;
-  }
-  *out = g_scratch_ptr[dev];
+  double *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress((void **)&p, g_norm_scratch);
+  if (e != cudaSuccess || !p)
+    return fail(MRA_ERR_CUDA, "mra_norm_noalloc: cudaGetSymbolAddress failed on device %d: %s", dev,
+                cudaGetErrorString(e));
+  *out = p;
   return MRA_OK;
 }
 

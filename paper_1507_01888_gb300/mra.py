@@ -44,6 +44,7 @@ EXPORTED = [
     "mra_apply_graph_create", "mra_apply_graph_launch", "mra_apply_graph_status", "mra_apply_graph_info",
     "mra_apply_graph_free", "mra_debug_inject_stall", "mra_debug_status", "mra_debug_selftest",
     "mra_operator_refit", "mra_operator_blocks", "mra_release_memory", "mra_apply_host",
+    "mra_measure_fp64_peak", "mra_scale",
 ]
 NOALLOC_MAX_BOXES = 1 << 20
 
@@ -166,6 +167,8 @@ def load(build_if_stale: bool = True):
         lib.mra_inner.argtypes = [P(TreeView), P(TreeView), P(d), vp]
         lib.mra_norm.argtypes = [P(TreeView), vp, P(d), vp]
         lib.mra_norm_noalloc.argtypes = [P(TreeView), vp, P(d), vp]
+        lib.mra_measure_fp64_peak.argtypes = [d, P(d), P(d), vp]
+        lib.mra_scale.argtypes = [P(TreeView), d, vp]
         lib.mra_compare.argtypes = [P(TreeView), P(TreeView), P(CompareResult), vp]
         u64, i64 = ctypes.c_uint64, ctypes.c_int64
         lib.mra_log_terms.argtypes = [vp, P(TreeView), P(ApplyOpts), i64, u64, vp, vp, P(i64), vp,
@@ -523,6 +526,13 @@ def norm_noalloc(tree: Tree, per_box: torch.Tensor | None = None, stream=None):
 
     For callers that cannot allocate device memory; per_box (float64, >= tree.n
     entries on the tree's device) is the caller's, or None."""
+    if per_box is not None:
+        if per_box.dtype != torch.float64 or not per_box.is_contiguous():
+            raise ValueError("norm_noalloc: per_box must be a contiguous float64 tensor")
+        if per_box.device != tree.coeffs.device:
+            raise ValueError(f"norm_noalloc: per_box is on {per_box.device}, the tree on {tree.coeffs.device}")
+        if per_box.numel() < tree.n:
+            raise ValueError(f"norm_noalloc: per_box holds {per_box.numel()} entries, the tree {tree.n} boxes")
     tot = ctypes.c_double()
     v = tree.view()
     ptr = ctypes.c_void_p(per_box.data_ptr()) if per_box is not None else None
@@ -723,6 +733,20 @@ def debug_selftest(stream=None):
 def debug_inject_stall():
     """mra_debug_inject_stall: the next split-precision apply's waits run out (MRA_ERR_TIMEOUT)."""
     _check(load().mra_debug_inject_stall())
+
+
+def scale(tree: Tree, alpha: float, stream=None) -> Tree:
+    """mra_scale: tree's coefficients times alpha, in place (returns the tree)."""
+    v = tree.view()
+    _check(load().mra_scale(ctypes.byref(v), float(alpha), _stream(stream)))
+    return tree
+
+
+def measure_fp64_peak(seconds: float = 2.0, stream=None):
+    """mra_measure_fp64_peak: (DFMA TFLOP/s, DMMA TFLOP/s) of the current device, measured."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().mra_measure_fp64_peak(float(seconds), ctypes.byref(a), ctypes.byref(b), _stream(stream)))
+    return a.value, b.value
 
 
 def release_memory():

@@ -7,8 +7,8 @@ and psi~ normalised for the next step.  Every step is a library call: the nuclea
 -Z/r is projected as the Gaussian sum of the library's own 1/r fit (mra_project), V psi is a
 product on the common refinement (mra_multiply), G_E is the BSH operator with mu = sqrt(-2E)
 applied in non-standard form on the adaptive tree (mra_apply_ns_tree; the library's kernel is
-exp(-mu r)/r, so -2 G_E = -(1/2 pi) times it), the result is truncated (mra_truncate) and the
-inner products come from mra_inner.  For Z = 1 the exact answer is E = -1/2, psi = e^{-r}/sqrt(pi).
+exp(-mu r)/r, so -2 G_E = -(1/2 pi) times it), the result is scaled (mra_scale), truncated (mra_truncate)
+and normalised (mra_scale), and the inner products come from mra_inner.  For Z = 1 the exact answer is E = -1/2, psi = e^{-r}/sqrt(pi).
 """
 from __future__ import annotations
 
@@ -55,13 +55,13 @@ def bsh_step(V, psi, E: float, thresh: float, M_bsh: int = 60, fit_eps: float = 
     else:
         opts = mra.make_opts(precision=precision, stencil=mra.STENCIL_SHELLS, max_disp=max_disp)
     r, st = mra.apply_ns_tree(op, ns, Vpsi, 1, opts)
-    r.coeffs[: r.n] *= -1.0 / (2.0 * math.pi)
+    mra.scale(r, -1.0 / (2.0 * math.pi))
     new, _ = mra.truncate(r, thresh)
     vp = mra.inner(Vpsi, psi)
     vn = mra.inner(Vpsi, new)
     nn = mra.inner(new, new)
     dE = -(vp - vn) / nn
-    new.coeffs[: new.n] /= math.sqrt(nn)
+    mra.scale(new, 1.0 / math.sqrt(nn))
     if info is not None:
         info.update(apply_stats=st, n_vpsi=Vpsi.n, n_result=r.n, n_psi=new.n)
     return E + dE, new, dE
@@ -74,7 +74,7 @@ def gaussian_start(Z: float, k: int, L: float, thresh: float, device="cuda"):
     g = {"coef": np.array([(2 * a / math.pi) ** 0.75]), "expnt": np.array([a]), "cx": np.zeros(1),
          "cy": np.zeros(1), "cz": np.zeros(1)}
     psi = mra.project(g, k, L, thresh=thresh, init_level=2, max_level=19, device=device)
-    psi.coeffs[: psi.n] /= math.sqrt(mra.inner(psi, psi))
+    mra.scale(psi, 1.0 / math.sqrt(mra.inner(psi, psi)))
     return psi
 
 

@@ -386,11 +386,59 @@ def test_oracle_mlp_gradient_matches_finite_differences():
         e = np.zeros(M.NALL); e[i] = h
         fd = (M.loss_and_grad(p + e, x, y)[0] - M.loss_and_grad(p - e, x, y)[0]) / (2 * h)
         assert abs(fd - g[i]) <= 1e-7 * max(1.0, abs(g[i]))
-    # forward is the documented composition
-    W1, b1, W2, b2, W3, b3, xm, xs, ym, ys = M.unpack(p)
-    z = (x[0] - xm) / xs
-    o = W3 @ np.tanh(W2 @ np.tanh(W1 @ z + b1) + b2) + b3
-    assert M.forward(p, x[:1])[0] == pytest.approx(o * ys + ym, rel=1e-14)
+
+
+def test_oracle_mlp_forward_hand_worked_case():
+    """A parameter vector in the documented flat layout with a few non-zero entries, chosen so
+    that every tanh is known in closed form: with z0 = (x0 - x_mean0)/x_std0 = atanh(1/2),
+    h1[0] = tanh(z0) = 1/2; W2[1][0] = 2 (output unit 1, input unit 0) gives h2[1] = tanh(1);
+    W3[1] = 3, b3 = 1/2 and the output scaling (y_std, y_mean) = (2, 1) give
+    (3 tanh(1) + 1/2) * 2 + 1.  A transposed W2 (h2[0] = tanh(2 h1[1]) = 0), swapped
+    (x_mean, x_std) or swapped (y_mean, y_std) all change the value."""
+    import oracle.mlp as M
+    H = 64
+    p = np.zeros(M.NALL)
+    o_W1, o_b1 = 0, 4 * H
+    o_W2 = o_b1 + H
+    o_b2 = o_W2 + H * H
+    o_W3 = o_b2 + H
+    o_b3 = o_W3 + H
+    o_std = o_b3 + 1
+    p[o_W1 + 0 * 4 + 0] = 1.0             # W1[0][0]
+    p[o_W2 + 1 * H + 0] = 2.0             # W2[1][0]
+    p[o_W3 + 1] = 3.0                     # W3[1]
+    p[o_b3] = 0.5                         # b3
+    p[o_std:o_std + 4] = [0.25, -1.0, 3.0, 0.5]   # x_mean
+    p[o_std + 4:o_std + 8] = [2.0, 1.0, 1.0, 4.0]  # x_std
+    p[o_std + 8], p[o_std + 9] = 1.0, 2.0          # y_mean, y_std
+    x = np.array([[0.25 + 2.0 * math.atanh(0.5), 7.0, -2.0, 0.1]])
+    want = (3.0 * math.tanh(1.0) + 0.5) * 2.0 + 1.0
+    assert M.forward(p, x)[0] == pytest.approx(want, rel=1e-15)
+
+
+def test_oracle_mlp_forward_matches_torch_sequential():
+    """The network rebuilt from torch.nn layers in float64, with the weights sliced from the flat
+    vector by the documented layout (not by oracle.mlp.unpack) and the standardisation applied
+    outside the layers: Linear(4,64), Tanh, Linear(64,64), Tanh, Linear(64,1)."""
+    torch = pytest.importorskip("torch")
+    import oracle.mlp as M
+    H = 64
+    rng = np.random.default_rng(3)
+    p = np.concatenate([rng.standard_normal(M.NP) * 0.4,
+                        [0.3, -0.7, 1.9, 0.05], [1.7, 0.6, 2.2, 0.9], [-2.5], [1.3]])
+    x = rng.standard_normal((50, 4)) * 2.0
+    net = torch.nn.Sequential(torch.nn.Linear(4, H), torch.nn.Tanh(), torch.nn.Linear(H, H), torch.nn.Tanh(),
+                              torch.nn.Linear(H, 1)).double()
+    o = 0
+    with torch.no_grad():
+        for lin, (n_out, n_in) in zip((net[0], net[2], net[4]), ((H, 4), (H, H), (1, H))):
+            lin.weight.copy_(torch.from_numpy(p[o:o + n_out * n_in].reshape(n_out, n_in)))
+            o += n_out * n_in
+            lin.bias.copy_(torch.from_numpy(p[o:o + n_out]))
+            o += n_out
+        xm, xs, ym, ys = p[o:o + 4], p[o + 4:o + 8], p[o + 8], p[o + 9]
+        ref = net(torch.from_numpy((x - xm) / xs)).numpy()[:, 0] * ys + ym
+    np.testing.assert_allclose(M.forward(p, x), ref, rtol=1e-13, atol=1e-13)
 
 
 # ----------------------------------------------------------------- non-standard form (Sec. 2.2)
