@@ -120,7 +120,14 @@ typedef struct {
                                 key lies in [dest_lo, dest_hi) are computed and written, with the
                                 screen's shell decisions of the whole apply; dest_hi = 0 keeps all.
                                 mra_apply only (not batched, not the non-standard form) */
+  int split_kernel; /* MRA_PREC_SPLIT_BF16: MRA_SPLIT_AUTO (0) runs the source-stationary kernel
+                       where it applies (even k from 4 to 10, records with |l|_inf <= 2) and the
+                       destination-stationary one elsewhere; MRA_SPLIT_DEST (1) always the
+                       destination-stationary one (tile_variant picks its shape) */
 } mra_apply_opts;
+
+#define MRA_SPLIT_AUTO 0
+#define MRA_SPLIT_DEST 1
 
 typedef struct {
   int64_t n_in;               /* source boxes */

@@ -10,6 +10,8 @@
 // destination are contiguous; each destination box is then produced by one
 // CTA that gathers its sources and sums their terms in registers, and written
 // exactly once.  No atomics touch the result.
+#include <algorithm>
+
 #include <cub/cub.cuh>
 
 #include "apply_internal.cuh"
@@ -562,7 +564,7 @@ struct Layout {
   size_t split_bytes, tmp_bytes, total;
 };
 
-static Layout make_layout(int64_t n_in, int64_t P, bool learned) {
+static Layout make_layout(int64_t n_in, int64_t P, bool learned, bool src_path = false) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -597,7 +599,7 @@ static Layout make_layout(int64_t n_in, int64_t P, bool learned) {
   L.dfunc = take(np * 4);
   L.fnoff = take((MRA_MAX_FUNCS + 1) * 8);
   L.lev = take(2 * (MRA_MAX_LEVEL + 1) * 8);
-  L.split_bytes = split_workspace_bytes(np);
+  L.split_bytes = src_path ? std::max(split_workspace_bytes(np), src_workspace_bytes(nb)) : split_workspace_bytes(np);
   L.split = take(L.split_bytes);
   // CUB temporary storage: the largest of the calls below
   size_t a = 0, b = 0, c = 0, d = 0, e = 0;
@@ -615,8 +617,26 @@ static Layout make_layout(int64_t n_in, int64_t P, bool learned) {
   return L;
 }
 
+// The records' largest |l|_inf on level n: the stencil's radius within the operator's and the cell's.
+static int records_disp(const Operator &op, const mra_apply_opts &o, int n) {
+  int D = apply_max_disp(op, o);
+  if (n < op.min_level || n > op.max_level) return 0;
+  const int Dop = op.D[n - op.min_level];
+  if (D > Dop) D = Dop;
+  if ((int64_t)D > (1LL << n) - 1) D = (int)((1LL << n) - 1);
+  return D;
+}
+
+bool apply_uses_src_path(const Operator &op, const mra_apply_opts &o) {
+  if (o.precision != MRA_PREC_SPLIT_BF16 || o.split_kernel == MRA_SPLIT_DEST) return false;
+  int dmax = 0;
+  for (int n = op.min_level; n <= op.max_level; ++n) dmax = std::max(dmax, records_disp(op, o, n));
+  return src_path_supported(op.k, dmax);
+}
+
 size_t apply_workspace_bytes(const Operator &op, const mra_apply_opts &o, int64_t n_in) {
-  return make_layout(n_in, apply_max_records(op, o, n_in), o.screen == MRA_SCREEN_LEARNED).total;
+  return make_layout(n_in, apply_max_records(op, o, n_in), o.screen == MRA_SCREEN_LEARNED,
+                     apply_uses_src_path(op, o)).total;
 }
 
 // Pointers into a carved workspace.
@@ -811,7 +831,8 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
   const int k = op.k, k3 = k * k * k;
   const int64_t n_in = in.n;
   const int64_t Pmax = apply_max_records(op, o, n_in);
-  Layout L = make_layout(n_in, Pmax, o.screen == MRA_SCREEN_LEARNED);
+  const bool src_path = apply_uses_src_path(op, o);
+  Layout L = make_layout(n_in, Pmax, o.screen == MRA_SCREEN_LEARNED, src_path);
   if (ws_bytes < L.total)
     return fail(MRA_ERR_CAPACITY, "mra_apply: workspace of %zu bytes < %zu needed", ws_bytes, L.total);
   WsPtrs W = carve(L, ws);
@@ -896,6 +917,9 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
   wk.rec_l = rl;
   wk.rec_mask = rmask;
   wk.dest_key = dkey;
+  wk.rec_cnt = W.cnt;
+  wk.rec_off = W.off;
+  wk.box_kept = W.bkept;
   wk.split_ws = w + L.split;
   wk.split_ws_bytes = L.split_bytes;
   wk.ev0 = ev0;
@@ -913,6 +937,17 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
     MRA_CUDA_TRY(cudaGetLastError());
     if (ev1) MRA_CUDA_TRY(cudaEventRecord(ev1, s));
     rc = MRA_OK;
+  } else if (src_path) {
+    // the partial sums (one k^3 block of floats per record): the graph's own buffer when
+    // recorded, else from the library's memory pool for this call
+    int dap[MRA_MAX_LEVEL + 1];
+    for (int n = 0; n <= MRA_MAX_LEVEL; ++n) dap[n] = records_disp(op, o, n);
+    float *partial = fx ? fx->partial : nullptr;
+    if (!fx) MRA_CUDA_TRY(pool_malloc((void **)&partial, (size_t)P * k3 * sizeof(float), s));
+    if (!partial) return fail(MRA_ERR_ARG, "mra_apply: no partial-sum buffer for the recorded apply");
+    rc = apply_src_run(op, in, o, out, wk, dap, partial, s);
+    if (!fx) cudaFreeAsync(partial, s);
+    if (rc != MRA_OK) return rc;
   } else {
     rc = apply_split_run(op, in, o, out, wk, stats, s);
     if (rc != MRA_OK) return rc;

@@ -14,6 +14,7 @@ struct FixedSizes {
   int64_t P = 0, nd = 0;
   int *status = nullptr;                  // device word
   const int64_t *d_in_offsets = nullptr;  // device copy of the batched input offsets (nfunc + 1)
+  float *partial = nullptr;               // the source-stationary kernel's partial sums (P k^3 floats)
 };
 
 // The sorted work list handed from the screen/sort stage to an apply kernel.
@@ -30,6 +31,9 @@ struct ApplyWork {
   const int *rec_l;
   const uint64_t *rec_mask;
   const uint64_t *dest_key;
+  const int64_t *rec_cnt;     // records of each source box (source order) and their offsets
+  const int64_t *rec_off;
+  const int64_t *box_kept;    // kept terms of each source box
   void *split_ws;             // scratch for the tensor-core path's grouping
   size_t split_ws_bytes;
   cudaEvent_t ev0, ev1;       // recorded around the apply kernel when non-null
@@ -45,6 +49,18 @@ int apply_split_run(const Operator &op, const mra_tree_view &in, const mra_apply
                     mra_tree_view &out, const ApplyWork &wk, mra_apply_stats *stats,
                     cudaStream_t s);
 size_t split_workspace_bytes(int64_t P);
+// source-stationary tensor-core apply (apply_src.cu): orders and displacement ranges it covers,
+// its scratch, and the run (dap: the records' |l|_inf range per absolute level)
+bool src_path_supported(int k, int max_rec_disp);
+size_t src_workspace_bytes(int64_t n_in);
+int apply_src_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts &o, mra_tree_view &out,
+                  const ApplyWork &wk, const int *dap, float *partial, cudaStream_t s);
+// whether an apply with these options runs the source-stationary kernel (its partial sums need
+// P k^3 floats besides the workspace)
+bool apply_uses_src_path(const Operator &op, const mra_apply_opts &o);
+// test hook of the failure path (one-shot), and the fixed-size mode's status from a kernel error word
+bool take_injected_stall();
+void split_fixed_err(const int *err, int *status, cudaStream_t s);
 // BF16 pieces of the operator's blocks and of c_m times them (allocated once; rebuild = true
 // recomputes them, after the blocks or the coefficients changed)
 int split_blocks_build(Operator &op, cudaStream_t s, bool rebuild = false);

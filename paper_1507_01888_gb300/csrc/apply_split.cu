@@ -27,48 +27,24 @@
 // the tensor-memory accumulator (JOIN).
 #include <atomic>
 
-#include <cuda_bf16.h>
-
 #include <cub/cub.cuh>
 
 #include "apply_internal.cuh"
+#include "split_common.cuh"
 #include "tcgen05.cuh"
 
 namespace mra {
 
 namespace {
 
+using namespace split;
+
 constexpr int SPLIT_THREADS = 256;      // 8 warps: two warps per tensor-memory lane quarter
-constexpr int MG_BYTES = 272;           // stride of the 8-row groups: 256 B of core matrices + 16 B
-                                        // so that consecutive groups start 4 banks apart
-constexpr int TILE_BYTES = 16 * MG_BYTES;  // one 128 x 16 BF16 operand tile
-constexpr int BPIECE_BYTES = 512;       // one 16 x 16 BF16 block piece
-constexpr int BSTAGE_BYTES = 3 * BPIECE_BYTES;  // the three pieces of one block
 constexpr int BTERM_BYTES = 3 * BSTAGE_BYTES;   // the three blocks (x, y, z) of one term
 constexpr int NBUF = 4;                         // most block buffers a CTA uses
 constexpr int RING = 4;                         // term-info ring from warpgroup 0 to 1
 constexpr int MAX_G = 32;
 constexpr int JOIN = 2;                         // terms summed in tensor memory per flush
-constexpr long long WAIT_CYCLES = 4000000000LL;  // bounded mbarrier wait (~2 s)
-
-
-// byte offset of element (row m, contraction kk) in an MN-major operand: core
-// matrices of 8 contraction rows x 8 consecutive rows (128 B); the two
-// contraction groups of a row group 128 B apart (descriptor LBO), the 16 row
-// groups of a 128-row tile MG_BYTES apart (descriptor SBO)
-__device__ __forceinline__ uint32_t a_off(int m, int kk) {
-  return (uint32_t)((m >> 7) * TILE_BYTES + ((m & 127) >> 3) * MG_BYTES + (kk >> 3) * 128 +
-                    (kk & 7) * 16 + (m & 7) * 2);
-}
-
-__device__ __forceinline__ void split3(double x, __nv_bfloat16 &p0, __nv_bfloat16 &p1,
-                                       __nv_bfloat16 &p2) {
-  p0 = __double2bfloat16(x);
-  double r = x - (double)__bfloat162float(p0);
-  p1 = __double2bfloat16(r);
-  r -= (double)__bfloat162float(p1);
-  p2 = __double2bfloat16(r);
-}
 
 
 struct SplitArgs {
@@ -93,24 +69,6 @@ struct SplitArgs {
   int64_t n_src, n_rec, n_blocks;  // sizes for the index checks of the checking build
 };
 
-// Named barrier over one warpgroup (128 threads) with an OR vote.
-__device__ __forceinline__ bool wg_vote_or(int barrier_id, bool flag) {
-  uint32_t out;
-  asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, 128, p;\n"
-      " selp.u32 %0, 1, 0, q;\n}\n"
-      : "=r"(out)
-      : "r"((uint32_t)flag), "r"(barrier_id)
-      : "memory");
-  return out != 0;
-}
-__device__ __forceinline__ void wg_sync(int barrier_id) {
-  asm volatile("bar.sync %0, 128;" ::"r"(barrier_id) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
 // Tile shapes for an even k.  A CTA owns G consecutive destination boxes (slots) whose
 // G k^2 operand rows fill T <= TT tiles of 128 rows.  Tensor memory holds the stage-1
 // and stage-2 outputs (48 columns per tile each: three 16-column piece groups) and the
@@ -134,17 +92,6 @@ __host__ __device__ constexpr uint32_t tile_slots(int t, int k2, int G) {
   for (int i = 0; i < G; ++i)
     if (i * k2 < 128 * (t + 1) && (i + 1) * k2 > 128 * t) m |= 1u << i;
   return m;
-}
-
-// Split x and y into three BF16 pieces each (x = x0 + x1 + x2 to 24 bits), packed in pairs.
-__device__ __forceinline__ void split_pair(float x, float y, __nv_bfloat162 &h0, __nv_bfloat162 &h1,
-                                           __nv_bfloat162 &h2) {
-  h0 = __floats2bfloat162_rn(x, y);
-  float2 f0 = __bfloat1622float2(h0);
-  float rx = x - f0.x, ry = y - f0.y;
-  h1 = __floats2bfloat162_rn(rx, ry);
-  float2 f1 = __bfloat1622float2(h1);
-  h2 = __floats2bfloat162_rn(rx - f1.x, ry - f1.y);
 }
 
 // Warp roles and the term pipeline.  Terms of a group flow through three MMA stages:
@@ -271,10 +218,8 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(TT)) apply_split_kerne
 #pragma unroll
     for (int u = 0; u < U; ++u) addr[u] = a0 + a_off(mrow + (K % 8 == 0 ? 8 : 2) * u, a_idx);
   };
-  auto st32 = [](uint32_t addr, uint32_t v) { asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory"); };
-  auto st128 = [](uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
-  };
+  auto st32 = st_shared32;
+  auto st128 = st_shared128;
   // a thread's k values split into P pieces, stored at its precomputed unit addresses
   auto store_units = [&](const uint32_t *addr, const float *v) {
     const uint32_t stride = T * TILE_BYTES;
@@ -652,10 +597,6 @@ __global__ void __launch_bounds__(SPLIT_THREADS, minb_for(TT)) apply_split_kerne
   if (warp == 0) tc::tmem_dealloc(tmem, NCOL);
 }
 
-// ---------------------------------------------------------------- failure-path test hook
-std::atomic<int> g_inject_stall{0};
-bool take_injected_stall() { return g_inject_stall.exchange(0) != 0; }
-
 // ---------------------------------------------------------------- work-list kernels
 // Fixed-size (graph) mode: the kernel's error word into the graph's status.
 __global__ void fixed_err_kernel(const int *err, int *status) {
@@ -698,27 +639,40 @@ __global__ void group_bounds_kernel(int64_t P, const uint64_t *key2s, const int 
 
 // Block pieces in the K-major core-matrix layout the MMA reads: piece p of block
 // x R (N = output index i, K = input index j), element (i, j) at
-// p*512 + (i/8)*256 + (j/8)*128 + (i%8)*16 + (j%8)*2; zero outside k x k.  Blocks are
-// numbered m * nl + (l + D) within one level; x = c[m] when c is given, else 1.
+// (i/8)*256 + (j/8)*128 + (i%8)*16 + (j%8)*2 of a 512-byte piece; zero outside k x k.  Blocks
+// are numbered m * nl + (l + D) within one level; x = c[m] when c is given, else 1.  Piece p
+// of block (m, l) sits at byte (m nl + l + D) 1536 + p 512 (block-major: the three pieces of a
+// block together), or with piece_major at (m nl 3 + p nl + l + D) 512 (all displacements of
+// one piece together, so that the pieces of consecutive displacements are consecutive).
 __global__ void split_blocks_kernel(int64_t n_blocks, int k, int nl, const double *c, const double *R,
-                                    unsigned char *out) {
+                                    unsigned char *out, int piece_major) {
   int64_t blk = blockIdx.x;
   if (blk >= n_blocks) return;
   const double x = c ? c[blk / nl] : 1.0;
+  const int64_t m = blk / nl, l = blk - m * nl;
   for (int e = threadIdx.x; e < 256; e += blockDim.x) {
     int i = e / 16, j = e % 16;
     double y = (i < k && j < k) ? x * R[blk * k * k + i * k + j] : 0.0;
-    __nv_bfloat16 p0, p1, p2;
-    split3(y, p0, p1, p2);
+    __nv_bfloat16 pc[3];
+    split3(y, pc[0], pc[1], pc[2]);
     uint32_t off = (i / 8) * 256 + (j / 8) * 128 + (i % 8) * 16 + (j % 8) * 2;
-    unsigned char *b = out + blk * BSTAGE_BYTES;
-    *(__nv_bfloat16 *)(b + off) = p0;
-    *(__nv_bfloat16 *)(b + BPIECE_BYTES + off) = p1;
-    *(__nv_bfloat16 *)(b + 2 * BPIECE_BYTES + off) = p2;
+    for (int p = 0; p < 3; ++p) {
+      const int64_t at = piece_major ? ((m * nl * 3 + p * nl + l) * BPIECE_BYTES)
+                                     : (blk * BSTAGE_BYTES + p * BPIECE_BYTES);
+      *(__nv_bfloat16 *)(out + at + off) = pc[p];
+    }
   }
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------- failure-path test hook
+std::atomic<int> g_inject_stall{0};
+bool take_injected_stall() { return g_inject_stall.exchange(0) != 0; }
+
+void split_fixed_err(const int *err, int *status, cudaStream_t s) {
+  fixed_err_kernel<<<counted(1), 1, 0, s>>>(err, status);
+}
 
 size_t split_workspace_bytes(int64_t P) {
   int64_t np = P > 0 ? P : 1;
@@ -734,17 +688,20 @@ size_t split_workspace_bytes(int64_t P) {
 
 int split_blocks_build(Operator &op, cudaStream_t s, bool rebuild) {
   if (op.d_Rsplit && !rebuild) return MRA_OK;
-  // two tables: the blocks R (stages 1 and 2) and c_m R (stage 3)
-  if (!op.d_Rsplit) MRA_CUDA_TRY(cudaMalloc(&op.d_Rsplit, (size_t)2 * op.n_blocks * BSTAGE_BYTES));
+  // three tables: the blocks R (stages 1 and 2) and c_m R (stage 3 of the destination-stationary
+  // kernel), block-major; c_m R piece-major (stage 3 of the source-stationary kernel)
+  if (!op.d_Rsplit) MRA_CUDA_TRY(cudaMalloc(&op.d_Rsplit, (size_t)3 * op.n_blocks * BSTAGE_BYTES));
   unsigned char *plain = (unsigned char *)op.d_Rsplit;
   unsigned char *scaled = plain + (size_t)op.n_blocks * BSTAGE_BYTES;
+  unsigned char *zpack = plain + (size_t)2 * op.n_blocks * BSTAGE_BYTES;
   for (size_t li = 0; li < op.D.size(); ++li) {
     const int nl = 2 * op.D[li] + 1;
     const int64_t nb = (int64_t)op.M * nl, base = op.level_off[li];
     if (nb <= 0) continue;
     const double *R = op.d_R + base * op.k * op.k;
-    split_blocks_kernel<<<counted((unsigned)nb), 128, 0, s>>>(nb, op.k, nl, nullptr, R, plain + base * BSTAGE_BYTES);
-    split_blocks_kernel<<<counted((unsigned)nb), 128, 0, s>>>(nb, op.k, nl, op.d_c, R, scaled + base * BSTAGE_BYTES);
+    split_blocks_kernel<<<counted((unsigned)nb), 128, 0, s>>>(nb, op.k, nl, nullptr, R, plain + base * BSTAGE_BYTES, 0);
+    split_blocks_kernel<<<counted((unsigned)nb), 128, 0, s>>>(nb, op.k, nl, op.d_c, R, scaled + base * BSTAGE_BYTES, 0);
+    split_blocks_kernel<<<counted((unsigned)nb), 128, 0, s>>>(nb, op.k, nl, op.d_c, R, zpack + base * BSTAGE_BYTES, 1);
     MRA_CUDA_TRY(cudaGetLastError());
   }
   return MRA_OK;

@@ -20,6 +20,7 @@ struct ApplyGraph {
   cudaStream_t cap = nullptr;
   int *d_status = nullptr;
   int64_t *d_in_offsets = nullptr;
+  float *d_partial = nullptr;
   FixedSizes fx;
   int64_t n_out = 0;
   long long kernels = 0;
@@ -31,6 +32,7 @@ void destroy(ApplyGraph *g) {
   if (g->graph) cudaGraphDestroy(g->graph);
   if (g->d_status) cudaFree(g->d_status);
   if (g->d_in_offsets) cudaFree(g->d_in_offsets);
+  if (g->d_partial) cudaFree(g->d_partial);
   if (g->cap) cudaStreamDestroy(g->cap);
   delete g;
 }
@@ -81,9 +83,14 @@ int mra_apply_graph_create(const mra_operator *h, int nfunc, const mra_tree_view
   g->fx.status = g->d_status;
   g->fx.d_in_offsets = g->d_in_offsets;
   g->n_out = out->n;
+  const Operator *op = reinterpret_cast<const Operator *>(h);
+  if (apply_uses_src_path(*op, *o) && st.pairs > 0) {  // the recorded apply's partial sums, owned by the graph
+    e = cudaMalloc((void **)&g->d_partial, (size_t)st.pairs * op->k * op->k * op->k * sizeof(float));
+    if (e != cudaSuccess) return bail(MRA_ERR_CUDA, "partial-sum buffer", e);
+    g->fx.partial = g->d_partial;
+  }
   e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) return bail(MRA_ERR_CUDA, "capture stream", e);
-  const Operator *op = reinterpret_cast<const Operator *>(h);
   const long long k0 = launch_total();
   e = cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return bail(MRA_ERR_CUDA, "begin capture", e);

@@ -33,6 +33,8 @@ SCREEN_LEARNED = 2
 MLP_PARAMS = 4555
 STENCIL_SHELLS = 0
 STENCIL_NEAREST = 1
+SPLIT_AUTO = 0
+SPLIT_DEST = 1
 
 EXPORTED = [
     "mra_last_error", "mra_version", "mra_project", "mra_operator_create", "mra_operator_fit",
@@ -70,7 +72,8 @@ class ApplyOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("pieces", ctypes.c_int), ("screen", ctypes.c_int),
                 ("tau", ctypes.c_double), ("stencil", ctypes.c_int), ("max_disp", ctypes.c_int),
                 ("mlp", ctypes.c_void_p), ("delta", ctypes.c_double), ("tile_variant", ctypes.c_int),
-                ("delta_level", ctypes.c_void_p), ("dest_lo", ctypes.c_uint64), ("dest_hi", ctypes.c_uint64)]
+                ("delta_level", ctypes.c_void_p), ("dest_lo", ctypes.c_uint64), ("dest_hi", ctypes.c_uint64),
+                ("split_kernel", ctypes.c_int)]
 
 
 class ApplyStats(ctypes.Structure):
@@ -333,12 +336,14 @@ class NSOperator(Operator):
 
 def make_opts(precision=PREC_FP64, pieces=3, screen=SCREEN_NONE, tau=0.0, stencil=STENCIL_NEAREST,
               max_disp=1, mlp: torch.Tensor | None = None, delta: float = 0.0, tile_variant: int = 0,
-              delta_level=None, dest_range=None) -> ApplyOpts:
+              delta_level=None, dest_range=None, split_kernel: int = 0) -> ApplyOpts:
     """delta_level: optional per-source-level margins (MAX_LEVEL + 1 values; inf keeps every term
     of a level) replacing delta for the learned screen.  dest_range: (lo, hi) destination keys
-    to compute (owner computes; hi exclusive), None for all."""
+    to compute (owner computes; hi exclusive), None for all.  split_kernel: SPLIT_AUTO (the
+    source-stationary kernel where it applies) or SPLIT_DEST (the destination-stationary one)."""
     lo, hi = (0, 0) if dest_range is None else (int(dest_range[0]), int(dest_range[1]))
-    o = ApplyOpts(precision, pieces, screen, tau, stencil, max_disp, None, delta, tile_variant, None, lo, hi)
+    o = ApplyOpts(precision, pieces, screen, tau, stencil, max_disp, None, delta, tile_variant, None, lo, hi,
+                  split_kernel)
     if mlp is not None:
         o.mlp = mlp.data_ptr()
         o._mlp_ref = mlp  # keep the tensor alive with the options

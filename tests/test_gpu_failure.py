@@ -27,12 +27,15 @@ def mra():
     return m
 
 
-@pytest.mark.parametrize("tile_variant", [0, 2])
-def test_split_wait_runs_out_and_the_context_survives(mra, tile_variant):
+@pytest.mark.parametrize("kern,tile_variant", [(0, 0), (1, 0), (1, 2)])
+def test_split_wait_runs_out_and_the_context_survives(mra, kern, tile_variant):
+    """Both kernels: the source-stationary one (k = 6 here) and the destination-stationary one's
+    four-tile and one-tile shapes."""
     f = W.gaussian_sum(2, 1.0, 20.0, seed=41, centre_box=3.0)
     keys, coeffs, _ = O.project(f, 6, 8.0, uniform_level=2)
     op = mra.Operator(mra.POISSON, 8, 6, 8.0, 2, 2, max_disp=1, fit_eps=1e-4)
-    opts = mra.make_opts(precision=mra.PREC_SPLIT_BF16, stencil=mra.STENCIL_NEAREST, tile_variant=tile_variant)
+    opts = mra.make_opts(precision=mra.PREC_SPLIT_BF16, stencil=mra.STENCIL_NEAREST, tile_variant=tile_variant,
+                         split_kernel=kern)
     tree = mra.Tree.from_host(keys, coeffs, 8.0)
     ref, _ = mra.apply(op, tree, opts)
     mra.debug_inject_stall()

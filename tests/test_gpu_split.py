@@ -68,14 +68,15 @@ def test_split_random_trees_ragged(mra, k, lev, nbox, seed):
 @pytest.mark.parametrize("k,lev,nbox,seed", [(4, 3, 300, 30), (6, 3, 200, 31), (8, 3, 150, 32), (10, 3, 90, 33),
                                               (12, 2, 40, 34), (14, 2, 30, 35), (16, 2, 20, 36)])
 def test_split_tile_variants(mra, k, lev, nbox, seed):
-    """Tile variants 1 and 2 (two or one 128-row tiles per CTA) equal the oracle like variant 0."""
+    """The source-stationary kernel (k = 4 to 10) and the destination-stationary kernel's tile
+    variants 0, 1 and 2 (four, two or one 128-row tiles per CTA) all equal the oracle."""
     keys, coeffs = W.random_tree_coeffs(nbox, k, lev, seed=seed)
     op = mra.Operator(0, 16, k, 16.0, 0, lev, max_disp=1, fit_eps=1e-4)
     fit = oracle_fit(op)
     ref = O.apply(keys, coeffs, fit["c"], fit["t"], 16.0, stencil=1, tau=0.0)
     tree = mra.Tree.from_host(keys, coeffs, 16.0)
-    for v in (0, 1, 2):
-        o = split_opts(mra, stencil=mra.STENCIL_NEAREST)
+    for kern, v in ((mra.SPLIT_AUTO, 0), (mra.SPLIT_DEST, 0), (mra.SPLIT_DEST, 1), (mra.SPLIT_DEST, 2)):
+        o = split_opts(mra, stencil=mra.STENCIL_NEAREST, split_kernel=kern)
         o.tile_variant = v
         out, _ = mra.apply(op, tree, o)
         gk, gc = out.host()
@@ -96,17 +97,18 @@ def test_split_shells_and_screen_adaptive(mra):
     assert rel_l2(gc, ref.coeffs) <= TOL_MIXED
 
 
-@pytest.mark.parametrize("tile_variant", [0, 2])
-def test_split_full_size_vs_fp64_and_oracle(mra, tile_variant):
+@pytest.mark.parametrize("kern,tile_variant", [(0, 0), (1, 0), (1, 2)])
+def test_split_full_size_vs_fp64_and_oracle(mra, kern, tile_variant):
     """BSH M=60 adaptive k=10 (17,200 boxes): split vs FP64 GPU on every box, vs the oracle on a
-    sample; the four-tile shape and the one-tile shape the benchmark's tuner picks."""
+    sample; the source-stationary kernel the benchmark times, and the destination-stationary
+    kernel's four-tile and one-tile shapes."""
     w = W.bsh_m60_adaptive_k10()
     ok, oc, _ = O.project(w.funcs[0], w.k, w.L, thresh=w.thresh, init_level=w.init_level, max_level=w.max_level)
     op = mra.Operator(w.kernel, w.M, w.k, w.L, 2, 19, max_disp=w.max_disp, mu=w.mu, fit_eps=w.fit_eps)
     fit = oracle_fit(op)
     tree = mra.Tree.from_host(ok, oc, w.L)
     kw = dict(stencil=w.stencil, max_disp=w.max_disp, screen=mra.SCREEN_NORM, tau=w.tau)
-    sp, _ = mra.apply(op, tree, split_opts(mra, tile_variant=tile_variant, **kw))
+    sp, _ = mra.apply(op, tree, split_opts(mra, tile_variant=tile_variant, split_kernel=kern, **kw))
     f64, _ = mra.apply(op, tree, mra.make_opts(**kw))
     cmp = mra.compare(sp, f64)
     assert cmp["n_only_test"] == 0 and cmp["n_only_ref"] == 0
@@ -119,6 +121,27 @@ def test_split_full_size_vs_fp64_and_oracle(mra, tile_variant):
     pos = np.searchsorted(gk, ref.keys)
     assert (gk[pos] == ref.keys).all()
     assert rel_l2(gc[pos], ref.coeffs) <= TOL_MIXED
+
+
+@pytest.mark.parametrize("k", [4, 6, 8, 10])
+def test_source_stationary_with_wide_operator_and_two_shells(mra, k):
+    """Records up to |l|_inf = 2 (two windows of three lz, the second cut by the cell) from an
+    operator whose blocks reach |l| = 3 (seven blocks per term: stage-3 blocks copied piece by
+    piece), shells with the norm screen: the source-stationary kernel equals the oracle and agrees
+    with the destination-stationary kernel."""
+    keys, coeffs = W.random_tree_coeffs({4: 200, 6: 120, 8: 70, 10: 40}[k], k, 3, seed=50 + k)
+    op = mra.Operator(1, 20, k, 16.0, 0, 3, max_disp=3, mu=0.7, fit_eps=1e-6)
+    fit = oracle_fit(op)
+    ref = O.apply(keys, coeffs, fit["c"], fit["t"], 16.0, stencil=0, max_disp=2, tau=1e-9)
+    tree = mra.Tree.from_host(keys, coeffs, 16.0)
+    kw = dict(stencil=mra.STENCIL_SHELLS, max_disp=2, screen=mra.SCREEN_NORM, tau=1e-9)
+    src, st = mra.apply(op, tree, split_opts(mra, **kw))
+    dst, _ = mra.apply(op, tree, split_opts(mra, split_kernel=mra.SPLIT_DEST, **kw))
+    gk, gc = src.host()
+    assert st["terms_kept"] == ref.terms
+    assert (gk == ref.keys).all()
+    assert rel_l2(gc, ref.coeffs) <= TOL_MIXED
+    assert mra.compare(src, dst)["rel_l2"] <= TOL_MIXED
 
 
 def test_split_two_pieces_is_coarser(mra):
