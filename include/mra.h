@@ -177,8 +177,8 @@ long long mra_launch_count(void);
  * allocations still in flight on a stream is not affected. */
 int mra_release_memory(void);
 
-/* Test hook for the failure path: the next MRA_PREC_SPLIT_BF16 apply in this process has its
- * first CTA skip the block copies of its first term, so that the kernel's bounded waits on them
+/* Test hook for the failure path: the next MRA_PREC_SPLIT_BF16 apply in this process has one
+ * CTA (the one that takes the first tile) skip the block copies of its first term, so that the kernel's bounded waits on them
  * run out (about two seconds each); that apply returns MRA_ERR_TIMEOUT with the device context
  * intact, and later calls run normally.  One-shot; nothing else is changed. */
 int mra_debug_inject_stall(void);

@@ -79,7 +79,7 @@ struct SrcArgs {
   int *tile_ctr;                // next tile (zero before the launch)
   float *partial;               // [n_rec][k^3]
   int *err;
-  int inject_stall;             // test hook: CTA 0 never issues the block copies of its first term
+  int inject_stall;             // test hook: the CTA that takes tile 0 never issues the copies of its first term
   int64_t n_src, n_rec, n_blocks;
 };
 
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
     int it = 0;       // terms issued by this CTA so far (all tiles)
     int nfetch = 0;   // block copies issued (thread 32), for iterations 0 .. nfetch-1 in order
     bool bad = false;
-    bool stalled = a.inject_stall && blockIdx.x == 0;
+    bool stalled = false;  // test hook: set for the CTA that takes tile 0
     // the tile's iteration cursor of thread 32 (copies AHEAD terms ahead): group and the terms left
     int f_g = 0;
     uint64_t f_u0 = 0, f_u1 = 0;
@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
       wg_sync(1);
       const int tile = s_tile;
       if (tile >= *a.n_tiles) break;
+      if (a.inject_stall && tile == 0 && nfetch == 0) stalled = true;
       if (tid < G) t_src[tid] = a.tile_src[(int64_t)tile * G + tid];
       for (int e = tid; e < SRC_NG * G * 3; e += 128) {
         grp_rec[e] = -1;
