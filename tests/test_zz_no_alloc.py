@@ -54,22 +54,31 @@ def test_noalloc_norm_matches_norm_on_two_calls_in_a_row(mra):
 
 def test_noalloc_norm_allocates_nothing(mra):
     """After a first call, further calls leave the device's free memory and torch's reserved
-    memory unchanged: the scratch is the library's fixed array, nothing is allocated."""
+    memory unchanged: the scratch is the library's fixed array, nothing is allocated.  Python's
+    garbage collector is run first and held off while measuring, so that objects of earlier
+    tests (a graph frees its buffers when collected) cannot change the free memory meanwhile."""
+    import gc
     import torch
     keys, coeffs = W.random_tree_coeffs(500, 8, 4, seed=5)
     tree = mra.Tree.from_host(keys, coeffs, 8.0)
     per = torch.empty(500, dtype=torch.float64, device="cuda")
     _call(mra, tree, per)
+    gc.collect()
     torch.cuda.synchronize()
-    free0, _ = torch.cuda.mem_get_info()
-    res0 = torch.cuda.memory_reserved()
-    for _ in range(3):
-        _call(mra, tree, per)
-        _call(mra, tree, None)
-    torch.cuda.synchronize()
-    free1, _ = torch.cuda.mem_get_info()
+    gc.disable()
+    try:
+        free0, _ = torch.cuda.mem_get_info()
+        res0 = torch.cuda.memory_reserved()
+        for _ in range(3):
+            _call(mra, tree, per)
+            _call(mra, tree, None)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        res1 = torch.cuda.memory_reserved()
+    finally:
+        gc.enable()
     assert free1 == free0
-    assert torch.cuda.memory_reserved() == res0
+    assert res1 == res0
 
 
 def test_noalloc_norm_without_per_box_and_empty_tree(mra):
