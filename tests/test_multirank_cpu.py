@@ -193,3 +193,89 @@ def test_exchange_fails_loudly_when_a_rank_is_lost():
     for r in range(world - 1):
         assert res[r][1] != "completed", res[r]
         assert res[r][2] < 60.0
+
+
+# ----------------------------------------------------------------- halo-only exchange
+
+def _halo_rank(rank, world, port, q):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1507_01888_gb300 import partition as PT
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        keys, coeffs = W.random_tree_coeffs(400, 3, 4, seed=9)
+        weights = 1.0 + (keys >> np.uint64(57)).astype(float) ** 2  # uneven work per box
+        ranges = PT.split_ranges(keys, world, weights)
+        plan = PT.HaloPlan(keys, ranges, rank, 1)
+        own = torch.from_numpy(coeffs[plan.own].copy())
+        got = plan.exchange(own)
+        q.put((rank, plan.halo_keys.copy(), got.numpy().copy(), plan.n_received, plan.n_sent, plan.n_halo))
+    finally:
+        dist.destroy_process_group()
+
+
+def _run_ranks(target, world):
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=target, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = {}
+    for _ in range(world):
+        r = q.get(timeout=120)
+        res[r[0]] = r
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    return res
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_halo_exchange_gives_each_rank_exactly_its_halo(world):
+    """gloo ranks cut the key space by work; one all-to-all leaves each rank with exactly the
+    boxes within |l|_inf <= 1 of its destination range (brute-force halo), in key order, and it
+    received only the halo boxes other ranks own (less than the whole tree minus its own part)."""
+    import numpy as np
+    from paper_1507_01888_gb300 import partition as PT
+    res = _run_ranks(_halo_rank, world)
+    keys, coeffs = W.random_tree_coeffs(400, 3, 4, seed=9)
+    weights = 1.0 + (keys >> np.uint64(57)).astype(float) ** 2
+    ranges = PT.split_ranges(keys, world, weights)
+    sent = recv = 0
+    for r in range(world):
+        _, hk, hc, n_recv, n_sent, n_halo = res[r]
+        want = PT.halo_mask(keys, *ranges[r], 1)
+        assert (hk == keys[want]).all() and np.array_equal(hc, coeffs[want])
+        own = PT.in_range(keys, *ranges[r])
+        assert n_recv == int((want & ~own).sum()) < len(keys) - int(own.sum())
+        sent += n_sent
+        recv += n_recv
+    assert sent == recv
+
+
+def test_halo_shrinks_as_ranges_narrow_and_weights_balance_work():
+    """Without communication: the largest per-rank halo (and so the bytes a rank receives and
+    holds) shrinks as the number of ranks grows, and work-weighted ranges balance the weight
+    where box-count ranges do not."""
+    import numpy as np
+    from paper_1507_01888_gb300 import partition as PT
+    keys = np.unique(np.concatenate([W.random_tree_coeffs(150, 3, 3, seed=13)[0],
+                                     W.random_tree_coeffs(450, 3, 5, seed=14)[0]]))
+    lv = (keys >> np.uint64(57)).astype(int)
+    halos = []
+    for world in (1, 2, 4):
+        ranges = PT.split_ranges(keys, world)
+        halos.append(max(PT.HaloPlan(keys, ranges, r, 1).n_halo for r in range(world)))
+    assert halos[0] == len(keys) and halos[0] > halos[1] > halos[2]
+    w = PT.level_weights(keys, np.bincount(lv, minlength=20), np.bincount(lv, weights=10.0 ** lv, minlength=20))
+    by_count = PT.split_ranges(keys, 4)
+    by_work = PT.split_ranges(keys, 4, w)
+    def spread(ranges):
+        loads = [w[PT.in_range(keys, lo, hi)].sum() for lo, hi in ranges]
+        return max(loads) / (sum(loads) / len(loads))
+    assert spread(by_work) < spread(by_count)
