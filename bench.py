@@ -548,9 +548,11 @@ def run_post(args, w, rank, world):
 
 def run_partitioned(args, w, rank, world, local):
     """One function over N ranks by destination key ranges (owner computes).  Each rank holds
-    its key range of the input tree; a step is the all-gather of the parts (NCCL) and the
-    rank's apply on its halo of sources with its destination range.  value = the function's
-    boxes / the slowest rank's step time (strong scaling: the total work is fixed)."""
+    its key range of the input tree; the ranges are cut by work (the kept terms per source box of
+    each level, from one untimed apply).  A step is one halo exchange (partition.HaloPlan: an
+    all-to-all in which each rank receives exactly the boxes other ranks own in its halo) and
+    the rank's apply on its halo with its destination range.  value = the function's boxes / the
+    slowest rank's step time (strong scaling: the total work is fixed)."""
     import torch
     import torch.distributed as dist
     from paper_1507_01888_gb300 import mra, partition as PT
@@ -560,26 +562,29 @@ def run_partitioned(args, w, rank, world, local):
                        uniform_level=w.uniform_level)
     keys_h, coeffs_h = tree.host()
     lv = (keys_h >> np.uint64(57)).astype(int)
-    lo, hi = PT.split_ranges(keys_h, world)[rank]
-    own = PT.in_range(keys_h, lo, hi)
-    halo_idx = torch.from_numpy(np.nonzero(PT.halo_mask(keys_h, lo, hi, w.max_disp))[0]).to(dev)
-    local_keys = tree.keys[: tree.n][torch.from_numpy(own).to(dev)].contiguous()
-    local_coeffs = tree.coeffs[: tree.n][torch.from_numpy(own).to(dev)].contiguous()
     op = mra.Operator(w.kernel, w.M, w.k, w.L, int(lv.min()), int(lv.max()), max_disp=w.max_disp, mu=w.mu,
                       fit_eps=w.fit_eps)
     screen = mra.SCREEN_NORM if w.tau > 0 else mra.SCREEN_NONE
-    opts = mra.make_opts(precision=prec, pieces=args.pieces, screen=screen, tau=w.tau, stencil=w.stencil,
-                         max_disp=w.max_disp, tile_variant=2 if prec == mra.PREC_SPLIT_BF16 and 4 <= w.k <= 10 else 0,
-                         dest_range=(lo, hi))
-    sub = mra.Tree(tree.keys[halo_idx].contiguous(), tree.coeffs[halo_idx].contiguous(), int(halo_idx.numel()),
-                   w.k, w.L)
+    base = dict(precision=prec, pieces=args.pieces, screen=screen, tau=w.tau, stencil=w.stencil,
+                max_disp=w.max_disp, tile_variant=2 if prec == mra.PREC_SPLIT_BF16 and 4 <= w.k <= 10 else 0)
+    _, st_all = mra.apply(op, tree, mra.make_opts(**base))  # per-level work, for the ranges
+    lev = st_all["levels"]
+    weights = PT.level_weights(keys_h, [lev.get(n, {}).get("sources", 0) for n in range(20)],
+                               [lev.get(n, {}).get("terms_kept", 0) for n in range(20)])
+    ranges = PT.split_ranges(keys_h, world, weights)
+    lo, hi = ranges[rank]
+    D = 1 if w.stencil == 1 else w.max_disp
+    plan = PT.HaloPlan(keys_h, ranges, rank, D)
+    local_coeffs = torch.from_numpy(coeffs_h[plan.own].copy()).to(dev)
+    opts = mra.make_opts(**base, dest_range=(lo, hi))
+    sub = mra.Tree(torch.from_numpy(plan.halo_keys.view(np.int64).copy()).to(dev),
+                   torch.empty((plan.n_halo, w.k, w.k, w.k), dtype=torch.float64, device=dev), plan.n_halo, w.k, w.L)
     ap = mra.Applier(op, sub, opts)
     stream = torch.cuda.current_stream()
+    del tree
 
     def step():
-        keys_all, coeffs_all = PT.exchange(local_keys, local_coeffs)
-        torch.index_select(keys_all, 0, halo_idx, out=sub.keys)
-        torch.index_select(coeffs_all, 0, halo_idx, out=sub.coeffs)
+        plan.exchange(local_coeffs, out=sub.coeffs)
         ap(sub, stream)
 
     for _ in range(args.warmup):
@@ -613,15 +618,16 @@ def run_partitioned(args, w, rank, world, local):
     achieved = terms.item() * (6 * k ** 4 + k ** 3) / (kmax.item() / 1e3) / 1e12
     peak = pk.get("bf16_tflops", 1856.3) * world if prec == mra.PREC_SPLIT_BF16 else \
         fp64_peak(local)["dfma_tflops"] * world
-    line = {"metric": METRIC, "value": tree.n / (ms / 1e3), "unit": "boxes/s", "n_gpus": world,
+    line = {"metric": METRIC, "value": len(keys_h) / (ms / 1e3), "unit": "boxes/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None,
             "dtype": "f64" if prec == mra.PREC_FP64 else split_dtype(args.pieces),
             "data": "synthetic",
-            "config": workload_config(w), "run": {"n_boxes": tree.n, "k": k, "M": w.M,
-                       "parallelism": f"{world} ranks, destination key ranges (owner computes), "
-                                      f"{args.dist_backend} all-gather of the input parts every step",
-                       "l2": "inputs gathered anew every step"},
+            "config": workload_config(w), "run": {"n_boxes": len(keys_h), "k": k, "M": w.M,
+                       "parallelism": f"{world} ranks, destination key ranges cut by work (owner computes), "
+                                      f"{args.dist_backend} all-to-all of each rank's halo every step",
+                       "halo_boxes_this_rank": plan.n_halo, "received_boxes_this_rank": plan.n_received,
+                       "own_boxes_this_rank": int(plan.own.sum())},
             "roofline": {"bound": "tensor" if prec == mra.PREC_SPLIT_BF16 else "alu", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                          "kernel": "apply kernel, slowest rank", "peak_source": f"{world} x per-GPU peak, {pk_kind}"},

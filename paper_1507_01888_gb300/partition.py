@@ -153,7 +153,12 @@ class HaloPlan:
         in_split = [len(self.send_idx[r]) * width for r in range(self.world)]
         out_split = [self.recv_counts[s] * width for s in range(self.world)]
         in_split[self.rank] = out_split[self.rank] = 0
-        dist.all_to_all_single(rbuf.reshape(-1), sbuf.reshape(-1), out_split, in_split, group=group)
+        if dev.type != "cpu" and dist.get_backend(group) == "gloo":  # gloo moves host memory only
+            rhost = torch.empty(rbuf.shape, dtype=rbuf.dtype)
+            dist.all_to_all_single(rhost.reshape(-1), sbuf.cpu().reshape(-1), out_split, in_split, group=group)
+            rbuf.copy_(rhost)
+        else:
+            dist.all_to_all_single(rbuf.reshape(-1), sbuf.reshape(-1), out_split, in_split, group=group)
         res = out if out is not None else torch.empty((self.n_halo, width), dtype=flat.dtype, device=dev)
         res = res.reshape(self.n_halo, width)
         res.index_copy_(0, place[self.rank], flat.index_select(0, send_idx[self.rank]))
