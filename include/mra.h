@@ -124,10 +124,19 @@ typedef struct {
                        where it applies (even k from 4 to 10, records with |l|_inf <= 2) and the
                        destination-stationary one elsewhere; MRA_SPLIT_DEST (1) always the
                        destination-stationary one (tile_variant picks its shape) */
+  int join;  /* source-stationary kernel, one source per tile (k >= 9 here: k = 10): consecutive
+                terms of a record group with the same kept records are summed in the tensor-memory
+                accumulator, up to `join` of them (1..8), before one flush adds them into the record
+                sums; 0 = 2.  More terms per flush cost accuracy (the accumulator truncates) */
+  int sums;  /* source-stationary kernel: MRA_SUMS_COMPENSATED (0, FP32 sum + Kahan correction) or
+                MRA_SUMS_PLAIN (1, FP32 sum) for each record's sum over terms */
+  int ahead; /* source-stationary kernel: block copies run this many terms ahead (1..4; 0 = 2) */
 } mra_apply_opts;
 
 #define MRA_SPLIT_AUTO 0
 #define MRA_SPLIT_DEST 1
+#define MRA_SUMS_COMPENSATED 0
+#define MRA_SUMS_PLAIN 1
 
 typedef struct {
   int64_t n_in;               /* source boxes */

@@ -44,8 +44,9 @@ namespace {
 using namespace split;
 
 constexpr int SRC_THREADS = 256;
-constexpr int SRC_NB = 4;                          // block buffers (terms whose blocks are in shared memory)
-constexpr int SRC_AHEAD = SRC_NB - 2;              // how many terms ahead the block copies run
+constexpr int SRC_NB = 6;                          // block buffers (terms whose blocks are in shared memory)
+constexpr int SRC_MAX_AHEAD = SRC_NB - 2;          // the block copies run up to this many terms ahead
+constexpr int SRC_MAX_JOIN = 8;                    // most terms summed in tensor memory per flush
 constexpr int SRC_RING = 4;                        // term-info ring from warpgroup 0 to 1
 constexpr int SRC_MAX_G = 8;                       // sources per tile
 constexpr int SRC_MAX_DAP = 2;                     // largest |l|_inf of the records (else the other kernel)
@@ -80,6 +81,9 @@ struct SrcArgs {
   float *partial;               // [n_rec][k^3]
   int *err;
   int inject_stall;             // test hook: the CTA that takes tile 0 never issues the copies of its first term
+  int join;                     // terms summed in D3 by the stage-3 MMAs before one flush (one-source tiles)
+  int compensated;              // record sums: 1 = FP32 sum + Kahan correction, 0 = plain FP32 sum
+  int ahead;                    // block copies run this many terms ahead (1 .. SRC_MAX_AHEAD)
   int64_t n_src, n_rec, n_blocks;
 };
 
@@ -146,10 +150,11 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
     return tc::smem_desc(tc::smem_u32(A + p * TILE_BYTES), 128, MG_BYTES);
   };
   auto bdesc = [&](const unsigned char *B) { return tc::smem_desc(tc::smem_u32(B), 128, 256); };
-  // A piece p times B pieces 0..P-1-p (stacked along N, nb blocks per piece) into column groups p..P-1
-  auto issue_stacked = [&](uint32_t d, const unsigned char *A, const unsigned char *B, int nb) {
+  // A piece p times B pieces 0..P-1-p (stacked along N, nb blocks per piece) into column groups
+  // p..P-1; the first MMA overwrites D unless acc0
+  auto issue_stacked = [&](uint32_t d, const unsigned char *A, const unsigned char *B, int nb, uint32_t acc0) {
     for (int p = 0; p < P; ++p)
-      tc::mma_bf16(d + (uint32_t)(16 * nb * p), adesc(A, p), bdesc(B), idesc_n(nb * (P - p)), p > 0 ? 1u : 0u);
+      tc::mma_bf16(d + (uint32_t)(16 * nb * p), adesc(A, p), bdesc(B), idesc_n(nb * (P - p)), p > 0 ? 1u : acc0);
   };
   // store units of a thread's run: 16-byte core-matrix rows when 8 divides k, else 4-byte pairs
   constexpr int U = K % 8 == 0 ? K / 8 : K / 2;
@@ -209,6 +214,8 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
     for (int j = 0; j < K; ++j) v[j] += c[0][j];
   };
   const int mrow = quarter * 32 + lane;  // this thread's row of the tile (lane of tensor memory)
+  const int ahead = max(1, min(a.ahead, SRC_MAX_AHEAD));
+  const int join = G == 1 ? max(1, min(a.join, SRC_MAX_JOIN)) : 1;
 
   if (wg == 0) {
     // ======================================================= warpgroup 0
@@ -329,7 +336,7 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
         f_g = -1;
         f_u0 = f_u1 = 0ull;
         int m;
-        for (int j = 0; j < SRC_AHEAD; ++j) {
+        for (int j = 0; j < ahead; ++j) {
           int g0 = f_g;
           if (!cursor_next(f_g, f_u0, f_u1, m)) break;
           (void)g0;
@@ -378,7 +385,7 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
                                            &abort_flag);
           if (ok) {
             tc::fence_after_sync();
-            issue_stacked(tD1, A1, Bb + BX_OFF, 1);  // ---- stage 1: rows (i, jy, jz), contraction jx
+            issue_stacked(tD1, A1, Bb + BX_OFF, 1, 0u);  // ---- stage 1: rows (i, jy, jz), contraction jx
             tc::mma_commit(bs1);
           } else {
             abort_flag = 1;
@@ -386,7 +393,7 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
         }
         if (tid == 32) {
           int m2;
-          if (cursor_next(f_g, f_u0, f_u1, m2) && !fetch(it + SRC_AHEAD, f_g, m2)) abort_flag = 1;
+          if (cursor_next(f_g, f_u0, f_u1, m2) && !fetch(it + ahead, f_g, m2)) abort_flag = 1;
         }
         bool ok = true;
         if (quarter == 0) {
@@ -419,7 +426,7 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
           }
           if (ok2) {
             tc::fence_after_sync();
-            issue_stacked(tD2, A2, Bb + BY_OFF, 1);
+            issue_stacked(tD2, A2, Bb + BY_OFF, 1, 0u);
             tc::mma_commit(bs2);
           } else {
             abort_flag = 1;
@@ -483,12 +490,17 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
         float v[K];
         load_groups(tD3 + (uint32_t)(16 * w), 3, v);
         if (slot >= 0 && ((kp >> (3 * slot + w)) & 1u)) {
+          if (a.compensated) {
 #pragma unroll
-          for (int j = 0; j < K; ++j) {  // lo holds minus the running compensation
-            const float y = v[j] + lo[w][j];
-            const float s = hi[w][j] + y;
-            lo[w][j] = y - (s - hi[w][j]);
-            hi[w][j] = s;
+            for (int j = 0; j < K; ++j) {  // lo holds minus the running compensation
+              const float y = v[j] + lo[w][j];
+              const float s = hi[w][j] + y;
+              lo[w][j] = y - (s - hi[w][j]);
+              hi[w][j] = s;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < K; ++j) hi[w][j] += v[j];
           }
         }
       }
@@ -514,6 +526,7 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
     };
     uint32_t prev_keep = 0;
     int prev_flags = 0, prev_slot = 0;
+    int joined = 0;  // terms summed in D3 since its last flush
     int it = 0;
     for (;; ++it) {
       const int r = it % SRC_RING;
@@ -535,10 +548,13 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
       tc::fence_before_sync();
       wg_sync(2);
       if (tid == 128) mbar_arrive(bd2free);
-      // the previous pass's D3 into the record sums; a finished group is written out
-      if (it > 0) {
+      // the previous pass's D3 into the record sums and a finished group written out, unless this
+      // term's stage 3 joins it in D3 (same group, same records keeping it, room left)
+      const bool join_now = joined > 0 && joined < join && keep == prev_keep && !(prev_flags & FLAG_GROUP_END);
+      if (it > 0 && !join_now) {
         flush(prev_keep);
         if (prev_flags & FLAG_GROUP_END) write_group(ring_rec[prev_slot]);
+        joined = 0;
       }
       // stage-2 output -> stage-3 operand: element [jz][(i, ix, iy)]
       if (mrow < rows) store_units(a3_addr, v);
@@ -553,7 +569,7 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
         if (okb) {
           tc::fence_after_sync();
           // ---- stage 3: rows (i, ix, iy), contraction jz, B = c_m R_{m,lz} of the window's three lz
-          issue_stacked(tD3, A3, B3, 3);
+          issue_stacked(tD3, A3, B3, 3, join_now ? 1u : 0u);
           tc::mma_commit(bs3);
           tc::mma_commit(tc::smem_u32(&bar_bfree[b]));
         } else {
@@ -563,6 +579,7 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
       prev_keep = keep;
       prev_flags = flags;
       prev_slot = r;
+      ++joined;
     }
     if (!bad && it > 0) {
       bool ok = quarter != 0 || tc::mbar_wait_or_abort(bs3, (uint32_t)((it - 1) & 1), WAIT_CYCLES, &abort_flag);
@@ -733,6 +750,9 @@ int apply_src_run(const Operator &op, const mra_tree_view &in, const mra_apply_o
   a.partial = partial;
   a.err = err;
   a.inject_stall = take_injected_stall() ? 1 : 0;
+  a.join = o.join > 0 ? o.join : 2;
+  a.compensated = o.sums == MRA_SUMS_PLAIN ? 0 : 1;
+  a.ahead = o.ahead > 0 ? o.ahead : 2;
   a.n_src = n_in;
   a.n_rec = P;
   a.n_blocks = op.n_blocks;

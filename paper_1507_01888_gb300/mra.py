@@ -35,6 +35,8 @@ STENCIL_SHELLS = 0
 STENCIL_NEAREST = 1
 SPLIT_AUTO = 0
 SPLIT_DEST = 1
+SUMS_COMPENSATED = 0
+SUMS_PLAIN = 1
 
 EXPORTED = [
     "mra_last_error", "mra_version", "mra_project", "mra_operator_create", "mra_operator_fit",
@@ -73,7 +75,8 @@ class ApplyOpts(ctypes.Structure):
                 ("tau", ctypes.c_double), ("stencil", ctypes.c_int), ("max_disp", ctypes.c_int),
                 ("mlp", ctypes.c_void_p), ("delta", ctypes.c_double), ("tile_variant", ctypes.c_int),
                 ("delta_level", ctypes.c_void_p), ("dest_lo", ctypes.c_uint64), ("dest_hi", ctypes.c_uint64),
-                ("split_kernel", ctypes.c_int)]
+                ("split_kernel", ctypes.c_int), ("join", ctypes.c_int), ("sums", ctypes.c_int),
+                ("ahead", ctypes.c_int)]
 
 
 class ApplyStats(ctypes.Structure):
@@ -336,14 +339,16 @@ class NSOperator(Operator):
 
 def make_opts(precision=PREC_FP64, pieces=3, screen=SCREEN_NONE, tau=0.0, stencil=STENCIL_NEAREST,
               max_disp=1, mlp: torch.Tensor | None = None, delta: float = 0.0, tile_variant: int = 0,
-              delta_level=None, dest_range=None, split_kernel: int = 0) -> ApplyOpts:
+              delta_level=None, dest_range=None, split_kernel: int = 0, join: int = 0, sums: int = 0,
+              ahead: int = 0) -> ApplyOpts:
     """delta_level: optional per-source-level margins (MAX_LEVEL + 1 values; inf keeps every term
     of a level) replacing delta for the learned screen.  dest_range: (lo, hi) destination keys
     to compute (owner computes; hi exclusive), None for all.  split_kernel: SPLIT_AUTO (the
-    source-stationary kernel where it applies) or SPLIT_DEST (the destination-stationary one)."""
+    source-stationary kernel where it applies) or SPLIT_DEST (the destination-stationary one).
+    join, sums, ahead: the source-stationary kernel's knobs (see mra_apply_opts; 0 = defaults)."""
     lo, hi = (0, 0) if dest_range is None else (int(dest_range[0]), int(dest_range[1]))
     o = ApplyOpts(precision, pieces, screen, tau, stencil, max_disp, None, delta, tile_variant, None, lo, hi,
-                  split_kernel)
+                  split_kernel, join, sums, ahead)
     if mlp is not None:
         o.mlp = mlp.data_ptr()
         o._mlp_ref = mlp  # keep the tensor alive with the options
