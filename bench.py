@@ -345,7 +345,7 @@ def run_ns(args, w, rank, world):
     tuning = {}
     if prec == mra.PREC_SPLIT_BF16:
         opts, table = autotune.tune(op, tree, opts, make_applier=make)
-        tuning = {"tile_variant": opts.tile_variant, "candidates_ms": table}
+        tuning = {"choice": autotune.describe(opts), "candidates": table}
     ap = make(opts)
     ap(tree)
     torch.cuda.synchronize()
@@ -846,7 +846,7 @@ def main():
         def batched_applier(o):
             return mra.BatchedApplier(op, tree, offsets, o)
         opts, table = autotune.tune(op, tree, opts, make_applier=batched_applier if batched else None)
-        tuning = {"tile_variant": opts.tile_variant, "candidates_ms": table}
+        tuning = {"choice": autotune.describe(opts), "candidates": table}
 
     def make_applier(o):
         if batched:
