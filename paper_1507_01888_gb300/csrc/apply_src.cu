@@ -340,6 +340,19 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
       }
       return true;
     };
+    // stage 1 of iteration i (thread 0): its blocks landed, then three MMAs and a commit
+    auto issue_s1 = [&](int i, const unsigned char *Bb) {
+      bool ok = tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[i % SRC_NB]), (uint32_t)((i / SRC_NB) & 1), WAIT_CYCLES,
+                                       &abort_flag);
+      if (ok) {
+        tc::fence_after_sync();
+        issue_stacked(tD1, A1, Bb + BX_OFF, 1, 0u);  // ---- stage 1: rows (i, jy, jz), contraction jx
+        tc::mma_commit(bs1);
+      } else {
+        abort_flag = 1;
+      }
+    };
+    bool s1_ahead = false;  // stage 1 of the current term was issued at the end of the previous one
     // D3 of the previous term into the sums (once its stage 3 is done), its group written out if
     // it ended one, and D3 released for the next stage 3 -- unless the next term joins it in D3
     auto retire_prev = [&](bool join_next) -> bool {
@@ -454,18 +467,9 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
         // the same records, and D3 holds fewer than `join` terms
         const bool join_now = joined > 0 && joined < join && keep == prev_keep && !prev_end;
         // asynchronous issue is spread over three threads of different warps: thread 0
-        // stage 1, thread 32 the block copies AHEAD terms ahead, thread 64 stage 2
-        if (tid == 0) {
-          bool ok = tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[b]), (uint32_t)((it / SRC_NB) & 1), WAIT_CYCLES,
-                                           &abort_flag);
-          if (ok) {
-            tc::fence_after_sync();
-            issue_stacked(tD1, A1, Bb + BX_OFF, 1, 0u);  // ---- stage 1: rows (i, jy, jz), contraction jx
-            tc::mma_commit(bs1);
-          } else {
-            abort_flag = 1;
-          }
-        }
+        // stage 1 (issued ahead, at the end of the previous term, when that was of this tile),
+        // thread 32 the block copies AHEAD terms ahead, thread 64 stage 2
+        if (tid == 0 && !s1_ahead) issue_s1(it, Bb);
         if (tid == 32) {
           int m2;
           if (cursor_next(f_g, f_u0, f_u1, m2) && !fetch(it + ahead, f_g, m2)) abort_flag = 1;
@@ -502,6 +506,14 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
           } else {
             abort_flag = 1;
           }
+        }
+        // stage 1 of the next term of this tile now (D1 has been read), so that its MMAs run
+        // while the previous term's D3 is added into the sums
+        {
+          int ng = cg, nm = 0;
+          uint64_t nu0 = cu0, nu1 = cu1;
+          s1_ahead = cursor_next(ng, nu0, nu1, nm);
+          if (s1_ahead && tid == 0) issue_s1(it + 1, Bt + ((it + 1) % SRC_NB) * BIT_BYTES);
         }
         // the previous term's D3, while this term's stages 2 and 3 are on their way
         if (!retire_prev(join_now)) { bad = true; break; }

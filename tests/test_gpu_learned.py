@@ -144,3 +144,56 @@ def test_learned_screen_training_gain_and_error(mra):
                          mlp=model, delta=0.5, delta_level=[float("inf")] * 20)
     out, st = mra.apply(op, test_tree, none)
     assert st["terms_learned_skipped"] == 0 and np.array_equal(out.host()[1], pc)
+
+
+def test_learned_screen_gain_on_a_held_out_function(mra):
+    """What the trained network gains over the norm screen alone, on the operator of the
+    learned-screen workload (BSH mu = 0.5, M = 80, k = 10, tau = 1e-9, threshold 1e-7) and
+    functions of its family (4 Gaussians each, a ~ logU[1, 1e4]): trained on eight functions,
+    applied to a ninth it has not seen.  The learned screen must drop at least 2% of the terms
+    the norm screen keeps, the split apply with it must take less kernel time than without it,
+    and the FP64 apply with it must stay within the threshold of the oracle's norm-screened
+    result on a seeded sample of destinations."""
+    from paper_1507_01888_gb300 import learned
+    k, L, thresh, tau, M = 10, 32.0, 1e-7, 1e-9, 80
+    funcs = [W.gaussian_sum(4, 1.0, 1e4, seed=4100 + i) for i in range(8)] + [W.gaussian_sum(4, 1.0, 1e4, seed=4200)]
+    trees = [mra.project(f, k, L, thresh=thresh, init_level=2, max_level=19) for f in funcs]
+    top = max(int((t.host()[0] >> np.uint64(57)).max()) for t in trees)
+    op = mra.Operator(mra.BSH, M, k, L, 2, top, max_disp=1, mu=0.5, fit_eps=thresh)
+    norm = dict(screen=mra.SCREEN_NORM, tau=tau, stencil=mra.STENCIL_SHELLS, max_disp=1)
+    model, info = learned.train_screen(op, trees[:8], mra.make_opts(**norm), terms_per_tree=20000, steps=2000,
+                                       batch=1024, lr=3e-3, seed=0, quantile=1.0)
+    test = trees[8]
+    lrn = dict(norm, screen=mra.SCREEN_LEARNED, mlp=model, delta=info["delta"], delta_level=info["delta_level"])
+
+    def best_ms(opts):
+        ap = mra.Applier(op, test, opts)
+        ap(test)
+        ms = []
+        for _ in range(5):
+            ap(test)
+            ms.append(ap.stats.kernel_ms)
+        return min(ms), ap.stats.as_dict()
+
+    ms_norm, st_norm = best_ms(mra.make_opts(precision=mra.PREC_SPLIT_BF16, **norm))
+    ms_lrn, st_lrn = best_ms(mra.make_opts(precision=mra.PREC_SPLIT_BF16, **lrn))
+    frac = st_lrn["terms_learned_skipped"] / st_norm["terms_kept"]
+    print(f"learned screen on a held-out function ({test.n} boxes): drops {frac:.1%} of the "
+          f"{st_norm['terms_kept']} kept terms; split kernel {ms_norm:.2f} -> {ms_lrn:.2f} ms")
+    assert st_lrn["terms_kept"] + st_lrn["terms_learned_skipped"] == st_norm["terms_kept"]
+    assert frac >= 0.02
+    assert ms_lrn < ms_norm
+    # the error it adds, judged in FP64 against the oracle's plain (norm-screened) apply
+    out, _ = mra.apply(op, test, mra.make_opts(**lrn))
+    gk, gc = out.host()
+    ok, oc = test.host()
+    r_lo, r_hi = O.kernel_range(1, 0.5, L, thresh)
+    _, _, _, c, t = O.fit_search(0.5, M, r_lo, r_hi)
+    rng = np.random.default_rng(17)
+    sample = np.sort(rng.choice(gk, 40, replace=False))
+    ref = O.apply(ok, oc, c, t, L, stencil=0, max_disp=1, tau=tau, sample_keys=sample)
+    pos = np.searchsorted(gk, ref.keys)
+    assert (gk[pos] == ref.keys).all()
+    err = float(np.sqrt(((gc[pos] - ref.coeffs) ** 2).sum() / (ref.coeffs ** 2).sum()))
+    print(f"FP64 apply with the learned screen vs the oracle: {err:.2e} (threshold {thresh:g})")
+    assert err <= thresh
