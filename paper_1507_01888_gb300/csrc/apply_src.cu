@@ -57,7 +57,7 @@ constexpr int BX_OFF = 0, BY_OFF = BSTAGE_BYTES, BZ_OFF = 2 * BSTAGE_BYTES;
 constexpr int BIT_BYTES = 2 * BSTAGE_BYTES + 3 * BSTAGE_BYTES;  // blocks x, y and the z window of one term
 constexpr uint32_t D1_COL = 0, D2_COL = 48, D3_COL = 96;          // tensor-memory columns (3 groups of 16,
 constexpr uint32_t SRC_TMEM_COLS = 256;                           // D3: 3 groups x 3 lz x 16)
-constexpr int FLAG_JOIN = 1, FLAG_TERM = 2;
+constexpr int FLAG_GROUP_END = 1, FLAG_TERM = 2;
 
 __host__ __device__ constexpr int src_g(int k) {
   return (128 / (k * k)) > SRC_MAX_G ? SRC_MAX_G : 128 / (k * k);
@@ -101,14 +101,15 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
   int *grp_rec = (int *)(Bt + SRC_NB * BIT_BYTES);                      // [SRC_NG][G][3]
   uint64_t *grp_mask = (uint64_t *)(grp_rec + SRC_NG * G * 3 + (SRC_NG * G * 3) % 2);  // [SRC_NG][G][3][2]
   uint64_t *grp_union = grp_mask + SRC_NG * G * 3 * 2;                  // [SRC_NG][2]
-  __shared__ __align__(8) uint64_t bar_s1, bar_s2, bar_s3, bar_ring, bar_d2free, bar_d3free, bar_drain0, bar_drain1,
-      bar_drain2;
+  __shared__ __align__(8) uint64_t bar_s1, bar_s2, bar_s3, bar_ring, bar_d2free, bar_drain0, bar_drain1, bar_drain2;
   __shared__ __align__(8) uint64_t bar_bb[SRC_NB], bar_bfree[SRC_NB];
   __shared__ uint32_t tmem_holder;
   __shared__ int t_src[SRC_MAX_G];
   __shared__ int s_tile, t_level, t_dap, t_dop;
   __shared__ long long t_lbase;
-  __shared__ int ring_flags[SRC_RING];
+  __shared__ int ring_m[SRC_RING], ring_flags[SRC_RING];
+  __shared__ uint32_t ring_keep[SRC_RING];
+  __shared__ int ring_rec[SRC_RING][SRC_MAX_G * 3];
   __shared__ volatile int abort_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -125,7 +126,6 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
     tc::mbar_init(tc::smem_u32(&bar_s3), 1);
     tc::mbar_init(tc::smem_u32(&bar_ring), 1);
     tc::mbar_init(tc::smem_u32(&bar_d2free), 1);
-    tc::mbar_init(tc::smem_u32(&bar_d3free), 1);
     tc::mbar_init(tc::smem_u32(&bar_drain0), 1);
     tc::mbar_init(tc::smem_u32(&bar_drain1), 1);
     tc::mbar_init(tc::smem_u32(&bar_drain2), 1);
@@ -219,8 +219,6 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
 
   if (wg == 0) {
     // ======================================================= warpgroup 0
-    // stages the sources, turns D1 into the stage-2 operand, adds D3 into the record sums and
-    // writes finished records; threads 0, 32 and 64 issue stage 1, the block copies and stage 2
     // where this thread's stage-1 output row (i, jy, jz) goes in the stage-2 operand:
     // element [jy][(i, jz, 0..k-1)]
     uint32_t a2_addr[U];
@@ -229,67 +227,11 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
       const int i = m1 / k2, rem = m1 - i * k2, jy = rem / K, jz = rem - jy * K;
       run_addrs(A2, i * k2 + jz * K, jy, a2_addr);
     }
-    const int slot = mrow < rows ? mrow / k2 : -1;
-    const int rem3 = mrow < rows ? mrow - slot * k2 : 0;  // (ix, iy) of this thread's stage-3 row
-    // per (lz in window, iz): the record sum over terms as FP32 hi + running compensation lo
-    float hi[3][K], lo[3][K];
-#pragma unroll
-    for (int w = 0; w < 3; ++w)
-#pragma unroll
-      for (int j = 0; j < K; ++j) hi[w][j] = lo[w][j] = 0.f;
-    // add D3 (the terms since the last flush, kept by the records `kp`) into the record sums
-    auto flush = [&](uint32_t kp) {
-#pragma unroll
-      for (int w = 0; w < 3; ++w) {
-        uint32_t any = 0;
-#pragma unroll
-        for (int i = 0; i < G; ++i) any |= (kp >> (3 * i + w)) & 1u;
-        if (!any) continue;  // uniform over the CTA: the tensor-memory loads are warp-collective
-        float v[K];
-        load_groups(tD3 + (uint32_t)(16 * w), 3, v);
-        if (slot >= 0 && ((kp >> (3 * slot + w)) & 1u)) {
-          if (a.compensated) {
-#pragma unroll
-            for (int j = 0; j < K; ++j) {  // lo holds minus the running compensation
-              const float y = v[j] + lo[w][j];
-              const float s = hi[w][j] + y;
-              lo[w][j] = y - (s - hi[w][j]);
-              hi[w][j] = s;
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < K; ++j) hi[w][j] += v[j];
-          }
-        }
-      }
-    };
-    // the sums of a finished group (records rec[0..2] of this thread's slot) to the partial
-    // buffer as FP32, then cleared
-    auto write_group = [&](const int *rec) {
-#pragma unroll
-      for (int w = 0; w < 3; ++w) {
-        const int p = rec[w];
-        if (slot >= 0 && p >= 0) {
-          float *o = a.partial + (int64_t)MRA_IDX(p, a.n_rec) * k3 + (int64_t)rem3 * K;
-#pragma unroll
-          for (int j = 0; j < K; j += 2)
-            *(float2 *)(o + j) = make_float2(hi[w][j] + lo[w][j], hi[w][j + 1] + lo[w][j + 1]);
-        }
-#pragma unroll
-        for (int j = 0; j < K; ++j) hi[w][j] = lo[w][j] = 0.f;
-      }
-    };
     uint32_t p1 = 0;
     int it = 0;       // terms issued by this CTA so far (all tiles)
     int nfetch = 0;   // block copies issued (thread 32), for iterations 0 .. nfetch-1 in order
     bool bad = false;
     bool stalled = false;  // test hook: set for the CTA that takes tile 0
-    // the previous term: its kept records, whether it ended its group, the group's records of
-    // this thread's slot, and how many terms D3 holds since its last flush
-    uint32_t prev_keep = 0;
-    bool prev_end = false;
-    int prev_rec[3] = {-1, -1, -1};
-    int joined = 0;
     // the tile's iteration cursor of thread 32 (copies AHEAD terms ahead): group and the terms left
     int f_g = 0;
     uint64_t f_u0 = 0, f_u1 = 0;
@@ -338,35 +280,6 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
           tc::bulk_g2s(tc::smem_u32(Bb + BZ_OFF + q * BSTAGE_BYTES + (lzf - lz0) * BPIECE_BYTES),
                        z0 + ((int64_t)q * nl + lzf + dop) * BPIECE_BYTES, (uint32_t)(cnt * BPIECE_BYTES), bar);
       }
-      return true;
-    };
-    // stage 1 of iteration i (thread 0): its blocks landed, then three MMAs and a commit
-    auto issue_s1 = [&](int i, const unsigned char *Bb) {
-      bool ok = tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[i % SRC_NB]), (uint32_t)((i / SRC_NB) & 1), WAIT_CYCLES,
-                                       &abort_flag);
-      if (ok) {
-        tc::fence_after_sync();
-        issue_stacked(tD1, A1, Bb + BX_OFF, 1, 0u);  // ---- stage 1: rows (i, jy, jz), contraction jx
-        tc::mma_commit(bs1);
-      } else {
-        abort_flag = 1;
-      }
-    };
-    bool s1_ahead = false;  // stage 1 of the current term was issued at the end of the previous one
-    // D3 of the previous term into the sums (once its stage 3 is done), its group written out if
-    // it ended one, and D3 released for the next stage 3 -- unless the next term joins it in D3
-    auto retire_prev = [&](bool join_next) -> bool {
-      if (it > 0 && !join_next) {
-        bool ok = quarter != 0 || tc::mbar_wait_or_abort(bs3, (uint32_t)((it - 1) & 1), WAIT_CYCLES, &abort_flag);
-        if (wg_vote_or(1, !ok || abort_flag)) return false;
-        tc::fence_after_sync();
-        flush(prev_keep);
-        if (prev_end) write_group(prev_rec);
-        joined = 0;
-        tc::fence_before_sync();
-      }
-      wg_sync(1);
-      if (tid == 0 && it > 0) mbar_arrive(tc::smem_u32(&bar_d3free));
       return true;
     };
 
@@ -424,7 +337,9 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
         f_u0 = f_u1 = 0ull;
         int m;
         for (int j = 0; j < ahead; ++j) {
+          int g0 = f_g;
           if (!cursor_next(f_g, f_u0, f_u1, m)) break;
+          (void)g0;
           if (!fetch(it + j, f_g, m)) abort_flag = 1;
         }
       }
@@ -463,13 +378,19 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
             const int e = (g * G + i) * 3 + w;
             keep |= (uint32_t)((grp_mask[2 * e + (m >> 6)] >> (m & 63)) & 1ull) << (3 * i + w);
           }
-        // this term's stage 3 adds onto D3 when the previous term was of the same group, kept by
-        // the same records, and D3 holds fewer than `join` terms
-        const bool join_now = joined > 0 && joined < join && keep == prev_keep && !prev_end;
         // asynchronous issue is spread over three threads of different warps: thread 0
-        // stage 1 (issued ahead, at the end of the previous term, when that was of this tile),
-        // thread 32 the block copies AHEAD terms ahead, thread 64 stage 2
-        if (tid == 0 && !s1_ahead) issue_s1(it, Bb);
+        // stage 1, thread 32 the block copies AHEAD terms ahead, thread 64 stage 2
+        if (tid == 0) {
+          bool ok = tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[b]), (uint32_t)((it / SRC_NB) & 1), WAIT_CYCLES,
+                                           &abort_flag);
+          if (ok) {
+            tc::fence_after_sync();
+            issue_stacked(tD1, A1, Bb + BX_OFF, 1, 0u);  // ---- stage 1: rows (i, jy, jz), contraction jx
+            tc::mma_commit(bs1);
+          } else {
+            abort_flag = 1;
+          }
+        }
         if (tid == 32) {
           int m2;
           if (cursor_next(f_g, f_u0, f_u1, m2) && !fetch(it + ahead, f_g, m2)) abort_flag = 1;
@@ -494,7 +415,11 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
           bool ok2 = it == 0 || tc::mbar_wait_or_abort(bd2free, (uint32_t)((it - 1) & 1), WAIT_CYCLES, &abort_flag);
           if (ok2) {
             const int r = it % SRC_RING;
-            ring_flags[r] = join_now ? FLAG_JOIN : 0;
+            ring_m[r] = m;
+            ring_keep[r] = keep;
+            ring_flags[r] = group_end ? FLAG_GROUP_END : 0;
+            if (group_end)
+              for (int e = 0; e < G * 3; ++e) ring_rec[r][e] = grp_rec[g * G * 3 + e];
             mbar_arrive(bring);
             ok2 = tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[b]), (uint32_t)((it / SRC_NB) & 1), WAIT_CYCLES,
                                          &abort_flag);
@@ -507,27 +432,11 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
             abort_flag = 1;
           }
         }
-        // stage 1 of the next term of this tile now (D1 has been read), so that its MMAs run
-        // while the previous term's D3 is added into the sums
-        {
-          int ng = cg, nm = 0;
-          uint64_t nu0 = cu0, nu1 = cu1;
-          s1_ahead = cursor_next(ng, nu0, nu1, nm);
-          if (s1_ahead && tid == 0) issue_s1(it + 1, Bt + ((it + 1) % SRC_NB) * BIT_BYTES);
-        }
-        // the previous term's D3, while this term's stages 2 and 3 are on their way
-        if (!retire_prev(join_now)) { bad = true; break; }
-        prev_keep = keep;
-        prev_end = group_end;
-        if (group_end && slot >= 0)
-#pragma unroll
-          for (int w = 0; w < 3; ++w) prev_rec[w] = grp_rec[(g * G + slot) * 3 + w];
-        ++joined;
         ++it;
       }
+      // a thread that left the loop early by the vote has bad set
     }
-    // no more terms: tell warpgroup 1 (after it has read the last term's D2), then retire the
-    // last term's D3
+    // no more terms: tell warpgroup 1 (after it has read the last term's D2)
     if (!bad && tid == 64) {
       bool ok2 = it == 0 || tc::mbar_wait_or_abort(bd2free, (uint32_t)((it - 1) & 1), WAIT_CYCLES, &abort_flag);
       if (ok2) {
@@ -537,7 +446,6 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
         abort_flag = 1;
       }
     }
-    if (!bad && it > 0 && !retire_prev(false)) bad = true;
     if (bad) abort_flag = 1;
     // block copies still in flight (after an abort) land before the CTA exits, and every MMA an
     // issuing thread started is complete before the tensor memory is released
@@ -554,7 +462,6 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
     }
   } else {
     // ======================================================= warpgroup 1
-    // turns D2 into the stage-3 operand; thread 160 issues stage 3
     // where this thread's stage-2 output row (i, jz, ix) goes in the stage-3 operand:
     // element [jz][(i, ix, 0..k-1)]
     uint32_t a3_addr[U];
@@ -563,7 +470,63 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
       const int i = m2 / k2, rem = m2 - i * k2, jz = rem / K, ix = rem - jz * K;
       run_addrs(A3, i * k2 + ix * K, jz, a3_addr);
     }
+    const int slot = mrow < rows ? mrow / k2 : -1;
+    const int rem3 = mrow < rows ? mrow - slot * k2 : 0;  // (ix, iy) of this thread's stage-3 row
+    // per (lz in window, iz): the record sum over terms as FP32 hi + running compensation lo
+    float hi[3][K], lo[3][K];
+#pragma unroll
+    for (int w = 0; w < 3; ++w)
+#pragma unroll
+      for (int j = 0; j < K; ++j) hi[w][j] = lo[w][j] = 0.f;
     bool bad = false;
+    // add D3 (the terms of one pass, kept as `kp`) into this thread's record sums
+    auto flush = [&](uint32_t kp) {
+#pragma unroll
+      for (int w = 0; w < 3; ++w) {
+        uint32_t any = 0;
+#pragma unroll
+        for (int i = 0; i < G; ++i) any |= (kp >> (3 * i + w)) & 1u;
+        if (!any) continue;  // uniform over the CTA: the tensor-memory loads are warp-collective
+        float v[K];
+        load_groups(tD3 + (uint32_t)(16 * w), 3, v);
+        if (slot >= 0 && ((kp >> (3 * slot + w)) & 1u)) {
+          if (a.compensated) {
+#pragma unroll
+            for (int j = 0; j < K; ++j) {  // lo holds minus the running compensation
+              const float y = v[j] + lo[w][j];
+              const float s = hi[w][j] + y;
+              lo[w][j] = y - (s - hi[w][j]);
+              hi[w][j] = s;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < K; ++j) hi[w][j] += v[j];
+          }
+        }
+      }
+    };
+    // the record sums of a finished group to the partial buffer (FP32), then cleared
+    auto write_group = [&](const int *rec) {
+#pragma unroll
+      for (int w = 0; w < 3; ++w) {
+        const int p = slot >= 0 ? rec[3 * slot + w] : -1;
+        if (p >= 0) {
+          float *o = a.partial + (int64_t)MRA_IDX(p, a.n_rec) * k3 + (int64_t)rem3 * K;
+          if constexpr (K % 2 == 0) {
+#pragma unroll
+            for (int j = 0; j < K; j += 2) *(float2 *)(o + j) = make_float2(hi[w][j] + lo[w][j], hi[w][j + 1] + lo[w][j + 1]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < K; ++j) o[j] = hi[w][j] + lo[w][j];
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < K; ++j) hi[w][j] = lo[w][j] = 0.f;
+      }
+    };
+    uint32_t prev_keep = 0;
+    int prev_flags = 0, prev_slot = 0;
+    int joined = 0;  // terms summed in D3 since its last flush
     int it = 0;
     for (;; ++it) {
       const int r = it % SRC_RING;
@@ -572,19 +535,27 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
       if (wg_vote_or(2, !ok || abort_flag)) { bad = true; break; }
       const int flags = ring_flags[r];
       if (flags & FLAG_TERM) break;
-      // stage 2 of this term done (D2 holds it); stage 3 of the previous term done (A3 is free)
       if (quarter == 0) {
         ok = tc::mbar_wait_or_abort(bs2, (uint32_t)(it & 1), WAIT_CYCLES, &abort_flag);
         if (ok && it > 0) ok = tc::mbar_wait_or_abort(bs3, (uint32_t)((it - 1) & 1), WAIT_CYCLES, &abort_flag);
       }
       if (wg_vote_or(2, !ok || abort_flag)) { bad = true; break; }
       tc::fence_after_sync();
+      const uint32_t keep = ring_keep[r];
       // D2 -> registers, then D2 is released for the next term's stage 2
       float v[K];
       load_groups(tD2, 1, v);
       tc::fence_before_sync();
       wg_sync(2);
       if (tid == 128) mbar_arrive(bd2free);
+      // the previous pass's D3 into the record sums and a finished group written out, unless this
+      // term's stage 3 joins it in D3 (same group, same records keeping it, room left)
+      const bool join_now = joined > 0 && joined < join && keep == prev_keep && !(prev_flags & FLAG_GROUP_END);
+      if (it > 0 && !join_now) {
+        flush(prev_keep);
+        if (prev_flags & FLAG_GROUP_END) write_group(ring_rec[prev_slot]);
+        joined = 0;
+      }
       // stage-2 output -> stage-3 operand: element [jz][(i, ix, iy)]
       if (mrow < rows) store_units(a3_addr, v);
       tc::fence_proxy_async_smem();
@@ -593,20 +564,31 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
       if (tid == 160) {  // a thread of another warp than the polling one issues stage 3
         const int b = it % SRC_NB;
         const unsigned char *B3 = Bt + b * BIT_BYTES + BZ_OFF;
-        // D3 retired by warpgroup 0 (or kept for this term to join), and the blocks landed
-        bool okb = it == 0 ||
-                   tc::mbar_wait_or_abort(tc::smem_u32(&bar_d3free), (uint32_t)((it - 1) & 1), WAIT_CYCLES, &abort_flag);
-        okb = okb && tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[b]), (uint32_t)((it / SRC_NB) & 1), WAIT_CYCLES,
-                                            &abort_flag);
+        bool okb = tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[b]), (uint32_t)((it / SRC_NB) & 1), WAIT_CYCLES,
+                                          &abort_flag);
         if (okb) {
           tc::fence_after_sync();
           // ---- stage 3: rows (i, ix, iy), contraction jz, B = c_m R_{m,lz} of the window's three lz
-          issue_stacked(tD3, A3, B3, 3, (flags & FLAG_JOIN) ? 1u : 0u);
+          issue_stacked(tD3, A3, B3, 3, join_now ? 1u : 0u);
           tc::mma_commit(bs3);
           tc::mma_commit(tc::smem_u32(&bar_bfree[b]));
         } else {
           abort_flag = 1;
         }
+      }
+      prev_keep = keep;
+      prev_flags = flags;
+      prev_slot = r;
+      ++joined;
+    }
+    if (!bad && it > 0) {
+      bool ok = quarter != 0 || tc::mbar_wait_or_abort(bs3, (uint32_t)((it - 1) & 1), WAIT_CYCLES, &abort_flag);
+      if (wg_vote_or(2, !ok || abort_flag)) {
+        bad = true;
+      } else {
+        tc::fence_after_sync();
+        flush(prev_keep);
+        if (prev_flags & FLAG_GROUP_END) write_group(ring_rec[prev_slot]);
       }
     }
     if (bad) abort_flag = 1;
