@@ -57,7 +57,7 @@ constexpr int BX_OFF = 0, BY_OFF = BSTAGE_BYTES, BZ_OFF = 2 * BSTAGE_BYTES;
 constexpr int BIT_BYTES = 2 * BSTAGE_BYTES + 3 * BSTAGE_BYTES;  // blocks x, y and the z window of one term
 constexpr uint32_t D1_COL = 0, D2_COL = 48, D3_COL = 96;          // tensor-memory columns (3 groups of 16,
 constexpr uint32_t SRC_TMEM_COLS = 256;                           // D3: 3 groups x 3 lz x 16)
-constexpr int FLAG_GROUP_END = 1, FLAG_TERM = 2;
+constexpr int FLAG_GROUP_END = 1, FLAG_TERM = 2, FLAG_JOIN = 4;
 
 __host__ __device__ constexpr int src_g(int k) {
   return (128 / (k * k)) > SRC_MAX_G ? SRC_MAX_G : 128 / (k * k);
@@ -87,8 +87,11 @@ struct SrcArgs {
   int64_t n_src, n_rec, n_blocks;
 };
 
-template <int K>
-__global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
+// PLAIN: record sums in plain FP32 (fewer registers), which leaves room for a ninth warp that issues
+// stage 3, so that warpgroup 1 does not wait on that issue; otherwise compensated sums and thread
+// 160 issues stage 3
+template <int K, bool PLAIN>
+__global__ void __launch_bounds__(PLAIN ? SRC_THREADS + 32 : SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
   constexpr int k2 = K * K, k3 = K * K * K;
   constexpr int G = src_g(K), rows = G * k2;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -101,7 +104,9 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
   int *grp_rec = (int *)(Bt + SRC_NB * BIT_BYTES);                      // [SRC_NG][G][3]
   uint64_t *grp_mask = (uint64_t *)(grp_rec + SRC_NG * G * 3 + (SRC_NG * G * 3) % 2);  // [SRC_NG][G][3][2]
   uint64_t *grp_union = grp_mask + SRC_NG * G * 3 * 2;                  // [SRC_NG][2]
-  __shared__ __align__(8) uint64_t bar_s1, bar_s2, bar_s3, bar_ring, bar_d2free, bar_drain0, bar_drain1, bar_drain2;
+  __shared__ __align__(8) uint64_t bar_s1, bar_s2, bar_s3, bar_ring, bar_d2free, bar_a3ready, bar_drain0, bar_drain1,
+      bar_drain2;
+  __shared__ int s3_flags[SRC_RING];  // from warpgroup 1 to the stage-3 issuer: join / no more terms
   __shared__ __align__(8) uint64_t bar_bb[SRC_NB], bar_bfree[SRC_NB];
   __shared__ uint32_t tmem_holder;
   __shared__ int t_src[SRC_MAX_G];
@@ -118,7 +123,7 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
   {  // zero the operand tiles once: contraction and row padding stay zero
     int4 *z = (int4 *)smem;
     const int n16 = (9 * TILE_BYTES) / 16;
-    for (int i = tid; i < n16; i += SRC_THREADS) z[i] = make_int4(0, 0, 0, 0);
+    for (int i = tid; i < n16; i += (int)blockDim.x) z[i] = make_int4(0, 0, 0, 0);
   }
   if (tid == 0) {
     tc::mbar_init(tc::smem_u32(&bar_s1), 1);
@@ -126,6 +131,7 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
     tc::mbar_init(tc::smem_u32(&bar_s3), 1);
     tc::mbar_init(tc::smem_u32(&bar_ring), 1);
     tc::mbar_init(tc::smem_u32(&bar_d2free), 1);
+    tc::mbar_init(tc::smem_u32(&bar_a3ready), 1);
     tc::mbar_init(tc::smem_u32(&bar_drain0), 1);
     tc::mbar_init(tc::smem_u32(&bar_drain1), 1);
     tc::mbar_init(tc::smem_u32(&bar_drain2), 1);
@@ -460,7 +466,7 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
       tc::mma_commit(bd);
       tc::mbar_wait(bd, 0, WAIT_CYCLES);
     }
-  } else {
+  } else if (wg == 1) {
     // ======================================================= warpgroup 1
     // where this thread's stage-2 output row (i, jz, ix) goes in the stage-3 operand:
     // element [jz][(i, ix, 0..k-1)]
@@ -490,7 +496,7 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
         float v[K];
         load_groups(tD3 + (uint32_t)(16 * w), 3, v);
         if (slot >= 0 && ((kp >> (3 * slot + w)) & 1u)) {
-          if (a.compensated) {
+          if constexpr (!PLAIN) {
 #pragma unroll
             for (int j = 0; j < K; ++j) {  // lo holds minus the running compensation
               const float y = v[j] + lo[w][j];
@@ -561,7 +567,12 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
       tc::fence_proxy_async_smem();
       tc::fence_before_sync();
       wg_sync(2);
-      if (tid == 160) {  // a thread of another warp than the polling one issues stage 3
+      if constexpr (PLAIN) {  // the stage-3 issuer warp takes it from here
+        if (tid == 128) {
+          s3_flags[it % SRC_RING] = join_now ? FLAG_JOIN : 0;
+          mbar_arrive(tc::smem_u32(&bar_a3ready));
+        }
+      } else if (tid == 160) {  // a thread of another warp than the polling one issues stage 3
         const int b = it % SRC_NB;
         const unsigned char *B3 = Bt + b * BIT_BYTES + BZ_OFF;
         bool okb = tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[b]), (uint32_t)((it / SRC_NB) & 1), WAIT_CYCLES,
@@ -592,10 +603,38 @@ __global__ void __launch_bounds__(SRC_THREADS, 2) apply_src_kernel(SrcArgs a) {
       }
     }
     if (bad) abort_flag = 1;
-    if (tid == 160) {
+    if constexpr (PLAIN) {
+      if (tid == 128) {  // no more terms for the stage-3 issuer
+        s3_flags[it % SRC_RING] = FLAG_TERM;
+        mbar_arrive(tc::smem_u32(&bar_a3ready));
+      }
+    } else if (tid == 160) {
       tc::mma_commit(tc::smem_u32(&bar_drain1));
       tc::mbar_wait(tc::smem_u32(&bar_drain1), 0, WAIT_CYCLES);
     }
+  } else if (PLAIN && tid == SRC_THREADS) {
+    // ======================================================= the stage-3 issuer (warp 8, one thread)
+    for (int it = 0;; ++it) {
+      if (!tc::mbar_wait_or_abort(tc::smem_u32(&bar_a3ready), (uint32_t)(it & 1), WAIT_CYCLES, &abort_flag)) {
+        abort_flag = 1;
+        break;
+      }
+      const int f = s3_flags[it % SRC_RING];
+      if (f & FLAG_TERM) break;
+      const int b = it % SRC_NB;
+      const unsigned char *B3 = Bt + b * BIT_BYTES + BZ_OFF;
+      if (!tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[b]), (uint32_t)((it / SRC_NB) & 1), WAIT_CYCLES, &abort_flag)) {
+        abort_flag = 1;
+        break;
+      }
+      tc::fence_after_sync();
+      // ---- stage 3: rows (i, ix, iy), contraction jz, B = c_m R_{m,lz} of the window's three lz
+      issue_stacked(tD3, A3, B3, 3, (f & FLAG_JOIN) ? 1u : 0u);
+      tc::mma_commit(bs3);
+      tc::mma_commit(tc::smem_u32(&bar_bfree[b]));
+    }
+    tc::mma_commit(tc::smem_u32(&bar_drain1));
+    tc::mbar_wait(tc::smem_u32(&bar_drain1), 0, WAIT_CYCLES);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -763,11 +802,16 @@ int apply_src_run(const Operator &op, const mra_tree_view &in, const mra_apply_o
   const size_t smem_floor = (size_t)233472 / (512 / SRC_TMEM_COLS + 1) + 16;
   if (smem < smem_floor) smem = smem_floor;
   void (*kern)(SrcArgs) = nullptr;
-  switch (k) {
-    case 4: kern = apply_src_kernel<4>; break;
-    case 6: kern = apply_src_kernel<6>; break;
-    case 8: kern = apply_src_kernel<8>; break;
-    default: kern = apply_src_kernel<10>; break;
+  const bool plain = !a.compensated;
+  switch (k * 2 + (plain ? 1 : 0)) {
+    case 8: kern = apply_src_kernel<4, false>; break;
+    case 9: kern = apply_src_kernel<4, true>; break;
+    case 12: kern = apply_src_kernel<6, false>; break;
+    case 13: kern = apply_src_kernel<6, true>; break;
+    case 16: kern = apply_src_kernel<8, false>; break;
+    case 17: kern = apply_src_kernel<8, true>; break;
+    case 21: kern = apply_src_kernel<10, true>; break;
+    default: kern = apply_src_kernel<10, false>; break;
   }
   MRA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   MRA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
@@ -778,7 +822,7 @@ int apply_src_run(const Operator &op, const mra_tree_view &in, const mra_apply_o
   // than sources
   const int64_t max_tiles = G == 1 ? n_in : n_in / G + MRA_MAX_LEVEL + 1;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)sms, max_tiles));
-  kern<<<counted(grid), SRC_THREADS, smem, s>>>(a);
+  kern<<<counted(grid), plain ? SRC_THREADS + 32 : SRC_THREADS, smem, s>>>(a);
   MRA_CUDA_TRY(cudaGetLastError());
   dest_sum_kernel<<<counted((unsigned)std::max<int64_t>(nd, 1)), 256, 0, s>>>(
       nd, k3, wk.seg, wk.perm, partial, wk.dest_key, out.keys, out.coeffs, P);

@@ -150,15 +150,15 @@ def test_learned_screen_gain_on_a_held_out_function(mra):
     """What the trained network gains over the norm screen alone, on the operator of the
     learned-screen workload (BSH mu = 0.5, M = 80, k = 10, tau = 1e-9, threshold 1e-7) and
     functions of its family (4 Gaussians each, a ~ logU[1, 1e4]): trained on eight functions; its
-    margin chosen on a ninth (the smallest extra margin whose change of the FP64 result stays
-    within half the threshold); judged on a tenth it has seen in neither role.  There the learned
+    margin chosen on two more (the smallest extra margin whose change of the FP64 result stays
+    within a quarter of the threshold on both); judged on another it has seen in neither role.  There the learned
     screen must drop at least 2% of the terms the norm screen keeps, the split apply with it must
     take less kernel time than without it, and the FP64 apply with it must stay within the
     threshold of the oracle's norm-screened result on a seeded sample of destinations."""
     import torch
     from paper_1507_01888_gb300 import learned
     k, L, thresh, tau, M = 10, 32.0, 1e-7, 1e-9, 80
-    seeds = [4100 + i for i in range(8)] + [4300, 4200]
+    seeds = [4100 + i for i in range(8)] + [4300, 4301, 4200]
     trees = [mra.project(W.gaussian_sum(4, 1.0, 1e4, seed=sd), k, L, thresh=thresh, init_level=2, max_level=19)
              for sd in seeds]
     top = max(int((t.host()[0] >> np.uint64(57)).max()) for t in trees)
@@ -172,16 +172,17 @@ def test_learned_screen_gain_on_a_held_out_function(mra):
         return mra.make_opts(precision=precision, mlp=model, delta=info["delta"] + extra, delta_level=dl,
                              **dict(norm, screen=mra.SCREEN_LEARNED))
 
-    val = trees[8]
-    vref, _ = mra.apply(op, val, mra.make_opts(**norm))
+    vals = trees[8:10]
+    vrefs = [mra.apply(op, v, mra.make_opts(**norm))[0] for v in vals]
     extra = None
-    for e in (0.0, 0.25, 0.5, 1.0, 1.5, 2.0):
-        out, _ = mra.apply(op, val, lopts(e))
-        if mra.compare(out, vref)["rel_l2"] <= 0.5 * thresh:
+    for e in (0.0, 0.25, 0.5, 1.0, 1.5, 2.0, 3.0):
+        errs = [mra.compare(mra.apply(op, v, lopts(e))[0], r)["rel_l2"] for v, r in zip(vals, vrefs)]
+        print(f"margin +{e}: validation errors {errs}")
+        if max(errs) <= 0.25 * thresh:
             extra = e
             break
     assert extra is not None
-    test = trees[9]
+    test = trees[10]
 
     def best_ms(opts):
         ap = mra.Applier(op, test, opts)
