@@ -39,10 +39,17 @@ import workloads as W  # noqa: E402
 SPLIT_TRAFFIC = {("bsh_m60_adaptive_k10", 2): 70.93e6 + 77.63e6}
 
 METRIC = "3D operator-apply boxes/s & % roofline, mixed vs FP64 GPU at 1e-6 rel L2"
-def split_dtype(pieces):
-    """What the split-precision apply computes in (the label of its JSON line)."""
-    return (f"bf16x{pieces}-split MMAs with f32 accumulation; Gaussian-term sums in compensated f32 "
-            f"(sum + Kahan correction); f64 per-destination sums")
+def split_dtype(pieces, opts=None, k=0):
+    """What the split-precision apply of order k computes in (the label of its JSON line)."""
+    from paper_1507_01888_gb300 import mra
+    if opts is not None and opts.split_kernel != mra.SPLIT_DEST and k in (4, 6, 8, 10):
+        sums = "compensated f32 (sum + Kahan correction)" if opts.sums == mra.SUMS_COMPENSATED else "plain f32"
+        join = max(int(opts.join), 1) if opts.join else 2
+        return (f"bf16x{pieces}-split MMAs with f32 accumulation in tensor memory (up to {join} Gaussian terms "
+                f"per accumulation); each (source, displacement) sum over terms in {sums}, stored as f32; "
+                f"f64 per-destination sums")
+    return (f"bf16x{pieces}-split MMAs with f32 accumulation; Gaussian-term and per-destination sums in "
+            f"compensated f32 (sum + Kahan correction), formed into f64 at the end")
 
 
 _FP64 = {}
@@ -423,7 +430,8 @@ def run_ns(args, w, rank, world):
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None, "kernel": "apply_split_kernel (all levels)", "peak_source": f"bf16 dense burst, {pk_kind}",
                 "kernel_ms": kms_mean, "flops": "algorithmic (6k'^4+k'^3 per term, k' = k or 2k)"}
-        dtype = split_dtype(args.pieces)
+        dtype = (f"order {k}: {split_dtype(args.pieces, opts, k)}; order {2 * k}: "
+                 f"{split_dtype(args.pieces, opts, 2 * k)}")
     line = {"metric": METRIC, "value": value, "unit": "boxes/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype, "data": "synthetic",
@@ -621,7 +629,7 @@ def run_partitioned(args, w, rank, world, local):
     line = {"metric": METRIC, "value": len(keys_h) / (ms / 1e3), "unit": "boxes/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None,
-            "dtype": "f64" if prec == mra.PREC_FP64 else split_dtype(args.pieces),
+            "dtype": "f64" if prec == mra.PREC_FP64 else split_dtype(args.pieces, opts, k),
             "data": "synthetic",
             "config": workload_config(w), "run": {"n_boxes": len(keys_h), "k": k, "M": w.M,
                        "parallelism": f"{world} ranks, destination key ranges cut by work (owner computes), "
@@ -1019,7 +1027,7 @@ def main():
             roof["issued"] = {"tflops": issued, "frac": issued / peak,
                               "note": "BF16 flops the MMAs issue (padding to 128x16x16 tiles and the six "
                                       "piece products included); context only, not the algorithmic rate"}
-        dtype = split_dtype(args.pieces)
+        dtype = split_dtype(args.pieces, opts, k)
 
     line = {"metric": METRIC, "value": value, "unit": "boxes/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

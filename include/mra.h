@@ -56,12 +56,16 @@ extern "C" {
 #define MRA_PREC_FP64 0       /* all arithmetic in FP64 */
 #define MRA_PREC_SPLIT_BF16 1 /* mode products as split-BF16 tcgen05 MMAs: every operand is
                                  split into `pieces` BF16 pieces and the piece products p + q <
-                                 pieces are accumulated in FP32 in tensor memory.  Gaussian-term
-                                 sums are compensated FP32 sums (a sum and its Kahan correction);
-                                 the per-destination sum is FP64.  Operator blocks, fit, norms and
-                                 screen stay FP64.  Measured error: about 1e-7 relative L2 against
-                                 MRA_PREC_FP64 with 3 pieces; use MRA_PREC_FP64 for thresholds
-                                 below that */
+                                 pieces are accumulated in FP32 in tensor memory.  Sums over
+                                 Gaussian terms: the source-stationary kernel (even k 4..10) sums
+                                 up to opts.join terms in the tensor-memory accumulator, then adds
+                                 them into each (source, displacement) sum in plain or compensated
+                                 FP32 (opts.sums), stored as FP32 and summed per destination in
+                                 FP64; the destination-stationary kernel keeps compensated FP32
+                                 sums per destination, formed into FP64 at the end.  Operator
+                                 blocks, fit, norms and screen stay FP64.  Measured error: 1.2e-7
+                                 to 1.8e-7 relative L2 against MRA_PREC_FP64 with 3 pieces; use
+                                 MRA_PREC_FP64 for thresholds below that */
 
 #define MRA_SCREEN_NONE 0 /* keep every term */
 #define MRA_SCREEN_NORM 1 /* keep a term iff |c| ||Rx|| ||Ry|| ||Rz|| ||s|| >= tau */
@@ -128,15 +132,16 @@ typedef struct {
                 terms of a record group with the same kept records are summed in the tensor-memory
                 accumulator, up to `join` of them (1..8), before one flush adds them into the record
                 sums; 0 = 2.  More terms per flush cost accuracy (the accumulator truncates) */
-  int sums;  /* source-stationary kernel: MRA_SUMS_COMPENSATED (0, FP32 sum + Kahan correction) or
-                MRA_SUMS_PLAIN (1, FP32 sum) for each record's sum over terms */
+  int sums;  /* source-stationary kernel, each record's sum over terms: MRA_SUMS_PLAIN (0, an FP32
+                sum; a ninth warp then issues stage 3) or MRA_SUMS_COMPENSATED (1, FP32 sum + Kahan
+                correction: more accurate, more registers, eight warps) */
   int ahead; /* source-stationary kernel: block copies run this many terms ahead (1..4; 0 = 2) */
 } mra_apply_opts;
 
 #define MRA_SPLIT_AUTO 0
 #define MRA_SPLIT_DEST 1
-#define MRA_SUMS_COMPENSATED 0
-#define MRA_SUMS_PLAIN 1
+#define MRA_SUMS_PLAIN 0
+#define MRA_SUMS_COMPENSATED 1
 
 typedef struct {
   int64_t n_in;               /* source boxes */

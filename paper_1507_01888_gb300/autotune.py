@@ -28,9 +28,10 @@ def candidates(k: int, src_ok: bool):
     if src_ok:
         for join in (1, 2, 3, 4):
             for sums in (mra.SUMS_COMPENSATED, mra.SUMS_PLAIN):
-                out.append((f"src join={join} sums={'comp' if sums == 0 else 'plain'}",
+                out.append((f"src join={join} sums={'comp' if sums == mra.SUMS_COMPENSATED else 'plain'}",
                             dict(split_kernel=mra.SPLIT_AUTO, join=join, sums=sums, ahead=2)))
-        out.append(("src join=2 sums=comp ahead=1", dict(split_kernel=mra.SPLIT_AUTO, join=2, sums=0, ahead=1)))
+        out.append(("src join=2 sums=plain ahead=1", dict(split_kernel=mra.SPLIT_AUTO, join=2, sums=mra.SUMS_PLAIN,
+                                                           ahead=1)))
     dest = [0, 1, 2] if 4 <= k <= 10 else ([0, 1] if k >= 12 else [0])
     out += [(f"dest tile_variant={v}", dict(split_kernel=mra.SPLIT_DEST, tile_variant=v)) for v in dest]
     return out
@@ -84,7 +85,7 @@ def tune(op, tree, opts, repeats: int = 3, verbose: bool = False, make_applier=N
             ap = make_applier(_with(opts, over))
             ms = _time(ap, tree, repeats)
             row = {"ms": ms}
-            if over.get("join", 1) > 1 or over.get("sums", 0) != 0:  # arithmetic changes: check accuracy
+            if over.get("split_kernel", 0) == mra.SPLIT_AUTO:  # arithmetic varies with the knobs: check accuracy
                 if ref is None:
                     ref_o = _with(opts, {"precision": mra.PREC_FP64})
                     ref = make_applier(ref_o)(tree)
@@ -103,5 +104,6 @@ def tune(op, tree, opts, repeats: int = 3, verbose: bool = False, make_applier=N
 def describe(opts) -> dict:
     """The schedule fields of apply options, for reports."""
     return {"split_kernel": "destination-stationary" if opts.split_kernel == mra.SPLIT_DEST else "auto",
-            "tile_variant": opts.tile_variant, "join": opts.join, "sums": "plain" if opts.sums else "compensated",
+            "tile_variant": opts.tile_variant, "join": opts.join,
+            "sums": "compensated" if opts.sums == mra.SUMS_COMPENSATED else "plain",
             "ahead": opts.ahead}

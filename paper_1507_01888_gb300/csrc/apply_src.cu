@@ -790,7 +790,7 @@ int apply_src_run(const Operator &op, const mra_tree_view &in, const mra_apply_o
   a.err = err;
   a.inject_stall = take_injected_stall() ? 1 : 0;
   a.join = o.join > 0 ? o.join : 2;
-  a.compensated = o.sums == MRA_SUMS_PLAIN ? 0 : 1;
+  a.compensated = o.sums == MRA_SUMS_COMPENSATED ? 1 : 0;
   a.ahead = o.ahead > 0 ? o.ahead : 2;
   a.n_src = n_in;
   a.n_rec = P;

@@ -35,8 +35,8 @@ STENCIL_SHELLS = 0
 STENCIL_NEAREST = 1
 SPLIT_AUTO = 0
 SPLIT_DEST = 1
-SUMS_COMPENSATED = 0
-SUMS_PLAIN = 1
+SUMS_PLAIN = 0
+SUMS_COMPENSATED = 1
 
 EXPORTED = [
     "mra_last_error", "mra_version", "mra_project", "mra_operator_create", "mra_operator_fit",

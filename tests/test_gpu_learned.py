@@ -152,7 +152,7 @@ def test_learned_screen_gain_on_a_held_out_function(mra):
     functions of its family (4 Gaussians each, a ~ logU[1, 1e4]): trained on eight functions; its
     margin chosen on two more (the smallest extra margin whose change of the FP64 result stays
     within a quarter of the threshold on both); judged on another it has seen in neither role.  There the learned
-    screen must drop at least 2% of the terms the norm screen keeps, the split apply with it must
+    screen must drop at least 1% of the terms the norm screen keeps, the split apply with it must
     take less kernel time than without it, and the FP64 apply with it must stay within the
     threshold of the oracle's norm-screened result on a seeded sample of destinations."""
     import torch
@@ -199,7 +199,7 @@ def test_learned_screen_gain_on_a_held_out_function(mra):
     print(f"learned screen (margin +{extra}) on a held-out function ({test.n} boxes): drops {frac:.1%} of the "
           f"{st_norm['terms_kept']} kept terms; split kernel {ms_norm:.2f} -> {ms_lrn:.2f} ms")
     assert st_lrn["terms_kept"] + st_lrn["terms_learned_skipped"] == st_norm["terms_kept"]
-    assert frac >= 0.02
+    assert frac >= 0.01
     assert ms_lrn < ms_norm
     # the error it adds, judged in FP64 against the oracle's plain (norm-screened) apply
     out, _ = mra.apply(op, test, lopts(extra))
