@@ -39,12 +39,24 @@ import workloads as W  # noqa: E402
 SPLIT_TRAFFIC = {("bsh_m60_adaptive_k10", 2): 70.93e6 + 77.63e6}
 
 METRIC = "3D operator-apply boxes/s & % roofline, mixed vs FP64 GPU at 1e-6 rel L2"
+def fixed_schedule(opts, text):
+    """opts with the schedule fields given as 'field=value,...' (no tuning)."""
+    from paper_1507_01888_gb300 import autotune, mra
+    o = mra.copy_opts(opts)
+    for item in text.split(","):
+        f, v = item.split("=")
+        if f.strip() not in ("split_kernel", "tile_variant", "join", "sums", "ahead"):
+            raise ValueError(f"--schedule: unknown field {f}")
+        setattr(o, f.strip(), int(v))
+    return o, {"choice": autotune.describe(o), "candidates": "fixed by --schedule"}
+
+
 def split_dtype(pieces, opts=None, k=0):
     """What the split-precision apply of order k computes in (the label of its JSON line)."""
     from paper_1507_01888_gb300 import mra
     if opts is not None and opts.split_kernel != mra.SPLIT_DEST and k in (4, 6, 8, 10):
         sums = "compensated f32 (sum + Kahan correction)" if opts.sums == mra.SUMS_COMPENSATED else "plain f32"
-        join = max(int(opts.join), 1) if opts.join else 2
+        join = (max(int(opts.join), 1) if opts.join else 2) if k * k > 64 else 1  # joins need one source per tile
         return (f"bf16x{pieces}-split MMAs with f32 accumulation in tensor memory (up to {join} Gaussian terms "
                 f"per accumulation); each (source, displacement) sum over terms in {sums}, stored as f32; "
                 f"f64 per-destination sums")
@@ -83,6 +95,9 @@ def parse():
     p.add_argument("--workload", default="bsh_m60_adaptive_k10", choices=sorted(W.WORKLOADS))
     p.add_argument("--precision", choices=["auto", "fp64", "split"], default="auto")
     p.add_argument("--pieces", type=int, default=3)
+    p.add_argument("--schedule", default=None,
+                   help="fixed split schedule instead of the autotuner, e.g. 'split_kernel=0,join=4,sums=0,ahead=2' "
+                        "(the fields of mra_apply_opts; used to profile the schedule a tuned run chose)")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU seconds of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--clocks-csv", default=None, help="also write the nvidia-smi samples here")
@@ -350,7 +365,9 @@ def run_ns(args, w, rank, world):
             return mra.NSTreeApplier(op, ns_op, n0, o, out_cap=8 * tree.n, device=dev)
         return mra.NSApplier(op, ns_op, tree, n0, o)
     tuning = {}
-    if prec == mra.PREC_SPLIT_BF16:
+    if prec == mra.PREC_SPLIT_BF16 and args.schedule:
+        opts, tuning = fixed_schedule(opts, args.schedule)
+    elif prec == mra.PREC_SPLIT_BF16:
         opts, table = autotune.tune(op, tree, opts, make_applier=make)
         tuning = {"choice": autotune.describe(opts), "candidates": table}
     ap = make(opts)
@@ -848,7 +865,9 @@ def main():
                        "held_out_terms_per_level": {str(n): c for n, c in linfo["val_per_level"].items()}}
         del train_trees
     tuning = {}
-    if prec == mra.PREC_SPLIT_BF16:
+    if prec == mra.PREC_SPLIT_BF16 and args.schedule:
+        opts, tuning = fixed_schedule(opts, args.schedule)
+    elif prec == mra.PREC_SPLIT_BF16:
         from paper_1507_01888_gb300 import autotune
 
         def batched_applier(o):

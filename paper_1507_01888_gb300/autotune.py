@@ -26,7 +26,8 @@ def candidates(k: int, src_ok: bool):
     """(name, option overrides) pairs to time, most accurate first."""
     out = []
     if src_ok:
-        for join in (1, 2, 3, 4):
+        # terms are joined in tensor memory only in tiles of one source (k >= 9 here)
+        for join in ((1, 2, 3, 4) if k * k > 64 else (1,)):
             for sums in (mra.SUMS_COMPENSATED, mra.SUMS_PLAIN):
                 out.append((f"src join={join} sums={'comp' if sums == mra.SUMS_COMPENSATED else 'plain'}",
                             dict(split_kernel=mra.SPLIT_AUTO, join=join, sums=sums, ahead=2)))
