@@ -200,38 +200,25 @@ __global__ void __launch_bounds__(PLAIN ? SRC_THREADS + 32 : SRC_THREADS, 2) app
     }
   };
   // the first K columns of each of the P column groups (16 nb columns apart) starting at
-  // column `col` of this warp's lanes, summed smallest first: with plain sums all loads are in
-  // flight before one wait; the compensated sums' registers leave room for two at a time
+  // column `col` of this warp's lanes, summed smallest first (groups P-1 and P-2 first, then
+  // group 0: two loads in flight at a time)
   auto load_groups = [&](uint32_t col, int nb, float *v) {
     const uint32_t base = col + ((uint32_t)(32 * quarter) << 16);
     float c[2][K];
-    if constexpr (PLAIN) {
-      tc::tmem_ldk<K>(base, v);
+    if (P == 3) {
+      tc::tmem_ldk<K>(base + 32u * nb, c[0]);
       tc::tmem_ldk<K>(base + 16u * nb, c[1]);
-      if (P == 3) tc::tmem_ldk<K>(base + 32u * nb, c[0]);
       tc::tmem_ld_wait();
-      if (P == 3) {
 #pragma unroll
-        for (int j = 0; j < K; ++j) c[1][j] += c[0][j];
-      }
-#pragma unroll
-      for (int j = 0; j < K; ++j) v[j] += c[1][j];
+      for (int j = 0; j < K; ++j) v[j] = c[0][j] + c[1][j];
     } else {
-      if (P == 3) {
-        tc::tmem_ldk<K>(base + 32u * nb, c[0]);
-        tc::tmem_ldk<K>(base + 16u * nb, c[1]);
-        tc::tmem_ld_wait();
-#pragma unroll
-        for (int j = 0; j < K; ++j) v[j] = c[0][j] + c[1][j];
-      } else {
-        tc::tmem_ldk<K>(base + 16u * nb, v);
-        tc::tmem_ld_wait();
-      }
-      tc::tmem_ldk<K>(base, c[0]);
+      tc::tmem_ldk<K>(base + 16u * nb, v);
       tc::tmem_ld_wait();
-#pragma unroll
-      for (int j = 0; j < K; ++j) v[j] += c[0][j];
     }
+    tc::tmem_ldk<K>(base, c[0]);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] += c[0][j];
   };
   const int mrow = quarter * 32 + lane;  // this thread's row of the tile (lane of tensor memory)
   const int ahead = max(1, min(a.ahead, SRC_MAX_AHEAD));
