@@ -104,9 +104,9 @@ __global__ void __launch_bounds__(PLAIN ? SRC_THREADS + 32 : SRC_THREADS, 2) app
   int *grp_rec = (int *)(Bt + SRC_NB * BIT_BYTES);                      // [SRC_NG][G][3]
   uint64_t *grp_mask = (uint64_t *)(grp_rec + SRC_NG * G * 3 + (SRC_NG * G * 3) % 2);  // [SRC_NG][G][3][2]
   uint64_t *grp_union = grp_mask + SRC_NG * G * 3 * 2;                  // [SRC_NG][2]
-  __shared__ __align__(8) uint64_t bar_s1, bar_s2, bar_s3, bar_ring, bar_d2free, bar_a3ready, bar_drain0, bar_drain1,
-      bar_drain2;
+  __shared__ __align__(8) uint64_t bar_s1, bar_s2, bar_s3, bar_ring, bar_d2free, bar_drain0, bar_drain1, bar_drain2;
   __shared__ int s3_flags[SRC_RING];  // from warpgroup 1 to the stage-3 issuer: join / no more terms
+  __shared__ volatile int s_nfetch;    // terms whose block copies thread 32 has issued
   __shared__ __align__(8) uint64_t bar_bb[SRC_NB], bar_bfree[SRC_NB];
   __shared__ uint32_t tmem_holder;
   __shared__ int t_src[SRC_MAX_G];
@@ -131,7 +131,6 @@ __global__ void __launch_bounds__(PLAIN ? SRC_THREADS + 32 : SRC_THREADS, 2) app
     tc::mbar_init(tc::smem_u32(&bar_s3), 1);
     tc::mbar_init(tc::smem_u32(&bar_ring), 1);
     tc::mbar_init(tc::smem_u32(&bar_d2free), 1);
-    tc::mbar_init(tc::smem_u32(&bar_a3ready), 1);
     tc::mbar_init(tc::smem_u32(&bar_drain0), 1);
     tc::mbar_init(tc::smem_u32(&bar_drain1), 1);
     tc::mbar_init(tc::smem_u32(&bar_drain2), 1);
@@ -140,6 +139,7 @@ __global__ void __launch_bounds__(PLAIN ? SRC_THREADS + 32 : SRC_THREADS, 2) app
       tc::mbar_init(tc::smem_u32(&bar_bfree[b]), 1);
     }
     abort_flag = 0;
+    s_nfetch = 0;
   }
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(&tmem_holder), SRC_TMEM_COLS);
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -220,6 +220,8 @@ __global__ void __launch_bounds__(PLAIN ? SRC_THREADS + 32 : SRC_THREADS, 2) app
 #pragma unroll
     for (int j = 0; j < K; ++j) v[j] += c[0][j];
   };
+  // warpgroup 1 hands a term (or the end) to the stage-3 issuer warp: named barrier 3, 128 + 32
+  auto wg_arrive_issuer = [&]() { asm volatile("bar.arrive 3, 160;" ::: "memory"); };
   const int mrow = quarter * 32 + lane;  // this thread's row of the tile (lane of tensor memory)
   const int ahead = max(1, min(a.ahead, SRC_MAX_AHEAD));
   const int join = G == 1 ? max(1, min(a.join, SRC_MAX_JOIN)) : 1;
@@ -263,6 +265,7 @@ __global__ void __launch_bounds__(PLAIN ? SRC_THREADS + 32 : SRC_THREADS, 2) app
       unsigned char *Bb = Bt + b * BIT_BYTES;
       const uint32_t bar = tc::smem_u32(&bar_bb[b]);
       ++nfetch;
+      s_nfetch = nfetch;
       if (stalled) {  // the copies never land: the waits run out
         stalled = false;
         return true;
@@ -568,11 +571,9 @@ __global__ void __launch_bounds__(PLAIN ? SRC_THREADS + 32 : SRC_THREADS, 2) app
       tc::fence_proxy_async_smem();
       tc::fence_before_sync();
       wg_sync(2);
-      if constexpr (PLAIN) {  // the stage-3 issuer warp takes it from here
-        if (tid == 128) {
-          s3_flags[it % SRC_RING] = join_now ? FLAG_JOIN : 0;
-          mbar_arrive(tc::smem_u32(&bar_a3ready));
-        }
+      if constexpr (PLAIN) {  // the stage-3 issuer warp takes it from here (named barrier 3)
+        if (tid == 128) s3_flags[it % SRC_RING] = join_now ? FLAG_JOIN : 0;
+        wg_arrive_issuer();
       } else if (tid == 160) {  // a thread of another warp than the polling one issues stage 3
         const int b = it % SRC_NB;
         const unsigned char *B3 = Bt + b * BIT_BYTES + BZ_OFF;
@@ -604,38 +605,52 @@ __global__ void __launch_bounds__(PLAIN ? SRC_THREADS + 32 : SRC_THREADS, 2) app
       }
     }
     if (bad) abort_flag = 1;
-    if constexpr (PLAIN) {
-      if (tid == 128) {  // no more terms for the stage-3 issuer
-        s3_flags[it % SRC_RING] = FLAG_TERM;
-        mbar_arrive(tc::smem_u32(&bar_a3ready));
-      }
+    if constexpr (PLAIN) {  // no more terms for the stage-3 issuer (also after an abort)
+      if (tid == 128) s3_flags[it % SRC_RING] = FLAG_TERM;
+      wg_arrive_issuer();
     } else if (tid == 160) {
       tc::mma_commit(tc::smem_u32(&bar_drain1));
       tc::mbar_wait(tc::smem_u32(&bar_drain1), 0, WAIT_CYCLES);
     }
-  } else if (PLAIN && tid == SRC_THREADS) {
-    // ======================================================= the stage-3 issuer (warp 8, one thread)
+  } else if (PLAIN && warp == SRC_THREADS / 32) {
+    // ======================================================= the stage-3 issuer (warp 8; lane 0 issues)
+    // Warpgroup 1 hands each term over on named barrier 3 (its 128 threads arrive, this warp
+    // waits: cheaper than an mbarrier round trip) and arrives once more when there are no more
+    // terms, also after an abort, so the wait always ends.  The blocks of the next term are
+    // checked as soon as their copies are known to be issued.
+    int ready = -1;  // the term whose blocks lane 0 has already seen land
     for (int it = 0;; ++it) {
-      if (!tc::mbar_wait_or_abort(tc::smem_u32(&bar_a3ready), (uint32_t)(it & 1), WAIT_CYCLES, &abort_flag)) {
-        abort_flag = 1;
-        break;
-      }
+      asm volatile("bar.sync 3, 160;" ::: "memory");
       const int f = s3_flags[it % SRC_RING];
       if (f & FLAG_TERM) break;
       const int b = it % SRC_NB;
       const unsigned char *B3 = Bt + b * BIT_BYTES + BZ_OFF;
-      if (!tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[b]), (uint32_t)((it / SRC_NB) & 1), WAIT_CYCLES, &abort_flag)) {
-        abort_flag = 1;
-        break;
+      if (lane == 0) {
+        bool ok = ready == it ||
+                  tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[b]), (uint32_t)((it / SRC_NB) & 1), WAIT_CYCLES, &abort_flag);
+        if (ok) {
+          tc::fence_after_sync();
+          // ---- stage 3: rows (i, ix, iy), contraction jz, B = c_m R_{m,lz} of the window's three lz
+          issue_stacked(tD3, A3, B3, 3, (f & FLAG_JOIN) ? 1u : 0u);
+          tc::mma_commit(bs3);
+          tc::mma_commit(tc::smem_u32(&bar_bfree[b]));
+          const int nx = it + 1;  // the next term's blocks, if their copies are issued
+          if (nx < s_nfetch &&
+              tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[nx % SRC_NB]), (uint32_t)((nx / SRC_NB) & 1), WAIT_CYCLES,
+                                     &abort_flag))
+            ready = nx;
+        } else {
+          abort_flag = 1;
+        }
       }
-      tc::fence_after_sync();
-      // ---- stage 3: rows (i, ix, iy), contraction jz, B = c_m R_{m,lz} of the window's three lz
-      issue_stacked(tD3, A3, B3, 3, (f & FLAG_JOIN) ? 1u : 0u);
-      tc::mma_commit(bs3);
-      tc::mma_commit(tc::smem_u32(&bar_bfree[b]));
+      // one decision for the whole warp (lane 0's view), so that no lane waits alone at bar.sync
+      if (__shfl_sync(0xffffffffu, (int)abort_flag, 0)) break;
     }
-    tc::mma_commit(tc::smem_u32(&bar_drain1));
-    tc::mbar_wait(tc::smem_u32(&bar_drain1), 0, WAIT_CYCLES);
+    if (lane == 0) {
+      tc::mma_commit(tc::smem_u32(&bar_drain1));
+      tc::mbar_wait(tc::smem_u32(&bar_drain1), 0, WAIT_CYCLES);
+    }
+    __syncwarp();
   }
   tc::fence_before_sync();
   __syncthreads();
