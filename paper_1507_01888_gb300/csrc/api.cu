@@ -272,9 +272,9 @@ int mra_release_memory(void) {
 int mra_debug_status(int *line, void *stream) {
   if (!line) return fail(MRA_ERR_ARG, "mra_debug_status: NULL line");
   cudaStream_t s = (cudaStream_t)stream;
-  const int a = debug_line_apply(s), b = debug_line_split(s);
-  if (a < 0 || b < 0) return fail(MRA_ERR_CUDA, "mra_debug_status: reading the check words failed");
-  *line = a ? a : b;
+  const int a = debug_line_apply(s), b = debug_line_split(s), c = debug_line_src(s);
+  if (a < 0 || b < 0 || c < 0) return fail(MRA_ERR_CUDA, "mra_debug_status: reading the check words failed");
+  *line = a ? a : (b ? b : c);
   return MRA_OK;
 }
 

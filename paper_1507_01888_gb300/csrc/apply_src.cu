@@ -887,3 +887,7 @@ int apply_src_run(const Operator &op, const mra_tree_view &in, const mra_apply_o
 }
 
 }  // namespace mra
+
+namespace mra {
+int debug_line_src(cudaStream_t s) { return debug_take_line(s); }
+}  // namespace mra

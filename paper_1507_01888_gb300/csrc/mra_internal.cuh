@@ -70,6 +70,7 @@ static inline int debug_take_line(cudaStream_t) { return 0; }
 #endif
 int debug_line_apply(cudaStream_t s);
 int debug_line_split(cudaStream_t s);
+int debug_line_src(cudaStream_t s);
 
 // ---------------------------------------------------------------- keys
 __host__ __device__ inline uint64_t make_key(int n, int64_t x, int64_t y, int64_t z) {

@@ -2,8 +2,9 @@
 test), and stay silent on the apply paths while giving the release build's results.
 
 Runs in a child process (the checking library is selected by MRA_DEBUG=1 when the binding
-loads), on small cases of the leaf-level apply (FP64, split in the four-tile and one-tile
-shapes, batched), the non-standard apply on an adaptive tree and a graph replay.
+loads), on small cases of the leaf-level apply (FP64; split on the source-stationary kernel with
+plain and compensated sums and on the destination-stationary kernel's four-tile and one-tile
+shapes; batched), the non-standard apply on an adaptive tree and a graph replay.
 """
 import os
 import subprocess
@@ -33,8 +34,12 @@ CHILD = textwrap.dedent("""
     tree = mra.Tree.from_host(keys, coeffs, 32.0)
     out = {{}}
     for name, o in (("f64", mra.make_opts(stencil=mra.STENCIL_SHELLS, max_disp=1, screen=mra.SCREEN_NORM, tau=1e-8)),
-                    ("split0", mra.make_opts(precision=1, stencil=mra.STENCIL_SHELLS, max_disp=1, tile_variant=0)),
-                    ("split2", mra.make_opts(precision=1, stencil=mra.STENCIL_SHELLS, max_disp=1, tile_variant=2))):
+                    ("src", mra.make_opts(precision=1, stencil=mra.STENCIL_SHELLS, max_disp=1)),
+                    ("src_comp", mra.make_opts(precision=1, stencil=mra.STENCIL_SHELLS, max_disp=1, sums=1)),
+                    ("dest0", mra.make_opts(precision=1, stencil=mra.STENCIL_SHELLS, max_disp=1, split_kernel=1,
+                                            tile_variant=0)),
+                    ("dest2", mra.make_opts(precision=1, stencil=mra.STENCIL_SHELLS, max_disp=1, split_kernel=1,
+                                            tile_variant=2))):
         r, _ = mra.apply(op, tree, o)
         out[name] = r.host()[1]
     big, offs = mra.concat_trees([tree, tree])
