@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(PLAIN ? SRC_THREADS + 32 : SRC_THREADS, 2) app
   int *grp_rec = (int *)(Bt + SRC_NB * BIT_BYTES);                      // [SRC_NG][G][3]
   uint64_t *grp_mask = (uint64_t *)(grp_rec + SRC_NG * G * 3 + (SRC_NG * G * 3) % 2);  // [SRC_NG][G][3][2]
   uint64_t *grp_union = grp_mask + SRC_NG * G * 3 * 2;                  // [SRC_NG][2]
-  __shared__ __align__(8) uint64_t bar_s1, bar_s2, bar_s3, bar_d2free, bar_drain0, bar_drain1, bar_drain2;
+  __shared__ __align__(8) uint64_t bar_s1, bar_s2, bar_s3, bar_ring, bar_d2free, bar_drain0, bar_drain1, bar_drain2;
   __shared__ int s3_flags[SRC_RING];  // from warpgroup 1 to the stage-3 issuer: join / no more terms
   __shared__ volatile int s_nfetch;    // terms whose block copies thread 32 has issued
   __shared__ __align__(8) uint64_t bar_bb[SRC_NB], bar_bfree[SRC_NB];
@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(PLAIN ? SRC_THREADS + 32 : SRC_THREADS, 2) app
     tc::mbar_init(tc::smem_u32(&bar_s1), 1);
     tc::mbar_init(tc::smem_u32(&bar_s2), 1);
     tc::mbar_init(tc::smem_u32(&bar_s3), 1);
+    tc::mbar_init(tc::smem_u32(&bar_ring), 1);
     tc::mbar_init(tc::smem_u32(&bar_d2free), 1);
     tc::mbar_init(tc::smem_u32(&bar_drain0), 1);
     tc::mbar_init(tc::smem_u32(&bar_drain1), 1);
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(PLAIN ? SRC_THREADS + 32 : SRC_THREADS, 2) app
   const uint32_t tmem = tmem_holder;
   const uint32_t tD1 = tmem + D1_COL, tD2 = tmem + D2_COL, tD3 = tmem + D3_COL;
   const uint32_t bs1 = tc::smem_u32(&bar_s1), bs2 = tc::smem_u32(&bar_s2), bs3 = tc::smem_u32(&bar_s3);
-  const uint32_t bd2free = tc::smem_u32(&bar_d2free);
+  const uint32_t bring = tc::smem_u32(&bar_ring), bd2free = tc::smem_u32(&bar_d2free);
   auto idesc_n = [](int n) { return tc::idesc_bf16(128, 16 * n, 1, 0); };
   auto adesc = [&](const unsigned char *A, int p) {
     return tc::smem_desc(tc::smem_u32(A + p * TILE_BYTES), 128, MG_BYTES);
@@ -221,9 +222,6 @@ __global__ void __launch_bounds__(PLAIN ? SRC_THREADS + 32 : SRC_THREADS, 2) app
   };
   // warpgroup 1 hands a term (or the end) to the stage-3 issuer warp: named barrier 3, 128 + 32
   auto wg_arrive_issuer = [&]() { asm volatile("bar.arrive 3, 160;" ::: "memory"); };
-  // warpgroup 0 (warp 2) hands a term (or the end) to warpgroup 1: named barrier 4, 32 + 128
-  auto ring_arrive = [&]() { asm volatile("bar.arrive 4, 160;" ::: "memory"); };
-  auto ring_wait = [&]() { asm volatile("bar.sync 4, 160;" ::: "memory"); };
   const int mrow = quarter * 32 + lane;  // this thread's row of the tile (lane of tensor memory)
   const int ahead = max(1, min(a.ahead, SRC_MAX_AHEAD));
   const int join = G == 1 ? max(1, min(a.join, SRC_MAX_JOIN)) : 1;
@@ -239,7 +237,6 @@ __global__ void __launch_bounds__(PLAIN ? SRC_THREADS + 32 : SRC_THREADS, 2) app
       run_addrs(A2, i * k2 + jz * K, jy, a2_addr);
     }
     uint32_t p1 = 0;
-    int last_arrived = -1;  // (thread 64) the last term handed to warpgroup 1 on barrier 4
     int it = 0;       // terms issued by this CTA so far (all tiles)
     int nfetch = 0;   // block copies issued (thread 32), for iterations 0 .. nfetch-1 in order
     bool bad = false;
@@ -424,11 +421,8 @@ __global__ void __launch_bounds__(PLAIN ? SRC_THREADS + 32 : SRC_THREADS, 2) app
         tc::fence_proxy_async_smem();
         tc::fence_before_sync();
         wg_sync(1);
-        // ---- the term to warpgroup 1 (thread 64 fills the ring slot once D2 is free; warp 2
-        // arrives on named barrier 4, which warpgroup 1 waits on), then stage 2 (thread 64)
-        bool ok2 = true;
-        if (tid == 64) {
-          ok2 = it == 0 || tc::mbar_wait_or_abort(bd2free, (uint32_t)((it - 1) & 1), WAIT_CYCLES, &abort_flag);
+        if (tid == 64) {  // ---- stage 2: rows (i, jz, ix), contraction jy
+          bool ok2 = it == 0 || tc::mbar_wait_or_abort(bd2free, (uint32_t)((it - 1) & 1), WAIT_CYCLES, &abort_flag);
           if (ok2) {
             const int r = it % SRC_RING;
             ring_m[r] = m;
@@ -436,18 +430,10 @@ __global__ void __launch_bounds__(PLAIN ? SRC_THREADS + 32 : SRC_THREADS, 2) app
             ring_flags[r] = group_end ? FLAG_GROUP_END : 0;
             if (group_end)
               for (int e = 0; e < G * 3; ++e) ring_rec[r][e] = grp_rec[g * G * 3 + e];
-          }
-        }
-        // warp 2 arrives only once D2 was read for the previous term, i.e. once warpgroup 1 has
-        // passed its wait for that term: never two arrivals pending on barrier 4
-        if (warp == 2 && __shfl_sync(0xffffffffu, (int)ok2, 0)) {
-          ring_arrive();
-          if (lane == 0) last_arrived = it;
-        }
-        if (tid == 64) {  // ---- stage 2: rows (i, jz, ix), contraction jy
-          if (ok2)
+            mbar_arrive(bring);
             ok2 = tc::mbar_wait_or_abort(tc::smem_u32(&bar_bb[b]), (uint32_t)((it / SRC_NB) & 1), WAIT_CYCLES,
                                          &abort_flag);
+          }
           if (ok2) {
             tc::fence_after_sync();
             issue_stacked(tD2, A2, Bb + BY_OFF, 1, 0u);
@@ -460,17 +446,16 @@ __global__ void __launch_bounds__(PLAIN ? SRC_THREADS + 32 : SRC_THREADS, 2) app
       }
       // a thread that left the loop early by the vote has bad set
     }
-    // no more terms (or an abort): the slot after the last published one says so.  Warpgroup 1
-    // waits for that slot only after reading the previous term's D2 (so it arrives on d2free):
-    // once that arrival is seen, one more arrival on barrier 4 ends its wait and none is pending;
-    // if it never comes within the bound, warpgroup 1 has left on the abort and waits no more.
-    int send_term = 1;
-    if (tid == 64) {
-      const int j = last_arrived;
-      if (j >= 0 && !tc::mbar_wait(bd2free, (uint32_t)(j & 1), WAIT_CYCLES)) send_term = 0;
-      ring_flags[(j + 1) % SRC_RING] = FLAG_TERM;
+    // no more terms: tell warpgroup 1 (after it has read the last term's D2)
+    if (!bad && tid == 64) {
+      bool ok2 = it == 0 || tc::mbar_wait_or_abort(bd2free, (uint32_t)((it - 1) & 1), WAIT_CYCLES, &abort_flag);
+      if (ok2) {
+        ring_flags[it % SRC_RING] = FLAG_TERM;
+        mbar_arrive(bring);
+      } else {
+        abort_flag = 1;
+      }
     }
-    if (warp == 2 && __shfl_sync(0xffffffffu, send_term, 0)) ring_arrive();
     if (bad) abort_flag = 1;
     // block copies still in flight (after an abort) land before the CTA exits, and every MMA an
     // issuing thread started is complete before the tensor memory is released
@@ -557,10 +542,10 @@ __global__ void __launch_bounds__(PLAIN ? SRC_THREADS + 32 : SRC_THREADS, 2) app
     for (;; ++it) {
       const int r = it % SRC_RING;
       bool ok = true;
-      ring_wait();  // the term (or the end) from warpgroup 0
+      if (quarter == 0) ok = tc::mbar_wait_or_abort(bring, (uint32_t)(it & 1), WAIT_CYCLES, &abort_flag);
+      if (wg_vote_or(2, !ok || abort_flag)) { bad = true; break; }
       const int flags = ring_flags[r];
       if (flags & FLAG_TERM) break;
-      if (wg_vote_or(2, abort_flag)) { bad = true; break; }
       if (quarter == 0) {
         ok = tc::mbar_wait_or_abort(bs2, (uint32_t)(it & 1), WAIT_CYCLES, &abort_flag);
         if (ok && it > 0) ok = tc::mbar_wait_or_abort(bs3, (uint32_t)((it - 1) & 1), WAIT_CYCLES, &abort_flag);
