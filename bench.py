@@ -35,8 +35,8 @@ import workloads as W  # noqa: E402
 
 # DRAM bytes (read + written) of one launch of the dominant kernel, from a one-pass ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of this bench's own command, keyed by
-# (workload, tile variant).  An entry is removed whenever the kernel changes.
-SPLIT_TRAFFIC = {("bsh_m60_adaptive_k10", 2): 70.93e6 + 77.63e6}
+# (workload, kernel).  An entry is removed whenever the kernel changes.
+SPLIT_TRAFFIC = {("bsh_m60_adaptive_k10", "apply_src_kernel"): 69.47e6 + 687.50e6}
 
 METRIC = "3D operator-apply boxes/s & % roofline, mixed vs FP64 GPU at 1e-6 rel L2"
 def fixed_schedule(opts, text):
@@ -445,7 +445,10 @@ def run_ns(args, w, rank, world):
     else:
         peak = pk.get("bf16_tflops", 1856.3)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "apply_split_kernel (all levels)", "peak_source": f"bf16 dense burst, {pk_kind}",
+                "traffic": None, "kernel": ("apply_src_kernel (order k) and apply_split_kernel (order 2k), all levels"
+                                            if k in (4, 6, 8, 10) and opts.split_kernel != mra.SPLIT_DEST
+                                            else "apply_split_kernel (all levels)"),
+                "peak_source": f"bf16 dense burst, {pk_kind}",
                 "kernel_ms": kms_mean, "flops": "algorithmic (6k'^4+k'^3 per term, k' = k or 2k)"}
         dtype = (f"order {k}: {split_dtype(args.pieces, opts, k)}; order {2 * k}: "
                  f"{split_dtype(args.pieces, opts, 2 * k)}")
@@ -955,7 +958,7 @@ def main():
     torch.cuda.synchronize()
     clk = clocks_start(args.clocks_csv)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    kernel_ms = []
+    kernel_ms, main_ms = [], []
     launches0 = mra.launch_count()
     t_wall = time.perf_counter()
     for i in range(args.steps):
@@ -965,6 +968,7 @@ def main():
         ev[i][1].record(stream)
         if graph is None:
             kernel_ms.append(ap.stats.kernel_ms)
+            main_ms.append(ap.stats.main_kernel_ms)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
     launches = mra.launch_count() - launches0
@@ -973,6 +977,7 @@ def main():
         for _ in range(3):  # the apply kernel's own time, from plain applies of the same input
             ap(tree, stream)
             kernel_ms.append(ap.stats.kernel_ms)
+            main_ms.append(ap.stats.main_kernel_ms)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -1021,7 +1026,8 @@ def main():
 
     # ---------------- roofline of the dominant kernel (the apply kernel)
     pk, pk_kind = peaks()
-    kms = statistics.mean(kernel_ms)
+    kms = statistics.mean(main_ms)  # the dominant kernel alone
+    apply_ms = statistics.mean(kernel_ms)  # with the kernels around it
     terms = st0["terms_kept"]
     achieved_tflops = terms * flops_per_term / (kms / 1e3) / 1e12
     if prec == mra.PREC_FP64:
@@ -1035,11 +1041,16 @@ def main():
         peak = pk.get("bf16_tflops", 1856.3)
         roof = {"bound": "tensor", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved_tflops / peak,
-                "traffic": SPLIT_TRAFFIC.get((w.name, int(opts.tile_variant))) if not batched else None,
-                "kernel": "apply_split_kernel",
+                "traffic": SPLIT_TRAFFIC.get((w.name, mra.KERNEL_NAMES[st0["kernel"]])) if not batched else None,
+                "kernel": mra.KERNEL_NAMES[st0["kernel"]],
+                "apply_ms": apply_ms,
+                "apply_ms_covers": ("the kernel with its work-list (sort, tiles) and per-destination "
+                                    "summation kernels" if st0["kernel"] == mra.KERNEL_SPLIT_SRC else
+                                    "the kernel alone"),
                 "peak_source": f"bf16 dense burst, {pk_kind}", "kernel_ms": kms,
                 "flops": "algorithmic (6k^4+k^3 per kept term)"}
-        if int(opts.tile_variant) == 2 and k * k <= 128 and 128 // (k * k) == 1 and args.pieces == 3:
+        if (st0["kernel"] == mra.KERNEL_SPLIT_DEST and int(opts.tile_variant) == 2 and k * k <= 128
+                and 128 // (k * k) == 1 and args.pieces == 3):
             # one slot per 128-row tile: each kept term issues 3 + 3 + 5 MMAs of M=128, K=16 with
             # N = 48, 32, 16 | 48, 32, 16 | 32, 16, 16, 16, 16 -- the tensor core's own work
             issued = terms * 2 * 128 * 16 * (96 + 96 + 96) / (kms / 1e3) / 1e12

@@ -152,14 +152,25 @@ typedef struct {
   int64_t terms_issued;       /* triples the kernel evaluated (kept + tile padding) */
   int64_t sources_truncated;  /* sources whose last allowed shell still kept terms */
   double skipped_bound;       /* sum of the screen bounds of dropped triples */
-  double kernel_ms;           /* device time of the apply kernel (CUDA events on `stream`) */
+  double kernel_ms;           /* device time of the apply kernel and the kernels around it that its
+                                 result needs (CUDA events on `stream`) */
   int64_t terms_learned_skipped; /* triples the norm screen kept and the learned screen dropped */
   double learned_skipped_bound;  /* sum of the norm-screen bounds of those triples */
   double algo_flops;  /* algorithmic flops of the kept triples: 6 k^4 + k^3 each, k the order
                          of the operator that applied them (k or 2k in the non-standard form) */
   int64_t level_sources[MRA_MAX_LEVEL + 1];    /* source boxes per level */
   int64_t level_terms_kept[MRA_MAX_LEVEL + 1]; /* kept triples per source level */
+  int32_t kernel;     /* the apply kernel that ran: MRA_KERNEL_F64, MRA_KERNEL_SPLIT_DEST or
+                         MRA_KERNEL_SPLIT_SRC (kernel_ms covers it with its work-list and
+                         summation kernels); for the non-standard form, that of its last apply */
+  double main_kernel_ms; /* device time of that kernel alone (CUDA events on `stream` around its
+                            launch; equal to kernel_ms where the apply runs one kernel; summed
+                            over the applies of the non-standard form) */
 } mra_apply_stats;
+
+#define MRA_KERNEL_F64 0        /* FP64 destination-stationary kernel */
+#define MRA_KERNEL_SPLIT_DEST 1 /* split-BF16 destination-stationary tensor-core kernel */
+#define MRA_KERNEL_SPLIT_SRC 2  /* split-BF16 source-stationary tensor-core kernel */
 
 typedef struct {
   double diff_norm;  /* || test - ref ||_2 over the union of boxes */
@@ -221,6 +232,11 @@ const char *mra_last_error(void);
 
 /* Library version string. */
 const char *mra_version(void);
+
+/* Size in bytes of the ABI structure named `name` ("mra_gauss_sum", "mra_tree_view",
+ * "mra_apply_opts", "mra_apply_stats", "mra_compare_result"), or -1 for another name.  Lets a
+ * binding check its copies of the structures' layouts without a GPU. */
+int64_t mra_abi_sizeof(const char *name);
 
 /* Project f onto the scaling functions (Sec. 2.1, eq. projection):
  * s^n_b = int f phi^n_b, computed per box from exact 1-D Gaussian integrals.

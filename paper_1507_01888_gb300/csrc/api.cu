@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <string>
 #include <cub/cub.cuh>
 #include <vector>
 
@@ -256,6 +257,17 @@ extern "C" {
 const char *mra_last_error(void) { return g_err; }
 
 const char *mra_version(void) { return "mra-gb300 0.1 (sm_103a)"; }
+
+int64_t mra_abi_sizeof(const char *name) {
+  if (!name) return -1;
+  const std::string n(name);
+  if (n == "mra_gauss_sum") return (int64_t)sizeof(mra_gauss_sum);
+  if (n == "mra_tree_view") return (int64_t)sizeof(mra_tree_view);
+  if (n == "mra_apply_opts") return (int64_t)sizeof(mra_apply_opts);
+  if (n == "mra_apply_stats") return (int64_t)sizeof(mra_apply_stats);
+  if (n == "mra_compare_result") return (int64_t)sizeof(mra_compare_result);
+  return -1;
+}
 
 long long mra_launch_count(void) { return mra::g_launches.load(std::memory_order_relaxed); }
 

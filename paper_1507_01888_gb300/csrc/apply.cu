@@ -901,10 +901,14 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
     out_offsets[1] = nd;
   }
   int rc;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evk0 = nullptr, evk1 = nullptr;
   if (stats) {
     MRA_CUDA_TRY(cudaEventCreate(&ev0));
     MRA_CUDA_TRY(cudaEventCreate(&ev1));
+    if (src_path) {
+      MRA_CUDA_TRY(cudaEventCreate(&evk0));
+      MRA_CUDA_TRY(cudaEventCreate(&evk1));
+    }
   }
   ApplyWork wk{};
   wk.n_dest = nd;
@@ -924,7 +928,11 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
   wk.split_ws_bytes = L.split_bytes;
   wk.ev0 = ev0;
   wk.ev1 = ev1;
+  wk.evk0 = evk0;
+  wk.evk1 = evk1;
   wk.fx = fx;
+  if (stats)
+    stats->kernel = o.precision == MRA_PREC_FP64 ? MRA_KERNEL_F64 : src_path ? MRA_KERNEL_SPLIT_SRC : MRA_KERNEL_SPLIT_DEST;
   if (o.precision == MRA_PREC_FP64) {
     if (ev0) MRA_CUDA_TRY(cudaEventRecord(ev0, s));
     size_t smem = (size_t)(3 * k3 + 3 * k * k) * sizeof(double);
@@ -959,6 +967,13 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
     float ms = 0.0f;
     MRA_CUDA_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
     stats->kernel_ms = ms;
+    stats->main_kernel_ms = ms;
+    if (evk0) {
+      MRA_CUDA_TRY(cudaEventElapsedTime(&ms, evk0, evk1));
+      stats->main_kernel_ms = ms;
+      cudaEventDestroy(evk0);
+      cudaEventDestroy(evk1);
+    }
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
   }

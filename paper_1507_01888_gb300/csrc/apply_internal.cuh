@@ -37,6 +37,7 @@ struct ApplyWork {
   void *split_ws;             // scratch for the tensor-core path's grouping
   size_t split_ws_bytes;
   cudaEvent_t ev0, ev1;       // recorded around the apply kernel when non-null
+  cudaEvent_t evk0, evk1;     // around the main kernel alone, where the apply runs more kernels
   const FixedSizes *fx;       // fixed-size (graph) mode when non-null
 };
 

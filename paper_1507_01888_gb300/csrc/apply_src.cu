@@ -853,8 +853,10 @@ int apply_src_run(const Operator &op, const mra_tree_view &in, const mra_apply_o
   // than sources
   const int64_t max_tiles = G == 1 ? n_in : n_in / G + MRA_MAX_LEVEL + 1;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)sms, max_tiles));
+  if (wk.evk0) MRA_CUDA_TRY(cudaEventRecord(wk.evk0, s));
   kern<<<counted(grid), plain ? SRC_THREADS + 32 : SRC_THREADS, smem, s>>>(a);
   MRA_CUDA_TRY(cudaGetLastError());
+  if (wk.evk1) MRA_CUDA_TRY(cudaEventRecord(wk.evk1, s));
   dest_sum_kernel<<<counted((unsigned)std::max<int64_t>(nd, 1)), 256, 0, s>>>(
       nd, k3, wk.seg, wk.perm, partial, wk.dest_key, out.keys, out.coeffs, P);
   MRA_CUDA_TRY(cudaGetLastError());

@@ -859,6 +859,8 @@ extern "C" int mra_apply_ns(const mra_operator *h, const mra_operator *hns, cons
     acc.sources_truncated += st.sources_truncated;
     acc.skipped_bound += st.skipped_bound;
     acc.kernel_ms += st.kernel_ms;
+    acc.main_kernel_ms += st.main_kernel_ms;
+    acc.kernel = st.kernel;
     acc.algo_flops += st.algo_flops;
     for (int q = 0; q <= MRA_MAX_LEVEL; ++q) {
       acc.level_sources[q] += st.level_sources[q];
@@ -1082,6 +1084,8 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
     acc.terms_issued += st.terms_issued;
     acc.skipped_bound += st.skipped_bound;
     acc.kernel_ms += st.kernel_ms;
+    acc.main_kernel_ms += st.main_kernel_ms;
+    acc.kernel = st.kernel;
     acc.algo_flops += st.algo_flops;
     for (int q = 0; q <= MRA_MAX_LEVEL; ++q) {
       acc.level_sources[q] += st.level_sources[q];

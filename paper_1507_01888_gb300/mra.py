@@ -37,9 +37,14 @@ SPLIT_AUTO = 0
 SPLIT_DEST = 1
 SUMS_PLAIN = 0
 SUMS_COMPENSATED = 1
+KERNEL_F64 = 0
+KERNEL_SPLIT_DEST = 1
+KERNEL_SPLIT_SRC = 2
+KERNEL_NAMES = {KERNEL_F64: "apply_f64_kernel", KERNEL_SPLIT_DEST: "apply_split_kernel",
+                KERNEL_SPLIT_SRC: "apply_src_kernel"}
 
 EXPORTED = [
-    "mra_last_error", "mra_version", "mra_project", "mra_operator_create", "mra_operator_fit",
+    "mra_last_error", "mra_version", "mra_abi_sizeof", "mra_project", "mra_operator_create", "mra_operator_fit",
     "mra_operator_info", "mra_operator_block", "mra_operator_free", "mra_apply_workspace_size",
     "mra_apply", "mra_apply_batched", "mra_norm", "mra_norm_noalloc", "mra_compare", "mra_log_terms", "mra_mlp_init",
     "mra_mlp_standardize", "mra_mlp_forward", "mra_mlp_workspace_size", "mra_mlp_grad", "mra_mlp_train",
@@ -86,10 +91,11 @@ class ApplyStats(ctypes.Structure):
                 ("skipped_bound", ctypes.c_double), ("kernel_ms", ctypes.c_double),
                 ("terms_learned_skipped", ctypes.c_int64), ("learned_skipped_bound", ctypes.c_double),
                 ("algo_flops", ctypes.c_double), ("level_sources", ctypes.c_int64 * 20),
-                ("level_terms_kept", ctypes.c_int64 * 20)]
+                ("level_terms_kept", ctypes.c_int64 * 20), ("kernel", ctypes.c_int32),
+                ("main_kernel_ms", ctypes.c_double)]
 
     def as_dict(self):
-        d = {f: getattr(self, f) for f, _ in self._fields_[:-2]}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("level_")}
         d["levels"] = {n: {"sources": int(self.level_sources[n]), "terms_kept": int(self.level_terms_kept[n])}
                        for n in range(20) if self.level_sources[n] > 0}
         return d
@@ -140,6 +146,8 @@ def load(build_if_stale: bool = True):
         vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
         lib.mra_last_error.restype = ctypes.c_char_p
         lib.mra_version.restype = ctypes.c_char_p
+        lib.mra_abi_sizeof.restype = ctypes.c_int64
+        lib.mra_abi_sizeof.argtypes = [ctypes.c_char_p]
         lib.mra_launch_count.restype = ctypes.c_longlong
         lib.mra_debug_status.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]
         lib.mra_project.argtypes = [P(GaussSum), i, d, d, i, i, i, P(TreeView), vp]

@@ -42,6 +42,21 @@ def test_library_exports_every_declared_symbol(lib_path):
     assert b"sm_103a" in lib.mra_version()
 
 
+def test_binding_structures_match_the_library(lib_path):
+    """The binding's ctypes copies of the ABI structures have the library's sizes (a field added
+    on one side only shifts every field after it)."""
+    from paper_1507_01888_gb300 import mra
+    lib = ctypes.CDLL(lib_path)
+    lib.mra_abi_sizeof.restype = ctypes.c_int64
+    lib.mra_abi_sizeof.argtypes = [ctypes.c_char_p]
+    for cname, py in (("mra_gauss_sum", mra.GaussSum), ("mra_tree_view", mra.TreeView),
+                      ("mra_apply_opts", mra.ApplyOpts), ("mra_apply_stats", mra.ApplyStats),
+                      ("mra_compare_result", mra.CompareResult)):
+        assert lib.mra_abi_sizeof(cname.encode()) == ctypes.sizeof(py), cname
+    assert lib.mra_abi_sizeof(b"no_such_struct") == -1
+    assert "kernel" in dict(mra.ApplyStats._fields_) and "main_kernel_ms" in dict(mra.ApplyStats._fields_)
+
+
 def test_binding_lists_every_declared_symbol():
     from paper_1507_01888_gb300 import mra
     assert sorted(mra.EXPORTED) == declared_functions()
