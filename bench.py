@@ -59,7 +59,7 @@ def split_dtype(pieces, opts=None, k=0):
         join = (max(int(opts.join), 1) if opts.join else 2) if k * k > 64 else 1  # joins need one source per tile
         return (f"bf16x{pieces}-split MMAs with f32 accumulation in tensor memory (up to {join} Gaussian terms "
                 f"per accumulation); each (source, displacement) sum over terms in {sums}, stored as f32; "
-                f"f64 per-destination sums")
+                f"per-destination sums of those in f32 pairs (error-free TwoSum, ~48 bits), formed into f64")
     return (f"bf16x{pieces}-split MMAs with f32 accumulation; Gaussian-term and per-destination sums in "
             f"compensated f32 (sum + Kahan correction), formed into f64 at the end")
 

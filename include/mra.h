@@ -61,7 +61,8 @@ extern "C" {
                                  up to opts.join terms in the tensor-memory accumulator, then adds
                                  them into each (source, displacement) sum in plain or compensated
                                  FP32 (opts.sums), stored as FP32 and summed per destination in
-                                 FP64; the destination-stationary kernel keeps compensated FP32
+                                 FP32 pairs (error-free TwoSum additions, about 48 bits) formed
+                                 into FP64; the destination-stationary kernel keeps compensated FP32
                                  sums per destination, formed into FP64 at the end.  Operator
                                  blocks, fit, norms and screen stay FP64.  Measured error: 1.2e-7
                                  to 1.8e-7 relative L2 against MRA_PREC_FP64 with 3 pieces; use

@@ -19,9 +19,9 @@
 //   * each record's sum over m (the partial result of source b for destination b + l) stays in
 //     registers as a compensated FP32 sum (a sum and its Kahan correction per coefficient) and
 //     is written once, as FP32, to a partial buffer indexed by the record;
-//   * a second kernel sums the partials of every destination in FP64, in the order of the
-//     records sorted on the destination key, and writes each destination once (no atomics on
-//     results).
+//   * a second kernel sums the partials of every destination in FP32 pairs (error-free
+//     TwoSum additions, about 48 bits), in the order of the records sorted on the destination
+//     key, and writes each destination once in FP64 (no atomics on results).
 // Operands are split into P BF16 pieces and the piece products p + q < P are kept; each stage
 // stacks the B pieces along N (one MMA per A piece) into column groups g = p + q, which the
 // epilogues sum smallest first.  The FP32 accumulation of one stage happens in tensor memory.
@@ -731,20 +731,62 @@ __global__ void src_scatter_kernel(int64_t n, int G, const uint64_t *skey, const
   tile_src[(int64_t)(tile_base[l] + j / G) * G + j % G] = sval[i];
 }
 
-// Sum the partials of every destination (records in destination order) in FP64; one CTA per
-// destination, every coefficient written once.
+// s + c += x: s is the running FP32 sum and c the FP32 sum of its rounding errors, each taken
+// exactly by Knuth's TwoSum (the cascaded summation Sum2 of Ogita, Rump and Oishi), so that
+// s + c carries about twice FP32's precision.
+__device__ __forceinline__ void sum2_add(float &s, float &c, float x) {
+  const float t = s + x;
+  const float z = t - s;
+  c += (s - (t - z)) + (x - z);
+  s = t;
+}
+
+// Sum the partials of every destination, records in destination order; one CTA per destination,
+// every coefficient written once.  The FP32 partials are added in FP32 pairs (sum2_add: error
+// about 2^-48 of the sum's magnitude, far below the partials' own 2^-24 rounding) and the pair is
+// formed into FP64 once per coefficient; an FP64 addition per partial would cost a conversion
+// and an add on the FP64 pipe for every one of them.  k^3 is a multiple of 4 for the orders this
+// path covers: each thread takes four consecutive coefficients (16-byte streaming loads, read
+// once) and four records at a time.
 __global__ void dest_sum_kernel(int64_t nd, int k3, const int64_t *seg, const int *perm, const float *partial,
                                 const uint64_t *dest_key, uint64_t *out_keys, double *out_coeffs, int64_t n_rec) {
   const int64_t d = blockIdx.x;
   if (d >= nd) return;
   const int64_t r0 = seg[d], r1 = seg[d + 1];
-  for (int e = threadIdx.x; e < k3; e += blockDim.x) {
-    double acc = 0.0;
-    for (int64_t r = r0; r < r1; ++r) {
+  const int q4 = k3 / 4;
+  for (int e = threadIdx.x; e < q4; e += blockDim.x) {
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+    auto add = [&](const float4 v) {
+      sum2_add(s0, c0, v.x);
+      sum2_add(s1, c1, v.y);
+      sum2_add(s2, c2, v.z);
+      sum2_add(s3, c3, v.w);
+    };
+    auto rec = [&](int64_t r) {
       const int64_t p = MRA_IDX((int64_t)perm[MRA_IDX(r, n_rec)], n_rec);
-      acc += (double)partial[p * k3 + e];
+      return (const float4 *)(partial + p * k3) + e;
+    };
+    int64_t r = r0;
+    for (; r + 4 <= r1; r += 4) {
+      const float4 v0 = __ldcs(rec(r)), v1 = __ldcs(rec(r + 1)), v2 = __ldcs(rec(r + 2)), v3 = __ldcs(rec(r + 3));
+      add(v0);
+      add(v1);
+      add(v2);
+      add(v3);
     }
-    out_coeffs[d * k3 + e] = acc;
+    for (; r < r1; ++r) add(__ldcs(rec(r)));
+    const double a0 = (double)s0 + (double)c0, a1 = (double)s1 + (double)c1;
+    const double a2 = (double)s2 + (double)c2, a3 = (double)s3 + (double)c3;
+    double *o = out_coeffs + d * k3 + 4 * e;
+    if (((uintptr_t)out_coeffs & 15) == 0) {  // the caller's buffer: 16-byte stores where aligned
+      ((double2 *)o)[0] = make_double2(a0, a1);
+      ((double2 *)o)[1] = make_double2(a2, a3);
+    } else {
+      o[0] = a0;
+      o[1] = a1;
+      o[2] = a2;
+      o[3] = a3;
+    }
   }
   if (threadIdx.x == 0) out_keys[d] = dest_key[d];
 }
@@ -853,6 +895,8 @@ int apply_src_run(const Operator &op, const mra_tree_view &in, const mra_apply_o
   // than sources
   const int64_t max_tiles = G == 1 ? n_in : n_in / G + MRA_MAX_LEVEL + 1;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)sms, max_tiles));
+  if (((uintptr_t)partial & 15) != 0 || k3 % 4 != 0)
+    return fail(MRA_ERR_ARG, "split apply: partial-sum buffer not 16-byte aligned or k^3 = %d not a multiple of 4", k3);
   if (wk.evk0) MRA_CUDA_TRY(cudaEventRecord(wk.evk0, s));
   kern<<<counted(grid), plain ? SRC_THREADS + 32 : SRC_THREADS, smem, s>>>(a);
   MRA_CUDA_TRY(cudaGetLastError());
