@@ -1049,6 +1049,15 @@ def main():
                                     "the kernel alone"),
                 "peak_source": f"bf16 dense burst, {pk_kind}", "kernel_ms": kms,
                 "flops": "algorithmic (6k^4+k^3 per kept term)"}
+        if st0["kernel"] == mra.KERNEL_SPLIT_SRC and st0.get("mma_passes", 0) > 0:
+            # each pass issues M=128, K=16 MMAs over 16 (P(P+1)/2) columns in stages 1 and 2 and 48
+            # (P(P+1)/2) in stage 3 (three l_z): the tensor core's own work, padding included
+            cols = 80 * args.pieces * (args.pieces + 1) // 2
+            issued = st0["mma_passes"] * 2 * 128 * 16 * cols / (kms / 1e3) / 1e12
+            roof["issued"] = {"tflops": issued, "frac": issued / peak, "passes": st0["mma_passes"],
+                              "terms_per_pass": terms / st0["mma_passes"],
+                              "note": "BF16 flops the MMAs issue (k padded to 16, the six piece products, "
+                                      "windows of three l_z); context only, not the algorithmic rate"}
         if (st0["kernel"] == mra.KERNEL_SPLIT_DEST and int(opts.tile_variant) == 2 and k * k <= 128
                 and 128 // (k * k) == 1 and args.pieces == 3):
             # one slot per 128-row tile: each kept term issues 3 + 3 + 5 MMAs of M=128, K=16 with

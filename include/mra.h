@@ -167,6 +167,8 @@ typedef struct {
   double main_kernel_ms; /* device time of that kernel alone (CUDA events on `stream` around its
                             launch; equal to kernel_ms where the apply runs one kernel; summed
                             over the applies of the non-standard form) */
+  int64_t mma_passes; /* source-stationary kernel: its passes (source tile, l_x, l_y, window of
+                         three l_z, term), each one set of stage-1, 2 and 3 MMAs; 0 otherwise */
 } mra_apply_stats;
 
 #define MRA_KERNEL_F64 0        /* FP64 destination-stationary kernel */

@@ -95,9 +95,10 @@ struct ScreenArgs {
   float learned_cut[MRA_MAX_LEVEL + 1];  // per source level: log10(tau) - delta (-inf: keep all)
   int64_t *box_learned;
   double *box_lbound;
-  // the network's inputs depend on the displacement only through |l|^2: pass 0 evaluates it
-  // once per (box, class |l|^2 <= LD_Q - 1, term) and stores the drop bits, pass 1 reads them
-  uint64_t *learned_drop;     // [n_in][LD_Q][2]
+  // pass 0 stores the kept-term mask of every (box, l) it screens, l at index
+  // ((lx + dmax) S + ly + dmax) S + lz + dmax with S = 2 dmax + 1; pass 1 writes the records
+  // from these masks (the same decisions, nothing recomputed)
+  uint64_t *box_mask;         // [n_in][S^3][2]
   // several functions in one apply: boxes [fn_off[f], fn_off[f+1]) belong to function f,
   // and records sort on (f, level, x, y, z) packed as f<<53 | n<<48 | x<<32 | y<<16 | z
   int nfunc;
@@ -113,12 +114,14 @@ __device__ __forceinline__ uint64_t public_key(uint64_t bk) {
                   (int64_t)(bk & 0xFFFF));
 }
 
-template <int PASS>
-__global__ void screen_kernel(ScreenArgs a) {
+// PASS 0 screens and counts (LEARNED: with the learned screen), PASS 1 writes the records.
+template <int PASS, bool LEARNED = false>
+__global__ void __launch_bounds__(256, LEARNED ? 1 : 2) screen_kernel(ScreenArgs a) {
   extern __shared__ __align__(16) float mlp_sh[];  // the learned screen's parameters, when used
   __shared__ uint64_t drop_sh[8][LD_Q][2];  // per warp: learned-screen drop bits by |l|^2 class
-  if (a.mlp && PASS == 0) {
-    for (int i = threadIdx.x; i < MLP_NALL; i += blockDim.x) mlp_sh[i] = a.mlp[i];
+  const float *mlp = LEARNED ? a.mlp : nullptr;
+  if (mlp && PASS == 0) {
+    for (int i = threadIdx.x; i < MLP_NALL; i += blockDim.x) mlp_sh[i] = mlp[i];
     __syncthreads();
   }
   int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -130,13 +133,13 @@ __global__ void screen_kernel(ScreenArgs a) {
   int64_t x = key_x(key), y = key_y(key), z = key_z(key);
   int64_t nb = 1LL << n;
   if (a.level_off[n] < 0) {
-    if (lane == 0) atomicExch(a.err, 1);  // level outside the operator's table
+    if (lane == 0 && PASS == 0) atomicExch(a.err, 1);  // level outside the operator's table
     return;
   }
   int func = 0;
   if (a.nfunc > 1) {
     if (n > 15) {
-      if (lane == 0) atomicExch(a.err, 3);  // batched sort keys hold levels <= 15
+      if (lane == 0 && PASS == 0) atomicExch(a.err, 3);  // batched sort keys hold levels <= 15
       return;
     }
     int lo = 0, hi = a.nfunc - 1;  // last f with fn_off[f] <= b
@@ -150,82 +153,119 @@ __global__ void screen_kernel(ScreenArgs a) {
   int D = a.stencil == MRA_STENCIL_NEAREST ? 1 : a.dmax;
   if (D > Dop) D = Dop;
   if (D > nb - 1) D = (int)(nb - 1);
+  const int S = 2 * a.dmax + 1;
+  uint64_t *bmask = a.box_mask + (size_t)b * S * S * S * 2;
+  auto mask_at = [&](int lx, int ly, int lz) {
+    return bmask + (((lx + a.dmax) * S + ly + a.dmax) * S + lz + a.dmax) * 2;
+  };
+  if (PASS == 1) {
+    // the records, in pass 0's order, from its masks: shells before the one it stopped at
+    int64_t wpos = a.off[b];
+    const int dstop = a.dstop[b];
+    for (int d = 0; d <= D && d < dstop; ++d)
+      for (int lx = -d; lx <= d; ++lx)
+        for (int ly = -d; ly <= d; ++ly)
+          for (int lz = -d; lz <= d; ++lz) {
+            if (max(abs(lx), max(abs(ly), abs(lz))) != d) continue;
+            if (x + lx < 0 || x + lx >= nb || y + ly < 0 || y + ly >= nb || z + lz < 0 || z + lz >= nb) continue;
+            const uint64_t tkey = make_key(n, x + lx, y + ly, z + lz);
+            if (!(a.dest_hi == 0 || (tkey >= a.dest_lo && tkey < a.dest_hi))) continue;
+            const uint64_t *mk = mask_at(lx, ly, lz);
+            const uint64_t m0 = mk[0], m1 = mk[1];
+            if (!(m0 | m1)) continue;
+            if (lane == 0) {
+              const int64_t wp = MRA_IDX(wpos, a.rec_cap);
+              a.rec_key[wp] = a.nfunc > 1 ? batched_key(func, n, x + lx, y + ly, z + lz)
+                                          : make_key(n, x + lx, y + ly, z + lz);
+              a.rec_src[wp] = (int)b;
+              a.rec_l[wp] = (lx + 128) | ((ly + 128) << 8) | ((lz + 128) << 16);
+              a.rec_mask[2 * wp] = m0;
+              a.rec_mask[2 * wp + 1] = m1;
+            }
+            ++wpos;
+          }
+    return;
+  }
   int nl = 2 * Dop + 1;
   const double *Nl = a.N + a.level_off[n];
   double sn = a.snorm[b];
   int64_t count = 0, kept = 0, screened = 0, learned = 0;
   double skipped = 0.0, lbound = 0.0;
   const float log_sn = (float)log10(fmax(sn, 1e-300));
-  int64_t wpos = PASS == 1 ? a.off[b] : 0;
   // learned screen: drop bits of every (|l|^2 class, term) this box can meet, by the network
-  // in pass 0 (terms the norm screen would drop anyway are never looked up)
+  // (terms the norm screen would drop anyway are never looked up)
   uint64_t(*drop)[2] = drop_sh[wib];
-  if (a.mlp && D <= 2) {
-    if (PASS == 0) {
-      for (int q = 0; q <= 3 * D * D; ++q) {
-        bool occurs = false;  // q = lx^2 + ly^2 + lz^2 with |l|_inf <= D
-        for (int u = 0; u <= D; ++u)
-          for (int v = 0; v <= D; ++v)
-            for (int w = 0; w <= D; ++w) occurs |= u * u + v * v + w * w == q;
-        uint64_t w0 = 0ull, w1 = 0ull;
-        if (occurs) {
-          for (int m0 = 0; m0 < a.M; m0 += 32) {
-            const int m = m0 + lane;
-            bool dr = false;
-            if (m < a.M) {
-              float f[4] = {(float)n, sqrtf((float)q), (float)log10(a.t[m]), log_sn};
-              dr = mlp_predict(mlp_sh, f) < a.learned_cut[n];
-            }
-            const uint64_t bal = (uint64_t)__ballot_sync(0xffffffffu, dr) << (m0 & 63);
-            if (m0 < 64) w0 |= bal; else w1 |= bal;
+  if (mlp && D <= 2) {
+    for (int q = 0; q <= 3 * D * D; ++q) {
+      bool occurs = false;  // q = lx^2 + ly^2 + lz^2 with |l|_inf <= D
+      for (int u = 0; u <= D; ++u)
+        for (int v = 0; v <= D; ++v)
+          for (int w = 0; w <= D; ++w) occurs |= u * u + v * v + w * w == q;
+      uint64_t w0 = 0ull, w1 = 0ull;
+      if (occurs) {
+        for (int m0 = 0; m0 < a.M; m0 += 32) {
+          const int m = m0 + lane;
+          bool dr = false;
+          if (m < a.M) {
+            float f[4] = {(float)n, sqrtf((float)q), (float)log10(a.t[m]), log_sn};
+            dr = mlp_predict(mlp_sh, f) < a.learned_cut[n];
           }
-        }
-        if (lane == 0) {
-          drop[q][0] = w0;
-          drop[q][1] = w1;
-          a.learned_drop[(b * LD_Q + q) * 2] = w0;
-          a.learned_drop[(b * LD_Q + q) * 2 + 1] = w1;
+          const uint64_t bal = (uint64_t)__ballot_sync(0xffffffffu, dr) << (m0 & 63);
+          if (m0 < 64) w0 |= bal; else w1 |= bal;
         }
       }
-    } else if (lane < 2 * (3 * D * D + 1)) {
-      drop[lane >> 1][lane & 1] = a.learned_drop[b * LD_Q * 2 + lane];
+      if (lane == 0) {
+        drop[q][0] = w0;
+        drop[q][1] = w1;
+      }
     }
     __syncwarp();
   }
+  // |c_m| of this lane's terms (m = 32 j + lane)
+  double cabs[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) cabs[j] = 32 * j + lane < a.M ? fabs(a.c[32 * j + lane]) : 0.0;
   int d;
   for (d = 0; d <= D; ++d) {
     int any = 0;
     for (int lx = -d; lx <= d; ++lx)
-      for (int ly = -d; ly <= d; ++ly)
+      for (int ly = -d; ly <= d; ++ly) {
+        if (x + lx < 0 || x + lx >= nb || y + ly < 0 || y + ly >= nb) continue;
+        // the bound is (((|c_m| N_x) N_y) N_z) |s_b|: its first two products hold for every l_z
+        double qxy[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int m = 32 * j + lane;
+          qxy[j] = m < a.M ? cabs[j] * Nl[m * nl + lx + Dop] * Nl[m * nl + ly + Dop] : 0.0;
+        }
         for (int lz = -d; lz <= d; ++lz) {
           int m_inf = max(abs(lx), max(abs(ly), abs(lz)));
           if (m_inf != d) continue;
-          if (x + lx < 0 || x + lx >= nb || y + ly < 0 || y + ly >= nb || z + lz < 0 ||
-              z + lz >= nb)
-            continue;
+          if (z + lz < 0 || z + lz >= nb) continue;
           // destinations outside the caller's key range are screened (so that the shell logic
           // is that of the whole apply) but neither counted nor emitted
           const uint64_t tkey = make_key(n, x + lx, y + ly, z + lz);
           const bool owned = a.dest_hi == 0 || (tkey >= a.dest_lo && tkey < a.dest_hi);
           uint64_t mask[2] = {0ull, 0ull};
-          for (int m0 = 0; m0 < a.M; m0 += 32) {
-            int m = m0 + lane;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int m0 = 32 * j;
+            if (m0 >= a.M) break;
+            const int m = m0 + lane;
             bool keep = false;
             double B = 0.0;
             bool dropped_by_model = false;
             if (m < a.M) {
-              B = fabs(a.c[m]) * Nl[m * nl + lx + Dop] * Nl[m * nl + ly + Dop] *
-                  Nl[m * nl + lz + Dop] * sn;
+              B = qxy[j] * Nl[m * nl + lz + Dop] * sn;
               keep = a.screen == MRA_SCREEN_NONE ? true : (B >= a.tau);
-              if (keep && a.mlp) {
+              if (keep && mlp) {
                 const int q = lx * lx + ly * ly + lz * lz;
                 bool dr;
                 if (D <= 2) {
                   dr = (drop[q][m >> 6] >> (m & 63)) & 1ull;
-                } else {  // wide stencils: evaluate the network for this term (pass 0 only
-                          // sees the parameters in shared memory; pass 1 reads them from global)
+                } else {  // wide stencils: evaluate the network for this term
                   float f[4] = {(float)n, sqrtf((float)q), (float)log10(a.t[m]), log_sn};
-                  dr = mlp_predict(PASS == 0 ? (const float *)mlp_sh : a.mlp, f) < a.learned_cut[n];
+                  dr = mlp_predict((const float *)mlp_sh, f) < a.learned_cut[n];
                 }
                 if (dr) {
                   keep = false;
@@ -233,15 +273,20 @@ __global__ void screen_kernel(ScreenArgs a) {
                 }
               }
             }
-            if (PASS == 0 && owned) {  // per-lane sums, reduced over the warp once per box
-              if (a.mlp) {
+            if (owned) {  // per-lane sums, reduced over the warp once per box
+              if (mlp) {
                 learned += __popc(__ballot_sync(0xffffffffu, dropped_by_model));
                 if (dropped_by_model) lbound += B;
               }
               if (m < a.M && !keep && !dropped_by_model) skipped += B;
             }
             unsigned bal = __ballot_sync(0xffffffffu, keep);
-            mask[m0 >> 6] |= (uint64_t)bal << (m0 & 63);
+            mask[j >> 1] |= (uint64_t)bal << (m0 & 63);
+          }
+          if (owned && lane == 0) {
+            uint64_t *mk = mask_at(lx, ly, lz);
+            mk[0] = mask[0];
+            mk[1] = mask[1];
           }
           int pk = __popcll(mask[0]) + __popcll(mask[1]);
           if (pk == 0) {
@@ -252,25 +297,14 @@ __global__ void screen_kernel(ScreenArgs a) {
           if (!owned) continue;
           kept += pk;
           screened += a.M - pk;
-          if (PASS == 1 && lane == 0) {
-            const int64_t wp = MRA_IDX(wpos, a.rec_cap);
-            a.rec_key[wp] = a.nfunc > 1 ? batched_key(func, n, x + lx, y + ly, z + lz)
-                                        : make_key(n, x + lx, y + ly, z + lz);
-            a.rec_src[wp] = (int)b;
-            a.rec_l[wp] = (lx + 128) | ((ly + 128) << 8) | ((lz + 128) << 16);
-            a.rec_mask[2 * wp] = mask[0];
-            a.rec_mask[2 * wp + 1] = mask[1];
-          }
-          ++wpos;
           ++count;
         }
+      }
     if (a.stencil == MRA_STENCIL_SHELLS && !any) break;
   }
-  if (PASS == 0) {
-    skipped = warp_sum(skipped);
-    lbound = warp_sum(lbound);
-  }
-  if (PASS == 0 && lane == 0) {
+  skipped = warp_sum(skipped);
+  lbound = warp_sum(lbound);
+  if (lane == 0) {
     a.cnt[b] = count;
     a.dstop[b] = d;
     a.box_kept[b] = kept;
@@ -554,17 +588,18 @@ int64_t apply_max_records(const Operator &op, const mra_apply_opts &o, int64_t n
 }
 
 // Workspace layout (all offsets 256-byte aligned):
-//   per box: snorm, dstop, cnt, off, kept, screened, skipped, trunc
+//   per box: snorm, dstop, cnt, off, kept, screened, skipped, trunc, learned, lbound, and the
+//     screen's kept-term masks of its (2 dmax + 1)^3 displacements
 //   per record: key, src, l, mask[2], sorted key, perm in/out, head, dest id
 //   per destination (<= records): dest key, seg (+1)
 //   CUB temp storage (max over scan / sort / reduce needs)
 struct Layout {
-  size_t snorm, dstop, cnt, off, kept, screened, skipped, trunc, learned, lbound, ldrop;
+  size_t snorm, dstop, cnt, off, kept, screened, skipped, trunc, learned, lbound, bmask;
   size_t rkey, rsrc, rl, rmask, skey, pin, pout, head, did, dkey, seg, ndest, dfunc, fnoff, lev, split, tmp;
   size_t split_bytes, tmp_bytes, total;
 };
 
-static Layout make_layout(int64_t n_in, int64_t P, bool learned, bool src_path = false) {
+static Layout make_layout(int64_t n_in, int64_t P, int dmax, bool src_path = false) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -583,7 +618,8 @@ static Layout make_layout(int64_t n_in, int64_t P, bool learned, bool src_path =
   L.trunc = take(nb * 4);
   L.learned = take(nb * 8);
   L.lbound = take(nb * 8);
-  L.ldrop = take(learned ? nb * LD_Q * 16 : 0);
+  const int64_t S = 2 * (int64_t)dmax + 1;
+  L.bmask = take(nb * S * S * S * 16);
   L.rkey = take(np * 8);
   L.rsrc = take(np * 4);
   L.rl = take(np * 4);
@@ -635,7 +671,7 @@ bool apply_uses_src_path(const Operator &op, const mra_apply_opts &o) {
 }
 
 size_t apply_workspace_bytes(const Operator &op, const mra_apply_opts &o, int64_t n_in) {
-  return make_layout(n_in, apply_max_records(op, o, n_in), o.screen == MRA_SCREEN_LEARNED,
+  return make_layout(n_in, apply_max_records(op, o, n_in), apply_max_disp(op, o),
                      apply_uses_src_path(op, o)).total;
 }
 
@@ -645,7 +681,7 @@ struct WsPtrs {
   int *dstop;
   int64_t *cnt, *off, *bkept, *bscr, *blearned;
   double *bskip, *blbound;
-  uint64_t *ldrop;
+  uint64_t *bmask;
   int *btrunc;
   uint64_t *rkey, *skey, *rmask, *dkey;
   int *rsrc, *rl, *pin, *pout, *head, *did;
@@ -670,7 +706,7 @@ static WsPtrs carve(const Layout &L, void *ws) {
   p.btrunc = (int *)(w + L.trunc);
   p.blearned = (int64_t *)(w + L.learned);
   p.blbound = (double *)(w + L.lbound);
-  p.ldrop = (uint64_t *)(w + L.ldrop);
+  p.bmask = (uint64_t *)(w + L.bmask);
   p.rkey = (uint64_t *)(w + L.rkey);
   p.skey = (uint64_t *)(w + L.skey);
   p.rsrc = (int *)(w + L.rsrc);
@@ -742,11 +778,14 @@ static int screen_run(const Operator &op, const mra_tree_view &in, const mra_app
   }
   a.box_learned = w.blearned;
   a.box_lbound = w.blbound;
-  a.learned_drop = w.ldrop;
+  a.box_mask = w.bmask;
   a.nfunc = nfunc;
   a.fn_off = w.fnoff;
   const size_t ssm = a.mlp ? (size_t)MLP_NALL * sizeof(float) : 0;
-  screen_kernel<0><<<counted(gboxes), 32 * wpb, ssm, s>>>(a);
+  if (a.mlp)
+    screen_kernel<0, true><<<counted(gboxes), 32 * wpb, ssm, s>>>(a);
+  else
+    screen_kernel<0, false><<<counted(gboxes), 32 * wpb, 0, s>>>(a);
   MRA_CUDA_TRY(cudaGetLastError());
   void *tmp = w.tmp;
   size_t tmpb = w.tmpb;
@@ -755,7 +794,7 @@ static int screen_run(const Operator &op, const mra_tree_view &in, const mra_app
     fixed_count_check_kernel<<<counted(1), 1, 0, s>>>(w.off, w.cnt, n_in, fx->P, d_err, fx->status);
     MRA_CUDA_TRY(cudaGetLastError());
     if (fx->P > 0) {
-      screen_kernel<1><<<counted(gboxes), 32 * wpb, ssm, s>>>(a);
+      screen_kernel<1><<<counted(gboxes), 32 * wpb, 0, s>>>(a);
       MRA_CUDA_TRY(cudaGetLastError());
     }
     *P_out = fx->P;
@@ -817,7 +856,7 @@ static int screen_run(const Operator &op, const mra_tree_view &in, const mra_app
     }
   }
   if (P > 0) {
-    screen_kernel<1><<<counted(gboxes), 32 * wpb, ssm, s>>>(a);
+    screen_kernel<1><<<counted(gboxes), 32 * wpb, 0, s>>>(a);
     MRA_CUDA_TRY(cudaGetLastError());
   }
   *P_out = P;
@@ -832,7 +871,7 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
   const int64_t n_in = in.n;
   const int64_t Pmax = apply_max_records(op, o, n_in);
   const bool src_path = apply_uses_src_path(op, o);
-  Layout L = make_layout(n_in, Pmax, o.screen == MRA_SCREEN_LEARNED, src_path);
+  Layout L = make_layout(n_in, Pmax, apply_max_disp(op, o), src_path);
   if (ws_bytes < L.total)
     return fail(MRA_ERR_CAPACITY, "mra_apply: workspace of %zu bytes < %zu needed", ws_bytes, L.total);
   WsPtrs W = carve(L, ws);
@@ -953,7 +992,9 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
     float *partial = fx ? fx->partial : nullptr;
     if (!fx) MRA_CUDA_TRY(pool_malloc((void **)&partial, (size_t)P * k3 * sizeof(float), s));
     if (!partial) return fail(MRA_ERR_ARG, "mra_apply: no partial-sum buffer for the recorded apply");
-    rc = apply_src_run(op, in, o, out, wk, dap, partial, s);
+    int64_t passes = 0;
+    rc = apply_src_run(op, in, o, out, wk, dap, partial, s, &passes);
+    if (stats && rc == MRA_OK) stats->mma_passes = passes;
     if (!fx) cudaFreeAsync(partial, s);
     if (rc != MRA_OK) return rc;
   } else {
@@ -1105,7 +1146,7 @@ int log_terms_run(const Operator &op, const mra_tree_view &in, const mra_apply_o
   const int64_t n_in = in.n;
   if (n_in == 0 || max_terms <= 0) return MRA_OK;
   const int64_t Pmax = apply_max_records(op, o, n_in);
-  Layout L = make_layout(n_in, Pmax, o.screen == MRA_SCREEN_LEARNED);
+  Layout L = make_layout(n_in, Pmax, apply_max_disp(op, o));
   if (ws_bytes < L.total)
     return fail(MRA_ERR_CAPACITY, "mra_log_terms: workspace of %zu bytes < %zu needed", ws_bytes, L.total);
   WsPtrs W = carve(L, ws);

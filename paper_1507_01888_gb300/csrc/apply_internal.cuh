@@ -54,8 +54,10 @@ size_t split_workspace_bytes(int64_t P);
 // its scratch, and the run (dap: the records' |l|_inf range per absolute level)
 bool src_path_supported(int k, int max_rec_disp);
 size_t src_workspace_bytes(int64_t n_in);
+// *passes (when not null, and not in graph mode): the kernel's passes, each one set of stage-1,
+// 2 and 3 MMAs
 int apply_src_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts &o, mra_tree_view &out,
-                  const ApplyWork &wk, const int *dap, float *partial, cudaStream_t s);
+                  const ApplyWork &wk, const int *dap, float *partial, cudaStream_t s, int64_t *passes = nullptr);
 // whether an apply with these options runs the source-stationary kernel (its partial sums need
 // P k^3 floats besides the workspace)
 bool apply_uses_src_path(const Operator &op, const mra_apply_opts &o);

@@ -79,6 +79,7 @@ struct SrcArgs {
   const int *n_tiles;           // device count
   int *tile_ctr;                // next tile (zero before the launch)
   float *partial;               // [n_rec][k^3]
+  unsigned long long *pass_ctr; // passes of all CTAs (each CTA adds its own once)
   int *err;
   int inject_stall;             // test hook: the CTA that takes tile 0 never issues the copies of its first term
   int join;                     // terms summed in D3 by the stage-3 MMAs before one flush (one-source tiles)
@@ -470,6 +471,7 @@ __global__ void __launch_bounds__(PLAIN ? SRC_THREADS + 32 : SRC_THREADS, 2) app
       tc::mma_commit(bd);
       tc::mbar_wait(bd, 0, WAIT_CYCLES);
     }
+    if (tid == 0 && it > 0) atomicAdd(a.pass_ctr, (unsigned long long)it);
   } else if (wg == 1) {
     // ======================================================= warpgroup 1
     // where this thread's stage-2 output row (i, jz, ix) goes in the stage-3 operand:
@@ -810,7 +812,7 @@ size_t src_workspace_bytes(int64_t n_in) {
 }
 
 int apply_src_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts &o, mra_tree_view &out,
-                  const ApplyWork &wk, const int *dap, float *partial, cudaStream_t s) {
+                  const ApplyWork &wk, const int *dap, float *partial, cudaStream_t s, int64_t *passes) {
   const int k = op.k, k3 = k * k * k;
   const int G = src_g(k);
   const int64_t P = wk.P, nd = wk.n_dest, n_in = in.n;
@@ -825,6 +827,7 @@ int apply_src_run(const Operator &op, const mra_tree_view &in, const mra_apply_o
   int *small = (int *)w; w += al(4 * (MRA_MAX_LEVEL + 2) * 4);
   int *lev_first = small, *tile_base = small + (MRA_MAX_LEVEL + 2), *n_tiles = small + 2 * (MRA_MAX_LEVEL + 2);
   int *tile_ctr = n_tiles + 1, *err = n_tiles + 2;
+  unsigned long long *pass_ctr = (unsigned long long *)(small + 3 * (MRA_MAX_LEVEL + 2));  // 8-byte aligned
   void *tmp = w;
   size_t tmpb = wk.split_ws_bytes - (size_t)(w - (char *)wk.split_ws);
   const size_t tile_bytes = (size_t)(nb + 2 * SRC_MAX_G + 64) * SRC_MAX_G * 4;
@@ -861,6 +864,7 @@ int apply_src_run(const Operator &op, const mra_tree_view &in, const mra_apply_o
   a.tile_ctr = tile_ctr;
   a.partial = partial;
   a.err = err;
+  a.pass_ctr = pass_ctr;
   a.inject_stall = take_injected_stall() ? 1 : 0;
   a.join = o.join > 0 ? o.join : 2;
   a.compensated = o.sums == MRA_SUMS_COMPENSATED ? 1 : 0;
@@ -910,8 +914,11 @@ int apply_src_run(const Operator &op, const mra_tree_view &in, const mra_apply_o
     return MRA_OK;
   }
   int herr = 0;
+  unsigned long long hpass = 0;
   MRA_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MRA_CUDA_TRY(cudaMemcpyAsync(&hpass, pass_ctr, sizeof(hpass), cudaMemcpyDeviceToHost, s));
   MRA_CUDA_TRY(cudaStreamSynchronize(s));
+  if (passes) *passes = (int64_t)hpass;
   if (herr == 1) return fail(MRA_ERR_TIMEOUT, "split apply: a tensor-core completion wait gave up");
   if (herr) return fail(MRA_ERR_ARG, "split apply: inconsistent work list (%d)", herr);
   return MRA_OK;

@@ -860,6 +860,7 @@ extern "C" int mra_apply_ns(const mra_operator *h, const mra_operator *hns, cons
     acc.skipped_bound += st.skipped_bound;
     acc.kernel_ms += st.kernel_ms;
     acc.main_kernel_ms += st.main_kernel_ms;
+    acc.mma_passes += st.mma_passes;
     acc.kernel = st.kernel;
     acc.algo_flops += st.algo_flops;
     for (int q = 0; q <= MRA_MAX_LEVEL; ++q) {
@@ -1085,6 +1086,7 @@ extern "C" int mra_apply_ns_tree(const mra_operator *h, const mra_operator *hns,
     acc.skipped_bound += st.skipped_bound;
     acc.kernel_ms += st.kernel_ms;
     acc.main_kernel_ms += st.main_kernel_ms;
+    acc.mma_passes += st.mma_passes;
     acc.kernel = st.kernel;
     acc.algo_flops += st.algo_flops;
     for (int q = 0; q <= MRA_MAX_LEVEL; ++q) {

@@ -92,7 +92,7 @@ class ApplyStats(ctypes.Structure):
                 ("terms_learned_skipped", ctypes.c_int64), ("learned_skipped_bound", ctypes.c_double),
                 ("algo_flops", ctypes.c_double), ("level_sources", ctypes.c_int64 * 20),
                 ("level_terms_kept", ctypes.c_int64 * 20), ("kernel", ctypes.c_int32),
-                ("main_kernel_ms", ctypes.c_double)]
+                ("main_kernel_ms", ctypes.c_double), ("mma_passes", ctypes.c_int64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("level_")}

@@ -139,6 +139,11 @@ def test_source_stationary_with_wide_operator_and_two_shells(mra, k):
     dst, _ = mra.apply(op, tree, split_opts(mra, split_kernel=mra.SPLIT_DEST, **kw))
     gk, gc = src.host()
     assert st["terms_kept"] == ref.terms
+    # every pass (tile, l_x, l_y, l_z window, term) has a kept term and serves at most three l_z
+    # of each of the tile's G sources
+    G = {4: 8, 6: 3, 8: 2, 10: 1}[k]
+    assert st["kernel"] == mra.KERNEL_SPLIT_SRC
+    assert 0 < st["mma_passes"] <= st["terms_kept"] <= 3 * G * st["mma_passes"]
     assert (gk == ref.keys).all()
     assert rel_l2(gc, ref.coeffs) <= TOL_MIXED
     assert mra.compare(src, dst)["rel_l2"] <= TOL_MIXED
