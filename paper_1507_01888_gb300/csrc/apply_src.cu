@@ -827,7 +827,12 @@ int apply_src_run(const Operator &op, const mra_tree_view &in, const mra_apply_o
   int *small = (int *)w; w += al(4 * (MRA_MAX_LEVEL + 2) * 4);
   int *lev_first = small, *tile_base = small + (MRA_MAX_LEVEL + 2), *n_tiles = small + 2 * (MRA_MAX_LEVEL + 2);
   int *tile_ctr = n_tiles + 1, *err = n_tiles + 2;
-  unsigned long long *pass_ctr = (unsigned long long *)(small + 3 * (MRA_MAX_LEVEL + 2));  // 8-byte aligned
+  // the pass counter: bytes 256..263 of the zeroed scratch (its 45 ints end at byte 180; the
+  // scratch is 256-byte aligned and 336 bytes long), so 8-byte aligned for the 64-bit atomic
+  static_assert(3 * (MRA_MAX_LEVEL + 2) * 4 <= 256 && 256 + 8 <= 4 * (MRA_MAX_LEVEL + 2) * 4,
+                "pass counter inside the scratch, after its ints");
+  unsigned long long *pass_ctr = (unsigned long long *)((char *)small + 256);
+  if (((uintptr_t)small & 255) != 0) return fail(MRA_ERR_ARG, "split apply: workspace not 256-byte aligned");
   void *tmp = w;
   size_t tmpb = wk.split_ws_bytes - (size_t)(w - (char *)wk.split_ws);
   const size_t tile_bytes = (size_t)(nb + 2 * SRC_MAX_G + 64) * SRC_MAX_G * 4;
