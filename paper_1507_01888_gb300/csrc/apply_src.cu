@@ -853,6 +853,7 @@ int apply_src_run(const Operator &op, const mra_tree_view &in, const mra_apply_o
   a.k = k;
   a.M = op.M;
   a.P = o.pieces;
+  if (a.P < 2 || a.P > 3) return fail(MRA_ERR_ARG, "split apply: pieces must be 2 or 3");
   a.Bsplit = (const unsigned char *)op.d_Rsplit;
   a.Bzpack = a.Bsplit + (size_t)2 * op.n_blocks * BSTAGE_BYTES;
   a.Dlev = op.d_D;
