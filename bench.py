@@ -56,7 +56,7 @@ def split_dtype(pieces, opts=None, k=0):
     from paper_1507_01888_gb300 import mra
     if opts is not None and opts.split_kernel != mra.SPLIT_DEST and k in (4, 6, 8, 10):
         sums = "compensated f32 (sum + Kahan correction)" if opts.sums == mra.SUMS_COMPENSATED else "plain f32"
-        join = (max(int(opts.join), 1) if opts.join else 2) if k * k > 64 else 1  # joins need one source per tile
+        join = int(opts.join) if opts.join else (2 if k * k > 64 else 1)  # 0: 2 in one-source tiles only
         return (f"bf16x{pieces}-split MMAs with f32 accumulation in tensor memory (up to {join} Gaussian terms "
                 f"per accumulation); each (source, displacement) sum over terms in {sums}, stored as f32; "
                 f"per-destination sums of those in f32 pairs (error-free TwoSum, ~48 bits), formed into f64")

@@ -129,10 +129,13 @@ typedef struct {
                        where it applies (even k from 4 to 10, records with |l|_inf <= 2) and the
                        destination-stationary one elsewhere; MRA_SPLIT_DEST (1) always the
                        destination-stationary one (tile_variant picks its shape) */
-  int join;  /* source-stationary kernel, one source per tile (k >= 9 here: k = 10): consecutive
-                terms of a record group with the same kept records are summed in the tensor-memory
+  int join;  /* source-stationary kernel: consecutive terms of a record group that the tile's
+                records keep alike (the same records keep both) are summed in the tensor-memory
                 accumulator, up to `join` of them (1..8), before one flush adds them into the record
-                sums; 0 = 2.  More terms per flush cost accuracy (the accumulator truncates) */
+                sums.  0: 2 in tiles of one source (k = 10) and 1 in tiles of several, whose results
+                then do not depend on which sources share a tile (batched or partitioned applies
+                equal the single ones bit for bit); a value >= 1 applies to every tile.  More terms
+                per flush cost accuracy (the accumulator truncates) */
   int sums;  /* source-stationary kernel, each record's sum over terms: MRA_SUMS_PLAIN (0, an FP32
                 sum; a ninth warp then issues stage 3) or MRA_SUMS_COMPENSATED (1, FP32 sum + Kahan
                 correction: more accurate, more registers, eight warps) */

@@ -4,7 +4,9 @@ apply on the caller's own input.
 Candidates (all compiled into the library; nothing is generated at run time):
   * the source-stationary kernel (even k from 4 to 10, records with |l|_inf <= 2), with its
     schedule knobs: `join`, the terms summed in the tensor-memory accumulator per flush (1 to 4;
-    more is faster and less accurate, since the accumulator truncates), `sums`, compensated or
+    more is faster and less accurate, since the accumulator truncates; at k < 10, where tiles
+    hold several sources, a join > 1 makes the result depend on which sources share a tile, so
+    batched or partitioned applies then match the single ones to rounding, not bit for bit), `sums`, compensated or
     plain FP32 record sums, and `ahead`, how many terms ahead the block copies run;
   * the destination-stationary kernel's tile shapes: four 128-row tiles per CTA with one CTA per
     SM (tile_variant 0), two tiles with two CTAs per SM (1, k >= 4) and one tile with four CTAs
@@ -26,8 +28,7 @@ def candidates(k: int, src_ok: bool):
     """(name, option overrides) pairs to time, most accurate first."""
     out = []
     if src_ok:
-        # terms are joined in tensor memory only in tiles of one source (k >= 9 here)
-        for join in ((1, 2, 3, 4) if k * k > 64 else (1,)):
+        for join in (1, 2, 3, 4):
             for sums in (mra.SUMS_COMPENSATED, mra.SUMS_PLAIN):
                 out.append((f"src join={join} sums={'comp' if sums == mra.SUMS_COMPENSATED else 'plain'}",
                             dict(split_kernel=mra.SPLIT_AUTO, join=join, sums=sums, ahead=2)))

@@ -82,7 +82,8 @@ struct SrcArgs {
   unsigned long long *pass_ctr; // passes of all CTAs (each CTA adds its own once)
   int *err;
   int inject_stall;             // test hook: the CTA that takes tile 0 never issues the copies of its first term
-  int join;                     // terms summed in D3 by the stage-3 MMAs before one flush (one-source tiles)
+  int join;                     // terms summed in D3 by the stage-3 MMAs before one flush
+  int join_all;                 // 1: join in tiles of several sources too (else those flush every term)
   int compensated;              // record sums: 1 = FP32 sum + Kahan correction, 0 = plain FP32 sum
   int ahead;                    // block copies run this many terms ahead (1 .. SRC_MAX_AHEAD)
   int64_t n_src, n_rec, n_blocks;
@@ -225,7 +226,9 @@ __global__ void __launch_bounds__(PLAIN ? SRC_THREADS + 32 : SRC_THREADS, 2) app
   auto wg_arrive_issuer = [&]() { asm volatile("bar.arrive 3, 160;" ::: "memory"); };
   const int mrow = quarter * 32 + lane;  // this thread's row of the tile (lane of tensor memory)
   const int ahead = max(1, min(a.ahead, SRC_MAX_AHEAD));
-  const int join = G == 1 ? max(1, min(a.join, SRC_MAX_JOIN)) : 1;
+  // tiles of several sources join only when asked: a join depends on all the tile's records,
+  // so it would make a result depend on which sources share its tile
+  const int join = (G == 1 || a.join_all) ? max(1, min(a.join, SRC_MAX_JOIN)) : 1;
 
   if (wg == 0) {
     // ======================================================= warpgroup 0
@@ -873,6 +876,7 @@ int apply_src_run(const Operator &op, const mra_tree_view &in, const mra_apply_o
   a.pass_ctr = pass_ctr;
   a.inject_stall = take_injected_stall() ? 1 : 0;
   a.join = o.join > 0 ? o.join : 2;
+  a.join_all = o.join > 0 ? 1 : 0;
   a.compensated = o.sums == MRA_SUMS_COMPENSATED ? 1 : 0;
   a.ahead = o.ahead > 0 ? o.ahead : 2;
   a.n_src = n_in;

@@ -175,6 +175,27 @@ def test_source_stationary_output_buffer_8_bytes_off_alignment(mra):
     assert np.array_equal(gc, rc)
 
 
+@pytest.mark.parametrize("k", [6, 8])
+def test_source_stationary_joins_in_tiles_of_several_sources(mra, k):
+    """Tiles of several sources (k = 6, 8) flush every term by default, so the default equals
+    join = 1 bit for bit; an explicit join sums up to that many terms in tensor memory in those
+    tiles too and stays within the parity bar of the oracle."""
+    keys, coeffs = W.random_tree_coeffs(150, k, 3, seed=60 + k)
+    op = mra.Operator(0, 20, k, 16.0, 0, 3, max_disp=1, fit_eps=1e-6)
+    fit = oracle_fit(op)
+    ref = O.apply(keys, coeffs, fit["c"], fit["t"], 16.0, stencil=1, tau=0.0)
+    tree = mra.Tree.from_host(keys, coeffs, 16.0)
+    out0, _ = mra.apply(op, tree, split_opts(mra, stencil=1))
+    out1, _ = mra.apply(op, tree, split_opts(mra, stencil=1, join=1))
+    out4, st4 = mra.apply(op, tree, split_opts(mra, stencil=1, join=4))
+    assert st4["kernel"] == mra.KERNEL_SPLIT_SRC
+    assert np.array_equal(out0.host()[1], out1.host()[1])
+    gk, gc = out4.host()
+    assert (gk == ref.keys).all()
+    assert rel_l2(gc, ref.coeffs) <= TOL_MIXED
+    assert not np.array_equal(gc, out1.host()[1])  # the joins took effect
+
+
 def test_split_two_pieces_is_coarser(mra):
     """Two BF16 pieces carry ~16 significant bits: the error grows to ~1e-5 but stays bounded."""
     keys, coeffs = W.random_tree_coeffs(60, 8, 3, seed=12)
