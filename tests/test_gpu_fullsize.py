@@ -57,7 +57,7 @@ def check_sample(w, fit, ok, oc, gk, gc, n, seed, tol=TOL_MIXED):
 
 
 def test_batched_64_functions_full_size(mra):
-    """Poisson M=40 k=8, 64 functions (1,057,400 boxes) in one batched apply, one-tile shape."""
+    """Poisson M=40 k=8, 64 functions (1,057,400 boxes) in one batched apply."""
     w = W.poisson_batched_64()
     rng = np.random.default_rng(3)
     picked = sorted(int(f) for f in rng.choice(len(w.funcs), 3, replace=False))
@@ -74,9 +74,10 @@ def test_batched_64_functions_full_size(mra):
     op = mra.Operator(w.kernel, w.M, w.k, w.L, int(lv.min()), int(lv.max()), max_disp=w.max_disp, mu=w.mu,
                       fit_eps=w.fit_eps)
     fit = oracle_fit(op)
+    # the benchmark's launch: one graph per step, the schedule its tuner picks (four terms per flush)
     opts = mra.make_opts(precision=mra.PREC_SPLIT_BF16, screen=mra.SCREEN_NORM, tau=w.tau, stencil=w.stencil,
-                         max_disp=w.max_disp, tile_variant=2)
-    g = mra.ApplyGraph(op, big, opts, offsets=offs)  # the benchmark's launch: one graph per step
+                         max_disp=w.max_disp, join=4)
+    g = mra.ApplyGraph(op, big, opts, offsets=offs)
     g.launch()
     g.status()
     gk_all, gc_all = g.out.host()
@@ -88,7 +89,7 @@ def test_batched_64_functions_full_size(mra):
 
 
 def test_learned_workload_tree_full_size(mra):
-    """BSH mu=0.5 M=80 k=10, 133,456 boxes (the learned-screen workload's tree), one-tile shape."""
+    """BSH mu=0.5 M=80 k=10, 133,456 boxes (the learned-screen workload's tree)."""
     w = W.bsh_learned_k10()
     t, ok, oc = project_both(mra, w, w.funcs[0])
     lv = (ok >> np.uint64(57)).astype(int)
@@ -96,7 +97,7 @@ def test_learned_workload_tree_full_size(mra):
                       fit_eps=w.fit_eps)
     fit = oracle_fit(op)
     opts = mra.make_opts(precision=mra.PREC_SPLIT_BF16, screen=mra.SCREEN_NORM, tau=w.tau, stencil=w.stencil,
-                         max_disp=w.max_disp, tile_variant=2)
+                         max_disp=w.max_disp, join=4)  # the schedule the benchmark's tuner picks
     out, _ = mra.apply(op, t, opts)
     gk, gc = out.host()
     check_sample(w, fit, ok, oc, gk, gc, 24, seed=7)

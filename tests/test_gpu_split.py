@@ -97,18 +97,19 @@ def test_split_shells_and_screen_adaptive(mra):
     assert rel_l2(gc, ref.coeffs) <= TOL_MIXED
 
 
-@pytest.mark.parametrize("kern,tile_variant", [(0, 0), (1, 0), (1, 2)])
-def test_split_full_size_vs_fp64_and_oracle(mra, kern, tile_variant):
+@pytest.mark.parametrize("kern,tile_variant,join", [(0, 0, 0), (0, 0, 4), (1, 0, 0), (1, 2, 0)])
+def test_split_full_size_vs_fp64_and_oracle(mra, kern, tile_variant, join):
     """BSH M=60 adaptive k=10 (17,200 boxes): split vs FP64 GPU on every box, vs the oracle on a
-    sample; the source-stationary kernel the benchmark times, and the destination-stationary
-    kernel's four-tile and one-tile shapes."""
+    sample; the source-stationary kernel (its default schedule and four terms per flush, the one
+    the benchmark's tuner picks), and the destination-stationary kernel's four-tile and one-tile
+    shapes."""
     w = W.bsh_m60_adaptive_k10()
     ok, oc, _ = O.project(w.funcs[0], w.k, w.L, thresh=w.thresh, init_level=w.init_level, max_level=w.max_level)
     op = mra.Operator(w.kernel, w.M, w.k, w.L, 2, 19, max_disp=w.max_disp, mu=w.mu, fit_eps=w.fit_eps)
     fit = oracle_fit(op)
     tree = mra.Tree.from_host(ok, oc, w.L)
     kw = dict(stencil=w.stencil, max_disp=w.max_disp, screen=mra.SCREEN_NORM, tau=w.tau)
-    sp, _ = mra.apply(op, tree, split_opts(mra, tile_variant=tile_variant, split_kernel=kern, **kw))
+    sp, _ = mra.apply(op, tree, split_opts(mra, tile_variant=tile_variant, split_kernel=kern, join=join, **kw))
     f64, _ = mra.apply(op, tree, mra.make_opts(**kw))
     cmp = mra.compare(sp, f64)
     assert cmp["n_only_test"] == 0 and cmp["n_only_ref"] == 0
@@ -116,6 +117,40 @@ def test_split_full_size_vs_fp64_and_oracle(mra, kern, tile_variant):
     gk, gc = sp.host()
     rng = np.random.default_rng(11)
     sample = np.sort(rng.choice(gk, 80, replace=False))
+    ref = O.apply(ok, oc, fit["c"], fit["t"], w.L, stencil=w.stencil, max_disp=w.max_disp, tau=w.tau,
+                  sample_keys=sample)
+    pos = np.searchsorted(gk, ref.keys)
+    assert (gk[pos] == ref.keys).all()
+    assert rel_l2(gc[pos], ref.coeffs) <= TOL_MIXED
+
+
+def test_headline_graph_replay_with_the_tuned_schedule(mra):
+    """The benchmark's timed step on the BSH M=60 k=10 tree: the apply recorded as one CUDA graph
+    with the schedule its tuner picks (source-stationary kernel, four terms per flush, plain
+    record sums), replayed twice; every replay equals a plain apply bit for bit, and the result
+    matches the FP64 apply and a sample of the oracle's destinations."""
+    w = W.bsh_m60_adaptive_k10()
+    ok, oc, _ = O.project(w.funcs[0], w.k, w.L, thresh=w.thresh, init_level=w.init_level, max_level=w.max_level)
+    op = mra.Operator(w.kernel, w.M, w.k, w.L, 2, 19, max_disp=w.max_disp, mu=w.mu, fit_eps=w.fit_eps)
+    fit = oracle_fit(op)
+    tree = mra.Tree.from_host(ok, oc, w.L)
+    kw = dict(stencil=w.stencil, max_disp=w.max_disp, screen=mra.SCREEN_NORM, tau=w.tau)
+    opts = split_opts(mra, join=4, sums=mra.SUMS_PLAIN, ahead=2, **kw)
+    plain, st = mra.apply(op, tree, opts)
+    assert st["kernel"] == mra.KERNEL_SPLIT_SRC
+    g = mra.ApplyGraph(op, tree, opts)
+    for _ in range(2):
+        g.launch()
+        g.status()
+        gk, gc = g.out.host()
+        pk, pc = plain.host()
+        assert (gk == pk).all() and np.array_equal(gc, pc)
+    f64, _ = mra.apply(op, tree, mra.make_opts(**kw))
+    cmp = mra.compare(g.out, f64)
+    assert cmp["n_only_test"] == 0 and cmp["n_only_ref"] == 0
+    assert cmp["rel_l2"] <= 2e-7  # the tuner's error budget
+    rng = np.random.default_rng(12)
+    sample = np.sort(rng.choice(gk, 60, replace=False))
     ref = O.apply(ok, oc, fit["c"], fit["t"], w.L, stencil=w.stencil, max_disp=w.max_disp, tau=w.tau,
                   sample_keys=sample)
     pos = np.searchsorted(gk, ref.keys)
