@@ -247,6 +247,7 @@ __global__ void __launch_bounds__(256, LEARNED ? 1 : 2) screen_kernel(ScreenArgs
           const uint64_t tkey = make_key(n, x + lx, y + ly, z + lz);
           const bool owned = a.dest_hi == 0 || (tkey >= a.dest_lo && tkey < a.dest_hi);
           uint64_t mask[2] = {0ull, 0ull};
+          bool norm_kept = false;  // any term of this l passes the norm screen
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const int m0 = 32 * j;
@@ -282,7 +283,11 @@ __global__ void __launch_bounds__(256, LEARNED ? 1 : 2) screen_kernel(ScreenArgs
             }
             unsigned bal = __ballot_sync(0xffffffffu, keep);
             mask[j >> 1] |= (uint64_t)bal << (m0 & 63);
+            if (mlp) norm_kept |= __ballot_sync(0xffffffffu, keep || dropped_by_model) != 0u;
           }
+          // the shells follow the norm screen: the learned screen removes terms it kept, and a shell
+          // whose kept terms it all removes does not end the shells (their terms count as its drops)
+          if (norm_kept) any = 1;
           if (owned && lane == 0) {
             uint64_t *mk = mask_at(lx, ly, lz);
             mk[0] = mask[0];

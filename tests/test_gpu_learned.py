@@ -215,3 +215,37 @@ def test_learned_screen_gain_on_a_held_out_function(mra):
     err = float(np.sqrt(((gc[pos] - ref.coeffs) ** 2).sum() / (ref.coeffs ** 2).sum()))
     print(f"FP64 apply with the learned screen vs the oracle: {err:.2e} (threshold {thresh:g})")
     assert err <= thresh
+
+
+def test_learned_screen_with_shells_wider_than_two(mra):
+    """Shells up to |l|_inf = 3: the network is evaluated per term inside the counting pass (the
+    drop bits by |l|^2 class cover |l|_inf <= 2 only).  What the learned screen drops is exactly
+    what the norm screen kept minus what it keeps, and the result moves from the norm-screen apply
+    by at most the norm bound of what it dropped."""
+    from paper_1507_01888_gb300 import learned
+    k, L, thresh, tau = 6, 32.0, 1e-4, 1e-6
+    funcs = [W.gaussian_sum(3, 1.0, 300.0, seed=760 + i, centre_box=15.0) for i in range(3)]
+    trees = [mra.project(f, k, L, thresh=thresh, init_level=2, max_level=10) for f in funcs]
+    op = mra.Operator(1, 30, k, L, 1, 10, max_disp=3, mu=1.0, fit_eps=1e-6)
+    base = mra.make_opts(screen=mra.SCREEN_NORM, tau=tau, stencil=mra.STENCIL_SHELLS, max_disp=3)
+    model, info = learned.train_screen(op, trees[:2], base, terms_per_tree=20000, steps=400, batch=1024,
+                                       lr=3e-3, seed=5, quantile=1.0)
+    test_tree = trees[2]
+    plain, st_plain = mra.apply(op, test_tree, base)
+    for precision in (mra.PREC_FP64, mra.PREC_SPLIT_BF16):
+        popts = mra.copy_opts(base)
+        popts.precision = precision
+        ref, _ = mra.apply(op, test_tree, popts)
+        lopts = mra.make_opts(precision=precision, screen=mra.SCREEN_LEARNED, tau=tau,
+                              stencil=mra.STENCIL_SHELLS, max_disp=3, mlp=model, delta=0.3)
+        out, st = mra.apply(op, test_tree, lopts)
+        assert st["terms_kept"] + st["terms_learned_skipped"] == st_plain["terms_kept"]
+        assert st["terms_learned_skipped"] > 0
+        gk, gc = out.host()
+        rk, rc = ref.host()
+        common = np.isin(rk, gk)
+        pos = np.searchsorted(gk, rk[common])
+        err = np.sqrt(((gc[pos] - rc[common]) ** 2).sum() + (rc[~common] ** 2).sum())
+        rn = np.sqrt((rc ** 2).sum())
+        slack = 1e-12 if precision == mra.PREC_FP64 else 2e-6  # the split path's own rounding
+        assert err <= st["learned_skipped_bound"] * (1 + 1e-9) + slack * rn
