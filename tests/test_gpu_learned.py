@@ -249,3 +249,58 @@ def test_learned_screen_with_shells_wider_than_two(mra):
         rn = np.sqrt((rc ** 2).sum())
         slack = 1e-12 if precision == mra.PREC_FP64 else 2e-6  # the split path's own rounding
         assert err <= st["learned_skipped_bound"] * (1 + 1e-9) + slack * rn
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_learned_screen_in_graph_batched_and_partitioned_applies(mra, precision):
+    """The learned screen inside the other launch forms: a CUDA-graph replay equals the plain
+    learned apply bit for bit; a batched learned apply of two functions equals their single
+    learned applies bit for bit; two destination ranges with their halos make up the whole
+    learned apply bit for bit, with each kept and each dropped term counted once."""
+    from paper_1507_01888_gb300 import learned
+    from paper_1507_01888_gb300 import partition as PT
+    k, L, thresh, tau = 6, 32.0, 1e-4, 1e-6
+    funcs = [W.gaussian_sum(3, 1.0, 300.0, seed=800 + i, centre_box=15.0) for i in range(4)]
+    trees = [mra.project(f, k, L, thresh=thresh, init_level=2, max_level=10) for f in funcs]
+    op = mra.Operator(1, 30, k, L, 1, 10, max_disp=1, mu=1.0, fit_eps=1e-6)
+    base = mra.make_opts(screen=mra.SCREEN_NORM, tau=tau, stencil=mra.STENCIL_SHELLS, max_disp=1)
+    model, info = learned.train_screen(op, trees[:2], base, terms_per_tree=20000, steps=300, batch=1024,
+                                       lr=3e-3, seed=3, quantile=1.0)
+    lopts = mra.make_opts(precision=precision, screen=mra.SCREEN_LEARNED, tau=tau, stencil=mra.STENCIL_SHELLS,
+                          max_disp=1, mlp=model, delta=0.3)
+    t2, t3 = trees[2], trees[3]
+    ref, st = mra.apply(op, t2, lopts)
+    assert st["terms_learned_skipped"] > 0
+    rk, rc = ref.host()
+    # graph replay
+    g = mra.ApplyGraph(op, t2, lopts)
+    g.out.coeffs.zero_()
+    g.launch()
+    g.status()
+    gk, gc = g.out.host()
+    assert (gk == rk).all() and np.array_equal(gc, rc)
+    # batched
+    big, offs = mra.concat_trees([t2, t3])
+    ba = mra.BatchedApplier(op, big, offs, lopts)
+    out, out_offs = ba(big)
+    bk, bc = out.host()
+    for i, t in enumerate((t2, t3)):
+        sk, sc = mra.apply(op, t, lopts)[0].host()
+        a, b = out_offs[i], out_offs[i + 1]
+        assert (bk[a:b] == sk).all() and np.array_equal(bc[a:b], sc)
+    # two destination ranges
+    keys, coeffs = t2.host()
+    pk, pc, kept, dropped = [], [], 0, 0
+    for lo, hi in PT.split_ranges(keys, 2):
+        halo = PT.halo_mask(keys, lo, hi, 1)
+        sub = mra.Tree.from_host(keys[halo], coeffs[halo], L)
+        o = mra.copy_opts(lopts)
+        o.dest_lo, o.dest_hi = lo, hi
+        part, stp = mra.apply(op, sub, o)
+        k_, c_ = part.host()
+        pk.append(k_)
+        pc.append(c_)
+        kept += stp["terms_kept"]
+        dropped += stp["terms_learned_skipped"]
+    assert (np.concatenate(pk) == rk).all() and np.array_equal(np.concatenate(pc), rc)
+    assert kept == st["terms_kept"] and dropped == st["terms_learned_skipped"]
