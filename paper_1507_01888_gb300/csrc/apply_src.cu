@@ -17,8 +17,10 @@
 //                window stacked along N                                    -> D3[(i,ix,iy)][(lz, iz)]
 //     so one pass serves up to three terms;
 //   * each record's sum over m (the partial result of source b for destination b + l) stays in
-//     registers as a compensated FP32 sum (a sum and its Kahan correction per coefficient) and
-//     is written once, as FP32, to a partial buffer indexed by the record;
+//     registers, as a plain FP32 sum or a compensated one (a sum and its Kahan correction per
+//     coefficient; the `sums` option), and is written once, as FP32, to a partial buffer indexed
+//     by the record; up to `join` consecutive terms kept by the same records are first summed by
+//     the stage-3 MMAs in the tensor-memory accumulator;
 //   * a second kernel sums the partials of every destination in FP32 pairs (error-free
 //     TwoSum additions, about 48 bits), in the order of the records sorted on the destination
 //     key, and writes each destination once in FP64 (no atomics on results).
@@ -28,8 +30,9 @@
 //
 // Pipeline (two warpgroups, as in the destination-stationary kernel): warpgroup 0 stages the
 // sources, turns D1 into the stage-2 operand and issues stages 1 and 2 and the block copies;
-// warpgroup 1 turns D2 into the stage-3 operand, issues stage 3 and adds D3 into the record
-// sums, so the two warpgroups work on consecutive terms.  The kernel is persistent: CTAs take
+// warpgroup 1 turns D2 into the stage-3 operand and adds D3 into the record sums, and stage 3 is
+// issued by a ninth warp (plain sums) or by a thread of warpgroup 1 (compensated sums), so the
+// two warpgroups work on consecutive terms.  The kernel is persistent: CTAs take
 // tiles from a device counter until none are left; tiles come heaviest first.
 #include <cub/cub.cuh>
 
