@@ -36,7 +36,7 @@ import workloads as W  # noqa: E402
 # DRAM bytes (read + written) of one launch of the dominant kernel, from a one-pass ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of this bench's own command, keyed by
 # (workload, kernel).  An entry is removed whenever the kernel changes.
-SPLIT_TRAFFIC = {("bsh_m60_adaptive_k10", "apply_src_kernel"): 69.52e6 + 687.56e6}
+SPLIT_TRAFFIC = {("bsh_m60_adaptive_k10", "apply_src_kernel"): 68.46e6 + 687.48e6}
 
 METRIC = "3D operator-apply boxes/s & % roofline, mixed vs FP64 GPU at 1e-6 rel L2"
 def fixed_schedule(opts, text):
