@@ -179,6 +179,12 @@ def test_source_stationary_with_wide_operator_and_two_shells(mra, k):
     G = {4: 8, 6: 3, 8: 2, 10: 1}[k]
     assert st["kernel"] == mra.KERNEL_SPLIT_SRC
     assert 0 < st["mma_passes"] <= st["terms_kept"] <= 3 * G * st["mma_passes"]
+    # the kernel's own time lies inside the apply's (tile list, kernel, per-destination sums)
+    assert 0 < st["main_kernel_ms"] <= st["kernel_ms"]
+    _, st_d = mra.apply(op, tree, split_opts(mra, split_kernel=mra.SPLIT_DEST, **kw))
+    _, st_f = mra.apply(op, tree, mra.make_opts(**kw))
+    assert st_d["kernel"] == mra.KERNEL_SPLIT_DEST and st_d["mma_passes"] == 0
+    assert st_f["kernel"] == mra.KERNEL_F64 and st_f["main_kernel_ms"] == st_f["kernel_ms"]
     assert (gk == ref.keys).all()
     assert rel_l2(gc, ref.coeffs) <= TOL_MIXED
     assert mra.compare(src, dst)["rel_l2"] <= TOL_MIXED
