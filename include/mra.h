@@ -155,7 +155,9 @@ typedef struct {
   int64_t terms_screened;     /* triples dropped by the screen inside the displacement set */
   int64_t terms_issued;       /* triples the kernel evaluated (kept + tile padding) */
   int64_t sources_truncated;  /* sources whose last allowed shell still kept terms */
-  double skipped_bound;       /* sum of the screen bounds of dropped triples */
+  double skipped_bound;       /* sum of the screen bounds of dropped triples, or an upper bound of
+                                 it: a bound the screen's FP32 log2 filter decided enters as
+                                 2^(its FP32 log2 + 2^-8), at most 0.4% above it */
   double kernel_ms;           /* device time of the apply kernel and the kernels around it that its
                                  result needs (CUDA events on `stream`) */
   int64_t terms_learned_skipped; /* triples the norm screen kept and the learned screen dropped */

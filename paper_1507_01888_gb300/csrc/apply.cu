@@ -4,12 +4,15 @@
 // Work list.  For every source box b (level n) and displacement l in D(b) the
 // screen computes, per Gaussian term m, the bound
 //     B = |c_m| * ||R^n_{m,lx}||_F * ||R^n_{m,ly}||_F * ||R^n_{m,lz}||_F * ||s_b||_F
-// and keeps the term iff B >= tau.  A (b, l) pair with at least one kept term
+// and keeps the term iff B >= tau (the sum of FP32 logs of the five factors decides first, the
+// FP64 product wherever that sum is within its error margin of log2 tau, so every decision is
+// the FP64 product's).  A (b, l) pair with at least one kept term
 // becomes a record {dest key = key(n, b + l), b, l, kept-term mask}.  Records
 // are sorted on the destination key (stable radix sort), so the records of one
 // destination are contiguous; each destination box is then produced by one
 // CTA that gathers its sources and sums their terms in registers, and written
 // exactly once.  No atomics touch the result.
+#include <cmath>
 #include <algorithm>
 
 #include <cub/cub.cuh>
@@ -99,11 +102,31 @@ struct ScreenArgs {
   // ((lx + dmax) S + ly + dmax) S + lz + dmax with S = 2 dmax + 1; pass 1 writes the records
   // from these masks (the same decisions, nothing recomputed)
   uint64_t *box_mask;         // [n_in][S^3][2]
+  // exact filter of the bound in log2 (pass 0): FP32 log2 of every block norm (indexed like N)
+  // and of every |c_m|; a term is decided from the FP32 sum of the five logs when it lies more
+  // than SCREEN_LMARGIN from log2(tau), else from the FP64 product
+  const float *lN, *lc;
+  int lfilter;
+  float ltau_hi, ltau_lo;
   // several functions in one apply: boxes [fn_off[f], fn_off[f+1]) belong to function f,
   // and records sort on (f, level, x, y, z) packed as f<<53 | n<<48 | x<<32 | y<<16 | z
   int nfunc;
   const int64_t *fn_off;
 };
+
+// Margin (in log2) of the screen's FP32 filter.  The five FP32 logs of a bound are each within
+// half an ulp (<= 2^-14 for |log2| < 2048) of the true ones and the four FP32 additions of sums
+// below 2^13 in magnitude each add at most 2^-12: at most 1.3e-3 in all, under the margin, so a
+// term the filter decides is decided as the FP64 product would decide it.
+constexpr float SCREEN_LMARGIN = 1.0f / 256.0f;
+
+// FP32 log2 of the block norms and of |c_m| (-inf for 0), for the screen's filter.
+__global__ void screen_log_tables_kernel(int64_t n_blocks, int M, const double *N, const double *c, float *out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_blocks + M; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = i < n_blocks ? N[i] : fabs(c[i - n_blocks]);
+    out[i] = v > 0.0 ? (float)log2(v) : -INFINITY;
+  }
+}
 
 // Sort key of a destination box of function f in a batched apply (levels <= 15).
 __device__ __forceinline__ uint64_t batched_key(int f, int n, int64_t x, int64_t y, int64_t z) {
@@ -221,22 +244,32 @@ __global__ void __launch_bounds__(256, LEARNED ? 1 : 2) screen_kernel(ScreenArgs
     }
     __syncwarp();
   }
-  // |c_m| of this lane's terms (m = 32 j + lane)
-  double cabs[4];
+  // log2 |c_m| of this lane's terms (m = 32 j + lane), log2 of the box norm
+  float lcm[4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) cabs[j] = 32 * j + lane < a.M ? fabs(a.c[32 * j + lane]) : 0.0;
+  for (int j = 0; j < 4; ++j) lcm[j] = a.lfilter && 32 * j + lane < a.M ? a.lc[32 * j + lane] : 0.f;
+  const float lsn = sn > 0.0 ? (float)log2(sn) : -INFINITY;
+  const float *lNl = a.lfilter ? a.lN + a.level_off[n] : nullptr;
+  // the bounds of terms the filter drops, as an FP32 sum per lane, and how many (its rounding
+  // bound: a sum of n non-negative FP32 terms is within (n - 1) 2^-24 of its value)
+  float skipped32 = 0.f;
+  int n32 = 0;
+  // the FP64 bound (((|c_m| N_x) N_y) N_z) |s_b|, in the oracle's order
+  auto bound64 = [&](int m, int lx, int ly, int lz) {
+    return fabs(a.c[m]) * Nl[m * nl + lx + Dop] * Nl[m * nl + ly + Dop] * Nl[m * nl + lz + Dop] * sn;
+  };
   int d;
   for (d = 0; d <= D; ++d) {
     int any = 0;
     for (int lx = -d; lx <= d; ++lx)
       for (int ly = -d; ly <= d; ++ly) {
         if (x + lx < 0 || x + lx >= nb || y + ly < 0 || y + ly >= nb) continue;
-        // the bound is (((|c_m| N_x) N_y) N_z) |s_b|: its first two products hold for every l_z
-        double qxy[4];
+        // log2 of the bound's first three factors, the same for every l_z
+        float lq[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int m = 32 * j + lane;
-          qxy[j] = m < a.M ? cabs[j] * Nl[m * nl + lx + Dop] * Nl[m * nl + ly + Dop] : 0.0;
+          lq[j] = a.lfilter && m < a.M ? (lcm[j] + lNl[m * nl + lx + Dop]) + lNl[m * nl + ly + Dop] : 0.f;
         }
         for (int lz = -d; lz <= d; ++lz) {
           int m_inf = max(abs(lx), max(abs(ly), abs(lz)));
@@ -255,10 +288,29 @@ __global__ void __launch_bounds__(256, LEARNED ? 1 : 2) screen_kernel(ScreenArgs
             const int m = m0 + lane;
             bool keep = false;
             double B = 0.0;
+            bool have_B = false;   // B holds the FP64 bound
+            float b_up = 0.f;      // an upper bound of the bound, where the filter dropped the term
             bool dropped_by_model = false;
             if (m < a.M) {
-              B = qxy[j] * Nl[m * nl + lz + Dop] * sn;
-              keep = a.screen == MRA_SCREEN_NONE ? true : (B >= a.tau);
+              if (a.screen == MRA_SCREEN_NONE) {
+                keep = true;
+              } else {
+                bool decided = false;
+                if (a.lfilter) {
+                  const float lb = (lq[j] + lNl[m * nl + lz + Dop]) + lsn;
+                  if (lb >= a.ltau_hi) {
+                    keep = decided = true;
+                  } else if (lb < a.ltau_lo) {
+                    decided = true;
+                    b_up = fmaxf(exp2f(lb + SCREEN_LMARGIN), 1.5e-45f);
+                  }
+                }
+                if (!decided) {
+                  B = bound64(m, lx, ly, lz);
+                  have_B = true;
+                  keep = B >= a.tau;
+                }
+              }
               if (keep && mlp) {
                 const int q = lx * lx + ly * ly + lz * lz;
                 bool dr;
@@ -271,6 +323,7 @@ __global__ void __launch_bounds__(256, LEARNED ? 1 : 2) screen_kernel(ScreenArgs
                 if (dr) {
                   keep = false;
                   dropped_by_model = true;
+                  if (!have_B) B = bound64(m, lx, ly, lz);
                 }
               }
             }
@@ -279,7 +332,14 @@ __global__ void __launch_bounds__(256, LEARNED ? 1 : 2) screen_kernel(ScreenArgs
                 learned += __popc(__ballot_sync(0xffffffffu, dropped_by_model));
                 if (dropped_by_model) lbound += B;
               }
-              if (m < a.M && !keep && !dropped_by_model) skipped += B;
+              if (m < a.M && !keep && !dropped_by_model) {
+                if (have_B) {
+                  skipped += B;
+                } else {
+                  skipped32 += b_up;
+                  ++n32;
+                }
+              }
             }
             unsigned bal = __ballot_sync(0xffffffffu, keep);
             mask[j >> 1] |= (uint64_t)bal << (m0 & 63);
@@ -307,6 +367,7 @@ __global__ void __launch_bounds__(256, LEARNED ? 1 : 2) screen_kernel(ScreenArgs
       }
     if (a.stencil == MRA_STENCIL_SHELLS && !any) break;
   }
+  skipped += (double)skipped32 * (1.0 + n32 * 0x1p-24);
   skipped = warp_sum(skipped);
   lbound = warp_sum(lbound);
   if (lane == 0) {
@@ -599,12 +660,12 @@ int64_t apply_max_records(const Operator &op, const mra_apply_opts &o, int64_t n
 //   per destination (<= records): dest key, seg (+1)
 //   CUB temp storage (max over scan / sort / reduce needs)
 struct Layout {
-  size_t snorm, dstop, cnt, off, kept, screened, skipped, trunc, learned, lbound, bmask;
+  size_t snorm, dstop, cnt, off, kept, screened, skipped, trunc, learned, lbound, bmask, ltab;
   size_t rkey, rsrc, rl, rmask, skey, pin, pout, head, did, dkey, seg, ndest, dfunc, fnoff, lev, split, tmp;
   size_t split_bytes, tmp_bytes, total;
 };
 
-static Layout make_layout(int64_t n_in, int64_t P, int dmax, bool src_path = false) {
+static Layout make_layout(int64_t n_in, int64_t P, int dmax, int64_t n_tab, bool src_path = false) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -625,6 +686,7 @@ static Layout make_layout(int64_t n_in, int64_t P, int dmax, bool src_path = fal
   L.lbound = take(nb * 8);
   const int64_t S = 2 * (int64_t)dmax + 1;
   L.bmask = take(nb * S * S * S * 16);
+  L.ltab = take((size_t)n_tab * 4);
   L.rkey = take(np * 8);
   L.rsrc = take(np * 4);
   L.rl = take(np * 4);
@@ -676,7 +738,7 @@ bool apply_uses_src_path(const Operator &op, const mra_apply_opts &o) {
 }
 
 size_t apply_workspace_bytes(const Operator &op, const mra_apply_opts &o, int64_t n_in) {
-  return make_layout(n_in, apply_max_records(op, o, n_in), apply_max_disp(op, o),
+  return make_layout(n_in, apply_max_records(op, o, n_in), apply_max_disp(op, o), op.n_blocks + op.M,
                      apply_uses_src_path(op, o)).total;
 }
 
@@ -687,6 +749,7 @@ struct WsPtrs {
   int64_t *cnt, *off, *bkept, *bscr, *blearned;
   double *bskip, *blbound;
   uint64_t *bmask;
+  float *ltab;
   int *btrunc;
   uint64_t *rkey, *skey, *rmask, *dkey;
   int *rsrc, *rl, *pin, *pout, *head, *did;
@@ -712,6 +775,7 @@ static WsPtrs carve(const Layout &L, void *ws) {
   p.blearned = (int64_t *)(w + L.learned);
   p.blbound = (double *)(w + L.lbound);
   p.bmask = (uint64_t *)(w + L.bmask);
+  p.ltab = (float *)(w + L.ltab);
   p.rkey = (uint64_t *)(w + L.rkey);
   p.skey = (uint64_t *)(w + L.skey);
   p.rsrc = (int *)(w + L.rsrc);
@@ -760,6 +824,18 @@ static int screen_run(const Operator &op, const mra_tree_view &in, const mra_app
   a.dmax = apply_max_disp(op, o);
   a.screen = o.screen == MRA_SCREEN_LEARNED ? MRA_SCREEN_NORM : o.screen;
   a.tau = o.tau;
+  // the log2 filter, where a norm screen runs with a threshold log2 can represent
+  a.lfilter = a.screen != MRA_SCREEN_NONE && o.tau > 0.0 && std::isfinite(std::log2(o.tau)) ? 1 : 0;
+  if (a.lfilter) {
+    const double lt = std::log2(o.tau);
+    a.ltau_hi = (float)(lt + SCREEN_LMARGIN);
+    a.ltau_lo = (float)(lt - SCREEN_LMARGIN);
+    a.lN = w.ltab;
+    a.lc = w.ltab + op.n_blocks;
+    screen_log_tables_kernel<<<counted((unsigned)std::min<int64_t>((op.n_blocks + op.M + 255) / 256, 1024)), 256, 0,
+                               s>>>(op.n_blocks, op.M, op.d_N, op.d_c, w.ltab);
+    MRA_CUDA_TRY(cudaGetLastError());
+  }
   a.dstop = w.dstop;
   a.cnt = w.cnt;
   a.off = w.off;
@@ -876,7 +952,7 @@ int apply_run(const Operator &op, const mra_tree_view &in, const mra_apply_opts 
   const int64_t n_in = in.n;
   const int64_t Pmax = apply_max_records(op, o, n_in);
   const bool src_path = apply_uses_src_path(op, o);
-  Layout L = make_layout(n_in, Pmax, apply_max_disp(op, o), src_path);
+  Layout L = make_layout(n_in, Pmax, apply_max_disp(op, o), op.n_blocks + op.M, src_path);
   if (ws_bytes < L.total)
     return fail(MRA_ERR_CAPACITY, "mra_apply: workspace of %zu bytes < %zu needed", ws_bytes, L.total);
   WsPtrs W = carve(L, ws);
@@ -1151,7 +1227,7 @@ int log_terms_run(const Operator &op, const mra_tree_view &in, const mra_apply_o
   const int64_t n_in = in.n;
   if (n_in == 0 || max_terms <= 0) return MRA_OK;
   const int64_t Pmax = apply_max_records(op, o, n_in);
-  Layout L = make_layout(n_in, Pmax, apply_max_disp(op, o));
+  Layout L = make_layout(n_in, Pmax, apply_max_disp(op, o), op.n_blocks + op.M);
   if (ws_bytes < L.total)
     return fail(MRA_ERR_CAPACITY, "mra_log_terms: workspace of %zu bytes < %zu needed", ws_bytes, L.total);
   WsPtrs W = carve(L, ws);
